@@ -1,0 +1,337 @@
+"""Pins for the oracle's branch and bound (Algorithm 1 with Alg. 2-5) against
+closed forms, brute force, the cut-off corollary (Cor. 2) and the paper's
+printed benchmark optima (Appendix A; Table I)."""
+import numpy as np
+import pytest
+import sympy as sp
+from numpy.polynomial import polynomial as npoly
+
+import oracle
+from paper_2003_01758_b300 import workloads as W
+from tests import benchmarks
+
+
+def poly_from_sympy(expr, syms, degree):
+    out = np.zeros(tuple(d + 1 for d in degree))
+    for m, c in sp.Poly(sp.expand(expr), *syms).terms():
+        out[m] += float(c)
+    return out
+
+
+def grid_points(lo, hi, n):
+    axes = [np.linspace(a, b, n) for a, b in zip(lo, hi)]
+    return np.stack(np.meshgrid(*axes, indexing="ij"), -1).reshape(-1, len(lo))
+
+
+def eval_many(a, x):
+    if a.ndim == 2:
+        return npoly.polyval2d(x[:, 0], x[:, 1], a)
+    if a.ndim == 3:
+        return npoly.polyval3d(x[:, 0], x[:, 1], x[:, 2], a)
+    raise NotImplementedError
+
+
+def lipschitz_bound(a, lo, hi):
+    """Upper bound of the gradient norm of a on the box from coefficient sums."""
+    l = a.ndim
+    m = np.maximum(np.abs(lo), np.abs(hi))
+    total = 0.0
+    for r in range(l):
+        s = 0.0
+        for J in np.ndindex(*a.shape):
+            if J[r] == 0:
+                continue
+            term = abs(a[J]) * J[r]
+            for q in range(l):
+                term *= m[q] ** (J[q] - (1 if q == r else 0))
+            s += term
+        total += s * s
+    return float(np.sqrt(total))
+
+
+# --------------------------------------------------------------------------
+# closed forms
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("c", [(0.3, -0.45), (-0.81, 0.123), (0.0, 0.0)])
+def test_separable_quadratic_closed_form(c):
+    x1, x2 = sp.symbols("x1 x2")
+    a = poly_from_sympy((x1 - c[0]) ** 2 + 3 * (x2 - c[1]) ** 2, (x1, x2), (2, 2))
+    res = oracle.solve(a, None, None, [-1, -1], [1, 1], opt_tol=1e-6, max_iters=40)
+    assert res["status"] == oracle.OPTIMAL
+    assert res["lower"] <= 0.0 <= res["upper"]
+    assert res["upper"] - res["lower"] <= 1e-6
+    assert np.abs(res["x"] - np.array(c)).max() < 2e-3
+
+
+def test_quartic_sum_closed_form():
+    """p = sum_r q_r(x_r) with 1-D quartics; p* = sum of the 1-D minima, found
+    from the real roots of q_r' by numpy."""
+    rng = np.random.default_rng(7)
+    qs = []
+    for _ in range(2):
+        roots = np.sort(rng.uniform(-0.8, 0.8, 2))
+        q = npoly.polymul(npoly.polyfromroots(roots), npoly.polyfromroots(roots))
+        q = npoly.polyadd(q, [0.0, rng.uniform(-0.05, 0.05)])
+        qs.append(q)
+    best = 0.0
+    for q in qs:
+        crit = npoly.polyroots(npoly.polyder(q))
+        crit = np.concatenate([crit[np.abs(crit.imag) < 1e-12].real, [-1.0, 1.0]])
+        crit = crit[(crit >= -1) & (crit <= 1)]
+        best += npoly.polyval(crit, q).min()
+    a = np.zeros((5, 5))
+    a[:, 0] += qs[0]
+    a[0, :] += qs[1]
+    res = oracle.solve(a, None, None, [-1, -1], [1, 1], opt_tol=1e-7, max_iters=40)
+    assert res["status"] == oracle.OPTIMAL
+    assert res["lower"] - 1e-12 <= best <= res["upper"] + 1e-12
+
+
+def test_equality_circle_closed_form():
+    """min x1 + x2 s.t. x1^2 + x2^2 - 1 = 0: p* = -sqrt(2).  With eq_tol e the
+    relaxed feasible set gives p_up >= -sqrt(2 (1 + e))."""
+    x1, x2 = sp.symbols("x1 x2")
+    cost = poly_from_sympy(x1 + x2, (x1, x2), (1, 1))
+    h = poly_from_sympy(x1 ** 2 + x2 ** 2 - 1, (x1, x2), (2, 2))[None]
+    e = 1e-3
+    res = oracle.solve(cost, None, h, [-2, -2], [2, 2], opt_tol=1e-3, eq_tol=e, max_iters=30)
+    assert res["status"] == oracle.OPTIMAL
+    assert res["lower"] <= -np.sqrt(2) + 1e-12
+    assert res["upper"] >= -np.sqrt(2 * (1 + e)) - 1e-12
+    assert abs(x1.subs(x1, 0)) == 0  # keep sympy import honest
+    xs = res["x"]
+    assert abs(xs[0] ** 2 + xs[1] ** 2 - 1) <= e + 1e-9
+
+
+def test_certified_infeasible():
+    x1, x2 = sp.symbols("x1 x2")
+    cost = poly_from_sympy(x1 * x2, (x1, x2), (1, 1))
+    g = np.stack([poly_from_sympy(x1 - sp.Rational(1, 5), (x1, x2), (1, 1)),
+                  poly_from_sympy(sp.Rational(3, 10) - x1, (x1, x2), (1, 1))])
+    res = oracle.solve(cost, g, None, [-1, -1], [1, 1])
+    assert res["status"] == oracle.INFEASIBLE
+    assert np.isnan(res["x"]).all()
+    g2 = poly_from_sympy(1 + x1 ** 2 + x2 ** 2, (x1, x2), (2, 2))[None]
+    res2 = oracle.solve(cost, g2, None, [-1, -1], [1, 1])
+    assert res2["status"] == oracle.INFEASIBLE and res2["steps"] == 2
+
+
+# --------------------------------------------------------------------------
+# brute force on small random problems
+# --------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [1000, 1001, 1002, 1003, 1005])
+def test_tiny_against_grid_brute_force(seed):
+    p = W.tiny(seed)
+    tol = 1e-3
+    res = oracle.solve(p.cost, p.ineq, p.eq, p.lo, p.hi, opt_tol=tol)
+    assert res["status"] == oracle.OPTIMAL
+    n = 401
+    x = grid_points(p.lo, p.hi, n)
+    pv = eval_many(p.cost, x)
+    gv = np.max(np.stack([eval_many(g, x) for g in p.ineq]), axis=0)
+    h = (p.hi[0] - p.lo[0]) / (n - 1)
+    rad = h * np.sqrt(2) / 2
+    Lp = lipschitz_bound(p.cost, p.lo, p.hi)
+    Lg = max(lipschitz_bound(g, p.lo, p.hi) for g in p.ineq)
+    # every feasible grid point bounds p* from above, so p_lo cannot exceed it
+    assert res["lower"] <= pv[gv <= 0].min() + 1e-12
+    # p* is attained at a feasible point within rad of a grid point whose
+    # constraints are at most Lg*rad: p* >= min over those of p - Lp*rad
+    near = pv[gv <= Lg * rad].min() - Lp * rad
+    assert res["upper"] >= near - 1e-12
+    assert res["upper"] - res["lower"] <= tol
+    # the returned point is feasible
+    assert max(oracle.eval_monomial(g, res["x"]) for g in p.ineq) <= 1e-12
+
+
+def test_rtd_against_grid_brute_force():
+    p = W.rtd(2000, n_obstacles=64)
+    res = oracle.solve(p.cost, p.ineq, p.eq, p.lo, p.hi, opt_tol=1e-3)
+    assert res["status"] == oracle.OPTIMAL
+    x = grid_points(p.lo, p.hi, 301)
+    pv = eval_many(p.cost, x)
+    gv = np.max(np.stack([eval_many(g, x) for g in p.ineq]), axis=0)
+    assert res["lower"] <= pv[gv <= 0].min() + 1e-12
+    assert max(oracle.eval_monomial(g, res["x"]) for g in p.ineq) <= 1e-12
+    assert res["lower"] <= oracle.eval_monomial(p.cost, res["x"]) <= res["upper"]
+
+
+# --------------------------------------------------------------------------
+# run behaviour: Cor. 2, monotone bounds, Alg. 5 bookkeeping, caps
+# --------------------------------------------------------------------------
+
+def test_minimiser_box_never_eliminated():
+    """Cor. 2: some item always contains the global minimiser."""
+    x1, x2 = sp.symbols("x1 x2")
+    c = np.array([0.3125 + 1e-3, -0.6 + 2e-3])  # not on a dyadic grid line
+    a = poly_from_sympy((x1 - c[0]) ** 2 + (x2 - c[1]) ** 2 + x1 * x2 / 10 - c[0] * x2 / 10
+                        - c[1] * x1 / 10, (x1, x2), (2, 2))
+    # the minimiser of this strictly convex quadratic, solved with numpy
+    H = np.array([[2.0, 0.1], [0.1, 2.0]])
+    g0 = np.array([-2 * c[0] - c[1] / 10, -2 * c[1] - c[0] / 10])
+    xstar = np.linalg.solve(H, -g0)
+    s = oracle.Solver(a, None, None, [-1, -1], [1, 1])
+    while True:
+        st = s.step(opt_tol=1e-8, max_iters=25)
+        L = s.get_list()
+        w = 2.0 / 2.0 ** L["level"]
+        lo = -1 + L["index"] * w
+        inside = np.all((lo <= xstar) & (xstar <= lo + w), axis=1)
+        assert inside.any()
+        if st != oracle.RUNNING:
+            break
+
+
+@pytest.mark.parametrize("maker,seed", [(W.tiny, 1000), (W.tiny, 1004), (W.rtd, 2001)])
+def test_bounds_are_monotone(maker, seed):
+    p = maker(seed)
+    res = oracle.solve(p.cost, p.ineq, p.eq, p.lo, p.hi, opt_tol=1e-4)
+    tr = res["trace"]
+    up, lo = tr[:, 2], tr[:, 3]
+    fin = np.isfinite(up)
+    assert np.all(np.diff(up[fin]) <= 0)
+    assert np.all(np.diff(lo) >= 0)
+    assert np.all(lo[fin] <= up[fin])
+
+
+def test_eliminate_keeps_exactly_the_saved_items_in_paper_order():
+    """Alg. 5: kept items below K_save stay put; each hole below K_save is
+    filled from the top of the save list."""
+    p = W.tiny(1002)
+    s = oracle.Solver(p.cost, p.ineq, p.eq, p.lo, p.hi)
+    for _ in range(9):
+        before = s.get_list()
+        K = before["cost"].shape[0]
+        st = s.step(opt_tol=1e-9)
+        if st != oracle.RUNNING:
+            break
+        r = int(np.argmax(s.get_list()["level"] - before["level"]))
+        kids = []
+        for k in range(K):
+            kids.append(oracle.subdivide_patch(before["cost"][k], r))
+        children = [kd[0] for kd in kids] + [kd[1] for kd in kids]
+        keep = s.get_keep(2 * K).astype(bool)
+        save = np.flatnonzero(keep)
+        K_save = len(save)
+        order = list(range(2 * K))
+        holes = [k for k in range(K_save) if not keep[k]]
+        for j, hole in enumerate(holes):
+            order[hole] = save[K_save - 1 - j]
+        after = s.get_list()
+        assert after["cost"].shape[0] == K_save
+        for k in range(K_save):
+            assert np.array_equal(after["cost"][k], children[order[k]])
+
+
+def test_memcap_and_maxiter():
+    p = W.rtd(2002, n_obstacles=32)
+    res = oracle.solve(p.cost, p.ineq, p.eq, p.lo, p.hi, max_items=16)
+    assert res["status"] == oracle.MEMCAP
+    assert res["peak_items"] <= 16
+    assert res["lower"] <= res["upper"] or not np.isfinite(res["upper"])
+    res = oracle.solve(p.cost, p.ineq, p.eq, p.lo, p.hi, max_iters=3)
+    assert res["status"] == oracle.MAXITER
+    assert res["steps"] == (3 - 1) * 2 and res["sweeps"] == 3
+
+
+# --------------------------------------------------------------------------
+# the paper's benchmark problems (Appendix A, Table I)
+# --------------------------------------------------------------------------
+
+def paper_eps(cost, lo, hi):
+    """Eq. (benchmarking_epsilon): eps = 1e-7 (max B(U) - min B(U))."""
+    b = oracle.bernstein_from_monomial(cost, lo, hi)
+    return 1e-7 * (b.max() - b.min())
+
+
+@pytest.mark.parametrize("name", ["P1", "P2", "P3", "P4", "P6"])
+def test_benchmark_brackets_printed_optimum(name):
+    p = benchmarks.load(name)
+    eps = paper_eps(p["cost"], p["lo"], p["hi"])
+    res = oracle.solve(p["cost"], p["ineq"], p["eq"], p["lo"], p["hi"], opt_tol=eps,
+                       max_iters=28, max_items=1 << 22)
+    assert res["status"] == oracle.OPTIMAL
+    slack = 1e-6 * max(1.0, abs(p["optimum"]))
+    assert res["lower"] - slack <= p["optimum"] <= res["upper"] + slack
+    # 22-28 iterations in Table I; here the count of sweeps n at return
+    assert 20 <= res["sweeps"] <= 28
+
+
+def test_p8_brackets_cost_at_printed_location():
+    """P8's printed value (42.4440570797) disagrees with the cost at its own
+    printed location (42.66699797...); the interval must hold the latter."""
+    p = benchmarks.load("P8")
+    v = oracle.eval_monomial(p["cost"], p["x_opt"])
+    eps = paper_eps(p["cost"], p["lo"], p["hi"])
+    res = oracle.solve(p["cost"], p["ineq"], p["eq"], p["lo"], p["hi"], opt_tol=eps,
+                       max_iters=28, max_items=1 << 22)
+    assert res["status"] == oracle.OPTIMAL
+    assert res["lower"] - 1e-6 * v <= v <= res["upper"] + 1e-6 * v
+    assert abs(v - p["optimum"]) > 0.2
+
+
+def test_p5_as_printed_is_certified_infeasible():
+    """P5 as printed needs |f1| <= x3 and |f2| <= x3 with f1 - f2 = 8 - 16 x1;
+    a brute-force grid finds no point with max(|f1|, |f2|) <= 5 in the box,
+    and the oracle certifies infeasibility."""
+    p = benchmarks.load("P5")
+    x = grid_points(p["lo"][:2], p["hi"][:2], 801)
+    f1 = 2 * x[:, 0] ** 2 + 4 * x[:, 0] * x[:, 1] - 42 * x[:, 0] + 4 * x[:, 0] ** 3 - 14
+    f2 = 2 * x[:, 0] ** 2 + 4 * x[:, 0] * x[:, 1] - 26 * x[:, 0] + 4 * x[:, 0] ** 3 - 22
+    assert np.maximum(np.abs(f1), np.abs(f2)).min() > 5.0 + 1.0
+    res = oracle.solve(p["cost"], p["ineq"], p["eq"], p["lo"], p["hi"], opt_tol=1e-6)
+    assert res["status"] == oracle.INFEASIBLE
+
+
+def test_p7_with_equality_tolerance():
+    p = benchmarks.load("P7")
+    res = oracle.solve(p["cost"], p["ineq"], p["eq"], p["lo"], p["hi"], opt_tol=1e-3,
+                       eq_tol=0.1, max_iters=28, max_items=1 << 20)
+    assert res["status"] == oracle.OPTIMAL
+    assert res["lower"] <= p["optimum"] + 1e-9
+    assert res["upper"] - res["lower"] <= 1e-3
+    assert abs(oracle.eval_monomial(p["eq"][0], res["x"])) <= 0.1 + 1e-9
+
+
+def test_p4_list_length_follows_fig3():
+    """Fig. 3: on P4 the list peaks early (iteration 5 in the paper), then stays
+    under 400 patches from iteration 9 on; the run takes about 24 iterations."""
+    p = benchmarks.load("P4")
+    eps = paper_eps(p["cost"], p["lo"], p["hi"])
+    res = oracle.solve(p["cost"], p["ineq"], p["eq"], p["lo"], p["hi"], opt_tol=eps,
+                       max_iters=28)
+    K = res["trace"][:, 0]
+    per_sweep = [K[i:i + 3].max() for i in range(0, len(K), 3)]
+    peak = int(np.argmax(per_sweep)) + 1
+    assert 4 <= peak <= 7
+    assert max(per_sweep[9:]) < 400
+    assert 23 <= res["sweeps"] <= 26
+
+
+@pytest.mark.parametrize("name", ["Beale", "Bukin02"])
+def test_increasing_constraint_objectives_unconstrained(name):
+    p = benchmarks.load(name)
+    eps = 1e-7 * max(1.0, abs(p["optimum"]))
+    res = oracle.solve(p["cost"], p["ineq"], p["eq"], p["lo"], p["hi"], opt_tol=eps,
+                       max_iters=40, max_items=1 << 22)
+    assert res["status"] in (oracle.OPTIMAL, oracle.MAXITER)
+    slack = 1e-6 * max(1.0, abs(p["optimum"]))
+    assert res["lower"] - slack <= p["optimum"] <= res["upper"] + slack
+
+
+def test_evd_shows_plain_fp64_conditioning_limit():
+    """On [-100,100]^2 the E-V-D root patch reaches ~1e12, so plain FP64
+    rounding of the Bernstein coefficients (as in the paper's method, which has
+    no rounding control) moves the interval by ~1e-3: the printed optimum then
+    sits just outside [p_lo, p_up], by no more than the FP64 rounding scale
+    of the root patch.  The directed-rounding FP32 mode of the CUDA library
+    carries an explicit error bound for exactly this reason."""
+    p = benchmarks.load("EVD")
+    b = oracle.bernstein_from_monomial(p["cost"], p["lo"], p["hi"])
+    scale = np.abs(b).max() * 2.0 ** -53
+    res = oracle.solve(p["cost"], p["ineq"], p["eq"], p["lo"], p["hi"],
+                       opt_tol=1e-7 * p["optimum"], max_iters=40, max_items=1 << 22)
+    miss = max(res["lower"] - p["optimum"], p["optimum"] - res["upper"], 0.0)
+    assert miss <= 1e3 * scale
