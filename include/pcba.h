@@ -1,0 +1,211 @@
+/*
+ * pcba.h - C ABI of libpcba.so, a B300 (sm_103a) implementation of the
+ * Parallel Constrained Bernstein Algorithm (PCBA) of
+ * "Safe, Optimal, Real-time Trajectory Planning with a Parallel Constrained
+ * Bernstein Algorithm" (arXiv 2003.01758).
+ *
+ * The library solves polynomial optimisation problems (POPs, Eq. (P)):
+ *
+ *     min p(x)   s.t.  g_i(x) <= 0 (i = 1..alpha),  h_j(x) = 0 (j = 1..beta),
+ *     x in the box D = [lo_1, hi_1] x ... x [lo_l, hi_l],
+ *
+ * by the branch and bound of Algorithm 1: every surviving box of the list is
+ * bisected (Alg. 2), every Bernstein patch is bounded by the min and max of its
+ * coefficients (Thm. 1, Alg. 3), the solution estimate p_up is the least upper
+ * bound over feasible items (Def. 4), infeasible and suboptimal items are cut
+ * off (Def. 3, Def. 5, Thm. 3, Alg. 4) and the list is compacted in place
+ * (Alg. 5).  The result is a certified interval [lower, upper] on the optimum
+ * and a point whose box achieved the upper bound.
+ *
+ * Conventions
+ *   - Every function returns 0 on success or a negative PCBA_ERR_* code;
+ *     pcba_last_error() then gives a static, thread-local message.
+ *   - Host arrays passed in are copied; the caller keeps ownership.  A handle
+ *     owns its device memory until pcba_destroy.
+ *   - A non-negative result.status is a solver outcome, not an error.
+ *   - Polynomials are dense monomial tensors in row-major order, axis 0
+ *     slowest: coeff[j_1 (N_2+1)...(N_l+1) + ... + j_l] multiplies
+ *     x_1^j_1 ... x_l^j_l (Sec. II-A, Eq. (poly_monomial_basis)).
+ *   - One handle is used by one host thread at a time.
+ *   - l <= PCBA_MAX_DIM, every multi-degree entry <= PCBA_MAX_DEGREE, and a
+ *     patch has at most PCBA_MAX_PATCH coefficients; larger inputs are
+ *     rejected with PCBA_ERR_INVALID.
+ */
+#ifndef PCBA_H_
+#define PCBA_H_
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PCBA_MAX_DIM 8
+#define PCBA_MAX_DEGREE 16
+#define PCBA_MAX_PATCH 8192
+
+/* Solver outcomes (result.status) and error codes (return values). */
+enum {
+  PCBA_OPTIMAL = 0,      /* p_up - p_lo <= opt_tol (Alg. 1 line 9, Def. 2)      */
+  PCBA_INFEASIBLE = 1,   /* every item infeasible: certified (Alg. 1 line 8)    */
+  PCBA_MEMCAP = 2,       /* 2 * length(L) > M (Alg. 1 line 4); best so far      */
+  PCBA_MAXITER = 3,      /* the sweep counter reached max_iters (Alg. 1 line 11) */
+  PCBA_STEPLIMIT = 5,    /* stopped after max_steps steps (pcba_solve_steps)     */
+  PCBA_ERR_INVALID = -1, /* bad argument                                         */
+  PCBA_ERR_CUDA = -2,    /* a CUDA runtime call failed                           */
+  PCBA_ERR_OOM = -3,     /* device allocation failed                             */
+  PCBA_ERR_DEVICE_TIMEOUT = -4 /* the device loop hit its step guard             */
+};
+
+/* Arithmetic of the list (pcba_create 'precision'). */
+enum {
+  PCBA_FP64 = 64, /* plain IEEE double patches, no rounding control, as the
+                     paper's method; bit-for-bit reproducible                   */
+  PCBA_FP32 = 32  /* float patches with a per-patch error bound kept with
+                     directed rounding, so every bound encloses the exact range
+                     (Thm. 1 holds for the stored patches); the root patches are
+                     converted in FP64 and the returned point is checked in FP64 */
+};
+
+typedef struct pcba_handle pcba_handle;
+typedef struct pcba_batch pcba_batch;
+
+/* A polynomial in nvars variables of multi-degree degree[0..nvars) (Def. 1),
+ * coefficient tensor of prod(degree[r]+1) doubles. */
+typedef struct {
+  int nvars;
+  const int* degree;
+  const double* coeff;
+} pcba_poly;
+
+/* The box domain D (Sec. II-A); lo[r] < hi[r]. */
+typedef struct {
+  int nvars;
+  const double* lo;
+  const double* hi;
+} pcba_box;
+
+/* One solve's outcome. */
+typedef struct {
+  int status;               /* PCBA_OPTIMAL .. PCBA_STEPLIMIT                      */
+  int steps;                /* bisection steps done (one direction each)           */
+  int sweeps;               /* iteration counter n of Alg. 1 at return             */
+  int from_warm_start;      /* 1 if 'upper' and 'x' come from a certified warm point */
+  double lower;             /* certified lower bound p_lo (Alg. 4; +inf if none)   */
+  double upper;             /* solution estimate p_up (Def. 4; +inf if no feasible item) */
+  double x[PCBA_MAX_DIM];   /* returned point: centre of the box achieving 'upper' */
+  double box_lo[PCBA_MAX_DIM], box_hi[PCBA_MAX_DIM]; /* that box (Alg. 1 line 12)  */
+  long long peak_items;     /* largest list length 2K reached                      */
+  long long peak_bytes;     /* peak_items * stored bytes per item                  */
+  double verify_cost;       /* p(x) evaluated in FP64                              */
+  double verify_max_g;      /* max_i g_i(x) + its FP64 rounding bound              */
+  double verify_max_abs_h;  /* max_j |h_j(x)| + its FP64 rounding bound            */
+  double time_ms;           /* device time from the batch start to this problem's end */
+} pcba_result;
+
+/* Builds a problem: cost p (Eq. (P)), n_ineq inequality constraints g_i <= 0,
+ * n_eq equality constraints h_j = 0 and the box.  All polynomials must have
+ * box->nvars variables.  Each constraint family is zero-padded to one common
+ * multi-degree G (resp. H), which leaves the polynomials unchanged (Sec. IV-C,
+ * Eq. (memory_per_item)).  precision is PCBA_FP64 or PCBA_FP32.  The monomial
+ * coefficients are copied to the device; the monomial-to-Bernstein conversion
+ * (Sec. II-D, Alg. 1 line 1) runs on the device at the start of every solve. */
+int pcba_create(pcba_handle** out, const pcba_poly* cost, const pcba_poly* ineq,
+                int n_ineq, const pcba_poly* eq, int n_eq, const pcba_box* box,
+                int precision);
+
+/* As pcba_create, but the coefficient tensors already hold Bernstein patches
+ * over 'box' (Eq. (BF)); the conversion step is skipped.  Used to start the
+ * branch and bound from given patches. */
+int pcba_create_bernstein(pcba_handle** out, const pcba_poly* cost, const pcba_poly* ineq,
+                          int n_ineq, const pcba_poly* eq, int n_eq, const pcba_box* box,
+                          int precision);
+
+/* Runs Algorithm 1 to completion on one problem.
+ *   opt_tol   optimality tolerance epsilon > 0 (Def. 2): stop when p_up - p_lo <= opt_tol
+ *   eq_tol    equality tolerance epsilon_eq > 0 (Def. 2, Def. 3 (b))
+ *   max_iters N of Alg. 1: the solve ends with PCBA_MAXITER when the sweep
+ *             counter n reaches N, i.e. after (N-1) l steps at most
+ *   mem_cap   bytes of list storage; M = floor(mem_cap / bytes per item)
+ *             (Eq. (memory_per_item) as stored here, see pcba_item_bytes)
+ * Blocks until the result is on the host.  Returns 0 or a PCBA_ERR_* code. */
+int pcba_solve(pcba_handle* h, double opt_tol, double eq_tol, int max_iters,
+               size_t mem_cap, pcba_result* out);
+
+/* As pcba_solve, but stops after at most max_steps steps (status
+ * PCBA_STEPLIMIT if the solve was not over); the list stays on the device and
+ * can be read with pcba_get_list.  The cut-off bookkeeping of the last step
+ * (Alg. 5) is complete when it returns. */
+int pcba_solve_steps(pcba_handle* h, double opt_tol, double eq_tol, int max_iters,
+                     size_t mem_cap, int max_steps, pcba_result* out);
+
+/* Solves n independent problems together on the device: each keeps its own
+ * list, incumbent and status, and all advance one bisection step per
+ * iteration of one device loop.  All handles must share the precision.
+ * mem_cap_total bytes are shared so that every problem gets the same item
+ * capacity M = floor(mem_cap_total / sum of bytes per item).
+ * warm_start is NULL or n * PCBA_MAX_DIM doubles (row k = point of problem k,
+ * first nvars used; a NaN first entry means none); each point is evaluated in
+ * FP64 and, only if it is certified feasible, lowers that problem's p_up to
+ * its certified cost (this never removes a feasible minimiser, Thm. 3).
+ * out receives n results. */
+int pcba_solve_batch(pcba_handle** hs, int n, double opt_tol, double eq_tol, int max_iters,
+                     size_t mem_cap_total, const double* warm_start, pcba_result* out);
+
+/* A reusable batch: device buffers are allocated once and the device loop is
+ * built once, so repeated solves do no allocation.  flags: 0 = device loop in a
+ * CUDA graph with a conditional WHILE node (default); 1 = host loop that reads
+ * one status word per step. */
+int pcba_batch_create(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_total,
+                      int flags);
+int pcba_batch_solve(pcba_batch* b, double opt_tol, double eq_tol, int max_iters,
+                     const double* warm_start, pcba_result* out);
+/* As pcba_batch_solve, but the monomial coefficients of every problem are
+ * first copied from the given pinned or pageable host buffer (the layout of
+ * pcba_batch_input_layout) inside the same stream: the end-to-end call. */
+int pcba_batch_solve_from_host(pcba_batch* b, const double* host_coeffs, double opt_tol,
+                               double eq_tol, int max_iters, const double* warm_start,
+                               pcba_result* out);
+/* Number of doubles pcba_batch_solve_from_host reads. */
+long long pcba_batch_input_doubles(const pcba_batch* b);
+/* Per-step records (K before the step, K_save, p_up, p_lo) of problem k of the
+ * last solve; returns the number of rows written (at most max_rows). */
+int pcba_batch_trace(const pcba_batch* b, int k, double* rows, int max_rows);
+/* Device time in ms of the last solve (CUDA events around the whole device
+ * work on the batch stream), and the kernel-level split used for the roofline:
+ * ms spent in the subdivide/bound kernel and its algorithmic bytes. */
+int pcba_batch_timing(const pcba_batch* b, double* total_ms, double* subdiv_ms,
+                      double* subdiv_bytes, long long* subdiv_launches);
+int pcba_batch_set_stream(pcba_batch* b, void* cuda_stream);
+void pcba_batch_destroy(pcba_batch* b);
+
+/* Copies the list of the last pcba_solve / pcba_solve_steps to the host in the
+ * layout of the oracle: cost[K][cp], ineq[K][alpha][cg], eq[K][beta][ch] as
+ * doubles (FP32 patches are widened, and their stored per-patch error bounds
+ * go to err[K][1 + alpha + beta] if err is not NULL), index[K][nvars] dyadic
+ * box indices and level[nvars].  *K_out = list length.  Any output pointer may
+ * be NULL to skip it; call once with all NULL to learn K. */
+int pcba_get_list(pcba_handle* h, long long* K_out, double* cost, double* ineq, double* eq,
+                  float* err, unsigned* index, int* level);
+
+/* Root Bernstein patches (Alg. 1 line 1) of the problem as computed on the
+ * device in FP64: cost[cp], ineq[alpha][cg], eq[beta][ch]. */
+int pcba_root_patches(pcba_handle* h, double* cost, double* ineq, double* eq);
+
+/* Stored bytes of one list item of this problem (the per-item storage behind
+ * M = floor(mem_cap / bytes)). */
+long long pcba_item_bytes(const pcba_handle* h);
+
+int pcba_set_stream(pcba_handle* h, void* cuda_stream);
+int pcba_set_warm_start(pcba_handle* h, const double* x);  /* NULL clears */
+void pcba_destroy(pcba_handle* h);
+
+const char* pcba_status_string(int status);
+const char* pcba_last_error(void);
+int pcba_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PCBA_H_ */

@@ -1,0 +1,926 @@
+// libpcba: host engine and C ABI (see include/pcba.h).
+//
+// A solve of n problems runs as:
+//   prologue  k1_matrices, k1_convert (Alg. 1 line 1), k_eval (warm start),
+//             k_init (Alg. 1 lines 2-3, first memory test)
+//   loop      k2_subdivide, k3_classify, k4_index, k4_move, k_control, one
+//             bisection step of every running problem per iteration
+//             (Alg. 1 lines 4-11); by default the loop is a CUDA graph with a
+//             conditional WHILE node whose condition k_control sets on the
+//             device, so the host never waits inside the loop
+//   epilogue  k_eval (FP64 check of the returned point), copies to the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "pcba.h"
+#include "pcba_kernels.cuh"
+
+static_assert(PCBA_MAX_DIM == PCBA_MAXD, "dimension limits differ");
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+#define PCBA_CK(call)                                                              \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(PCBA_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// Test hook: PCBA_TEST_FAIL_ALLOC=1 makes every device allocation fail, so the
+// out-of-memory path can be exercised without exhausting a GPU.
+cudaError_t dev_alloc(void** p, size_t bytes) {
+  const char* f = std::getenv("PCBA_TEST_FAIL_ALLOC");
+  if (f && f[0] == '1') {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  if (bytes == 0) bytes = 256;
+  return cudaMalloc(p, bytes);
+}
+
+long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
+
+struct HostProblem {
+  int l = 0, precision = 64, form = 0;
+  int P[PCBA_MAXD] = {0}, G[PCBA_MAXD] = {0}, H[PCBA_MAXD] = {0};
+  int alpha = 0, beta = 0;
+  long long cp = 1, cg = 0, ch = 0;
+  double lo[PCBA_MAXD] = {0}, hi[PCBA_MAXD] = {0};
+  std::vector<double> mono;  // cost | ineq (alpha * cg) | eq (beta * ch)
+};
+
+struct Grids {
+  int sms = 148;
+  int k1_grid = 1, k1_wpb = 1, k1_cmax = 1;
+  size_t k1_smem = 0;
+  int k2_grid = 1;
+  size_t k2_smem = 0;
+  int k3_grid = 1, k4_grid = 1;
+};
+
+}  // namespace
+
+struct pcba_batch {
+  int np = 0;
+  int precision = 64;
+  int flags = 0;
+  std::vector<ProbDesc> desc;
+  std::vector<const HostProblem*> probs;
+  long long mono_doubles = 0;
+  long long M = 0;
+  long long sum_item_bytes = 0;
+  int max_l = 1;
+  // device
+  ProbDesc* d_desc = nullptr;
+  ProbState* d_state = nullptr;
+  Plan* d_plan = nullptr;
+  SolveParams* d_params = nullptr;
+  unsigned* d_pre = nullptr;  // 5 arrays of np+1
+  char* d_arena = nullptr;
+  ChildRec* d_rec = nullptr;
+  unsigned* d_slots = nullptr;  // flagrank | arrive | hole | filler
+  unsigned* d_tilecnt = nullptr;
+  double* d_mono = nullptr;
+  double* d_trace = nullptr;
+  double* d_warm = nullptr;
+  double* d_mat = nullptr;
+  double* d_norm = nullptr;
+  double* d_raw = nullptr;
+  EvalOut* d_eval = nullptr;
+  long long trace_rows_total = 0;
+  // host mirrors (pinned)
+  ProbState* h_state = nullptr;
+  EvalOut* h_eval = nullptr;
+  Plan* h_plan = nullptr;
+  SolveParams* h_params = nullptr;
+  int* h_running = nullptr;
+  // streams and graph
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  cudaStream_t cap_stream = nullptr;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  cudaGraphConditionalHandle cond = 0;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  std::vector<cudaEvent_t> kev;
+  Engine E{};
+  Grids g;
+  // timing of the last solve
+  double total_ms = 0, subdiv_ms = 0, subdiv_bytes = 0;
+  long long subdiv_launches = 0;
+};
+
+struct pcba_handle {
+  HostProblem prob;
+  cudaStream_t stream = nullptr;
+  bool has_warm = false;
+  double warm[PCBA_MAXD];
+  pcba_batch* own = nullptr;
+  size_t own_cap = 0;
+};
+
+namespace {
+
+int check_poly(const pcba_poly* q, int l, const char* what) {
+  if (!q || !q->degree || !q->coeff) return fail(PCBA_ERR_INVALID, std::string(what) + ": null");
+  if (q->nvars != l) return fail(PCBA_ERR_INVALID, std::string(what) + ": nvars differs from box");
+  long long c = 1;
+  for (int r = 0; r < l; ++r) {
+    if (q->degree[r] < 0 || q->degree[r] > PCBA_MAX_DEGREE)
+      return fail(PCBA_ERR_INVALID, std::string(what) + ": degree out of range");
+    c *= q->degree[r] + 1;
+  }
+  if (c > PCBA_MAX_PATCH) return fail(PCBA_ERR_INVALID, std::string(what) + ": patch too large");
+  return 0;
+}
+
+// Copies a polynomial of multi-degree deg into a tensor of multi-degree big
+// (zero padding = degree elevation of the tensor, the polynomial is unchanged).
+void embed(const pcba_poly* q, int l, const int* big, double* out) {
+  long long total = 1;
+  for (int r = 0; r < l; ++r) total *= big[r] + 1;
+  std::fill(out, out + total, 0.0);
+  long long src_total = 1;
+  for (int r = 0; r < l; ++r) src_total *= q->degree[r] + 1;
+  for (long long s = 0; s < src_total; ++s) {
+    long long rem = s, dst = 0, mul = 1;
+    int digit[PCBA_MAXD];
+    for (int r = l - 1; r >= 0; --r) {
+      digit[r] = (int)(rem % (q->degree[r] + 1));
+      rem /= q->degree[r] + 1;
+    }
+    for (int r = l - 1; r >= 0; --r) {
+      dst += digit[r] * mul;
+      mul *= big[r] + 1;
+    }
+    out[dst] = q->coeff[s];
+  }
+}
+
+int create_impl(pcba_handle** out, const pcba_poly* cost, const pcba_poly* ineq, int n_ineq,
+                const pcba_poly* eq, int n_eq, const pcba_box* box, int precision, int form) {
+  if (!out) return fail(PCBA_ERR_INVALID, "out is null");
+  *out = nullptr;
+  if (!box || !box->lo || !box->hi) return fail(PCBA_ERR_INVALID, "box is null");
+  const int l = box->nvars;
+  if (l < 1 || l > PCBA_MAX_DIM) return fail(PCBA_ERR_INVALID, "nvars out of range");
+  if (precision != PCBA_FP64 && precision != PCBA_FP32)
+    return fail(PCBA_ERR_INVALID, "precision must be PCBA_FP64 or PCBA_FP32");
+  if (n_ineq < 0 || n_eq < 0 || (n_ineq > 0 && !ineq) || (n_eq > 0 && !eq))
+    return fail(PCBA_ERR_INVALID, "constraint arrays");
+  for (int r = 0; r < l; ++r)
+    if (!(box->lo[r] < box->hi[r]) || !std::isfinite(box->lo[r]) || !std::isfinite(box->hi[r]))
+      return fail(PCBA_ERR_INVALID, "box needs finite lo < hi");
+  int rc = check_poly(cost, l, "cost");
+  if (rc) return rc;
+  for (int i = 0; i < n_ineq; ++i)
+    if ((rc = check_poly(ineq + i, l, "ineq"))) return rc;
+  for (int j = 0; j < n_eq; ++j)
+    if ((rc = check_poly(eq + j, l, "eq"))) return rc;
+  pcba_handle* h = new pcba_handle();
+  HostProblem& P = h->prob;
+  P.l = l;
+  P.precision = precision;
+  P.form = form;
+  P.alpha = n_ineq;
+  P.beta = n_eq;
+  for (int r = 0; r < l; ++r) {
+    P.lo[r] = box->lo[r];
+    P.hi[r] = box->hi[r];
+    P.P[r] = cost->degree[r];
+    for (int i = 0; i < n_ineq; ++i) P.G[r] = std::max(P.G[r], ineq[i].degree[r]);
+    for (int j = 0; j < n_eq; ++j) P.H[r] = std::max(P.H[r], eq[j].degree[r]);
+  }
+  P.cp = 1;
+  P.cg = n_ineq ? 1 : 0;
+  P.ch = n_eq ? 1 : 0;
+  for (int r = 0; r < l; ++r) {
+    P.cp *= P.P[r] + 1;
+    if (n_ineq) P.cg *= P.G[r] + 1;
+    if (n_eq) P.ch *= P.H[r] + 1;
+  }
+  if (P.cg > PCBA_MAX_PATCH || P.ch > PCBA_MAX_PATCH) {
+    delete h;
+    return fail(PCBA_ERR_INVALID, "padded patch too large");
+  }
+  if (form == 1) {
+    // Bernstein patches cannot be zero-padded: every family must share its degree
+    for (int i = 0; i < n_ineq; ++i)
+      for (int r = 0; r < l; ++r)
+        if (ineq[i].degree[r] != P.G[r]) { delete h; return fail(PCBA_ERR_INVALID, "Bernstein ineq degrees differ"); }
+    for (int j = 0; j < n_eq; ++j)
+      for (int r = 0; r < l; ++r)
+        if (eq[j].degree[r] != P.H[r]) { delete h; return fail(PCBA_ERR_INVALID, "Bernstein eq degrees differ"); }
+  }
+  P.mono.assign((size_t)(P.cp + n_ineq * P.cg + n_eq * P.ch), 0.0);
+  embed(cost, l, P.P, P.mono.data());
+  for (int i = 0; i < n_ineq; ++i) embed(ineq + i, l, P.G, P.mono.data() + P.cp + i * P.cg);
+  for (int j = 0; j < n_eq; ++j)
+    embed(eq + j, l, P.H, P.mono.data() + P.cp + n_ineq * P.cg + j * P.ch);
+  for (double v : P.mono)
+    if (!std::isfinite(v)) { delete h; return fail(PCBA_ERR_INVALID, "non-finite coefficient"); }
+  *out = h;
+  return 0;
+}
+
+void free_batch(pcba_batch* b) {
+  if (!b) return;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  for (cudaEvent_t e : b->kev) cudaEventDestroy(e);
+  if (b->ev0) cudaEventDestroy(b->ev0);
+  if (b->ev1) cudaEventDestroy(b->ev1);
+  void* dev[] = {b->d_desc, b->d_state, b->d_plan, b->d_params, b->d_pre, b->d_arena, b->d_rec,
+                 b->d_slots, b->d_tilecnt, b->d_mono, b->d_trace, b->d_warm, b->d_mat,
+                 b->d_norm, b->d_raw, b->d_eval};
+  for (void* p : dev)
+    if (p) cudaFree(p);
+  void* host[] = {b->h_state, b->h_eval, b->h_plan, b->h_params, b->h_running};
+  for (void* p : host)
+    if (p) cudaFreeHost(p);
+  delete b;
+}
+
+template <typename T>
+int launch_loop_body(pcba_batch* b, cudaStream_t s, int use_graph) {
+  const Grids& g = b->g;
+  k2_subdivide<T><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
+  k3_classify<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
+  k4_index<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
+  k4_move<<<g.k4_grid, PCBA_TPB, 0, s>>>(b->E);
+  k_control<<<1, PCBA_TPB, 0, s>>>(b->E, b->cond, use_graph);
+  PCBA_CK(cudaGetLastError());
+  return 0;
+}
+
+template <typename T>
+int setup_kernels(pcba_batch* b) {
+  Grids& g = b->g;
+  int dev = 0;
+  PCBA_CK(cudaGetDevice(&dev));
+  PCBA_CK(cudaDeviceGetAttribute(&g.sms, cudaDevAttrMultiProcessorCount, dev));
+  int smem_optin = 0;
+  PCBA_CK(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+  long long cmax = 1, cpmax = 1;
+  for (const ProbDesc& d : b->desc) {
+    cmax = std::max<long long>(cmax, std::max<long long>(d.cp, std::max<long long>(d.cg, d.ch)));
+    cpmax = std::max<long long>(cpmax, d.cp);
+  }
+  g.k1_cmax = (int)cmax;
+  // K1: warps per block limited by shared memory
+  const size_t per_warp = (size_t)(2 * cmax + 289) * sizeof(double);
+  g.k1_wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(smem_optin - 1024) / per_warp));
+  g.k1_smem = per_warp * g.k1_wpb;
+  if (g.k1_smem > (size_t)smem_optin) return fail(PCBA_ERR_INVALID, "patch too large for shared memory");
+  PCBA_CK(cudaFuncSetAttribute(k1_convert<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)g.k1_smem));
+  int occ = 0;
+  PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k1_convert<T>, 32 * g.k1_wpb,
+                                                        g.k1_smem));
+  g.k1_grid = std::max(1, occ) * g.sms;
+  // K2: cost staging in shared memory
+  g.k2_smem = (size_t)(2 * cpmax) * sizeof(T);
+  PCBA_CK(cudaFuncSetAttribute(k2_subdivide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)std::max<size_t>(g.k2_smem, 1)));
+  PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2_subdivide<T>, PCBA_TPB,
+                                                        g.k2_smem));
+  g.k2_grid = std::max(1, occ) * g.sms;
+  PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_classify, PCBA_TPB, 0));
+  g.k3_grid = std::max(1, occ) * g.sms;
+  PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_move, PCBA_TPB, 0));
+  g.k4_grid = std::max(1, occ) * g.sms;
+  return 0;
+}
+
+template <typename T>
+int build_graph(pcba_batch* b) {
+  PCBA_CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
+  PCBA_CK(cudaGraphCreate(&b->graph, 0));
+  PCBA_CK(cudaGraphConditionalHandleCreate(&b->cond, b->graph, 1, cudaGraphCondAssignDefault));
+  // the parameter union has no default constructor: build it in zeroed storage
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)];
+  std::memset(raw, 0, sizeof(raw));
+  cudaGraphNodeParams* cp = reinterpret_cast<cudaGraphNodeParams*>(raw);
+  cp->type = cudaGraphNodeTypeConditional;
+  cp->conditional.handle = b->cond;
+  cp->conditional.type = cudaGraphCondTypeWhile;
+  cp->conditional.size = 1;
+  cudaGraphNode_t node;
+  PCBA_CK(cudaGraphAddNode(&node, b->graph, nullptr, nullptr, 0, cp));
+  cudaGraph_t body = cp->conditional.phGraph_out[0];
+  PCBA_CK(cudaStreamBeginCaptureToGraph(b->cap_stream, body, nullptr, nullptr, 0,
+                                        cudaStreamCaptureModeThreadLocal));
+  int rc = launch_loop_body<T>(b, b->cap_stream, 1);
+  cudaGraph_t captured = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->cap_stream, &captured);
+  if (rc) return rc;
+  if (e != cudaSuccess) return fail(PCBA_ERR_CUDA, std::string("capture: ") + cudaGetErrorString(e));
+  PCBA_CK(cudaGraphInstantiate(&b->gexec, b->graph, 0));
+  return 0;
+}
+
+int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_total, int flags) {
+  if (!out) return fail(PCBA_ERR_INVALID, "out is null");
+  *out = nullptr;
+  if (!hs || n < 1) return fail(PCBA_ERR_INVALID, "need at least one problem");
+  const int prec = hs[0] ? hs[0]->prob.precision : 0;
+  for (int k = 0; k < n; ++k)
+    if (!hs[k] || hs[k]->prob.precision != prec)
+      return fail(PCBA_ERR_INVALID, "every handle must exist and share one precision");
+  pcba_batch* b = new pcba_batch();
+  b->np = n;
+  b->precision = prec;
+  b->flags = flags;
+  b->stream = hs[0]->stream;
+  const int w = prec == PCBA_FP32 ? 4 : 8;
+  b->desc.resize(n);
+  long long mono = 0, sum_item = 0, trace_rows = 0;
+  for (int k = 0; k < n; ++k) {
+    const HostProblem& P = hs[k]->prob;
+    b->probs.push_back(&P);
+    ProbDesc& d = b->desc[k];
+    std::memset(&d, 0, sizeof(d));
+    d.l = P.l;
+    b->max_l = std::max(b->max_l, P.l);
+    d.cp = (int)P.cp;
+    d.cg = (int)P.cg;
+    d.ch = (int)P.ch;
+    d.alpha = P.alpha;
+    d.beta = P.beta;
+    d.apad = (int)round_up(P.alpha, 32);
+    d.bpad = (int)round_up(P.beta, 32);
+    d.tiles_g = (P.alpha + PCBA_TPB - 1) / PCBA_TPB;
+    d.tiles_h = (P.beta + PCBA_TPB - 1) / PCBA_TPB;
+    d.tiles = std::max(1, d.tiles_g + d.tiles_h);
+    d.form_bernstein = P.form;
+    for (int r = 0; r < PCBA_MAXD; ++r) {
+      d.P[r] = P.P[r];
+      d.G[r] = P.G[r];
+      d.H[r] = P.H[r];
+      d.lo[r] = P.lo[r];
+      d.hi[r] = P.hi[r];
+    }
+    long long off = 64;
+    d.off_cost = off;
+    off = round_up(off + P.cp * w, 128);
+    d.off_eg = off;
+    if (prec == PCBA_FP32) off = round_up(off + d.apad * 4LL, 128);
+    d.off_eh = off;
+    if (prec == PCBA_FP32) off = round_up(off + d.bpad * 4LL, 128);
+    d.off_g = off;
+    off = round_up(off + P.cg * d.apad * w, 128);
+    d.off_h = off;
+    off = off + P.ch * d.bpad * w;
+    d.item_bytes = round_up(off, 256);
+    d.payload_bytes = 4LL * P.l + (P.cp + P.alpha * P.cg + P.beta * P.ch) * w +
+                      (prec == PCBA_FP32 ? 12LL + 4LL * (P.alpha + P.beta) : 0);
+    d.move_chunks = (int)std::max<long long>(1, (d.item_bytes + 16383) / 16384);
+    d.mono_off = mono;
+    mono += (long long)P.mono.size();
+    d.trace_rows = PCBA_TRACE_PER_DIM * P.l;
+    d.trace_off = trace_rows;
+    trace_rows += d.trace_rows;
+    d.units_k1 = 1 + P.alpha + P.beta;
+    sum_item += d.item_bytes;
+  }
+  long long M = (long long)(mem_cap_total / (size_t)sum_item);
+  M = std::min<long long>(M, 1LL << 30);
+  b->M = M;
+  b->sum_item_bytes = sum_item;
+  b->mono_doubles = mono;
+  b->trace_rows_total = trace_rows;
+  const long long Mslots = std::max<long long>(M, 2);
+  const long long tiles_per = (Mslots + PCBA_TPB - 1) / PCBA_TPB + 1;
+  long long list_off = 0;
+  for (int k = 0; k < n; ++k) {
+    ProbDesc& d = b->desc[k];
+    d.M = M;
+    d.list_off = list_off;
+    list_off += std::max<long long>(M, 1) * d.item_bytes;
+    d.slot_off = (long long)k * Mslots;
+    d.tile_off = (long long)k * tiles_per;
+  }
+  const long long arena_bytes = list_off;
+  const long long nslots = (long long)n * Mslots;
+  int rc = 0;
+#define PCBA_ALLOC(ptr, bytes)                                                        \
+  do {                                                                                \
+    cudaError_t e_ = dev_alloc((void**)&(ptr), (size_t)(bytes));                     \
+    if (e_ != cudaSuccess) {                                                          \
+      free_batch(b);                                                                  \
+      return fail(PCBA_ERR_OOM, std::string("device allocation of ") +                \
+                                    std::to_string((long long)(bytes)) + " bytes failed"); \
+    }                                                                                 \
+  } while (0)
+  PCBA_ALLOC(b->d_desc, sizeof(ProbDesc) * n);
+  PCBA_ALLOC(b->d_state, sizeof(ProbState) * n);
+  PCBA_ALLOC(b->d_plan, sizeof(Plan));
+  PCBA_ALLOC(b->d_params, sizeof(SolveParams));
+  PCBA_ALLOC(b->d_pre, sizeof(unsigned) * 5 * (n + 1));
+  PCBA_ALLOC(b->d_arena, arena_bytes);
+  PCBA_ALLOC(b->d_rec, sizeof(ChildRec) * nslots);
+  PCBA_ALLOC(b->d_slots, sizeof(unsigned) * 4 * nslots);
+  PCBA_ALLOC(b->d_tilecnt, sizeof(unsigned) * tiles_per * n);
+  PCBA_ALLOC(b->d_mono, sizeof(double) * mono);
+  PCBA_ALLOC(b->d_trace, sizeof(double) * 4 * trace_rows);
+  PCBA_ALLOC(b->d_warm, sizeof(double) * PCBA_MAXD * n);
+  PCBA_ALLOC(b->d_mat, sizeof(double) * 3 * PCBA_MAXD * 289 * n);
+  PCBA_ALLOC(b->d_norm, sizeof(double) * 3 * PCBA_MAXD * n);
+  PCBA_ALLOC(b->d_raw, sizeof(double) * mono);
+  PCBA_ALLOC(b->d_eval, sizeof(EvalOut) * n);
+#undef PCBA_ALLOC
+  auto host_alloc = [&](void** p, size_t bytes) { return cudaMallocHost(p, bytes); };
+  if (host_alloc((void**)&b->h_state, sizeof(ProbState) * n) != cudaSuccess ||
+      host_alloc((void**)&b->h_eval, sizeof(EvalOut) * n) != cudaSuccess ||
+      host_alloc((void**)&b->h_plan, sizeof(Plan)) != cudaSuccess ||
+      host_alloc((void**)&b->h_params, sizeof(SolveParams)) != cudaSuccess ||
+      host_alloc((void**)&b->h_running, sizeof(int)) != cudaSuccess) {
+    free_batch(b);
+    return fail(PCBA_ERR_OOM, "pinned host allocation failed");
+  }
+  if (!b->stream) {
+    if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      free_batch(b);
+      return fail(PCBA_ERR_CUDA, "stream creation failed");
+    }
+    b->own_stream = true;
+  }
+  auto cleanup_ck = [&](cudaError_t e, const char* what) -> int {
+    if (e == cudaSuccess) return 0;
+    free_batch(b);
+    return fail(PCBA_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+  };
+  if ((rc = cleanup_ck(cudaMemcpy(b->d_desc, b->desc.data(), sizeof(ProbDesc) * n,
+                                  cudaMemcpyHostToDevice), "desc upload")))
+    return rc;
+  {
+    std::vector<double> all((size_t)mono);
+    for (int k = 0; k < n; ++k)
+      std::copy(b->probs[k]->mono.begin(), b->probs[k]->mono.end(),
+                all.begin() + b->desc[k].mono_off);
+    if ((rc = cleanup_ck(cudaMemcpy(b->d_mono, all.data(), sizeof(double) * mono,
+                                    cudaMemcpyHostToDevice), "mono upload")))
+      return rc;
+  }
+  std::vector<unsigned> k1pre(n + 1, 0);
+  for (int k = 0; k < n; ++k) k1pre[k + 1] = k1pre[k] + (unsigned)b->desc[k].units_k1;
+  unsigned* pre = b->d_pre;
+  if ((rc = cleanup_ck(cudaMemcpy(pre + 4 * (n + 1), k1pre.data(), sizeof(unsigned) * (n + 1),
+                                  cudaMemcpyHostToDevice), "k1 prefix")))
+    return rc;
+  if ((rc = cleanup_ck(cudaMemset(b->d_rec, 0, sizeof(ChildRec) * nslots), "rec clear"))) return rc;
+  if ((rc = cleanup_ck(cudaMemset(b->d_slots, 0, sizeof(unsigned) * 4 * nslots), "slot clear")))
+    return rc;
+  if ((rc = cleanup_ck(cudaMemset(b->d_state, 0, sizeof(ProbState) * n), "state clear"))) return rc;
+  if ((rc = cleanup_ck(cudaEventCreate(&b->ev0), "event"))) return rc;
+  if ((rc = cleanup_ck(cudaEventCreate(&b->ev1), "event"))) return rc;
+  Engine& E = b->E;
+  E.np = n;
+  E.precision = prec;
+  E.desc = b->d_desc;
+  E.state = b->d_state;
+  E.plan = b->d_plan;
+  E.params = b->d_params;
+  E.k2_pre = pre;
+  E.k3_pre = pre + (n + 1);
+  E.k3_pre_next = pre + 2 * (n + 1);
+  E.k4_pre = pre + 3 * (n + 1);
+  E.k1_pre = pre + 4 * (n + 1);
+  E.arena = b->d_arena;
+  E.rec = b->d_rec;
+  E.flagrank = b->d_slots;
+  E.arrive = b->d_slots + nslots;
+  E.hole = b->d_slots + 2 * nslots;
+  E.filler = b->d_slots + 3 * nslots;
+  E.tilecnt = b->d_tilecnt;
+  E.mono = b->d_mono;
+  E.trace = b->d_trace;
+  E.warm = b->d_warm;
+  E.root_raw = nullptr;
+  rc = prec == PCBA_FP32 ? setup_kernels<float>(b) : setup_kernels<double>(b);
+  if (!rc && (flags & 3) == 0) rc = prec == PCBA_FP32 ? build_graph<float>(b) : build_graph<double>(b);
+  if (rc) {
+    std::string msg = g_err;
+    free_batch(b);
+    return fail(rc, msg);
+  }
+  *out = b;
+  return 0;
+}
+
+template <typename T>
+int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double eq_tol,
+              int max_iters, int max_steps, const double* warm, bool want_raw) {
+  cudaStream_t s = b->stream;
+  const int n = b->np;
+  SolveParams& P = *b->h_params;
+  P.opt_tol = opt_tol;
+  P.eq_tol = eq_tol;
+  P.max_iters = max_iters;
+  P.max_steps = max_steps;
+  P.step_guard = b->max_l * max_iters + 4;
+  P.np = n;
+  PCBA_CK(cudaEventRecord(b->ev0, s));
+  if (host_coeffs)
+    PCBA_CK(cudaMemcpyAsync(b->d_mono, host_coeffs, sizeof(double) * b->mono_doubles,
+                            cudaMemcpyHostToDevice, s));
+  PCBA_CK(cudaMemcpyAsync(b->d_params, b->h_params, sizeof(SolveParams), cudaMemcpyHostToDevice, s));
+  if (warm)
+    PCBA_CK(cudaMemcpyAsync(b->d_warm, warm, sizeof(double) * PCBA_MAXD * n,
+                            cudaMemcpyHostToDevice, s));
+  else
+    PCBA_CK(cudaMemsetAsync(b->d_warm, 0xFF, sizeof(double) * PCBA_MAXD * n, s));  // NaN
+  PCBA_CK(cudaMemsetAsync(b->d_norm, 0, sizeof(double) * 3 * PCBA_MAXD * n, s));
+  Engine E1 = b->E;
+  E1.root_raw = want_raw ? b->d_raw : nullptr;
+  const int nmat = n * 3 * PCBA_MAXD * 17;
+  k1_matrices<<<(nmat + 255) / 256, 256, 0, s>>>(E1, b->d_mat, b->d_norm);
+  k1_convert<T><<<b->g.k1_grid, 32 * b->g.k1_wpb, b->g.k1_smem, s>>>(E1, b->d_mat, b->d_norm,
+                                                                   b->g.k1_cmax, b->g.k1_wpb);
+  k_eval<<<n, PCBA_TPB, 0, s>>>(E1, 0, nullptr);
+  k_init<<<1, PCBA_TPB, 0, s>>>(E1);
+  PCBA_CK(cudaGetLastError());
+  b->subdiv_ms = 0;
+  b->subdiv_bytes = 0;
+  b->subdiv_launches = 0;
+  const bool instrument = (b->flags & 2) != 0;
+  if ((b->flags & 3) == 0) {
+    PCBA_CK(cudaGraphLaunch(b->gexec, s));
+  } else {
+    const int guard = b->max_l * max_iters + 8;
+    std::vector<double> launch_bytes;
+    if (instrument) {
+      PCBA_CK(cudaMemcpyAsync(b->h_state, b->d_state, sizeof(ProbState) * n,
+                              cudaMemcpyDeviceToHost, s));
+      PCBA_CK(cudaStreamSynchronize(s));
+      while ((int)b->kev.size() < 2 * guard) {
+        cudaEvent_t e;
+        PCBA_CK(cudaEventCreate(&e));
+        b->kev.push_back(e);
+      }
+    }
+    int it = 0;
+    for (;; ++it) {
+      if (it >= guard) return fail(PCBA_ERR_DEVICE_TIMEOUT, "host loop guard reached");
+      if (instrument) {
+        double bytes = 0;
+        for (int k = 0; k < n; ++k)
+          if (b->h_state[k].status == PCBA_RUNNING)
+            bytes += 3.0 * (double)b->h_state[k].K * (double)b->desc[k].payload_bytes;
+        launch_bytes.push_back(bytes);
+        PCBA_CK(cudaEventRecord(b->kev[2 * it], s));
+      }
+      k2_subdivide<T><<<b->g.k2_grid, PCBA_TPB, b->g.k2_smem, s>>>(b->E);
+      if (instrument) PCBA_CK(cudaEventRecord(b->kev[2 * it + 1], s));
+      k3_classify<<<b->g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
+      k4_index<<<b->g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
+      k4_move<<<b->g.k4_grid, PCBA_TPB, 0, s>>>(b->E);
+      k_control<<<1, PCBA_TPB, 0, s>>>(b->E, b->cond, 0);
+      PCBA_CK(cudaGetLastError());
+      PCBA_CK(cudaMemcpyAsync(b->h_running, &b->d_plan->any_running, sizeof(int),
+                              cudaMemcpyDeviceToHost, s));
+      if (instrument)
+        PCBA_CK(cudaMemcpyAsync(b->h_state, b->d_state, sizeof(ProbState) * n,
+                                cudaMemcpyDeviceToHost, s));
+      PCBA_CK(cudaStreamSynchronize(s));
+      if (!*b->h_running) break;
+    }
+    if (instrument) {
+      for (int q = 0; q <= it; ++q) {
+        if (launch_bytes[q] <= 0) continue;
+        float ms = 0;
+        PCBA_CK(cudaEventElapsedTime(&ms, b->kev[2 * q], b->kev[2 * q + 1]));
+        b->subdiv_ms += ms;
+        b->subdiv_bytes += launch_bytes[q];
+        b->subdiv_launches += 1;
+      }
+    }
+  }
+  k_eval<<<n, PCBA_TPB, 0, s>>>(b->E, 1, b->d_eval);
+  PCBA_CK(cudaGetLastError());
+  PCBA_CK(cudaMemcpyAsync(b->h_state, b->d_state, sizeof(ProbState) * n, cudaMemcpyDeviceToHost, s));
+  PCBA_CK(cudaMemcpyAsync(b->h_eval, b->d_eval, sizeof(EvalOut) * n, cudaMemcpyDeviceToHost, s));
+  PCBA_CK(cudaMemcpyAsync(b->h_plan, b->d_plan, sizeof(Plan), cudaMemcpyDeviceToHost, s));
+  PCBA_CK(cudaEventRecord(b->ev1, s));
+  PCBA_CK(cudaStreamSynchronize(s));
+  float ms = 0;
+  PCBA_CK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
+  b->total_ms = ms;
+  if (b->h_plan->guard_hit) return fail(PCBA_ERR_DEVICE_TIMEOUT, "device loop guard reached");
+  return 0;
+}
+
+void fill_results(const pcba_batch* b, pcba_result* out) {
+  for (int k = 0; k < b->np; ++k) {
+    const ProbState& S = b->h_state[k];
+    const ProbDesc& d = b->desc[k];
+    const EvalOut& ev = b->h_eval[k];
+    pcba_result& R = out[k];
+    std::memset(&R, 0, sizeof(R));
+    R.status = S.status;
+    R.steps = S.steps;
+    R.sweeps = S.n;
+    R.lower = S.p_lo;
+    R.upper = S.p_up;
+    R.peak_items = S.peak_items;
+    R.peak_bytes = S.peak_items * d.item_bytes;
+    const bool point = S.status != PCBA_INFEASIBLE && (S.have_box || S.from_warm);
+    R.from_warm_start = point && !S.have_box && S.from_warm ? 1 : 0;
+    for (int q = 0; q < PCBA_MAX_DIM; ++q) {
+      R.x[q] = R.box_lo[q] = R.box_hi[q] = NAN;
+    }
+    if (point) {
+      for (int q = 0; q < d.l; ++q) {
+        if (S.have_box) {
+          const double w = std::ldexp(d.hi[q] - d.lo[q], -S.best_level[q]);
+          R.box_lo[q] = d.lo[q] + w * (double)S.best_index[q];
+          R.box_hi[q] = d.lo[q] + w * (double)(S.best_index[q] + 1u);
+          R.x[q] = 0.5 * (R.box_lo[q] + R.box_hi[q]);
+        } else {
+          R.x[q] = S.warm_x[q];
+        }
+      }
+    }
+    if (S.status == PCBA_INFEASIBLE) {
+      R.verify_cost = R.verify_max_g = R.verify_max_abs_h = NAN;
+    } else {
+      R.verify_cost = ev.ok ? ev.cost : NAN;
+      R.verify_max_g = ev.ok ? ev.max_g : NAN;
+      R.verify_max_abs_h = ev.ok ? ev.max_abs_h : NAN;
+    }
+    const unsigned long long t0 = b->h_plan->t0;
+    R.time_ms = S.t_end >= t0 ? (double)(S.t_end - t0) * 1e-6 : 0.0;
+  }
+}
+
+int batch_solve_impl(pcba_batch* b, const double* host_coeffs, double opt_tol, double eq_tol,
+                     int max_iters, int max_steps, const double* warm, pcba_result* out,
+                     bool want_raw = false) {
+  if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
+  if (!(opt_tol > 0) || !(eq_tol > 0)) return fail(PCBA_ERR_INVALID, "tolerances must be > 0");
+  if (max_iters < 1 || max_iters > 64) return fail(PCBA_ERR_INVALID, "max_iters must be in [1, 64]");
+  if (max_steps < 0) return fail(PCBA_ERR_INVALID, "max_steps must be >= 0");
+  const int rc = b->precision == PCBA_FP32
+                     ? run_solve<float>(b, host_coeffs, opt_tol, eq_tol, max_iters, max_steps, warm, want_raw)
+                     : run_solve<double>(b, host_coeffs, opt_tol, eq_tol, max_iters, max_steps, warm, want_raw);
+  if (rc) return rc;
+  if (out) fill_results(b, out);
+  return 0;
+}
+
+int own_batch(pcba_handle* h, size_t mem_cap, pcba_batch** out) {
+  if (h->own && h->own_cap == mem_cap) {
+    *out = h->own;
+    return 0;
+  }
+  if (h->own) {
+    free_batch(h->own);
+    h->own = nullptr;
+  }
+  pcba_handle* hs[1] = {h};
+  const int rc = batch_create_impl(&h->own, hs, 1, mem_cap, 0);
+  if (rc) return rc;
+  h->own_cap = mem_cap;
+  *out = h->own;
+  return 0;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+int pcba_version(void) { return 1; }
+
+const char* pcba_last_error(void) { return g_err.c_str(); }
+
+const char* pcba_status_string(int s) {
+  switch (s) {
+    case PCBA_OPTIMAL: return "OPTIMAL";
+    case PCBA_INFEASIBLE: return "INFEASIBLE";
+    case PCBA_MEMCAP: return "MEMCAP";
+    case PCBA_MAXITER: return "MAXITER";
+    case PCBA_STEPLIMIT: return "STEPLIMIT";
+    case PCBA_ERR_INVALID: return "ERR_INVALID";
+    case PCBA_ERR_CUDA: return "ERR_CUDA";
+    case PCBA_ERR_OOM: return "ERR_OOM";
+    case PCBA_ERR_DEVICE_TIMEOUT: return "ERR_DEVICE_TIMEOUT";
+    default: return "UNKNOWN";
+  }
+}
+
+int pcba_create(pcba_handle** out, const pcba_poly* cost, const pcba_poly* ineq, int n_ineq,
+                const pcba_poly* eq, int n_eq, const pcba_box* box, int precision) {
+  return create_impl(out, cost, ineq, n_ineq, eq, n_eq, box, precision, 0);
+}
+
+int pcba_create_bernstein(pcba_handle** out, const pcba_poly* cost, const pcba_poly* ineq,
+                          int n_ineq, const pcba_poly* eq, int n_eq, const pcba_box* box,
+                          int precision) {
+  return create_impl(out, cost, ineq, n_ineq, eq, n_eq, box, precision, 1);
+}
+
+void pcba_destroy(pcba_handle* h) {
+  if (!h) return;
+  free_batch(h->own);
+  delete h;
+}
+
+int pcba_set_stream(pcba_handle* h, void* stream) {
+  if (!h) return fail(PCBA_ERR_INVALID, "handle is null");
+  h->stream = (cudaStream_t)stream;
+  if (h->own) {
+    free_batch(h->own);
+    h->own = nullptr;
+  }
+  return 0;
+}
+
+int pcba_set_warm_start(pcba_handle* h, const double* x) {
+  if (!h) return fail(PCBA_ERR_INVALID, "handle is null");
+  if (!x) {
+    h->has_warm = false;
+    return 0;
+  }
+  for (int q = 0; q < h->prob.l; ++q)
+    if (!std::isfinite(x[q])) return fail(PCBA_ERR_INVALID, "warm start must be finite");
+  h->has_warm = true;
+  for (int q = 0; q < PCBA_MAXD; ++q) h->warm[q] = q < h->prob.l ? x[q] : 0.0;
+  return 0;
+}
+
+long long pcba_item_bytes(const pcba_handle* h) {
+  if (!h) return fail(PCBA_ERR_INVALID, "handle is null");
+  const HostProblem& P = h->prob;
+  const int w = P.precision == PCBA_FP32 ? 4 : 8;
+  long long off = 64;
+  off = round_up(off + P.cp * w, 128);
+  if (P.precision == PCBA_FP32) off = round_up(off + round_up(P.alpha, 32) * 4LL, 128);
+  if (P.precision == PCBA_FP32) off = round_up(off + round_up(P.beta, 32) * 4LL, 128);
+  off = round_up(off + P.cg * round_up(P.alpha, 32) * w, 128);
+  off = off + P.ch * round_up(P.beta, 32) * w;
+  return round_up(off, 256);
+}
+
+int pcba_solve_steps(pcba_handle* h, double opt_tol, double eq_tol, int max_iters, size_t mem_cap,
+                     int max_steps, pcba_result* out) {
+  if (!h) return fail(PCBA_ERR_INVALID, "handle is null");
+  pcba_batch* b = nullptr;
+  int rc = own_batch(h, mem_cap, &b);
+  if (rc) return rc;
+  return batch_solve_impl(b, nullptr, opt_tol, eq_tol, max_iters, max_steps,
+                          h->has_warm ? h->warm : nullptr, out);
+}
+
+int pcba_solve(pcba_handle* h, double opt_tol, double eq_tol, int max_iters, size_t mem_cap,
+               pcba_result* out) {
+  return pcba_solve_steps(h, opt_tol, eq_tol, max_iters, mem_cap, 0, out);
+}
+
+int pcba_batch_create(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_total, int flags) {
+  if (flags < 0 || flags > 3) return fail(PCBA_ERR_INVALID, "flags must be 0..3");
+  return batch_create_impl(out, hs, n, mem_cap_total, flags);
+}
+
+int pcba_batch_solve(pcba_batch* b, double opt_tol, double eq_tol, int max_iters,
+                     const double* warm_start, pcba_result* out) {
+  return batch_solve_impl(b, nullptr, opt_tol, eq_tol, max_iters, 0, warm_start, out);
+}
+
+int pcba_batch_solve_from_host(pcba_batch* b, const double* host_coeffs, double opt_tol,
+                               double eq_tol, int max_iters, const double* warm_start,
+                               pcba_result* out) {
+  if (!host_coeffs) return fail(PCBA_ERR_INVALID, "host_coeffs is null");
+  return batch_solve_impl(b, host_coeffs, opt_tol, eq_tol, max_iters, 0, warm_start, out);
+}
+
+long long pcba_batch_input_doubles(const pcba_batch* b) { return b ? b->mono_doubles : 0; }
+
+int pcba_batch_trace(const pcba_batch* b, int k, double* rows, int max_rows) {
+  if (!b || k < 0 || k >= b->np || !rows) return fail(PCBA_ERR_INVALID, "bad trace request");
+  const int steps = std::min(b->h_state[k].steps, b->desc[k].trace_rows);
+  const int nrow = std::min(steps, max_rows);
+  if (nrow <= 0) return 0;
+  PCBA_CK(cudaMemcpy(rows, b->d_trace + b->desc[k].trace_off * 4, sizeof(double) * 4 * nrow,
+                     cudaMemcpyDeviceToHost));
+  return nrow;
+}
+
+int pcba_batch_timing(const pcba_batch* b, double* total_ms, double* subdiv_ms,
+                      double* subdiv_bytes, long long* subdiv_launches) {
+  if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
+  if (total_ms) *total_ms = b->total_ms;
+  if (subdiv_ms) *subdiv_ms = b->subdiv_ms;
+  if (subdiv_bytes) *subdiv_bytes = b->subdiv_bytes;
+  if (subdiv_launches) *subdiv_launches = b->subdiv_launches;
+  return 0;
+}
+
+int pcba_batch_set_stream(pcba_batch* b, void* stream) {
+  if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
+  if (b->own_stream && b->stream) {
+    PCBA_CK(cudaStreamSynchronize(b->stream));
+    cudaStreamDestroy(b->stream);
+    b->own_stream = false;
+  }
+  b->stream = (cudaStream_t)stream;
+  return 0;
+}
+
+void pcba_batch_destroy(pcba_batch* b) { free_batch(b); }
+
+int pcba_solve_batch(pcba_handle** hs, int n, double opt_tol, double eq_tol, int max_iters,
+                     size_t mem_cap_total, const double* warm_start, pcba_result* out) {
+  pcba_batch* b = nullptr;
+  int rc = batch_create_impl(&b, hs, n, mem_cap_total, 0);
+  if (rc) return rc;
+  rc = batch_solve_impl(b, nullptr, opt_tol, eq_tol, max_iters, 0, warm_start, out);
+  free_batch(b);
+  return rc;
+}
+
+int pcba_get_list(pcba_handle* h, long long* K_out, double* cost, double* ineq, double* eq,
+                  float* err, unsigned* index, int* level) {
+  if (!h || !h->own) return fail(PCBA_ERR_INVALID, "no solve has run on this handle");
+  pcba_batch* b = h->own;
+  const ProbState& S = b->h_state[0];
+  const ProbDesc& d = b->desc[0];
+  const long long K = S.K;
+  if (K_out) *K_out = K;
+  if (level)
+    for (int q = 0; q < d.l; ++q) level[q] = S.level[q];
+  if (!cost && !ineq && !eq && !err && !index) return 0;
+  std::vector<char> buf((size_t)(K * d.item_bytes));
+  PCBA_CK(cudaMemcpy(buf.data(), b->d_arena + d.list_off, buf.size(), cudaMemcpyDeviceToHost));
+  const bool f32 = b->precision == PCBA_FP32;
+  const int nerr = 1 + d.alpha + d.beta;
+  for (long long k = 0; k < K; ++k) {
+    const char* it = buf.data() + k * d.item_bytes;
+    if (index)
+      for (int q = 0; q < d.l; ++q) index[k * d.l + q] = ((const unsigned*)it)[q];
+    const double O = f32 ? *(const double*)(it + 32) : 0.0;
+    auto val = [&](long long off, long long e) -> double {
+      return f32 ? (double)((const float*)(it + off))[e] : ((const double*)(it + off))[e];
+    };
+    if (cost)
+      for (int j = 0; j < d.cp; ++j) cost[k * d.cp + j] = f32 ? O + val(d.off_cost, j) : val(d.off_cost, j);
+    if (ineq)
+      for (int i = 0; i < d.alpha; ++i)
+        for (int j = 0; j < d.cg; ++j)
+          ineq[(k * d.alpha + i) * d.cg + j] = val(d.off_g, (long long)j * d.apad + i);
+    if (eq)
+      for (int i = 0; i < d.beta; ++i)
+        for (int j = 0; j < d.ch; ++j)
+          eq[(k * d.beta + i) * d.ch + j] = val(d.off_h, (long long)j * d.bpad + i);
+    if (err) {
+      float* e = err + k * nerr;
+      if (f32) {
+        e[0] = *(const float*)(it + 40);
+        for (int i = 0; i < d.alpha; ++i) e[1 + i] = ((const float*)(it + d.off_eg))[i];
+        for (int i = 0; i < d.beta; ++i) e[1 + d.alpha + i] = ((const float*)(it + d.off_eh))[i];
+      } else {
+        for (int i = 0; i < nerr; ++i) e[i] = 0.0f;
+      }
+    }
+  }
+  return 0;
+}
+
+int pcba_root_patches(pcba_handle* h, double* cost, double* ineq, double* eq) {
+  if (!h) return fail(PCBA_ERR_INVALID, "handle is null");
+  pcba_batch* b = nullptr;
+  const size_t cap = h->own ? h->own_cap : (size_t)pcba_item_bytes(h) * 4;
+  int rc = own_batch(h, cap, &b);
+  if (rc) return rc;
+  rc = batch_solve_impl(b, nullptr, 1.0, 1.0, 2, 1, nullptr, nullptr, true);
+  if (rc) return rc;
+  const HostProblem& P = h->prob;
+  std::vector<double> raw((size_t)b->mono_doubles);
+  PCBA_CK(cudaMemcpy(raw.data(), b->d_raw, sizeof(double) * raw.size(), cudaMemcpyDeviceToHost));
+  if (cost) std::copy(raw.begin(), raw.begin() + P.cp, cost);
+  if (ineq) std::copy(raw.begin() + P.cp, raw.begin() + P.cp + P.alpha * P.cg, ineq);
+  if (eq)
+    std::copy(raw.begin() + P.cp + P.alpha * P.cg,
+              raw.begin() + P.cp + P.alpha * P.cg + P.beta * P.ch, eq);
+  return 0;
+}
+
+}  // extern "C"

@@ -1,0 +1,223 @@
+// Device-side data structures and small helpers of libpcba (sm_103a).
+//
+// The list of items (Sec. III-B) of every problem lives in one device arena.
+// One item is one contiguous block of item_bytes (a multiple of 256):
+//
+//   [0, 32)            box: dyadic index per axis (u32[l]); the level per axis
+//                      is shared by all items of a problem and kept in its state
+//   [32, 48)           cost meta (FP32 mode): f64 offset O, f32 error bound e_p
+//   off_cost           cost patch B_p, cp values of T (FP32: stored = value - O)
+//   off_eg, off_eh     FP32 mode: error bound per inequality / equality patch
+//   off_g              inequality patches, coefficient-major: [cg][apad] of T,
+//                      so patch i is the column i ("constraint-minor")
+//   off_h              equality patches, [ch][bpad] of T
+//
+// Constraint-minor storage makes every load and store of the subdivision
+// kernel unit-stride across the threads of a warp for every bisection
+// direction: thread i owns patch i and walks its fibres.
+#pragma once
+
+#include <cstdint>
+
+#define PCBA_TPB 256
+#define PCBA_MAXD 8
+#define PCBA_NONE 0xFFFFFFFFu
+#define PCBA_RUNNING 10
+#define PCBA_TRACE_PER_DIM 40
+
+struct ProbDesc {
+  int l;
+  int cp, cg, ch;            // coefficients per patch of p, g, h
+  int alpha, beta;           // constraint counts
+  int apad, bpad;            // padded to multiples of 32
+  int tiles_g, tiles_h, tiles;  // subdivision work units per item
+  int form_bernstein;        // 1: inputs already Bernstein patches
+  int move_chunks;           // compaction work units per item
+  int P[PCBA_MAXD], G[PCBA_MAXD], H[PCBA_MAXD];
+  double lo[PCBA_MAXD], hi[PCBA_MAXD];
+  long long item_bytes;      // stride of the list
+  long long payload_bytes;   // algorithmic bytes of one item (no padding)
+  long long off_cost, off_eg, off_eh, off_g, off_h;
+  long long list_off;        // byte offset of the list in the arena
+  long long M;               // capacity in items (memory test of Alg. 1 line 4)
+  long long slot_off;        // offset of this problem in the per-slot scratch arrays
+  long long tile_off;        // offset in the per-tile scratch array
+  long long mono_off;        // offset (doubles) of the monomial input
+  long long trace_off;       // offset (rows) in the trace buffer
+  int trace_rows;
+  int units_k1;              // 1 + alpha + beta patches to convert
+};
+
+// Per-child bound record, each field an order-preserving 64-bit key of a
+// double so that it can be reduced with integer atomics.  A zero field is the
+// identity of a max-reduction ("minus infinity").
+struct ChildRec {
+  unsigned long long pmin, pmax;      // min / max B_p
+  unsigned long long gminmax;         // max_i min B_gi   (infeasible iff > 0)
+  unsigned long long gmaxmax;         // max_i max B_gi   (feasible iff <= 0)
+  unsigned long long hminmax;         // max_j min B_hj
+  unsigned long long hnegmaxmin;      // max_j (-max B_hj) = -(min_j max B_hj)
+  unsigned long long habsmax;         // max_j max(max B_hj, -min B_hj)
+  unsigned long long pad;
+};
+
+struct ProbState {
+  int status;
+  int K;            // list length before the next step's subdivision
+  int twoK;         // children of the current step
+  int K_save;
+  int F;            // hole-filling moves of the current step (Alg. 5)
+  int r;            // next bisection direction (0-based)
+  int n;            // iteration counter n of Alg. 1 (sweeps)
+  int steps;
+  int level[PCBA_MAXD];
+  unsigned best_slot;
+  unsigned k3_arrive;
+  int have_box;
+  int from_warm;
+  unsigned best_index[PCBA_MAXD];
+  int best_level[PCBA_MAXD];
+  unsigned long long pup_key;   // atomicMin over feasible children (this step)
+  unsigned long long plo_key;   // atomicMin over kept children (this step)
+  double p_up, p_lo;            // reported bounds
+  double p_up_carry;            // incumbent carried across steps (or warm start)
+  double warm_x[PCBA_MAXD];
+  long long peak_items;
+  unsigned long long t_end;
+  int done_flag;
+  int pad;
+};
+
+struct SolveParams {
+  double opt_tol, eq_tol;
+  int max_iters;
+  int max_steps;      // 0: no step limit
+  int step_guard;     // hard bound on device loop iterations
+  int np;
+};
+
+struct Plan {
+  unsigned k2_units;
+  unsigned k3_tiles;
+  unsigned k3_tiles_next;
+  unsigned k4_units;
+  unsigned k3_done;
+  int any_running;
+  int steps_global;
+  int guard_hit;
+  unsigned long long t0;
+};
+
+// Everything a kernel needs, passed by value.
+struct Engine {
+  int np;
+  int precision;           // 32 or 64
+  const ProbDesc* desc;
+  ProbState* state;
+  Plan* plan;
+  const SolveParams* params;
+  unsigned* k2_pre;        // [np + 1]
+  unsigned* k3_pre;        // [np + 1]
+  unsigned* k3_pre_next;   // [np + 1]
+  unsigned* k4_pre;        // [np + 1]
+  char* arena;
+  ChildRec* rec;           // per slot
+  unsigned* flagrank;      // per slot: keep << 31 | rank within its tile
+  unsigned* arrive;        // per slot (parent): tiles finished
+  unsigned* hole;          // per slot
+  unsigned* filler;        // per slot
+  unsigned* tilecnt;       // per tile: kept count, then exclusive offset
+  const double* mono;      // monomial inputs of every problem
+  double* trace;           // rows of (K, K_save, p_up, p_lo)
+  const double* warm;      // [np][PCBA_MAXD] or null
+  double* root_raw;        // optional FP64 root patch dump
+  const unsigned* k1_pre;  // [np + 1] patches per problem prefix
+};
+
+// ---------------------------------------------------------------------------
+// order-preserving keys
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned long long okey(double x) {
+  unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
+}
+__device__ __forceinline__ double okey_dec(unsigned long long k) {
+  unsigned long long b = (k & 0x8000000000000000ull) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
+  return __longlong_as_double((long long)b);
+}
+// decode a max-reduced field: 0 means nothing was reduced
+__device__ __forceinline__ double okey_dec_max(unsigned long long k) {
+  return k == 0ull ? -INFINITY : okey_dec(k);
+}
+// decode a min-reduced field: all ones means nothing was reduced
+__device__ __forceinline__ double okey_dec_min(unsigned long long k) {
+  return k == ~0ull ? INFINITY : okey_dec(k);
+}
+
+__device__ __forceinline__ unsigned long long ld_cg_u64(const unsigned long long* p) {
+  return __ldcg(p);
+}
+
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// problem owning work unit u: largest p with pre[p] <= u (pre[0] = 0)
+__device__ __forceinline__ int find_problem(const unsigned* pre, int np, unsigned u) {
+  int lo = 0, hi = np;
+  while (hi - lo > 1) {
+    int mid = (lo + hi) >> 1;
+    if (__ldg(pre + mid) <= u) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---------------------------------------------------------------------------
+// block-wide reductions and scans (PCBA_TPB threads)
+// ---------------------------------------------------------------------------
+template <int NV>
+__device__ __forceinline__ void block_max(double (&v)[NV], double* smem /* 8*NV */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) smem[wid * NV + q] = v[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    double m = smem[q];
+    for (int w = 1; w < PCBA_TPB / 32; ++w) m = fmax(m, smem[w * NV + q]);
+    v[q] = m;
+  }
+  __syncthreads();
+}
+
+// exclusive scan of one unsigned per thread; returns the exclusive prefix and
+// writes the block total to *total
+__device__ __forceinline__ unsigned block_exclusive_scan(unsigned x, unsigned* smem /* 8 */,
+                                                        unsigned* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned inc = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    unsigned y = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += y;
+  }
+  if (lane == 31) smem[wid] = inc;
+  __syncthreads();
+  unsigned woff = 0, tot = 0;
+  for (int w = 0; w < PCBA_TPB / 32; ++w) {
+    if (w < wid) woff += smem[w];
+    tot += smem[w];
+  }
+  __syncthreads();
+  *total = tot;
+  return woff + inc - x;
+}

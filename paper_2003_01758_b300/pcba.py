@@ -1,0 +1,316 @@
+"""Python binding of libpcba.so (include/pcba.h): argument marshalling only.
+
+Every step of a solve runs in the library's CUDA kernels; this module turns
+numpy arrays into the C structs of the ABI and back.  It loads the in-tree
+``libpcba.so`` and raises if it is missing: there is no fallback.
+
+Tensor convention as in ``workloads``: a polynomial of multi-degree N is a
+float64 array of shape N+1; a constraint family is stacked on a leading axis.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpcba.so")
+MAX_DIM = 8
+
+OPTIMAL, INFEASIBLE, MEMCAP, MAXITER, STEPLIMIT = 0, 1, 2, 3, 5
+FP64, FP32 = 64, 32
+STATUS_NAMES = {0: "OPTIMAL", 1: "INFEASIBLE", 2: "MEMCAP", 3: "MAXITER", 5: "STEPLIMIT"}
+
+
+class PcbaError(RuntimeError):
+    pass
+
+
+class pcba_poly(ctypes.Structure):
+    _fields_ = [("nvars", ctypes.c_int), ("degree", ctypes.POINTER(ctypes.c_int)),
+                ("coeff", ctypes.POINTER(ctypes.c_double))]
+
+
+class pcba_box(ctypes.Structure):
+    _fields_ = [("nvars", ctypes.c_int), ("lo", ctypes.POINTER(ctypes.c_double)),
+                ("hi", ctypes.POINTER(ctypes.c_double))]
+
+
+class pcba_result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("steps", ctypes.c_int), ("sweeps", ctypes.c_int),
+                ("from_warm_start", ctypes.c_int),
+                ("lower", ctypes.c_double), ("upper", ctypes.c_double),
+                ("x", ctypes.c_double * MAX_DIM), ("box_lo", ctypes.c_double * MAX_DIM),
+                ("box_hi", ctypes.c_double * MAX_DIM),
+                ("peak_items", ctypes.c_longlong), ("peak_bytes", ctypes.c_longlong),
+                ("verify_cost", ctypes.c_double), ("verify_max_g", ctypes.c_double),
+                ("verify_max_abs_h", ctypes.c_double), ("time_ms", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libpcba.so (raises PcbaError if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise PcbaError("libpcba.so is not built (run paper_2003_01758_b300/build.py); "
+                        "there is no CPU fallback")
+    L = ctypes.CDLL(LIB_PATH)
+    P, I, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_size_t
+    LL = ctypes.c_longlong
+    sigs = {
+        "pcba_create": ([P, P, P, I, P, I, P, I], I),
+        "pcba_create_bernstein": ([P, P, P, I, P, I, P, I], I),
+        "pcba_solve": ([P, D, D, I, S, P], I),
+        "pcba_solve_steps": ([P, D, D, I, S, I, P], I),
+        "pcba_solve_batch": ([P, I, D, D, I, S, P, P], I),
+        "pcba_batch_create": ([P, P, I, S, I], I),
+        "pcba_batch_solve": ([P, D, D, I, P, P], I),
+        "pcba_batch_solve_from_host": ([P, P, D, D, I, P, P], I),
+        "pcba_batch_input_doubles": ([P], LL),
+        "pcba_batch_trace": ([P, I, P, I], I),
+        "pcba_batch_timing": ([P, P, P, P, P], I),
+        "pcba_batch_set_stream": ([P, P], I),
+        "pcba_batch_destroy": ([P], None),
+        "pcba_get_list": ([P, P, P, P, P, P, P, P], I),
+        "pcba_root_patches": ([P, P, P, P], I),
+        "pcba_item_bytes": ([P], LL),
+        "pcba_set_stream": ([P, P], I),
+        "pcba_set_warm_start": ([P, P], I),
+        "pcba_destroy": ([P], None),
+        "pcba_status_string": ([I], ctypes.c_char_p),
+        "pcba_last_error": ([], ctypes.c_char_p),
+        "pcba_version": ([], I),
+    }
+    for name, (args, res) in sigs.items():
+        f = getattr(L, name)
+        f.argtypes = args
+        f.restype = res
+    _lib = L
+    return L
+
+
+def exported_symbols():
+    """Names the binding expects libpcba.so to export."""
+    return ["pcba_create", "pcba_create_bernstein", "pcba_solve", "pcba_solve_steps",
+            "pcba_solve_batch", "pcba_batch_create", "pcba_batch_solve",
+            "pcba_batch_solve_from_host", "pcba_batch_input_doubles", "pcba_batch_trace",
+            "pcba_batch_timing", "pcba_batch_set_stream", "pcba_batch_destroy",
+            "pcba_get_list", "pcba_root_patches", "pcba_item_bytes", "pcba_set_stream",
+            "pcba_set_warm_start", "pcba_destroy", "pcba_status_string", "pcba_last_error",
+            "pcba_version"]
+
+
+def _check(rc):
+    if rc < 0:
+        raise PcbaError("%s: %s" % (lib().pcba_status_string(rc).decode(),
+                                    lib().pcba_last_error().decode()))
+    return rc
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _result_dict(r: pcba_result, l: int) -> dict:
+    return {
+        "status": r.status, "steps": r.steps, "sweeps": r.sweeps,
+        "from_warm_start": bool(r.from_warm_start), "lower": r.lower, "upper": r.upper,
+        "x": np.array(r.x[:l]), "box_lo": np.array(r.box_lo[:l]), "box_hi": np.array(r.box_hi[:l]),
+        "peak_items": r.peak_items, "peak_bytes": r.peak_bytes, "verify_cost": r.verify_cost,
+        "verify_max_g": r.verify_max_g, "verify_max_abs_h": r.verify_max_abs_h,
+        "time_ms": r.time_ms,
+    }
+
+
+class Solver:
+    """One problem (pcba_create) and its single-problem solves (pcba_solve)."""
+
+    def __init__(self, cost, ineq=None, eq=None, lo=-1.0, hi=1.0, precision=FP32,
+                 form="monomial"):
+        cost = np.ascontiguousarray(cost, dtype=np.float64)
+        l = cost.ndim
+        self.l = l
+        ineq = np.zeros((0,) + (1,) * l) if ineq is None else np.ascontiguousarray(ineq, np.float64)
+        eq = np.zeros((0,) + (1,) * l) if eq is None else np.ascontiguousarray(eq, np.float64)
+        self.n_ineq, self.n_eq = int(ineq.shape[0]), int(eq.shape[0])
+        self.precision = precision
+        lo = np.ascontiguousarray(np.broadcast_to(lo, (l,)), dtype=np.float64)
+        hi = np.ascontiguousarray(np.broadcast_to(hi, (l,)), dtype=np.float64)
+        keep = [cost, ineq, eq, lo, hi]
+
+        def poly(a):
+            deg = np.ascontiguousarray(np.array(a.shape) - 1, dtype=np.int32)
+            a = np.ascontiguousarray(a)
+            keep.extend([deg, a])
+            return pcba_poly(l, deg.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                             a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+
+        c = poly(cost)
+        gi = (pcba_poly * max(1, self.n_ineq))(*[poly(g) for g in ineq])
+        hj = (pcba_poly * max(1, self.n_eq))(*[poly(h) for h in eq])
+        box = pcba_box(l, lo.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       hi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        h = ctypes.c_void_p()
+        fn = lib().pcba_create if form == "monomial" else lib().pcba_create_bernstein
+        _check(fn(ctypes.byref(h), ctypes.byref(c), gi, self.n_ineq, hj, self.n_eq,
+                  ctypes.byref(box), precision))
+        self._h = h
+        self.P = np.array(cost.shape) - 1
+        self.G = np.array(ineq.shape[1:]) - 1 if self.n_ineq else np.zeros(l, int)
+        self.H = np.array(eq.shape[1:]) - 1 if self.n_eq else np.zeros(l, int)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            lib().pcba_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def item_bytes(self) -> int:
+        return int(lib().pcba_item_bytes(self._h))
+
+    def set_warm_start(self, x):
+        if x is None:
+            _check(lib().pcba_set_warm_start(self._h, None))
+        else:
+            x = np.ascontiguousarray(x, dtype=np.float64)
+            _check(lib().pcba_set_warm_start(self._h, _p(x)))
+
+    def solve(self, opt_tol=1e-3, eq_tol=1e-4, max_iters=28, mem_cap=1 << 30, max_steps=0):
+        r = pcba_result()
+        _check(lib().pcba_solve_steps(self._h, opt_tol, eq_tol, max_iters, mem_cap, max_steps,
+                                      ctypes.byref(r)))
+        return _result_dict(r, self.l)
+
+    def get_list(self):
+        """List of the last solve, in the oracle's layout."""
+        K = ctypes.c_longlong()
+        lev = np.zeros(MAX_DIM, dtype=np.int32)
+        _check(lib().pcba_get_list(self._h, ctypes.byref(K), None, None, None, None, None,
+                                   _p(lev)))
+        K = K.value
+        cp = int(np.prod(self.P + 1))
+        cg = int(np.prod(self.G + 1)) if self.n_ineq else 0
+        ch = int(np.prod(self.H + 1)) if self.n_eq else 0
+        cost = np.empty((K, cp))
+        ineq = np.empty((K, self.n_ineq, cg))
+        eq = np.empty((K, self.n_eq, ch))
+        err = np.empty((K, 1 + self.n_ineq + self.n_eq), dtype=np.float32)
+        idx = np.empty((K, self.l), dtype=np.uint32)
+        _check(lib().pcba_get_list(self._h, ctypes.byref(ctypes.c_longlong()), _p(cost),
+                                   _p(ineq), _p(eq), _p(err), _p(idx), _p(lev)))
+        return {"cost": cost.reshape((K,) + tuple(self.P + 1)),
+                "ineq": ineq.reshape((K, self.n_ineq) + tuple(self.G + 1)),
+                "eq": eq.reshape((K, self.n_eq) + tuple(self.H + 1)),
+                "err": err, "index": idx, "level": lev[:self.l].copy()}
+
+    def root_patches(self):
+        """FP64 root Bernstein patches computed on the device (Alg. 1 line 1)."""
+        cp = int(np.prod(self.P + 1))
+        cg = int(np.prod(self.G + 1)) if self.n_ineq else 0
+        ch = int(np.prod(self.H + 1)) if self.n_eq else 0
+        cost = np.empty(cp)
+        ineq = np.empty(max(1, self.n_ineq * cg))
+        eq = np.empty(max(1, self.n_eq * ch))
+        _check(lib().pcba_root_patches(self._h, _p(cost), _p(ineq), _p(eq)))
+        return (cost.reshape(tuple(self.P + 1)),
+                ineq[:self.n_ineq * cg].reshape((self.n_ineq,) + tuple(self.G + 1)),
+                eq[:self.n_eq * ch].reshape((self.n_eq,) + tuple(self.H + 1)))
+
+
+def solver_from_problem(prob, precision=FP32):
+    return Solver(prob.cost, prob.ineq, prob.eq, prob.lo, prob.hi, precision=precision)
+
+
+class Batch:
+    """A reusable batch of problems solved together (pcba_batch_*)."""
+
+    GRAPH, HOST_LOOP, INSTRUMENT = 0, 1, 3
+
+    def __init__(self, solvers, mem_cap_total, flags=0):
+        self.solvers = list(solvers)
+        self.n = len(self.solvers)
+        arr = (ctypes.c_void_p * self.n)(*[s.handle for s in self.solvers])
+        b = ctypes.c_void_p()
+        _check(lib().pcba_batch_create(ctypes.byref(b), arr, self.n, int(mem_cap_total), flags))
+        self._b = b
+        self._results = (pcba_result * self.n)()
+
+    def close(self):
+        if getattr(self, "_b", None):
+            lib().pcba_batch_destroy(self._b)
+            self._b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _warm(self, warm):
+        if warm is None:
+            return None
+        w = np.full((self.n, MAX_DIM), np.nan)
+        for k, x in enumerate(warm):
+            if x is not None:
+                w[k, :len(x)] = x
+        return w
+
+    def solve(self, opt_tol=1e-3, eq_tol=1e-4, max_iters=28, warm=None, raw=False):
+        w = self._warm(warm)
+        _check(lib().pcba_batch_solve(self._b, opt_tol, eq_tol, max_iters,
+                                      None if w is None else _p(w), self._results))
+        if raw:
+            return self._results
+        return [_result_dict(self._results[k], self.solvers[k].l) for k in range(self.n)]
+
+    def input_doubles(self) -> int:
+        return int(lib().pcba_batch_input_doubles(self._b))
+
+    def solve_from_host(self, host_coeffs, opt_tol=1e-3, eq_tol=1e-4, max_iters=28, warm=None,
+                        raw=False):
+        assert host_coeffs.dtype == np.float64 and host_coeffs.size == self.input_doubles()
+        w = self._warm(warm)
+        _check(lib().pcba_batch_solve_from_host(self._b, _p(host_coeffs), opt_tol, eq_tol,
+                                                max_iters, None if w is None else _p(w),
+                                                self._results))
+        if raw:
+            return self._results
+        return [_result_dict(self._results[k], self.solvers[k].l) for k in range(self.n)]
+
+    def trace(self, k, max_rows=4096):
+        rows = np.empty((max_rows, 4))
+        n = _check(lib().pcba_batch_trace(self._b, k, _p(rows), max_rows))
+        return rows[:n].copy()
+
+    def timing(self):
+        t, s, b, n = ctypes.c_double(), ctypes.c_double(), ctypes.c_double(), ctypes.c_longlong()
+        _check(lib().pcba_batch_timing(self._b, ctypes.byref(t), ctypes.byref(s), ctypes.byref(b),
+                                       ctypes.byref(n)))
+        return {"total_ms": t.value, "subdiv_ms": s.value, "subdiv_bytes": b.value,
+                "subdiv_launches": n.value}
+
+    def set_stream(self, stream_ptr: int):
+        _check(lib().pcba_batch_set_stream(self._b, ctypes.c_void_p(stream_ptr)))
+
+
+def solve_batch(solvers, opt_tol=1e-3, eq_tol=1e-4, max_iters=28, mem_cap_total=1 << 32,
+                warm=None):
+    b = Batch(solvers, mem_cap_total)
+    try:
+        return b.solve(opt_tol, eq_tol, max_iters, warm)
+    finally:
+        b.close()
