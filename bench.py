@@ -1,0 +1,382 @@
+"""Benchmark: certified-optimal PCBA solves per second on RTD-shaped problems.
+
+One step = one batched solve, through the C ABI, of B problems per GPU: the
+whole path (FP64 monomial-to-Bernstein conversion, the branch and bound loop of
+subdivide / bound / incumbent / cut-off / compaction, FP64 check of the
+returned points) until every problem is certified or stops.
+
+  python bench.py [--gpus N --steps K --warmup W]      the CUDA library
+  python bench.py --impl reference [...]               the CPU oracle on host cores
+
+Problems: l = 2 on [-1,1]^2, a degree-(3,3) map F with N(0, 0.5^2)
+coefficients, 512 obstacle points, constraints r^2 - ||F(q) - o_i||^2 <= 0 of
+degree (6,6), cost ||F(q) - goal||^2; rank k solves seeds 2000 + B*k + j.
+Patches are FP32 with directed-rounding error bounds (FP64 mode is timed
+beside it).  Inputs are resident in HBM when the timed region starts; L2 is
+flushed between timed steps by writing a 256 MiB buffer.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "certified-optimal solves/sec and p50/p99 time-to-certify (opt_tol 1e-3), 1 B300"
+UNIT = "solves/s"
+BATCH = 64
+OBSTACLES = 512
+OPT_TOL = 1e-3
+EQ_TOL = 1e-4
+MAX_ITERS = 28
+BASE_SEED = 2000
+MEM_CAP = 64 << 30
+WORKLOAD = ("rtd-shaped POPs: l=2 on [-1,1]^2, F degree (3,3) N(0,0.5^2), %d obstacles "
+            "U([-2,2]^2) r=0.15, constraints degree (6,6), cost ||F-goal||^2; batch of %d "
+            "problems per GPU (seeds %d+%d*rank+j); FP32 patches with directed-rounding "
+            "error bounds; opt_tol %g" % (OBSTACLES, BATCH, BASE_SEED, BATCH, OPT_TOL))
+
+
+def shard_seeds(rank: int, batch: int = BATCH, base: int = BASE_SEED):
+    """Seeds of the problems one rank solves (independent problems, no exchange)."""
+    return [base + batch * rank + j for j in range(batch)]
+
+
+def reduce_max(value: float, world: int) -> float:
+    """Max over ranks of a host scalar (gloo, CPU tensors)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": reasons,
+                "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (cpu_baseline leg and --impl reference)
+# ---------------------------------------------------------------------------
+
+def _oracle_one(seed):
+    import oracle
+    from paper_2003_01758_b300 import workloads as W
+    p = W.rtd(seed, n_obstacles=OBSTACLES)
+    t = time.perf_counter()
+    r = oracle.solve(p.cost, p.ineq, p.eq, p.lo, p.hi, opt_tol=OPT_TOL, eq_tol=EQ_TOL,
+                     max_iters=MAX_ITERS)
+    return r["status"], time.perf_counter() - t
+
+
+def oracle_pool(procs):
+    import multiprocessing as mp
+    from concurrent.futures import ProcessPoolExecutor
+    return ProcessPoolExecutor(procs, mp_context=mp.get_context("spawn"))
+
+
+def run_oracle(pool, seeds):
+    t = time.perf_counter()
+    out = list(pool.map(_oracle_one, seeds))
+    return out, time.perf_counter() - t
+
+
+def cpu_procs():
+    return max(1, min(os.cpu_count() or 1, 32))
+
+
+def cpu_baseline(pool, procs, per_proc=2):
+    seeds = [BASE_SEED + j for j in range(procs * per_proc)]
+    run_oracle(pool, seeds[:procs])  # start-up of the workers
+    out, dt = run_oracle(pool, seeds)
+    ok = sum(1 for s, _ in out if s in (0, 1))
+    return {"value": ok / dt, "unit": UNIT, "cores": procs, "kind": "oracle",
+            "sample": "%d rtd problems (seeds %d..%d), FP64 oracle, one problem per process, "
+                      "%d processes, %.1f s wall" % (len(seeds), seeds[0], seeds[-1], procs, dt),
+            "p50_ms": 1e3 * float(np.median([t for _, t in out])),
+            "p99_ms": 1e3 * float(np.percentile([t for _, t in out], 99))}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return 0
+    procs = cpu_procs()
+    pool = oracle_pool(procs)
+    per_step = procs
+    seeds = lambda s: [BASE_SEED + (s * per_step + j) % (BATCH * 16) for j in range(per_step)]
+    for s in range(args.warmup):
+        run_oracle(pool, seeds(s))
+    total, solved, lat = 0.0, 0, []
+    for s in range(args.steps):
+        out, dt = run_oracle(pool, seeds(args.warmup + s))
+        total += dt
+        solved += sum(1 for st, _ in out if st in (0, 1))
+        lat += [t for _, t in out]
+    pool.shutdown()
+    value = solved / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD.replace("FP32 patches with "
+                                                                     "directed-rounding error bounds",
+                                                                     "FP64 CPU oracle"),
+                                        "problems_per_step": per_step},
+        "p50_ms": 1e3 * float(np.median(lat)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
+                         "sample": "%d problems per step, one per process" % per_step},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def make_batch(seeds, precision, flags=0, mem_cap=MEM_CAP):
+    from paper_2003_01758_b300 import pcba
+    from paper_2003_01758_b300 import workloads as W
+    probs = [W.rtd(s, n_obstacles=OBSTACLES) for s in seeds]
+    solvers = [pcba.Solver(p.cost, p.ineq, p.eq, p.lo, p.hi, precision=precision) for p in probs]
+    host = np.concatenate([np.concatenate([p.cost.ravel(), p.ineq.ravel(), p.eq.ravel()])
+                           for p in probs])
+    return pcba.Batch(solvers, mem_cap, flags=flags), solvers, host
+
+
+def timed_steps(batch, steps, flush):
+    """K solves; per-step device time from the library's CUDA events on its stream."""
+    import torch
+    ms, times, status = [], [], []
+    for _ in range(steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        res = batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS, raw=True)
+        ms.append(batch.timing()["total_ms"])
+        times += [r.time_ms for r in res]
+        status += [r.status for r in res]
+    return ms, times, status
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--problems", type=int, default=BATCH, help="problems per GPU and step")
+    ap.add_argument("--mem-gb", type=float, default=MEM_CAP / 2 ** 30)
+    ap.add_argument("--loop", default="graph", choices=["graph", "host"],
+                    help="device loop in a conditional CUDA graph, or driven from the host")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="timed solves only (no e2e, FP64, latency or roofline legs)")
+    args = ap.parse_args()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1 and "MASTER_ADDR" in os.environ:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    else:
+        world = 1
+    if args.impl == "reference":
+        rc = run_reference(args, rank, world)
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        return rc
+    args.warmup = max(args.warmup, 3)
+
+    # the oracle pool starts before the first CUDA call (spawned workers)
+    base = None
+    pool = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        pool = oracle_pool(cpu_procs())
+
+    import torch
+    from paper_2003_01758_b300 import build, pcba
+    build.build()
+    torch.cuda.set_device(local)
+    seeds = shard_seeds(rank, batch=args.problems)
+    mem_cap = int(args.mem_gb * 2 ** 30)
+    loop_flag = 0 if args.loop == "graph" else pcba.Batch.HOST_LOOP
+    batch, solvers, host_np = make_batch(seeds, pcba.FP32, flags=loop_flag, mem_cap=mem_cap)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    for _ in range(args.warmup):
+        batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+
+    # ---- timed region: K batched solves, inputs resident in HBM ----
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    ms, times, status = timed_steps(batch, args.steps, flush)
+    clk = clocks.stop()
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    total_ms = reduce_max(float(sum(ms)), world)
+    stats = batch.stats()
+    launches = stats["kernel_launches"] * args.steps  # same loop count each step
+
+    value = world * len(seeds) * args.steps / (total_ms / 1e3)
+    optimal = sum(1 for s in status if s == pcba.OPTIMAL)
+    infeasible = sum(1 for s in status if s == pcba.INFEASIBLE)
+    if args.no_extras:
+        if rank == 0:
+            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                              "steps": args.steps, "ms_per_step": total_ms / args.steps,
+                              "problems_per_step": len(seeds), "loop": args.loop,
+                              "certified": optimal + infeasible, "clocks": clk}))
+        return 0
+
+    # ---- end to end: host coefficients in, results out, wall clock ----
+    host = torch.from_numpy(host_np).pin_memory().numpy()
+    batch.solve_from_host(host, OPT_TOL, EQ_TOL, MAX_ITERS)
+    e2e_s = 0.0
+    for _ in range(args.steps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        batch.solve_from_host(host, OPT_TOL, EQ_TOL, MAX_ITERS, raw=True)
+        e2e_s += time.perf_counter() - t
+    e2e_stats = batch.stats()
+    e2e_total = reduce_max(e2e_s, world)
+    e2e_value = world * len(seeds) * args.steps / e2e_total
+
+    # ---- roofline of the subdivide/bound kernel: CUDA events around each launch ----
+    ibatch, _, _ = make_batch(seeds, pcba.FP32, flags=pcba.Batch.INSTRUMENT, mem_cap=mem_cap)
+    ibatch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+    ibatch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+    it = ibatch.timing()
+    ibatch.close()
+    peak, peak_kind = load_peaks()
+    achieved = it["subdiv_bytes"] / (it["subdiv_ms"] * 1e-3) / 1e9 if it["subdiv_ms"] > 0 else 0.0
+
+    # ---- FP64 mode, same problems ----
+    b64, s64, _ = make_batch(seeds, pcba.FP64, mem_cap=mem_cap)
+    b64.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+    ms64, _, st64 = timed_steps(b64, max(1, args.steps // 2), flush)
+    fp64_value = len(seeds) * len(ms64) / (sum(ms64) / 1e3)
+    b64.close()
+
+    # ---- one problem at a time (latency of a single solve) ----
+    single = []
+    for s in solvers[:16]:
+        sb = pcba.Batch([s], mem_cap // 8)
+        sb.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+        sb.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+        single.append(sb.timing()["total_ms"])
+        sb.close()
+
+    if pool is not None:
+        base = cpu_baseline(pool, cpu_procs())
+        pool.shutdown()
+
+    if rank != 0:
+        return 0
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "problems_per_step": len(seeds),
+                   "l2": "flushed between timed steps (256 MiB write)",
+                   "parallelism": "independent problems per GPU (dp%d)" % world,
+                   "device_loop": args.loop},
+        "p50_ms": float(np.median(times)), "p99_ms": float(np.percentile(times, 99)),
+        "certified": {"optimal": optimal, "infeasible": infeasible,
+                      "failed": len(status) - optimal - infeasible},
+        "fp64_value": fp64_value,
+        "fp64_certified": sum(1 for s in st64 if s in (0, 1)),
+        "single_problem_ms": {"p50": float(np.median(single)),
+                              "p99": float(np.percentile(single, 99)),
+                              "solves_per_s": 1e3 / float(np.mean(single))},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "k2_subdivide<float>", "peak_kind": peak_kind,
+                     "launches": it["subdiv_launches"],
+                     "algorithmic_bytes_per_launch": it["subdiv_bytes"] / max(1, it["subdiv_launches"]),
+                     "avg_launch_ms": it["subdiv_ms"] / max(1, it["subdiv_launches"])},
+        "cpu_baseline": base,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_stats["h2d_bytes"],
+                "d2h_bytes_per_step": e2e_stats["d2h_bytes"]},
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

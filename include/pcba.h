@@ -176,6 +176,11 @@ int pcba_batch_trace(const pcba_batch* b, int k, double* rows, int max_rows);
  * ms spent in the subdivide/bound kernel and its algorithmic bytes. */
 int pcba_batch_timing(const pcba_batch* b, double* total_ms, double* subdiv_ms,
                       double* subdiv_bytes, long long* subdiv_launches);
+/* Counters of the last solve: iterations of the device loop (one bisection
+ * step of every running problem each), kernels this library launched, and the
+ * bytes the call copied host->device and device->host. */
+int pcba_batch_stats(const pcba_batch* b, long long* loop_iters, long long* kernel_launches,
+                     long long* h2d_bytes, long long* d2h_bytes);
 int pcba_batch_set_stream(pcba_batch* b, void* cuda_stream);
 void pcba_batch_destroy(pcba_batch* b);
 

@@ -54,6 +54,11 @@ cudaError_t dev_alloc(void** p, size_t bytes) {
 
 long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
 
+// Row length of a constraint family in the coefficient-major layout: a
+// multiple of 32 patches (128-byte rows in FP32) for large families, of 4
+// (16-byte rows) for small ones so that a single constraint is not padded 32x.
+long long family_pad(long long n) { return n >= 32 ? round_up(n, 32) : round_up(n, 4); }
+
 struct HostProblem {
   int l = 0, precision = 64, form = 0;
   int P[PCBA_MAXD] = {0}, G[PCBA_MAXD] = {0}, H[PCBA_MAXD] = {0};
@@ -64,6 +69,7 @@ struct HostProblem {
 };
 
 struct Grids {
+  int nmax = 16;  // degree class of the subdivision kernel (4, 8 or 16)
   int sms = 148;
   int k1_grid = 1, k1_wpb = 1, k1_cmax = 1;
   size_t k1_smem = 0;
@@ -98,7 +104,6 @@ struct pcba_batch {
   double* d_trace = nullptr;
   double* d_warm = nullptr;
   double* d_mat = nullptr;
-  double* d_norm = nullptr;
   double* d_raw = nullptr;
   EvalOut* d_eval = nullptr;
   long long trace_rows_total = 0;
@@ -122,6 +127,7 @@ struct pcba_batch {
   // timing of the last solve
   double total_ms = 0, subdiv_ms = 0, subdiv_bytes = 0;
   long long subdiv_launches = 0;
+  long long h2d_bytes = 0, d2h_bytes = 0;
 };
 
 struct pcba_handle {
@@ -248,7 +254,7 @@ void free_batch(pcba_batch* b) {
   if (b->ev1) cudaEventDestroy(b->ev1);
   void* dev[] = {b->d_desc, b->d_state, b->d_plan, b->d_params, b->d_pre, b->d_arena, b->d_rec,
                  b->d_slots, b->d_tilecnt, b->d_mono, b->d_trace, b->d_warm, b->d_mat,
-                 b->d_norm, b->d_raw, b->d_eval};
+                 b->d_raw, b->d_eval};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {b->h_state, b->h_eval, b->h_plan, b->h_params, b->h_running};
@@ -258,9 +264,17 @@ void free_batch(pcba_batch* b) {
 }
 
 template <typename T>
+void launch_k2(const pcba_batch* b, cudaStream_t s) {
+  const Grids& g = b->g;
+  if (g.nmax <= 4) k2_subdivide<T, 4><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
+  else if (g.nmax <= 8) k2_subdivide<T, 8><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
+  else k2_subdivide<T, 16><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
+}
+
+template <typename T>
 int launch_loop_body(pcba_batch* b, cudaStream_t s, int use_graph) {
   const Grids& g = b->g;
-  k2_subdivide<T><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
+  launch_k2<T>(b, s);
   k3_classify<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
   k4_index<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
   k4_move<<<g.k4_grid, PCBA_TPB, 0, s>>>(b->E);
@@ -284,7 +298,7 @@ int setup_kernels(pcba_batch* b) {
   }
   g.k1_cmax = (int)cmax;
   // K1: warps per block limited by shared memory
-  const size_t per_warp = (size_t)(2 * cmax + 289) * sizeof(double);
+  const size_t per_warp = (size_t)(4 * cmax + 578) * sizeof(double);
   g.k1_wpb = (int)std::max<size_t>(1, std::min<size_t>(4, (size_t)(smem_optin - 1024) / per_warp));
   g.k1_smem = per_warp * g.k1_wpb;
   if (g.k1_smem > (size_t)smem_optin) return fail(PCBA_ERR_INVALID, "patch too large for shared memory");
@@ -294,12 +308,18 @@ int setup_kernels(pcba_batch* b) {
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k1_convert<T>, 32 * g.k1_wpb,
                                                         g.k1_smem));
   g.k1_grid = std::max(1, occ) * g.sms;
-  // K2: cost staging in shared memory
+  // K2: cost staging in shared memory; kernel variant by the largest degree
+  int dmax = 0;
+  for (const ProbDesc& d : b->desc)
+    for (int r = 0; r < d.l; ++r) dmax = std::max(dmax, std::max(d.P[r], std::max(d.G[r], d.H[r])));
+  g.nmax = dmax <= 4 ? 4 : (dmax <= 8 ? 8 : 16);
   g.k2_smem = (size_t)(2 * cpmax) * sizeof(T);
-  PCBA_CK(cudaFuncSetAttribute(k2_subdivide<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  const void* k2 = g.nmax == 4 ? (const void*)k2_subdivide<T, 4>
+                               : (g.nmax == 8 ? (const void*)k2_subdivide<T, 8>
+                                              : (const void*)k2_subdivide<T, 16>);
+  PCBA_CK(cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)std::max<size_t>(g.k2_smem, 1)));
-  PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2_subdivide<T>, PCBA_TPB,
-                                                        g.k2_smem));
+  PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2, PCBA_TPB, g.k2_smem));
   g.k2_grid = std::max(1, occ) * g.sms;
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_classify, PCBA_TPB, 0));
   g.k3_grid = std::max(1, occ) * g.sms;
@@ -363,8 +383,8 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
     d.ch = (int)P.ch;
     d.alpha = P.alpha;
     d.beta = P.beta;
-    d.apad = (int)round_up(P.alpha, 32);
-    d.bpad = (int)round_up(P.beta, 32);
+    d.apad = (int)family_pad(P.alpha);
+    d.bpad = (int)family_pad(P.beta);
     d.tiles_g = (P.alpha + PCBA_TPB - 1) / PCBA_TPB;
     d.tiles_h = (P.beta + PCBA_TPB - 1) / PCBA_TPB;
     d.tiles = std::max(1, d.tiles_g + d.tiles_h);
@@ -440,8 +460,7 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   PCBA_ALLOC(b->d_mono, sizeof(double) * mono);
   PCBA_ALLOC(b->d_trace, sizeof(double) * 4 * trace_rows);
   PCBA_ALLOC(b->d_warm, sizeof(double) * PCBA_MAXD * n);
-  PCBA_ALLOC(b->d_mat, sizeof(double) * 3 * PCBA_MAXD * 289 * n);
-  PCBA_ALLOC(b->d_norm, sizeof(double) * 3 * PCBA_MAXD * n);
+  PCBA_ALLOC(b->d_mat, sizeof(double) * 3 * PCBA_MAXD * 578 * n);
   PCBA_ALLOC(b->d_raw, sizeof(double) * mono);
   PCBA_ALLOC(b->d_eval, sizeof(EvalOut) * n);
 #undef PCBA_ALLOC
@@ -537,6 +556,9 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   P.step_guard = b->max_l * max_iters + 4;
   P.np = n;
   PCBA_CK(cudaEventRecord(b->ev0, s));
+  b->h2d_bytes = (long long)sizeof(SolveParams) + (host_coeffs ? 8LL * b->mono_doubles : 0) +
+                 (warm ? 8LL * PCBA_MAXD * n : 0);
+  b->d2h_bytes = (long long)(sizeof(ProbState) + sizeof(EvalOut)) * n + (long long)sizeof(Plan);
   if (host_coeffs)
     PCBA_CK(cudaMemcpyAsync(b->d_mono, host_coeffs, sizeof(double) * b->mono_doubles,
                             cudaMemcpyHostToDevice, s));
@@ -546,13 +568,12 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
                             cudaMemcpyHostToDevice, s));
   else
     PCBA_CK(cudaMemsetAsync(b->d_warm, 0xFF, sizeof(double) * PCBA_MAXD * n, s));  // NaN
-  PCBA_CK(cudaMemsetAsync(b->d_norm, 0, sizeof(double) * 3 * PCBA_MAXD * n, s));
   Engine E1 = b->E;
   E1.root_raw = want_raw ? b->d_raw : nullptr;
   const int nmat = n * 3 * PCBA_MAXD * 17;
-  k1_matrices<<<(nmat + 255) / 256, 256, 0, s>>>(E1, b->d_mat, b->d_norm);
-  k1_convert<T><<<b->g.k1_grid, 32 * b->g.k1_wpb, b->g.k1_smem, s>>>(E1, b->d_mat, b->d_norm,
-                                                                   b->g.k1_cmax, b->g.k1_wpb);
+  k1_matrices<<<(nmat + 255) / 256, 256, 0, s>>>(E1, b->d_mat);
+  k1_convert<T><<<b->g.k1_grid, 32 * b->g.k1_wpb, b->g.k1_smem, s>>>(E1, b->d_mat, b->g.k1_cmax,
+                                                                   b->g.k1_wpb);
   k_eval<<<n, PCBA_TPB, 0, s>>>(E1, 0, nullptr);
   k_init<<<1, PCBA_TPB, 0, s>>>(E1);
   PCBA_CK(cudaGetLastError());
@@ -586,7 +607,7 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
         launch_bytes.push_back(bytes);
         PCBA_CK(cudaEventRecord(b->kev[2 * it], s));
       }
-      k2_subdivide<T><<<b->g.k2_grid, PCBA_TPB, b->g.k2_smem, s>>>(b->E);
+      launch_k2<T>(b, s);
       if (instrument) PCBA_CK(cudaEventRecord(b->kev[2 * it + 1], s));
       k3_classify<<<b->g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
       k4_index<<<b->g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
@@ -773,10 +794,10 @@ long long pcba_item_bytes(const pcba_handle* h) {
   const int w = P.precision == PCBA_FP32 ? 4 : 8;
   long long off = 64;
   off = round_up(off + P.cp * w, 128);
-  if (P.precision == PCBA_FP32) off = round_up(off + round_up(P.alpha, 32) * 4LL, 128);
-  if (P.precision == PCBA_FP32) off = round_up(off + round_up(P.beta, 32) * 4LL, 128);
-  off = round_up(off + P.cg * round_up(P.alpha, 32) * w, 128);
-  off = off + P.ch * round_up(P.beta, 32) * w;
+  if (P.precision == PCBA_FP32) off = round_up(off + family_pad(P.alpha) * 4LL, 128);
+  if (P.precision == PCBA_FP32) off = round_up(off + family_pad(P.beta) * 4LL, 128);
+  off = round_up(off + P.cg * family_pad(P.alpha) * w, 128);
+  off = off + P.ch * family_pad(P.beta) * w;
   return round_up(off, 256);
 }
 
@@ -831,6 +852,19 @@ int pcba_batch_timing(const pcba_batch* b, double* total_ms, double* subdiv_ms,
   if (subdiv_ms) *subdiv_ms = b->subdiv_ms;
   if (subdiv_bytes) *subdiv_bytes = b->subdiv_bytes;
   if (subdiv_launches) *subdiv_launches = b->subdiv_launches;
+  return 0;
+}
+
+int pcba_batch_stats(const pcba_batch* b, long long* loop_iters, long long* kernel_launches,
+                     long long* h2d_bytes, long long* d2h_bytes) {
+  if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
+  const long long it = b->h_plan ? b->h_plan->steps_global : 0;
+  if (loop_iters) *loop_iters = it;
+  // prologue: k1_matrices, k1_convert, k_eval, k_init; 5 kernels per loop
+  // iteration; epilogue: k_eval
+  if (kernel_launches) *kernel_launches = 5 + 5 * it;
+  if (h2d_bytes) *h2d_bytes = b->h2d_bytes;
+  if (d2h_bytes) *d2h_bytes = b->d2h_bytes;
   return 0;
 }
 

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <math.h>
 
+#include <type_traits>
+
 #include "pcba_device.cuh"
 
 // ---------------------------------------------------------------------------
@@ -51,11 +53,14 @@ __device__ __forceinline__ double mulrn(double a, double b) { return __dmul_rn(a
 // ---------------------------------------------------------------------------
 // K1: monomial -> Bernstein
 // ---------------------------------------------------------------------------
-// mat layout: ((p * 3 + fam) * PCBA_MAXD + r) * 289 doubles; norm: same index.
+// mat layout: ((p * 3 + fam) * PCBA_MAXD + r) * 578 doubles: first T_r, then
+// the entrywise bound |B||S| of the same size.
 // T_r[i][j] = sum_{k <= min(i,j)} [C(i,k)/C(n,k)] * C(j,k) lo^(j-k) w^k maps
 // the power coefficients of one fibre to its Bernstein coefficients over
-// [lo, lo+w]; norm = max row sum of |B||S| (bounds |T| and its rounding).
-__global__ void k1_matrices(Engine E, double* mat, double* norm) {
+// [lo, lo+w].  Since |T| <= |B||S| and the rounding of the computed T and of
+// its products is bounded by gamma * |B||S| |a| entrywise, the conversion
+// error of a patch is at most gamma * (|B_1||S_1| x ... x |B_l||S_l|) |a|.
+__global__ void k1_matrices(Engine E, double* mat) {
   const int gid = blockIdx.x * blockDim.x + threadIdx.x;
   if (gid == 0) E.plan->t0 = globaltimer();
   const int per = 3 * PCBA_MAXD * 17;
@@ -71,34 +76,33 @@ __global__ void k1_matrices(Engine E, double* mat, double* norm) {
   const int n = deg[r];
   if (i > n) return;
   const double lo = D.lo[r], w = D.hi[r] - D.lo[r];
-  double* T = mat + ((size_t)(p * 3 + fam) * PCBA_MAXD + r) * 289;
-  double rowabs = 0.0;
+  double* T = mat + ((size_t)(p * 3 + fam) * PCBA_MAXD + r) * 578;
+  double* A = T + 289;
   for (int j = 0; j <= n; ++j) {
-    double t = 0.0;
+    double t = 0.0, ta = 0.0;
     const int kmax = i < j ? i : j;
     for (int k = 0; k <= kmax; ++k) {
       const double term = dev_binom(i, k) / dev_binom(n, k) * dev_binom(j, k) *
                           dev_pow(lo, j - k) * dev_pow(w, k);
       t += term;
-      rowabs += fabs(term);
+      ta += fabs(term);
     }
     T[i * (n + 1) + j] = t;
+    A[i * (n + 1) + j] = ta * (1.0 + 0x1p-40);  // covers the rounding of the bound itself
   }
-  // row maxima combined by the max over i (one writer per (p,fam,r) after)
-  atomicMax((unsigned long long*)(norm + (size_t)(p * 3 + fam) * PCBA_MAXD + r),
-            (unsigned long long)__double_as_longlong(rowabs));  // rowabs >= 0: bit order = value order
 }
 
 // One warp converts one patch: load the monomial tensor into shared memory,
 // apply the l mode products, then store it into item 0 of the list.
 template <typename T>
-__global__ void __launch_bounds__(128) k1_convert(Engine E, const double* mat, const double* norm,
-                                                  int cmax, int wpb) {
+__global__ void __launch_bounds__(128) k1_convert(Engine E, const double* mat, int cmax, int wpb) {
   extern __shared__ double k1s[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  double* sA = k1s + (size_t)wid * (2 * cmax + 289);
+  double* sA = k1s + (size_t)wid * (4 * cmax + 578);
   double* sB = sA + cmax;
-  double* sT = sB + cmax;
+  double* sX = sB + cmax;   // |a| carried through the |B||S| products
+  double* sY = sX + cmax;
+  double* sT = sY + cmax;
   const unsigned total = E.k1_pre[E.np];
   for (unsigned u = blockIdx.x * wpb + wid; u < total; u += gridDim.x * wpb) {
     const int p = find_problem(E.k1_pre, E.np, u);
@@ -116,24 +120,24 @@ __global__ void __launch_bounds__(128) k1_convert(Engine E, const double* mat, c
       aoff = D.cp + (long long)D.alpha * D.cg + (long long)idx * D.ch;
     }
     const double* a = E.mono + D.mono_off + aoff;
-    double amax = 0.0;
     for (int j = lane; j < C; j += 32) {
       const double v = a[j];
       sA[j] = v;
-      amax = fmax(amax, fabs(v));
+      sX[j] = fabs(v);
     }
-    for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
     __syncwarp();
     double err64 = 0.0;
     if (!D.form_bernstein) {
-      double nprod = 1.0, gterms = 0.0;
+      double gterms = 0.0;
       for (int r = 0; r < D.l; ++r) {
         const int n = deg[r];
         int stride = 1;
         for (int s = r + 1; s < D.l; ++s) stride *= deg[s] + 1;
-        const double* Tg = mat + ((size_t)(p * 3 + fam) * PCBA_MAXD + r) * 289;
-        for (int e = lane; e < (n + 1) * (n + 1); e += 32) sT[e] = Tg[e];
-        nprod *= norm[(size_t)(p * 3 + fam) * PCBA_MAXD + r];
+        const double* Tg = mat + ((size_t)(p * 3 + fam) * PCBA_MAXD + r) * 578;
+        for (int e = lane; e < (n + 1) * (n + 1); e += 32) {
+          sT[e] = Tg[e];
+          sT[289 + e] = Tg[289 + e];
+        }
         gterms += 4.0 * n + 8.0;
         __syncwarp();
         const int blk = (n + 1) * stride;
@@ -143,15 +147,25 @@ __global__ void __launch_bounds__(128) k1_convert(Engine E, const double* mat, c
           const int i = rem / stride;
           const int in = rem - i * stride;
           const double* src = sA + hp * blk + in;
-          double s = 0.0;
-          for (int j = 0; j <= n; ++j) s = fma(sT[i * (n + 1) + j], src[j * stride], s);
+          const double* srcx = sX + hp * blk + in;
+          double s = 0.0, sx = 0.0;
+          for (int j = 0; j <= n; ++j) {
+            s = fma(sT[i * (n + 1) + j], src[j * stride], s);
+            sx = __dadd_ru(sx, __dmul_ru(sT[289 + i * (n + 1) + j], srcx[j * stride]));
+          }
           sB[o] = s;
+          sY[o] = sx;
         }
         __syncwarp();
         double* tmp = sA; sA = sB; sB = tmp;
+        tmp = sX; sX = sY; sY = tmp;
       }
-      // FP64 rounding of the conversion: |b - exact| <= gamma * prod_r ||T_r|| * max|a|
-      err64 = __dmul_ru(__dmul_ru(__dmul_ru(2.0 * gterms, 0x1p-53), nprod), amax);
+      // FP64 rounding of the conversion, per patch:
+      //   |b - exact| <= gamma * max_J ((|B_1||S_1| x ... x |B_l||S_l|) |a|)_J
+      double amax = 0.0;
+      for (int j = lane; j < C; j += 32) amax = fmax(amax, sX[j]);
+      for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+      err64 = __dmul_ru(__dmul_ru(2.0 * gterms, 0x1p-53), amax);
     }
     if (E.root_raw) {
       double* raw = E.root_raw + D.mono_off + aoff;
@@ -285,26 +299,18 @@ __device__ __forceinline__ void cost_fibre(const T* src, T* sL, T* sR, int base,
   }
 }
 
-#define PCBA_DISPATCH_N(n, CALL)      \
-  switch (n) {                        \
-    case 1: { constexpr int N_ = 1; CALL; } break;   \
-    case 2: { constexpr int N_ = 2; CALL; } break;   \
-    case 3: { constexpr int N_ = 3; CALL; } break;   \
-    case 4: { constexpr int N_ = 4; CALL; } break;   \
-    case 5: { constexpr int N_ = 5; CALL; } break;   \
-    case 6: { constexpr int N_ = 6; CALL; } break;   \
-    case 7: { constexpr int N_ = 7; CALL; } break;   \
-    case 8: { constexpr int N_ = 8; CALL; } break;   \
-    case 9: { constexpr int N_ = 9; CALL; } break;   \
-    case 10: { constexpr int N_ = 10; CALL; } break; \
-    case 11: { constexpr int N_ = 11; CALL; } break; \
-    case 12: { constexpr int N_ = 12; CALL; } break; \
-    case 13: { constexpr int N_ = 13; CALL; } break; \
-    case 14: { constexpr int N_ = 14; CALL; } break; \
-    case 15: { constexpr int N_ = 15; CALL; } break; \
-    case 16: { constexpr int N_ = 16; CALL; } break; \
-    default: break;                   \
+// Calls f(std::integral_constant<int, N>) for the runtime degree n, for
+// N = 0..NMAX only: a kernel compiled for a smaller NMAX keeps fewer registers.
+template <int NMAX, int N = 0, typename F>
+__device__ __forceinline__ void dispatch_degree(int n, F&& f) {
+  if constexpr (N <= NMAX) {
+    if (n == N) {
+      f(std::integral_constant<int, N>{});
+      return;
+    }
+    dispatch_degree<NMAX, N + 1>(n, f);
   }
+}
 
 __device__ __forceinline__ int axis_stride(const int* deg, int l, int r) {
   int s = 1;
@@ -319,7 +325,7 @@ __device__ __forceinline__ int axis_stride(const int* deg, int l, int r) {
 //   half 2^-23 + 2^-149           re-centring, half = half the child's range,
 //   |O'| 2^-52                    rounding of the new offset,
 // all accumulated with upward rounding.
-template <typename T>
+template <typename T, int NMAX>
 __device__ void cost_part(const ProbDesc* D, char* parent, char* right, int r, ChildRec* recL,
                           ChildRec* recR, T* stage, double* red, double* meta) {
   const int cp = D->cp;
@@ -339,7 +345,9 @@ __device__ void cost_part(const ProbDesc* D, char* parent, char* right, int r, C
   for (int f = threadIdx.x; f < nf; f += PCBA_TPB) {
     const int o = f / stride;
     const int base = o * blk + (f - o * stride);
-    PCBA_DISPATCH_N(n, (cost_fibre<T, N_>(src, sL, sR, base, stride, v)));
+    dispatch_degree<NMAX>(n, [&](auto nc) {
+      cost_fibre<T, decltype(nc)::value>(src, sL, sR, base, stride, v);
+    });
   }
   block_max<5>(v, red);  // also orders the staging writes before the reads below
   const double minL = -v[0], maxL = v[1], minR = -v[2], maxR = v[3];
@@ -400,7 +408,7 @@ __device__ void cost_part(const ProbDesc* D, char* parent, char* right, int r, C
 }
 
 // One tile of up to PCBA_TPB constraint patches of one family.
-template <typename T>
+template <typename T, int NMAX>
 __device__ void constraint_part(const ProbDesc* D, char* parent, char* right, int r, int fam,
                                 int tt, ChildRec* recL, ChildRec* recR, double* red) {
   constexpr bool RIG = sizeof(T) == 4;
@@ -420,7 +428,9 @@ __device__ void constraint_part(const ProbDesc* D, char* parent, char* right, in
     a.minL = a.minR = T(INFINITY);
     a.maxL = a.maxR = T(-INFINITY);
     a.m = T(0);
-    PCBA_DISPATCH_N(n, (constraint_fibres<T, N_, RIG>(src, dR, pad, C, stride, i, a)));
+    dispatch_degree<NMAX>(n, [&](auto nc) {
+      constraint_fibres<T, decltype(nc)::value, RIG>(src, dR, pad, C, stride, i, a);
+    });
     double loL, hiL, loR, hiR;
     if constexpr (RIG) {
       float* ep = (float*)(parent + (fam ? D->off_eh : D->off_eg));
@@ -492,19 +502,45 @@ __device__ __forceinline__ ChildRec load_rec_cg(const ChildRec* p) {
 // patch and the box; every tile splits up to PCBA_TPB constraint patches.  The
 // last tile of an item to finish reads the two complete child records and, for
 // each feasible child, lowers p_up (Def. 4) with an atomic min.
-template <typename T>
-__global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
+//
+// Each block takes one contiguous range of units, so consecutive units mostly
+// belong to one problem; the problem's descriptor and step state are copied to
+// shared memory once per problem instead of being re-read from global memory
+// by every unit.
+template <typename T, int NMAX>
+__global__ void __launch_bounds__(PCBA_TPB, 2) k2_subdivide(Engine E) {
   extern __shared__ __align__(16) unsigned char k2stage[];
   __shared__ double red[8 * 6];
   __shared__ double meta[2];
+  __shared__ __align__(16) ProbDesc sD;
+  __shared__ int sK, sR;
   const unsigned units = E.plan->k2_units;
   const double eq_tol = E.params->eq_tol;
-  for (unsigned u = blockIdx.x; u < units; u += gridDim.x) {
-    const int p = find_problem(E.k2_pre, E.np, u);
-    const ProbDesc* D = E.desc + p;
+  const unsigned per = (units + gridDim.x - 1) / gridDim.x;
+  const unsigned u0 = blockIdx.x * per;
+  const unsigned u1 = min(units, u0 + per);
+  int p = -1;
+  unsigned pbeg = 0, pend = 0;
+  for (unsigned u = u0; u < u1; ++u) {
+    if (u >= pend) {
+      p = find_problem(E.k2_pre, E.np, u);
+      pbeg = E.k2_pre[p];
+      pend = E.k2_pre[p + 1];
+      __syncthreads();  // nobody still reads the previous descriptor
+      const int* src = (const int*)(E.desc + p);
+      int* dst = (int*)&sD;
+      for (int q = threadIdx.x; q < (int)(sizeof(ProbDesc) / sizeof(int)); q += PCBA_TPB)
+        dst[q] = src[q];
+      if (threadIdx.x == 0) {
+        sK = E.state[p].K;
+        sR = E.state[p].r;
+      }
+      __syncthreads();
+    }
+    const ProbDesc* D = &sD;
     ProbState* S = E.state + p;
-    const int K = S->K, r = S->r, tiles = D->tiles;
-    const unsigned local = u - E.k2_pre[p];
+    const int K = sK, r = sR, tiles = D->tiles;
+    const unsigned local = u - pbeg;
     const int k = (int)(local / (unsigned)tiles);
     const int t = (int)(local - (unsigned)k * tiles);
     char* parent = E.arena + D->list_off + (size_t)k * D->item_bytes;
@@ -512,7 +548,7 @@ __global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
     ChildRec* recL = E.rec + D->slot_off + k;
     ChildRec* recR = E.rec + D->slot_off + k + K;
     if (t == 0) {
-      cost_part<T>(D, parent, right, r, recL, recR, (T*)k2stage, red, meta);
+      cost_part<T, NMAX>(D, parent, right, r, recL, recR, (T*)k2stage, red, meta);
       if (threadIdx.x == 0) {
         unsigned* iL = (unsigned*)parent;
         unsigned* iR = (unsigned*)right;
@@ -525,7 +561,7 @@ __global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
     const int fam = t < D->tiles_g ? 0 : 1;
     const int tt = fam ? t - D->tiles_g : t;
     if (tt < (fam ? D->tiles_h : D->tiles_g))
-      constraint_part<T>(D, parent, right, r, fam, tt, recL, recR, red);
+      constraint_part<T, NMAX>(D, parent, right, r, fam, tt, recL, recR, red);
     __syncthreads();
     if (threadIdx.x == 0) {
       __threadfence();

@@ -74,6 +74,7 @@ def lib():
         "pcba_batch_input_doubles": ([P], LL),
         "pcba_batch_trace": ([P, I, P, I], I),
         "pcba_batch_timing": ([P, P, P, P, P], I),
+        "pcba_batch_stats": ([P, P, P, P, P], I),
         "pcba_batch_set_stream": ([P, P], I),
         "pcba_batch_destroy": ([P], None),
         "pcba_get_list": ([P, P, P, P, P, P, P, P], I),
@@ -99,7 +100,7 @@ def exported_symbols():
     return ["pcba_create", "pcba_create_bernstein", "pcba_solve", "pcba_solve_steps",
             "pcba_solve_batch", "pcba_batch_create", "pcba_batch_solve",
             "pcba_batch_solve_from_host", "pcba_batch_input_doubles", "pcba_batch_trace",
-            "pcba_batch_timing", "pcba_batch_set_stream", "pcba_batch_destroy",
+            "pcba_batch_timing", "pcba_batch_stats", "pcba_batch_set_stream", "pcba_batch_destroy",
             "pcba_get_list", "pcba_root_patches", "pcba_item_bytes", "pcba_set_stream",
             "pcba_set_warm_start", "pcba_destroy", "pcba_status_string", "pcba_last_error",
             "pcba_version"]
@@ -302,6 +303,13 @@ class Batch:
                                        ctypes.byref(n)))
         return {"total_ms": t.value, "subdiv_ms": s.value, "subdiv_bytes": b.value,
                 "subdiv_launches": n.value}
+
+    def stats(self):
+        it, kl, hd, dh = (ctypes.c_longlong() for _ in range(4))
+        _check(lib().pcba_batch_stats(self._b, ctypes.byref(it), ctypes.byref(kl),
+                                      ctypes.byref(hd), ctypes.byref(dh)))
+        return {"loop_iters": it.value, "kernel_launches": kl.value, "h2d_bytes": hd.value,
+                "d2h_bytes": dh.value}
 
     def set_stream(self, stream_ptr: int):
         _check(lib().pcba_batch_set_stream(self._b, ctypes.c_void_p(stream_ptr)))

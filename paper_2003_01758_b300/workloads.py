@@ -142,8 +142,10 @@ def dim4(seed: int, n_ineq: int = 64, n_eq: int = 2) -> Problem:
     l = 4
     q_star = rng.uniform(-1.0, 1.0, size=l)
     cost = rng.standard_normal((5,) * l)
-    ineq = np.stack([_shifted(rng, (4,) * l, q_star, -0.1) for _ in range(n_ineq)])
-    eq = np.stack([_shifted(rng, (3,) * l, q_star, 0.0) for _ in range(n_eq)])
+    ineq = np.stack([_shifted(rng, (4,) * l, q_star, -0.1) for _ in range(n_ineq)]) \
+        if n_ineq else _empty_family(l)
+    eq = np.stack([_shifted(rng, (3,) * l, q_star, 0.0) for _ in range(n_eq)]) \
+        if n_eq else _empty_family(l)
     return Problem(cost, ineq, eq, -np.ones(l), np.ones(l),
                    {"q_star": q_star, "workload": "dim4", "seed": seed})
 
