@@ -246,56 +246,74 @@ struct FibAcc {
 
 // Thread i walks every fibre of constraint patch i (column i of a
 // coefficient-major [C][pad] block); the left child overwrites the parent.
+// The de Casteljau triangle (see split_fibre) is evaluated in place: after
+// level k, q[0] is left_k and q[N-k] is right_(N-k), and both are stored at
+// once, so only the N+1 working values stay in registers.  Writing left_k over
+// the parent's coefficient k is safe: it was loaded before the first level.
 template <typename T, int N, bool RIG>
 __device__ __forceinline__ void constraint_fibres(T* src, T* dR, size_t pad, int C, int stride,
                                                   int i, FibAcc<T>& a) {
   const int nf = C / (N + 1);
   const int blk = (N + 1) * stride;
   const size_t st = (size_t)stride * pad;
-#pragma unroll 2
+#pragma unroll 1
   for (int f = 0; f < nf; ++f) {
     const int o = f / stride;
     const int in = f - o * stride;
-    const size_t base = (size_t)(o * blk + in) * pad + i;
-    T q[N + 1], L[N + 1], R[N + 1];
+    T* colL = src + (size_t)(o * blk + in) * pad + i;
+    T* colR = dR + (size_t)(o * blk + in) * pad + i;
+    T q[N + 1];
 #pragma unroll
-    for (int j = 0; j <= N; ++j) q[j] = src[base + j * st];
-    if (RIG) {
+    for (int j = 0; j <= N; ++j) q[j] = colL[j * st];
+    if constexpr (RIG) {
 #pragma unroll
       for (int j = 0; j <= N; ++j) a.m = fmax(a.m, fabs(q[j]));
     }
-    split_fibre<T, N>(q, L, R);
+    colR[N * st] = q[N];
+    a.minR = fmin(a.minR, q[N]);
+    a.maxR = fmax(a.maxR, q[N]);
+    a.minL = fmin(a.minL, q[0]);
+    a.maxL = fmax(a.maxL, q[0]);
 #pragma unroll
-    for (int j = 0; j <= N; ++j) {
-      src[base + j * st] = L[j];
-      dR[base + j * st] = R[j];
-      a.minL = fmin(a.minL, L[j]);
-      a.maxL = fmax(a.maxL, L[j]);
-      a.minR = fmin(a.minR, R[j]);
-      a.maxR = fmax(a.maxR, R[j]);
+    for (int k = 1; k <= N; ++k) {
+#pragma unroll
+      for (int j = 0; j <= N - k; ++j) q[j] = mulrn(addrn(q[j], q[j + 1]), T(0.5));
+      colL[k * st] = q[0];
+      colR[(N - k) * st] = q[N - k];
+      a.minL = fmin(a.minL, q[0]);
+      a.maxL = fmax(a.maxL, q[0]);
+      a.minR = fmin(a.minR, q[N - k]);
+      a.maxR = fmax(a.maxR, q[N - k]);
     }
   }
 }
 
-// One cost fibre into shared staging buffers.
+// One cost fibre into shared staging buffers (same in-place triangle).
 template <typename T, int N>
 __device__ __forceinline__ void cost_fibre(const T* src, T* sL, T* sR, int base, int stride,
                                            double (&v)[5]) {
-  T q[N + 1], L[N + 1], R[N + 1];
+  T q[N + 1];
 #pragma unroll
   for (int j = 0; j <= N; ++j) {
     q[j] = src[base + j * stride];
     v[4] = fmax(v[4], (double)fabs(q[j]));
   }
-  split_fibre<T, N>(q, L, R);
+  sL[base] = q[0];
+  sR[base + N * stride] = q[N];
+  v[0] = fmax(v[0], -(double)q[0]);
+  v[1] = fmax(v[1], (double)q[0]);
+  v[2] = fmax(v[2], -(double)q[N]);
+  v[3] = fmax(v[3], (double)q[N]);
 #pragma unroll
-  for (int j = 0; j <= N; ++j) {
-    sL[base + j * stride] = L[j];
-    sR[base + j * stride] = R[j];
-    v[0] = fmax(v[0], -(double)L[j]);
-    v[1] = fmax(v[1], (double)L[j]);
-    v[2] = fmax(v[2], -(double)R[j]);
-    v[3] = fmax(v[3], (double)R[j]);
+  for (int k = 1; k <= N; ++k) {
+#pragma unroll
+    for (int j = 0; j <= N - k; ++j) q[j] = mulrn(addrn(q[j], q[j + 1]), T(0.5));
+    sL[base + k * stride] = q[0];
+    sR[base + (N - k) * stride] = q[N - k];
+    v[0] = fmax(v[0], -(double)q[0]);
+    v[1] = fmax(v[1], (double)q[0]);
+    v[2] = fmax(v[2], -(double)q[N - k]);
+    v[3] = fmax(v[3], (double)q[N - k]);
   }
 }
 
@@ -318,7 +336,25 @@ __device__ __forceinline__ int axis_stride(const int* deg, int l, int r) {
   return s;
 }
 
-// Cost patch of one parent, processed by the whole block (tile 0 only).
+// order-preserving 32-bit key of a float (0 = below everything)
+__device__ __forceinline__ unsigned okey32(float x) {
+  const unsigned b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float okey32_dec(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+template <int NV>
+__device__ __forceinline__ void warp_max_d(double (&v)[NV]) {
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] = fmax(v[q], __shfl_xor_sync(0xffffffffu, v[q], o));
+  }
+}
+
+// Cost patch of one parent, processed by one warp (tile 0, warp 0).
 // FP64: children stored as computed.  FP32: each child is re-centred on the
 // middle of its stored range, and its error bound grows by
 //   n (m 2^-24 + 2^-149)          de Casteljau rounding, m = max |parent|,
@@ -327,7 +363,8 @@ __device__ __forceinline__ int axis_stride(const int* deg, int l, int r) {
 // all accumulated with upward rounding.
 template <typename T, int NMAX>
 __device__ void cost_part(const ProbDesc* D, char* parent, char* right, int r, ChildRec* recL,
-                          ChildRec* recR, T* stage, double* red, double* meta) {
+                          ChildRec* recR, T* stage) {
+  const int lane = threadIdx.x & 31;
   const int cp = D->cp;
   const int n = D->P[r];
   const int stride = axis_stride(D->P, D->l, r);
@@ -337,42 +374,43 @@ __device__ void cost_part(const ProbDesc* D, char* parent, char* right, int r, C
   T* dstR = (T*)(right + D->off_cost);
   T* sL = stage;
   T* sR = stage + cp;
-  if (sizeof(T) == 4 && threadIdx.x == 0) {  // FP32: offset and error of the parent
-    meta[0] = *(const double*)(parent + 32);
-    meta[1] = (double)*(const float*)(parent + 40);
+  double O = 0.0, ep = 0.0;
+  if constexpr (sizeof(T) == 4) {
+    O = *(const double*)(parent + 32);
+    ep = (double)*(const float*)(parent + 40);
   }
   double v[5] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
-  for (int f = threadIdx.x; f < nf; f += PCBA_TPB) {
+  for (int f = lane; f < nf; f += 32) {
     const int o = f / stride;
     const int base = o * blk + (f - o * stride);
     dispatch_degree<NMAX>(n, [&](auto nc) {
       cost_fibre<T, decltype(nc)::value>(src, sL, sR, base, stride, v);
     });
   }
-  block_max<5>(v, red);  // also orders the staging writes before the reads below
+  warp_max_d<5>(v);
+  __syncwarp();
   const double minL = -v[0], maxL = v[1], minR = -v[2], maxR = v[3];
   if constexpr (sizeof(T) == 8) {
-    for (int j = threadIdx.x; j < cp; j += PCBA_TPB) {
+    for (int j = lane; j < cp; j += 32) {
       src[j] = sL[j];
       dstR[j] = sR[j];
     }
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
       recL->pmin = okey(minL);
       recL->pmax = okey(maxL);
       recR->pmin = okey(minR);
       recR->pmax = okey(maxR);
     }
   } else {
-    const double O = meta[0];
-    const float ep = (float)meta[1];
     const float fn = (float)n;
-    const float e1f = __fadd_ru(__fadd_ru(ep, __fmul_ru((float)v[4], fn * 0x1p-24f)), fn * 0x1p-149f);
+    const float e1f = __fadd_ru(__fadd_ru((float)ep, __fmul_ru((float)v[4], fn * 0x1p-24f)),
+                                fn * 0x1p-149f);
     const double e1 = (double)e1f;
     double mids[2], Os[2], efs[2], lows[2], highs[2];
     const double cmins[2] = {minL, minR}, cmaxs[2] = {maxL, maxR};
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      const double mid = 0.5 * (cmins[c] + cmaxs[c]);          // exact
+      const double mid = 0.5 * (cmins[c] + cmaxs[c]);  // exact
       const double half = __dsub_ru(cmaxs[c], mid);
       const double e2 = __dadd_ru(__dadd_ru(e1, __dmul_ru(half, 0x1p-23)), 0x1p-149);
       const double On = O + mid;
@@ -390,11 +428,11 @@ __device__ void cost_part(const ProbDesc* D, char* parent, char* right, int r, C
     float* fdst = (float*)dstR;
     const float* fL = (const float*)sL;
     const float* fR = (const float*)sR;
-    for (int j = threadIdx.x; j < cp; j += PCBA_TPB) {
+    for (int j = lane; j < cp; j += 32) {
       fsrc[j] = __double2float_rn((double)fL[j] - mids[0]);
       fdst[j] = __double2float_rn((double)fR[j] - mids[1]);
     }
-    if (threadIdx.x == 0) {
+    if (lane == 0) {
       *(double*)(parent + 32) = Os[0];
       *(float*)(parent + 40) = (float)efs[0];
       *(double*)(right + 32) = Os[1];
@@ -405,13 +443,16 @@ __device__ void cost_part(const ProbDesc* D, char* parent, char* right, int r, C
       recR->pmax = okey(highs[1]);
     }
   }
+  __syncwarp();
 }
 
-// One tile of up to PCBA_TPB constraint patches of one family.
+// One warp's share (32 patches) of a tile of constraint patches of one family;
+// the warp's maxima go to the child records with fire-and-forget atomics.
 template <typename T, int NMAX>
 __device__ void constraint_part(const ProbDesc* D, char* parent, char* right, int r, int fam,
-                                int tt, ChildRec* recL, ChildRec* recR, double* red) {
+                                int tt, ChildRec* recL, ChildRec* recR) {
   constexpr bool RIG = sizeof(T) == 4;
+  const int lane = threadIdx.x & 31;
   const int i = tt * PCBA_TPB + threadIdx.x;
   const int cnt = fam ? D->beta : D->alpha;
   const size_t pad = fam ? D->bpad : D->apad;
@@ -422,7 +463,9 @@ __device__ void constraint_part(const ProbDesc* D, char* parent, char* right, in
   T* dR = (T*)(right + off);
   const int n = deg[r];
   const int stride = axis_stride(deg, D->l, r);
-  double v[6] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY, -INFINITY};
+  // reduced quantities of this thread (identity for masked lanes):
+  //   fam 0: lo_L, hi_L, lo_R, hi_R;  fam 1: lo_L, -hi_L, |.|_L, lo_R, -hi_R, |.|_R
+  T v[6] = {T(-INFINITY), T(-INFINITY), T(-INFINITY), T(-INFINITY), T(-INFINITY), T(-INFINITY)};
   if (i < cnt) {
     FibAcc<T> a;
     a.minL = a.minR = T(INFINITY);
@@ -431,7 +474,7 @@ __device__ void constraint_part(const ProbDesc* D, char* parent, char* right, in
     dispatch_degree<NMAX>(n, [&](auto nc) {
       constraint_fibres<T, decltype(nc)::value, RIG>(src, dR, pad, C, stride, i, a);
     });
-    double loL, hiL, loR, hiR;
+    T loL, hiL, loR, hiR;
     if constexpr (RIG) {
       float* ep = (float*)(parent + (fam ? D->off_eh : D->off_eg));
       float* er = (float*)(right + (fam ? D->off_eh : D->off_eg));
@@ -440,15 +483,15 @@ __device__ void constraint_part(const ProbDesc* D, char* parent, char* right, in
                                  fn * 0x1p-149f);
       ep[i] = ec;
       er[i] = ec;
-      loL = (double)__fsub_rd((float)a.minL, ec);
-      hiL = (double)__fadd_ru((float)a.maxL, ec);
-      loR = (double)__fsub_rd((float)a.minR, ec);
-      hiR = (double)__fadd_ru((float)a.maxR, ec);
+      loL = __fsub_rd((float)a.minL, ec);
+      hiL = __fadd_ru((float)a.maxL, ec);
+      loR = __fsub_rd((float)a.minR, ec);
+      hiR = __fadd_ru((float)a.maxR, ec);
     } else {
-      loL = (double)a.minL;
-      hiL = (double)a.maxL;
-      loR = (double)a.minR;
-      hiR = (double)a.maxR;
+      loL = a.minL;
+      hiL = a.maxL;
+      loR = a.minR;
+      hiR = a.maxR;
     }
     if (fam == 0) {
       v[0] = loL; v[1] = hiL; v[2] = loR; v[3] = hiR;
@@ -457,20 +500,33 @@ __device__ void constraint_part(const ProbDesc* D, char* parent, char* right, in
       v[3] = loR; v[4] = -hiR; v[5] = fmax(hiR, -loR);
     }
   }
-  block_max<6>(v, red);
-  if (threadIdx.x == 0) {
+  const int nv = fam ? 6 : 4;
+  double w[6];
+  if constexpr (RIG) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const unsigned k = q < nv ? __reduce_max_sync(0xffffffffu, okey32(v[q])) : 0u;
+      w[q] = (double)okey32_dec(k);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) w[q] = v[q];
+    warp_max_d<6>(w);
+  }
+  const int base_lane_i = tt * PCBA_TPB + (threadIdx.x & ~31);
+  if (lane == 0 && base_lane_i < cnt) {
     if (fam == 0) {
-      atomicMax(&recL->gminmax, okey(v[0]));
-      atomicMax(&recL->gmaxmax, okey(v[1]));
-      atomicMax(&recR->gminmax, okey(v[2]));
-      atomicMax(&recR->gmaxmax, okey(v[3]));
+      atomicMax(&recL->gminmax, okey(w[0]));
+      atomicMax(&recL->gmaxmax, okey(w[1]));
+      atomicMax(&recR->gminmax, okey(w[2]));
+      atomicMax(&recR->gmaxmax, okey(w[3]));
     } else {
-      atomicMax(&recL->hminmax, okey(v[0]));
-      atomicMax(&recL->hnegmaxmin, okey(v[1]));
-      atomicMax(&recL->habsmax, okey(v[2]));
-      atomicMax(&recR->hminmax, okey(v[3]));
-      atomicMax(&recR->hnegmaxmin, okey(v[4]));
-      atomicMax(&recR->habsmax, okey(v[5]));
+      atomicMax(&recL->hminmax, okey(w[0]));
+      atomicMax(&recL->hnegmaxmin, okey(w[1]));
+      atomicMax(&recL->habsmax, okey(w[2]));
+      atomicMax(&recR->hminmax, okey(w[3]));
+      atomicMax(&recR->hnegmaxmin, okey(w[4]));
+      atomicMax(&recR->habsmax, okey(w[5]));
     }
   }
 }
@@ -499,19 +555,19 @@ __device__ __forceinline__ ChildRec load_rec_cg(const ChildRec* p) {
 }
 
 // Work unit = (problem, parent item k, tile t).  Tile 0 also splits the cost
-// patch and the box; every tile splits up to PCBA_TPB constraint patches.  The
-// last tile of an item to finish reads the two complete child records and, for
-// each feasible child, lowers p_up (Def. 4) with an atomic min.
+// patch (warp 0) and the box; every tile splits up to PCBA_TPB constraint
+// patches, 32 per warp.  Warps never wait for each other inside a unit: each
+// warp publishes its maxima with atomics and then counts itself in the item's
+// arrival counter; the last of the tiles x 8 warps of an item to arrive reads
+// the two complete child records and, for each feasible child, lowers p_up
+// (Def. 4) with an atomic min.
 //
 // Each block takes one contiguous range of units, so consecutive units mostly
 // belong to one problem; the problem's descriptor and step state are copied to
-// shared memory once per problem instead of being re-read from global memory
-// by every unit.
+// shared memory once per problem.
 template <typename T, int NMAX>
-__global__ void __launch_bounds__(PCBA_TPB, 2) k2_subdivide(Engine E) {
+__global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
   extern __shared__ __align__(16) unsigned char k2stage[];
-  __shared__ double red[8 * 6];
-  __shared__ double meta[2];
   __shared__ __align__(16) ProbDesc sD;
   __shared__ int sK, sR;
   const unsigned units = E.plan->k2_units;
@@ -519,6 +575,8 @@ __global__ void __launch_bounds__(PCBA_TPB, 2) k2_subdivide(Engine E) {
   const unsigned per = (units + gridDim.x - 1) / gridDim.x;
   const unsigned u0 = blockIdx.x * per;
   const unsigned u1 = min(units, u0 + per);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  constexpr unsigned WARPS = PCBA_TPB / 32;
   int p = -1;
   unsigned pbeg = 0, pend = 0;
   for (unsigned u = u0; u < u1; ++u) {
@@ -538,7 +596,6 @@ __global__ void __launch_bounds__(PCBA_TPB, 2) k2_subdivide(Engine E) {
       __syncthreads();
     }
     const ProbDesc* D = &sD;
-    ProbState* S = E.state + p;
     const int K = sK, r = sR, tiles = D->tiles;
     const unsigned local = u - pbeg;
     const int k = (int)(local / (unsigned)tiles);
@@ -547,9 +604,9 @@ __global__ void __launch_bounds__(PCBA_TPB, 2) k2_subdivide(Engine E) {
     char* right = E.arena + D->list_off + (size_t)(k + K) * D->item_bytes;
     ChildRec* recL = E.rec + D->slot_off + k;
     ChildRec* recR = E.rec + D->slot_off + k + K;
-    if (t == 0) {
-      cost_part<T, NMAX>(D, parent, right, r, recL, recR, (T*)k2stage, red, meta);
-      if (threadIdx.x == 0) {
+    if (t == 0 && warp == 0) {
+      cost_part<T, NMAX>(D, parent, right, r, recL, recR, (T*)k2stage);
+      if (lane == 0) {
         unsigned* iL = (unsigned*)parent;
         unsigned* iR = (unsigned*)right;
         for (int s = 0; s < D->l; ++s) iR[s] = iL[s];
@@ -561,12 +618,11 @@ __global__ void __launch_bounds__(PCBA_TPB, 2) k2_subdivide(Engine E) {
     const int fam = t < D->tiles_g ? 0 : 1;
     const int tt = fam ? t - D->tiles_g : t;
     if (tt < (fam ? D->tiles_h : D->tiles_g))
-      constraint_part<T, NMAX>(D, parent, right, r, fam, tt, recL, recR, red);
-    __syncthreads();
-    if (threadIdx.x == 0) {
+      constraint_part<T, NMAX>(D, parent, right, r, fam, tt, recL, recR);
+    if (lane == 0) {
       __threadfence();
       const unsigned old = atomicAdd(E.arrive + D->slot_off + k, 1u);
-      if (old == (unsigned)tiles - 1) {
+      if (old == (unsigned)tiles * WARPS - 1) {
         E.arrive[D->slot_off + k] = 0u;
         __threadfence();
         const ChildRec cl = load_rec_cg(recL);
@@ -574,10 +630,10 @@ __global__ void __launch_bounds__(PCBA_TPB, 2) k2_subdivide(Engine E) {
         unsigned long long best = ~0ull;
         if (rec_feasible(cl, eq_tol)) best = cl.pmax;
         if (rec_feasible(cr, eq_tol) && cr.pmax < best) best = cr.pmax;
-        if (best != ~0ull) atomicMin(&S->pup_key, best);
+        if (best != ~0ull) atomicMin(&E.state[p].pup_key, best);
       }
     }
-    __syncthreads();
+    __syncwarp();
   }
 }
 
