@@ -205,6 +205,30 @@ int pcba_set_stream(pcba_handle* h, void* cuda_stream);
 int pcba_set_warm_start(pcba_handle* h, const double* x);  /* NULL clears */
 void pcba_destroy(pcba_handle* h);
 
+/* Monomial-to-Bernstein conversion (the step pcba_root_patches runs) that
+ * allocates nothing.  There is no counterpart in the paper: it exists for
+ * callers that cannot call cudaMalloc - code running inside another
+ * framework's memory pool or a real-time loop where allocation is forbidden
+ * after start-up, or a caller that hands every buffer in from its own arena.
+ *   d_mono     device pointer: n_patches dense monomial tensors of multi-degree
+ *              degree[0..nvars), each prod(degree[r]+1) doubles, row-major
+ *   degree, lo, hi   host arrays of nvars entries: the multi-degree and the box
+ *   d_out      device pointer, same layout: the Bernstein patches over the box
+ *   stream     cudaStream_t to launch on (NULL: the default stream)
+ * Returns once the work is queued on the stream; the caller synchronises.
+ * Limits: nvars <= 8, every degree <= 16 and at most 8192 coefficients per
+ * patch (the fixed scratch holds one 17x17 matrix per axis); anything larger
+ * returns PCBA_ERR_INVALID.
+ * The per-axis matrices live in one fixed 18.5 KB device array in the library,
+ * kept by every GPU that loads the library until the process exits.  The first
+ * call on a device looks up that array's device address, so make the first
+ * call on each device before capturing a stream into a CUDA graph.  All calls
+ * share the array: two calls that overlap on the GPU (for instance on two
+ * streams) race on it. */
+int pcba_bernstein_convert_noalloc(const double* d_mono, int n_patches, int nvars,
+                                   const int* degree, const double* lo, const double* hi,
+                                   double* d_out, void* stream);
+
 const char* pcba_status_string(int status);
 const char* pcba_last_error(void);
 int pcba_version(void);

@@ -6,7 +6,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpcba.so")
-SOURCES = [os.path.join(HERE, "csrc", "pcba.cu")]
+SOURCES = [os.path.join(HERE, "csrc", "pcba.cu"), os.path.join(HERE, "csrc", "pcba_noalloc.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("pcba_device.cuh", "pcba_kernels.cuh")] \
     + [os.path.join(ROOT, "include", "pcba.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")

@@ -724,6 +724,9 @@ int own_batch(pcba_handle* h, size_t mem_cap, pcba_batch** out) {
 
 }  // namespace
 
+// error reporting shared with the other source files of the library
+int pcba_internal_fail(int code, const std::string& msg) { return fail(code, msg); }
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------

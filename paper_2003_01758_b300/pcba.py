@@ -83,6 +83,7 @@ def lib():
         "pcba_set_stream": ([P, P], I),
         "pcba_set_warm_start": ([P, P], I),
         "pcba_destroy": ([P], None),
+        "pcba_bernstein_convert_noalloc": ([P, I, I, P, P, P, P, P], I),
         "pcba_status_string": ([I], ctypes.c_char_p),
         "pcba_last_error": ([], ctypes.c_char_p),
         "pcba_version": ([], I),
@@ -103,7 +104,7 @@ def exported_symbols():
             "pcba_batch_timing", "pcba_batch_stats", "pcba_batch_set_stream", "pcba_batch_destroy",
             "pcba_get_list", "pcba_root_patches", "pcba_item_bytes", "pcba_set_stream",
             "pcba_set_warm_start", "pcba_destroy", "pcba_status_string", "pcba_last_error",
-            "pcba_version"]
+            "pcba_version", "pcba_bernstein_convert_noalloc"]
 
 
 def _check(rc):
@@ -230,6 +231,20 @@ class Solver:
         return (cost.reshape(tuple(self.P + 1)),
                 ineq[:self.n_ineq * cg].reshape((self.n_ineq,) + tuple(self.G + 1)),
                 eq[:self.n_eq * ch].reshape((self.n_eq,) + tuple(self.H + 1)))
+
+
+def bernstein_convert_noalloc(d_mono_ptr: int, n_patches: int, degree, lo, hi, d_out_ptr: int,
+                              stream_ptr: int = 0):
+    """pcba_bernstein_convert_noalloc on caller-owned device buffers (raw
+    device pointers, e.g. torch's data_ptr()); queues the work on the stream."""
+    degree = np.ascontiguousarray(degree, dtype=np.int32)
+    l = degree.size
+    lo = np.ascontiguousarray(np.broadcast_to(lo, (l,)), dtype=np.float64)
+    hi = np.ascontiguousarray(np.broadcast_to(hi, (l,)), dtype=np.float64)
+    _check(lib().pcba_bernstein_convert_noalloc(ctypes.c_void_p(d_mono_ptr), int(n_patches), l,
+                                                _p(degree), _p(lo), _p(hi),
+                                                ctypes.c_void_p(d_out_ptr),
+                                                ctypes.c_void_p(stream_ptr)))
 
 
 def solver_from_problem(prob, precision=FP32):
