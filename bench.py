@@ -73,6 +73,24 @@ def load_peaks():
         return 6400.0, "fallback"
 
 
+def profiled_traffic():
+    """DRAM bytes per subdivision launch from the committed ncu summary, or None
+    when the kernel source changed since that capture."""
+    import hashlib
+    import re
+    src = os.path.join(ROOT, "paper_2003_01758_b300", "csrc", "pcba_kernels.cuh")
+    prof = os.path.join(ROOT, "profiles", "k2_subdivide_rtd512_fp32.md")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        text = open(prof).read()
+        if "`%s`" % sha not in text:
+            return None
+        m = re.search(r"TRAFFIC_BYTES_PER_LAUNCH = ([0-9.e+]+)", text)
+        return float(m.group(1)) if m else None
+    except Exception:
+        return None
+
+
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
 
@@ -238,6 +256,9 @@ def main():
                     help="device loop in a conditional CUDA graph, or driven from the host")
     ap.add_argument("--no-extras", action="store_true",
                     help="timed solves only (no e2e, FP64, latency or roofline legs)")
+    ap.add_argument("--launch-bytes", action="store_true",
+                    help="with --no-extras: one instrumented solve, print the algorithmic "
+                         "bytes of each subdivision launch")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
@@ -294,6 +315,11 @@ def main():
     optimal = sum(1 for s in status if s == pcba.OPTIMAL)
     infeasible = sum(1 for s in status if s == pcba.INFEASIBLE)
     if args.no_extras:
+        if args.launch_bytes and rank == 0:
+            ib, _, _ = make_batch(seeds, pcba.FP32, flags=pcba.Batch.INSTRUMENT, mem_cap=mem_cap)
+            ib.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+            print(json.dumps({"launch_bytes": ib.launch_bytes().tolist(), "timing": ib.timing()}))
+            ib.close()
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                               "steps": args.steps, "ms_per_step": total_ms / args.steps,
@@ -363,7 +389,7 @@ def main():
                               "p99": float(np.percentile(single, 99)),
                               "solves_per_s": 1e3 / float(np.mean(single))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak, "traffic": profiled_traffic(),
                      "kernel": "k2_subdivide<float>", "peak_kind": peak_kind,
                      "launches": it["subdiv_launches"],
                      "algorithmic_bytes_per_launch": it["subdiv_bytes"] / max(1, it["subdiv_launches"]),

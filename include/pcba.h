@@ -176,6 +176,10 @@ int pcba_batch_trace(const pcba_batch* b, int k, double* rows, int max_rows);
  * ms spent in the subdivide/bound kernel and its algorithmic bytes. */
 int pcba_batch_timing(const pcba_batch* b, double* total_ms, double* subdiv_ms,
                       double* subdiv_bytes, long long* subdiv_launches);
+/* Algorithmic bytes (3 x K x stored bytes of the patches of every running
+ * problem: one parent read, two children written) of each subdivision launch
+ * of the last instrumented solve (flags 3); returns the number written. */
+int pcba_batch_launch_bytes(const pcba_batch* b, double* bytes, int max_launches);
 /* Counters of the last solve: iterations of the device loop (one bisection
  * step of every running problem each), kernels this library launched, and the
  * bytes the call copied host->device and device->host. */

@@ -128,6 +128,7 @@ struct pcba_batch {
   double total_ms = 0, subdiv_ms = 0, subdiv_bytes = 0;
   long long subdiv_launches = 0;
   long long h2d_bytes = 0, d2h_bytes = 0;
+  std::vector<double> launch_bytes;
 };
 
 struct pcba_handle {
@@ -623,6 +624,7 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
       if (!*b->h_running) break;
     }
     if (instrument) {
+      b->launch_bytes = launch_bytes;
       for (int q = 0; q <= it; ++q) {
         if (launch_bytes[q] <= 0) continue;
         float ms = 0;
@@ -856,6 +858,13 @@ int pcba_batch_timing(const pcba_batch* b, double* total_ms, double* subdiv_ms,
   if (subdiv_bytes) *subdiv_bytes = b->subdiv_bytes;
   if (subdiv_launches) *subdiv_launches = b->subdiv_launches;
   return 0;
+}
+
+int pcba_batch_launch_bytes(const pcba_batch* b, double* bytes, int max_launches) {
+  if (!b || !bytes || max_launches < 0) return fail(PCBA_ERR_INVALID, "bad launch-bytes request");
+  const int n = std::min<int>(max_launches, (int)b->launch_bytes.size());
+  for (int q = 0; q < n; ++q) bytes[q] = b->launch_bytes[q];
+  return n;
 }
 
 int pcba_batch_stats(const pcba_batch* b, long long* loop_iters, long long* kernel_launches,

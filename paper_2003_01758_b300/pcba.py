@@ -75,6 +75,7 @@ def lib():
         "pcba_batch_trace": ([P, I, P, I], I),
         "pcba_batch_timing": ([P, P, P, P, P], I),
         "pcba_batch_stats": ([P, P, P, P, P], I),
+        "pcba_batch_launch_bytes": ([P, P, I], I),
         "pcba_batch_set_stream": ([P, P], I),
         "pcba_batch_destroy": ([P], None),
         "pcba_get_list": ([P, P, P, P, P, P, P, P], I),
@@ -101,7 +102,7 @@ def exported_symbols():
     return ["pcba_create", "pcba_create_bernstein", "pcba_solve", "pcba_solve_steps",
             "pcba_solve_batch", "pcba_batch_create", "pcba_batch_solve",
             "pcba_batch_solve_from_host", "pcba_batch_input_doubles", "pcba_batch_trace",
-            "pcba_batch_timing", "pcba_batch_stats", "pcba_batch_set_stream", "pcba_batch_destroy",
+            "pcba_batch_timing", "pcba_batch_stats", "pcba_batch_launch_bytes", "pcba_batch_set_stream", "pcba_batch_destroy",
             "pcba_get_list", "pcba_root_patches", "pcba_item_bytes", "pcba_set_stream",
             "pcba_set_warm_start", "pcba_destroy", "pcba_status_string", "pcba_last_error",
             "pcba_version", "pcba_bernstein_convert_noalloc"]
@@ -325,6 +326,11 @@ class Batch:
                                       ctypes.byref(hd), ctypes.byref(dh)))
         return {"loop_iters": it.value, "kernel_launches": kl.value, "h2d_bytes": hd.value,
                 "d2h_bytes": dh.value}
+
+    def launch_bytes(self, max_launches=4096):
+        out = np.empty(max_launches)
+        n = _check(lib().pcba_batch_launch_bytes(self._b, _p(out), max_launches))
+        return out[:n].copy()
 
     def set_stream(self, stream_ptr: int):
         _check(lib().pcba_batch_set_stream(self._b, ctypes.c_void_p(stream_ptr)))
