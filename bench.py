@@ -357,6 +357,26 @@ def main():
     fp64_value = len(seeds) * len(ms64) / (sum(ms64) / 1e3)
     b64.close()
 
+    # ---- uneven batch: 256 problems, obstacle counts log-uniform in [16, 4096] ----
+    uneven = None
+    if rank == 0 and world == 1:
+        from paper_2003_01758_b300 import workloads as W
+        counts = W.batch_obstacle_counts(256, 4000)
+        up = [W.rtd(4000 + k, n_obstacles=int(c)) for k, c in enumerate(counts)]
+        ub = pcba.Batch([pcba.Solver(q.cost, q.ineq, q.eq, q.lo, q.hi, precision=pcba.FP32)
+                         for q in up], 160 << 30)
+        tune = ub.autotune(OPT_TOL, EQ_TOL, MAX_ITERS)
+        ums, utimes, ustatus = timed_steps(ub, 3, flush)
+        uneven = {"workload": "256 rtd problems, obstacles floor(exp U(ln 16, ln 4096)), "
+                              "seeds 4000+k, FP32, one batched solve per step",
+                  "value": 256 * len(ums) / (sum(ums) / 1e3), "unit": UNIT,
+                  "ms_per_step": float(np.mean(ums)),
+                  "p50_ms": float(np.median(utimes)), "p99_ms": float(np.percentile(utimes, 99)),
+                  "certified": sum(1 for s_ in ustatus if s_ in (0, 1)),
+                  "infeasible": sum(1 for s_ in ustatus if s_ == 1), "solves": len(ustatus),
+                  "autotune": tune}
+        ub.close()
+
     # ---- one problem at a time (latency of a single solve) ----
     single = []
     for s in solvers[:16]:
@@ -397,6 +417,7 @@ def main():
         "cpu_baseline": base,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_stats["h2d_bytes"],
                 "d2h_bytes_per_step": e2e_stats["d2h_bytes"]},
+        "uneven_batch": uneven,
         "gpu_launches": launches,
         "clocks": clk,
     }

@@ -153,9 +153,12 @@ int pcba_solve_batch(pcba_handle** hs, int n, double opt_tol, double eq_tol, int
                      size_t mem_cap_total, const double* warm_start, pcba_result* out);
 
 /* A reusable batch: device buffers are allocated once and the device loop is
- * built once, so repeated solves do no allocation.  flags: 0 = device loop in a
- * CUDA graph with a conditional WHILE node (default); 1 = host loop that reads
- * one status word per step. */
+ * built once, so repeated solves do no allocation.  flags (bits):
+ *   0 = device loop in a CUDA graph with a conditional WHILE node (default);
+ *   1 = host loop that reads one status word per step;
+ *   3 = host loop with CUDA events around every subdivision launch;
+ *   4 = do not use the TMA-staged subdivision kernel (the direct-load one runs;
+ *       it is also used when a constraint patch exceeds 256 coefficients). */
 int pcba_batch_create(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_total,
                       int flags);
 int pcba_batch_solve(pcba_batch* b, double opt_tol, double eq_tol, int max_iters,
@@ -176,6 +179,18 @@ int pcba_batch_trace(const pcba_batch* b, int k, double* rows, int max_rows);
  * ms spent in the subdivide/bound kernel and its algorithmic bytes. */
 int pcba_batch_timing(const pcba_batch* b, double* total_ms, double* subdiv_ms,
                       double* subdiv_bytes, long long* subdiv_launches);
+/* Autotuner (not in the paper): times one solve of this batch under every
+ * feasible configuration of the subdivision kernel - direct loads, or TMA
+ * staging with 8/4/2 warps per block and 2/3 pipeline stages per warp - keeps
+ * the fastest and rebuilds the device loop for it.  ms_per_config[i] (if not
+ * NULL, up to max_configs entries) receives each configuration's solve time,
+ * *chosen the index kept.  Returns the number of configurations. */
+int pcba_batch_autotune(pcba_batch* b, double opt_tol, double eq_tol, int max_iters,
+                        double* ms_per_config, int max_configs, int* chosen);
+/* The subdivision configuration in use: returns its index and, if not NULL,
+ * whether it uses TMA staging, warps per block, stages and grid size. */
+int pcba_batch_config(const pcba_batch* b, int* tma, int* warps_per_block, int* stages,
+                      int* grid);
 /* Algorithmic bytes (3 x K x stored bytes of the patches of every running
  * problem: one parent read, two children written) of each subdivision launch
  * of the last instrumented solve (flags 3); returns the number written. */
@@ -185,6 +200,10 @@ int pcba_batch_launch_bytes(const pcba_batch* b, double* bytes, int max_launches
  * bytes the call copied host->device and device->host. */
 int pcba_batch_stats(const pcba_batch* b, long long* loop_iters, long long* kernel_launches,
                      long long* h2d_bytes, long long* d2h_bytes);
+/* FP32 mode: patches marked for a refresh from the FP64 monomials during the
+ * last solve (their error bound changed a classification) and patches actually
+ * refreshed (marked children that survived the cut-off). */
+int pcba_batch_refresh_stats(const pcba_batch* b, long long* marked, long long* refreshed);
 int pcba_batch_set_stream(pcba_batch* b, void* cuda_stream);
 void pcba_batch_destroy(pcba_batch* b);
 

@@ -9,6 +9,8 @@
 //             conditional WHILE node whose condition k_control sets on the
 //             device, so the host never waits inside the loop
 //   epilogue  k_eval (FP64 check of the returned point), copies to the host.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -70,18 +72,36 @@ struct HostProblem {
 
 struct Grids {
   int nmax = 16;  // degree class of the subdivision kernel (4, 8 or 16)
+  bool tma = false;  // TMA-staged subdivision kernel
+  int tma_wpb = 8, tma_stages = 2, tma_stage_elems = 0, tma_cpmax = 1;
+  size_t tma_smem = 0;
+  int tma_grid = 1;
+  // feasible subdivision configurations: index 0 = direct loads, then TMA
+  // (warps per block, stages, shared bytes, grid)
+  struct K2Cfg {
+    bool tma;
+    int wpb, stages;
+    size_t smem;
+    int grid;
+  };
+  std::vector<K2Cfg> cfgs;
+  int cfg = 0;
   int sms = 148;
   int k1_grid = 1, k1_wpb = 1, k1_cmax = 1;
   size_t k1_smem = 0;
   int k2_grid = 1;
   size_t k2_smem = 0;
   int k3_grid = 1, k4_grid = 1;
+  // FP32 refresh kernel
+  int kr_grid = 1, kr_wpb = 4, kr_cmax = 1, kr_lmax = 1;
+  size_t kr_smem = 0;
 };
 
 }  // namespace
 
 struct pcba_batch {
   int np = 0;
+  bool want_tma = true;
   int precision = 64;
   int flags = 0;
   std::vector<ProbDesc> desc;
@@ -98,12 +118,14 @@ struct pcba_batch {
   unsigned* d_pre = nullptr;  // 5 arrays of np+1
   char* d_arena = nullptr;
   ChildRec* d_rec = nullptr;
-  unsigned* d_slots = nullptr;  // flagrank | arrive | hole | filler
+  unsigned* d_slots = nullptr;  // flagrank | hole | filler
   unsigned* d_tilecnt = nullptr;
   double* d_mono = nullptr;
   double* d_trace = nullptr;
   double* d_warm = nullptr;
   double* d_mat = nullptr;
+  void* d_tmaps = nullptr;
+  uint4* d_marks = nullptr;
   double* d_raw = nullptr;
   EvalOut* d_eval = nullptr;
   long long trace_rows_total = 0;
@@ -255,7 +277,7 @@ void free_batch(pcba_batch* b) {
   if (b->ev1) cudaEventDestroy(b->ev1);
   void* dev[] = {b->d_desc, b->d_state, b->d_plan, b->d_params, b->d_pre, b->d_arena, b->d_rec,
                  b->d_slots, b->d_tilecnt, b->d_mono, b->d_trace, b->d_warm, b->d_mat,
-                 b->d_raw, b->d_eval};
+                 b->d_raw, b->d_eval, b->d_tmaps, b->d_marks};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {b->h_state, b->h_eval, b->h_plan, b->h_params, b->h_running};
@@ -267,6 +289,19 @@ void free_batch(pcba_batch* b) {
 template <typename T>
 void launch_k2(const pcba_batch* b, cudaStream_t s) {
   const Grids& g = b->g;
+  if (g.tma) {
+    const dim3 blk(32 * g.tma_wpb);
+    if (g.nmax <= 4)
+      k2_subdivide_tma<T, 4><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, g.tma_stages,
+                                                                 g.tma_stage_elems, g.tma_cpmax);
+    else if (g.nmax <= 8)
+      k2_subdivide_tma<T, 8><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, g.tma_stages,
+                                                                 g.tma_stage_elems, g.tma_cpmax);
+    else
+      k2_subdivide_tma<T, 16><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, g.tma_stages,
+                                                                  g.tma_stage_elems, g.tma_cpmax);
+    return;
+  }
   if (g.nmax <= 4) k2_subdivide<T, 4><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
   else if (g.nmax <= 8) k2_subdivide<T, 8><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
   else k2_subdivide<T, 16><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
@@ -275,7 +310,10 @@ void launch_k2(const pcba_batch* b, cudaStream_t s) {
 template <typename T>
 int launch_loop_body(pcba_batch* b, cudaStream_t s, int use_graph) {
   const Grids& g = b->g;
+  if (sizeof(T) == 4)
+    k_refresh<<<g.kr_grid, 32 * g.kr_wpb, g.kr_smem, s>>>(b->E, g.kr_cmax, g.kr_lmax);
   launch_k2<T>(b, s);
+  k_pup<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
   k3_classify<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
   k4_index<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
   k4_move<<<g.k4_grid, PCBA_TPB, 0, s>>>(b->E);
@@ -322,6 +360,74 @@ int setup_kernels(pcba_batch* b) {
                                (int)std::max<size_t>(g.k2_smem, 1)));
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2, PCBA_TPB, g.k2_smem));
   g.k2_grid = std::max(1, occ) * g.sms;
+  // candidate configurations: direct loads, then TMA-staged with per warp
+  // 'stages' copies of a [C][32] column block (C <= 256, the TMA box limit)
+  g.cfgs.clear();
+  g.cfgs.push_back({false, 8, 1, g.k2_smem, g.k2_grid});
+  {
+    long long cstage = 1;
+    bool fits = true;
+    for (const ProbDesc& d : b->desc) {
+      if (d.alpha > 0) cstage = std::max<long long>(cstage, d.cg);
+      if (d.beta > 0) cstage = std::max<long long>(cstage, d.ch);
+      if ((d.alpha > 0 && d.cg > 256) || (d.beta > 0 && d.ch > 256)) fits = false;
+    }
+    g.tma_stage_elems = (int)(cstage * 32);
+    g.tma_cpmax = (int)cpmax;
+    const size_t head_cap = ((size_t)64 + (size_t)cpmax * sizeof(T) + 127) / 128 * 128;
+    const size_t stage_bytes = (size_t)g.tma_stage_elems * sizeof(T) + 128 + head_cap;
+    const int cand[][2] = {{8, 2}, {8, 3}, {4, 2}, {4, 3}, {2, 2}};
+    const void* kt = g.nmax == 4 ? (const void*)k2_subdivide_tma<T, 4>
+                                 : (g.nmax == 8 ? (const void*)k2_subdivide_tma<T, 8>
+                                                : (const void*)k2_subdivide_tma<T, 16>);
+    size_t smem_max = 0;
+    for (const auto& c : cand) {
+      const size_t wb = ((size_t)c[1] * stage_bytes + 2 * (size_t)cpmax * sizeof(T) + 127) / 128 * 128;
+      const size_t total = (size_t)c[0] * wb + (size_t)c[0] * c[1] * 8;
+      if (fits && total <= (size_t)smem_optin) {
+        g.cfgs.push_back({true, c[0], c[1], total, 0});
+        smem_max = std::max(smem_max, total);
+      }
+    }
+    if (g.cfgs.size() > 1) {
+      PCBA_CK(cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
+      for (auto& c : g.cfgs) {
+        if (!c.tma) continue;
+        PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kt, 32 * c.wpb, c.smem));
+        c.grid = std::max(1, occ) * g.sms;
+      }
+    }
+  }
+  // FP32 refresh: per warp 4 patch buffers of the largest patch and the
+  // per-axis matrices; warps per block limited by shared memory
+  if (sizeof(T) == 4) {
+    g.kr_lmax = b->max_l;
+    g.kr_cmax = (int)cmax;
+    auto need = [&](int wpb, long long c) {
+      return (size_t)wpb * (size_t)(4 * c + 2 * 289 * g.kr_lmax) * sizeof(double);
+    };
+    g.kr_wpb = 4;
+    while (g.kr_wpb > 1 && need(g.kr_wpb, g.kr_cmax) > (size_t)smem_optin - 4096) g.kr_wpb /= 2;
+    while (g.kr_cmax > 1 && need(g.kr_wpb, g.kr_cmax) > (size_t)smem_optin - 4096) g.kr_cmax /= 2;
+    g.kr_smem = need(g.kr_wpb, g.kr_cmax);
+    PCBA_CK(cudaFuncSetAttribute(k_refresh, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)g.kr_smem));
+    PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_refresh, 32 * g.kr_wpb,
+                                                          g.kr_smem));
+    // marks are few (thousands per solve): two blocks per SM at most
+    g.kr_grid = std::max(1, std::min(occ, 2)) * g.sms;
+    double binom[17 * 17];
+    for (int n = 0; n < 17; ++n)
+      for (int k = 0; k < 17; ++k) {
+        double c = 0.0;
+        if (k <= n) {
+          c = 1.0;
+          for (int i = 1; i <= k; ++i) c = c * (double)(n - k + i) / (double)i;
+        }
+        binom[n * 17 + k] = c;
+      }
+    PCBA_CK(cudaMemcpyToSymbol(c_binom, binom, sizeof(binom)));
+  }
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_classify, PCBA_TPB, 0));
   g.k3_grid = std::max(1, occ) * g.sms;
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_move, PCBA_TPB, 0));
@@ -356,6 +462,86 @@ int build_graph(pcba_batch* b) {
   return 0;
 }
 
+// One 3-D tensor map per problem and constraint family over the list:
+// dims (patch column, coefficient row, item), strides (row bytes, item bytes),
+// box (32, C, 1): one copy brings the [C][32] column block of one parent.
+int build_tensor_maps(pcba_batch* b) {
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  PCBA_CK(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q));
+  if (!fn || q != cudaDriverEntryPointSuccess)
+    return fail(PCBA_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  auto encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+  const int n = b->np;
+  std::vector<CUtensorMap> maps((size_t)2 * n);
+  std::memset(maps.data(), 0, sizeof(CUtensorMap) * maps.size());
+  const bool f32 = b->precision == PCBA_FP32;
+  const size_t w = f32 ? 4 : 8;
+  for (int k = 0; k < n; ++k) {
+    const ProbDesc& d = b->desc[k];
+    for (int fam = 0; fam < 2; ++fam) {
+      const int cnt = fam ? d.beta : d.alpha;
+      if (cnt == 0) continue;
+      const cuuint64_t pad = (cuuint64_t)(fam ? d.bpad : d.apad);
+      const cuuint64_t C = (cuuint64_t)(fam ? d.ch : d.cg);
+      char* base = b->d_arena + d.list_off + (fam ? d.off_h : d.off_g);
+      const cuuint64_t dims[3] = {pad, C, (cuuint64_t)std::max<long long>(d.M, 1)};
+      const cuuint64_t strides[2] = {pad * w, (cuuint64_t)d.item_bytes};
+      const cuuint32_t box[3] = {32, (cuuint32_t)C, 1};
+      const cuuint32_t estr[3] = {1, 1, 1};
+      CUresult r = encode(&maps[(size_t)2 * k + fam],
+                          f32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                          base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+      if (r != CUDA_SUCCESS)
+        return fail(PCBA_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+    }
+  }
+  cudaError_t e = dev_alloc(&b->d_tmaps, sizeof(CUtensorMap) * maps.size());
+  if (e != cudaSuccess) return fail(PCBA_ERR_OOM, "tensor map allocation failed");
+  PCBA_CK(cudaMemcpy(b->d_tmaps, maps.data(), sizeof(CUtensorMap) * maps.size(),
+                     cudaMemcpyHostToDevice));
+  b->E.tmaps = b->d_tmaps;
+  return 0;
+}
+
+// Selects subdivision configuration 'idx' (0 = direct loads, >= 1 TMA):
+// the work units per item follow the kernel (256-patch tiles or 32-patch
+// groups), so the descriptors are re-uploaded.
+int apply_k2_config(pcba_batch* b, int idx) {
+  Grids& g = b->g;
+  if (idx < 0 || idx >= (int)g.cfgs.size()) return fail(PCBA_ERR_INVALID, "no such configuration");
+  const Grids::K2Cfg& c = g.cfgs[idx];
+  g.cfg = idx;
+  g.tma = c.tma;
+  if (c.tma) {
+    g.tma_wpb = c.wpb;
+    g.tma_stages = c.stages;
+    g.tma_smem = c.smem;
+    g.tma_grid = c.grid;
+    if (!b->d_tmaps) {
+      const int rc = build_tensor_maps(b);
+      if (rc) return rc;
+    }
+  }
+  for (ProbDesc& d : b->desc)
+    d.tiles = c.tma ? std::max(1, d.groups_g + d.groups_h) : std::max(1, d.tiles_g + d.tiles_h);
+  PCBA_CK(cudaMemcpy(b->d_desc, b->desc.data(), sizeof(ProbDesc) * b->np, cudaMemcpyHostToDevice));
+  return 0;
+}
+
+int rebuild_graph(pcba_batch* b) {
+  if ((b->flags & 3) != 0) return 0;
+  if (b->gexec) cudaGraphExecDestroy(b->gexec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  b->gexec = nullptr;
+  b->graph = nullptr;
+  b->cap_stream = nullptr;
+  return b->precision == PCBA_FP32 ? build_graph<float>(b) : build_graph<double>(b);
+}
+
 int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_total, int flags) {
   if (!out) return fail(PCBA_ERR_INVALID, "out is null");
   *out = nullptr;
@@ -368,6 +554,10 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   b->np = n;
   b->precision = prec;
   b->flags = flags;
+  {
+    const char* nt = std::getenv("PCBA_NO_TMA");
+    b->want_tma = !(flags & 4) && !(nt && nt[0] == '1');
+  }
   b->stream = hs[0]->stream;
   const int w = prec == PCBA_FP32 ? 4 : 8;
   b->desc.resize(n);
@@ -389,6 +579,8 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
     d.tiles_g = (P.alpha + PCBA_TPB - 1) / PCBA_TPB;
     d.tiles_h = (P.beta + PCBA_TPB - 1) / PCBA_TPB;
     d.tiles = std::max(1, d.tiles_g + d.tiles_h);
+    d.groups_g = (P.alpha + 31) / 32;
+    d.groups_h = (P.beta + 31) / 32;
     d.form_bernstein = P.form;
     for (int r = 0; r < PCBA_MAXD; ++r) {
       d.P[r] = P.P[r];
@@ -453,10 +645,10 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   PCBA_ALLOC(b->d_state, sizeof(ProbState) * n);
   PCBA_ALLOC(b->d_plan, sizeof(Plan));
   PCBA_ALLOC(b->d_params, sizeof(SolveParams));
-  PCBA_ALLOC(b->d_pre, sizeof(unsigned) * 5 * (n + 1));
+  PCBA_ALLOC(b->d_pre, sizeof(unsigned) * 6 * (n + 1));
   PCBA_ALLOC(b->d_arena, arena_bytes);
   PCBA_ALLOC(b->d_rec, sizeof(ChildRec) * nslots);
-  PCBA_ALLOC(b->d_slots, sizeof(unsigned) * 4 * nslots);
+  PCBA_ALLOC(b->d_slots, sizeof(unsigned) * 3 * nslots);
   PCBA_ALLOC(b->d_tilecnt, sizeof(unsigned) * tiles_per * n);
   PCBA_ALLOC(b->d_mono, sizeof(double) * mono);
   PCBA_ALLOC(b->d_trace, sizeof(double) * 4 * trace_rows);
@@ -464,6 +656,8 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   PCBA_ALLOC(b->d_mat, sizeof(double) * 3 * PCBA_MAXD * 578 * n);
   PCBA_ALLOC(b->d_raw, sizeof(double) * mono);
   PCBA_ALLOC(b->d_eval, sizeof(EvalOut) * n);
+  const unsigned mark_cap = 1u << 20;  // marked patches per step (extra marks are dropped)
+  PCBA_ALLOC(b->d_marks, sizeof(uint4) * 2 * (prec == PCBA_FP32 ? mark_cap : 1));
 #undef PCBA_ALLOC
   auto host_alloc = [&](void** p, size_t bytes) { return cudaMallocHost(p, bytes); };
   if (host_alloc((void**)&b->h_state, sizeof(ProbState) * n) != cudaSuccess ||
@@ -505,7 +699,7 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
                                   cudaMemcpyHostToDevice), "k1 prefix")))
     return rc;
   if ((rc = cleanup_ck(cudaMemset(b->d_rec, 0, sizeof(ChildRec) * nslots), "rec clear"))) return rc;
-  if ((rc = cleanup_ck(cudaMemset(b->d_slots, 0, sizeof(unsigned) * 4 * nslots), "slot clear")))
+  if ((rc = cleanup_ck(cudaMemset(b->d_slots, 0, sizeof(unsigned) * 3 * nslots), "slot clear")))
     return rc;
   if ((rc = cleanup_ck(cudaMemset(b->d_state, 0, sizeof(ProbState) * n), "state clear"))) return rc;
   if ((rc = cleanup_ck(cudaEventCreate(&b->ev0), "event"))) return rc;
@@ -522,18 +716,21 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   E.k3_pre_next = pre + 2 * (n + 1);
   E.k4_pre = pre + 3 * (n + 1);
   E.k1_pre = pre + 4 * (n + 1);
+  E.kr_pre = pre + 5 * (n + 1);
+  E.marks = b->d_marks;
+  E.mark_cap = prec == PCBA_FP32 ? mark_cap : 0;
   E.arena = b->d_arena;
   E.rec = b->d_rec;
   E.flagrank = b->d_slots;
-  E.arrive = b->d_slots + nslots;
-  E.hole = b->d_slots + 2 * nslots;
-  E.filler = b->d_slots + 3 * nslots;
+  E.hole = b->d_slots + nslots;
+  E.filler = b->d_slots + 2 * nslots;
   E.tilecnt = b->d_tilecnt;
   E.mono = b->d_mono;
   E.trace = b->d_trace;
   E.warm = b->d_warm;
   E.root_raw = nullptr;
   rc = prec == PCBA_FP32 ? setup_kernels<float>(b) : setup_kernels<double>(b);
+  if (!rc) rc = apply_k2_config(b, (b->want_tma && b->g.cfgs.size() > 1) ? 1 : 0);
   if (!rc && (flags & 3) == 0) rc = prec == PCBA_FP32 ? build_graph<float>(b) : build_graph<double>(b);
   if (rc) {
     std::string msg = g_err;
@@ -600,6 +797,9 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
     int it = 0;
     for (;; ++it) {
       if (it >= guard) return fail(PCBA_ERR_DEVICE_TIMEOUT, "host loop guard reached");
+      if (sizeof(T) == 4)
+        k_refresh<<<b->g.kr_grid, 32 * b->g.kr_wpb, b->g.kr_smem, s>>>(b->E, b->g.kr_cmax,
+                                                                      b->g.kr_lmax);
       if (instrument) {
         double bytes = 0;
         for (int k = 0; k < n; ++k)
@@ -610,6 +810,7 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
       }
       launch_k2<T>(b, s);
       if (instrument) PCBA_CK(cudaEventRecord(b->kev[2 * it + 1], s));
+      k_pup<<<b->g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
       k3_classify<<<b->g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
       k4_index<<<b->g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
       k4_move<<<b->g.k4_grid, PCBA_TPB, 0, s>>>(b->E);
@@ -645,6 +846,8 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   float ms = 0;
   PCBA_CK(cudaEventElapsedTime(&ms, b->ev0, b->ev1));
   b->total_ms = ms;
+  if (b->h_plan->guard_hit == 2)
+    return fail(PCBA_ERR_DEVICE_TIMEOUT, "a bulk copy of the subdivision kernel did not complete");
   if (b->h_plan->guard_hit) return fail(PCBA_ERR_DEVICE_TIMEOUT, "device loop guard reached");
   return 0;
 }
@@ -822,7 +1025,7 @@ int pcba_solve(pcba_handle* h, double opt_tol, double eq_tol, int max_iters, siz
 }
 
 int pcba_batch_create(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_total, int flags) {
-  if (flags < 0 || flags > 3) return fail(PCBA_ERR_INVALID, "flags must be 0..3");
+  if (flags < 0 || flags > 7) return fail(PCBA_ERR_INVALID, "flags must be 0..7");
   return batch_create_impl(out, hs, n, mem_cap_total, flags);
 }
 
@@ -860,6 +1063,43 @@ int pcba_batch_timing(const pcba_batch* b, double* total_ms, double* subdiv_ms,
   return 0;
 }
 
+int pcba_batch_autotune(pcba_batch* b, double opt_tol, double eq_tol, int max_iters,
+                        double* ms_per_config, int max_configs, int* chosen) {
+  if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
+  const int ncfg = (int)b->g.cfgs.size();
+  double best = 1e300;
+  int best_i = b->g.cfg;
+  for (int i = 0; i < ncfg; ++i) {
+    if (b->g.cfgs[i].tma && !b->want_tma) continue;
+    int rc = apply_k2_config(b, i);
+    if (!rc) rc = rebuild_graph(b);
+    if (!rc) rc = batch_solve_impl(b, nullptr, opt_tol, eq_tol, max_iters, 0, nullptr, nullptr);
+    if (!rc) rc = batch_solve_impl(b, nullptr, opt_tol, eq_tol, max_iters, 0, nullptr, nullptr);
+    if (rc) return rc;
+    if (ms_per_config && i < max_configs) ms_per_config[i] = b->total_ms;
+    if (b->total_ms < best) {
+      best = b->total_ms;
+      best_i = i;
+    }
+  }
+  int rc = apply_k2_config(b, best_i);
+  if (!rc) rc = rebuild_graph(b);
+  if (rc) return rc;
+  if (chosen) *chosen = best_i;
+  return ncfg;
+}
+
+int pcba_batch_config(const pcba_batch* b, int* tma, int* warps_per_block, int* stages,
+                      int* grid) {
+  if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
+  const Grids::K2Cfg& c = b->g.cfgs[b->g.cfg];
+  if (tma) *tma = c.tma ? 1 : 0;
+  if (warps_per_block) *warps_per_block = c.wpb;
+  if (stages) *stages = c.stages;
+  if (grid) *grid = c.grid;
+  return b->g.cfg;
+}
+
 int pcba_batch_launch_bytes(const pcba_batch* b, double* bytes, int max_launches) {
   if (!b || !bytes || max_launches < 0) return fail(PCBA_ERR_INVALID, "bad launch-bytes request");
   const int n = std::min<int>(max_launches, (int)b->launch_bytes.size());
@@ -872,11 +1112,18 @@ int pcba_batch_stats(const pcba_batch* b, long long* loop_iters, long long* kern
   if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
   const long long it = b->h_plan ? b->h_plan->steps_global : 0;
   if (loop_iters) *loop_iters = it;
-  // prologue: k1_matrices, k1_convert, k_eval, k_init; 5 kernels per loop
-  // iteration; epilogue: k_eval
-  if (kernel_launches) *kernel_launches = 5 + 5 * it;
+  // prologue: k1_matrices, k1_convert, k_eval, k_init; 6 kernels per loop
+  // iteration (7 with the FP32 refresh); epilogue: k_eval
+  if (kernel_launches) *kernel_launches = 5 + (b->precision == PCBA_FP32 ? 7 : 6) * it;
   if (h2d_bytes) *h2d_bytes = b->h2d_bytes;
   if (d2h_bytes) *d2h_bytes = b->d2h_bytes;
+  return 0;
+}
+
+int pcba_batch_refresh_stats(const pcba_batch* b, long long* marked, long long* refreshed) {
+  if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
+  if (marked) *marked = (long long)b->h_plan->marks_total;
+  if (refreshed) *refreshed = (long long)b->h_plan->refreshed_total;
   return 0;
 }
 
@@ -940,8 +1187,10 @@ int pcba_get_list(pcba_handle* h, long long* K_out, double* cost, double* ineq, 
       float* e = err + k * nerr;
       if (f32) {
         e[0] = *(const float*)(it + 40);
-        for (int i = 0; i < d.alpha; ++i) e[1 + i] = ((const float*)(it + d.off_eg))[i];
-        for (int i = 0; i < d.beta; ++i) e[1 + d.alpha + i] = ((const float*)(it + d.off_eh))[i];
+        // the sign bit marks refresh candidates; the bound is the magnitude
+        for (int i = 0; i < d.alpha; ++i) e[1 + i] = std::fabs(((const float*)(it + d.off_eg))[i]);
+        for (int i = 0; i < d.beta; ++i)
+          e[1 + d.alpha + i] = std::fabs(((const float*)(it + d.off_eh))[i]);
       } else {
         for (int i = 0; i < nerr; ++i) e[i] = 0.0f;
       }

@@ -33,6 +33,7 @@ struct ProbDesc {
   int tiles_g, tiles_h, tiles;  // subdivision work units per item
   int form_bernstein;        // 1: inputs already Bernstein patches
   int move_chunks;           // compaction work units per item
+  int groups_g, groups_h;    // 32-patch column groups per family (TMA subdivision)
   int P[PCBA_MAXD], G[PCBA_MAXD], H[PCBA_MAXD];
   double lo[PCBA_MAXD], hi[PCBA_MAXD];
   long long item_bytes;      // stride of the list
@@ -101,6 +102,9 @@ struct Plan {
   unsigned k3_tiles;
   unsigned k3_tiles_next;
   unsigned k4_units;
+  unsigned kr_units;
+  unsigned mark_count[2];  // marked patches appended by the subdivision of even / odd steps
+  unsigned long long marks_total, refreshed_total;
   unsigned k3_done;
   int any_running;
   int steps_global;
@@ -120,10 +124,12 @@ struct Engine {
   unsigned* k3_pre;        // [np + 1]
   unsigned* k3_pre_next;   // [np + 1]
   unsigned* k4_pre;        // [np + 1]
+  unsigned* kr_pre;        // [np + 1] (unused)
+  uint4* marks;            // [2][mark_cap] (problem, child slot, family, patch) of marked patches
+  unsigned mark_cap;
   char* arena;
   ChildRec* rec;           // per slot
   unsigned* flagrank;      // per slot: keep << 31 | rank within its tile
-  unsigned* arrive;        // per slot (parent): tiles finished
   unsigned* hole;          // per slot
   unsigned* filler;        // per slot
   unsigned* tilecnt;       // per tile: kept count, then exclusive offset
@@ -132,6 +138,7 @@ struct Engine {
   const double* warm;      // [np][PCBA_MAXD] or null
   double* root_raw;        // optional FP64 root patch dump
   const unsigned* k1_pre;  // [np + 1] patches per problem prefix
+  const void* tmaps;       // [np][2] tensor maps (CUtensorMap) of the g / h blocks, or null
 };
 
 // ---------------------------------------------------------------------------

@@ -345,6 +345,57 @@ __device__ __forceinline__ float okey32_dec(unsigned k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
 }
 
+// FP32 error bounds are stored with a mark in the sign bit, set when the bound
+// itself changes a decision of Def. 3 for this patch: the stored coefficients
+// (min s, max s) would decide it (infeasible, feasible, or inside the
+// equality window) but the enclosure [s_min - e, s_max + e] does not.  The
+// magnitude is the bound; k_refresh recomputes marked patches.
+__device__ __forceinline__ float mark_err(float e, float smin, float smax, float lo, float hi,
+                                          int fam, float eqt) {
+  // a refresh cannot go below about one rounding of the coefficients: leave
+  // patches whose bound is already close to that floor
+  if (e <= 8.0f * fmaxf(fabsf(smin), fabsf(smax)) * 0x1p-24f) return e;
+  bool flip;
+  if (fam == 0) {
+    flip = (lo <= 0.0f && hi >= 0.0f) && (smin > 0.0f || smax < 0.0f);
+  } else {
+    const bool inf_e = lo > 0.0f || hi < 0.0f, inf_s = smin > 0.0f || smax < 0.0f;
+    const bool win_e = lo >= -eqt && lo <= 0.0f && hi >= 0.0f && hi <= eqt;
+    const bool win_s = smin >= -eqt && smin <= 0.0f && smax >= 0.0f && smax <= eqt;
+    flip = inf_e != inf_s || win_e != win_s;
+  }
+  return flip ? -e : e;
+}
+
+// Where a marked patch lives: problem, the two child slots, and the list of
+// the current step (steps alternate between two lists).
+struct MarkCtx {
+  int p, kL, kR;
+  uint4* list;
+  unsigned* count;
+  unsigned cap;
+};
+
+// Warp-aggregated append of the marked children of this warp's patches
+// (fam 0/1: constraint family, fam 2: the cost patch, ip = patch index).
+__device__ __forceinline__ void append_marks(const MarkCtx& m, bool mL, bool mR, int fam, int ip) {
+  const unsigned bl = __ballot_sync(0xffffffffu, mL), br = __ballot_sync(0xffffffffu, mR);
+  if (!(bl | br)) return;
+  const int lane = threadIdx.x & 31;
+  unsigned base = 0;
+  if (lane == 0) base = atomicAdd(m.count, (unsigned)(__popc(bl) + __popc(br)));
+  base = __shfl_sync(0xffffffffu, base, 0);
+  const unsigned below = (1u << lane) - 1u;
+  if (mL) {
+    const unsigned q = base + __popc(bl & below);
+    if (q < m.cap) m.list[q] = make_uint4((unsigned)m.p, (unsigned)m.kL, (unsigned)fam, (unsigned)ip);
+  }
+  if (mR) {
+    const unsigned q = base + __popc(bl) + __popc(br & below);
+    if (q < m.cap) m.list[q] = make_uint4((unsigned)m.p, (unsigned)m.kR, (unsigned)fam, (unsigned)ip);
+  }
+}
+
 template <int NV>
 __device__ __forceinline__ void warp_max_d(double (&v)[NV]) {
 #pragma unroll
@@ -361,23 +412,27 @@ __device__ __forceinline__ void warp_max_d(double (&v)[NV]) {
 //   half 2^-23 + 2^-149           re-centring, half = half the child's range,
 //   |O'| 2^-52                    rounding of the new offset,
 // all accumulated with upward rounding.
+// head: where the parent's head bytes (box, meta, cost) are read from: the
+// parent item itself, or a shared-memory copy of them.
 template <typename T, int NMAX>
-__device__ void cost_part(const ProbDesc* D, char* parent, char* right, int r, ChildRec* recL,
-                          ChildRec* recR, T* stage) {
+__device__ void cost_part(const ProbDesc* D, const char* head, char* parent, char* right, int r,
+                          ChildRec* recL, ChildRec* recR, T* stage, const MarkCtx& mk,
+                          double cost_thr) {
   const int lane = threadIdx.x & 31;
   const int cp = D->cp;
   const int n = D->P[r];
   const int stride = axis_stride(D->P, D->l, r);
   const int nf = cp / (n + 1);
   const int blk = (n + 1) * stride;
-  T* src = (T*)(parent + D->off_cost);
+  const T* src = (const T*)(head + D->off_cost);
+  T* dstL = (T*)(parent + D->off_cost);
   T* dstR = (T*)(right + D->off_cost);
   T* sL = stage;
   T* sR = stage + cp;
   double O = 0.0, ep = 0.0;
   if constexpr (sizeof(T) == 4) {
-    O = *(const double*)(parent + 32);
-    ep = (double)*(const float*)(parent + 40);
+    O = *(const double*)(head + 32);
+    ep = (double)*(const float*)(head + 40);
   }
   double v[5] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
   for (int f = lane; f < nf; f += 32) {
@@ -392,7 +447,7 @@ __device__ void cost_part(const ProbDesc* D, char* parent, char* right, int r, C
   const double minL = -v[0], maxL = v[1], minR = -v[2], maxR = v[3];
   if constexpr (sizeof(T) == 8) {
     for (int j = lane; j < cp; j += 32) {
-      src[j] = sL[j];
+      dstL[j] = sL[j];
       dstR[j] = sR[j];
     }
     if (lane == 0) {
@@ -424,7 +479,7 @@ __device__ void cost_part(const ProbDesc* D, char* parent, char* right, int r, C
       lows[c] = __dsub_rd(__dadd_rd(On, smin), (double)ef);
       highs[c] = __dadd_ru(__dadd_ru(On, smax), (double)ef);
     }
-    float* fsrc = (float*)src;
+    float* fsrc = (float*)dstL;
     float* fdst = (float*)dstR;
     const float* fL = (const float*)sL;
     const float* fR = (const float*)sR;
@@ -442,6 +497,8 @@ __device__ void cost_part(const ProbDesc* D, char* parent, char* right, int r, C
       recR->pmin = okey(lows[1]);
       recR->pmax = okey(highs[1]);
     }
+    // the cost bound is refreshed once it is a visible part of opt_tol
+    append_marks(mk, lane == 0 && efs[0] > cost_thr, lane == 0 && efs[1] > cost_thr, 2, 0);
   }
   __syncwarp();
 }
@@ -450,7 +507,8 @@ __device__ void cost_part(const ProbDesc* D, char* parent, char* right, int r, C
 // the warp's maxima go to the child records with fire-and-forget atomics.
 template <typename T, int NMAX>
 __device__ void constraint_part(const ProbDesc* D, char* parent, char* right, int r, int fam,
-                                int tt, ChildRec* recL, ChildRec* recR) {
+                                int tt, ChildRec* recL, ChildRec* recR, float eqt,
+                                const MarkCtx& mk) {
   constexpr bool RIG = sizeof(T) == 4;
   const int lane = threadIdx.x & 31;
   const int i = tt * PCBA_TPB + threadIdx.x;
@@ -466,6 +524,7 @@ __device__ void constraint_part(const ProbDesc* D, char* parent, char* right, in
   // reduced quantities of this thread (identity for masked lanes):
   //   fam 0: lo_L, hi_L, lo_R, hi_R;  fam 1: lo_L, -hi_L, |.|_L, lo_R, -hi_R, |.|_R
   T v[6] = {T(-INFINITY), T(-INFINITY), T(-INFINITY), T(-INFINITY), T(-INFINITY), T(-INFINITY)};
+  bool mL = false, mR = false;
   if (i < cnt) {
     FibAcc<T> a;
     a.minL = a.minR = T(INFINITY);
@@ -479,14 +538,18 @@ __device__ void constraint_part(const ProbDesc* D, char* parent, char* right, in
       float* ep = (float*)(parent + (fam ? D->off_eh : D->off_eg));
       float* er = (float*)(right + (fam ? D->off_eh : D->off_eg));
       const float fn = (float)n;
-      const float ec = __fadd_ru(__fadd_ru(ep[i], __fmul_ru((float)a.m, fn * 0x1p-24f)),
+      const float ec = __fadd_ru(__fadd_ru(fabsf(ep[i]), __fmul_ru((float)a.m, fn * 0x1p-24f)),
                                  fn * 0x1p-149f);
-      ep[i] = ec;
-      er[i] = ec;
       loL = __fsub_rd((float)a.minL, ec);
       hiL = __fadd_ru((float)a.maxL, ec);
       loR = __fsub_rd((float)a.minR, ec);
       hiR = __fadd_ru((float)a.maxR, ec);
+      const float eL = mark_err(ec, (float)a.minL, (float)a.maxL, loL, hiL, fam, eqt);
+      const float eR = mark_err(ec, (float)a.minR, (float)a.maxR, loR, hiR, fam, eqt);
+      ep[i] = eL;
+      er[i] = eR;
+      mL = __float_as_uint(eL) >> 31;
+      mR = __float_as_uint(eR) >> 31;
     } else {
       loL = a.minL;
       hiL = a.maxL;
@@ -500,6 +563,7 @@ __device__ void constraint_part(const ProbDesc* D, char* parent, char* right, in
       v[3] = loR; v[4] = -hiR; v[5] = fmax(hiR, -loR);
     }
   }
+  if constexpr (RIG) append_marks(mk, mL, mR, fam, i);
   const int nv = fam ? 6 : 4;
   double w[6];
   if constexpr (RIG) {
@@ -557,10 +621,8 @@ __device__ __forceinline__ ChildRec load_rec_cg(const ChildRec* p) {
 // Work unit = (problem, parent item k, tile t).  Tile 0 also splits the cost
 // patch (warp 0) and the box; every tile splits up to PCBA_TPB constraint
 // patches, 32 per warp.  Warps never wait for each other inside a unit: each
-// warp publishes its maxima with atomics and then counts itself in the item's
-// arrival counter; the last of the tiles x 8 warps of an item to arrive reads
-// the two complete child records and, for each feasible child, lowers p_up
-// (Def. 4) with an atomic min.
+// warp publishes its bound maxima with fire-and-forget atomics into the two
+// child records; p_up is computed from the finished records by k_pup.
 //
 // Each block takes one contiguous range of units, so consecutive units mostly
 // belong to one problem; the problem's descriptor and step state are copied to
@@ -571,12 +633,13 @@ __global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
   __shared__ __align__(16) ProbDesc sD;
   __shared__ int sK, sR;
   const unsigned units = E.plan->k2_units;
-  const double eq_tol = E.params->eq_tol;
+  const float eqt = __double2float_ru(E.params->eq_tol);
+  const double cost_thr = E.params->opt_tol * (1.0 / 64.0);
+  const int mpar = E.plan->steps_global & 1;
   const unsigned per = (units + gridDim.x - 1) / gridDim.x;
   const unsigned u0 = blockIdx.x * per;
   const unsigned u1 = min(units, u0 + per);
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  constexpr unsigned WARPS = PCBA_TPB / 32;
   int p = -1;
   unsigned pbeg = 0, pend = 0;
   for (unsigned u = u0; u < u1; ++u) {
@@ -604,8 +667,10 @@ __global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
     char* right = E.arena + D->list_off + (size_t)(k + K) * D->item_bytes;
     ChildRec* recL = E.rec + D->slot_off + k;
     ChildRec* recR = E.rec + D->slot_off + k + K;
+    const MarkCtx mk{p, k, k + K, E.marks + (size_t)mpar * E.mark_cap, &E.plan->mark_count[mpar],
+                     E.mark_cap};
     if (t == 0 && warp == 0) {
-      cost_part<T, NMAX>(D, parent, right, r, recL, recR, (T*)k2stage);
+      cost_part<T, NMAX>(D, parent, parent, right, r, recL, recR, (T*)k2stage, mk, cost_thr);
       if (lane == 0) {
         unsigned* iL = (unsigned*)parent;
         unsigned* iR = (unsigned*)right;
@@ -618,22 +683,598 @@ __global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
     const int fam = t < D->tiles_g ? 0 : 1;
     const int tt = fam ? t - D->tiles_g : t;
     if (tt < (fam ? D->tiles_h : D->tiles_g))
-      constraint_part<T, NMAX>(D, parent, right, r, fam, tt, recL, recR);
+      constraint_part<T, NMAX>(D, parent, right, r, fam, tt, recL, recR, eqt, mk);
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// K2 with TMA staging (sm_90+ bulk tensor copies; used on sm_103a)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      " selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, int y, int z,
+                                            unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes,
+                                          unsigned long long* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+          "r"(smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// Waits for phase 'parity' of a stage barrier; gives up after ~1 s (a copy that
+// never lands), records it in the plan and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsigned parity,
+                                                  Plan* plan) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  for (unsigned it = 0;; ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if ((it & 255u) == 255u && globaltimer() - t0 > 1000000000ull) {
+      atomicExch(&plan->guard_hit, 2);
+      return false;
+    }
+  }
+}
+
+// Resolves a warp work unit u = (problem p, parent item k, column group g).
+struct WarpUnit {
+  int p, k, g, fam, x;
+};
+__device__ __forceinline__ WarpUnit resolve_unit(const Engine& E, unsigned u, int& p,
+                                                 unsigned& pbeg, unsigned& pend) {
+  if (u >= pend || u < pbeg) {
+    p = find_problem(E.k2_pre, E.np, u);
+    pbeg = E.k2_pre[p];
+    pend = E.k2_pre[p + 1];
+  }
+  const ProbDesc* D = E.desc + p;
+  const int groups = D->tiles;
+  const unsigned local = u - pbeg;
+  WarpUnit w;
+  w.p = p;
+  w.k = (int)(local / (unsigned)groups);
+  w.g = (int)(local - (unsigned)w.k * groups);
+  if (w.g < D->groups_g) {
+    w.fam = 0;
+    w.x = w.g * 32;
+  } else if (w.g < D->groups_g + D->groups_h) {
+    w.fam = 1;
+    w.x = (w.g - D->groups_g) * 32;
+  } else {
+    w.fam = -1;  // cost-only unit of a problem without constraints
+    w.x = 0;
+  }
+  return w;
+}
+
+// Lane 0 starts the copies of one unit into a stage: the [C][32] column block
+// of the parent (one 3-D tensor copy) and, in FP32 mode, its 32 error bounds.
+// Bytes of the item head (box, cost meta, cost patch) copied for group 0.
+__device__ __forceinline__ unsigned head_bytes(const ProbDesc* D, unsigned w) {
+  return (unsigned)((D->off_cost + (long long)D->cp * w + 15) / 16 * 16);
+}
+
+template <typename T>
+__device__ __forceinline__ void issue_unit(const Engine& E, const WarpUnit& w, T* stage,
+                                           float* estage, unsigned char* head,
+                                           unsigned long long* bar) {
+  const ProbDesc* D = E.desc + w.p;
+  const char* item = E.arena + D->list_off + (size_t)w.k * D->item_bytes;
+  const unsigned hb = w.g == 0 ? head_bytes(D, (unsigned)sizeof(T)) : 0u;
+  if (w.fam < 0) {
+    mbar_arrive_expect_tx(bar, hb);
+    bulk_load(head, item, hb, bar);
+    return;
+  }
+  const int C = w.fam ? D->ch : D->cg;
+  unsigned bytes = (unsigned)C * 32u * (unsigned)sizeof(T) + hb;
+  if (sizeof(T) == 4) bytes += 128u;
+  mbar_arrive_expect_tx(bar, bytes);
+  if (hb) bulk_load(head, item, hb, bar);
+  const char* tm = (const char*)E.tmaps + ((size_t)w.p * 2 + w.fam) * 128;
+  tma_load_3d(stage, tm, w.x, 0, w.k, bar);
+  if (sizeof(T) == 4)
+    bulk_load(estage, item + (w.fam ? D->off_eh : D->off_eg) + (size_t)w.x * 4, 128u, bar);
+}
+
+// Fibres of one column (lane) of a staged [C][32] block: loads from shared
+// memory, children stored straight to global memory (coalesced across lanes).
+template <typename T, int N, bool RIG>
+__device__ __forceinline__ void staged_fibres(const T* stage, T* gL, T* gR, size_t pad, int C,
+                                              int stride, int lane, FibAcc<T>& a) {
+  const int nf = C / (N + 1);
+  const int blk = (N + 1) * stride;
+  const size_t st = (size_t)stride * pad;
+#pragma unroll 1
+  for (int f = 0; f < nf; ++f) {
+    const int o = f / stride;
+    const int c0 = o * blk + (f - o * stride);
+    const T* sc = stage + c0 * 32 + lane;
+    T* colL = gL + (size_t)c0 * pad;
+    T* colR = gR + (size_t)c0 * pad;
+    T q[N + 1];
+#pragma unroll
+    for (int j = 0; j <= N; ++j) q[j] = sc[j * stride * 32];
+    if constexpr (RIG) {
+#pragma unroll
+      for (int j = 0; j <= N; ++j) a.m = fmax(a.m, fabs(q[j]));
+    }
+    // left_0 = f_0 already sits in the parent slot the left child overwrites
+    colR[N * st] = q[N];
+    a.minL = fmin(a.minL, q[0]);
+    a.maxL = fmax(a.maxL, q[0]);
+    a.minR = fmin(a.minR, q[N]);
+    a.maxR = fmax(a.maxR, q[N]);
+#pragma unroll
+    for (int k = 1; k <= N; ++k) {
+#pragma unroll
+      for (int j = 0; j <= N - k; ++j) q[j] = mulrn(addrn(q[j], q[j + 1]), T(0.5));
+      colL[k * st] = q[0];
+      colR[(N - k) * st] = q[N - k];
+      a.minL = fmin(a.minL, q[0]);
+      a.maxL = fmax(a.maxL, q[0]);
+      a.minR = fmin(a.minR, q[N - k]);
+      a.maxR = fmax(a.maxR, q[N - k]);
+    }
+  }
+}
+
+// The bound reductions of one warp's 32 patches, published with atomics
+// (same quantities as constraint_part).
+template <typename T>
+__device__ __forceinline__ void publish_bounds(int fam, bool any_valid, T (&v)[6],
+                                               ChildRec* recL, ChildRec* recR) {
+  constexpr bool RIG = sizeof(T) == 4;
+  const int lane = threadIdx.x & 31;
+  const int nv = fam ? 6 : 4;
+  double w[6];
+  if constexpr (RIG) {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const unsigned k = q < nv ? __reduce_max_sync(0xffffffffu, okey32(v[q])) : 0u;
+      w[q] = (double)okey32_dec(k);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 6; ++q) w[q] = v[q];
+    warp_max_d<6>(w);
+  }
+  if (lane == 0 && any_valid) {
+    if (fam == 0) {
+      atomicMax(&recL->gminmax, okey(w[0]));
+      atomicMax(&recL->gmaxmax, okey(w[1]));
+      atomicMax(&recR->gminmax, okey(w[2]));
+      atomicMax(&recR->gmaxmax, okey(w[3]));
+    } else {
+      atomicMax(&recL->hminmax, okey(w[0]));
+      atomicMax(&recL->hnegmaxmin, okey(w[1]));
+      atomicMax(&recL->habsmax, okey(w[2]));
+      atomicMax(&recR->hminmax, okey(w[3]));
+      atomicMax(&recR->hnegmaxmin, okey(w[4]));
+      atomicMax(&recR->habsmax, okey(w[5]));
+    }
+  }
+}
+
+// Work unit = (problem, parent item k, group g of 32 constraint patches); one
+// warp per unit.  Every warp runs its own pipeline of 'stages' shared-memory
+// stages: while it computes unit j, the copies of units j+1 .. j+stages-1 are
+// in flight (TMA, completion on an mbarrier).  Group 0 also splits the cost
+// patch and the box, whose bytes (box, meta, cost) come with the same copy.
+// The kernel only streams: no fence and no value-returning atomic on the way.
+template <typename T, int NMAX>
+__global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, int stage_elems,
+                                                        int cpmax) {
+  constexpr bool RIG = sizeof(T) == 4;
+  extern __shared__ __align__(128) unsigned char k2t_smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  // per warp: stages x (stage_elems T + 32 floats + head), then 2*cpmax T of cost
+  // staging; head = box, cost meta and cost patch of the parent (group 0)
+  const size_t head_cap = ((size_t)64 + (size_t)cpmax * sizeof(T) + 127) / 128 * 128;
+  const size_t stage_bytes = (size_t)stage_elems * sizeof(T) + 128 + head_cap;
+  const size_t warp_bytes = (size_t)stages * stage_bytes + (size_t)2 * cpmax * sizeof(T);
+  const size_t warp_bytes_al = (warp_bytes + 127) / 128 * 128;
+  unsigned char* wb = k2t_smem + (size_t)warp * warp_bytes_al;
+  unsigned long long* bars =
+      (unsigned long long*)(k2t_smem + (size_t)wpb * warp_bytes_al) + (size_t)warp * stages;
+  T* cost_stage = (T*)(wb + (size_t)stages * stage_bytes);
+  if (lane == 0) {
+    for (int s = 0; s < stages; ++s) mbar_init(&bars[s], 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  fence_proxy_async_smem();
+  const unsigned units = E.plan->k2_units;
+  const float eqt = __double2float_ru(E.params->eq_tol);
+  const double cost_thr = E.params->opt_tol * (1.0 / 64.0);
+  const int mpar = E.plan->steps_global & 1;
+  const unsigned per = (units + gridDim.x - 1) / gridDim.x;
+  const unsigned u0 = blockIdx.x * per;
+  const unsigned u1 = min(units, u0 + per);
+  const unsigned first = u0 + warp;
+  const int J = first < u1 ? (int)((u1 - first + wpb - 1) / wpb) : 0;
+  int ip = -1, cp_ = -1;
+  unsigned ibeg = 0, iend = 0, cbeg = 0, cend = 0;
+  // prologue
+  for (int j = 0; j < J && j < stages; ++j) {
     if (lane == 0) {
-      __threadfence();
-      const unsigned old = atomicAdd(E.arrive + D->slot_off + k, 1u);
-      if (old == (unsigned)tiles * WARPS - 1) {
-        E.arrive[D->slot_off + k] = 0u;
-        __threadfence();
-        const ChildRec cl = load_rec_cg(recL);
-        const ChildRec cr = load_rec_cg(recR);
-        unsigned long long best = ~0ull;
-        if (rec_feasible(cl, eq_tol)) best = cl.pmax;
-        if (rec_feasible(cr, eq_tol) && cr.pmax < best) best = cr.pmax;
-        if (best != ~0ull) atomicMin(&E.state[p].pup_key, best);
+      const WarpUnit w = resolve_unit(E, first + (unsigned)j * wpb, ip, ibeg, iend);
+      unsigned char* st = wb + (size_t)j * stage_bytes;
+      issue_unit<T>(E, w, (T*)st, (float*)(st + (size_t)stage_elems * sizeof(T)),
+                    st + (size_t)stage_elems * sizeof(T) + 128, &bars[j]);
+    }
+  }
+  for (int j = 0; j < J; ++j) {
+    const int s = j % stages;
+    const unsigned parity = (unsigned)(j / stages) & 1u;
+    unsigned char* st = wb + (size_t)s * stage_bytes;
+    const T* stage = (const T*)st;
+    const float* estage = (const float*)(st + (size_t)stage_elems * sizeof(T));
+    const WarpUnit w = resolve_unit(E, first + (unsigned)j * wpb, cp_, cbeg, cend);
+    const ProbDesc* D = E.desc + w.p;
+    ProbState* S = E.state + w.p;
+    const int K = S->K, r = S->r;
+    char* parent = E.arena + D->list_off + (size_t)w.k * D->item_bytes;
+    char* right = E.arena + D->list_off + (size_t)(w.k + K) * D->item_bytes;
+    ChildRec* recL = E.rec + D->slot_off + w.k;
+    ChildRec* recR = E.rec + D->slot_off + w.k + K;
+    const MarkCtx mk{w.p, w.k, w.k + K, E.marks + (size_t)mpar * E.mark_cap,
+                     &E.plan->mark_count[mpar], E.mark_cap};
+    bool ok = true;
+    if (lane == 0) ok = mbar_wait_bounded(&bars[s], parity, E.plan);
+    ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+    if (!ok) {
+      // copies did not land (recorded in the plan): wait, bounded, for the
+      // copies still in flight into this warp's other stages, then leave
+      if (lane == 0)
+        for (int jj = j + 1; jj < J && jj < j + stages; ++jj)
+          mbar_wait_bounded(&bars[jj % stages], (unsigned)(jj / stages) & 1u, E.plan);
+      __syncwarp();
+      return;
+    }
+    if (w.g == 0) {
+      const unsigned char* head = st + (size_t)stage_elems * sizeof(T) + 128;
+      cost_part<T, NMAX>(D, (const char*)head, parent, right, r, recL, recR, cost_stage, mk,
+                         cost_thr);
+      if (lane == 0) {
+        const unsigned* iP = (const unsigned*)head;
+        unsigned* iL = (unsigned*)parent;
+        unsigned* iR = (unsigned*)right;
+        for (int q = 0; q < D->l; ++q) {
+          iL[q] = iP[q];
+          iR[q] = iP[q];
+        }
+        iL[r] = 2u * iP[r];
+        iR[r] = 2u * iP[r] + 1u;
       }
     }
+    if (w.fam >= 0) {
+      const int fam = w.fam;
+      const int cnt = fam ? D->beta : D->alpha;
+      const size_t pad = fam ? D->bpad : D->apad;
+      const int* deg = fam ? D->H : D->G;
+      const int C = fam ? D->ch : D->cg;
+      const long long off = fam ? D->off_h : D->off_g;
+      const int n = deg[r];
+      const int stride = axis_stride(deg, D->l, r);
+      const int i = w.x + lane;
+      T v[6] = {T(-INFINITY), T(-INFINITY), T(-INFINITY), T(-INFINITY), T(-INFINITY), T(-INFINITY)};
+      bool mL = false, mR = false;
+      if (i < cnt) {
+        FibAcc<T> a;
+        a.minL = a.minR = T(INFINITY);
+        a.maxL = a.maxR = T(-INFINITY);
+        a.m = T(0);
+        T* gL = (T*)(parent + off) + i;
+        T* gR = (T*)(right + off) + i;
+        dispatch_degree<NMAX>(n, [&](auto nc) {
+          staged_fibres<T, decltype(nc)::value, RIG>(stage, gL, gR, pad, C, stride, lane, a);
+        });
+        T loL, hiL, loR, hiR;
+        if constexpr (RIG) {
+          const float fnn = (float)n;
+          const float ec = __fadd_ru(__fadd_ru(fabsf(estage[lane]),
+                                               __fmul_ru((float)a.m, fnn * 0x1p-24f)),
+                                     fnn * 0x1p-149f);
+          loL = __fsub_rd((float)a.minL, ec);
+          hiL = __fadd_ru((float)a.maxL, ec);
+          loR = __fsub_rd((float)a.minR, ec);
+          hiR = __fadd_ru((float)a.maxR, ec);
+          const float eL = mark_err(ec, (float)a.minL, (float)a.maxL, loL, hiL, fam, eqt);
+          const float eR = mark_err(ec, (float)a.minR, (float)a.maxR, loR, hiR, fam, eqt);
+          ((float*)(parent + (fam ? D->off_eh : D->off_eg)))[i] = eL;
+          ((float*)(right + (fam ? D->off_eh : D->off_eg)))[i] = eR;
+          mL = __float_as_uint(eL) >> 31;
+          mR = __float_as_uint(eR) >> 31;
+        } else {
+          loL = a.minL;
+          hiL = a.maxL;
+          loR = a.minR;
+          hiR = a.maxR;
+        }
+        if (fam == 0) {
+          v[0] = loL; v[1] = hiL; v[2] = loR; v[3] = hiR;
+        } else {
+          v[0] = loL; v[1] = -hiL; v[2] = fmax(hiL, -loL);
+          v[3] = loR; v[4] = -hiR; v[5] = fmax(hiR, -loR);
+        }
+      }
+      if constexpr (RIG) append_marks(mk, mL, mR, fam, i);
+      publish_bounds<T>(fam, w.x < cnt, v, recL, recR);
+    }
+    // the stage is free again: reuse it for unit j + stages
     __syncwarp();
+    fence_proxy_async_smem();
+    if (lane == 0 && j + stages < J) {
+      const WarpUnit wn = resolve_unit(E, first + (unsigned)(j + stages) * wpb, ip, ibeg, iend);
+      issue_unit<T>(E, wn, (T*)st, (float*)(st + (size_t)stage_elems * sizeof(T)),
+                    st + (size_t)stage_elems * sizeof(T) + 128, &bars[s]);
+    }
+    __syncwarp();
+  }
+  // every issued unit was consumed above: no copy is in flight at exit
+}
+
+// ---------------------------------------------------------------------------
+// FP32 mode: refresh of marked patches from the FP64 monomials
+// ---------------------------------------------------------------------------
+// The error bound of an FP32 patch only grows from step to step, and most of
+// it is collected in the first bisections, when Bernstein coefficients on the
+// large boxes are far larger than the polynomial's values.  Once per sweep
+// (from the third sweep on) this kernel recomputes, for every item, the cost
+// patch and every constraint patch marked by the subdivision kernel (enclosure
+// meeting zero, see mark_err) directly from the FP64 monomial coefficients
+// over the item's current box (Sec. II-D, the conversion of k1_convert with
+// the box of the item): the new bound is the FP64 conversion bound plus one
+// rounding to FP32.  Unmarked patches keep their (larger, still valid) bound.
+//
+// Work unit = (problem, item, 32-patch group); each warp takes a contiguous
+// range of units so that the per-axis matrices of an item's box are built once.
+__device__ __forceinline__ void refresh_matrices(const double* binom, int l, const int* deg,
+                                                 const double* blo, const double* bhi,
+                                                 double* sT, int lane) {
+  for (int r = 0; r < l; ++r) {
+    const int n = deg[r];
+    const double lo = blo[r], w = bhi[r] - blo[r];
+    // powers lo^e and w^e (same products as dev_pow, kept in registers)
+    double lp[17], wp[17];
+    lp[0] = 1.0;
+    wp[0] = 1.0;
+#pragma unroll
+    for (int e = 1; e < 17; ++e) {
+      lp[e] = lp[e - 1] * lo;
+      wp[e] = wp[e - 1] * w;
+    }
+    double* T = sT + r * 578;
+    double* A = T + 289;
+    for (int e = lane; e < (n + 1) * (n + 1); e += 32) {
+      const int i = e / (n + 1), j = e - (e / (n + 1)) * (n + 1);
+      double t = 0.0, ta = 0.0;
+      const int kmax = i < j ? i : j;
+      for (int k = 0; k <= kmax; ++k) {
+        const double term = binom[i * 17 + k] / binom[n * 17 + k] * binom[j * 17 + k] *
+                            lp[j - k] * wp[k];
+        t += term;
+        ta += fabs(term);
+      }
+      T[e] = t;
+      A[e] = ta * (1.0 + 0x1p-40);
+    }
+  }
+  __syncwarp();
+}
+
+// Warp-cooperative conversion of one monomial tensor a (C coefficients,
+// multi-degree deg) with the matrices in sT; result in *sA, bound base in *sX.
+__device__ __forceinline__ double refresh_convert(const double* a, int C, int l, const int* deg,
+                                                  const double* sT, double*& sA, double*& sB,
+                                                  double*& sX, double*& sY, int lane) {
+  for (int j = lane; j < C; j += 32) {
+    const double v = a[j];
+    sA[j] = v;
+    sX[j] = fabs(v);
+  }
+  __syncwarp();
+  double gterms = 0.0;
+  for (int r = 0; r < l; ++r) {
+    const int n = deg[r];
+    int stride = 1;
+    for (int q = r + 1; q < l; ++q) stride *= deg[q] + 1;
+    const double* T = sT + r * 578;
+    const double* A = T + 289;
+    gterms += 4.0 * n + 8.0;
+    const int blk = (n + 1) * stride;
+    for (int o = lane; o < C; o += 32) {
+      const int hp = o / blk;
+      const int rem = o - hp * blk;
+      const int i = rem / stride;
+      const int in = rem - i * stride;
+      const double* src = sA + hp * blk + in;
+      const double* srcx = sX + hp * blk + in;
+      double s = 0.0, sx = 0.0;
+      for (int j = 0; j <= n; ++j) {
+        s = fma(T[i * (n + 1) + j], src[j * stride], s);
+        sx = __dadd_ru(sx, __dmul_ru(A[i * (n + 1) + j], srcx[j * stride]));
+      }
+      sB[o] = s;
+      sY[o] = sx;
+    }
+    __syncwarp();
+    double* t = sA; sA = sB; sB = t;
+    t = sX; sX = sY; sY = t;
+  }
+  double amax = 0.0;
+  for (int j = lane; j < C; j += 32) amax = fmax(amax, sX[j]);
+  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  return __dmul_ru(__dmul_ru(2.0 * gterms, 0x1p-53), amax);
+}
+
+// Slot of a child of the previous step after that step's compaction (Alg. 5),
+// or -1 if it was eliminated: kept children below K_save stay, kept children
+// above fill the holes from the top of the save list.
+__device__ __forceinline__ int slot_after_compaction(const Engine& E, const ProbDesc* D,
+                                                     const ProbState* S, int c) {
+  if (c >= S->twoK) return -1;
+  const unsigned fr = E.flagrank[D->slot_off + c];
+  if (!(fr >> 31)) return -1;
+  if (c < S->K_save) return c;
+  const int grank = (int)(E.tilecnt[D->tile_off + c / PCBA_TPB] + (fr & 0x7FFFFFFFu));
+  return (int)E.hole[D->slot_off + (S->K_save - 1 - grank)];
+}
+
+// Binomial coefficients C(n, k), n, k <= 16 (exact integers), filled once by
+// the library at start-up.
+__constant__ double c_binom[17 * 17];
+
+__global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
+  extern __shared__ double krs[];
+  const int par = (E.plan->steps_global + 1) & 1;  // the list of the previous step
+  const unsigned count = min(E.plan->mark_count[par], E.mark_cap);
+  if (count == 0) return;
+  const double* binom = c_binom;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  double* wbase = krs + (size_t)warp * (4 * cmax + 2 * 289 * lmax);
+  double* sA = wbase;
+  double* sB = sA + cmax;
+  double* sX = sB + cmax;
+  double* sY = sX + cmax;
+  double* sT = sY + cmax;
+  const uint4* list = E.marks + (size_t)par * E.mark_cap;
+  for (unsigned q = blockIdx.x * wpb + warp; q < count; q += gridDim.x * wpb) {
+    const uint4 m = list[q];
+    const int p = (int)m.x, fam = (int)m.z, ip = (int)m.w;
+    const ProbDesc* D = E.desc + p;
+    const ProbState* S = E.state + p;
+    if (S->status != PCBA_RUNNING) continue;
+    const int slot = slot_after_compaction(E, D, S, (int)m.y);
+    if (slot < 0) continue;
+    char* item = E.arena + D->list_off + (size_t)slot * D->item_bytes;
+    double blo[PCBA_MAXD], bhi[PCBA_MAXD];
+    for (int r = 0; r < D->l; ++r) {
+      const double w = ldexp(D->hi[r] - D->lo[r], -S->level[r]);
+      const unsigned idx = ((const unsigned*)item)[r];
+      blo[r] = D->lo[r] + w * (double)idx;
+      bhi[r] = D->lo[r] + w * (double)(idx + 1u);
+    }
+    const double* mono = E.mono + D->mono_off;
+    if (fam == 2) {
+      if (D->cp > cmax) continue;
+      // the cost patch: recomputed and re-centred on its range
+      refresh_matrices(binom, D->l, D->P, blo, bhi, sT, lane);
+      const double err64 = refresh_convert(mono, D->cp, D->l, D->P, sT, sA, sB, sX, sY, lane);
+      double bmin = INFINITY, bmax = -INFINITY;
+      for (int j = lane; j < D->cp; j += 32) { bmin = fmin(bmin, sA[j]); bmax = fmax(bmax, sA[j]); }
+      for (int o = 16; o > 0; o >>= 1) {
+        bmin = fmin(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
+        bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+      }
+      const double O = 0.5 * (bmin + bmax);
+      float* dst = (float*)(item + D->off_cost);
+      double emax = 0.0;
+      for (int j = lane; j < D->cp; j += 32) {
+        const double d = sA[j] - O;
+        const float sv = __double2float_rn(d);
+        dst[j] = sv;
+        emax = fmax(emax, __dadd_ru(fabs((double)sv - d), __dmul_ru(fabs(d), 0x1p-52)));
+      }
+      for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+      if (lane == 0) {
+        *(double*)(item + 32) = O;
+        *(float*)(item + 40) = __double2float_ru(__dadd_ru(emax, err64));
+        atomicAdd(&E.plan->refreshed_total, 1ull);
+      }
+      __syncwarp();
+      continue;
+    }
+    const int C = fam ? D->ch : D->cg;
+    if (C > cmax) continue;
+    const int* deg = fam ? D->H : D->G;
+    refresh_matrices(binom, D->l, deg, blo, bhi, sT, lane);
+    const size_t pad = fam ? D->bpad : D->apad;
+    float* block = (float*)(item + (fam ? D->off_h : D->off_g));
+    float* earr = (float*)(item + (fam ? D->off_eh : D->off_eg));
+    const double* fam_mono = mono + D->cp + (fam ? (long long)D->alpha * D->cg : 0);
+    const double err64 =
+        refresh_convert(fam_mono + (long long)ip * C, C, D->l, deg, sT, sA, sB, sX, sY, lane);
+    double emax = 0.0;
+    for (int j = lane; j < C; j += 32) {
+      const float sv = __double2float_rn(sA[j]);
+      block[(size_t)j * pad + ip] = sv;
+      emax = fmax(emax, fabs((double)sv - sA[j]));
+    }
+    for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    if (lane == 0) {
+      earr[ip] = __double2float_ru(__dadd_ru(emax, err64));
+      atomicAdd(&E.plan->refreshed_total, 1ull);
+    }
+    __syncwarp();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Def. 4: p_up over the feasible children, from the finished records
+// ---------------------------------------------------------------------------
+// Runs after the subdivision kernel, over the same child tiles as k3_classify:
+// each warp reduces the pmax of its feasible children and one atomic min per
+// warp lowers the problem's p_up key.
+__global__ void __launch_bounds__(PCBA_TPB) k_pup(Engine E) {
+  const unsigned tiles_total = E.plan->k3_tiles;
+  const double eq_tol = E.params->eq_tol;
+  for (unsigned u = blockIdx.x; u < tiles_total; u += gridDim.x) {
+    const int p = find_problem(E.k3_pre, E.np, u);
+    const ProbDesc* D = E.desc + p;
+    ProbState* S = E.state + p;
+    const int twoK = 2 * S->K;
+    const int c = (int)(u - E.k3_pre[p]) * PCBA_TPB + threadIdx.x;
+    unsigned long long best = ~0ull;
+    if (c < twoK) {
+      const ChildRec rc = load_rec_cg(E.rec + D->slot_off + c);
+      if (rec_feasible(rc, eq_tol)) best = rc.pmax;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
+      best = other < best ? other : best;
+    }
+    if ((threadIdx.x & 31) == 0 && best != ~0ull) atomicMin(&S->pup_key, best);
   }
 }
 
@@ -727,42 +1368,49 @@ __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
 }
 
 __device__ void plan_next(const Engine& E, unsigned* sscan) {
-  unsigned run2 = 0, run3 = 0, run4 = 0;
+  unsigned run2 = 0, run3 = 0, run4 = 0, runr = 0;
   for (int base = 0; base < E.np; base += PCBA_TPB) {
     const int p = base + threadIdx.x;
-    unsigned a2 = 0, a3 = 0, a4 = 0;
+    unsigned a2 = 0, a3 = 0, a4 = 0, ar = 0;
     if (p < E.np) {
       const ProbState* S = E.state + p;
       const ProbDesc* D = E.desc + p;
       const int st = *(volatile const int*)&S->status;
       const int K = *(volatile const int*)&S->K;
       const int F = *(volatile const int*)&S->F;
+      const int steps = *(volatile const int*)&S->steps;
       if (st == PCBA_RUNNING) {
         a2 = (unsigned)K * (unsigned)D->tiles;
         a3 = (unsigned)((2 * K + PCBA_TPB - 1) / PCBA_TPB);
+        (void)steps;
       }
       a4 = (unsigned)F * (unsigned)D->move_chunks;
     }
-    unsigned t2, t3, t4;
+    unsigned t2, t3, t4, tr;
     const unsigned e2 = block_exclusive_scan(a2, sscan, &t2);
     const unsigned e3 = block_exclusive_scan(a3, sscan, &t3);
     const unsigned e4 = block_exclusive_scan(a4, sscan, &t4);
+    const unsigned er = block_exclusive_scan(ar, sscan, &tr);
     if (p < E.np) {
       E.k2_pre[p] = run2 + e2;
       E.k3_pre_next[p] = run3 + e3;
       E.k4_pre[p] = run4 + e4;
+      E.kr_pre[p] = runr + er;
     }
     run2 += t2;
     run3 += t3;
     run4 += t4;
+    runr += tr;
   }
   if (threadIdx.x == 0) {
     E.k2_pre[E.np] = run2;
     E.k3_pre_next[E.np] = run3;
     E.k4_pre[E.np] = run4;
+    E.kr_pre[E.np] = runr;
     E.plan->k2_units = run2;
     E.plan->k3_tiles_next = run3;
     E.plan->k4_units = run4;
+    E.plan->kr_units = runr;
     E.plan->any_running = run2 > 0 ? 1 : 0;
     E.plan->k3_done = 0u;
     __threadfence();
@@ -885,6 +1533,10 @@ __global__ void k_control(Engine E, cudaGraphConditionalHandle handle, int use_g
   for (int q = threadIdx.x; q <= E.np; q += blockDim.x) E.k3_pre[q] = E.k3_pre_next[q];
   if (threadIdx.x == 0) {
     pl->k3_tiles = pl->k3_tiles_next;
+    // the refresh of this iteration consumed the list of the previous step,
+    // which the next step's subdivision fills again
+    pl->marks_total += min(pl->mark_count[(pl->steps_global + 1) & 1], E.mark_cap);
+    pl->mark_count[(pl->steps_global + 1) & 1] = 0u;
     pl->steps_global += 1;
     const int running = pl->any_running;
     const SolveParams* P = E.params;
@@ -955,6 +1607,7 @@ __global__ void k_init(Engine E) {
       E.k2_pre[p] = run2 + e2;
       E.k3_pre[p] = run3 + e3;
       E.k4_pre[p] = 0;
+      E.kr_pre[p] = 0;
     }
     run2 += t2;
     run3 += t3;
@@ -968,6 +1621,12 @@ __global__ void k_init(Engine E) {
     pl->k3_tiles = run3;
     pl->k3_tiles_next = 0;
     pl->k4_units = 0;
+    pl->kr_units = 0;
+    pl->mark_count[0] = 0u;
+    pl->mark_count[1] = 0u;
+    pl->marks_total = 0ull;
+    pl->refreshed_total = 0ull;
+    E.kr_pre[E.np] = 0;
     pl->k3_done = 0;
     pl->any_running = run2 > 0;
     pl->steps_global = 0;

@@ -76,6 +76,9 @@ def lib():
         "pcba_batch_timing": ([P, P, P, P, P], I),
         "pcba_batch_stats": ([P, P, P, P, P], I),
         "pcba_batch_launch_bytes": ([P, P, I], I),
+        "pcba_batch_autotune": ([P, D, D, I, P, I, P], I),
+        "pcba_batch_config": ([P, P, P, P, P], I),
+        "pcba_batch_refresh_stats": ([P, P, P], I),
         "pcba_batch_set_stream": ([P, P], I),
         "pcba_batch_destroy": ([P], None),
         "pcba_get_list": ([P, P, P, P, P, P, P, P], I),
@@ -102,7 +105,8 @@ def exported_symbols():
     return ["pcba_create", "pcba_create_bernstein", "pcba_solve", "pcba_solve_steps",
             "pcba_solve_batch", "pcba_batch_create", "pcba_batch_solve",
             "pcba_batch_solve_from_host", "pcba_batch_input_doubles", "pcba_batch_trace",
-            "pcba_batch_timing", "pcba_batch_stats", "pcba_batch_launch_bytes", "pcba_batch_set_stream", "pcba_batch_destroy",
+            "pcba_batch_timing", "pcba_batch_stats", "pcba_batch_launch_bytes",
+            "pcba_batch_autotune", "pcba_batch_config", "pcba_batch_refresh_stats", "pcba_batch_set_stream", "pcba_batch_destroy",
             "pcba_get_list", "pcba_root_patches", "pcba_item_bytes", "pcba_set_stream",
             "pcba_set_warm_start", "pcba_destroy", "pcba_status_string", "pcba_last_error",
             "pcba_version", "pcba_bernstein_convert_noalloc"]
@@ -255,7 +259,7 @@ def solver_from_problem(prob, precision=FP32):
 class Batch:
     """A reusable batch of problems solved together (pcba_batch_*)."""
 
-    GRAPH, HOST_LOOP, INSTRUMENT = 0, 1, 3
+    GRAPH, HOST_LOOP, INSTRUMENT, NO_TMA = 0, 1, 3, 4
 
     def __init__(self, solvers, mem_cap_total, flags=0):
         self.solvers = list(solvers)
@@ -327,10 +331,30 @@ class Batch:
         return {"loop_iters": it.value, "kernel_launches": kl.value, "h2d_bytes": hd.value,
                 "d2h_bytes": dh.value}
 
+    def autotune(self, opt_tol=1e-3, eq_tol=1e-4, max_iters=28):
+        """Times every subdivision configuration on this batch, keeps the fastest."""
+        ms = np.full(16, np.nan)
+        chosen = ctypes.c_int()
+        n = _check(lib().pcba_batch_autotune(self._b, opt_tol, eq_tol, max_iters, _p(ms), 16,
+                                             ctypes.byref(chosen)))
+        return {"chosen": chosen.value, "ms_per_config": ms[:n].tolist(), "config": self.config()}
+
+    def config(self):
+        t, w, s, g = (ctypes.c_int() for _ in range(4))
+        idx = _check(lib().pcba_batch_config(self._b, ctypes.byref(t), ctypes.byref(w),
+                                             ctypes.byref(s), ctypes.byref(g)))
+        return {"index": idx, "tma": bool(t.value), "warps_per_block": w.value,
+                "stages": s.value, "grid": g.value}
+
     def launch_bytes(self, max_launches=4096):
         out = np.empty(max_launches)
         n = _check(lib().pcba_batch_launch_bytes(self._b, _p(out), max_launches))
         return out[:n].copy()
+
+    def refresh_stats(self):
+        m, r = ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib().pcba_batch_refresh_stats(self._b, ctypes.byref(m), ctypes.byref(r)))
+        return {"marked": m.value, "refreshed": r.value}
 
     def set_stream(self, stream_ptr: int):
         _check(lib().pcba_batch_set_stream(self._b, ctypes.c_void_p(stream_ptr)))

@@ -356,3 +356,52 @@ def test_full_size_batch_sampled_against_oracle():
         o = oracle_solve(probs[k], opt_tol=1e-3)
         assert_interval_parity(res[k], o, 1e-3)
     assert [r["status"] for r in res] == [pcba.OPTIMAL] * 64
+
+
+@pytest.mark.parametrize("precision", [pcba.FP64, pcba.FP32])
+def test_tma_and_direct_subdivision_agree(precision):
+    """The TMA-staged subdivision kernel and the direct-load one perform the
+    same arithmetic, so every result must be identical."""
+    probs = [W.rtd(2000 + k, n_obstacles=n) for k, n in enumerate((512, 37, 300, 100))]
+    probs.append(W.dim4(3002, n_ineq=40, n_eq=1))
+    kw = dict(opt_tol=1e-3, eq_tol=1e-2, max_iters=10)
+    a = pcba.Batch([gpu_solver(p, precision) for p in probs], 8 << 30).solve(**kw)
+    b = pcba.Batch([gpu_solver(p, precision) for p in probs], 8 << 30,
+                   flags=pcba.Batch.NO_TMA).solve(**kw)
+    for x, y in zip(a, b):
+        for key in ("status", "lower", "upper", "steps", "peak_items"):
+            assert x[key] == y[key], key
+
+
+def test_fp64_lists_bit_exact_without_tma(monkeypatch):
+    monkeypatch.setenv("PCBA_NO_TMA", "1")
+    test_fp64_lists_bit_exact(12, 2, 6, 37, 0)
+
+
+def test_autotune_keeps_results_and_picks_a_config():
+    probs = [W.rtd(2000 + k, n_obstacles=n) for k, n in enumerate((512, 64, 700, 200, 33, 1000))]
+    base = pcba.Batch([gpu_solver(p, pcba.FP32) for p in probs], 8 << 30).solve()
+    b = pcba.Batch([gpu_solver(p, pcba.FP32) for p in probs], 8 << 30)
+    tune = b.autotune()
+    assert len(tune["ms_per_config"]) >= 2 and 0 <= tune["chosen"] < len(tune["ms_per_config"])
+    assert b.config()["index"] == tune["chosen"]
+    for x, y in zip(base, b.solve()):
+        for key in ("status", "lower", "upper", "steps"):
+            assert x[key] == y[key]
+
+
+def test_uneven_batch_sampled_against_oracle():
+    """Obstacle counts log-uniform in [16, 4096]: a 48-problem slice of the
+    256-problem batch workload, every sixth problem checked by the oracle."""
+    counts = W.batch_obstacle_counts(256, 4000)
+    ks = list(range(0, 256, 16)) + [5, 77, 130, 201] + list(range(3, 256, 9))[:28]
+    probs = [W.rtd(4000 + k, n_obstacles=int(counts[k])) for k in ks]
+    b = pcba.Batch([gpu_solver(p, pcba.FP32) for p in probs], 48 << 30)
+    b.autotune()
+    res = b.solve()
+    for j in range(0, len(ks), 6):
+        o = oracle_solve(probs[j], opt_tol=1e-3)
+        assert_interval_parity(res[j], o, 1e-3)
+    bad = [(ks[j], int(counts[ks[j]]), r["status"], r["steps"], r["peak_items"], r["lower"], r["upper"])
+           for j, r in enumerate(res) if r["status"] not in (pcba.OPTIMAL, pcba.INFEASIBLE)]
+    assert not bad, bad
