@@ -1,0 +1,110 @@
+"""FP64 reference of the learned warm start's set-encoder network.
+
+TEST INFRASTRUCTURE: only tests/ use this module; it shares no code with the
+CUDA kernels of paper_2003_01758_b300 (the network is not part of the paper;
+its definition here is the plain one, written out layer by layer).
+
+Network (per problem: a set of points x_p in R^dp and a global vector u in R^dg):
+    h1_p = relu(x_p W1 + b1)          dp  -> H
+    h2_p = relu(h1_p W2 + b2)         H   -> H
+    h3_p = relu(h2_p W3 + b3)         H   -> H
+    z    = max_p h3_p                 (elementwise max over the set)
+    h4   = relu([z, u] W4 + b4)       H+dg -> H
+    h5   = relu(h4 W5 + b5)           H   -> H
+    y    = tanh(h5 W6 + b6)           H   -> 2
+Loss over a batch of B problems with targets t: L = (1/B) sum_b ||y_b - t_b||^2.
+
+Parameters are kept in one flat vector in the order
+W1, b1, W2, b2, W3, b3, W4, b4, W5, b5, W6, b6 (weights row-major [in][out]).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def layer_shapes(dp=2, dg=34, H=128, dout=2):
+    return [(dp, H), (H,), (H, H), (H,), (H, H), (H,), (H + dg, H), (H,), (H, H), (H,),
+            (H, dout), (dout,)]
+
+
+def unflatten(theta, dp=2, dg=34, H=128, dout=2):
+    out, o = [], 0
+    for shp in layer_shapes(dp, dg, H, dout):
+        n = int(np.prod(shp))
+        out.append(np.asarray(theta[o:o + n], dtype=np.float64).reshape(shp))
+        o += n
+    return out
+
+
+def n_params(dp=2, dg=34, H=128, dout=2):
+    return int(sum(np.prod(s) for s in layer_shapes(dp, dg, H, dout)))
+
+
+def relu(v):
+    return np.maximum(v, 0.0)
+
+
+def forward(theta, points, offsets, glob, dims=(2, 34, 128, 2)):
+    """points [P, dp], offsets [B+1] (set b = points[offsets[b]:offsets[b+1]]),
+    glob [B, dg]; returns y [B, 2] and the cache for backward."""
+    W1, b1, W2, b2, W3, b3, W4, b4, W5, b5, W6, b6 = unflatten(theta, *dims)
+    h1 = relu(points @ W1 + b1)
+    h2 = relu(h1 @ W2 + b2)
+    h3 = relu(h2 @ W3 + b3)
+    B = len(offsets) - 1
+    z = np.empty((B, h3.shape[1]))
+    arg = np.empty((B, h3.shape[1]), dtype=np.int64)
+    for b in range(B):
+        seg = h3[offsets[b]:offsets[b + 1]]
+        k = np.argmax(seg, axis=0)
+        arg[b] = offsets[b] + k
+        z[b] = seg[k, np.arange(seg.shape[1])]
+    u = np.concatenate([z, glob], axis=1)
+    h4 = relu(u @ W4 + b4)
+    h5 = relu(h4 @ W5 + b5)
+    y = np.tanh(h5 @ W6 + b6)
+    return y, (points, h1, h2, h3, arg, u, h4, h5, y)
+
+
+def loss(y, target):
+    return float(np.sum((y - target) ** 2) / y.shape[0])
+
+
+def backward(theta, cache, target, dims=(2, 34, 128, 2)):
+    """Gradient of the loss with respect to the flat parameter vector."""
+    W1, b1, W2, b2, W3, b3, W4, b4, W5, b5, W6, b6 = unflatten(theta, *dims)
+    points, h1, h2, h3, arg, u, h4, h5, y = cache
+    B = y.shape[0]
+    H = h1.shape[1]
+    dy = 2.0 * (y - target) / B
+    d6 = dy * (1.0 - y * y)
+    gW6, gb6 = h5.T @ d6, d6.sum(0)
+    d5 = (d6 @ W6.T) * (h5 > 0)
+    gW5, gb5 = h4.T @ d5, d5.sum(0)
+    d4 = (d5 @ W5.T) * (h4 > 0)
+    gW4, gb4 = u.T @ d4, d4.sum(0)
+    du = d4 @ W4.T
+    dz = du[:, :H]
+    dh3 = np.zeros_like(h3)
+    for b in range(B):
+        dh3[arg[b], np.arange(H)] += dz[b]
+    d3 = dh3 * (h3 > 0)
+    gW3, gb3 = h2.T @ d3, d3.sum(0)
+    d2 = (d3 @ W3.T) * (h2 > 0)
+    gW2, gb2 = h1.T @ d2, d2.sum(0)
+    d1 = (d2 @ W2.T) * (h1 > 0)
+    gW1, gb1 = points.T @ d1, d1.sum(0)
+    return np.concatenate([g.ravel() for g in (gW1, gb1, gW2, gb2, gW3, gb3, gW4, gb4, gW5, gb5,
+                                               gW6, gb6)])
+
+
+def init_params(seed, dims=(2, 34, 128, 2)):
+    """He-style initialisation with a seeded generator (the layout above)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for shp in layer_shapes(*dims):
+        if len(shp) == 2:
+            out.append(rng.normal(0.0, np.sqrt(2.0 / shp[0]), size=shp).ravel())
+        else:
+            out.append(np.zeros(shp))
+    return np.concatenate(out)

@@ -1,0 +1,56 @@
+"""Pins for the FP64 reference of the warm-start network (oracle/mlp.py):
+central finite differences of the loss against the analytic gradient, set
+permutation invariance of the max-pool, and closed-form outputs."""
+import numpy as np
+import pytest
+
+from oracle import mlp
+
+DIMS = (2, 3, 8, 2)  # small network for the finite-difference pin
+
+
+def batch(seed, B=3):
+    rng = np.random.default_rng(seed)
+    sizes = rng.integers(2, 7, size=B)
+    offsets = np.concatenate([[0], np.cumsum(sizes)])
+    points = rng.normal(size=(offsets[-1], DIMS[0]))
+    glob = rng.normal(size=(B, DIMS[1]))
+    target = rng.uniform(-0.9, 0.9, size=(B, 2))
+    return points, offsets, glob, target
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_gradient_matches_central_differences(seed):
+    theta = mlp.init_params(seed, DIMS) + np.random.default_rng(seed + 10).normal(
+        0, 0.05, mlp.n_params(*DIMS))
+    points, offsets, glob, target = batch(seed)
+    y, cache = mlp.forward(theta, points, offsets, glob, DIMS)
+    g = mlp.backward(theta, cache, target, DIMS)
+    h = 1e-6
+    rng = np.random.default_rng(seed)
+    for i in rng.choice(len(theta), size=60, replace=False):
+        tp, tm = theta.copy(), theta.copy()
+        tp[i] += h
+        tm[i] -= h
+        fp = mlp.loss(mlp.forward(tp, points, offsets, glob, DIMS)[0], target)
+        fm = mlp.loss(mlp.forward(tm, points, offsets, glob, DIMS)[0], target)
+        fd = (fp - fm) / (2 * h)
+        assert abs(fd - g[i]) <= 1e-6 * max(1.0, abs(fd)), (i, fd, g[i])
+
+
+def test_set_order_does_not_matter():
+    theta = mlp.init_params(5, DIMS)
+    points, offsets, glob, _ = batch(5, B=2)
+    y, _ = mlp.forward(theta, points, offsets, glob, DIMS)
+    perm = points.copy()
+    perm[offsets[0]:offsets[1]] = perm[offsets[0]:offsets[1]][::-1]
+    y2, _ = mlp.forward(theta, perm, offsets, glob, DIMS)
+    assert np.array_equal(y, y2)
+
+
+def test_bias_only_network_outputs_tanh_of_bias():
+    theta = np.zeros(mlp.n_params(*DIMS))
+    theta[-2:] = [0.3, -1.2]
+    points, offsets, glob, _ = batch(7)
+    y, _ = mlp.forward(theta, points, offsets, glob, DIMS)
+    assert np.allclose(y, np.tanh([0.3, -1.2]))
