@@ -108,3 +108,14 @@ def init_params(seed, dims=(2, 34, 128, 2)):
         else:
             out.append(np.zeros(shp))
     return np.concatenate(out)
+
+
+def adam_step(theta, grad, m, v, t, lr, beta1=0.9, beta2=0.999, eps=1e-8):
+    """One step of Adam (Kingma & Ba, 2015, Algorithm 1) at step count t >= 1:
+    moments updated, bias-corrected, parameters moved.  Returns the new
+    (theta, m, v)."""
+    m = beta1 * m + (1.0 - beta1) * grad
+    v = beta2 * v + (1.0 - beta2) * grad * grad
+    m_hat = m / (1.0 - beta1 ** t)
+    v_hat = v / (1.0 - beta2 ** t)
+    return theta - lr * m_hat / (np.sqrt(v_hat) + eps), m, v

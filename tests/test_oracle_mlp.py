@@ -54,3 +54,20 @@ def test_bias_only_network_outputs_tanh_of_bias():
     points, offsets, glob, _ = batch(7)
     y, _ = mlp.forward(theta, points, offsets, glob, DIMS)
     assert np.allclose(y, np.tanh([0.3, -1.2]))
+
+
+def test_adam_first_step_is_signed_learning_rate():
+    """From zero moments the bias-corrected first Adam step is lr * g / (|g| + eps),
+    i.e. lr * sign(g) wherever |g| >> eps; a second step with the same gradient
+    is again lr * sign(g)."""
+    rng = np.random.default_rng(7)
+    th = rng.normal(size=50)
+    g = rng.normal(size=50)
+    g[0] = 0.0
+    z = np.zeros(50)
+    t1, m, v = mlp.adam_step(th, g, z, z, 1, 0.01)
+    tol = 0.01 * 2e-8 / np.abs(g[1:]) + 1e-14   # the eps term, relative to |g|
+    assert np.all(np.abs(t1[1:] - (th[1:] - 0.01 * np.sign(g[1:]))) <= tol)
+    assert t1[0] == th[0]
+    t2, _, _ = mlp.adam_step(t1, g, m, v, 2, 0.01)
+    assert np.all(np.abs(t2[1:] - (t1[1:] - 0.01 * np.sign(g[1:]))) <= tol)
