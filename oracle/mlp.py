@@ -16,6 +16,13 @@ Loss over a batch of B problems with targets t: L = (1/B) sum_b ||y_b - t_b||^2.
 
 Parameters are kept in one flat vector in the order
 W1, b1, W2, b2, W3, b3, W4, b4, W5, b5, W6, b6 (weights row-major [in][out]).
+
+Operand rounding: with rnd=bf16_round, both operands of every matrix product
+of the forward pass, and of the weight-gradient and input-gradient products of
+layers 1-5 in the backward pass, are rounded to bfloat16 before an exact (FP64)
+product; sums, biases, activations and the output layer's backward stay FP64.
+This is the definition of the network's BF16 precision; rnd=None is the plain
+FP64 network.
 """
 from __future__ import annotations
 
@@ -44,13 +51,25 @@ def relu(v):
     return np.maximum(v, 0.0)
 
 
-def forward(theta, points, offsets, glob, dims=(2, 34, 128, 2)):
+def bf16_round(a):
+    """Round to the nearest bfloat16 value (8-bit significand, ties to even),
+    returned as float64.  Finite normal-range inputs only."""
+    m, e = np.frexp(np.asarray(a, dtype=np.float64))    # a = m 2^e, 0.5 <= |m| < 1
+    return np.ldexp(np.rint(m * 256.0), e - 8)
+
+
+def _ident(a):
+    return a
+
+
+def forward(theta, points, offsets, glob, dims=(2, 34, 128, 2), rnd=None):
     """points [P, dp], offsets [B+1] (set b = points[offsets[b]:offsets[b+1]]),
     glob [B, dg]; returns y [B, 2] and the cache for backward."""
+    r = rnd or _ident
     W1, b1, W2, b2, W3, b3, W4, b4, W5, b5, W6, b6 = unflatten(theta, *dims)
-    h1 = relu(points @ W1 + b1)
-    h2 = relu(h1 @ W2 + b2)
-    h3 = relu(h2 @ W3 + b3)
+    h1 = relu(r(points) @ r(W1) + b1)
+    h2 = relu(r(h1) @ r(W2) + b2)
+    h3 = relu(r(h2) @ r(W3) + b3)
     B = len(offsets) - 1
     z = np.empty((B, h3.shape[1]))
     arg = np.empty((B, h3.shape[1]), dtype=np.int64)
@@ -60,9 +79,9 @@ def forward(theta, points, offsets, glob, dims=(2, 34, 128, 2)):
         arg[b] = offsets[b] + k
         z[b] = seg[k, np.arange(seg.shape[1])]
     u = np.concatenate([z, glob], axis=1)
-    h4 = relu(u @ W4 + b4)
-    h5 = relu(h4 @ W5 + b5)
-    y = np.tanh(h5 @ W6 + b6)
+    h4 = relu(r(u) @ r(W4) + b4)
+    h5 = relu(r(h4) @ r(W5) + b5)
+    y = np.tanh(r(h5) @ r(W6) + b6)
     return y, (points, h1, h2, h3, arg, u, h4, h5, y)
 
 
@@ -70,8 +89,9 @@ def loss(y, target):
     return float(np.sum((y - target) ** 2) / y.shape[0])
 
 
-def backward(theta, cache, target, dims=(2, 34, 128, 2)):
+def backward(theta, cache, target, dims=(2, 34, 128, 2), rnd=None):
     """Gradient of the loss with respect to the flat parameter vector."""
+    r = rnd or _ident
     W1, b1, W2, b2, W3, b3, W4, b4, W5, b5, W6, b6 = unflatten(theta, *dims)
     points, h1, h2, h3, arg, u, h4, h5, y = cache
     B = y.shape[0]
@@ -80,20 +100,20 @@ def backward(theta, cache, target, dims=(2, 34, 128, 2)):
     d6 = dy * (1.0 - y * y)
     gW6, gb6 = h5.T @ d6, d6.sum(0)
     d5 = (d6 @ W6.T) * (h5 > 0)
-    gW5, gb5 = h4.T @ d5, d5.sum(0)
-    d4 = (d5 @ W5.T) * (h4 > 0)
-    gW4, gb4 = u.T @ d4, d4.sum(0)
-    du = d4 @ W4.T
+    gW5, gb5 = r(h4).T @ r(d5), d5.sum(0)
+    d4 = (r(d5) @ r(W5).T) * (h4 > 0)
+    gW4, gb4 = r(u).T @ r(d4), d4.sum(0)
+    du = r(d4) @ r(W4).T
     dz = du[:, :H]
     dh3 = np.zeros_like(h3)
     for b in range(B):
         dh3[arg[b], np.arange(H)] += dz[b]
     d3 = dh3 * (h3 > 0)
-    gW3, gb3 = h2.T @ d3, d3.sum(0)
-    d2 = (d3 @ W3.T) * (h2 > 0)
-    gW2, gb2 = h1.T @ d2, d2.sum(0)
-    d1 = (d2 @ W2.T) * (h1 > 0)
-    gW1, gb1 = points.T @ d1, d1.sum(0)
+    gW3, gb3 = r(h2).T @ r(d3), d3.sum(0)
+    d2 = (r(d3) @ r(W3).T) * (h2 > 0)
+    gW2, gb2 = r(h1).T @ r(d2), d2.sum(0)
+    d1 = (r(d2) @ r(W2).T) * (h1 > 0)
+    gW1, gb1 = r(points).T @ r(d1), d1.sum(0)
     return np.concatenate([g.ravel() for g in (gW1, gb1, gW2, gb2, gW3, gb3, gW4, gb4, gW5, gb5,
                                                gW6, gb6)])
 

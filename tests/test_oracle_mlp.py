@@ -71,3 +71,35 @@ def test_adam_first_step_is_signed_learning_rate():
     assert t1[0] == th[0]
     t2, _, _ = mlp.adam_step(t1, g, m, v, 2, 0.01)
     assert np.all(np.abs(t2[1:] - (t1[1:] - 0.01 * np.sign(g[1:]))) <= tol)
+
+
+def test_bf16_round_special_values_and_torch():
+    """Ties go to the even significand; the result equals torch's own
+    float64 -> bfloat16 conversion on random normal-range values."""
+    import torch
+    u = 2.0 ** -7                       # one bf16 ulp at 1
+    assert mlp.bf16_round(1.0 + u / 2) == 1.0            # tie -> even (1.0)
+    assert mlp.bf16_round(1.0 + 3 * u / 2) == 1.0 + 2 * u  # tie -> even (1 + 2u)
+    assert mlp.bf16_round(1.0 + 0.6 * u) == 1.0 + u
+    assert mlp.bf16_round(-3.0) == -3.0 and mlp.bf16_round(0.0) == 0.0
+    x = np.random.default_rng(0).normal(size=10000) * 10.0 ** np.random.default_rng(1).integers(
+        -20, 20, size=10000)
+    ref = torch.tensor(x, dtype=torch.float64).to(torch.bfloat16).to(torch.float64).numpy()
+    assert np.array_equal(mlp.bf16_round(x), ref)
+
+
+def test_bf16_network_stays_near_the_plain_network():
+    """Operand rounding is piecewise constant in the weights, so finite
+    differences do not apply to it; with weights and inputs on the bf16 grid,
+    rounding only the hidden activations moves the outputs by a few bf16 ulps
+    and the gradient by a few percent."""
+    theta = mlp.bf16_round(mlp.init_params(4, DIMS))
+    points, offsets, glob, target = batch(4)
+    points = mlp.bf16_round(points)
+    y0, _ = mlp.forward(theta, points, offsets, glob, DIMS)
+    y1, _ = mlp.forward(theta, points, offsets, glob, DIMS, rnd=mlp.bf16_round)
+    assert np.max(np.abs(y1 - y0)) <= 6 * 2.0 ** -8 * (1.0 + np.max(np.abs(y0)))
+    g0 = mlp.backward(theta, mlp.forward(theta, points, offsets, glob, DIMS)[1], target, DIMS)
+    g1 = mlp.backward(theta, mlp.forward(theta, points, offsets, glob, DIMS, mlp.bf16_round)[1],
+                      target, DIMS, mlp.bf16_round)
+    assert np.linalg.norm(g1 - g0) <= 0.1 * np.linalg.norm(g0)
