@@ -145,9 +145,11 @@ int pcba_solve_steps(pcba_handle* h, double opt_tol, double eq_tol, int max_iter
  * mem_cap_total bytes are shared so that every problem gets the same item
  * capacity M = floor(mem_cap_total / sum of bytes per item).
  * warm_start is NULL or n * PCBA_MAX_DIM doubles (row k = point of problem k,
- * first nvars used; a NaN first entry means none); each point is evaluated in
- * FP64 and, only if it is certified feasible, lowers that problem's p_up to
- * its certified cost (this never removes a feasible minimiser, Thm. 3).
+ * first nvars used; a NaN first entry means none); each point is rounded to
+ * FP32 coordinates, its constraints are evaluated in FP32 with a rigorous
+ * rounding-error bound and its cost in FP64 with one, and only if it is
+ * certified feasible does it lower that problem's p_up to its certified cost
+ * bound (this never removes a feasible minimiser, Thm. 3).
  * out receives n results. */
 int pcba_solve_batch(pcba_handle** hs, int n, double opt_tol, double eq_tol, int max_iters,
                      size_t mem_cap_total, const double* warm_start, pcba_result* out);

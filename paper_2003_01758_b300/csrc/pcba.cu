@@ -23,6 +23,7 @@
 
 #include "pcba.h"
 #include "pcba_kernels.cuh"
+#include "pcba_warmstart.h"
 
 static_assert(PCBA_MAX_DIM == PCBA_MAXD, "dimension limits differ");
 
@@ -121,6 +122,7 @@ struct pcba_batch {
   unsigned* d_slots = nullptr;  // flagrank | hole | filler
   unsigned* d_tilecnt = nullptr;
   double* d_mono = nullptr;
+  float* d_mono32 = nullptr;
   double* d_trace = nullptr;
   double* d_warm = nullptr;
   double* d_mat = nullptr;
@@ -128,6 +130,9 @@ struct pcba_batch {
   uint4* d_marks = nullptr;
   double* d_raw = nullptr;
   EvalOut* d_eval = nullptr;
+  double* d_cand = nullptr;     // guided solves: [np][cand_cap][PCBA_MAXD]
+  double* d_stencil = nullptr;  // guided solves: [stencil_cap] doubles
+  long long cand_cap = 0, stencil_cap = 0;
   long long trace_rows_total = 0;
   // host mirrors (pinned)
   ProbState* h_state = nullptr;
@@ -277,7 +282,8 @@ void free_batch(pcba_batch* b) {
   if (b->ev1) cudaEventDestroy(b->ev1);
   void* dev[] = {b->d_desc, b->d_state, b->d_plan, b->d_params, b->d_pre, b->d_arena, b->d_rec,
                  b->d_slots, b->d_tilecnt, b->d_mono, b->d_trace, b->d_warm, b->d_mat,
-                 b->d_raw, b->d_eval, b->d_tmaps, b->d_marks};
+                 b->d_raw, b->d_eval, b->d_tmaps, b->d_marks, b->d_cand, b->d_stencil,
+                 b->d_mono32};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {b->h_state, b->h_eval, b->h_plan, b->h_params, b->h_running};
@@ -651,6 +657,7 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   PCBA_ALLOC(b->d_slots, sizeof(unsigned) * 3 * nslots);
   PCBA_ALLOC(b->d_tilecnt, sizeof(unsigned) * tiles_per * n);
   PCBA_ALLOC(b->d_mono, sizeof(double) * mono);
+  PCBA_ALLOC(b->d_mono32, sizeof(float) * mono);
   PCBA_ALLOC(b->d_trace, sizeof(double) * 4 * trace_rows);
   PCBA_ALLOC(b->d_warm, sizeof(double) * PCBA_MAXD * n);
   PCBA_ALLOC(b->d_mat, sizeof(double) * 3 * PCBA_MAXD * 578 * n);
@@ -726,8 +733,10 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   E.filler = b->d_slots + 2 * nslots;
   E.tilecnt = b->d_tilecnt;
   E.mono = b->d_mono;
+  E.mono32 = b->d_mono32;
   E.trace = b->d_trace;
   E.warm = b->d_warm;
+  E.n_warm = 1;
   E.root_raw = nullptr;
   rc = prec == PCBA_FP32 ? setup_kernels<float>(b) : setup_kernels<double>(b);
   if (!rc) rc = apply_k2_config(b, (b->want_tma && b->g.cfgs.size() > 1) ? 1 : 0);
@@ -741,9 +750,18 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   return 0;
 }
 
+// Guesses of a guided solve (pcba_batch_solve_guided).
+struct Guide {
+  const float* guess;
+  int dim;
+  const double* stencil;  // host
+  int n;
+};
+
 template <typename T>
 int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double eq_tol,
-              int max_iters, int max_steps, const double* warm, bool want_raw) {
+              int max_iters, int max_steps, const double* warm, bool want_raw,
+              const Guide* guide) {
   cudaStream_t s = b->stream;
   const int n = b->np;
   SolveParams& P = *b->h_params;
@@ -755,7 +773,8 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   P.np = n;
   PCBA_CK(cudaEventRecord(b->ev0, s));
   b->h2d_bytes = (long long)sizeof(SolveParams) + (host_coeffs ? 8LL * b->mono_doubles : 0) +
-                 (warm ? 8LL * PCBA_MAXD * n : 0);
+                 (warm ? 8LL * PCBA_MAXD * n : 0) +
+                 (guide ? 8LL * guide->n * guide->dim : 0);
   b->d2h_bytes = (long long)(sizeof(ProbState) + sizeof(EvalOut)) * n + (long long)sizeof(Plan);
   if (host_coeffs)
     PCBA_CK(cudaMemcpyAsync(b->d_mono, host_coeffs, sizeof(double) * b->mono_doubles,
@@ -768,6 +787,19 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
     PCBA_CK(cudaMemsetAsync(b->d_warm, 0xFF, sizeof(double) * PCBA_MAXD * n, s));  // NaN
   Engine E1 = b->E;
   E1.root_raw = want_raw ? b->d_raw : nullptr;
+  if (guide || warm) {
+    const unsigned cg = (unsigned)std::min<long long>((b->mono_doubles + 255) / 256, 4LL * b->g.sms);
+    k_mono32<<<cg, 256, 0, s>>>(b->d_mono, b->d_mono32, b->mono_doubles);
+  }
+  if (guide) {
+    PCBA_CK(cudaMemcpyAsync(b->d_stencil, guide->stencil, sizeof(double) * guide->n * guide->dim,
+                            cudaMemcpyHostToDevice, s));
+    const long long nc = (long long)n * guide->n;
+    k_candidates<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(E1, guide->guess, guide->dim,
+                                                             b->d_stencil, guide->n, b->d_cand);
+    E1.warm = b->d_cand;
+    E1.n_warm = guide->n;
+  }
   const int nmat = n * 3 * PCBA_MAXD * 17;
   k1_matrices<<<(nmat + 255) / 256, 256, 0, s>>>(E1, b->d_mat);
   k1_convert<T><<<b->g.k1_grid, 32 * b->g.k1_wpb, b->g.k1_smem, s>>>(E1, b->d_mat, b->g.k1_cmax,
@@ -897,14 +929,16 @@ void fill_results(const pcba_batch* b, pcba_result* out) {
 
 int batch_solve_impl(pcba_batch* b, const double* host_coeffs, double opt_tol, double eq_tol,
                      int max_iters, int max_steps, const double* warm, pcba_result* out,
-                     bool want_raw = false) {
+                     bool want_raw = false, const Guide* guide = nullptr) {
   if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
   if (!(opt_tol > 0) || !(eq_tol > 0)) return fail(PCBA_ERR_INVALID, "tolerances must be > 0");
   if (max_iters < 1 || max_iters > 64) return fail(PCBA_ERR_INVALID, "max_iters must be in [1, 64]");
   if (max_steps < 0) return fail(PCBA_ERR_INVALID, "max_steps must be >= 0");
   const int rc = b->precision == PCBA_FP32
-                     ? run_solve<float>(b, host_coeffs, opt_tol, eq_tol, max_iters, max_steps, warm, want_raw)
-                     : run_solve<double>(b, host_coeffs, opt_tol, eq_tol, max_iters, max_steps, warm, want_raw);
+                     ? run_solve<float>(b, host_coeffs, opt_tol, eq_tol, max_iters, max_steps, warm,
+                                        want_raw, guide)
+                     : run_solve<double>(b, host_coeffs, opt_tol, eq_tol, max_iters, max_steps, warm,
+                                         want_raw, guide);
   if (rc) return rc;
   if (out) fill_results(b, out);
   return 0;
@@ -1039,6 +1073,58 @@ int pcba_batch_solve_from_host(pcba_batch* b, const double* host_coeffs, double 
                                pcba_result* out) {
   if (!host_coeffs) return fail(PCBA_ERR_INVALID, "host_coeffs is null");
   return batch_solve_impl(b, host_coeffs, opt_tol, eq_tol, max_iters, 0, warm_start, out);
+}
+
+int pcba_batch_solve_guided(pcba_batch* b, double opt_tol, double eq_tol, int max_iters,
+                            const float* d_guess, int guess_dim, const double* stencil,
+                            int n_stencil, pcba_result* out) {
+  if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
+  if (!d_guess || !stencil) return fail(PCBA_ERR_INVALID, "guess or stencil is null");
+  if (guess_dim < 1 || guess_dim > PCBA_MAX_DIM)
+    return fail(PCBA_ERR_INVALID, "guess_dim must be in [1, 8]");
+  if (n_stencil < 1 || n_stencil > 1024)
+    return fail(PCBA_ERR_INVALID, "n_stencil must be in [1, 1024]");
+  for (long long i = 0; i < (long long)n_stencil * guess_dim; ++i)
+    if (!std::isfinite(stencil[i])) return fail(PCBA_ERR_INVALID, "stencil must be finite");
+  if (b->cand_cap < n_stencil) {
+    if (b->d_cand) cudaFree(b->d_cand);
+    b->d_cand = nullptr;
+    b->cand_cap = 0;
+    if (cudaMalloc((void**)&b->d_cand, sizeof(double) * PCBA_MAXD * (size_t)b->np * n_stencil) !=
+        cudaSuccess)
+      return fail(PCBA_ERR_OOM, "candidate buffer allocation failed");
+    b->cand_cap = n_stencil;
+  }
+  if (b->stencil_cap < (long long)n_stencil * guess_dim) {
+    if (b->d_stencil) cudaFree(b->d_stencil);
+    b->d_stencil = nullptr;
+    b->stencil_cap = 0;
+    if (cudaMalloc((void**)&b->d_stencil, sizeof(double) * (size_t)n_stencil * guess_dim) !=
+        cudaSuccess)
+      return fail(PCBA_ERR_OOM, "stencil buffer allocation failed");
+    b->stencil_cap = (long long)n_stencil * guess_dim;
+  }
+  const Guide g{d_guess, guess_dim, stencil, n_stencil};
+  return batch_solve_impl(b, nullptr, opt_tol, eq_tol, max_iters, 0, nullptr, out, false, &g);
+}
+
+int pcba_batch_warm_point(const pcba_batch* b, int k, double* x, double* cost) {
+  if (!b || k < 0 || k >= b->np) return fail(PCBA_ERR_INVALID, "bad batch or index");
+  const ProbState& S = b->h_state[k];
+  if (!S.seeded) return 0;
+  if (x)
+    for (int q = 0; q < b->desc[k].l; ++q) x[q] = S.seed_x[q];
+  if (cost) *cost = S.seed_cost;
+  return 1;
+}
+
+int pcba_batch_cost_grid(pcba_batch* b, int G, float* d_out, int ld, int col0) {
+  if (!b || !d_out) return fail(PCBA_ERR_INVALID, "batch or output is null");
+  if (G < 2 || G > 32) return fail(PCBA_ERR_INVALID, "G must be in [2, 32]");
+  if (col0 < 0 || ld < col0 + G * G) return fail(PCBA_ERR_INVALID, "need ld >= col0 + G * G");
+  k_cost_grid<<<b->np, PCBA_TPB, 0, b->stream>>>(b->E, G, d_out, ld, col0);
+  PCBA_CK(cudaGetLastError());
+  return 0;
 }
 
 long long pcba_batch_input_doubles(const pcba_batch* b) { return b ? b->mono_doubles : 0; }

@@ -86,7 +86,9 @@ struct ProbState {
   long long peak_items;
   unsigned long long t_end;
   int done_flag;
-  int pad;
+  int seeded;                   // a warm-start candidate was certified feasible
+  double seed_cost;             // its certified cost bound (the initial p_up)
+  double seed_x[PCBA_MAXD];     // the candidate
 };
 
 struct SolveParams {
@@ -134,8 +136,10 @@ struct Engine {
   unsigned* filler;        // per slot
   unsigned* tilecnt;       // per tile: kept count, then exclusive offset
   const double* mono;      // monomial inputs of every problem
+  const float* mono32;     // the same rounded to FP32 (filled when candidates are evaluated)
   double* trace;           // rows of (K, K_save, p_up, p_lo)
-  const double* warm;      // [np][PCBA_MAXD] or null
+  const double* warm;      // [np][n_warm][PCBA_MAXD] candidate points, or null
+  int n_warm;              // candidates per problem (a row starting with NaN is empty)
   double* root_raw;        // optional FP64 root patch dump
   const unsigned* k1_pre;  // [np + 1] patches per problem prefix
   const void* tmaps;       // [np][2] tensor maps (CUtensorMap) of the g / h blocks, or null

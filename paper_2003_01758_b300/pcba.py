@@ -32,6 +32,13 @@ class pcba_poly(ctypes.Structure):
                 ("coeff", ctypes.POINTER(ctypes.c_double))]
 
 
+# numpy image of an array of pcba_poly (x86-64 layout: int, padding, two pointers)
+_POLY_DTYPE = np.dtype([("nvars", np.int32), ("pad", np.int32), ("degree", np.uint64),
+                        ("coeff", np.uint64)])
+assert _POLY_DTYPE.itemsize == ctypes.sizeof(pcba_poly)
+assert pcba_poly.degree.offset == 8 and pcba_poly.coeff.offset == 16
+
+
 class pcba_box(ctypes.Structure):
     _fields_ = [("nvars", ctypes.c_int), ("lo", ctypes.POINTER(ctypes.c_double)),
                 ("hi", ctypes.POINTER(ctypes.c_double))]
@@ -91,6 +98,17 @@ def lib():
         "pcba_status_string": ([I], ctypes.c_char_p),
         "pcba_last_error": ([], ctypes.c_char_p),
         "pcba_version": ([], I),
+        "pcba_batch_solve_guided": ([P, D, D, I, P, I, P, I, P], I),
+        "pcba_batch_warm_point": ([P, I, P, P], I),
+        "pcba_batch_cost_grid": ([P, I, P, I, I], I),
+        "pcba_mlp_create": ([P, I, I, I, I, ctypes.c_ulonglong], I),
+        "pcba_mlp_destroy": ([P], None),
+        "pcba_mlp_num_params": ([P], LL),
+        "pcba_mlp_set_params": ([P, P, LL], I),
+        "pcba_mlp_get_params": ([P, P, LL], I),
+        "pcba_mlp_forward": ([P, P, P, I, I, P, P, P], I),
+        "pcba_mlp_gradient": ([P, P, P, I, I, P, P, P, P, P], I),
+        "pcba_mlp_train_step": ([P, P, P, I, I, P, P, ctypes.c_float, P, P], I),
     }
     for name, (args, res) in sigs.items():
         f = getattr(L, name)
@@ -109,7 +127,10 @@ def exported_symbols():
             "pcba_batch_autotune", "pcba_batch_config", "pcba_batch_refresh_stats", "pcba_batch_set_stream", "pcba_batch_destroy",
             "pcba_get_list", "pcba_root_patches", "pcba_item_bytes", "pcba_set_stream",
             "pcba_set_warm_start", "pcba_destroy", "pcba_status_string", "pcba_last_error",
-            "pcba_version", "pcba_bernstein_convert_noalloc"]
+            "pcba_version", "pcba_bernstein_convert_noalloc", "pcba_batch_solve_guided",
+            "pcba_batch_warm_point", "pcba_batch_cost_grid", "pcba_mlp_create", "pcba_mlp_destroy", "pcba_mlp_num_params", "pcba_mlp_set_params",
+            "pcba_mlp_get_params", "pcba_mlp_forward", "pcba_mlp_gradient",
+            "pcba_mlp_train_step"]
 
 
 def _check(rc):
@@ -157,9 +178,20 @@ class Solver:
             return pcba_poly(l, deg.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
                              a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
 
+        def family(a):
+            # one pcba_poly record per stacked constraint, built without a Python loop
+            deg = np.ascontiguousarray(np.array(a.shape[1:]) - 1, dtype=np.int32)
+            n = a.shape[0]
+            rec = np.zeros(max(1, n), dtype=_POLY_DTYPE)
+            rec["nvars"][:n] = l
+            rec["degree"][:n] = deg.ctypes.data
+            rec["coeff"][:n] = a.ctypes.data + a.strides[0] * np.arange(n, dtype=np.uint64)
+            keep.extend([deg, rec])
+            return rec.ctypes.data_as(ctypes.c_void_p)
+
         c = poly(cost)
-        gi = (pcba_poly * max(1, self.n_ineq))(*[poly(g) for g in ineq])
-        hj = (pcba_poly * max(1, self.n_eq))(*[poly(h) for h in eq])
+        gi = family(ineq)
+        hj = family(eq)
         box = pcba_box(l, lo.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                        hi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
         h = ctypes.c_void_p()
@@ -298,6 +330,31 @@ class Batch:
             return self._results
         return [_result_dict(self._results[k], self.solvers[k].l) for k in range(self.n)]
 
+    def solve_guided(self, guess_ptr: int, guess_dim: int, stencil, opt_tol=1e-3, eq_tol=1e-4,
+                     max_iters=28, raw=False):
+        """pcba_batch_solve_guided: guess_ptr is a device pointer to [n][guess_dim]
+        float32 normalised guesses; stencil a [n_stencil][guess_dim] array."""
+        st = np.ascontiguousarray(stencil, dtype=np.float64).reshape(-1, guess_dim)
+        _check(lib().pcba_batch_solve_guided(self._b, opt_tol, eq_tol, max_iters,
+                                             ctypes.c_void_p(guess_ptr), guess_dim, _p(st),
+                                             st.shape[0], self._results))
+        if raw:
+            return self._results
+        return [_result_dict(self._results[k], self.solvers[k].l) for k in range(self.n)]
+
+    def warm_point(self, k, with_cost=False):
+        """The certified-feasible seed of problem k in the last solve (its point,
+        and its certified cost bound if with_cost), or None."""
+        x = np.empty(MAX_DIM)
+        c = ctypes.c_double()
+        if _check(lib().pcba_batch_warm_point(self._b, k, _p(x), ctypes.byref(c))) == 0:
+            return None
+        return (x[:self.solvers[k].l].copy(), c.value) if with_cost else x[:self.solvers[k].l].copy()
+
+    def cost_grid(self, G, out_ptr, ld, col0=0):
+        """pcba_batch_cost_grid into a device float buffer (queued on the batch stream)."""
+        _check(lib().pcba_batch_cost_grid(self._b, G, ctypes.c_void_p(out_ptr), ld, col0))
+
     def input_doubles(self) -> int:
         return int(lib().pcba_batch_input_doubles(self._b))
 
@@ -367,3 +424,67 @@ def solve_batch(solvers, opt_tol=1e-3, eq_tol=1e-4, max_iters=28, mem_cap_total=
         return b.solve(opt_tol, eq_tol, max_iters, warm)
     finally:
         b.close()
+
+
+class Mlp:
+    """The warm-start set-encoder network (pcba_mlp_*, include/pcba_warmstart.h).
+
+    Batch inputs are device pointers (e.g. torch CUDA tensors' data_ptr()):
+    points [P][point_dim] float32, offsets [B+1] int32, glob [B][global_dim]
+    float32, target / out [B][2] float32."""
+
+    BF16, FP32 = 16, 32
+
+    def __init__(self, point_dim=2, global_dim=34, hidden=128, precision=16, seed=0):
+        m = ctypes.c_void_p()
+        _check(lib().pcba_mlp_create(ctypes.byref(m), point_dim, global_dim, hidden, precision,
+                                     seed))
+        self._m = m
+        self.dims = (point_dim, global_dim, hidden, 2)
+        self.n_params = int(lib().pcba_mlp_num_params(m))
+
+    def close(self):
+        if getattr(self, "_m", None):
+            lib().pcba_mlp_destroy(self._m)
+            self._m = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().pcba_mlp_get_params(self._m, _p(out), self.n_params))
+        return out
+
+    def set_params(self, theta):
+        t = np.ascontiguousarray(theta, dtype=np.float32)
+        assert t.size == self.n_params
+        _check(lib().pcba_mlp_set_params(self._m, _p(t), self.n_params))
+
+    def forward(self, points, offsets, n_sets, n_points, glob, out, stream=0):
+        _check(lib().pcba_mlp_forward(self._m, ctypes.c_void_p(points), ctypes.c_void_p(offsets),
+                                      n_sets, n_points, ctypes.c_void_p(glob),
+                                      ctypes.c_void_p(out), ctypes.c_void_p(stream)))
+
+    def gradient(self, points, offsets, n_sets, n_points, glob, target, stream=0):
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(lib().pcba_mlp_gradient(self._m, ctypes.c_void_p(points), ctypes.c_void_p(offsets),
+                                       n_sets, n_points, ctypes.c_void_p(glob),
+                                       ctypes.c_void_p(target), _p(g), ctypes.byref(loss),
+                                       ctypes.c_void_p(stream)))
+        return g, loss.value
+
+    def train_step(self, points, offsets, n_sets, n_points, glob, target, lr, want_loss=True,
+                   stream=0):
+        loss = ctypes.c_float()
+        _check(lib().pcba_mlp_train_step(self._m, ctypes.c_void_p(points),
+                                         ctypes.c_void_p(offsets), n_sets, n_points,
+                                         ctypes.c_void_p(glob), ctypes.c_void_p(target),
+                                         ctypes.c_float(lr),
+                                         ctypes.byref(loss) if want_loss else None,
+                                         ctypes.c_void_p(stream)))
+        return loss.value if want_loss else None

@@ -125,12 +125,13 @@ def rtd(seed: int, n_obstacles: int = 512, radius: float = 0.15, f_degree: int =
     # cost = ||F||^2 - 2 goal.F + ||goal||^2
     cost = poly_add(FF, -2.0 * goal[0] * F[0] - 2.0 * goal[1] * F[1])
     cost = poly_add(cost, float(goal @ goal) * one)
-    # g_i = r^2 - ||o_i||^2 - ||F||^2 + 2 o_i.F
-    ineq = np.empty((n_obstacles,) + FF.shape)
-    for i, o in enumerate(obstacles):
-        g = poly_add(-FF, 2.0 * o[0] * F[0] + 2.0 * o[1] * F[1])
-        g = poly_add(g, (radius * radius - float(o @ o)) * one)
-        ineq[i] = pad_to(g, FF.shape)
+    # g_i = r^2 - ||o_i||^2 - ||F||^2 + 2 o_i.F, all obstacles at once
+    ineq = np.zeros((n_obstacles,) + FF.shape)
+    ineq += -FF
+    sl = (slice(None),) + tuple(slice(0, s) for s in shape)
+    ineq[sl] += (2.0 * obstacles[:, 0])[:, None, None] * F[0] \
+        + (2.0 * obstacles[:, 1])[:, None, None] * F[1]
+    ineq[:, 0, 0] += np.array([radius * radius - float(o @ o) for o in obstacles])
     return Problem(pad_to(cost, FF.shape), ineq, _empty_family(2), -np.ones(2), np.ones(2),
                    {"F": F, "obstacles": obstacles, "goal": goal, "radius": radius,
                     "workload": "rtd", "seed": seed})

@@ -21,7 +21,9 @@ def lib():
 
 
 def declared_functions():
-    text = open(os.path.join(ROOT, "include", "pcba.h")).read()
+    inc = os.path.join(ROOT, "include")
+    text = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc))
+                   if f.endswith(".h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     return sorted(set(re.findall(r"\b(pcba_[a-z_]+)\s*\(", text)))
 
@@ -69,3 +71,12 @@ def test_item_bytes_follow_memory_formula(lib):
     assert 4 * entries <= s.item_bytes() <= 4 * entries + 4 * 513 + 1024
     s64 = pcba.Solver(p.cost, p.ineq, p.eq, p.lo, p.hi, precision=pcba.FP64)
     assert 8 * (49 + 512 * 49) <= s64.item_bytes() <= 8 * (49 + 512 * 49) + 1024
+
+
+def test_network_create_validates_on_host(lib):
+    with pytest.raises(pcba.PcbaError, match="precision"):
+        pcba.Mlp(2, 34, 128, precision=8)
+    with pytest.raises(pcba.PcbaError, match="shape"):
+        pcba.Mlp(0, 34, 128)
+    with pytest.raises(pcba.PcbaError, match="shape"):
+        pcba.Mlp(2, 34, 0)
