@@ -1,9 +1,12 @@
 """Benchmark: certified-optimal PCBA solves per second on RTD-shaped problems.
 
-One step = one batched solve, through the C ABI, of B problems per GPU: the
-whole path (FP64 monomial-to-Bernstein conversion, the branch and bound loop of
-subdivide / bound / incumbent / cut-off / compaction, FP64 check of the
-returned points) until every problem is certified or stops.
+One step = one batched solve, through the C ABI, of B problems per GPU with the
+whole path: the learned warm start (cost-landscape features, the set-encoder
+network's forward pass, FP32-certified candidates seeding the incumbent), the
+FP64 monomial-to-Bernstein conversion, the branch and bound loop of subdivide /
+bound / incumbent / cut-off / compaction, and the FP64 check of the returned
+points, until every problem is certified or stops.  The same solve without
+the warm start, in FP32 and in FP64, is timed beside it.
 
   python bench.py [--gpus N --steps K --warmup W]      the CUDA library
   python bench.py --impl reference [...]               the CPU oracle on host cores
@@ -226,7 +229,55 @@ def make_batch(seeds, precision, flags=0, mem_cap=MEM_CAP):
     solvers = [pcba.Solver(p.cost, p.ineq, p.eq, p.lo, p.hi, precision=precision) for p in probs]
     host = np.concatenate([np.concatenate([p.cost.ravel(), p.ineq.ravel(), p.eq.ravel()])
                            for p in probs])
-    return pcba.Batch(solvers, mem_cap, flags=flags), solvers, host
+    return pcba.Batch(solvers, mem_cap, flags=flags), solvers, host, probs
+
+
+class Learned:
+    """The learned-warm-start step on one batch: features, forward pass and
+    guided solve, all queued on one stream."""
+
+    def __init__(self, batch, probs):
+        import torch
+        from paper_2003_01758_b300 import warmstart
+        self.ws = warmstart
+        self.batch = batch
+        self.model = warmstart.load_model()
+        self.stream = torch.cuda.Stream()
+        batch.set_stream(self.stream.cuda_stream)
+        self.points, self.offsets, self.glob = warmstart.host_inputs(probs)
+        self.pk = warmstart.Packed(self.points, self.offsets, self.glob)
+        self.y = torch.empty((len(probs), 2), dtype=torch.float32, device="cuda")
+        self.stencil = warmstart.default_stencil()
+        torch.cuda.synchronize()
+
+    def step(self, raw=True):
+        ws, b = self.ws, self.batch
+        b.cost_grid(ws.GRID, self.pk.glob.data_ptr(), ws.GLOBAL_DIM, ws.HOST_DIM)
+        self.model.forward(*self.pk.args(), self.y.data_ptr(), stream=self.stream.cuda_stream)
+        return b.solve_guided(self.y.data_ptr(), 2, self.stencil, OPT_TOL, EQ_TOL, MAX_ITERS,
+                              raw=raw)
+
+    def launches_per_step(self):
+        return self.batch.stats()["kernel_launches"] + 1 + 12
+
+    def timed(self, steps, flush):
+        """K learned steps; device time from CUDA events on the step's stream."""
+        import torch
+        ms, times, status, steps_ = [], [], [], []
+        for _ in range(steps):
+            flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(self.stream)
+            res = self.step()
+            e1.record(self.stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+            times += [r.time_ms for r in res]
+            status += [r.status for r in res]
+            steps_ += [r.steps for r in res]
+        return ms, times, status, steps_
 
 
 def timed_steps(batch, steps, flush):
@@ -289,35 +340,37 @@ def main():
     seeds = shard_seeds(rank, batch=args.problems)
     mem_cap = int(args.mem_gb * 2 ** 30)
     loop_flag = 0 if args.loop == "graph" else pcba.Batch.HOST_LOOP
-    batch, solvers, host_np = make_batch(seeds, pcba.FP32, flags=loop_flag, mem_cap=mem_cap)
+    batch, solvers, host_np, probs = make_batch(seeds, pcba.FP32, flags=loop_flag,
+                                                mem_cap=mem_cap)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    learned = Learned(batch, probs)
 
     for _ in range(args.warmup):
-        batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+        learned.step()
 
-    # ---- timed region: K batched solves, inputs resident in HBM ----
+    # ---- timed region: K learned-warm-start batched solves, inputs resident in HBM ----
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    ms, times, status = timed_steps(batch, args.steps, flush)
+    ms, times, status, nsteps = learned.timed(args.steps, flush)
     clk = clocks.stop()
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
     total_ms = reduce_max(float(sum(ms)), world)
-    stats = batch.stats()
-    launches = stats["kernel_launches"] * args.steps  # same loop count each step
+    launches = learned.launches_per_step() * args.steps
 
     value = world * len(seeds) * args.steps / (total_ms / 1e3)
     optimal = sum(1 for s in status if s == pcba.OPTIMAL)
     infeasible = sum(1 for s in status if s == pcba.INFEASIBLE)
     if args.no_extras:
         if args.launch_bytes and rank == 0:
-            ib, _, _ = make_batch(seeds, pcba.FP32, flags=pcba.Batch.INSTRUMENT, mem_cap=mem_cap)
-            ib.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+            ib, _, _, _ = make_batch(seeds, pcba.FP32, flags=pcba.Batch.INSTRUMENT,
+                                     mem_cap=mem_cap)
+            Learned(ib, probs).step()
             print(json.dumps({"launch_bytes": ib.launch_bytes().tolist(), "timing": ib.timing()}))
             ib.close()
         if rank == 0:
@@ -327,31 +380,57 @@ def main():
                               "certified": optimal + infeasible, "clocks": clk}))
         return 0
 
-    # ---- end to end: host coefficients in, results out, wall clock ----
+    # ---- the same solves without the warm start ----
+    with torch.cuda.stream(learned.stream):
+        batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+        cms, ctimes, cstatus = timed_steps(batch, args.steps, flush)
+        cold_steps = [r["steps"] for r in batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)]
+    cold = {"value": world * len(seeds) * len(cms) / (reduce_max(float(sum(cms)), world) / 1e3),
+            "unit": UNIT, "p50_ms": float(np.median(ctimes)),
+            "p99_ms": float(np.percentile(ctimes, 99)),
+            "certified": sum(1 for s in cstatus if s in (0, 1)), "solves": len(cstatus),
+            "mean_bisection_steps": float(np.mean(cold_steps))}
+
+    # ---- end to end: host inputs in (coefficients, obstacle points, goal and map
+    # features), network, guided solve, results out; wall clock ----
     host = torch.from_numpy(host_np).pin_memory().numpy()
-    batch.solve_from_host(host, OPT_TOL, EQ_TOL, MAX_ITERS)
+    h_points = torch.from_numpy(learned.points).pin_memory()
+    h_offsets = torch.from_numpy(learned.offsets).pin_memory()
+    h_glob = torch.from_numpy(learned.glob).pin_memory()
+    torch_h2d = 4 * (learned.points.size + learned.offsets.size + learned.glob.size)
+
+    def e2e_step():
+        with torch.cuda.stream(learned.stream):
+            batch.upload(host)
+            learned.pk.points.copy_(h_points, non_blocking=True)
+            learned.pk.offsets.copy_(h_offsets, non_blocking=True)
+            learned.pk.glob.copy_(h_glob, non_blocking=True)
+            return learned.step()
+
+    e2e_step()
     e2e_s = 0.0
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t = time.perf_counter()
-        batch.solve_from_host(host, OPT_TOL, EQ_TOL, MAX_ITERS, raw=True)
+        e2e_step()
         e2e_s += time.perf_counter() - t
     e2e_stats = batch.stats()
     e2e_total = reduce_max(e2e_s, world)
     e2e_value = world * len(seeds) * args.steps / e2e_total
 
     # ---- roofline of the subdivide/bound kernel: CUDA events around each launch ----
-    ibatch, _, _ = make_batch(seeds, pcba.FP32, flags=pcba.Batch.INSTRUMENT, mem_cap=mem_cap)
-    ibatch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
-    ibatch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+    ibatch, _, _, _ = make_batch(seeds, pcba.FP32, flags=pcba.Batch.INSTRUMENT, mem_cap=mem_cap)
+    ilearned = Learned(ibatch, probs)
+    ilearned.step()
+    ilearned.step()
     it = ibatch.timing()
     ibatch.close()
     peak, peak_kind = load_peaks()
     achieved = it["subdiv_bytes"] / (it["subdiv_ms"] * 1e-3) / 1e9 if it["subdiv_ms"] > 0 else 0.0
 
     # ---- FP64 mode, same problems ----
-    b64, s64, _ = make_batch(seeds, pcba.FP64, mem_cap=mem_cap)
+    b64, s64, _, _ = make_batch(seeds, pcba.FP64, mem_cap=mem_cap)
     b64.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
     ms64, _, st64 = timed_steps(b64, max(1, args.steps // 2), flush)
     fp64_value = len(seeds) * len(ms64) / (sum(ms64) / 1e3)
@@ -377,6 +456,39 @@ def main():
                   "autotune": tune}
         ub.close()
 
+    # ---- learned warm start A/B: 256 held-out problems, obstacles log-uniform in
+    # [64, 1024] (the training range), seeds 6000+k: cold / learned / fixed grid ----
+    ab = None
+    if rank == 0 and world == 1:
+        from paper_2003_01758_b300 import train_warmstart
+        ab = train_warmstart.ab_compare(learned.model, train_warmstart.held_out(256))
+        ab["workload"] = ("256 held-out rtd problems, obstacles floor(exp U(ln 64, ln 1024)), "
+                          "seeds 6000+k, FP32, one batched solve per arm and repeat; network "
+                          "trained on 100k solutions of seeds 5000000+k")
+
+    # ---- 4-D problems: 64 inequalities of degree 3, 2 equalities of degree 2,
+    # eq_tol 1e-4, 8 GiB list cap per problem, FP32 (and FP64) ----
+    dim4 = None
+    if rank == 0 and world == 1:
+        from paper_2003_01758_b300 import workloads as W
+        d4 = [W.dim4(3000 + k) for k in range(8)]
+        dim4 = {"workload": "8 problems l=4, cost degree 4, 64 g_i degree 3, 2 h_j degree 2, "
+                            "seeds 3000+k, eq_tol 1e-4, 8 GiB per problem"}
+        for prec, name in ((pcba.FP32, "fp32"), (pcba.FP64, "fp64")):
+            db = pcba.Batch([pcba.Solver(q.cost, q.ineq, q.eq, q.lo, q.hi, precision=prec)
+                             for q in d4], 8 * (8 << 30))
+            db.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+            dms, dtimes, dstatus = timed_steps(db, 2, flush)
+            dres = db.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+            dim4[name] = {"value": 8 * len(dms) / (sum(dms) / 1e3), "unit": UNIT,
+                          "ms_per_step": float(np.mean(dms)),
+                          "p50_ms": float(np.median(dtimes)),
+                          "p99_ms": float(np.percentile(dtimes, 99)),
+                          "status": [pcba.STATUS_NAMES.get(r["status"], r["status"]) for r in dres],
+                          "max_width": float(max(r["upper"] - r["lower"] for r in dres)),
+                          "max_abs_h": float(max(r["verify_max_abs_h"] for r in dres))}
+            db.close()
+
     # ---- one problem at a time (latency of a single solve) ----
     single = []
     for s in solvers[:16]:
@@ -397,12 +509,16 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "problems_per_step": len(seeds),
+                   "warm_start": "learned (set-encoder network, BF16; %d-candidate stencil "
+                                 "certified in FP32)" % len(learned.stencil),
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "independent problems per GPU (dp%d)" % world,
                    "device_loop": args.loop},
         "p50_ms": float(np.median(times)), "p99_ms": float(np.percentile(times, 99)),
         "certified": {"optimal": optimal, "infeasible": infeasible,
                       "failed": len(status) - optimal - infeasible},
+        "mean_bisection_steps": float(np.mean(nsteps)),
+        "no_warm_start": cold,
         "fp64_value": fp64_value,
         "fp64_certified": sum(1 for s in st64 if s in (0, 1)),
         "single_problem_ms": {"p50": float(np.median(single)),
@@ -410,14 +526,17 @@ def main():
                               "solves_per_s": 1e3 / float(np.mean(single))},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "traffic": profiled_traffic(),
-                     "kernel": "k2_subdivide<float>", "peak_kind": peak_kind,
+                     "kernel": "k2_subdivide_tma<float>", "peak_kind": peak_kind,
                      "launches": it["subdiv_launches"],
                      "algorithmic_bytes_per_launch": it["subdiv_bytes"] / max(1, it["subdiv_launches"]),
                      "avg_launch_ms": it["subdiv_ms"] / max(1, it["subdiv_launches"])},
         "cpu_baseline": base,
-        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": e2e_stats["h2d_bytes"],
+        "e2e": {"value": e2e_value, "unit": UNIT,
+                "h2d_bytes_per_step": e2e_stats["h2d_bytes"] + torch_h2d,
                 "d2h_bytes_per_step": e2e_stats["d2h_bytes"]},
         "uneven_batch": uneven,
+        "learned_warm_start_ab": ab,
+        "dim4": dim4,
         "gpu_launches": launches,
         "clocks": clk,
     }

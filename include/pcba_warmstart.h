@@ -51,6 +51,8 @@ int pcba_mlp_create(pcba_mlp** out, int point_dim, int global_dim, int hidden, i
                     unsigned long long seed);
 void pcba_mlp_destroy(pcba_mlp* m);
 long long pcba_mlp_num_params(const pcba_mlp* m);
+/* Kernels this network has launched since it was created. */
+long long pcba_mlp_kernel_launches(const pcba_mlp* m);
 /* Host copies of the FP32 parameter vector (n must equal pcba_mlp_num_params).
  * set_params also resets the Adam moments and step count. */
 int pcba_mlp_set_params(pcba_mlp* m, const float* host_params, long long n);
@@ -97,6 +99,14 @@ int pcba_mlp_train_step(pcba_mlp* m, const float* d_points, const int* d_offsets
 int pcba_batch_solve_guided(pcba_batch* b, double opt_tol, double eq_tol, int max_iters,
                             const float* d_guess, int guess_dim, const double* stencil,
                             int n_stencil, pcba_result* out);
+
+/* Queues the copy of every problem's monomial coefficients (the layout of
+ * pcba_batch_solve_from_host, pcba_batch_input_doubles of them) from host
+ * memory to the batch's device copy on the batch's stream, so that feature
+ * kernels (pcba_batch_cost_grid) and a following pcba_batch_solve_guided see
+ * new inputs; the bytes are counted in the next solve's host-to-device total.
+ * Pageable host memory makes the copy synchronous. */
+int pcba_batch_upload(pcba_batch* b, const double* host_coeffs);
 
 /* The incumbent seed of problem k in the last solve of the batch: returns 1
  * if a candidate (or the warm start point) was certified feasible, writing it

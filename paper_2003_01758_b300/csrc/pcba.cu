@@ -155,6 +155,8 @@ struct pcba_batch {
   double total_ms = 0, subdiv_ms = 0, subdiv_bytes = 0;
   long long subdiv_launches = 0;
   long long h2d_bytes = 0, d2h_bytes = 0;
+  long long pending_h2d = 0;      // bytes queued by pcba_batch_upload since the last solve
+  long long extra_launches = 0;   // prologue kernels of warm starts in the last solve
   std::vector<double> launch_bytes;
 };
 
@@ -774,7 +776,9 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   PCBA_CK(cudaEventRecord(b->ev0, s));
   b->h2d_bytes = (long long)sizeof(SolveParams) + (host_coeffs ? 8LL * b->mono_doubles : 0) +
                  (warm ? 8LL * PCBA_MAXD * n : 0) +
-                 (guide ? 8LL * guide->n * guide->dim : 0);
+                 (guide ? 8LL * guide->n * guide->dim : 0) + b->pending_h2d;
+  b->pending_h2d = 0;
+  b->extra_launches = (guide || warm ? 1 : 0) + (guide ? 1 : 0);
   b->d2h_bytes = (long long)(sizeof(ProbState) + sizeof(EvalOut)) * n + (long long)sizeof(Plan);
   if (host_coeffs)
     PCBA_CK(cudaMemcpyAsync(b->d_mono, host_coeffs, sizeof(double) * b->mono_doubles,
@@ -1108,6 +1112,14 @@ int pcba_batch_solve_guided(pcba_batch* b, double opt_tol, double eq_tol, int ma
   return batch_solve_impl(b, nullptr, opt_tol, eq_tol, max_iters, 0, nullptr, out, false, &g);
 }
 
+int pcba_batch_upload(pcba_batch* b, const double* host_coeffs) {
+  if (!b || !host_coeffs) return fail(PCBA_ERR_INVALID, "batch or host_coeffs is null");
+  PCBA_CK(cudaMemcpyAsync(b->d_mono, host_coeffs, sizeof(double) * b->mono_doubles,
+                          cudaMemcpyHostToDevice, b->stream));
+  b->pending_h2d += 8LL * b->mono_doubles;
+  return 0;
+}
+
 int pcba_batch_warm_point(const pcba_batch* b, int k, double* x, double* cost) {
   if (!b || k < 0 || k >= b->np) return fail(PCBA_ERR_INVALID, "bad batch or index");
   const ProbState& S = b->h_state[k];
@@ -1198,9 +1210,11 @@ int pcba_batch_stats(const pcba_batch* b, long long* loop_iters, long long* kern
   if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
   const long long it = b->h_plan ? b->h_plan->steps_global : 0;
   if (loop_iters) *loop_iters = it;
-  // prologue: k1_matrices, k1_convert, k_eval, k_init; 6 kernels per loop
-  // iteration (7 with the FP32 refresh); epilogue: k_eval
-  if (kernel_launches) *kernel_launches = 5 + (b->precision == PCBA_FP32 ? 7 : 6) * it;
+  // prologue: k1_matrices, k1_convert, k_eval, k_init (plus k_mono32 and
+  // k_candidates for warm starts); 6 kernels per loop iteration (7 with the
+  // FP32 refresh); epilogue: k_eval
+  if (kernel_launches)
+    *kernel_launches = 5 + (b->precision == PCBA_FP32 ? 7 : 6) * it + b->extra_launches;
   if (h2d_bytes) *h2d_bytes = b->h2d_bytes;
   if (d2h_bytes) *d2h_bytes = b->d2h_bytes;
   return 0;

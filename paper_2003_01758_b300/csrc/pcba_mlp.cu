@@ -286,6 +286,7 @@ struct pcba_mlp {
   long long off[12];  // offsets of W1, b1, ..., W6, b6 in the parameter vector
   float *d_par = nullptr, *d_grad = nullptr, *d_m = nullptr, *d_v = nullptr;
   long long step = 0;
+  long long launches = 0;  // kernels launched
   // workspace
   long long capP = 0, capB = 0;
   float *h1 = nullptr, *h2 = nullptr, *h3 = nullptr, *dA = nullptr, *dB = nullptr;
@@ -358,9 +359,10 @@ int check_batch(const pcba_mlp* m, int n_sets, int n_points) {
   return 0;
 }
 
-// forward pass; leaves activations in the workspace
+// forward pass; leaves activations in the workspace (12 kernels)
 void forward(pcba_mlp* m, cudaStream_t s, const float* pts, const int* off, int B, int P,
              const float* glob) {
+  m->launches += 12;
   const int H = m->H, W = m->H + m->dg;
   const float* par = m->d_par;
   const int bf16 = m->prec == 16;
@@ -380,9 +382,10 @@ void forward(pcba_mlp* m, cudaStream_t s, const float* pts, const int* off, int 
                                                       m->y, m->s6, bf16);
 }
 
-// backward pass into d_grad (zeroed here) for targets tgt
+// backward pass into d_grad (zeroed here) for targets tgt (21 kernels)
 void backward(pcba_mlp* m, cudaStream_t s, const float* pts, const int* off, int B, int P,
               const float* tgt) {
+  m->launches += 21;
   const int H = m->H, W = m->H + m->dg;
   const float* par = m->d_par;
   float* g = m->d_grad;
@@ -493,6 +496,8 @@ void pcba_mlp_destroy(pcba_mlp* m) {
 
 long long pcba_mlp_num_params(const pcba_mlp* m) { return m ? m->np : 0; }
 
+long long pcba_mlp_kernel_launches(const pcba_mlp* m) { return m ? m->launches : 0; }
+
 int pcba_mlp_set_params(pcba_mlp* m, const float* host_params, long long n) {
   if (!m || !host_params || n != m->np) return pcba_internal_fail(PCBA_ERR_INVALID, "bad parameters");
   MLP_CK(cudaMemcpy(m->d_par, host_params, sizeof(float) * n, cudaMemcpyHostToDevice));
@@ -551,6 +556,7 @@ int pcba_mlp_train_step(pcba_mlp* m, const float* d_points, const int* d_offsets
   const float c1 = 1.0f - (float)std::pow(0.9, (double)m->step);
   const float c2 = 1.0f - (float)std::pow(0.999, (double)m->step);
   adam<<<blocks(m->np), 256, 0, s>>>(m->d_par, m->d_grad, m->d_m, m->d_v, m->np, lr, c1, c2);
+  m->launches += 1;
   MLP_CK(cudaGetLastError());
   if (loss) {
     MLP_CK(cudaMemcpyAsync(m->h_loss, m->d_loss, sizeof(float), cudaMemcpyDeviceToHost, s));

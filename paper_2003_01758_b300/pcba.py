@@ -101,6 +101,8 @@ def lib():
         "pcba_batch_solve_guided": ([P, D, D, I, P, I, P, I, P], I),
         "pcba_batch_warm_point": ([P, I, P, P], I),
         "pcba_batch_cost_grid": ([P, I, P, I, I], I),
+        "pcba_batch_upload": ([P, P], I),
+        "pcba_mlp_kernel_launches": ([P], LL),
         "pcba_mlp_create": ([P, I, I, I, I, ctypes.c_ulonglong], I),
         "pcba_mlp_destroy": ([P], None),
         "pcba_mlp_num_params": ([P], LL),
@@ -128,7 +130,8 @@ def exported_symbols():
             "pcba_get_list", "pcba_root_patches", "pcba_item_bytes", "pcba_set_stream",
             "pcba_set_warm_start", "pcba_destroy", "pcba_status_string", "pcba_last_error",
             "pcba_version", "pcba_bernstein_convert_noalloc", "pcba_batch_solve_guided",
-            "pcba_batch_warm_point", "pcba_batch_cost_grid", "pcba_mlp_create", "pcba_mlp_destroy", "pcba_mlp_num_params", "pcba_mlp_set_params",
+            "pcba_batch_warm_point", "pcba_batch_cost_grid", "pcba_batch_upload", "pcba_mlp_kernel_launches",
+            "pcba_mlp_create", "pcba_mlp_destroy", "pcba_mlp_num_params", "pcba_mlp_set_params",
             "pcba_mlp_get_params", "pcba_mlp_forward", "pcba_mlp_gradient",
             "pcba_mlp_train_step"]
 
@@ -351,6 +354,11 @@ class Batch:
             return None
         return (x[:self.solvers[k].l].copy(), c.value) if with_cost else x[:self.solvers[k].l].copy()
 
+    def upload(self, host_coeffs):
+        """pcba_batch_upload: queue the host->device copy of all coefficients."""
+        assert host_coeffs.dtype == np.float64 and host_coeffs.size == self.input_doubles()
+        _check(lib().pcba_batch_upload(self._b, _p(host_coeffs)))
+
     def cost_grid(self, G, out_ptr, ld, col0=0):
         """pcba_batch_cost_grid into a device float buffer (queued on the batch stream)."""
         _check(lib().pcba_batch_cost_grid(self._b, G, ctypes.c_void_p(out_ptr), ld, col0))
@@ -453,6 +461,9 @@ class Mlp:
             self.close()
         except Exception:
             pass
+
+    def kernel_launches(self):
+        return int(lib().pcba_mlp_kernel_launches(self._m))
 
     def get_params(self):
         out = np.empty(self.n_params, dtype=np.float32)

@@ -38,12 +38,7 @@ def ab_compare(mlp, probs, mem_cap_total=64 << 30, repeats=3):
     b = pcba.Batch([pcba.solver_from_problem(p, pcba.FP32) for p in probs], mem_cap_total)
     stream = torch.cuda.Stream()
     b.set_stream(stream.cuda_stream)
-    feats = [warmstart.features(p) for p in probs]
-    sizes = [f[0].shape[0] for f in feats]
-    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
-    glob = np.zeros((len(probs), warmstart.GLOBAL_DIM), dtype=np.float32)
-    glob[:, :warmstart.HOST_DIM] = np.stack([f[1] for f in feats])
-    pk = warmstart.Packed(np.concatenate([f[0] for f in feats]), offsets, glob)
+    pk = warmstart.Packed(*warmstart.host_inputs(probs))
     zero = torch.zeros((len(probs), 2), dtype=torch.float32, device="cuda")
     torch.cuda.synchronize()
     out = {}

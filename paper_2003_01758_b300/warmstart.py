@@ -18,6 +18,7 @@ in libpcba's kernels.
 from __future__ import annotations
 
 import math
+import os
 import time
 
 import numpy as np
@@ -96,12 +97,7 @@ def pack_batch(problems, batch, targets=None, device="cuda"):
     """Packed network inputs of the problems of a pcba.Batch (same order): the
     host features plus the cost landscape, computed by the library on the
     device into the last GRID^2 columns of glob."""
-    feats = [features(p) for p in problems]
-    sizes = [f[0].shape[0] for f in feats]
-    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
-    points = np.concatenate([f[0] for f in feats])
-    glob = np.zeros((len(problems), GLOBAL_DIM), dtype=np.float32)
-    glob[:, :HOST_DIM] = np.stack([f[1] for f in feats])
+    points, offsets, glob = host_inputs(problems)
     pk = Packed(points, offsets, glob, targets, device)
     torch.cuda.synchronize()
     batch.cost_grid(GRID, pk.glob.data_ptr(), GLOBAL_DIM, HOST_DIM)
@@ -203,3 +199,26 @@ def predict(mlp, packed, stream=0):
 def load_params(path):
     z = np.load(path)
     return z["theta"].astype(np.float32), dict(hidden=int(z["hidden"]))
+
+
+DEFAULT_PARAMS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "warmstart_rtd.npz")
+
+
+def load_model(path=DEFAULT_PARAMS):
+    """The trained network (BF16) with the parameters stored at path."""
+    theta, meta = load_params(path)
+    m = pcba.Mlp(POINT_DIM, GLOBAL_DIM, meta["hidden"], pcba.Mlp.BF16)
+    m.set_params(theta)
+    return m
+
+
+def host_inputs(problems):
+    """Host arrays of the network inputs of a batch: points [P][2], offsets
+    [B+1] int32 and glob [B][GLOBAL_DIM] whose cost-landscape columns are zero
+    (pcba_batch_cost_grid fills them on the device)."""
+    feats = [features(p) for p in problems]
+    sizes = [f[0].shape[0] for f in feats]
+    offsets = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int32)
+    glob = np.zeros((len(problems), GLOBAL_DIM), dtype=np.float32)
+    glob[:, :HOST_DIM] = np.stack([f[1] for f in feats])
+    return np.concatenate([f[0] for f in feats]), offsets, glob
