@@ -76,17 +76,27 @@ def load_peaks():
         return 6400.0, "fallback"
 
 
+def kernel_code_hash(path):
+    """sha256 (first 16 hex) of a CUDA source with comments and whitespace
+    removed, so that the hash changes only when the code does."""
+    import hashlib
+    import re
+    text = open(path).read()
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    text = " ".join(text.split())
+    return hashlib.sha256(text.encode()).hexdigest()[:16]
+
+
 def profiled_traffic():
     """DRAM bytes per subdivision launch from the committed ncu summary, or None
-    when the kernel source changed since that capture."""
-    import hashlib
+    when the kernel code changed since that capture."""
     import re
     src = os.path.join(ROOT, "paper_2003_01758_b300", "csrc", "pcba_kernels.cuh")
     prof = os.path.join(ROOT, "profiles", "k2_subdivide_rtd512_fp32.md")
     try:
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
         text = open(prof).read()
-        if "`%s`" % sha not in text:
+        if "`%s`" % kernel_code_hash(src) not in text:
             return None
         m = re.search(r"TRAFFIC_BYTES_PER_LAUNCH = ([0-9.e+]+)", text)
         return float(m.group(1)) if m else None

@@ -5,11 +5,16 @@
 //                             the matrix T_r = (power -> Bernstein on [0,1]) x
 //                             (affine map [lo,hi] -> [0,1]), applied as l mode
 //                             products to every monomial tensor, in FP64.
-//   k2_subdivide              Alg. 2 + Alg. 3 + Def. 4: bisect every item in
-//                             direction r (de Casteljau at 1/2 on every fibre,
-//                             Sec. II-E), bound every child patch by the min and
-//                             max of its coefficients (Thm. 1) and lower the
-//                             solution estimate p_up with an atomic min.
+//   k2_subdivide(_tma)        Alg. 2 + Alg. 3: bisect every item in direction r
+//                             (de Casteljau at 1/2 on every fibre, Sec. II-E)
+//                             and bound every child patch by the min and max of
+//                             its coefficients (Thm. 1) into per-child records;
+//                             the _tma variant stages parent tiles in shared
+//                             memory with bulk tensor copies.
+//   k_pup                     Def. 4: the solution estimate p_up (min over
+//                             feasible children), and the returned box.
+//   k_refresh                 FP32 mode: recomputes marked patches from the
+//                             FP64 monomials over their box (tighter bounds).
 //   k3_classify               Alg. 4 (readings R3-R5): keep = not infeasible
 //                             (Def. 3) and not suboptimal (Def. 5); p_lo; scan of
 //                             the keep flags; the last tile of each problem runs
@@ -18,8 +23,12 @@
 //   k4_index / k4_move        Alg. 5 (reading R11): the j-th hole below K_save
 //                             receives the item at save position K_save-1-j.
 //   k_control                 device-side loop control (graph conditional).
-//   k_eval                    FP64 evaluation of p, g_i, h_j at a point with a
-//                             rounding-error bound (warm start, final check).
+//   k_eval                    warm start: certified candidate points seed p_up
+//                             (FP32 with error bounds); final check of the
+//                             returned point in FP64 with an error bound.
+//   k_candidates, k_mono32,   warm-start helpers: candidate points around a
+//   k_cost_grid               guess, FP32 copy of the monomials, and the cost
+//                             on a grid (network features).
 #pragma once
 
 #include <cuda_runtime.h>
@@ -1058,16 +1067,17 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
 // ---------------------------------------------------------------------------
 // The error bound of an FP32 patch only grows from step to step, and most of
 // it is collected in the first bisections, when Bernstein coefficients on the
-// large boxes are far larger than the polynomial's values.  Once per sweep
-// (from the third sweep on) this kernel recomputes, for every item, the cost
-// patch and every constraint patch marked by the subdivision kernel (enclosure
-// meeting zero, see mark_err) directly from the FP64 monomial coefficients
-// over the item's current box (Sec. II-D, the conversion of k1_convert with
-// the box of the item): the new bound is the FP64 conversion bound plus one
-// rounding to FP32.  Unmarked patches keep their (larger, still valid) bound.
+// large boxes are far larger than the polynomial's values.  Before every step
+// this kernel takes the list of patches the previous step's subdivision marked
+// (their bound changed a decision, see mark_err), finds where each marked
+// child sits after the compaction, and recomputes it directly from the FP64
+// monomial coefficients over the item's current box (Sec. II-D, the
+// conversion of k1_convert with the box of the item): the new bound is the
+// FP64 conversion bound plus one rounding to FP32.  Unmarked patches keep
+// their (larger, still valid) bound.
 //
-// Work unit = (problem, item, 32-patch group); each warp takes a contiguous
-// range of units so that the per-axis matrices of an item's box are built once.
+// One warp per marked patch; the per-axis matrices of the item's box are
+// built in the warp's shared memory.
 __device__ __forceinline__ void refresh_matrices(const double* binom, int l, const int* deg,
                                                  const double* blo, const double* bhi,
                                                  double* sT, int lane) {
