@@ -148,6 +148,8 @@ struct pcba_batch {
   cudaGraphExec_t gexec = nullptr;
   cudaGraphConditionalHandle cond = 0;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  cudaStream_t side = nullptr;                        // k_refresh beside k_pup..k4_index
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::vector<cudaEvent_t> kev;
   Engine E{};
   Grids g;
@@ -282,6 +284,9 @@ void free_batch(pcba_batch* b) {
   for (cudaEvent_t e : b->kev) cudaEventDestroy(e);
   if (b->ev0) cudaEventDestroy(b->ev0);
   if (b->ev1) cudaEventDestroy(b->ev1);
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->side) cudaStreamDestroy(b->side);
   void* dev[] = {b->d_desc, b->d_state, b->d_plan, b->d_params, b->d_pre, b->d_arena, b->d_rec,
                  b->d_slots, b->d_tilecnt, b->d_mono, b->d_trace, b->d_warm, b->d_mat,
                  b->d_raw, b->d_eval, b->d_tmaps, b->d_marks, b->d_cand, b->d_stencil,
@@ -315,19 +320,34 @@ void launch_k2(const pcba_batch* b, cudaStream_t s) {
   else k2_subdivide<T, 16><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
 }
 
+// The kernels of one device-loop iteration after the subdivision: the FP32
+// refresh of the patches it marked runs on a side stream beside k_pup,
+// k3_classify and k4_index (which read only the child records) and joins
+// before k4_move moves items.
 template <typename T>
-int launch_loop_body(pcba_batch* b, cudaStream_t s, int use_graph) {
+int launch_after_k2(pcba_batch* b, cudaStream_t s, int use_graph) {
   const Grids& g = b->g;
-  if (sizeof(T) == 4)
-    k_refresh<<<g.kr_grid, 32 * g.kr_wpb, g.kr_smem, s>>>(b->E, g.kr_cmax, g.kr_lmax);
-  launch_k2<T>(b, s);
+  const bool fp32 = sizeof(T) == 4;
+  if (fp32) {
+    PCBA_CK(cudaEventRecord(b->ev_fork, s));
+    PCBA_CK(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
+    k_refresh<<<g.kr_grid, 32 * g.kr_wpb, g.kr_smem, b->side>>>(b->E, g.kr_cmax, g.kr_lmax);
+    PCBA_CK(cudaEventRecord(b->ev_join, b->side));
+  }
   k_pup<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
   k3_classify<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
   k4_index<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
+  if (fp32) PCBA_CK(cudaStreamWaitEvent(s, b->ev_join, 0));
   k4_move<<<g.k4_grid, PCBA_TPB, 0, s>>>(b->E);
   k_control<<<1, PCBA_TPB, 0, s>>>(b->E, b->cond, use_graph);
   PCBA_CK(cudaGetLastError());
   return 0;
+}
+
+template <typename T>
+int launch_loop_body(pcba_batch* b, cudaStream_t s, int use_graph) {
+  launch_k2<T>(b, s);
+  return launch_after_k2<T>(b, s, use_graph);
 }
 
 template <typename T>
@@ -424,7 +444,7 @@ int setup_kernels(pcba_batch* b) {
                                                           g.kr_smem));
     // marks are few (thousands per solve): two blocks per SM at most
     g.kr_grid = std::max(1, std::min(occ, 2)) * g.sms;
-    double binom[17 * 17];
+    double binom[17 * 17], binom_inv[17 * 17];
     for (int n = 0; n < 17; ++n)
       for (int k = 0; k < 17; ++k) {
         double c = 0.0;
@@ -433,8 +453,10 @@ int setup_kernels(pcba_batch* b) {
           for (int i = 1; i <= k; ++i) c = c * (double)(n - k + i) / (double)i;
         }
         binom[n * 17 + k] = c;
+        binom_inv[n * 17 + k] = c > 0.0 ? 1.0 / c : 0.0;
       }
     PCBA_CK(cudaMemcpyToSymbol(c_binom, binom, sizeof(binom)));
+    PCBA_CK(cudaMemcpyToSymbol(c_binom_inv, binom_inv, sizeof(binom_inv)));
   }
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_classify, PCBA_TPB, 0));
   g.k3_grid = std::max(1, occ) * g.sms;
@@ -712,6 +734,12 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
     return rc;
   if ((rc = cleanup_ck(cudaMemset(b->d_state, 0, sizeof(ProbState) * n), "state clear"))) return rc;
   if ((rc = cleanup_ck(cudaEventCreate(&b->ev0), "event"))) return rc;
+  if ((rc = cleanup_ck(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event")))
+    return rc;
+  if ((rc = cleanup_ck(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming), "event")))
+    return rc;
+  if ((rc = cleanup_ck(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking), "stream")))
+    return rc;
   if ((rc = cleanup_ck(cudaEventCreate(&b->ev1), "event"))) return rc;
   Engine& E = b->E;
   E.np = n;
@@ -833,9 +861,6 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
     int it = 0;
     for (;; ++it) {
       if (it >= guard) return fail(PCBA_ERR_DEVICE_TIMEOUT, "host loop guard reached");
-      if (sizeof(T) == 4)
-        k_refresh<<<b->g.kr_grid, 32 * b->g.kr_wpb, b->g.kr_smem, s>>>(b->E, b->g.kr_cmax,
-                                                                      b->g.kr_lmax);
       if (instrument) {
         double bytes = 0;
         for (int k = 0; k < n; ++k)
@@ -846,12 +871,8 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
       }
       launch_k2<T>(b, s);
       if (instrument) PCBA_CK(cudaEventRecord(b->kev[2 * it + 1], s));
-      k_pup<<<b->g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
-      k3_classify<<<b->g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
-      k4_index<<<b->g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
-      k4_move<<<b->g.k4_grid, PCBA_TPB, 0, s>>>(b->E);
-      k_control<<<1, PCBA_TPB, 0, s>>>(b->E, b->cond, 0);
-      PCBA_CK(cudaGetLastError());
+      const int rc = launch_after_k2<T>(b, s, 0);
+      if (rc) return rc;
       PCBA_CK(cudaMemcpyAsync(b->h_running, &b->d_plan->any_running, sizeof(int),
                               cudaMemcpyDeviceToHost, s));
       if (instrument)

@@ -86,6 +86,8 @@ struct ProbState {
   long long peak_items;
   unsigned long long t_end;
   int done_flag;
+  int child_level[PCBA_MAXD];   // levels of the children of the coming step (set between steps)
+  int child_twoK;               // children of the coming step
   int seeded;                   // a warm-start candidate was certified feasible
   double seed_cost;             // its certified cost bound (the initial p_up)
   double seed_x[PCBA_MAXD];     // the candidate

@@ -1067,17 +1067,27 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
 // ---------------------------------------------------------------------------
 // The error bound of an FP32 patch only grows from step to step, and most of
 // it is collected in the first bisections, when Bernstein coefficients on the
-// large boxes are far larger than the polynomial's values.  Before every step
-// this kernel takes the list of patches the previous step's subdivision marked
-// (their bound changed a decision, see mark_err), finds where each marked
-// child sits after the compaction, and recomputes it directly from the FP64
-// monomial coefficients over the item's current box (Sec. II-D, the
-// conversion of k1_convert with the box of the item): the new bound is the
-// FP64 conversion bound plus one rounding to FP32.  Unmarked patches keep
-// their (larger, still valid) bound.
+// large boxes are far larger than the polynomial's values.  Right after the
+// subdivision, this kernel takes the patches that step marked (their bound
+// changed a decision, see mark_err) and recomputes each, in its child slot,
+// directly from the FP64 monomial coefficients over the child's box (Sec.
+// II-D, the conversion of k1_convert with the box of the item): the new bound
+// is the FP64 conversion bound plus one rounding to FP32.  Unmarked patches
+// keep their (larger, still valid) bound.  It runs beside k_pup, k3_classify
+// and k4_index, which read only the child records, and must finish before
+// k4_move moves items; the child boxes come from the state snapshot
+// child_level, which those kernels do not change.
 //
 // One warp per marked patch; the per-axis matrices of the item's box are
 // built in the warp's shared memory.
+// Binomial coefficients C(n, k), n, k <= 16 (exact integers), and their
+// rounded reciprocals, filled once by the library at start-up.
+__constant__ double c_binom[17 * 17];
+__constant__ double c_binom_inv[17 * 17];
+
+// T_r[i][j] = sum_k C(i,k) C(j,k) / C(n,k) lo^(j-k) w^k (power basis on the
+// box -> Bernstein basis), and A_r its absolute-value sum widened by 2^-40,
+// which covers the few roundings of every term (the reciprocal included).
 __device__ __forceinline__ void refresh_matrices(const double* binom, int l, const int* deg,
                                                  const double* blo, const double* bhi,
                                                  double* sT, int lane) {
@@ -1100,7 +1110,7 @@ __device__ __forceinline__ void refresh_matrices(const double* binom, int l, con
       double t = 0.0, ta = 0.0;
       const int kmax = i < j ? i : j;
       for (int k = 0; k <= kmax; ++k) {
-        const double term = binom[i * 17 + k] / binom[n * 17 + k] * binom[j * 17 + k] *
+        const double term = binom[i * 17 + k] * c_binom_inv[n * 17 + k] * binom[j * 17 + k] *
                             lp[j - k] * wp[k];
         t += term;
         ta += fabs(term);
@@ -1157,26 +1167,9 @@ __device__ __forceinline__ double refresh_convert(const double* a, int C, int l,
   return __dmul_ru(__dmul_ru(2.0 * gterms, 0x1p-53), amax);
 }
 
-// Slot of a child of the previous step after that step's compaction (Alg. 5),
-// or -1 if it was eliminated: kept children below K_save stay, kept children
-// above fill the holes from the top of the save list.
-__device__ __forceinline__ int slot_after_compaction(const Engine& E, const ProbDesc* D,
-                                                     const ProbState* S, int c) {
-  if (c >= S->twoK) return -1;
-  const unsigned fr = E.flagrank[D->slot_off + c];
-  if (!(fr >> 31)) return -1;
-  if (c < S->K_save) return c;
-  const int grank = (int)(E.tilecnt[D->tile_off + c / PCBA_TPB] + (fr & 0x7FFFFFFFu));
-  return (int)E.hole[D->slot_off + (S->K_save - 1 - grank)];
-}
-
-// Binomial coefficients C(n, k), n, k <= 16 (exact integers), filled once by
-// the library at start-up.
-__constant__ double c_binom[17 * 17];
-
 __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
   extern __shared__ double krs[];
-  const int par = (E.plan->steps_global + 1) & 1;  // the list of the previous step
+  const int par = E.plan->steps_global & 1;  // the list this step's subdivision filled
   const unsigned count = min(E.plan->mark_count[par], E.mark_cap);
   if (count == 0) return;
   const double* binom = c_binom;
@@ -1193,13 +1186,12 @@ __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
     const int p = (int)m.x, fam = (int)m.z, ip = (int)m.w;
     const ProbDesc* D = E.desc + p;
     const ProbState* S = E.state + p;
-    if (S->status != PCBA_RUNNING) continue;
-    const int slot = slot_after_compaction(E, D, S, (int)m.y);
-    if (slot < 0) continue;
+    const int slot = (int)m.y;
+    if (slot >= S->child_twoK) continue;
     char* item = E.arena + D->list_off + (size_t)slot * D->item_bytes;
     double blo[PCBA_MAXD], bhi[PCBA_MAXD];
     for (int r = 0; r < D->l; ++r) {
-      const double w = ldexp(D->hi[r] - D->lo[r], -S->level[r]);
+      const double w = ldexp(D->hi[r] - D->lo[r], -S->child_level[r]);
       const unsigned idx = ((const unsigned*)item)[r];
       blo[r] = D->lo[r] + w * (double)idx;
       bhi[r] = D->lo[r] + w * (double)(idx + 1u);
@@ -1543,10 +1535,9 @@ __global__ void k_control(Engine E, cudaGraphConditionalHandle handle, int use_g
   for (int q = threadIdx.x; q <= E.np; q += blockDim.x) E.k3_pre[q] = E.k3_pre_next[q];
   if (threadIdx.x == 0) {
     pl->k3_tiles = pl->k3_tiles_next;
-    // the refresh of this iteration consumed the list of the previous step,
-    // which the next step's subdivision fills again
-    pl->marks_total += min(pl->mark_count[(pl->steps_global + 1) & 1], E.mark_cap);
-    pl->mark_count[(pl->steps_global + 1) & 1] = 0u;
+    // the refresh of this iteration consumed this step's list
+    pl->marks_total += min(pl->mark_count[pl->steps_global & 1], E.mark_cap);
+    pl->mark_count[pl->steps_global & 1] = 0u;
     pl->steps_global += 1;
     const int running = pl->any_running;
     const SolveParams* P = E.params;
@@ -1565,6 +1556,12 @@ __global__ void k_control(Engine E, cudaGraphConditionalHandle handle, int use_g
         S->t_end = globaltimer();
       }
     }
+  }
+  // boxes of the children of the coming step, for k_refresh
+  for (int q = threadIdx.x; q < E.np; q += blockDim.x) {
+    ProbState* S = E.state + q;
+    for (int r = 0; r < PCBA_MAXD; ++r) S->child_level[r] = S->level[r] + (r == S->r ? 1 : 0);
+    S->child_twoK = 2 * S->K;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1589,7 +1586,13 @@ __global__ void k_init(Engine E) {
       S->r = 0;
       S->n = 1;
       S->steps = 0;
-      for (int q = 0; q < PCBA_MAXD; ++q) { S->level[q] = 0; S->best_index[q] = 0; S->best_level[q] = 0; }
+      for (int q = 0; q < PCBA_MAXD; ++q) {
+        S->level[q] = 0;
+        S->best_index[q] = 0;
+        S->best_level[q] = 0;
+        S->child_level[q] = q == 0 ? 1 : 0;
+      }
+      S->child_twoK = 2;
       S->best_slot = PCBA_NONE;
       S->k3_arrive = 0;
       S->have_box = 0;
@@ -1644,29 +1647,6 @@ __global__ void k_init(Engine E) {
   }
 }
 
-// FP64 value of a dense monomial tensor at x (powers in spw[r * 17 + j]) and
-// a bound on its rounding error: gamma_(C + d + l + 2) * sum |a_J x^J|.
-__device__ __forceinline__ void eval_mono(const double* a, int l, const int* deg, int C,
-                                          const double* spw, double* val, double* err) {
-  double s = 0.0, sa = 0.0;
-  int dsum = 0;
-  for (int r = 0; r < l; ++r) dsum += deg[r];
-  for (int idx = 0; idx < C; ++idx) {
-    int rem = idx;
-    double prod = a[idx];
-    for (int r = l - 1; r >= 0; --r) {
-      const int d1 = deg[r] + 1;
-      const int j = rem % d1;
-      rem /= d1;
-      prod *= spw[r * 17 + j];
-    }
-    s += prod;
-    sa += fabs(prod);
-  }
-  *val = s;
-  *err = __dmul_ru(__dmul_ru(2.0 * (double)(C + dsum + l + 2), 0x1p-53), sa);
-}
-
 // mode 0: warm start.  Candidate points of problem p (E.n_warm of them, at
 // most PCBA_MAX_CAND; FP32 coordinates) are ranked by an FP32 upper bound on
 // their cost, then checked in that order, PCBA_EVAL_CHUNK at a time: every
@@ -1692,17 +1672,6 @@ __global__ void k_mono32(const double* mono, float* out, long long n) {
 
 #define PCBA_EVAL_CHUNK 8
 #define PCBA_MAX_CAND 1024
-
-// value and error bound of a monomial tensor at x, powers built per thread
-__device__ __forceinline__ void eval_mono_at(const double* a, int l, const int* deg, int C,
-                                             const double* x, double* val, double* err) {
-  double pw[PCBA_MAXD * 17];
-  for (int r = 0; r < l; ++r) {
-    double v = 1.0;
-    for (int j = 0; j <= deg[r]; ++j) { pw[r * 17 + j] = v; v *= x[r]; }
-  }
-  eval_mono(a, l, deg, C, pw, val, err);
-}
 
 // Nested Horner evaluation in FP32 of a dense monomial tensor (coefficients
 // a = the FP64 ones rounded to nearest FP32, row-major, last axis fastest) at
@@ -1784,6 +1753,77 @@ __device__ __forceinline__ void horner_f32(const float* a, int l, const int* deg
   }
 }
 
+// The same nested Horner scheme in FP64 on the FP64 coefficients at an FP64
+// point: |v - p(x)| <= 2 (2 dsum + l + 2) 2^-53 S + (C + dsum) 2^-1074 M.
+template <int L>
+struct HornerF64 {
+  __device__ __forceinline__ static void eval(const double* a, const int* deg, const int* stride,
+                                              const double* x, const double* ax, double& v,
+                                              double& s) {
+    v = 0.0;
+    s = 0.0;
+    for (int i = deg[0]; i >= 0; --i) {
+      double vi, si;
+      HornerF64<L - 1>::eval(a + i * stride[0], deg + 1, stride + 1, x + 1, ax + 1, vi, si);
+      v = fma(v, x[0], vi);
+      s = __fma_ru(s, ax[0], si);
+    }
+  }
+};
+template <>
+struct HornerF64<1> {
+  __device__ __forceinline__ static void eval(const double* a, const int* deg, const int*,
+                                              const double* x, const double* ax, double& v,
+                                              double& s) {
+    v = 0.0;
+    s = 0.0;
+    for (int i = deg[0]; i >= 0; --i) {
+      const double ai = __ldg(a + i);
+      v = fma(v, x[0], ai);
+      s = __fma_ru(s, ax[0], fabs(ai));
+    }
+  }
+};
+
+template <int L>
+__device__ __forceinline__ void horner_f64_l(const double* a, const int* deg, const double* xin,
+                                             double* val, double* err) {
+  int d[L], st[L];
+  double x[L], ax[L];
+  int C = 1, dsum = 0;
+  double M = 1.0;
+#pragma unroll
+  for (int r = L - 1; r >= 0; --r) {
+    d[r] = deg[r];
+    st[r] = C;
+    C *= d[r] + 1;
+    dsum += d[r];
+    x[r] = xin[r];
+    ax[r] = fabs(x[r]);
+    const double m = fmax(1.0, ax[r]);
+    for (int k = 0; k < d[r]; ++k) M = __dmul_ru(M, m);
+  }
+  double v, S;
+  HornerF64<L>::eval(a, d, st, x, ax, v, S);
+  *val = v;
+  const double rel = __dmul_ru((double)(2 * (2 * dsum + L + 2)), 0x1p-53);
+  *err = __dadd_ru(__dmul_ru(rel, S), __dmul_ru(__dmul_ru((double)(C + dsum), 0x1p-1074), M));
+}
+
+__device__ __forceinline__ void horner_f64(const double* a, int l, const int* deg, const double* x,
+                                           double* val, double* err) {
+  switch (l) {
+    case 1: horner_f64_l<1>(a, deg, x, val, err); break;
+    case 2: horner_f64_l<2>(a, deg, x, val, err); break;
+    case 3: horner_f64_l<3>(a, deg, x, val, err); break;
+    case 4: horner_f64_l<4>(a, deg, x, val, err); break;
+    case 5: horner_f64_l<5>(a, deg, x, val, err); break;
+    case 6: horner_f64_l<6>(a, deg, x, val, err); break;
+    case 7: horner_f64_l<7>(a, deg, x, val, err); break;
+    default: horner_f64_l<8>(a, deg, x, val, err); break;
+  }
+}
+
 // candidate c of problem p: mode 0 a warm-start row (NaN first coordinate:
 // none), mode 1 the point the solve returns; false if there is none
 __device__ __forceinline__ bool eval_candidate(const Engine& E, int mode, int p, int c, double* x) {
@@ -1817,7 +1857,6 @@ __device__ __forceinline__ bool eval_candidate(const Engine& E, int mode, int p,
 __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* results) {
   __shared__ double s_key[PCBA_MAX_CAND];
   __shared__ int s_id[PCBA_MAX_CAND];
-  __shared__ double spw[PCBA_EVAL_CHUNK][PCBA_MAXD * 17];
   __shared__ double sx[PCBA_EVAL_CHUNK][PCBA_MAXD];
   __shared__ float sxf[PCBA_EVAL_CHUNK][PCBA_MAXD];
   __shared__ unsigned long long s_max[2];
@@ -1839,11 +1878,6 @@ __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* res
       s_has[0] = eval_candidate(E, 1, p, 0, sx[0]) ? 1 : 0;
       s_max[0] = 0ull;
       s_max[1] = 0ull;
-      if (s_has[0])
-        for (int q = 0; q < l; ++q) {
-          double pw = 1.0;
-          for (int j = 0; j < 17; ++j) { spw[0][q * 17 + j] = pw; pw *= sx[0][q]; }
-        }
     }
     __syncthreads();
     EvalOut* o = (EvalOut*)results + p;
@@ -1859,13 +1893,13 @@ __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* res
                              : base + D->cp + (long long)D->alpha * D->cg +
                                    (long long)(q - D->alpha) * D->ch;
       double val, err;
-      eval_mono(a, l, is_g ? D->G : D->H, is_g ? D->cg : D->ch, spw[0], &val, &err);
+      horner_f64(a, l, is_g ? D->G : D->H, sx[0], &val, &err);
       atomicMax(&s_max[is_g ? 0 : 1], okey(__dadd_ru(is_g ? val : fabs(val), err)));
     }
     __syncthreads();
     if (threadIdx.x == 0) {
       double pc, pe;
-      eval_mono(base, l, D->P, D->cp, spw[0], &pc, &pe);
+      horner_f64(base, l, D->P, sx[0], &pc, &pe);
       o->cost = pc;
       o->cost_err = pe;
       o->max_g = okey_dec_max(s_max[0]);
@@ -1974,7 +2008,7 @@ __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* res
     double offer = INFINITY;
     if (chosen >= 0) {
       double pc, pe;
-      eval_mono_at(base, l, D->P, D->cp, sx[chosen], &pc, &pe);
+      horner_f64(base, l, D->P, sx[chosen], &pc, &pe);
       offer = __dadd_ru(pc, pe);
       if (!(offer < INFINITY)) chosen = -1;
     }
@@ -2012,7 +2046,7 @@ __global__ void __launch_bounds__(PCBA_TPB) k_cost_grid(Engine E, int G, float* 
     x[0] = D->lo[0] + (D->hi[0] - D->lo[0]) * (double)i / (double)(G - 1);
     if (l >= 2) x[1] = D->lo[1] + (D->hi[1] - D->lo[1]) * (double)j / (double)(G - 1);
     double c, e;
-    eval_mono_at(base, l, D->P, D->cp, x, &c, &e);
+    horner_f64(base, l, D->P, x, &c, &e);
     s_c[node] = c;
     mn = fmin(mn, c);
   }
