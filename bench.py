@@ -92,7 +92,7 @@ def profiled_traffic():
     """DRAM bytes per subdivision launch from the committed ncu summary, or None
     when the kernel code changed since that capture."""
     import re
-    src = os.path.join(ROOT, "paper_2003_01758_b300", "csrc", "pcba_kernels.cuh")
+    src = os.path.join(ROOT, "paper_2003_01758_b300", "csrc", "pcba_subdivide.cuh")
     prof = os.path.join(ROOT, "profiles", "k2_subdivide_rtd512_fp32.md")
     try:
         text = open(prof).read()

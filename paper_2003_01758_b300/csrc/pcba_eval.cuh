@@ -1,0 +1,445 @@
+// Point evaluation kernels of libpcba (sm_103a): the warm start (candidate
+// points certified feasible in FP32 seed the incumbent p_up of Def. 4), the
+// final FP64 check of the returned point (Alg. 1 line 12), and the helpers of
+// the learned warm start (candidate stencil, FP32 monomials, cost grid).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include "pcba_device.cuh"
+
+// mode 0: warm start.  Candidate points of problem p (E.n_warm of them, at
+// most PCBA_MAX_CAND; FP32 coordinates) are ranked by an FP32 upper bound on
+// their cost, then checked in that order, PCBA_EVAL_CHUNK at a time: every
+// constraint in FP32 with a rigorous error bound (g_i + err <= 0,
+// |h_j| + err <= eq_tol).  The first certified-feasible candidate in rank
+// order (ties: lower index) is chosen and its cost bound recomputed in FP64
+// (cost + err) becomes the carried p_up.  A candidate is dropped at its first
+// violated bound, and the constraints that dropped earlier candidates (a
+// small ring of "killers") are tried first: neighbouring candidates tend to
+// fail on the same constraint.
+// mode 1: final check of the returned point in FP64, written to results.
+struct EvalOut {
+  double cost, cost_err, max_g, max_abs_h;
+  int ok;
+};
+
+// FP32 copy (round to nearest) of every monomial coefficient
+__global__ void k_mono32(const double* mono, float* out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = __double2float_rn(mono[i]);
+}
+
+#define PCBA_EVAL_CHUNK 8
+#define PCBA_MAX_CAND 1024
+
+// Nested Horner evaluation in FP32 of a dense monomial tensor (coefficients
+// a = the FP64 ones rounded to nearest FP32, row-major, last axis fastest) at
+// an FP32 point x, together with S >= sum |a_J| |x^J| (the same recursion on
+// absolute values, rounded up).  Horner with a fused multiply-add perturbs
+// each term by at most gamma_(2 dsum) relative over the nested levels
+// (Higham, Accuracy and Stability of Numerical Algorithms, Sec. 5.1), and the
+// coefficient rounding adds one more unit roundoff.
+template <int L>
+struct HornerF32 {
+  __device__ __forceinline__ static void eval(const float* a, const int* deg, const int* stride,
+                                              const float* x, const float* ax, float& v,
+                                              float& s) {
+    v = 0.0f;
+    s = 0.0f;
+    for (int i = deg[0]; i >= 0; --i) {
+      float vi, si;
+      HornerF32<L - 1>::eval(a + i * stride[0], deg + 1, stride + 1, x + 1, ax + 1, vi, si);
+      v = fmaf(v, x[0], vi);
+      s = __fmaf_ru(s, ax[0], si);
+    }
+  }
+};
+template <>
+struct HornerF32<1> {
+  __device__ __forceinline__ static void eval(const float* a, const int* deg, const int*,
+                                              const float* x, const float* ax, float& v,
+                                              float& s) {
+    v = 0.0f;
+    s = 0.0f;
+    for (int i = deg[0]; i >= 0; --i) {
+      const float af = __ldg(a + i);
+      v = fmaf(v, x[0], af);
+      s = __fmaf_ru(s, ax[0], fabsf(af));
+    }
+  }
+};
+
+// Value and rigorous error bound: |v - p(x)| <= err, where p has the FP64
+// coefficients.  err = 2 (2 dsum + l + 4) 2^-24 S, which is at least twice the
+// relative bound above, plus (C + dsum) 2^-149 M with M = prod max(1, |x_r|)^N_r
+// for the absolute errors of subnormal intermediate results.
+template <int L>
+__device__ __forceinline__ void horner_f32_l(const float* a, const int* deg, const float* xin,
+                                             float* val, float* err) {
+  int d[L], st[L];
+  float x[L], ax[L];
+  int C = 1, dsum = 0;
+  float M = 1.0f;
+#pragma unroll
+  for (int r = L - 1; r >= 0; --r) {
+    d[r] = deg[r];
+    st[r] = C;
+    C *= d[r] + 1;
+    dsum += d[r];
+    x[r] = xin[r];
+    ax[r] = fabsf(x[r]);
+    const float m = fmaxf(1.0f, ax[r]);
+    for (int k = 0; k < d[r]; ++k) M = __fmul_ru(M, m);
+  }
+  float v, S;
+  HornerF32<L>::eval(a, d, st, x, ax, v, S);
+  *val = v;
+  const float rel = __fmul_ru((float)(2 * (2 * dsum + L + 4)), 0x1p-24f);
+  *err = __fadd_ru(__fmul_ru(rel, S), __fmul_ru(__fmul_ru((float)(C + dsum), 0x1p-149f), M));
+}
+
+__device__ __forceinline__ void horner_f32(const float* a, int l, const int* deg, const float* x,
+                                           float* val, float* err) {
+  switch (l) {
+    case 1: horner_f32_l<1>(a, deg, x, val, err); break;
+    case 2: horner_f32_l<2>(a, deg, x, val, err); break;
+    case 3: horner_f32_l<3>(a, deg, x, val, err); break;
+    case 4: horner_f32_l<4>(a, deg, x, val, err); break;
+    case 5: horner_f32_l<5>(a, deg, x, val, err); break;
+    case 6: horner_f32_l<6>(a, deg, x, val, err); break;
+    case 7: horner_f32_l<7>(a, deg, x, val, err); break;
+    default: horner_f32_l<8>(a, deg, x, val, err); break;
+  }
+}
+
+// The same nested Horner scheme in FP64 on the FP64 coefficients at an FP64
+// point: |v - p(x)| <= 2 (2 dsum + l + 2) 2^-53 S + (C + dsum) 2^-1074 M.
+template <int L>
+struct HornerF64 {
+  __device__ __forceinline__ static void eval(const double* a, const int* deg, const int* stride,
+                                              const double* x, const double* ax, double& v,
+                                              double& s) {
+    v = 0.0;
+    s = 0.0;
+    for (int i = deg[0]; i >= 0; --i) {
+      double vi, si;
+      HornerF64<L - 1>::eval(a + i * stride[0], deg + 1, stride + 1, x + 1, ax + 1, vi, si);
+      v = fma(v, x[0], vi);
+      s = __fma_ru(s, ax[0], si);
+    }
+  }
+};
+template <>
+struct HornerF64<1> {
+  __device__ __forceinline__ static void eval(const double* a, const int* deg, const int*,
+                                              const double* x, const double* ax, double& v,
+                                              double& s) {
+    v = 0.0;
+    s = 0.0;
+    for (int i = deg[0]; i >= 0; --i) {
+      const double ai = __ldg(a + i);
+      v = fma(v, x[0], ai);
+      s = __fma_ru(s, ax[0], fabs(ai));
+    }
+  }
+};
+
+template <int L>
+__device__ __forceinline__ void horner_f64_l(const double* a, const int* deg, const double* xin,
+                                             double* val, double* err) {
+  int d[L], st[L];
+  double x[L], ax[L];
+  int C = 1, dsum = 0;
+  double M = 1.0;
+#pragma unroll
+  for (int r = L - 1; r >= 0; --r) {
+    d[r] = deg[r];
+    st[r] = C;
+    C *= d[r] + 1;
+    dsum += d[r];
+    x[r] = xin[r];
+    ax[r] = fabs(x[r]);
+    const double m = fmax(1.0, ax[r]);
+    for (int k = 0; k < d[r]; ++k) M = __dmul_ru(M, m);
+  }
+  double v, S;
+  HornerF64<L>::eval(a, d, st, x, ax, v, S);
+  *val = v;
+  const double rel = __dmul_ru((double)(2 * (2 * dsum + L + 2)), 0x1p-53);
+  *err = __dadd_ru(__dmul_ru(rel, S), __dmul_ru(__dmul_ru((double)(C + dsum), 0x1p-1074), M));
+}
+
+__device__ __forceinline__ void horner_f64(const double* a, int l, const int* deg, const double* x,
+                                           double* val, double* err) {
+  switch (l) {
+    case 1: horner_f64_l<1>(a, deg, x, val, err); break;
+    case 2: horner_f64_l<2>(a, deg, x, val, err); break;
+    case 3: horner_f64_l<3>(a, deg, x, val, err); break;
+    case 4: horner_f64_l<4>(a, deg, x, val, err); break;
+    case 5: horner_f64_l<5>(a, deg, x, val, err); break;
+    case 6: horner_f64_l<6>(a, deg, x, val, err); break;
+    case 7: horner_f64_l<7>(a, deg, x, val, err); break;
+    default: horner_f64_l<8>(a, deg, x, val, err); break;
+  }
+}
+
+// candidate c of problem p: mode 0 a warm-start row (NaN first coordinate:
+// none), mode 1 the point the solve returns; false if there is none
+__device__ __forceinline__ bool eval_candidate(const Engine& E, int mode, int p, int c, double* x) {
+  const ProbDesc* D = E.desc + p;
+  const ProbState* S = E.state + p;
+  const int l = D->l;
+  if (mode == 0) {
+    const double* w = E.warm + ((long long)p * E.n_warm + c) * PCBA_MAXD;
+    if (isnan(w[0])) return false;
+    for (int q = 0; q < l; ++q) x[q] = (double)__double2float_rn(w[q]);  // FP32 coordinates
+    return true;
+  }
+  if (S->have_box) {
+    for (int q = 0; q < l; ++q) {
+      const double w = ldexp(D->hi[q] - D->lo[q], -S->best_level[q]);
+      const double blo = D->lo[q] + w * (double)S->best_index[q];
+      const double bhi = D->lo[q] + w * (double)(S->best_index[q] + 1u);
+      x[q] = 0.5 * (blo + bhi);
+    }
+    return true;
+  }
+  if (S->from_warm) {
+    for (int q = 0; q < l; ++q) x[q] = S->warm_x[q];
+    return true;
+  }
+  return false;
+}
+
+#define PCBA_KILLERS 32
+
+__global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* results) {
+  __shared__ double s_key[PCBA_MAX_CAND];
+  __shared__ int s_id[PCBA_MAX_CAND];
+  __shared__ double sx[PCBA_EVAL_CHUNK][PCBA_MAXD];
+  __shared__ float sxf[PCBA_EVAL_CHUNK][PCBA_MAXD];
+  __shared__ unsigned long long s_max[2];
+  __shared__ int s_has[PCBA_EVAL_CHUNK];
+  __shared__ int s_viol[PCBA_EVAL_CHUNK];
+  __shared__ int s_kill[PCBA_KILLERS];
+  __shared__ unsigned s_nkill;
+  __shared__ int s_done;
+  const int p = blockIdx.x;
+  const ProbDesc* D = E.desc + p;
+  ProbState* S = E.state + p;
+  const int l = D->l;
+  const double* base = E.mono + D->mono_off;
+  const int total = D->alpha + D->beta;
+
+  if (mode == 1) {
+    // final check of one point, FP64
+    if (threadIdx.x == 0) {
+      s_has[0] = eval_candidate(E, 1, p, 0, sx[0]) ? 1 : 0;
+      s_max[0] = 0ull;
+      s_max[1] = 0ull;
+    }
+    __syncthreads();
+    EvalOut* o = (EvalOut*)results + p;
+    if (!s_has[0]) {
+      if (threadIdx.x == 0) {
+        o->cost = NAN; o->cost_err = NAN; o->max_g = NAN; o->max_abs_h = NAN; o->ok = 0;
+      }
+      return;
+    }
+    for (int q = threadIdx.x; q < total; q += PCBA_TPB) {
+      const bool is_g = q < D->alpha;
+      const double* a = is_g ? base + D->cp + (long long)q * D->cg
+                             : base + D->cp + (long long)D->alpha * D->cg +
+                                   (long long)(q - D->alpha) * D->ch;
+      double val, err;
+      horner_f64(a, l, is_g ? D->G : D->H, sx[0], &val, &err);
+      atomicMax(&s_max[is_g ? 0 : 1], okey(__dadd_ru(is_g ? val : fabs(val), err)));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double pc, pe;
+      horner_f64(base, l, D->P, sx[0], &pc, &pe);
+      o->cost = pc;
+      o->cost_err = pe;
+      o->max_g = okey_dec_max(s_max[0]);
+      o->max_abs_h = okey_dec_max(s_max[1]);
+      o->ok = 1;
+    }
+    return;
+  }
+
+  // ---- mode 0: rank the candidates by an FP32 bound on their cost
+  const int n_c = E.warm ? min(E.n_warm, PCBA_MAX_CAND) : 0;
+  const float* mono32 = E.mono32 + D->mono_off;
+  int n2 = 1;
+  while (n2 < n_c) n2 <<= 1;
+  for (int c = threadIdx.x; c < n2; c += PCBA_TPB) {
+    double key = INFINITY;
+    double x[PCBA_MAXD];
+    if (c < n_c && eval_candidate(E, 0, p, c, x)) {
+      float xf[PCBA_MAXD];
+      for (int q = 0; q < l; ++q) xf[q] = (float)x[q];
+      float v, e;
+      horner_f32(mono32, l, D->P, xf, &v, &e);
+      const float k = __fadd_ru(v, e);
+      if (!isnan(k)) key = (double)k;
+    }
+    s_key[c] = key;
+    s_id[c] = c < n_c ? c : 0x7fffffff;
+  }
+  if (threadIdx.x == 0) {
+    s_nkill = 0u;
+    s_done = 0;
+  }
+  __syncthreads();
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += PCBA_TPB) {
+        const int o = i ^ j;
+        if (o > i) {
+          const bool gt = s_key[i] > s_key[o] || (s_key[i] == s_key[o] && s_id[i] > s_id[o]);
+          if (gt == ((i & k) == 0)) {
+            const double tk = s_key[i]; s_key[i] = s_key[o]; s_key[o] = tk;
+            const int ti = s_id[i]; s_id[i] = s_id[o]; s_id[o] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+
+  // ---- check them in rank order
+  const float eq_tol = (float)E.params->eq_tol;
+  int chosen = -1;  // thread 0: chunk slot of the chosen candidate
+  for (int c0 = 0; c0 < n_c; c0 += PCBA_EVAL_CHUNK) {
+    const int nc = min(PCBA_EVAL_CHUNK, n_c - c0);
+    if (threadIdx.x < PCBA_EVAL_CHUNK) {
+      const int c = threadIdx.x;
+      int has = 0;
+      if (c < nc && s_key[c0 + c] < INFINITY)
+        has = eval_candidate(E, 0, p, s_id[c0 + c], sx[c]) ? 1 : 0;
+      s_has[c] = has;
+      s_viol[c] = 0;
+      if (has)
+        for (int q = 0; q < l; ++q) sxf[c][q] = (float)sx[c][q];
+    }
+    __syncthreads();
+    const int nk = (int)min(s_nkill, (unsigned)PCBA_KILLERS);
+    if (nk > 0) {
+      for (int it = threadIdx.x; it < nc * nk; it += PCBA_TPB) {
+        const int c = it / nk;
+        const int q = s_kill[it - c * nk];
+        if (!s_has[c] || s_viol[c]) continue;
+        const bool is_g = q < D->alpha;
+        const float* a = is_g ? mono32 + D->cp + (long long)q * D->cg
+                              : mono32 + D->cp + (long long)D->alpha * D->cg +
+                                    (long long)(q - D->alpha) * D->ch;
+        float val, err;
+        horner_f32(a, l, is_g ? D->G : D->H, sxf[c], &val, &err);
+        if (!(__fadd_ru(is_g ? val : fabsf(val), err) <= (is_g ? 0.0f : eq_tol))) s_viol[c] = 1;
+      }
+      __syncthreads();
+    }
+    for (int it = threadIdx.x; it < nc * total; it += PCBA_TPB) {
+      const int c = it / total;
+      const int q = it - c * total;
+      if (!s_has[c] || s_viol[c]) continue;
+      const bool is_g = q < D->alpha;
+      const float* a = is_g ? mono32 + D->cp + (long long)q * D->cg
+                            : mono32 + D->cp + (long long)D->alpha * D->cg +
+                                  (long long)(q - D->alpha) * D->ch;
+      float val, err;
+      horner_f32(a, l, is_g ? D->G : D->H, sxf[c], &val, &err);
+      if (!(__fadd_ru(is_g ? val : fabsf(val), err) <= (is_g ? 0.0f : eq_tol))) {
+        s_viol[c] = 1;
+        s_kill[atomicAdd(&s_nkill, 1u) % PCBA_KILLERS] = q;
+      }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int c = 0; c < nc; ++c)
+        if (s_has[c] && !s_viol[c]) { chosen = c; break; }
+      s_done = chosen >= 0 || (c0 + nc < n_c && !(s_key[c0 + nc] < INFINITY));
+    }
+    __syncthreads();
+    if (s_done) break;
+  }
+  if (threadIdx.x == 0) {
+    double offer = INFINITY;
+    if (chosen >= 0) {
+      double pc, pe;
+      horner_f64(base, l, D->P, sx[chosen], &pc, &pe);
+      offer = __dadd_ru(pc, pe);
+      if (!(offer < INFINITY)) chosen = -1;
+    }
+    const int found = chosen >= 0;
+    S->from_warm = found;
+    S->p_up_carry = found ? offer : INFINITY;
+    S->seeded = found;
+    S->seed_cost = found ? offer : INFINITY;
+    for (int q = 0; q < PCBA_MAXD; ++q) {
+      const double v = (found && q < l) ? sx[chosen][q] : NAN;
+      if (found && q < l) S->warm_x[q] = v;
+      S->seed_x[q] = v;
+    }
+  }
+}
+
+// Cost of problem p on a G x G grid over its first two axes (G nodes when
+// l = 1; other axes at the box centre), node (i, j) at
+// x_0 = lo_0 + i (hi_0 - lo_0) / (G - 1), x_1 likewise with j; written as
+// log(c - min over the grid + 1e-3) to out[p * ld + col0 + i * G + j] (floats).
+__global__ void __launch_bounds__(PCBA_TPB) k_cost_grid(Engine E, int G, float* out, int ld,
+                                                        int col0) {
+  __shared__ double s_c[PCBA_MAX_CAND];
+  __shared__ double red[PCBA_TPB / 32];
+  const int p = blockIdx.x;
+  const ProbDesc* D = E.desc + p;
+  const int l = D->l;
+  const int nodes = l >= 2 ? G * G : G;
+  const double* base = E.mono + D->mono_off;
+  double mn = INFINITY;
+  for (int node = threadIdx.x; node < nodes; node += PCBA_TPB) {
+    const int i = l >= 2 ? node / G : node, j = l >= 2 ? node - i * G : 0;
+    double x[PCBA_MAXD];
+    for (int q = 0; q < l; ++q) x[q] = 0.5 * (D->lo[q] + D->hi[q]);
+    x[0] = D->lo[0] + (D->hi[0] - D->lo[0]) * (double)i / (double)(G - 1);
+    if (l >= 2) x[1] = D->lo[1] + (D->hi[1] - D->lo[1]) * (double)j / (double)(G - 1);
+    double c, e;
+    horner_f64(base, l, D->P, x, &c, &e);
+    s_c[node] = c;
+    mn = fmin(mn, c);
+  }
+  for (int o = 16; o > 0; o >>= 1) mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mn;
+  __syncthreads();
+  mn = red[0];
+  for (int w = 1; w < PCBA_TPB / 32; ++w) mn = fmin(mn, red[w]);
+  for (int node = threadIdx.x; node < nodes; node += PCBA_TPB)
+    out[(long long)p * ld + col0 + node] = (float)log(s_c[node] - mn + 1e-3);
+}
+
+// Candidate points of guided solves: candidate c of problem p is the guess of
+// p (normalised coordinates, guess_dim axes) plus stencil row c, clamped to
+// [-1, 1] and mapped to the box; axes beyond guess_dim take the box centre.
+__global__ void k_candidates(Engine E, const float* guess, int guess_dim, const double* stencil,
+                             int n_stencil, double* cand) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)E.np * n_stencil) return;
+  const int p = (int)(t / n_stencil), c = (int)(t - (long long)p * n_stencil);
+  const ProbDesc* D = E.desc + p;
+  double* o = cand + t * PCBA_MAXD;
+  for (int r = 0; r < PCBA_MAXD; ++r) {
+    double x = 0.0;
+    if (r < D->l) {
+      double u = 0.0;
+      if (r < guess_dim)
+        u = (double)guess[(long long)p * guess_dim + r] + stencil[(long long)c * guess_dim + r];
+      u = fmin(fmax(u, -1.0), 1.0);
+      x = D->lo[r] + 0.5 * (u + 1.0) * (D->hi[r] - D->lo[r]);
+    }
+    o[r] = x;
+  }
+}
