@@ -119,7 +119,7 @@ struct pcba_batch {
   unsigned* d_pre = nullptr;  // 5 arrays of np+1
   char* d_arena = nullptr;
   ChildRec* d_rec = nullptr;
-  unsigned* d_slots = nullptr;  // flagrank | hole | filler
+  unsigned* d_slots = nullptr;  // flagrank | hole | filler | map | fstack
   unsigned* d_tilecnt = nullptr;
   double* d_mono = nullptr;
   float* d_mono32 = nullptr;
@@ -633,7 +633,7 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
     d.item_bytes = round_up(off, 256);
     d.payload_bytes = 4LL * P.l + (P.cp + P.alpha * P.cg + P.beta * P.ch) * w +
                       (prec == PCBA_FP32 ? 12LL + 4LL * (P.alpha + P.beta) : 0);
-    d.move_chunks = (int)std::max<long long>(1, (d.item_bytes + 16383) / 16384);
+    d.move_chunks = 1;  // Eliminate moves one map entry per hole
     d.mono_off = mono;
     mono += (long long)P.mono.size();
     d.trace_rows = PCBA_TRACE_PER_DIM * P.l;
@@ -678,7 +678,7 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   PCBA_ALLOC(b->d_pre, sizeof(unsigned) * 6 * (n + 1));
   PCBA_ALLOC(b->d_arena, arena_bytes);
   PCBA_ALLOC(b->d_rec, sizeof(ChildRec) * nslots);
-  PCBA_ALLOC(b->d_slots, sizeof(unsigned) * 3 * nslots);
+  PCBA_ALLOC(b->d_slots, sizeof(unsigned) * 5 * nslots);
   PCBA_ALLOC(b->d_tilecnt, sizeof(unsigned) * tiles_per * n);
   PCBA_ALLOC(b->d_mono, sizeof(double) * mono);
   PCBA_ALLOC(b->d_mono32, sizeof(float) * mono);
@@ -730,7 +730,7 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
                                   cudaMemcpyHostToDevice), "k1 prefix")))
     return rc;
   if ((rc = cleanup_ck(cudaMemset(b->d_rec, 0, sizeof(ChildRec) * nslots), "rec clear"))) return rc;
-  if ((rc = cleanup_ck(cudaMemset(b->d_slots, 0, sizeof(unsigned) * 3 * nslots), "slot clear")))
+  if ((rc = cleanup_ck(cudaMemset(b->d_slots, 0, sizeof(unsigned) * 5 * nslots), "slot clear")))
     return rc;
   if ((rc = cleanup_ck(cudaMemset(b->d_state, 0, sizeof(ProbState) * n), "state clear"))) return rc;
   if ((rc = cleanup_ck(cudaEventCreate(&b->ev0), "event"))) return rc;
@@ -761,6 +761,8 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   E.flagrank = b->d_slots;
   E.hole = b->d_slots + nslots;
   E.filler = b->d_slots + 2 * nslots;
+  E.map = b->d_slots + 3 * nslots;
+  E.fstack = b->d_slots + 4 * nslots;
   E.tilecnt = b->d_tilecnt;
   E.mono = b->d_mono;
   E.mono32 = b->d_mono32;
@@ -1283,7 +1285,14 @@ int pcba_get_list(pcba_handle* h, long long* K_out, double* cost, double* ineq, 
     for (int q = 0; q < d.l; ++q) level[q] = S.level[q];
   if (!cost && !ineq && !eq && !err && !index) return 0;
   std::vector<char> buf((size_t)(K * d.item_bytes));
-  PCBA_CK(cudaMemcpy(buf.data(), b->d_arena + d.list_off, buf.size(), cudaMemcpyDeviceToHost));
+  std::vector<unsigned> slot((size_t)std::max<long long>(K, 1));
+  const long long nslots_total = (long long)b->np * std::max<long long>(b->M, 2);
+  PCBA_CK(cudaMemcpy(slot.data(), b->d_slots + 3 * nslots_total + d.slot_off,
+                     sizeof(unsigned) * (size_t)K, cudaMemcpyDeviceToHost));
+  for (long long k = 0; k < K; ++k)
+    PCBA_CK(cudaMemcpy(buf.data() + k * d.item_bytes,
+                       b->d_arena + d.list_off + (size_t)slot[(size_t)k] * d.item_bytes,
+                       (size_t)d.item_bytes, cudaMemcpyDeviceToHost));
   const bool f32 = b->precision == PCBA_FP32;
   const int nerr = 1 + d.alpha + d.beta;
   for (long long k = 0; k < K; ++k) {

@@ -15,6 +15,14 @@
 // Constraint-minor storage makes every load and store of the subdivision
 // kernel unit-stride across the threads of a warp for every bisection
 // direction: thread i owns patch i and walks its fibres.
+//
+// The list order of the paper (children of parent k at positions k and k+K,
+// Alg. 2; holes filled from the top, Alg. 5) is kept as a map from logical
+// position to physical item slot.  A left child stays in its parent's slot, a
+// right child takes a free slot (popped from a per-problem stack, or a slot
+// never used before), and Eliminate moves map entries instead of items; the
+// slots of eliminated children are pushed back.  At most 2K slots are in use
+// during a step, so the memory test 2K <= M is unchanged.
 #pragma once
 
 #include <cstdint>
@@ -86,6 +94,9 @@ struct ProbState {
   long long peak_items;
   unsigned long long t_end;
   int done_flag;
+  int ftop;                     // free-slot stack height before the coming step's pops
+  int hw;                       // physical slots >= hw have never been used
+  int ftop_push;                // stack height after this step's pops (base of its pushes)
   int child_level[PCBA_MAXD];   // levels of the children of the coming step (set between steps)
   int child_twoK;               // children of the coming step
   int seeded;                   // a warm-start candidate was certified feasible
@@ -133,6 +144,8 @@ struct Engine {
   unsigned mark_cap;
   char* arena;
   ChildRec* rec;           // per slot
+  unsigned* map;           // per slot: logical list position -> physical item slot
+  unsigned* fstack;        // per slot: stack of free physical item slots
   unsigned* flagrank;      // per slot: keep << 31 | rank within its tile
   unsigned* hole;          // per slot
   unsigned* filler;        // per slot

@@ -358,7 +358,7 @@ __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
     const ProbState* S = E.state + p;
     const int slot = (int)m.y;
     if (slot >= S->child_twoK) continue;
-    char* item = E.arena + D->list_off + (size_t)slot * D->item_bytes;
+    char* item = E.arena + D->list_off + (size_t)E.map[D->slot_off + slot] * D->item_bytes;
     double blo[PCBA_MAXD], bhi[PCBA_MAXD];
     for (int r = 0; r < D->l; ++r) {
       const double w = ldexp(D->hi[r] - D->lo[r], -S->child_level[r]);
@@ -481,7 +481,8 @@ __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
   const double p_up = fmin(p_up_step, carry);
   const unsigned bs = S->best_slot;
   if (bs != PCBA_NONE) {
-    const unsigned* idx = (const unsigned*)(E.arena + D->list_off + (size_t)bs * D->item_bytes);
+    const unsigned* idx = (const unsigned*)(E.arena + D->list_off +
+                                            (size_t)__ldcg(E.map + D->slot_off + bs) * D->item_bytes);
     for (int q = 0; q < l; ++q) {
       S->best_index[q] = __ldcg(idx + q);
       S->best_level[q] = S->level[q];
@@ -502,6 +503,15 @@ __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
   }
   S->steps += 1;
   if ((long long)twoK > S->peak_items) S->peak_items = twoK;
+  // free slots: this step popped K = twoK / 2 (stack first, then fresh slots);
+  // k4_index pushes the slots of the twoK - K_save eliminated children
+  {
+    const int Kpar = twoK / 2, ftop0 = S->ftop;
+    const int ftop1 = ftop0 > Kpar ? ftop0 - Kpar : 0;
+    S->hw += Kpar > ftop0 ? Kpar - ftop0 : 0;
+    S->ftop_push = ftop1;
+    S->ftop = ftop1 + (twoK - K_save);
+  }
   S->twoK = twoK;
   S->K_save = K_save;
   int status = PCBA_RUNNING;
@@ -658,7 +668,10 @@ __global__ void __launch_bounds__(PCBA_TPB) k4_index(Engine E) {
   for (unsigned u = blockIdx.x; u < tiles_total; u += gridDim.x) {
     const int p = find_problem(E.k3_pre, E.np, u);
     const ProbState* S = E.state + p;
-    if (S->F == 0) continue;
+    // a problem that stops at this step (MEMCAP, MAXITER) is still compacted
+    // (its list is returned); only running problems recycle slots
+    const bool running = S->status == PCBA_RUNNING;
+    if (!running && S->F == 0) continue;
     const ProbDesc* D = E.desc + p;
     const int tile = (int)(u - E.k3_pre[p]);
     const int twoK = S->twoK, K_save = S->K_save;
@@ -669,27 +682,25 @@ __global__ void __launch_bounds__(PCBA_TPB) k4_index(Engine E) {
     const int grank = (int)(E.tilecnt[D->tile_off + tile] + (fr & 0x7FFFFFFFu));
     if (c < K_save && !keep) E.hole[D->slot_off + (c - grank)] = (unsigned)c;
     if (c >= K_save && keep) E.filler[D->slot_off + (K_save - 1 - grank)] = (unsigned)c;
+    // the slot of an eliminated child goes back on the free stack (grank =
+    // kept children before c, so c - grank eliminated ones precede it)
+    if (running && !keep)
+      E.fstack[D->slot_off + S->ftop_push + (c - grank)] = E.map[D->slot_off + c];
   }
 }
 
+// Alg. 5 on the map: the j-th hole below K_save takes the slot of the item at
+// save position K_save-1-j (reading R11); one thread per hole.
 __global__ void __launch_bounds__(PCBA_TPB) k4_move(Engine E) {
   const unsigned units = E.plan->k4_units;
-  for (unsigned u = blockIdx.x; u < units; u += gridDim.x) {
+  for (unsigned u = blockIdx.x * blockDim.x + threadIdx.x; u < units;
+       u += gridDim.x * blockDim.x) {
     const int p = find_problem(E.k4_pre, E.np, u);
     const ProbDesc* D = E.desc + p;
-    const unsigned local = u - E.k4_pre[p];
-    const int chunks = D->move_chunks;
-    const unsigned j = local / (unsigned)chunks;
-    const int ch = (int)(local - j * (unsigned)chunks);
-    const unsigned dst_slot = E.hole[D->slot_off + j];
-    const unsigned src_slot = E.filler[D->slot_off + j];
-    const long long n16 = D->item_bytes / 16;
-    const long long per = (n16 + chunks - 1) / chunks;
-    const long long b0 = (long long)ch * per;
-    const long long b1 = b0 + per < n16 ? b0 + per : n16;
-    const int4* s = (const int4*)(E.arena + D->list_off + (size_t)src_slot * D->item_bytes);
-    int4* d = (int4*)(E.arena + D->list_off + (size_t)dst_slot * D->item_bytes);
-    for (long long q = b0 + threadIdx.x; q < b1; q += PCBA_TPB) d[q] = __ldcs(s + q);
+    const unsigned j = u - E.k4_pre[p];
+    const unsigned h = E.hole[D->slot_off + j];
+    const unsigned f = E.filler[D->slot_off + j];
+    E.map[D->slot_off + h] = E.map[D->slot_off + f];
   }
 }
 
@@ -763,6 +774,10 @@ __global__ void k_init(Engine E) {
         S->child_level[q] = q == 0 ? 1 : 0;
       }
       S->child_twoK = 2;
+      S->ftop = 0;
+      S->ftop_push = 0;
+      S->hw = 1;
+      E.map[D->slot_off] = 0u;
       S->best_slot = PCBA_NONE;
       S->k3_arrive = 0;
       S->have_box = 0;

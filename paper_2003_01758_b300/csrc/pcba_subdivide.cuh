@@ -425,11 +425,18 @@ __device__ __forceinline__ ChildRec load_rec_cg(const ChildRec* p) {
 // Each block takes one contiguous range of units, so consecutive units mostly
 // belong to one problem; the problem's descriptor and step state are copied to
 // shared memory once per problem.
+// Physical slot of the right child of logical parent k: the k-th free slot
+// popped from the stack (top first), then slots never used before.
+__device__ __forceinline__ unsigned right_slot(const Engine& E, long long slot_off, int k,
+                                               int ftop, int hw) {
+  return k < ftop ? E.fstack[slot_off + ftop - 1 - k] : (unsigned)(hw + (k - ftop));
+}
+
 template <typename T, int NMAX>
 __global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
   extern __shared__ __align__(16) unsigned char k2stage[];
   __shared__ __align__(16) ProbDesc sD;
-  __shared__ int sK, sR;
+  __shared__ int sK, sR, sFtop, sHw;
   const unsigned units = E.plan->k2_units;
   const float eqt = __double2float_ru(E.params->eq_tol);
   const double cost_thr = E.params->opt_tol * (1.0 / 64.0);
@@ -453,6 +460,8 @@ __global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
       if (threadIdx.x == 0) {
         sK = E.state[p].K;
         sR = E.state[p].r;
+        sFtop = E.state[p].ftop;
+        sHw = E.state[p].hw;
       }
       __syncthreads();
     }
@@ -461,8 +470,10 @@ __global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
     const unsigned local = u - pbeg;
     const int k = (int)(local / (unsigned)tiles);
     const int t = (int)(local - (unsigned)k * tiles);
-    char* parent = E.arena + D->list_off + (size_t)k * D->item_bytes;
-    char* right = E.arena + D->list_off + (size_t)(k + K) * D->item_bytes;
+    const unsigned pslot = E.map[D->slot_off + k];
+    const unsigned rslot = right_slot(E, D->slot_off, k, sFtop, sHw);
+    char* parent = E.arena + D->list_off + (size_t)pslot * D->item_bytes;
+    char* right = E.arena + D->list_off + (size_t)rslot * D->item_bytes;
     ChildRec* recL = E.rec + D->slot_off + k;
     ChildRec* recR = E.rec + D->slot_off + k + K;
     const MarkCtx mk{p, k, k + K, E.marks + (size_t)mpar * E.mark_cap, &E.plan->mark_count[mpar],
@@ -470,6 +481,7 @@ __global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
     if (t == 0 && warp == 0) {
       cost_part<T, NMAX>(D, parent, parent, right, r, recL, recR, (T*)k2stage, mk, cost_thr);
       if (lane == 0) {
+        E.map[D->slot_off + k + K] = rslot;
         unsigned* iL = (unsigned*)parent;
         unsigned* iR = (unsigned*)right;
         for (int s = 0; s < D->l; ++s) iR[s] = iL[s];
@@ -595,7 +607,8 @@ __device__ __forceinline__ void issue_unit(const Engine& E, const WarpUnit& w, T
                                            float* estage, unsigned char* head,
                                            unsigned long long* bar) {
   const ProbDesc* D = E.desc + w.p;
-  const char* item = E.arena + D->list_off + (size_t)w.k * D->item_bytes;
+  const unsigned pslot = E.map[D->slot_off + w.k];
+  const char* item = E.arena + D->list_off + (size_t)pslot * D->item_bytes;
   const unsigned hb = w.g == 0 ? head_bytes(D, (unsigned)sizeof(T)) : 0u;
   if (w.fam < 0) {
     mbar_arrive_expect_tx(bar, hb);
@@ -608,51 +621,82 @@ __device__ __forceinline__ void issue_unit(const Engine& E, const WarpUnit& w, T
   mbar_arrive_expect_tx(bar, bytes);
   if (hb) bulk_load(head, item, hb, bar);
   const char* tm = (const char*)E.tmaps + ((size_t)w.p * 2 + w.fam) * 128;
-  tma_load_3d(stage, tm, w.x, 0, w.k, bar);
+  tma_load_3d(stage, tm, w.x, 0, (int)pslot, bar);
   if (sizeof(T) == 4)
     bulk_load(estage, item + (w.fam ? D->off_eh : D->off_eg) + (size_t)w.x * 4, 128u, bar);
 }
 
 // Fibres of one column (lane) of a staged [C][32] block: loads from shared
 // memory, children stored straight to global memory (coalesced across lanes).
+//
+// The triangle keeps its sums unhalved: level k holds 2^k times the de
+// Casteljau values, and each child coefficient is scaled by 2^-k only when it
+// is stored.  Scaling by a power of two commutes with round-to-nearest outside
+// the subnormal and overflow ranges, so every stored value equals the halved
+// triangle's bit for bit there; in the subnormal range the unhalved sums lose
+// nothing (the FP32 bound's 2^-149 term per level covers the final scaling).
+// Two fibres are processed together for instruction-level parallelism.
+template <typename T, int N, bool RIG, int NF>
+__device__ __forceinline__ void staged_fibre_group(const T* sl, T* gL, T* gR, size_t pad,
+                                                   size_t st, int blk, int stride, int f,
+                                                   FibAcc<T>& a) {
+  int c0[NF];
+  T q[NF][N + 1];
+#pragma unroll
+  for (int h = 0; h < NF; ++h) {
+    const int ff = f + h;
+    const int o = ff / stride;
+    c0[h] = o * blk + (ff - o * stride);
+    const T* sc = sl + c0[h] * 32;
+#pragma unroll
+    for (int j = 0; j <= N; ++j) q[h][j] = sc[j * stride * 32];
+  }
+#pragma unroll
+  for (int h = 0; h < NF; ++h) {
+    if constexpr (RIG) {
+#pragma unroll
+      for (int j = 0; j <= N; ++j) a.m = fmax(a.m, fabs(q[h][j]));
+    }
+    // left_0 = f_0 already sits in the parent slot the left child overwrites
+    gR[(size_t)c0[h] * pad + N * st] = q[h][N];
+    a.minL = fmin(a.minL, q[h][0]);
+    a.maxL = fmax(a.maxL, q[h][0]);
+    a.minR = fmin(a.minR, q[h][N]);
+    a.maxR = fmax(a.maxR, q[h][N]);
+  }
+  T scale = T(1);
+#pragma unroll
+  for (int k = 1; k <= N; ++k) {
+    scale = scale * T(0.5);
+#pragma unroll
+    for (int j = 0; j <= N - k; ++j)
+#pragma unroll
+      for (int h = 0; h < NF; ++h) q[h][j] = addrn(q[h][j], q[h][j + 1]);
+#pragma unroll
+    for (int h = 0; h < NF; ++h) {
+      const T l = mulrn(q[h][0], scale);
+      const T r = mulrn(q[h][N - k], scale);
+      gL[(size_t)c0[h] * pad + k * st] = l;
+      gR[(size_t)c0[h] * pad + (N - k) * st] = r;
+      a.minL = fmin(a.minL, l);
+      a.maxL = fmax(a.maxL, l);
+      a.minR = fmin(a.minR, r);
+      a.maxR = fmax(a.maxR, r);
+    }
+  }
+}
+
 template <typename T, int N, bool RIG>
 __device__ __forceinline__ void staged_fibres(const T* stage, T* gL, T* gR, size_t pad, int C,
                                               int stride, int lane, FibAcc<T>& a) {
   const int nf = C / (N + 1);
   const int blk = (N + 1) * stride;
   const size_t st = (size_t)stride * pad;
+  const T* sl = stage + lane;
+  int f = 0;
 #pragma unroll 1
-  for (int f = 0; f < nf; ++f) {
-    const int o = f / stride;
-    const int c0 = o * blk + (f - o * stride);
-    const T* sc = stage + c0 * 32 + lane;
-    T* colL = gL + (size_t)c0 * pad;
-    T* colR = gR + (size_t)c0 * pad;
-    T q[N + 1];
-#pragma unroll
-    for (int j = 0; j <= N; ++j) q[j] = sc[j * stride * 32];
-    if constexpr (RIG) {
-#pragma unroll
-      for (int j = 0; j <= N; ++j) a.m = fmax(a.m, fabs(q[j]));
-    }
-    // left_0 = f_0 already sits in the parent slot the left child overwrites
-    colR[N * st] = q[N];
-    a.minL = fmin(a.minL, q[0]);
-    a.maxL = fmax(a.maxL, q[0]);
-    a.minR = fmin(a.minR, q[N]);
-    a.maxR = fmax(a.maxR, q[N]);
-#pragma unroll
-    for (int k = 1; k <= N; ++k) {
-#pragma unroll
-      for (int j = 0; j <= N - k; ++j) q[j] = mulrn(addrn(q[j], q[j + 1]), T(0.5));
-      colL[k * st] = q[0];
-      colR[(N - k) * st] = q[N - k];
-      a.minL = fmin(a.minL, q[0]);
-      a.maxL = fmax(a.maxL, q[0]);
-      a.minR = fmin(a.minR, q[N - k]);
-      a.maxR = fmax(a.maxR, q[N - k]);
-    }
-  }
+  for (; f + 1 < nf; f += 2) staged_fibre_group<T, N, RIG, 2>(sl, gL, gR, pad, st, blk, stride, f, a);
+  if (f < nf) staged_fibre_group<T, N, RIG, 1>(sl, gL, gR, pad, st, blk, stride, f, a);
 }
 
 // The bound reductions of one warp's 32 patches, published with atomics
@@ -740,6 +784,15 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
                     st + (size_t)stage_elems * sizeof(T) + 128, &bars[j]);
     }
   }
+  // per-problem context, reloaded only when the unit's problem changes
+  int cx_p = -1, cx_K = 0, cx_r = 0, cx_ftop = 0, cx_hw = 0;
+  char* cx_list = nullptr;
+  long long cx_ib = 0, cx_slot = 0;
+  // family fields of the unit's family (units of one problem are ordered
+  // inequality groups first, then equality groups)
+  int cx_fam = -1, cx_cnt = 0, cx_C = 0, cx_n = 0, cx_stride = 1;
+  size_t cx_pad = 0;
+  long long cx_off = 0, cx_offe = 0;
   for (int j = 0; j < J; ++j) {
     const int s = j % stages;
     const unsigned parity = (unsigned)(j / stages) & 1u;
@@ -748,12 +801,37 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
     const float* estage = (const float*)(st + (size_t)stage_elems * sizeof(T));
     const WarpUnit w = resolve_unit(E, first + (unsigned)j * wpb, cp_, cbeg, cend);
     const ProbDesc* D = E.desc + w.p;
-    ProbState* S = E.state + w.p;
-    const int K = S->K, r = S->r;
-    char* parent = E.arena + D->list_off + (size_t)w.k * D->item_bytes;
-    char* right = E.arena + D->list_off + (size_t)(w.k + K) * D->item_bytes;
-    ChildRec* recL = E.rec + D->slot_off + w.k;
-    ChildRec* recR = E.rec + D->slot_off + w.k + K;
+    if (w.p != cx_p) {
+      const ProbState* S = E.state + w.p;
+      cx_p = w.p;
+      cx_K = S->K;
+      cx_r = S->r;
+      cx_ftop = S->ftop;
+      cx_hw = S->hw;
+      cx_list = E.arena + D->list_off;
+      cx_ib = D->item_bytes;
+      cx_slot = D->slot_off;
+      cx_fam = -1;
+    }
+    if (w.fam >= 0 && w.fam != cx_fam) {
+      const int fam = w.fam;
+      const int* deg = fam ? D->H : D->G;
+      cx_fam = fam;
+      cx_cnt = fam ? D->beta : D->alpha;
+      cx_C = fam ? D->ch : D->cg;
+      cx_pad = fam ? D->bpad : D->apad;
+      cx_off = fam ? D->off_h : D->off_g;
+      cx_offe = fam ? D->off_eh : D->off_eg;
+      cx_n = deg[cx_r];
+      cx_stride = axis_stride(deg, D->l, cx_r);
+    }
+    const int K = cx_K, r = cx_r;
+    const unsigned pslot = E.map[cx_slot + w.k];
+    const unsigned rslot = right_slot(E, cx_slot, w.k, cx_ftop, cx_hw);
+    char* parent = cx_list + (size_t)pslot * cx_ib;
+    char* right = cx_list + (size_t)rslot * cx_ib;
+    ChildRec* recL = E.rec + cx_slot + w.k;
+    ChildRec* recR = E.rec + cx_slot + w.k + K;
     const MarkCtx mk{w.p, w.k, w.k + K, E.marks + (size_t)mpar * E.mark_cap,
                      &E.plan->mark_count[mpar], E.mark_cap};
     bool ok = true;
@@ -773,6 +851,7 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
       cost_part<T, NMAX>(D, (const char*)head, parent, right, r, recL, recR, cost_stage, mk,
                          cost_thr);
       if (lane == 0) {
+        E.map[cx_slot + w.k + K] = rslot;
         const unsigned* iP = (const unsigned*)head;
         unsigned* iL = (unsigned*)parent;
         unsigned* iR = (unsigned*)right;
@@ -786,13 +865,12 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
     }
     if (w.fam >= 0) {
       const int fam = w.fam;
-      const int cnt = fam ? D->beta : D->alpha;
-      const size_t pad = fam ? D->bpad : D->apad;
-      const int* deg = fam ? D->H : D->G;
-      const int C = fam ? D->ch : D->cg;
-      const long long off = fam ? D->off_h : D->off_g;
-      const int n = deg[r];
-      const int stride = axis_stride(deg, D->l, r);
+      const int cnt = cx_cnt;
+      const size_t pad = cx_pad;
+      const int C = cx_C;
+      const long long off = cx_off;
+      const int n = cx_n;
+      const int stride = cx_stride;
       const int i = w.x + lane;
       T v[6] = {T(-INFINITY), T(-INFINITY), T(-INFINITY), T(-INFINITY), T(-INFINITY), T(-INFINITY)};
       bool mL = false, mR = false;
@@ -818,8 +896,8 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
           hiR = __fadd_ru((float)a.maxR, ec);
           const float eL = mark_err(ec, (float)a.minL, (float)a.maxL, loL, hiL, fam, eqt);
           const float eR = mark_err(ec, (float)a.minR, (float)a.maxR, loR, hiR, fam, eqt);
-          ((float*)(parent + (fam ? D->off_eh : D->off_eg)))[i] = eL;
-          ((float*)(right + (fam ? D->off_eh : D->off_eg)))[i] = eR;
+          ((float*)(parent + cx_offe))[i] = eL;
+          ((float*)(right + cx_offe))[i] = eR;
           mL = __float_as_uint(eL) >> 31;
           mR = __float_as_uint(eR) >> 31;
         } else {
