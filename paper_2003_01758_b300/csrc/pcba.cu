@@ -131,6 +131,10 @@ struct pcba_batch {
   double* d_raw = nullptr;
   EvalOut* d_eval = nullptr;
   double* d_cand = nullptr;     // guided solves: [np][cand_cap][PCBA_MAXD]
+  float* d_ckey = nullptr;      // warm starts: [np][ckey_cap] FP32 cost bounds of candidates
+  unsigned* d_cviol = nullptr;  // warm starts: [np][ckey_cap] violation flags
+  long long ckey_cap = 0;
+  int cand_cmax = 0, cand_tiles = 1;  // largest constraint patch, constraint tiles of 32
   double* d_stencil = nullptr;  // guided solves: [stencil_cap] doubles
   long long cand_cap = 0, stencil_cap = 0;
   long long trace_rows_total = 0;
@@ -290,7 +294,7 @@ void free_batch(pcba_batch* b) {
   void* dev[] = {b->d_desc, b->d_state, b->d_plan, b->d_params, b->d_pre, b->d_arena, b->d_rec,
                  b->d_slots, b->d_tilecnt, b->d_mono, b->d_trace, b->d_warm, b->d_mat,
                  b->d_raw, b->d_eval, b->d_tmaps, b->d_marks, b->d_cand, b->d_stencil,
-                 b->d_mono32};
+                 b->d_mono32, b->d_ckey, b->d_cviol};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {b->h_state, b->h_eval, b->h_plan, b->h_params, b->h_running};
@@ -402,7 +406,7 @@ int setup_kernels(pcba_batch* b) {
     }
     g.tma_stage_elems = (int)(cstage * 32);
     g.tma_cpmax = (int)cpmax;
-    const size_t head_cap = ((size_t)64 + (size_t)cpmax * sizeof(T) + 127) / 128 * 128;
+    const size_t head_cap = ((size_t)64 + (size_t)cpmax * sizeof(T) + 32 + 127) / 128 * 128;
     const size_t stage_bytes = (size_t)g.tma_stage_elems * sizeof(T) + 128 + head_cap;
     const int cand[][2] = {{8, 2}, {8, 3}, {4, 2}, {4, 3}, {2, 2}};
     const void* kt = g.nmax == 4 ? (const void*)k2_subdivide_tma<T, 4>
@@ -458,6 +462,8 @@ int setup_kernels(pcba_batch* b) {
     PCBA_CK(cudaMemcpyToSymbol(c_binom, binom, sizeof(binom)));
     PCBA_CK(cudaMemcpyToSymbol(c_binom_inv, binom_inv, sizeof(binom_inv)));
   }
+  PCBA_CK(cudaFuncSetAttribute(k_cand_feas, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               96 * 1024));
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_classify, PCBA_TPB, 0));
   g.k3_grid = std::max(1, occ) * g.sms;
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_move, PCBA_TPB, 0));
@@ -682,6 +688,13 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   PCBA_ALLOC(b->d_tilecnt, sizeof(unsigned) * tiles_per * n);
   PCBA_ALLOC(b->d_mono, sizeof(double) * mono);
   PCBA_ALLOC(b->d_mono32, sizeof(float) * mono);
+  PCBA_ALLOC(b->d_ckey, sizeof(float) * n);
+  PCBA_ALLOC(b->d_cviol, sizeof(unsigned) * n);
+  b->ckey_cap = 1;
+  for (const ProbDesc& d : b->desc) {
+    b->cand_cmax = std::max(b->cand_cmax, std::max(d.alpha ? d.cg : 0, d.beta ? d.ch : 0));
+    b->cand_tiles = std::max(b->cand_tiles, (d.alpha + d.beta + 31) / 32);
+  }
   PCBA_ALLOC(b->d_trace, sizeof(double) * 4 * trace_rows);
   PCBA_ALLOC(b->d_warm, sizeof(double) * PCBA_MAXD * n);
   PCBA_ALLOC(b->d_mat, sizeof(double) * 3 * PCBA_MAXD * 578 * n);
@@ -838,7 +851,22 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   k1_matrices<<<(nmat + 255) / 256, 256, 0, s>>>(E1, b->d_mat);
   k1_convert<T><<<b->g.k1_grid, 32 * b->g.k1_wpb, b->g.k1_smem, s>>>(E1, b->d_mat, b->g.k1_cmax,
                                                                    b->g.k1_wpb);
-  k_eval<<<n, PCBA_TPB, 0, s>>>(E1, 0, nullptr);
+  const size_t cand_smem =
+      sizeof(float) * ((size_t)32 * b->cand_cmax + (size_t)E1.n_warm * b->max_l);
+  const bool cand_fast = (guide || warm) && b->cand_cmax <= 512 && cand_smem <= 96 * 1024 &&
+                         b->ckey_cap >= E1.n_warm;
+  if (cand_fast) {
+    const long long nc = (long long)n * E1.n_warm;
+    PCBA_CK(cudaMemsetAsync(b->d_cviol, 0, sizeof(unsigned) * (size_t)nc, s));
+    k_cand_cost<<<(unsigned)std::min<long long>((nc + 255) / 256, 8LL * b->g.sms), 256, 0, s>>>(
+        E1, b->d_ckey);
+    k_cand_feas<<<dim3((unsigned)b->cand_tiles, (unsigned)n), 256, cand_smem, s>>>(
+        E1, b->d_ckey, b->d_cviol, b->cand_cmax);
+    k_cand_pick<<<n, PCBA_TPB, 0, s>>>(E1, b->d_ckey, b->d_cviol);
+    b->extra_launches += 2;
+  } else {
+    k_eval<<<n, PCBA_TPB, 0, s>>>(E1, 0, nullptr);
+  }
   k_init<<<1, PCBA_TPB, 0, s>>>(E1);
   PCBA_CK(cudaGetLastError());
   b->subdiv_ms = 0;
@@ -1130,6 +1158,18 @@ int pcba_batch_solve_guided(pcba_batch* b, double opt_tol, double eq_tol, int ma
         cudaSuccess)
       return fail(PCBA_ERR_OOM, "stencil buffer allocation failed");
     b->stencil_cap = (long long)n_stencil * guess_dim;
+  }
+  if (b->ckey_cap < n_stencil) {
+    if (b->d_ckey) cudaFree(b->d_ckey);
+    if (b->d_cviol) cudaFree(b->d_cviol);
+    b->d_ckey = nullptr;
+    b->d_cviol = nullptr;
+    b->ckey_cap = 0;
+    if (cudaMalloc((void**)&b->d_ckey, sizeof(float) * (size_t)b->np * n_stencil) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_cviol, sizeof(unsigned) * (size_t)b->np * n_stencil) !=
+            cudaSuccess)
+      return fail(PCBA_ERR_OOM, "candidate key allocation failed");
+    b->ckey_cap = n_stencil;
   }
   const Guide g{d_guess, guess_dim, stencil, n_stencil};
   return batch_solve_impl(b, nullptr, opt_tol, eq_tol, max_iters, 0, nullptr, out, false, &g);

@@ -65,7 +65,7 @@ struct HornerF32<1> {
     v = 0.0f;
     s = 0.0f;
     for (int i = deg[0]; i >= 0; --i) {
-      const float af = __ldg(a + i);
+      const float af = a[i];
       v = fmaf(v, x[0], af);
       s = __fmaf_ru(s, ax[0], fabsf(af));
     }
@@ -384,6 +384,129 @@ __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* res
       if (found && q < l) S->warm_x[q] = v;
       S->seed_x[q] = v;
     }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Warm start over many candidates, spread over the whole GPU: the same choice
+// as k_eval mode 0 (the certified-feasible candidate with the lowest FP32
+// cost bound, ties to the lower index, its FP64 cost bound as p_up), computed
+// as (1) every candidate's FP32 cost bound, (2) every (candidate, constraint)
+// pair in FP32 with its error bound, one block per (problem, 32 constraints)
+// with the coefficients in shared memory, and (3) a per-problem argmin.
+// ---------------------------------------------------------------------------
+__global__ void k_cand_cost(Engine E, float* key) {
+  const long long total = (long long)E.np * E.n_warm;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int p = (int)(t / E.n_warm), c = (int)(t - (long long)p * E.n_warm);
+    const ProbDesc* D = E.desc + p;
+    double x[PCBA_MAXD];
+    float k = INFINITY;
+    if (eval_candidate(E, 0, p, c, x)) {
+      float xf[PCBA_MAXD];
+      for (int q = 0; q < D->l; ++q) xf[q] = (float)x[q];
+      float v, e;
+      horner_f32(E.mono32 + D->mono_off, D->l, D->P, xf, &v, &e);
+      const float kk = __fadd_ru(v, e);
+      if (!isnan(kk)) k = kk;
+    }
+    key[t] = k;
+  }
+}
+
+// grid (constraint tiles, problems); dynamic shared memory: 32 * cmax floats
+// of coefficients, then n_warm * l floats of candidate coordinates
+__global__ void __launch_bounds__(256) k_cand_feas(Engine E, const float* key, unsigned* viol,
+                                                   int cmax) {
+  extern __shared__ float kcs[];
+  const int p = blockIdx.y;
+  const ProbDesc* D = E.desc + p;
+  const int total = D->alpha + D->beta;
+  const int q0 = blockIdx.x * 32;
+  if (q0 >= total) return;
+  const int nq = min(32, total - q0);
+  const int l = D->l;
+  const int n_c = E.n_warm;
+  float* sa = kcs;
+  float* sx = kcs + 32 * cmax;
+  const float* mono32 = E.mono32 + D->mono_off;
+  for (int t = threadIdx.x; t < nq * cmax; t += blockDim.x) {
+    const int qi = t / cmax, j = t - qi * cmax;
+    const int q = q0 + qi;
+    const bool is_g = q < D->alpha;
+    const int C = is_g ? D->cg : D->ch;
+    if (j < C) {
+      const float* a = is_g ? mono32 + D->cp + (long long)q * D->cg
+                            : mono32 + D->cp + (long long)D->alpha * D->cg +
+                                  (long long)(q - D->alpha) * D->ch;
+      sa[qi * cmax + j] = a[j];
+    }
+  }
+  for (int t = threadIdx.x; t < n_c * l; t += blockDim.x) {
+    const int c = t / l, r = t - c * l;
+    sx[t] = (float)E.warm[((long long)p * n_c + c) * PCBA_MAXD + r];
+  }
+  __syncthreads();
+  const float eq_tol = (float)E.params->eq_tol;
+  for (int t = threadIdx.x; t < n_c * nq; t += blockDim.x) {
+    const int c = t / nq, qi = t - c * nq;
+    if (!(key[(long long)p * n_c + c] < INFINITY)) continue;
+    const int q = q0 + qi;
+    const bool is_g = q < D->alpha;
+    float val, err;
+    horner_f32(sa + qi * cmax, l, is_g ? D->G : D->H, sx + c * l, &val, &err);
+    if (!(__fadd_ru(is_g ? val : fabsf(val), err) <= (is_g ? 0.0f : eq_tol)))
+      viol[(long long)p * n_c + c] = 1u;
+  }
+}
+
+__global__ void __launch_bounds__(PCBA_TPB) k_cand_pick(Engine E, const float* key,
+                                                        const unsigned* viol) {
+  __shared__ float s_k[PCBA_TPB / 32];
+  __shared__ int s_i[PCBA_TPB / 32];
+  const int p = blockIdx.x;
+  const ProbDesc* D = E.desc + p;
+  ProbState* S = E.state + p;
+  const int n_c = E.n_warm;
+  float bk = INFINITY;
+  int bi = 0x7fffffff;
+  for (int c = threadIdx.x; c < n_c; c += PCBA_TPB) {
+    const long long t = (long long)p * n_c + c;
+    const float k = key[t];
+    if (k < INFINITY && viol[t] == 0u && (k < bk || (k == bk && c < bi))) {
+      bk = k;
+      bi = c;
+    }
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    const float ok = __shfl_xor_sync(0xffffffffu, bk, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ok < bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
+  }
+  if ((threadIdx.x & 31) == 0) { s_k[threadIdx.x >> 5] = bk; s_i[threadIdx.x >> 5] = bi; }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < PCBA_TPB / 32; ++w)
+    if (s_k[w] < bk || (s_k[w] == bk && s_i[w] < bi)) { bk = s_k[w]; bi = s_i[w]; }
+  const int l = D->l;
+  double x[PCBA_MAXD];
+  double offer = INFINITY;
+  int found = 0;
+  if (bk < INFINITY && eval_candidate(E, 0, p, bi, x)) {
+    double pc, pe;
+    horner_f64(E.mono + D->mono_off, l, D->P, x, &pc, &pe);
+    offer = __dadd_ru(pc, pe);
+    found = offer < INFINITY;
+  }
+  S->from_warm = found;
+  S->p_up_carry = found ? offer : INFINITY;
+  S->seeded = found;
+  S->seed_cost = found ? offer : INFINITY;
+  for (int q = 0; q < PCBA_MAXD; ++q) {
+    const double v = (found && q < l) ? x[q] : NAN;
+    if (found && q < l) S->warm_x[q] = v;
+    S->seed_x[q] = v;
   }
 }
 

@@ -564,34 +564,58 @@ __device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, unsig
   }
 }
 
-// Resolves a warp work unit u = (problem p, parent item k, column group g).
+// A warp work unit u = (problem p, parent item k, column group g), resolved by
+// the lane that issues its copies and kept in the stage's header, together
+// with the physical slots of the parent and of the right child, so that the
+// warp that computes it reads everything from shared memory.
 struct WarpUnit {
   int p, k, g, fam, x;
+  unsigned pslot, rslot;
+  int pad;
 };
-__device__ __forceinline__ WarpUnit resolve_unit(const Engine& E, unsigned u, int& p,
-                                                 unsigned& pbeg, unsigned& pend) {
-  if (u >= pend || u < pbeg) {
-    p = find_problem(E.k2_pre, E.np, u);
-    pbeg = E.k2_pre[p];
-    pend = E.k2_pre[p + 1];
+
+// Per-problem values the issuing lane needs, reloaded when the problem changes.
+struct IssueCtx {
+  int p;
+  unsigned beg, end;
+  int tiles, groups_g, groups_h, K, ftop, hw;
+  long long slot_off;
+};
+
+__device__ __forceinline__ WarpUnit resolve_unit(const Engine& E, unsigned u, IssueCtx& c) {
+  if (u >= c.end || u < c.beg) {
+    const int p = find_problem(E.k2_pre, E.np, u);
+    const ProbDesc* D = E.desc + p;
+    const ProbState* S = E.state + p;
+    c.p = p;
+    c.beg = E.k2_pre[p];
+    c.end = E.k2_pre[p + 1];
+    c.tiles = D->tiles;
+    c.groups_g = D->groups_g;
+    c.groups_h = D->groups_h;
+    c.slot_off = D->slot_off;
+    c.K = S->K;
+    c.ftop = S->ftop;
+    c.hw = S->hw;
   }
-  const ProbDesc* D = E.desc + p;
-  const int groups = D->tiles;
-  const unsigned local = u - pbeg;
+  const unsigned local = u - c.beg;
   WarpUnit w;
-  w.p = p;
-  w.k = (int)(local / (unsigned)groups);
-  w.g = (int)(local - (unsigned)w.k * groups);
-  if (w.g < D->groups_g) {
+  w.p = c.p;
+  w.k = (int)(local / (unsigned)c.tiles);
+  w.g = (int)(local - (unsigned)w.k * c.tiles);
+  if (w.g < c.groups_g) {
     w.fam = 0;
     w.x = w.g * 32;
-  } else if (w.g < D->groups_g + D->groups_h) {
+  } else if (w.g < c.groups_g + c.groups_h) {
     w.fam = 1;
-    w.x = (w.g - D->groups_g) * 32;
+    w.x = (w.g - c.groups_g) * 32;
   } else {
     w.fam = -1;  // cost-only unit of a problem without constraints
     w.x = 0;
   }
+  w.pslot = E.map[c.slot_off + w.k];
+  w.rslot = right_slot(E, c.slot_off, w.k, c.ftop, c.hw);
+  w.pad = 0;
   return w;
 }
 
@@ -607,8 +631,7 @@ __device__ __forceinline__ void issue_unit(const Engine& E, const WarpUnit& w, T
                                            float* estage, unsigned char* head,
                                            unsigned long long* bar) {
   const ProbDesc* D = E.desc + w.p;
-  const unsigned pslot = E.map[D->slot_off + w.k];
-  const char* item = E.arena + D->list_off + (size_t)pslot * D->item_bytes;
+  const char* item = E.arena + D->list_off + (size_t)w.pslot * D->item_bytes;
   const unsigned hb = w.g == 0 ? head_bytes(D, (unsigned)sizeof(T)) : 0u;
   if (w.fam < 0) {
     mbar_arrive_expect_tx(bar, hb);
@@ -621,7 +644,7 @@ __device__ __forceinline__ void issue_unit(const Engine& E, const WarpUnit& w, T
   mbar_arrive_expect_tx(bar, bytes);
   if (hb) bulk_load(head, item, hb, bar);
   const char* tm = (const char*)E.tmaps + ((size_t)w.p * 2 + w.fam) * 128;
-  tma_load_3d(stage, tm, w.x, 0, (int)pslot, bar);
+  tma_load_3d(stage, tm, w.x, 0, (int)w.pslot, bar);
   if (sizeof(T) == 4)
     bulk_load(estage, item + (w.fam ? D->off_eh : D->off_eg) + (size_t)w.x * 4, 128u, bar);
 }
@@ -749,8 +772,9 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
   extern __shared__ __align__(128) unsigned char k2t_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   // per warp: stages x (stage_elems T + 32 floats + head), then 2*cpmax T of cost
-  // staging; head = box, cost meta and cost patch of the parent (group 0)
-  const size_t head_cap = ((size_t)64 + (size_t)cpmax * sizeof(T) + 127) / 128 * 128;
+  // staging; head = box, cost meta and cost patch of the parent (group 0),
+  // with the unit's WarpUnit header in its last 32 bytes
+  const size_t head_cap = ((size_t)64 + (size_t)cpmax * sizeof(T) + 32 + 127) / 128 * 128;
   const size_t stage_bytes = (size_t)stage_elems * sizeof(T) + 128 + head_cap;
   const size_t warp_bytes = (size_t)stages * stage_bytes + (size_t)2 * cpmax * sizeof(T);
   const size_t warp_bytes_al = (warp_bytes + 127) / 128 * 128;
@@ -773,19 +797,22 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
   const unsigned u1 = min(units, u0 + per);
   const unsigned first = u0 + warp;
   const int J = first < u1 ? (int)((u1 - first + wpb - 1) / wpb) : 0;
-  int ip = -1, cp_ = -1;
-  unsigned ibeg = 0, iend = 0, cbeg = 0, cend = 0;
+  IssueCtx ic;
+  ic.beg = 1u;
+  ic.end = 0u;
   // prologue
   for (int j = 0; j < J && j < stages; ++j) {
     if (lane == 0) {
-      const WarpUnit w = resolve_unit(E, first + (unsigned)j * wpb, ip, ibeg, iend);
+      const WarpUnit w = resolve_unit(E, first + (unsigned)j * wpb, ic);
       unsigned char* st = wb + (size_t)j * stage_bytes;
-      issue_unit<T>(E, w, (T*)st, (float*)(st + (size_t)stage_elems * sizeof(T)),
-                    st + (size_t)stage_elems * sizeof(T) + 128, &bars[j]);
+      unsigned char* head = st + (size_t)stage_elems * sizeof(T) + 128;
+      *(WarpUnit*)(head + head_cap - 32) = w;
+      issue_unit<T>(E, w, (T*)st, (float*)(st + (size_t)stage_elems * sizeof(T)), head, &bars[j]);
     }
   }
+  __syncwarp();
   // per-problem context, reloaded only when the unit's problem changes
-  int cx_p = -1, cx_K = 0, cx_r = 0, cx_ftop = 0, cx_hw = 0;
+  int cx_p = -1, cx_K = 0, cx_r = 0;
   char* cx_list = nullptr;
   long long cx_ib = 0, cx_slot = 0;
   // family fields of the unit's family (units of one problem are ordered
@@ -799,15 +826,13 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
     unsigned char* st = wb + (size_t)s * stage_bytes;
     const T* stage = (const T*)st;
     const float* estage = (const float*)(st + (size_t)stage_elems * sizeof(T));
-    const WarpUnit w = resolve_unit(E, first + (unsigned)j * wpb, cp_, cbeg, cend);
+    const WarpUnit w = *(const WarpUnit*)(st + (size_t)stage_elems * sizeof(T) + 128 + head_cap - 32);
     const ProbDesc* D = E.desc + w.p;
     if (w.p != cx_p) {
       const ProbState* S = E.state + w.p;
       cx_p = w.p;
       cx_K = S->K;
       cx_r = S->r;
-      cx_ftop = S->ftop;
-      cx_hw = S->hw;
       cx_list = E.arena + D->list_off;
       cx_ib = D->item_bytes;
       cx_slot = D->slot_off;
@@ -826,9 +851,8 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
       cx_stride = axis_stride(deg, D->l, cx_r);
     }
     const int K = cx_K, r = cx_r;
-    const unsigned pslot = E.map[cx_slot + w.k];
-    const unsigned rslot = right_slot(E, cx_slot, w.k, cx_ftop, cx_hw);
-    char* parent = cx_list + (size_t)pslot * cx_ib;
+    const unsigned rslot = w.rslot;
+    char* parent = cx_list + (size_t)w.pslot * cx_ib;
     char* right = cx_list + (size_t)rslot * cx_ib;
     ChildRec* recL = E.rec + cx_slot + w.k;
     ChildRec* recR = E.rec + cx_slot + w.k + K;
@@ -920,9 +944,10 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
     __syncwarp();
     fence_proxy_async_smem();
     if (lane == 0 && j + stages < J) {
-      const WarpUnit wn = resolve_unit(E, first + (unsigned)(j + stages) * wpb, ip, ibeg, iend);
-      issue_unit<T>(E, wn, (T*)st, (float*)(st + (size_t)stage_elems * sizeof(T)),
-                    st + (size_t)stage_elems * sizeof(T) + 128, &bars[s]);
+      const WarpUnit wn = resolve_unit(E, first + (unsigned)(j + stages) * wpb, ic);
+      unsigned char* head = st + (size_t)stage_elems * sizeof(T) + 128;
+      *(WarpUnit*)(head + head_cap - 32) = wn;
+      issue_unit<T>(E, wn, (T*)st, (float*)(st + (size_t)stage_elems * sizeof(T)), head, &bars[s]);
     }
     __syncwarp();
   }
