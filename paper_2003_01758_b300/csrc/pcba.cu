@@ -132,7 +132,9 @@ struct pcba_batch {
   EvalOut* d_eval = nullptr;
   double* d_cand = nullptr;     // guided solves: [np][cand_cap][PCBA_MAXD]
   float* d_ckey = nullptr;      // warm starts: [np][ckey_cap] FP32 cost bounds of candidates
-  unsigned* d_cviol = nullptr;  // warm starts: [np][ckey_cap] violation flags
+  unsigned* d_cviol = nullptr;  // warm starts: [np][ckey_cap] violation flags (by rank)
+  int* d_corder = nullptr;      // warm starts: [np][ckey_cap] candidates in rank order
+  int* d_cres = nullptr;        // warm starts: [np] resolved flags
   long long ckey_cap = 0;
   int cand_cmax = 0, cand_tiles = 1;  // largest constraint patch, constraint tiles of 32
   double* d_stencil = nullptr;  // guided solves: [stencil_cap] doubles
@@ -294,7 +296,7 @@ void free_batch(pcba_batch* b) {
   void* dev[] = {b->d_desc, b->d_state, b->d_plan, b->d_params, b->d_pre, b->d_arena, b->d_rec,
                  b->d_slots, b->d_tilecnt, b->d_mono, b->d_trace, b->d_warm, b->d_mat,
                  b->d_raw, b->d_eval, b->d_tmaps, b->d_marks, b->d_cand, b->d_stencil,
-                 b->d_mono32, b->d_ckey, b->d_cviol};
+                 b->d_mono32, b->d_ckey, b->d_cviol, b->d_corder, b->d_cres};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {b->h_state, b->h_eval, b->h_plan, b->h_params, b->h_running};
@@ -690,6 +692,8 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   PCBA_ALLOC(b->d_mono32, sizeof(float) * mono);
   PCBA_ALLOC(b->d_ckey, sizeof(float) * n);
   PCBA_ALLOC(b->d_cviol, sizeof(unsigned) * n);
+  PCBA_ALLOC(b->d_corder, sizeof(int) * n);
+  PCBA_ALLOC(b->d_cres, sizeof(int) * n);
   b->ckey_cap = 1;
   for (const ProbDesc& d : b->desc) {
     b->cand_cmax = std::max(b->cand_cmax, std::max(d.alpha ? d.cg : 0, d.beta ? d.ch : 0));
@@ -851,19 +855,30 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   k1_matrices<<<(nmat + 255) / 256, 256, 0, s>>>(E1, b->d_mat);
   k1_convert<T><<<b->g.k1_grid, 32 * b->g.k1_wpb, b->g.k1_smem, s>>>(E1, b->d_mat, b->g.k1_cmax,
                                                                    b->g.k1_wpb);
+  // ranks [0, head) are certified first; the rest only for problems that
+  // found no feasible candidate among them
+  const int head = std::min(E1.n_warm, 32);
   const size_t cand_smem =
-      sizeof(float) * ((size_t)32 * b->cand_cmax + (size_t)E1.n_warm * b->max_l);
+      sizeof(float) * ((size_t)32 * b->cand_cmax + (size_t)std::min(E1.n_warm, 1024) * b->max_l);
   const bool cand_fast = (guide || warm) && b->cand_cmax <= 512 && cand_smem <= 96 * 1024 &&
                          b->ckey_cap >= E1.n_warm;
   if (cand_fast) {
     const long long nc = (long long)n * E1.n_warm;
+    const dim3 fgrid((unsigned)b->cand_tiles, (unsigned)n);
     PCBA_CK(cudaMemsetAsync(b->d_cviol, 0, sizeof(unsigned) * (size_t)nc, s));
     k_cand_cost<<<(unsigned)std::min<long long>((nc + 255) / 256, 8LL * b->g.sms), 256, 0, s>>>(
         E1, b->d_ckey);
-    k_cand_feas<<<dim3((unsigned)b->cand_tiles, (unsigned)n), 256, cand_smem, s>>>(
-        E1, b->d_ckey, b->d_cviol, b->cand_cmax);
-    k_cand_pick<<<n, PCBA_TPB, 0, s>>>(E1, b->d_ckey, b->d_cviol);
-    b->extra_launches += 2;
+    k_cand_rank<<<n, PCBA_TPB, 0, s>>>(E1, b->d_ckey, b->d_corder, b->d_cres);
+    k_cand_feas<<<fgrid, 256, cand_smem, s>>>(E1, b->d_ckey, b->d_corder, b->d_cres, b->d_cviol,
+                                              b->cand_cmax, 0, head);
+    b->extra_launches += 3;
+    if (head < E1.n_warm) {
+      k_cand_check<<<n, 128, 0, s>>>(E1, b->d_ckey, b->d_corder, b->d_cviol, b->d_cres, head);
+      k_cand_feas<<<fgrid, 256, cand_smem, s>>>(E1, b->d_ckey, b->d_corder, b->d_cres,
+                                                b->d_cviol, b->cand_cmax, head, E1.n_warm);
+      b->extra_launches += 2;
+    }
+    k_cand_pick<<<n, PCBA_TPB, 0, s>>>(E1, b->d_ckey, b->d_corder, b->d_cviol);
   } else {
     k_eval<<<n, PCBA_TPB, 0, s>>>(E1, 0, nullptr);
   }
@@ -1162,12 +1177,15 @@ int pcba_batch_solve_guided(pcba_batch* b, double opt_tol, double eq_tol, int ma
   if (b->ckey_cap < n_stencil) {
     if (b->d_ckey) cudaFree(b->d_ckey);
     if (b->d_cviol) cudaFree(b->d_cviol);
+    if (b->d_corder) cudaFree(b->d_corder);
     b->d_ckey = nullptr;
     b->d_cviol = nullptr;
+    b->d_corder = nullptr;
     b->ckey_cap = 0;
     if (cudaMalloc((void**)&b->d_ckey, sizeof(float) * (size_t)b->np * n_stencil) != cudaSuccess ||
         cudaMalloc((void**)&b->d_cviol, sizeof(unsigned) * (size_t)b->np * n_stencil) !=
-            cudaSuccess)
+            cudaSuccess ||
+        cudaMalloc((void**)&b->d_corder, sizeof(int) * (size_t)b->np * n_stencil) != cudaSuccess)
       return fail(PCBA_ERR_OOM, "candidate key allocation failed");
     b->ckey_cap = n_stencil;
   }

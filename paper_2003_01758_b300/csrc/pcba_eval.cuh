@@ -415,21 +415,63 @@ __global__ void k_cand_cost(Engine E, float* key) {
   }
 }
 
-// grid (constraint tiles, problems); dynamic shared memory: 32 * cmax floats
-// of coefficients, then n_warm * l floats of candidate coordinates
-__global__ void __launch_bounds__(256) k_cand_feas(Engine E, const float* key, unsigned* viol,
-                                                   int cmax) {
+// Ranks the candidates of problem p by (FP32 cost bound, index): one block per
+// problem, bitonic sort in shared memory (at most PCBA_MAX_CAND candidates);
+// order[p][rank] = candidate index.  resolved[p] is cleared.
+__global__ void __launch_bounds__(PCBA_TPB) k_cand_rank(Engine E, const float* key, int* order,
+                                                        int* resolved) {
+  __shared__ float s_key[PCBA_MAX_CAND];
+  __shared__ int s_id[PCBA_MAX_CAND];
+  const int p = blockIdx.x;
+  const int n_c = min(E.n_warm, PCBA_MAX_CAND);
+  int n2 = 1;
+  while (n2 < n_c) n2 <<= 1;
+  for (int c = threadIdx.x; c < n2; c += PCBA_TPB) {
+    s_key[c] = c < n_c ? key[(long long)p * E.n_warm + c] : INFINITY;
+    s_id[c] = c < n_c ? c : 0x7fffffff;
+  }
+  if (threadIdx.x == 0) resolved[p] = 0;
+  __syncthreads();
+  for (int k = 2; k <= n2; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int i = threadIdx.x; i < n2; i += PCBA_TPB) {
+        const int o = i ^ j;
+        if (o > i) {
+          const bool gt = s_key[i] > s_key[o] || (s_key[i] == s_key[o] && s_id[i] > s_id[o]);
+          if (gt == ((i & k) == 0)) {
+            const float tk = s_key[i]; s_key[i] = s_key[o]; s_key[o] = tk;
+            const int ti = s_id[i]; s_id[i] = s_id[o]; s_id[o] = ti;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  for (int c = threadIdx.x; c < n_c; c += PCBA_TPB) order[(long long)p * E.n_warm + c] = s_id[c];
+}
+
+// Certifies the candidates of ranks [r0, r1) of every problem not yet
+// resolved: grid (constraint tiles, problems); dynamic shared memory: 32 * cmax
+// floats of coefficients, then (r1 - r0) * l floats of coordinates.
+// viol[p][rank] is set when a constraint bound exceeds its limit.
+__global__ void __launch_bounds__(256) k_cand_feas(Engine E, const float* key, const int* order,
+                                                   const int* resolved, unsigned* viol, int cmax,
+                                                   int r0, int r1) {
   extern __shared__ float kcs[];
   const int p = blockIdx.y;
+  if (resolved[p]) return;
   const ProbDesc* D = E.desc + p;
   const int total = D->alpha + D->beta;
   const int q0 = blockIdx.x * 32;
   if (q0 >= total) return;
+  const int n_c = min(E.n_warm, PCBA_MAX_CAND);
+  r1 = min(r1, n_c);
+  if (r0 >= r1) return;
+  const int nr = r1 - r0;
   const int nq = min(32, total - q0);
   const int l = D->l;
-  const int n_c = E.n_warm;
   float* sa = kcs;
   float* sx = kcs + 32 * cmax;
+  const long long base = (long long)p * E.n_warm;
   const float* mono32 = E.mono32 + D->mono_off;
   for (int t = threadIdx.x; t < nq * cmax; t += blockDim.x) {
     const int qi = t / cmax, j = t - qi * cmax;
@@ -443,57 +485,63 @@ __global__ void __launch_bounds__(256) k_cand_feas(Engine E, const float* key, u
       sa[qi * cmax + j] = a[j];
     }
   }
-  for (int t = threadIdx.x; t < n_c * l; t += blockDim.x) {
-    const int c = t / l, r = t - c * l;
-    sx[t] = (float)E.warm[((long long)p * n_c + c) * PCBA_MAXD + r];
+  for (int t = threadIdx.x; t < nr * l; t += blockDim.x) {
+    const int rr = t / l, r = t - rr * l;
+    const int c = order[base + r0 + rr];
+    sx[t] = (float)E.warm[(base + c) * PCBA_MAXD + r];
   }
   __syncthreads();
   const float eq_tol = (float)E.params->eq_tol;
-  for (int t = threadIdx.x; t < n_c * nq; t += blockDim.x) {
-    const int c = t / nq, qi = t - c * nq;
-    if (!(key[(long long)p * n_c + c] < INFINITY)) continue;
+  for (int t = threadIdx.x; t < nr * nq; t += blockDim.x) {
+    const int rr = t / nq, qi = t - rr * nq;
+    const int rank = r0 + rr;
+    if (!(key[base + order[base + rank]] < INFINITY)) continue;
     const int q = q0 + qi;
     const bool is_g = q < D->alpha;
     float val, err;
-    horner_f32(sa + qi * cmax, l, is_g ? D->G : D->H, sx + c * l, &val, &err);
+    horner_f32(sa + qi * cmax, l, is_g ? D->G : D->H, sx + rr * l, &val, &err);
     if (!(__fadd_ru(is_g ? val : fabsf(val), err) <= (is_g ? 0.0f : eq_tol)))
-      viol[(long long)p * n_c + c] = 1u;
+      viol[base + rank] = 1u;
   }
 }
 
+// After the ranks [0, r1) were checked: a problem is resolved when one of
+// them is certified feasible (a lower rank always wins).
+__global__ void k_cand_check(Engine E, const float* key, const int* order, const unsigned* viol,
+                             int* resolved, int r1) {
+  const int p = blockIdx.x;
+  const int n_c = min(E.n_warm, PCBA_MAX_CAND);
+  const long long base = (long long)p * E.n_warm;
+  int ok = 0;
+  for (int r = threadIdx.x; r < min(r1, n_c); r += blockDim.x)
+    if (key[base + order[base + r]] < INFINITY && viol[base + r] == 0u) ok = 1;
+  ok = __syncthreads_or(ok);
+  if (threadIdx.x == 0) resolved[p] = ok;
+}
+
+// The first certified-feasible candidate in rank order seeds p_up with its
+// FP64 cost bound.
 __global__ void __launch_bounds__(PCBA_TPB) k_cand_pick(Engine E, const float* key,
-                                                        const unsigned* viol) {
-  __shared__ float s_k[PCBA_TPB / 32];
-  __shared__ int s_i[PCBA_TPB / 32];
+                                                        const int* order, const unsigned* viol) {
+  __shared__ int s_r[PCBA_TPB / 32];
   const int p = blockIdx.x;
   const ProbDesc* D = E.desc + p;
   ProbState* S = E.state + p;
-  const int n_c = E.n_warm;
-  float bk = INFINITY;
-  int bi = 0x7fffffff;
-  for (int c = threadIdx.x; c < n_c; c += PCBA_TPB) {
-    const long long t = (long long)p * n_c + c;
-    const float k = key[t];
-    if (k < INFINITY && viol[t] == 0u && (k < bk || (k == bk && c < bi))) {
-      bk = k;
-      bi = c;
-    }
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    const float ok = __shfl_xor_sync(0xffffffffu, bk, o);
-    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-    if (ok < bk || (ok == bk && oi < bi)) { bk = ok; bi = oi; }
-  }
-  if ((threadIdx.x & 31) == 0) { s_k[threadIdx.x >> 5] = bk; s_i[threadIdx.x >> 5] = bi; }
+  const int n_c = min(E.n_warm, PCBA_MAX_CAND);
+  const long long base = (long long)p * E.n_warm;
+  int br = 0x7fffffff;
+  for (int r = threadIdx.x; r < n_c; r += PCBA_TPB)
+    if (r < br && key[base + order[base + r]] < INFINITY && viol[base + r] == 0u) br = r;
+  for (int o = 16; o > 0; o >>= 1) br = min(br, __shfl_xor_sync(0xffffffffu, br, o));
+  if ((threadIdx.x & 31) == 0) s_r[threadIdx.x >> 5] = br;
   __syncthreads();
   if (threadIdx.x != 0) return;
-  for (int w = 1; w < PCBA_TPB / 32; ++w)
-    if (s_k[w] < bk || (s_k[w] == bk && s_i[w] < bi)) { bk = s_k[w]; bi = s_i[w]; }
+  for (int w = 1; w < PCBA_TPB / 32; ++w) br = min(br, s_r[w]);
   const int l = D->l;
   double x[PCBA_MAXD];
   double offer = INFINITY;
   int found = 0;
-  if (bk < INFINITY && eval_candidate(E, 0, p, bi, x)) {
+  if (br < n_c && eval_candidate(E, 0, p, order[base + br], x)) {
     double pc, pe;
     horner_f64(E.mono + D->mono_off, l, D->P, x, &pc, &pe);
     offer = __dadd_ru(pc, pe);
