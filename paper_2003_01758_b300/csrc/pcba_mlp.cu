@@ -35,95 +35,218 @@ namespace {
 // ---------------------------------------------------------------------------
 // GEMM: C[M x N] (+)= A[M x K] B[K x N]; A(m,k) = A[m*lda+k] or, transposed,
 // A[k*lda+m]; B(k,n) = B[k*ldb+n] or, transposed, B[n*ldb+k].
+//
+// BF16 precision runs on the 5th-generation tensor cores: one CTA computes a
+// 128 x 128 tile of C with tcgen05.mma (kind::f16, BF16 operands, FP32
+// accumulation in tensor memory).  Operands are read as FP32, rounded to BF16
+// and written to shared memory in the canonical K-major layout without
+// swizzle: core matrices of 8 rows x 16 bytes, the 16 row groups of one 8-wide
+// k slice contiguous (stride 128 B), k slices 2 KB apart.  K advances in
+// chunks of 64 through two shared-memory stages; a single thread issues the
+// MMAs (K = 16 each) and commits them to the stage's mbarrier, which the
+// threads wait on (bounded) before refilling the stage.  The epilogue reads
+// the accumulators with tcgen05.ld (warp w owns rows 32w .. 32w+31).
 // ---------------------------------------------------------------------------
-constexpr int GBM = 64, GBN = 64, GBK = 32, GLDS = GBK + 8;
+constexpr int TC_M = 128, TC_N = 128, TC_K = 64;
+constexpr int TC_STAGE_BYTES = (TC_M + TC_N) * TC_K * 2;  // 32 KB: A then B
+constexpr int TC_SMEM = 2 * TC_STAGE_BYTES + 1024;        // + alignment slack
 
-__device__ __forceinline__ void mma_bf16(float (&c)[4], const uint32_t (&a)[4],
-                                         const uint32_t (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
-      "{%8,%9}, {%0,%1,%2,%3};"
-      : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
+__device__ __forceinline__ unsigned tc_smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
 }
 
-// Split-K: block z covers k in [z * kchunk, (z + 1) * kchunk) and, when the
-// grid has more than one z, adds its partial sums into C atomically (C must
-// then hold the accumulation target, beta = 1).
-__global__ void __launch_bounds__(128) gemm_bf16(int M, int N, int K, const float* __restrict__ A,
-                                                 int lda, int ta, const float* __restrict__ B,
-                                                 int ldb, int tb, float* C, int ldc, int beta,
-                                                 int kchunk) {
-  __shared__ __align__(16) __nv_bfloat16 sA[GBM][GLDS];
-  __shared__ __align__(16) __nv_bfloat16 sB[GBN][GLDS];
-  const int m0 = blockIdx.y * GBM, n0 = blockIdx.x * GBN;
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int wm = warp >> 1, wn = warp & 1;
-  const int gid = lane >> 2, tig = lane & 3;
-  float acc[2][4][4];
-#pragma unroll
-  for (int i = 0; i < 2; ++i)
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[i][j][q] = 0.0f;
-  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
-  for (int k0 = kbeg; k0 < kend; k0 += GBK) {
-    for (int idx = tid; idx < GBM * GBK; idx += 128) {
-      int m, k;
-      if (ta) { k = idx / GBM; m = idx % GBM; } else { m = idx / GBK; k = idx % GBK; }
-      const int gm = m0 + m, gk = k0 + k;
-      float v = 0.0f;
-      if (gm < M && gk < kend) v = ta ? A[(size_t)gk * lda + gm] : A[(size_t)gm * lda + gk];
-      sA[m][k] = __float2bfloat16_rn(v);
-    }
-    for (int idx = tid; idx < GBN * GBK; idx += 128) {
-      int n, k;
-      if (tb) { n = idx / GBK; k = idx % GBK; } else { k = idx / GBN; n = idx % GBN; }
-      const int gn = n0 + n, gk = k0 + k;
-      float v = 0.0f;
-      if (gn < N && gk < kend) v = tb ? B[(size_t)gn * ldb + gk] : B[(size_t)gk * ldb + gn];
-      sB[n][k] = __float2bfloat16_rn(v);
-    }
-    __syncthreads();
-#pragma unroll
-    for (int kk = 0; kk < GBK; kk += 16) {
-      uint32_t af[2][4], bf[4][2];
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi) {
-        const int row = wm * 32 + mi * 16 + gid;
-        af[mi][0] = *(const uint32_t*)&sA[row][kk + tig * 2];
-        af[mi][1] = *(const uint32_t*)&sA[row + 8][kk + tig * 2];
-        af[mi][2] = *(const uint32_t*)&sA[row][kk + 8 + tig * 2];
-        af[mi][3] = *(const uint32_t*)&sA[row + 8][kk + 8 + tig * 2];
-      }
-#pragma unroll
-      for (int ni = 0; ni < 4; ++ni) {
-        const int col = wn * 32 + ni * 8 + gid;
-        bf[ni][0] = *(const uint32_t*)&sB[col][kk + tig * 2];
-        bf[ni][1] = *(const uint32_t*)&sB[col][kk + 8 + tig * 2];
-      }
-#pragma unroll
-      for (int mi = 0; mi < 2; ++mi)
-#pragma unroll
-        for (int ni = 0; ni < 4; ++ni) mma_bf16(acc[mi][ni], af[mi], bf[ni]);
-    }
-    __syncthreads();
+// shared-memory matrix descriptor: K-major, no swizzle; LBO = 2048 B between
+// k slices, SBO = 128 B between 8-row groups; descriptor version 1
+__device__ __forceinline__ unsigned long long tc_desc(unsigned saddr) {
+  return (unsigned long long)((saddr & 0x3FFFFu) >> 4) | ((unsigned long long)(2048 >> 4) << 16) |
+         ((unsigned long long)(128 >> 4) << 32) | (1ull << 46);
+}
+
+// instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major
+__device__ __forceinline__ unsigned tc_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(n >> 3) << 17) | ((unsigned)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_mbar_init(unsigned long long* bar) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(tc_smem_u32(bar)) : "memory");
+}
+
+// bounded wait for the given phase parity; false after about one second
+__device__ __forceinline__ bool tc_mbar_wait(unsigned long long* bar, unsigned parity) {
+  unsigned long long t0;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t0));
+  for (;;) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(tc_smem_u32(bar)), "r"(parity)
+        : "memory");
+    if (ok) return true;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    if (t - t0 > 1000000000ull) return false;
   }
+}
+
+// stage one 128 x 64 operand block: row t of the tile (m for A, n for B) and
+// eight k slices of 8 values each, written as 16-byte rows of core matrices
+__device__ __forceinline__ void tc_stage(__nv_bfloat16* dst, const float* X, int ld, int trans,
+                                         int r0, int rows, int k0, int kend, int t) {
+  const int r = r0 + t;
+  // rows of X contiguous in k, 16-byte aligned and fully inside: two float4 loads per slice
+  const bool vec = !trans && r < rows && (ld & 3) == 0 && (k0 & 3) == 0 &&
+                   (((size_t)X) & 15) == 0;
+#pragma unroll 1
+  for (int c8 = 0; c8 < TC_K / 8; ++c8) {
+    __align__(16) __nv_bfloat16 v[8];
+    const int kb = k0 + c8 * 8;
+    if (vec && kb + 8 <= kend) {
+      const float4 a = *(const float4*)(X + (size_t)r * ld + kb);
+      const float4 b = *(const float4*)(X + (size_t)r * ld + kb + 4);
+      v[0] = __float2bfloat16_rn(a.x); v[1] = __float2bfloat16_rn(a.y);
+      v[2] = __float2bfloat16_rn(a.z); v[3] = __float2bfloat16_rn(a.w);
+      v[4] = __float2bfloat16_rn(b.x); v[5] = __float2bfloat16_rn(b.y);
+      v[6] = __float2bfloat16_rn(b.z); v[7] = __float2bfloat16_rn(b.w);
+    } else {
 #pragma unroll
-  for (int mi = 0; mi < 2; ++mi)
+      for (int e = 0; e < 8; ++e) {
+        const int k = kb + e;
+        float x = 0.0f;
+        if (r < rows && k < kend) x = trans ? X[(size_t)k * ld + r] : X[(size_t)r * ld + k];
+        v[e] = __float2bfloat16_rn(x);
+      }
+    }
+    *(uint4*)(dst + ((c8 * 16 + (t >> 3)) * 64 + (t & 7) * 8)) = *(const uint4*)v;
+  }
+}
+
+// A operand "row" = m, B operand "row" = n: A(m,k) and B(k,n) staged as [m][k], [n][k]
+__global__ void __launch_bounds__(128) gemm_tc(int M, int N, int K, const float* __restrict__ A,
+                                               int lda, int ta, const float* __restrict__ B,
+                                               int ldb, int tb, float* C, int ldc, int beta,
+                                               int kchunk, int* err) {
+  extern __shared__ unsigned char tc_raw[];
+  __shared__ __align__(8) unsigned long long bars[3];
+  __shared__ unsigned tmem_base;
+  unsigned char* sm = (unsigned char*)(((size_t)tc_raw + 1023) & ~(size_t)1023);
+  const int t = threadIdx.x, warp = t >> 5;
+  const int m0 = blockIdx.y * TC_M, n0 = blockIdx.x * TC_N;
+  const int kbeg = blockIdx.z * kchunk, kend = min(K, kbeg + kchunk);
+  const int nchunks = kend > kbeg ? (kend - kbeg + TC_K - 1) / TC_K : 0;
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 128;" ::"r"(
+                     tc_smem_u32(&tmem_base))
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (t == 0) {
+    for (int q = 0; q < 3; ++q) tc_mbar_init(&bars[q]);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const unsigned tmem = tmem_base;
+  const unsigned idesc = tc_idesc(TC_M, TC_N);
+  bool ok = true;
+  for (int c = 0; c < nchunks && ok; ++c) {
+    const int s = c & 1;
+    unsigned char* stage = sm + s * TC_STAGE_BYTES;
+    __nv_bfloat16* sA = (__nv_bfloat16*)stage;
+    __nv_bfloat16* sB = (__nv_bfloat16*)(stage + TC_M * TC_K * 2);
+    if (c >= 2) ok = tc_mbar_wait(&bars[s], (unsigned)((c - 2) >> 1) & 1u);
+    if (!__syncthreads_and(ok ? 1 : 0)) {
+      ok = false;
+      break;
+    }
+    const int k0 = kbeg + c * TC_K;
+    tc_stage(sA, A, lda, ta, m0, M, k0, kend, t);
+    tc_stage(sB, B, ldb, !tb, n0, N, k0, kend, t);
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (t == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-    for (int ni = 0; ni < 4; ++ni)
+      for (int ks = 0; ks < TC_K / 16; ++ks) {
+        const unsigned long long ad = tc_desc(tc_smem_u32(sA) + ks * 2 * 2048);
+        const unsigned long long bd = tc_desc(tc_smem_u32(sB) + ks * 2 * 2048);
+        const unsigned acc = (c > 0 || ks > 0) ? 1u : 0u;
+        asm volatile(
+            "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+            " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+            "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+            : "memory");
+      }
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              tc_smem_u32(&bars[s]))
+          : "memory");
+    }
+  }
+  if (nchunks > 0) {
+    if (t == 0)
+      asm volatile(
+          "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+              tc_smem_u32(&bars[2]))
+          : "memory");
+    // all MMAs issued (also after a timeout) finish before tensor memory is read or freed
+    const bool done = tc_mbar_wait(&bars[2], 0u);
+    ok = __syncthreads_and((ok && done) ? 1 : 0) != 0;
+    if (!done && t == 0) atomicExch(err, 1);
+  }
+  if (!ok && t == 0) atomicExch(err, 1);
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (ok && nchunks > 0) {
+    const int row = m0 + warp * 32 + (t & 31);
+    const bool split = gridDim.z > 1;
+#pragma unroll 1
+    for (int j = 0; j < TC_N / 32; ++j) {
+      unsigned v[32];
+      const unsigned taddr = tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(j * 32);
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+          "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+          : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+            "=r"(v[7]), "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]),
+            "=r"(v[13]), "=r"(v[14]), "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]),
+            "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]), "=r"(v[24]),
+            "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]),
+            "=r"(v[31])
+          : "r"(taddr));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      if (row < M) {
+        const int cb = n0 + j * 32;
+        float* drow = C + (size_t)row * ldc + cb;
+        if (!split && cb + 32 <= N && (ldc & 3) == 0 && (((size_t)drow) & 15) == 0) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int r = m0 + wm * 32 + mi * 16 + gid + (q >= 2 ? 8 : 0);
-        const int c = n0 + wn * 32 + ni * 8 + tig * 2 + (q & 1);
-        if (r < M && c < N) {
-          float* dst = C + (size_t)r * ldc + c;
-          if (gridDim.z > 1) atomicAdd(dst, acc[mi][ni][q]);
-          else *dst = acc[mi][ni][q] + (beta ? *dst : 0.0f);
+          for (int i = 0; i < 32; i += 4) {
+            float4 x = make_float4(__uint_as_float(v[i]), __uint_as_float(v[i + 1]),
+                                   __uint_as_float(v[i + 2]), __uint_as_float(v[i + 3]));
+            if (beta) {
+              const float4 o = *(const float4*)(drow + i);
+              x.x += o.x; x.y += o.y; x.z += o.z; x.w += o.w;
+            }
+            *(float4*)(drow + i) = x;
+          }
+        } else {
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            if (cb + i < N) {
+              const float x = __uint_as_float(v[i]);
+              if (split) atomicAdd(drow + i, x);
+              else drow[i] = x + (beta ? drow[i] : 0.0f);
+            }
+          }
         }
       }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 128;" ::"r"(tmem) : "memory");
 }
 
 __global__ void gemm_f32(int M, int N, int K, const float* __restrict__ A, int lda, int ta,
@@ -292,6 +415,7 @@ struct pcba_mlp {
   float *h1 = nullptr, *h2 = nullptr, *h3 = nullptr, *dA = nullptr, *dB = nullptr;
   float *z = nullptr, *u = nullptr, *h4 = nullptr, *h5 = nullptr, *y = nullptr, *du = nullptr;
   float *d4 = nullptr, *d5 = nullptr, *d6 = nullptr, *s6 = nullptr, *d_loss = nullptr;
+  int* d_err = nullptr;  // set by a tensor-core GEMM whose bounded wait ran out
   int* arg = nullptr;
   float* h_loss = nullptr;
 };
@@ -338,18 +462,32 @@ void gemm(const pcba_mlp* m, cudaStream_t s, int M, int N, int K, const float* A
           const float* B, int ldb, int tb, float* C, int ldc, int beta) {
   if (M <= 0 || N <= 0 || K <= 0) return;
   if (m->prec == 16) {
-    const int tiles = ((N + GBN - 1) / GBN) * ((M + GBM - 1) / GBM);
+    const int tiles = ((N + TC_N - 1) / TC_N) * ((M + TC_M - 1) / TC_M);
     int splits = 1;
-    if (beta && K > 4 * GBK * 8 && tiles < 2 * m->sms)
-      splits = std::min((K + 8 * GBK - 1) / (8 * GBK), (2 * m->sms + tiles - 1) / tiles);
-    const int kchunk = ((K + splits - 1) / splits + GBK - 1) / GBK * GBK;
+    if (beta && K > 8 * TC_K && tiles < 2 * m->sms)
+      splits = std::min((K + 4 * TC_K - 1) / (4 * TC_K), (2 * m->sms + tiles - 1) / tiles);
+    const int kchunk = ((K + splits - 1) / splits + TC_K - 1) / TC_K * TC_K;
     splits = (K + kchunk - 1) / kchunk;
-    const dim3 grid((N + GBN - 1) / GBN, (M + GBM - 1) / GBM, std::max(splits, 1));
-    gemm_bf16<<<grid, 128, 0, s>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc, beta, kchunk);
+    const dim3 grid((N + TC_N - 1) / TC_N, (M + TC_M - 1) / TC_M, std::max(splits, 1));
+    gemm_tc<<<grid, 128, TC_SMEM, s>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc, beta, kchunk,
+                                        m->d_err);
   } else {
     const dim3 blk(16, 16), grid((N + 15) / 16, (M + 15) / 16);
     gemm_f32<<<grid, blk, 0, s>>>(M, N, K, A, lda, ta, B, ldb, tb, C, ldc, beta);
   }
+}
+
+// a tensor-core GEMM that timed out leaves a flag; reported (and cleared) at
+// the next synchronising call
+int check_err(pcba_mlp* m) {
+  int e = 0;
+  if (cudaMemcpy(&e, m->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return pcba_internal_fail(PCBA_ERR_CUDA, "network error flag unreadable");
+  if (e) {
+    cudaMemset(m->d_err, 0, sizeof(int));
+    return pcba_internal_fail(PCBA_ERR_DEVICE_TIMEOUT, "a tensor-core GEMM wait timed out");
+  }
+  return 0;
 }
 
 int check_batch(const pcba_mlp* m, int n_sets, int n_points) {
@@ -473,6 +611,7 @@ int pcba_mlp_create(pcba_mlp** out, int point_dim, int global_dim, int hidden, i
       cudaMalloc((void**)&m->d_m, sizeof(float) * o) != cudaSuccess ||
       cudaMalloc((void**)&m->d_v, sizeof(float) * o) != cudaSuccess ||
       cudaMalloc((void**)&m->d_loss, sizeof(float)) != cudaSuccess ||
+      cudaMalloc((void**)&m->d_err, sizeof(int)) != cudaSuccess ||
       cudaMallocHost((void**)&m->h_loss, sizeof(float)) != cudaSuccess) {
     pcba_mlp_destroy(m);
     return pcba_internal_fail(PCBA_ERR_OOM, "network allocation failed");
@@ -480,6 +619,12 @@ int pcba_mlp_create(pcba_mlp** out, int point_dim, int global_dim, int hidden, i
   cudaMemcpy(m->d_par, init.data(), sizeof(float) * o, cudaMemcpyHostToDevice);
   cudaMemset(m->d_m, 0, sizeof(float) * o);
   cudaMemset(m->d_v, 0, sizeof(float) * o);
+  cudaMemset(m->d_err, 0, sizeof(int));
+  if (cudaFuncSetAttribute(gemm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, TC_SMEM) !=
+      cudaSuccess) {
+    pcba_mlp_destroy(m);
+    return pcba_internal_fail(PCBA_ERR_CUDA, "cannot configure the tensor-core GEMM");
+  }
   *out = m;
   return 0;
 }
@@ -490,6 +635,7 @@ void pcba_mlp_destroy(pcba_mlp* m) {
   float* f[] = {m->d_par, m->d_grad, m->d_m, m->d_v, m->d_loss};
   for (float* p : f)
     if (p) cudaFree(p);
+  if (m->d_err) cudaFree(m->d_err);
   if (m->h_loss) cudaFreeHost(m->h_loss);
   delete m;
 }
@@ -540,7 +686,7 @@ int pcba_mlp_gradient(pcba_mlp* m, const float* d_points, const int* d_offsets, 
   MLP_CK(cudaMemcpyAsync(m->h_loss, m->d_loss, sizeof(float), cudaMemcpyDeviceToHost, s));
   MLP_CK(cudaStreamSynchronize(s));
   if (loss) *loss = *m->h_loss;
-  return 0;
+  return check_err(m);
 }
 
 int pcba_mlp_train_step(pcba_mlp* m, const float* d_points, const int* d_offsets, int n_sets,
@@ -562,6 +708,7 @@ int pcba_mlp_train_step(pcba_mlp* m, const float* d_points, const int* d_offsets
     MLP_CK(cudaMemcpyAsync(m->h_loss, m->d_loss, sizeof(float), cudaMemcpyDeviceToHost, s));
     MLP_CK(cudaStreamSynchronize(s));
     *loss = *m->h_loss;
+    return check_err(m);
   }
   return 0;
 }
