@@ -98,7 +98,8 @@ __device__ __forceinline__ void tc_stage(__nv_bfloat16* dst, const float* X, int
   // rows of X contiguous in k, 16-byte aligned and fully inside: two float4 loads per slice
   const bool vec = !trans && r < rows && (ld & 3) == 0 && (k0 & 3) == 0 &&
                    (((size_t)X) & 15) == 0;
-#pragma unroll 1
+  // all eight slices unrolled: their loads are in flight together
+#pragma unroll
   for (int c8 = 0; c8 < TC_K / 8; ++c8) {
     __align__(16) __nv_bfloat16 v[8];
     const int kb = k0 + c8 * 8;
