@@ -344,8 +344,7 @@ int launch_after_k2(pcba_batch* b, cudaStream_t s, int use_graph) {
   k3_classify<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
   k4_index<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
   if (fp32) PCBA_CK(cudaStreamWaitEvent(s, b->ev_join, 0));
-  k4_move<<<g.k4_grid, PCBA_TPB, 0, s>>>(b->E);
-  k_control<<<1, PCBA_TPB, 0, s>>>(b->E, b->cond, use_graph);
+  k_move_control<<<g.k4_grid, PCBA_TPB, 0, s>>>(b->E, b->cond, use_graph);
   PCBA_CK(cudaGetLastError());
   return 0;
 }
@@ -468,6 +467,7 @@ int setup_kernels(pcba_batch* b) {
                                96 * 1024));
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_classify, PCBA_TPB, 0));
   g.k3_grid = std::max(1, occ) * g.sms;
+
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_move, PCBA_TPB, 0));
   g.k4_grid = std::max(1, occ) * g.sms;
   return 0;
@@ -950,6 +950,7 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   b->total_ms = ms;
   if (b->h_plan->guard_hit == 2)
     return fail(PCBA_ERR_DEVICE_TIMEOUT, "a bulk copy of the subdivision kernel did not complete");
+
   if (b->h_plan->guard_hit) return fail(PCBA_ERR_DEVICE_TIMEOUT, "device loop guard reached");
   return 0;
 }
@@ -1291,11 +1292,12 @@ int pcba_batch_stats(const pcba_batch* b, long long* loop_iters, long long* kern
   if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
   const long long it = b->h_plan ? b->h_plan->steps_global : 0;
   if (loop_iters) *loop_iters = it;
-  // prologue: k1_matrices, k1_convert, k_eval, k_init (plus k_mono32 and
-  // k_candidates for warm starts); 6 kernels per loop iteration (7 with the
-  // FP32 refresh); epilogue: k_eval
-  if (kernel_launches)
-    *kernel_launches = 5 + (b->precision == PCBA_FP32 ? 7 : 6) * it + b->extra_launches;
+  // prologue: k1_matrices, k1_convert, k_eval, k_init (plus the warm-start
+  // kernels); epilogue: k_eval
+  // per iteration: subdivision, k_pup, k3_classify, k4_index, k_move_control,
+  // and k_refresh in FP32
+  const long long per_it = 5 + (b->precision == PCBA_FP32 ? 1 : 0);
+  if (kernel_launches) *kernel_launches = 5 + per_it * it + b->extra_launches;
   if (h2d_bytes) *h2d_bytes = b->h2d_bytes;
   if (d2h_bytes) *d2h_bytes = b->d2h_bytes;
   return 0;

@@ -427,7 +427,7 @@ __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
 // Runs after the subdivision kernel, over the same child tiles as k3_classify:
 // each warp reduces the pmax of its feasible children and one atomic min per
 // warp lowers the problem's p_up key.
-__global__ void __launch_bounds__(PCBA_TPB) k_pup(Engine E) {
+__device__ __forceinline__ void pup_phase(const Engine& E) {
   const unsigned tiles_total = E.plan->k3_tiles;
   const double eq_tol = E.params->eq_tol;
   for (unsigned u = blockIdx.x; u < tiles_total; u += gridDim.x) {
@@ -449,6 +449,8 @@ __global__ void __launch_bounds__(PCBA_TPB) k_pup(Engine E) {
     if ((threadIdx.x & 31) == 0 && best != ~0ull) atomicMin(&S->pup_key, best);
   }
 }
+
+__global__ void __launch_bounds__(PCBA_TPB) k_pup(Engine E) { pup_phase(E); }
 
 // ---------------------------------------------------------------------------
 // K3: classify, scan, finalize, plan
@@ -599,10 +601,8 @@ __device__ void plan_next(const Engine& E, unsigned* sscan) {
   }
 }
 
-__global__ void __launch_bounds__(PCBA_TPB) k3_classify(Engine E) {
-  __shared__ unsigned sscan[8];
-  __shared__ double sred[8 * 2];
-  __shared__ int s_last, s_glast;
+__device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan, double* sred,
+                                               int& s_last, int& s_glast) {
   const unsigned tiles_total = E.plan->k3_tiles;
   const double eq_tol = E.params->eq_tol;
   for (unsigned u = blockIdx.x; u < tiles_total; u += gridDim.x) {
@@ -660,10 +660,17 @@ __global__ void __launch_bounds__(PCBA_TPB) k3_classify(Engine E) {
   }
 }
 
+__global__ void __launch_bounds__(PCBA_TPB) k3_classify(Engine E) {
+  __shared__ unsigned sscan[8];
+  __shared__ double sred[8 * 2];
+  __shared__ int s_last, s_glast;
+  classify_phase(E, sscan, sred, s_last, s_glast);
+}
+
 // ---------------------------------------------------------------------------
 // K4: Alg. 5 hole filling
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(PCBA_TPB) k4_index(Engine E) {
+__device__ __forceinline__ void index_phase(const Engine& E) {
   const unsigned tiles_total = E.plan->k3_tiles;
   for (unsigned u = blockIdx.x; u < tiles_total; u += gridDim.x) {
     const int p = find_problem(E.k3_pre, E.np, u);
@@ -689,9 +696,11 @@ __global__ void __launch_bounds__(PCBA_TPB) k4_index(Engine E) {
   }
 }
 
+__global__ void __launch_bounds__(PCBA_TPB) k4_index(Engine E) { index_phase(E); }
+
 // Alg. 5 on the map: the j-th hole below K_save takes the slot of the item at
 // save position K_save-1-j (reading R11); one thread per hole.
-__global__ void __launch_bounds__(PCBA_TPB) k4_move(Engine E) {
+__device__ __forceinline__ void move_phase(const Engine& E) {
   const unsigned units = E.plan->k4_units;
   for (unsigned u = blockIdx.x * blockDim.x + threadIdx.x; u < units;
        u += gridDim.x * blockDim.x) {
@@ -704,15 +713,17 @@ __global__ void __launch_bounds__(PCBA_TPB) k4_move(Engine E) {
   }
 }
 
+__global__ void __launch_bounds__(PCBA_TPB) k4_move(Engine E) { move_phase(E); }
+
 // ---------------------------------------------------------------------------
 // loop control, init, evaluation
 // ---------------------------------------------------------------------------
 // Runs once per loop iteration after the compaction: publishes the next
 // step's K3 tile prefix, counts the step, applies the optional step limit and
 // the hard guard, and sets the WHILE condition of the device loop.
-__global__ void k_control(Engine E, cudaGraphConditionalHandle handle, int use_graph) {
+__device__ __forceinline__ void control_phase(const Engine& E, cudaGraphConditionalHandle handle,
+                                              int use_graph, int& s_code, int& s_run) {
   Plan* pl = E.plan;
-  __shared__ int s_code, s_run;
   for (int q = threadIdx.x; q <= E.np; q += blockDim.x) E.k3_pre[q] = E.k3_pre_next[q];
   if (threadIdx.x == 0) {
     pl->k3_tiles = pl->k3_tiles_next;
@@ -749,6 +760,29 @@ __global__ void k_control(Engine E, cudaGraphConditionalHandle handle, int use_g
     pl->any_running = s_run;
     if (use_graph) cudaGraphSetConditional(handle, s_run ? 1u : 0u);
   }
+}
+
+__global__ void k_control(Engine E, cudaGraphConditionalHandle handle, int use_graph) {
+  __shared__ int s_code, s_run;
+  control_phase(E, handle, use_graph, s_code, s_run);
+}
+
+// Alg. 5 on the slot map, then the loop control in the last block to finish.
+__global__ void __launch_bounds__(PCBA_TPB) k_move_control(Engine E,
+                                                           cudaGraphConditionalHandle handle,
+                                                           int use_graph) {
+  __shared__ int s_last, s_code, s_run;
+  move_phase(E);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    s_last = atomicAdd(&E.plan->k4_done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) E.plan->k4_done = 0u;
+  control_phase(E, handle, use_graph, s_code, s_run);
 }
 
 __global__ void k_init(Engine E) {
@@ -826,6 +860,7 @@ __global__ void k_init(Engine E) {
     pl->refreshed_total = 0ull;
     E.kr_pre[E.np] = 0;
     pl->k3_done = 0;
+    pl->k4_done = 0u;
     pl->any_running = run2 > 0;
     pl->steps_global = 0;
     pl->guard_hit = 0;
