@@ -139,6 +139,8 @@ struct pcba_batch {
   int cand_cmax = 0, cand_tiles = 1;  // largest constraint patch, constraint tiles of 32
   double* d_stencil = nullptr;  // guided solves: [stencil_cap] doubles
   long long cand_cap = 0, stencil_cap = 0;
+  std::vector<double> refine;   // refinement stencil of guided solves (host copy)
+  int refine_n = 0, refine_dim = 0;
   long long trace_rows_total = 0;
   // host mirrors (pinned)
   ProbState* h_state = nullptr;
@@ -823,7 +825,8 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   PCBA_CK(cudaEventRecord(b->ev0, s));
   b->h2d_bytes = (long long)sizeof(SolveParams) + (host_coeffs ? 8LL * b->mono_doubles : 0) +
                  (warm ? 8LL * PCBA_MAXD * n : 0) +
-                 (guide ? 8LL * guide->n * guide->dim : 0) + b->pending_h2d;
+                 (guide ? 8LL * guide->n * guide->dim : 0) +
+                 (guide && b->refine_n > 0 ? 8LL * b->refine_n * b->refine_dim : 0) + b->pending_h2d;
   b->pending_h2d = 0;
   b->extra_launches = (guide || warm ? 1 : 0) + (guide ? 1 : 0);
   b->d2h_bytes = (long long)(sizeof(ProbState) + sizeof(EvalOut)) * n + (long long)sizeof(Plan);
@@ -847,7 +850,7 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
                             cudaMemcpyHostToDevice, s));
     const long long nc = (long long)n * guide->n;
     k_candidates<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(E1, guide->guess, guide->dim,
-                                                             b->d_stencil, guide->n, b->d_cand);
+                                                             b->d_stencil, guide->n, b->d_cand, 0);
     E1.warm = b->d_cand;
     E1.n_warm = guide->n;
   }
@@ -857,28 +860,52 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
                                                                    b->g.k1_wpb);
   // ranks [0, head) are certified first; the rest only for problems that
   // found no feasible candidate among them
-  const int head = std::min(E1.n_warm, 32);
-  const size_t cand_smem =
-      sizeof(float) * ((size_t)32 * b->cand_cmax + (size_t)std::min(E1.n_warm, 1024) * b->max_l);
-  const bool cand_fast = (guide || warm) && b->cand_cmax <= 512 && cand_smem <= 96 * 1024 &&
-                         b->ckey_cap >= E1.n_warm;
-  if (cand_fast) {
-    const long long nc = (long long)n * E1.n_warm;
+  auto certify = [&](const Engine& Ec) -> int {
+    const int head = std::min(Ec.n_warm, 32);
+    const size_t cand_smem = sizeof(float) * ((size_t)32 * b->cand_cmax +
+                                              (size_t)std::min(Ec.n_warm, 1024) * b->max_l);
+    const bool cand_fast =
+        b->cand_cmax <= 512 && cand_smem <= 96 * 1024 && b->ckey_cap >= Ec.n_warm;
+    if (!cand_fast) {
+      k_eval<<<n, PCBA_TPB, 0, s>>>(Ec, 0, nullptr);
+      return 0;
+    }
+    const long long nc = (long long)n * Ec.n_warm;
     const dim3 fgrid((unsigned)b->cand_tiles, (unsigned)n);
     PCBA_CK(cudaMemsetAsync(b->d_cviol, 0, sizeof(unsigned) * (size_t)nc, s));
     k_cand_cost<<<(unsigned)std::min<long long>((nc + 255) / 256, 8LL * b->g.sms), 256, 0, s>>>(
-        E1, b->d_ckey);
-    k_cand_rank<<<n, PCBA_TPB, 0, s>>>(E1, b->d_ckey, b->d_corder, b->d_cres);
-    k_cand_feas<<<fgrid, 256, cand_smem, s>>>(E1, b->d_ckey, b->d_corder, b->d_cres, b->d_cviol,
+        Ec, b->d_ckey);
+    k_cand_rank<<<n, PCBA_TPB, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres);
+    k_cand_feas<<<fgrid, 256, cand_smem, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres, b->d_cviol,
                                               b->cand_cmax, 0, head);
     b->extra_launches += 3;
-    if (head < E1.n_warm) {
-      k_cand_check<<<n, 128, 0, s>>>(E1, b->d_ckey, b->d_corder, b->d_cviol, b->d_cres, head);
-      k_cand_feas<<<fgrid, 256, cand_smem, s>>>(E1, b->d_ckey, b->d_corder, b->d_cres,
-                                                b->d_cviol, b->cand_cmax, head, E1.n_warm);
+    if (head < Ec.n_warm) {
+      k_cand_check<<<n, 128, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cviol, b->d_cres, head);
+      k_cand_feas<<<fgrid, 256, cand_smem, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres,
+                                                b->d_cviol, b->cand_cmax, head, Ec.n_warm);
       b->extra_launches += 2;
     }
-    k_cand_pick<<<n, PCBA_TPB, 0, s>>>(E1, b->d_ckey, b->d_corder, b->d_cviol);
+    k_cand_pick<<<n, PCBA_TPB, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cviol);
+    return 0;
+  };
+  if (guide || warm) {
+    int rc = certify(E1);
+    if (rc) return rc;
+    if (guide && b->refine_n > 0) {
+      // second round: a finer stencil around each problem's seed (the centre
+      // row of zeros keeps the first seed among the candidates)
+      PCBA_CK(cudaMemcpyAsync(b->d_stencil, b->refine.data(),
+                              sizeof(double) * b->refine_n * b->refine_dim,
+                              cudaMemcpyHostToDevice, s));
+      const long long nc = (long long)n * b->refine_n;
+      k_candidates<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(
+          E1, guide->guess, b->refine_dim, b->d_stencil, b->refine_n, b->d_cand, 1);
+      Engine E2 = E1;
+      E2.n_warm = b->refine_n;
+      b->extra_launches += 2;  // k_candidates; the certification replaces nothing
+      rc = certify(E2);
+      if (rc) return rc;
+    }
   } else {
     k_eval<<<n, PCBA_TPB, 0, s>>>(E1, 0, nullptr);
   }
@@ -1157,25 +1184,28 @@ int pcba_batch_solve_guided(pcba_batch* b, double opt_tol, double eq_tol, int ma
     return fail(PCBA_ERR_INVALID, "n_stencil must be in [1, 1024]");
   for (long long i = 0; i < (long long)n_stencil * guess_dim; ++i)
     if (!std::isfinite(stencil[i])) return fail(PCBA_ERR_INVALID, "stencil must be finite");
-  if (b->cand_cap < n_stencil) {
+  const int n_cap = std::max(n_stencil, b->refine_n);
+  if (b->refine_n > 0 && b->refine_dim != guess_dim)
+    return fail(PCBA_ERR_INVALID, "refinement stencil and guess dimensions differ");
+  if (b->cand_cap < n_cap) {
     if (b->d_cand) cudaFree(b->d_cand);
     b->d_cand = nullptr;
     b->cand_cap = 0;
-    if (cudaMalloc((void**)&b->d_cand, sizeof(double) * PCBA_MAXD * (size_t)b->np * n_stencil) !=
+    if (cudaMalloc((void**)&b->d_cand, sizeof(double) * PCBA_MAXD * (size_t)b->np * n_cap) !=
         cudaSuccess)
       return fail(PCBA_ERR_OOM, "candidate buffer allocation failed");
-    b->cand_cap = n_stencil;
+    b->cand_cap = n_cap;
   }
-  if (b->stencil_cap < (long long)n_stencil * guess_dim) {
+  if (b->stencil_cap < (long long)n_cap * guess_dim) {
     if (b->d_stencil) cudaFree(b->d_stencil);
     b->d_stencil = nullptr;
     b->stencil_cap = 0;
-    if (cudaMalloc((void**)&b->d_stencil, sizeof(double) * (size_t)n_stencil * guess_dim) !=
+    if (cudaMalloc((void**)&b->d_stencil, sizeof(double) * (size_t)n_cap * guess_dim) !=
         cudaSuccess)
       return fail(PCBA_ERR_OOM, "stencil buffer allocation failed");
-    b->stencil_cap = (long long)n_stencil * guess_dim;
+    b->stencil_cap = (long long)n_cap * guess_dim;
   }
-  if (b->ckey_cap < n_stencil) {
+  if (b->ckey_cap < n_cap) {
     if (b->d_ckey) cudaFree(b->d_ckey);
     if (b->d_cviol) cudaFree(b->d_cviol);
     if (b->d_corder) cudaFree(b->d_corder);
@@ -1183,15 +1213,34 @@ int pcba_batch_solve_guided(pcba_batch* b, double opt_tol, double eq_tol, int ma
     b->d_cviol = nullptr;
     b->d_corder = nullptr;
     b->ckey_cap = 0;
-    if (cudaMalloc((void**)&b->d_ckey, sizeof(float) * (size_t)b->np * n_stencil) != cudaSuccess ||
-        cudaMalloc((void**)&b->d_cviol, sizeof(unsigned) * (size_t)b->np * n_stencil) !=
+    if (cudaMalloc((void**)&b->d_ckey, sizeof(float) * (size_t)b->np * n_cap) != cudaSuccess ||
+        cudaMalloc((void**)&b->d_cviol, sizeof(unsigned) * (size_t)b->np * n_cap) !=
             cudaSuccess ||
-        cudaMalloc((void**)&b->d_corder, sizeof(int) * (size_t)b->np * n_stencil) != cudaSuccess)
+        cudaMalloc((void**)&b->d_corder, sizeof(int) * (size_t)b->np * n_cap) != cudaSuccess)
       return fail(PCBA_ERR_OOM, "candidate key allocation failed");
-    b->ckey_cap = n_stencil;
+    b->ckey_cap = n_cap;
   }
   const Guide g{d_guess, guess_dim, stencil, n_stencil};
   return batch_solve_impl(b, nullptr, opt_tol, eq_tol, max_iters, 0, nullptr, out, false, &g);
+}
+
+int pcba_batch_set_refine_stencil(pcba_batch* b, const double* stencil, int n_stencil,
+                                  int guess_dim) {
+  if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
+  if (n_stencil == 0) {
+    b->refine.clear();
+    b->refine_n = 0;
+    b->refine_dim = 0;
+    return 0;
+  }
+  if (!stencil || n_stencil < 0 || n_stencil > 1024 || guess_dim < 1 || guess_dim > PCBA_MAX_DIM)
+    return fail(PCBA_ERR_INVALID, "refinement stencil: 1..1024 rows of 1..8 values");
+  for (long long i = 0; i < (long long)n_stencil * guess_dim; ++i)
+    if (!std::isfinite(stencil[i])) return fail(PCBA_ERR_INVALID, "stencil must be finite");
+  b->refine.assign(stencil, stencil + (size_t)n_stencil * guess_dim);
+  b->refine_n = n_stencil;
+  b->refine_dim = guess_dim;
+  return 0;
 }
 
 int pcba_batch_upload(pcba_batch* b, const double* host_coeffs) {

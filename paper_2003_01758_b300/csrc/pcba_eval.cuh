@@ -595,19 +595,27 @@ __global__ void __launch_bounds__(PCBA_TPB) k_cost_grid(Engine E, int G, float* 
 // Candidate points of guided solves: candidate c of problem p is the guess of
 // p (normalised coordinates, guess_dim axes) plus stencil row c, clamped to
 // [-1, 1] and mapped to the box; axes beyond guess_dim take the box centre.
+// refine = 1: the centre is the seed already chosen for the problem (its
+// normalised coordinates), or the guess where no candidate was certified.
 __global__ void k_candidates(Engine E, const float* guess, int guess_dim, const double* stencil,
-                             int n_stencil, double* cand) {
+                             int n_stencil, double* cand, int refine) {
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (long long)E.np * n_stencil) return;
   const int p = (int)(t / n_stencil), c = (int)(t - (long long)p * n_stencil);
   const ProbDesc* D = E.desc + p;
+  const ProbState* S = E.state + p;
+  const bool from_seed = refine && S->seeded;
   double* o = cand + t * PCBA_MAXD;
   for (int r = 0; r < PCBA_MAXD; ++r) {
     double x = 0.0;
     if (r < D->l) {
       double u = 0.0;
-      if (r < guess_dim)
-        u = (double)guess[(long long)p * guess_dim + r] + stencil[(long long)c * guess_dim + r];
+      if (r < guess_dim) {
+        const double centre =
+            from_seed ? 2.0 * (S->seed_x[r] - D->lo[r]) / (D->hi[r] - D->lo[r]) - 1.0
+                      : (double)guess[(long long)p * guess_dim + r];
+        u = centre + stencil[(long long)c * guess_dim + r];
+      }
       u = fmin(fmax(u, -1.0), 1.0);
       x = D->lo[r] + 0.5 * (u + 1.0) * (D->hi[r] - D->lo[r]);
     }

@@ -102,6 +102,7 @@ def lib():
         "pcba_batch_warm_point": ([P, I, P, P], I),
         "pcba_batch_cost_grid": ([P, I, P, I, I], I),
         "pcba_batch_upload": ([P, P], I),
+        "pcba_batch_set_refine_stencil": ([P, P, I, I], I),
         "pcba_mlp_kernel_launches": ([P], LL),
         "pcba_mlp_create": ([P, I, I, I, I, ctypes.c_ulonglong], I),
         "pcba_mlp_destroy": ([P], None),
@@ -130,7 +131,8 @@ def exported_symbols():
             "pcba_get_list", "pcba_root_patches", "pcba_item_bytes", "pcba_set_stream",
             "pcba_set_warm_start", "pcba_destroy", "pcba_status_string", "pcba_last_error",
             "pcba_version", "pcba_bernstein_convert_noalloc", "pcba_batch_solve_guided",
-            "pcba_batch_warm_point", "pcba_batch_cost_grid", "pcba_batch_upload", "pcba_mlp_kernel_launches",
+            "pcba_batch_warm_point", "pcba_batch_cost_grid", "pcba_batch_upload", "pcba_batch_set_refine_stencil",
+            "pcba_mlp_kernel_launches",
             "pcba_mlp_create", "pcba_mlp_destroy", "pcba_mlp_num_params", "pcba_mlp_set_params",
             "pcba_mlp_get_params", "pcba_mlp_forward", "pcba_mlp_gradient",
             "pcba_mlp_train_step"]
@@ -353,6 +355,14 @@ class Batch:
         if _check(lib().pcba_batch_warm_point(self._b, k, _p(x), ctypes.byref(c))) == 0:
             return None
         return (x[:self.solvers[k].l].copy(), c.value) if with_cost else x[:self.solvers[k].l].copy()
+
+    def set_refine_stencil(self, stencil, guess_dim=2):
+        """pcba_batch_set_refine_stencil (None or an empty array: off)."""
+        if stencil is None or len(stencil) == 0:
+            _check(lib().pcba_batch_set_refine_stencil(self._b, None, 0, guess_dim))
+            return
+        st = np.ascontiguousarray(stencil, dtype=np.float64).reshape(-1, guess_dim)
+        _check(lib().pcba_batch_set_refine_stencil(self._b, _p(st), st.shape[0], guess_dim))
 
     def upload(self, host_coeffs):
         """pcba_batch_upload: queue the host->device copy of all coefficients."""

@@ -32,11 +32,13 @@ def held_out(n, lo=64, hi=1024):
 
 def ab_compare(mlp, probs, mem_cap_total=64 << 30, repeats=3):
     """One batch solved three ways: cold (the plain solver), learned (network
-    guess + default stencil; device time includes the feature kernel and the
-    network's forward pass) and grid (a fixed 25 x 25 grid of candidates, no
+    guess + default stencil, then the refinement stencil around the seed;
+    device time includes the feature kernel and the network's forward pass) and
+    grid (a fixed 25 x 25 grid of candidates, then the same refinement, no
     network: what the learned arm must beat to be worth its training)."""
     b = pcba.Batch([pcba.solver_from_problem(p, pcba.FP32) for p in probs], mem_cap_total)
     stream = torch.cuda.Stream()
+    refine = warmstart.refine_stencil()
     b.set_stream(stream.cuda_stream)
     pk = warmstart.Packed(*warmstart.host_inputs(probs))
     zero = torch.zeros((len(probs), 2), dtype=torch.float32, device="cuda")
@@ -51,11 +53,13 @@ def ab_compare(mlp, probs, mem_cap_total=64 << 30, repeats=3):
                 if arm == "cold":
                     res = b.solve(opt_tol=1e-3)
                 elif arm == "learned":
+                    b.set_refine_stencil(refine)
                     b.cost_grid(warmstart.GRID, pk.glob.data_ptr(), warmstart.GLOBAL_DIM,
                                 warmstart.HOST_DIM)
                     y = warmstart.predict(mlp, pk, stream=stream.cuda_stream)
                     res = b.solve_guided(y.data_ptr(), 2, warmstart.default_stencil(), opt_tol=1e-3)
                 else:
+                    b.set_refine_stencil(refine)
                     res = b.solve_guided(zero.data_ptr(), 2, warmstart.grid_stencil(), opt_tol=1e-3)
                 e1.record(stream)
             e1.synchronize()

@@ -67,6 +67,14 @@ def default_stencil(half=8, step=0.02, radii=(0.25, 0.35, 0.5, 0.7), n_dir=16):
     return np.concatenate(rows).astype(np.float64)
 
 
+def refine_stencil(half=8, step=0.005):
+    """Second-round stencil (pcba_batch_set_refine_stencil): a (2 half + 1)^2
+    square of spacing step around the first seed, the seed itself included."""
+    k = np.arange(-half, half + 1) * step
+    a, b = np.meshgrid(k, k, indexing="ij")
+    return np.stack([a.ravel(), b.ravel()], axis=1)
+
+
 def grid_stencil(n=25):
     """Guess-free candidates: an n x n grid over the whole normalised box
     (used with a zero guess; the non-learned arm of the comparison)."""

@@ -259,3 +259,26 @@ def test_fp32_certification_never_accepts_an_infeasible_point(margin):
             assert seed is None
         else:
             assert seed is not None and np.array_equal(seed, x0)
+
+
+def test_refinement_never_worsens_the_seed():
+    """The second round around the seed (its stencil holds the centre) gives,
+    problem by problem, a seed at most as costly, and the solves stay certified."""
+    probs = [W.rtd(2600 + k, n_obstacles=n) for k, n in enumerate((512, 128, 300, 900))]
+    b = pcba.Batch([pcba.solver_from_problem(p, pcba.FP32) for p in probs], 16 << 30)
+    guess = torch.zeros((len(probs), 2), dtype=torch.float32, device="cuda")
+    st = warmstart.default_stencil()
+    b.solve_guided(guess.data_ptr(), 2, st)
+    first = [b.warm_point(k, with_cost=True) for k in range(len(probs))]
+    b.set_refine_stencil(warmstart.refine_stencil())
+    res = b.solve_guided(guess.data_ptr(), 2, st)
+    second = [b.warm_point(k, with_cost=True) for k in range(len(probs))]
+    for p, f, g, r in zip(probs, first, second, res):
+        assert r["status"] == pcba.OPTIMAL
+        if f is not None:
+            assert g is not None and g[1] <= f[1] + RANK_TOL * (1.0 + abs(f[1]))
+            assert oracle_values(p, g[0])[1] <= 1e-12
+            assert g[1] >= r["lower"] - 1e-9
+    with pytest.raises(pcba.PcbaError, match="dimensions"):
+        b.set_refine_stencil(np.zeros((3, 1)), guess_dim=1)
+        b.solve_guided(guess.data_ptr(), 2, st)
