@@ -100,15 +100,17 @@ int pcba_batch_solve_guided(pcba_batch* b, double opt_tol, double eq_tol, int ma
                             const float* d_guess, int guess_dim, const double* stencil,
                             int n_stencil, pcba_result* out);
 
-/* Refinement of guided solves: after the first round of candidates, a second
- * round around each problem's seed (its normalised coordinates; the guess where
- * no candidate was certified): candidate c = centre + stencil row c, clamped,
- * certified and picked the same way.  Include a row of zeros so that the first
- * seed stays a candidate (the seed then never gets worse).  n_stencil = 0
- * turns the refinement off; otherwise 1..1024 rows of guess_dim values (the
- * guess_dim of the guided solves).  The library keeps a copy. */
-int pcba_batch_set_refine_stencil(pcba_batch* b, const double* stencil, int n_stencil,
-                                  int guess_dim);
+/* Refinement of guided solves: after the first round of candidates, up to
+ * four more rounds, each around each problem's current seed (its normalised
+ * coordinates; the guess where no candidate was certified yet): candidate
+ * c = centre + stencil row c, clamped, certified and picked the same way.
+ * Include a row of zeros so that the seed stays a candidate (it then never
+ * gets worse).  round: 0..3, at most one past the last round set; n_stencil =
+ * 0 removes this round and the later ones; otherwise 1..1024 rows of
+ * guess_dim values (the guess_dim of the guided solves, the same for every
+ * round).  The library keeps a copy. */
+int pcba_batch_set_refine_stencil(pcba_batch* b, int round, const double* stencil,
+                                  int n_stencil, int guess_dim);
 
 /* Queues the copy of every problem's monomial coefficients (the layout of
  * pcba_batch_solve_from_host, pcba_batch_input_doubles of them) from host

@@ -139,8 +139,20 @@ struct pcba_batch {
   int cand_cmax = 0, cand_tiles = 1;  // largest constraint patch, constraint tiles of 32
   double* d_stencil = nullptr;  // guided solves: [stencil_cap] doubles
   long long cand_cap = 0, stencil_cap = 0;
-  std::vector<double> refine;   // refinement stencil of guided solves (host copy)
-  int refine_n = 0, refine_dim = 0;
+  // refinement rounds of guided solves (host copies of their stencils)
+  std::vector<std::vector<double>> refine;
+  std::vector<int> refine_rows;
+  int refine_dim = 0;
+  long long refine_total() const {
+    long long t = 0;
+    for (int r : refine_rows) t += r;
+    return t;
+  }
+  int refine_max() const {
+    int m = 0;
+    for (int r : refine_rows) m = std::max(m, r);
+    return m;
+  }
   long long trace_rows_total = 0;
   // host mirrors (pinned)
   ProbState* h_state = nullptr;
@@ -826,7 +838,7 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   b->h2d_bytes = (long long)sizeof(SolveParams) + (host_coeffs ? 8LL * b->mono_doubles : 0) +
                  (warm ? 8LL * PCBA_MAXD * n : 0) +
                  (guide ? 8LL * guide->n * guide->dim : 0) +
-                 (guide && b->refine_n > 0 ? 8LL * b->refine_n * b->refine_dim : 0) + b->pending_h2d;
+                 (guide ? 8LL * b->refine_total() * b->refine_dim : 0) + b->pending_h2d;
   b->pending_h2d = 0;
   b->extra_launches = (guide || warm ? 1 : 0) + (guide ? 1 : 0);
   b->d2h_bytes = (long long)(sizeof(ProbState) + sizeof(EvalOut)) * n + (long long)sizeof(Plan);
@@ -891,18 +903,18 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   if (guide || warm) {
     int rc = certify(E1);
     if (rc) return rc;
-    if (guide && b->refine_n > 0) {
-      // second round: a finer stencil around each problem's seed (the centre
-      // row of zeros keeps the first seed among the candidates)
-      PCBA_CK(cudaMemcpyAsync(b->d_stencil, b->refine.data(),
-                              sizeof(double) * b->refine_n * b->refine_dim,
-                              cudaMemcpyHostToDevice, s));
-      const long long nc = (long long)n * b->refine_n;
+    for (size_t rd = 0; guide && rd < b->refine.size(); ++rd) {
+      // a finer stencil around each problem's seed (the centre row of zeros
+      // keeps the previous seed among the candidates)
+      const int rn = b->refine_rows[rd];
+      PCBA_CK(cudaMemcpyAsync(b->d_stencil, b->refine[rd].data(),
+                              sizeof(double) * rn * b->refine_dim, cudaMemcpyHostToDevice, s));
+      const long long nc = (long long)n * rn;
       k_candidates<<<(unsigned)((nc + 255) / 256), 256, 0, s>>>(
-          E1, guide->guess, b->refine_dim, b->d_stencil, b->refine_n, b->d_cand, 1);
+          E1, guide->guess, b->refine_dim, b->d_stencil, rn, b->d_cand, 1);
       Engine E2 = E1;
-      E2.n_warm = b->refine_n;
-      b->extra_launches += 2;  // k_candidates; the certification replaces nothing
+      E2.n_warm = rn;
+      b->extra_launches += 1;
       rc = certify(E2);
       if (rc) return rc;
     }
@@ -1184,8 +1196,8 @@ int pcba_batch_solve_guided(pcba_batch* b, double opt_tol, double eq_tol, int ma
     return fail(PCBA_ERR_INVALID, "n_stencil must be in [1, 1024]");
   for (long long i = 0; i < (long long)n_stencil * guess_dim; ++i)
     if (!std::isfinite(stencil[i])) return fail(PCBA_ERR_INVALID, "stencil must be finite");
-  const int n_cap = std::max(n_stencil, b->refine_n);
-  if (b->refine_n > 0 && b->refine_dim != guess_dim)
+  const int n_cap = std::max(n_stencil, b->refine_max());
+  if (!b->refine.empty() && b->refine_dim != guess_dim)
     return fail(PCBA_ERR_INVALID, "refinement stencil and guess dimensions differ");
   if (b->cand_cap < n_cap) {
     if (b->d_cand) cudaFree(b->d_cand);
@@ -1224,21 +1236,26 @@ int pcba_batch_solve_guided(pcba_batch* b, double opt_tol, double eq_tol, int ma
   return batch_solve_impl(b, nullptr, opt_tol, eq_tol, max_iters, 0, nullptr, out, false, &g);
 }
 
-int pcba_batch_set_refine_stencil(pcba_batch* b, const double* stencil, int n_stencil,
-                                  int guess_dim) {
+int pcba_batch_set_refine_stencil(pcba_batch* b, int round, const double* stencil,
+                                  int n_stencil, int guess_dim) {
   if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
+  if (round < 0 || round >= 4 || round > (int)b->refine.size())
+    return fail(PCBA_ERR_INVALID, "refinement round must be in [0, 4) and follow the set ones");
   if (n_stencil == 0) {
-    b->refine.clear();
-    b->refine_n = 0;
-    b->refine_dim = 0;
+    b->refine.resize((size_t)round);
+    b->refine_rows.resize((size_t)round);
     return 0;
   }
   if (!stencil || n_stencil < 0 || n_stencil > 1024 || guess_dim < 1 || guess_dim > PCBA_MAX_DIM)
     return fail(PCBA_ERR_INVALID, "refinement stencil: 1..1024 rows of 1..8 values");
+  if (round > 0 && guess_dim != b->refine_dim)
+    return fail(PCBA_ERR_INVALID, "refinement rounds must share the guess dimension");
   for (long long i = 0; i < (long long)n_stencil * guess_dim; ++i)
     if (!std::isfinite(stencil[i])) return fail(PCBA_ERR_INVALID, "stencil must be finite");
-  b->refine.assign(stencil, stencil + (size_t)n_stencil * guess_dim);
-  b->refine_n = n_stencil;
+  b->refine.resize((size_t)round + 1);
+  b->refine_rows.resize((size_t)round + 1);
+  b->refine[(size_t)round].assign(stencil, stencil + (size_t)n_stencil * guess_dim);
+  b->refine_rows[(size_t)round] = n_stencil;
   b->refine_dim = guess_dim;
   return 0;
 }

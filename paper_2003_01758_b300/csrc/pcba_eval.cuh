@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* res
     }
 
   // ---- check them in rank order
-  const float eq_tol = (float)E.params->eq_tol;
+  const float eq_tol = __double2float_rd(E.params->eq_tol);  // never above eq_tol
   int chosen = -1;  // thread 0: chunk slot of the chosen candidate
   for (int c0 = 0; c0 < n_c; c0 += PCBA_EVAL_CHUNK) {
     const int nc = min(PCBA_EVAL_CHUNK, n_c - c0);
@@ -491,7 +491,7 @@ __global__ void __launch_bounds__(256) k_cand_feas(Engine E, const float* key, c
     sx[t] = (float)E.warm[(base + c) * PCBA_MAXD + r];
   }
   __syncthreads();
-  const float eq_tol = (float)E.params->eq_tol;
+  const float eq_tol = __double2float_rd(E.params->eq_tol);  // never above eq_tol
   for (int t = threadIdx.x; t < nr * nq; t += blockDim.x) {
     const int rr = t / nq, qi = t - rr * nq;
     const int rank = r0 + rr;
@@ -500,8 +500,22 @@ __global__ void __launch_bounds__(256) k_cand_feas(Engine E, const float* key, c
     const bool is_g = q < D->alpha;
     float val, err;
     horner_f32(sa + qi * cmax, l, is_g ? D->G : D->H, sx + rr * l, &val, &err);
-    if (!(__fadd_ru(is_g ? val : fabsf(val), err) <= (is_g ? 0.0f : eq_tol)))
-      viol[base + rank] = 1u;
+    const float lim = is_g ? 0.0f : eq_tol;
+    if (__fadd_ru(is_g ? val : fabsf(val), err) <= lim) continue;  // certified in FP32
+    bool bad = true;
+    if (__fsub_rd(is_g ? val : fabsf(val), err) <= lim) {
+      // undecided in FP32 (the point is within the bound of the limit): decide
+      // in FP64 on the FP64 coefficients at the same (FP32) point
+      double xd[PCBA_MAXD];
+      for (int r = 0; r < l; ++r) xd[r] = (double)sx[rr * l + r];
+      const double* a = is_g ? E.mono + D->mono_off + D->cp + (long long)q * D->cg
+                             : E.mono + D->mono_off + D->cp + (long long)D->alpha * D->cg +
+                                   (long long)(q - D->alpha) * D->ch;
+      double v64, e64;
+      horner_f64(a, l, is_g ? D->G : D->H, xd, &v64, &e64);
+      bad = !(__dadd_ru(is_g ? v64 : fabs(v64), e64) <= (is_g ? 0.0 : E.params->eq_tol));
+    }
+    if (bad) viol[base + rank] = 1u;
   }
 }
 

@@ -102,7 +102,7 @@ def lib():
         "pcba_batch_warm_point": ([P, I, P, P], I),
         "pcba_batch_cost_grid": ([P, I, P, I, I], I),
         "pcba_batch_upload": ([P, P], I),
-        "pcba_batch_set_refine_stencil": ([P, P, I, I], I),
+        "pcba_batch_set_refine_stencil": ([P, I, P, I, I], I),
         "pcba_mlp_kernel_launches": ([P], LL),
         "pcba_mlp_create": ([P, I, I, I, I, ctypes.c_ulonglong], I),
         "pcba_mlp_destroy": ([P], None),
@@ -356,13 +356,21 @@ class Batch:
             return None
         return (x[:self.solvers[k].l].copy(), c.value) if with_cost else x[:self.solvers[k].l].copy()
 
-    def set_refine_stencil(self, stencil, guess_dim=2):
-        """pcba_batch_set_refine_stencil (None or an empty array: off)."""
+    def set_refine_stencil(self, stencil, guess_dim=2, round=0):
+        """pcba_batch_set_refine_stencil for one round (None or an empty array
+        removes this round and the later ones)."""
         if stencil is None or len(stencil) == 0:
-            _check(lib().pcba_batch_set_refine_stencil(self._b, None, 0, guess_dim))
+            _check(lib().pcba_batch_set_refine_stencil(self._b, round, None, 0, guess_dim))
             return
         st = np.ascontiguousarray(stencil, dtype=np.float64).reshape(-1, guess_dim)
-        _check(lib().pcba_batch_set_refine_stencil(self._b, _p(st), st.shape[0], guess_dim))
+        _check(lib().pcba_batch_set_refine_stencil(self._b, round, _p(st), st.shape[0],
+                                                   guess_dim))
+
+    def set_refine_stencils(self, stencils, guess_dim=2):
+        """All refinement rounds at once (an empty list: none)."""
+        self.set_refine_stencil(None, guess_dim, 0)
+        for r, st in enumerate(stencils):
+            self.set_refine_stencil(st, guess_dim, r)
 
     def upload(self, host_coeffs):
         """pcba_batch_upload: queue the host->device copy of all coefficients."""
