@@ -44,6 +44,7 @@ EQ_TOL = 1e-4
 MAX_ITERS = 28
 BASE_SEED = 2000
 MEM_CAP = 64 << 30
+UNEVEN_MEM = 200 << 30   # list memory shared by the 256 problems of the uneven batch
 WORKLOAD = ("rtd-shaped POPs: l=2 on [-1,1]^2, F degree (3,3) N(0,0.5^2), %d obstacles "
             "U([-2,2]^2) r=0.15, constraints degree (6,6), cost ||F-goal||^2; batch of %d "
             "problems per GPU (seeds %d+%d*rank+j); FP32 patches with directed-rounding "
@@ -448,6 +449,10 @@ def main():
     fp64_value = len(seeds) * len(ms64) / (sum(ms64) / 1e3)
     b64.close()
 
+    # the main batch's list memory is not needed any more
+    batch.close()
+    torch.cuda.synchronize()
+
     # ---- uneven batch: 256 problems, obstacle counts log-uniform in [16, 4096] ----
     uneven = None
     if rank == 0 and world == 1:
@@ -455,11 +460,12 @@ def main():
         counts = W.batch_obstacle_counts(256, 4000)
         up = [W.rtd(4000 + k, n_obstacles=int(c)) for k, c in enumerate(counts)]
         ub = pcba.Batch([pcba.Solver(q.cost, q.ineq, q.eq, q.lo, q.hi, precision=pcba.FP32)
-                         for q in up], 160 << 30)
+                         for q in up], UNEVEN_MEM)
         tune = ub.autotune(OPT_TOL, EQ_TOL, MAX_ITERS)
         ums, utimes, ustatus = timed_steps(ub, 3, flush)
         uneven = {"workload": "256 rtd problems, obstacles floor(exp U(ln 16, ln 4096)), "
-                              "seeds 4000+k, FP32, one batched solve per step",
+                              "seeds 4000+k, FP32, one batched solve per step, %d GiB of list "
+                              "memory shared (equal item capacity)" % (UNEVEN_MEM >> 30),
                   "value": 256 * len(ums) / (sum(ums) / 1e3), "unit": UNIT,
                   "ms_per_step": float(np.mean(ums)),
                   "p50_ms": float(np.median(utimes)), "p99_ms": float(np.percentile(utimes, 99)),
