@@ -22,9 +22,10 @@
 //                             the keep flags; the last tile of each problem runs
 //                             the stopping tests (Alg. 1 lines 4, 8, 9, 11) and
 //                             the last tile overall plans the next step.
-//   k4_index / k4_move        Alg. 5 (reading R11): the j-th hole below K_save
-//                             receives the item at save position K_save-1-j.
-//   k_control                 device-side loop control (graph conditional).
+//   k4_index / k_move_control Alg. 5 (reading R11) on the slot map: the j-th
+//                             hole below K_save receives the slot of the item at
+//                             save position K_save-1-j; the last block then runs
+//                             the device-side loop control (graph conditional).
 //   k_eval                    warm start: certified candidate points seed p_up
 //                             (FP32 with error bounds); final check of the
 //                             returned point in FP64 with an error bound.
@@ -713,7 +714,6 @@ __device__ __forceinline__ void move_phase(const Engine& E) {
   }
 }
 
-__global__ void __launch_bounds__(PCBA_TPB) k4_move(Engine E) { move_phase(E); }
 
 // ---------------------------------------------------------------------------
 // loop control, init, evaluation
@@ -762,10 +762,6 @@ __device__ __forceinline__ void control_phase(const Engine& E, cudaGraphConditio
   }
 }
 
-__global__ void k_control(Engine E, cudaGraphConditionalHandle handle, int use_graph) {
-  __shared__ int s_code, s_run;
-  control_phase(E, handle, use_graph, s_code, s_run);
-}
 
 // Alg. 5 on the slot map, then the loop control in the last block to finish.
 __global__ void __launch_bounds__(PCBA_TPB) k_move_control(Engine E,
