@@ -1,13 +1,15 @@
 // libpcba: host engine and C ABI (see include/pcba.h).
 //
 // A solve of n problems runs as:
-//   prologue  k1_matrices, k1_convert (Alg. 1 line 1), k_eval (warm start),
-//             k_init (Alg. 1 lines 2-3, first memory test)
-//   loop      k2_subdivide, k3_classify, k4_index, k4_move, k_control, one
-//             bisection step of every running problem per iteration
+//   prologue  k1_matrices, k1_convert (Alg. 1 line 1), the warm start
+//             (k_mono32, k_candidates, k_cand_* or k_eval), k_init (Alg. 1
+//             lines 2-3, first memory test)
+//   loop      the subdivision kernel, then k_refresh (FP32, forked stream)
+//             beside k_pup, k3_classify and k4_index, then k_move_control:
+//             one bisection step of every running problem per iteration
 //             (Alg. 1 lines 4-11); by default the loop is a CUDA graph with a
-//             conditional WHILE node whose condition k_control sets on the
-//             device, so the host never waits inside the loop
+//             conditional WHILE node whose condition the loop control sets on
+//             the device, so the host never waits inside the loop
 //   epilogue  k_eval (FP64 check of the returned point), copies to the host.
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -343,7 +345,7 @@ void launch_k2(const pcba_batch* b, cudaStream_t s) {
 // The kernels of one device-loop iteration after the subdivision: the FP32
 // refresh of the patches it marked runs on a side stream beside k_pup,
 // k3_classify and k4_index (which read only the child records) and joins
-// before k4_move moves items.
+// before k_move_control updates the slot map.
 template <typename T>
 int launch_after_k2(pcba_batch* b, cudaStream_t s, int use_graph) {
   const Grids& g = b->g;
@@ -482,7 +484,7 @@ int setup_kernels(pcba_batch* b) {
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_classify, PCBA_TPB, 0));
   g.k3_grid = std::max(1, occ) * g.sms;
 
-  PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k4_move, PCBA_TPB, 0));
+  PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_move_control, PCBA_TPB, 0));
   g.k4_grid = std::max(1, occ) * g.sms;
   return 0;
 }

@@ -121,7 +121,7 @@ struct Plan {
   unsigned mark_count[2];  // marked patches appended by the subdivision of even / odd steps
   unsigned long long marks_total, refreshed_total;
   unsigned k3_done;
-  unsigned k4_done;             // blocks of k4_move finished (the last one runs the control)
+  unsigned k4_done;             // blocks of k_move_control finished (the last one runs the control)
   int any_running;
   int steps_global;
   int guard_hit;

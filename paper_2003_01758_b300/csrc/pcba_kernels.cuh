@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(128) k1_convert(Engine E, const double* mat, i
 // is the FP64 conversion bound plus one rounding to FP32.  Unmarked patches
 // keep their (larger, still valid) bound.  It runs beside k_pup, k3_classify
 // and k4_index, which read only the child records, and must finish before
-// k4_move moves items; the child boxes come from the state snapshot
+// k_move_control updates the slot map; the child boxes come from the state snapshot
 // child_level, which those kernels do not change.
 //
 // One warp per marked patch; the per-axis matrices of the item's box are
