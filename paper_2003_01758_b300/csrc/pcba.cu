@@ -75,6 +75,7 @@ struct HostProblem {
 
 struct Grids {
   int nmax = 16;  // degree class of the subdivision kernel (4, 8 or 16)
+  int nfix = 0;   // every patch of the batch has this degree on every axis (4 or 6), else 0
   bool tma = false;  // TMA-staged subdivision kernel
   int tma_wpb = 8, tma_stages = 2, tma_stage_elems = 0, tma_cpmax = 1;
   size_t tma_smem = 0;
@@ -321,20 +322,32 @@ void free_batch(pcba_batch* b) {
   delete b;
 }
 
+// The TMA subdivision kernel instantiation for a degree class / fixed degree.
+template <typename T>
+const void* tma_kernel(int nmax, int nfix) {
+  if (nfix == 6) return (const void*)k2_subdivide_tma<T, 8, 6>;
+  if (nfix == 4) return (const void*)k2_subdivide_tma<T, 4, 4>;
+  if (nmax <= 4) return (const void*)k2_subdivide_tma<T, 4>;
+  if (nmax <= 8) return (const void*)k2_subdivide_tma<T, 8>;
+  return (const void*)k2_subdivide_tma<T, 16>;
+}
+
 template <typename T>
 void launch_k2(const pcba_batch* b, cudaStream_t s) {
   const Grids& g = b->g;
   if (g.tma) {
     const dim3 blk(32 * g.tma_wpb);
-    if (g.nmax <= 4)
-      k2_subdivide_tma<T, 4><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, g.tma_stages,
-                                                                 g.tma_stage_elems, g.tma_cpmax);
+    const int st = g.tma_stages, se = g.tma_stage_elems, cp = g.tma_cpmax;
+    if (g.nfix == 6)
+      k2_subdivide_tma<T, 8, 6><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, st, se, cp);
+    else if (g.nfix == 4)
+      k2_subdivide_tma<T, 4, 4><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, st, se, cp);
+    else if (g.nmax <= 4)
+      k2_subdivide_tma<T, 4><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, st, se, cp);
     else if (g.nmax <= 8)
-      k2_subdivide_tma<T, 8><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, g.tma_stages,
-                                                                 g.tma_stage_elems, g.tma_cpmax);
+      k2_subdivide_tma<T, 8><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, st, se, cp);
     else
-      k2_subdivide_tma<T, 16><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, g.tma_stages,
-                                                                  g.tma_stage_elems, g.tma_cpmax);
+      k2_subdivide_tma<T, 16><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, st, se, cp);
     return;
   }
   if (g.nmax <= 4) k2_subdivide<T, 4><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
@@ -401,6 +414,23 @@ int setup_kernels(pcba_batch* b) {
   for (const ProbDesc& d : b->desc)
     for (int r = 0; r < d.l; ++r) dmax = std::max(dmax, std::max(d.P[r], std::max(d.G[r], d.H[r])));
   g.nmax = dmax <= 4 ? 4 : (dmax <= 8 ? 8 : 16);
+  {
+    // a single degree on every axis of every patch of the batch: fixed-degree kernel
+    int fixed = -1;
+    bool uniform = true;
+    auto see = [&](int n) {
+      if (fixed < 0) fixed = n;
+      else if (fixed != n) uniform = false;
+    };
+    for (const ProbDesc& d : b->desc)
+      for (int r = 0; r < d.l; ++r) {
+        see(d.P[r]);
+        if (d.alpha > 0) see(d.G[r]);
+        if (d.beta > 0) see(d.H[r]);
+      }
+    g.nfix = (uniform && (fixed == 4 || fixed == 6) && !std::getenv("PCBA_NO_FIXED_DEGREE"))
+                 ? fixed : 0;
+  }
   g.k2_smem = (size_t)(2 * cpmax) * sizeof(T);
   const void* k2 = g.nmax == 4 ? (const void*)k2_subdivide<T, 4>
                                : (g.nmax == 8 ? (const void*)k2_subdivide<T, 8>
@@ -426,9 +456,7 @@ int setup_kernels(pcba_batch* b) {
     const size_t head_cap = ((size_t)64 + (size_t)cpmax * sizeof(T) + 32 + 127) / 128 * 128;
     const size_t stage_bytes = (size_t)g.tma_stage_elems * sizeof(T) + 128 + head_cap;
     const int cand[][2] = {{8, 2}, {8, 3}, {4, 2}, {4, 3}, {2, 2}};
-    const void* kt = g.nmax == 4 ? (const void*)k2_subdivide_tma<T, 4>
-                                 : (g.nmax == 8 ? (const void*)k2_subdivide_tma<T, 8>
-                                                : (const void*)k2_subdivide_tma<T, 16>);
+    const void* kt = tma_kernel<T>(g.nmax, g.nfix);
     size_t smem_max = 0;
     for (const auto& c : cand) {
       const size_t wb = ((size_t)c[1] * stage_bytes + 2 * (size_t)cpmax * sizeof(T) + 127) / 128 * 128;

@@ -128,6 +128,19 @@ __device__ __forceinline__ void dispatch_degree(int n, F&& f) {
   }
 }
 
+// With NFIX > 0 every patch of the batch has degree NFIX along every axis: the
+// kernel is built for that degree only (a smaller body for the instruction
+// cache); NFIX = 0 dispatches on n at run time.
+template <int NMAX, int NFIX, typename F>
+__device__ __forceinline__ void dispatch_fixed(int n, F&& f) {
+  if constexpr (NFIX > 0) {
+    (void)n;
+    f(std::integral_constant<int, NFIX>{});
+  } else {
+    dispatch_degree<NMAX>(n, f);
+  }
+}
+
 __device__ __forceinline__ int axis_stride(const int* deg, int l, int r) {
   int s = 1;
   for (int q = r + 1; q < l; ++q) s *= deg[q] + 1;
@@ -212,7 +225,7 @@ __device__ __forceinline__ void warp_max_d(double (&v)[NV]) {
 // all accumulated with upward rounding.
 // head: where the parent's head bytes (box, meta, cost) are read from: the
 // parent item itself, or a shared-memory copy of them.
-template <typename T, int NMAX>
+template <typename T, int NMAX, int NFIX = 0>
 __device__ void cost_part(const ProbDesc* D, const char* head, char* parent, char* right, int r,
                           ChildRec* recL, ChildRec* recR, T* stage, const MarkCtx& mk,
                           double cost_thr) {
@@ -236,7 +249,7 @@ __device__ void cost_part(const ProbDesc* D, const char* head, char* parent, cha
   for (int f = lane; f < nf; f += 32) {
     const int o = f / stride;
     const int base = o * blk + (f - o * stride);
-    dispatch_degree<NMAX>(n, [&](auto nc) {
+    dispatch_fixed<NMAX, NFIX>(n, [&](auto nc) {
       cost_fibre<T, decltype(nc)::value>(src, sL, sR, base, stride, v);
     });
   }
@@ -765,7 +778,7 @@ __device__ __forceinline__ void publish_bounds(int fam, bool any_valid, T (&v)[6
 // in flight (TMA, completion on an mbarrier).  Group 0 also splits the cost
 // patch and the box, whose bytes (box, meta, cost) come with the same copy.
 // The kernel only streams: no fence and no value-returning atomic on the way.
-template <typename T, int NMAX>
+template <typename T, int NMAX, int NFIX = 0>
 __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, int stage_elems,
                                                         int cpmax) {
   constexpr bool RIG = sizeof(T) == 4;
@@ -872,8 +885,8 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
     }
     if (w.g == 0) {
       const unsigned char* head = st + (size_t)stage_elems * sizeof(T) + 128;
-      cost_part<T, NMAX>(D, (const char*)head, parent, right, r, recL, recR, cost_stage, mk,
-                         cost_thr);
+      cost_part<T, NMAX, NFIX>(D, (const char*)head, parent, right, r, recL, recR, cost_stage,
+                               mk, cost_thr);
       if (lane == 0) {
         E.map[cx_slot + w.k + K] = rslot;
         const unsigned* iP = (const unsigned*)head;
@@ -905,7 +918,7 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
         a.m = T(0);
         T* gL = (T*)(parent + off) + i;
         T* gR = (T*)(right + off) + i;
-        dispatch_degree<NMAX>(n, [&](auto nc) {
+        dispatch_fixed<NMAX, NFIX>(n, [&](auto nc) {
           staged_fibres<T, decltype(nc)::value, RIG>(stage, gL, gR, pad, C, stride, lane, a);
         });
         T loL, hiL, loR, hiR;
