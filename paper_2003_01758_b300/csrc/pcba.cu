@@ -900,8 +900,8 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   k1_matrices<<<(nmat + 255) / 256, 256, 0, s>>>(E1, b->d_mat);
   k1_convert<T><<<b->g.k1_grid, 32 * b->g.k1_wpb, b->g.k1_smem, s>>>(E1, b->d_mat, b->g.k1_cmax,
                                                                    b->g.k1_wpb);
-  // ranks [0, head) are certified first; the rest only for problems that
-  // found no feasible candidate among them
+  // ranks [0, head) are certified first; later ranks only for problems that
+  // found no feasible candidate among the earlier ones
   auto certify = [&](const Engine& Ec) -> int {
     const int head = std::min(Ec.n_warm, 32);
     const size_t cand_smem = sizeof(float) * ((size_t)32 * b->cand_cmax +
@@ -921,11 +921,15 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
     k_cand_feas<<<fgrid, 256, cand_smem, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres, b->d_cviol,
                                               b->cand_cmax, 0, head);
     b->extra_launches += 3;
-    if (head < Ec.n_warm) {
-      k_cand_check<<<n, 128, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cviol, b->d_cres, head);
+    // later ranks in geometrically growing groups, each only for the problems
+    // still without a certified-feasible candidate
+    for (int r0 = head; r0 < Ec.n_warm;) {
+      const int r1 = std::min(Ec.n_warm, 4 * r0);
+      k_cand_check<<<n, 128, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cviol, b->d_cres, r0);
       k_cand_feas<<<fgrid, 256, cand_smem, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres,
-                                                b->d_cviol, b->cand_cmax, head, Ec.n_warm);
+                                                b->d_cviol, b->cand_cmax, r0, r1);
       b->extra_launches += 2;
+      r0 = r1;
     }
     k_cand_pick<<<n, PCBA_TPB, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cviol);
     return 0;
