@@ -5,9 +5,9 @@
 //   z = max_p h3_p,  h4 = relu([z, u] W4 + b4),  h5 = relu(h4 W5 + b5),
 //   y = tanh(h5 W6 + b6),  loss = (1/B) sum_b ||y_b - t_b||^2
 //
-// The dense layers run as GEMMs on the tensor cores (mma.sync m16n8k16, BF16
-// operands rounded from the FP32 master copies, FP32 accumulation); a plain
-// FP32 GEMM replaces them in the FP32 debug precision.  Weights are row-major
+// The dense layers run as GEMMs on the 5th-generation tensor cores (tcgen05,
+// BF16 operands rounded from the FP32 master copies, FP32 accumulation in
+// tensor memory); a plain FP32 GEMM replaces them in the FP32 debug precision.  Weights are row-major
 // [in][out]; the parameter vector is W1, b1, ..., W6, b6.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
