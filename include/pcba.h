@@ -206,6 +206,34 @@ int pcba_batch_stats(const pcba_batch* b, long long* loop_iters, long long* kern
  * last solve (their error bound changed a classification) and patches actually
  * refreshed (marked children that survived the cut-off). */
 int pcba_batch_refresh_stats(const pcba_batch* b, long long* marked, long long* refreshed);
+/* Local polish of the point each problem's last solve returned (not in the
+ * paper).  From the centre of the last solve's best box (or its certified
+ * warm point): a log-barrier Newton method in FP64 on
+ *   min p(x) - mu sum_i log(-g_i(x))  subject to  h_j(x) = 0, x in the box,
+ * starting at mu = mu0 max(1, |p(x0)|) and lowered tenfold per level down to
+ * gap / max(1, alpha) (for a convex program the barrier point is within
+ * alpha mu of the optimum), at most iters Newton steps per level.  After each
+ * level the iterate rounded to FP32 coordinates is kept if every g_i < 0 and
+ * sum_j |h_j| <= eq_tol / 2 there.  x receives np rows of PCBA_MAX_DIM
+ * doubles (host memory): the last kept point (entries past l are 0), or NaN
+ * where there is none (infeasible, no point, more than PCBA_MAX_DIM
+ * equalities, or no level kept).  The result is only a candidate: it lowers
+ * p_up only if a later solve's warm-start certification accepts it.  Runs on
+ * the batch's stream and blocks until x is written.  PCBA_ERR_INVALID unless
+ * mu0, gap, eq_tol > 0 and 1 <= iters <= 200. */
+int pcba_batch_polish(pcba_batch* b, double mu0, double gap, double eq_tol, int iters,
+                      double* x);
+/* Two solves for tight equality tolerances: a solve with eq_tol =
+ * relax_eq_tol, then pcba_batch_polish of its points (mu0 = 1e-2,
+ * gap = opt_tol / 10, 30 steps per level; the points stay on the device),
+ * then a solve with eq_tol whose warm starts are the polished points.  Every
+ * reported bound comes from the second solve, so the certificate is that of
+ * pcba_batch_solve with eq_tol; time_ms and pcba_batch_timing's total count
+ * from the start of the first solve, and pcba_batch_stats counts the kernel
+ * launches and copies of all three phases.  PCBA_ERR_INVALID unless
+ * 0 < eq_tol <= relax_eq_tol. */
+int pcba_batch_solve_polished(pcba_batch* b, double opt_tol, double eq_tol, double relax_eq_tol,
+                              int max_iters, pcba_result* out);
 int pcba_batch_set_stream(pcba_batch* b, void* cuda_stream);
 void pcba_batch_destroy(pcba_batch* b);
 

@@ -8,7 +8,8 @@ ROOT = os.path.dirname(HERE)
 LIB = os.path.join(HERE, "libpcba.so")
 SOURCES = [os.path.join(HERE, "csrc", f) for f in ("pcba.cu", "pcba_noalloc.cu", "pcba_mlp.cu")]
 DEPS = SOURCES + [os.path.join(HERE, "csrc", f) for f in ("pcba_device.cuh", "pcba_kernels.cuh",
-                                                          "pcba_subdivide.cuh", "pcba_eval.cuh")] \
+                                                          "pcba_subdivide.cuh", "pcba_eval.cuh",
+                                                          "pcba_polish.cuh")] \
     + [os.path.join(ROOT, "include", f) for f in ("pcba.h", "pcba_warmstart.h")]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",

@@ -141,6 +141,12 @@ struct pcba_batch {
   long long ckey_cap = 0;
   int cand_cmax = 0, cand_tiles = 1;  // largest constraint patch, constraint tiles of 32
   double* d_stencil = nullptr;  // guided solves: [stencil_cap] doubles
+  double* d_polish = nullptr;   // pcba_batch_polish output: [np][PCBA_MAXD]
+  // pcba_batch_solve_polished: the warm points are already in d_warm (written
+  // by the polish kernel), and the counts of the phases before the last solve
+  bool warm_on_device = false;
+  long long prior_launches = 0, prior_h2d = 0, prior_d2h = 0;
+  cudaEvent_t ev_pipe = nullptr;
   long long cand_cap = 0, stencil_cap = 0;
   // refinement rounds of guided solves (host copies of their stencils)
   std::vector<std::vector<double>> refine;
@@ -309,11 +315,12 @@ void free_batch(pcba_batch* b) {
   if (b->ev1) cudaEventDestroy(b->ev1);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->ev_pipe) cudaEventDestroy(b->ev_pipe);
   if (b->side) cudaStreamDestroy(b->side);
   void* dev[] = {b->d_desc, b->d_state, b->d_plan, b->d_params, b->d_pre, b->d_arena, b->d_rec,
                  b->d_slots, b->d_tilecnt, b->d_mono, b->d_trace, b->d_warm, b->d_mat,
                  b->d_raw, b->d_eval, b->d_tmaps, b->d_marks, b->d_cand, b->d_stencil,
-                 b->d_mono32, b->d_ckey, b->d_cviol, b->d_corder, b->d_cres};
+                 b->d_mono32, b->d_ckey, b->d_cviol, b->d_corder, b->d_cres, b->d_polish};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {b->h_state, b->h_eval, b->h_plan, b->h_params, b->h_running};
@@ -870,7 +877,8 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
                  (guide ? 8LL * guide->n * guide->dim : 0) +
                  (guide ? 8LL * b->refine_total() * b->refine_dim : 0) + b->pending_h2d;
   b->pending_h2d = 0;
-  b->extra_launches = (guide || warm ? 1 : 0) + (guide ? 1 : 0);
+  const bool have_warm = warm || b->warm_on_device;
+  b->extra_launches = (guide || have_warm ? 1 : 0) + (guide ? 1 : 0);
   b->d2h_bytes = (long long)(sizeof(ProbState) + sizeof(EvalOut)) * n + (long long)sizeof(Plan);
   if (host_coeffs)
     PCBA_CK(cudaMemcpyAsync(b->d_mono, host_coeffs, sizeof(double) * b->mono_doubles,
@@ -879,11 +887,11 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   if (warm)
     PCBA_CK(cudaMemcpyAsync(b->d_warm, warm, sizeof(double) * PCBA_MAXD * n,
                             cudaMemcpyHostToDevice, s));
-  else
+  else if (!b->warm_on_device)
     PCBA_CK(cudaMemsetAsync(b->d_warm, 0xFF, sizeof(double) * PCBA_MAXD * n, s));  // NaN
   Engine E1 = b->E;
   E1.root_raw = want_raw ? b->d_raw : nullptr;
-  if (guide || warm) {
+  if (guide || have_warm) {
     const unsigned cg = (unsigned)std::min<long long>((b->mono_doubles + 255) / 256, 4LL * b->g.sms);
     k_mono32<<<cg, 256, 0, s>>>(b->d_mono, b->d_mono32, b->mono_doubles);
   }
@@ -934,7 +942,7 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
     k_cand_pick<<<n, PCBA_TPB, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cviol);
     return 0;
   };
-  if (guide || warm) {
+  if (guide || have_warm) {
     int rc = certify(E1);
     if (rc) return rc;
     for (size_t rd = 0; guide && rd < b->refine.size(); ++rd) {
@@ -1071,6 +1079,38 @@ void fill_results(const pcba_batch* b, pcba_result* out) {
   }
 }
 
+// barrier weight of the first polish level relative to max(1, |p(x0)|), and
+// the Newton steps per level
+constexpr double kPolishMu0 = 1e-2;
+constexpr int kPolishIters = 30;
+
+// k_polish for every dimension present in the batch, on the batch's stream
+int launch_polish(pcba_batch* b, double* d_out, double mu0, double gap, double eq_tol, int iters,
+                  int* launches) {
+  if (!(mu0 > 0.0) || !(gap > 0.0) || !(eq_tol > 0.0) || iters < 1 || iters > 200)
+    return fail(PCBA_ERR_INVALID, "need mu0, gap, eq_tol > 0 and 1 <= iters <= 200");
+  bool seen[PCBA_MAXD + 1] = {};
+  for (int k = 0; k < b->np; ++k) seen[b->desc[k].l] = true;
+  cudaStream_t s = b->stream;
+  const unsigned g = (unsigned)b->np;
+  for (int L = 1; L <= PCBA_MAXD; ++L) {
+    if (!seen[L]) continue;
+    switch (L) {
+      case 1: k_polish<1><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
+      case 2: k_polish<2><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
+      case 3: k_polish<3><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
+      case 4: k_polish<4><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
+      case 5: k_polish<5><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
+      case 6: k_polish<6><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
+      case 7: k_polish<7><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
+      default: k_polish<8><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
+    }
+    PCBA_CK(cudaGetLastError());
+    ++*launches;
+  }
+  return 0;
+}
+
 int batch_solve_impl(pcba_batch* b, const double* host_coeffs, double opt_tol, double eq_tol,
                      int max_iters, int max_steps, const double* warm, pcba_result* out,
                      bool want_raw = false, const Guide* guide = nullptr) {
@@ -1078,6 +1118,7 @@ int batch_solve_impl(pcba_batch* b, const double* host_coeffs, double opt_tol, d
   if (!(opt_tol > 0) || !(eq_tol > 0)) return fail(PCBA_ERR_INVALID, "tolerances must be > 0");
   if (max_iters < 1 || max_iters > 64) return fail(PCBA_ERR_INVALID, "max_iters must be in [1, 64]");
   if (max_steps < 0) return fail(PCBA_ERR_INVALID, "max_steps must be >= 0");
+  b->prior_launches = b->prior_h2d = b->prior_d2h = 0;
   const int rc = b->precision == PCBA_FP32
                      ? run_solve<float>(b, host_coeffs, opt_tol, eq_tol, max_iters, max_steps, warm,
                                         want_raw, guide)
@@ -1321,6 +1362,56 @@ int pcba_batch_cost_grid(pcba_batch* b, int G, float* d_out, int ld, int col0) {
   return 0;
 }
 
+int pcba_batch_polish(pcba_batch* b, double mu0, double gap, double eq_tol, int iters,
+                      double* x) {
+  if (!b || !x) return fail(PCBA_ERR_INVALID, "batch or output is null");
+  if (!b->d_polish && cudaMalloc((void**)&b->d_polish, sizeof(double) * PCBA_MAXD * b->np) !=
+                          cudaSuccess) {
+    b->d_polish = nullptr;
+    return fail(PCBA_ERR_OOM, "cannot allocate the polish output");
+  }
+  int launches = 0;
+  const int rc = launch_polish(b, b->d_polish, mu0, gap, eq_tol, iters, &launches);
+  if (rc) return rc;
+  PCBA_CK(cudaMemcpyAsync(x, b->d_polish, sizeof(double) * PCBA_MAXD * b->np,
+                          cudaMemcpyDeviceToHost, b->stream));
+  PCBA_CK(cudaStreamSynchronize(b->stream));
+  return 0;
+}
+
+int pcba_batch_solve_polished(pcba_batch* b, double opt_tol, double eq_tol, double relax_eq_tol,
+                              int max_iters, pcba_result* out) {
+  if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
+  if (!(eq_tol > 0) || !(relax_eq_tol >= eq_tol))
+    return fail(PCBA_ERR_INVALID, "need 0 < eq_tol <= relax_eq_tol");
+  if (!b->ev_pipe && cudaEventCreate(&b->ev_pipe) != cudaSuccess) {
+    b->ev_pipe = nullptr;
+    return fail(PCBA_ERR_CUDA, "event creation failed");
+  }
+  PCBA_CK(cudaEventRecord(b->ev_pipe, b->stream));
+  int rc = batch_solve_impl(b, nullptr, opt_tol, relax_eq_tol, max_iters, 0, nullptr, nullptr);
+  if (rc) return rc;
+  long long l1 = 0, h1 = 0, d1 = 0;
+  pcba_batch_stats(b, nullptr, &l1, &h1, &d1);
+  const unsigned long long t0 = b->h_plan->t0;
+  int lp = 0;
+  rc = launch_polish(b, b->d_warm, kPolishMu0, 0.1 * opt_tol, eq_tol, kPolishIters, &lp);
+  if (rc) return rc;
+  b->warm_on_device = true;
+  rc = batch_solve_impl(b, nullptr, opt_tol, eq_tol, max_iters, 0, nullptr, nullptr);
+  b->warm_on_device = false;
+  if (rc) return rc;
+  b->prior_launches = l1 + lp;
+  b->prior_h2d = h1;
+  b->prior_d2h = d1;
+  float ms = 0;
+  PCBA_CK(cudaEventElapsedTime(&ms, b->ev_pipe, b->ev1));
+  b->total_ms = ms;
+  b->h_plan->t0 = t0;  // per-problem times count from the start of the first solve
+  if (out) fill_results(b, out);
+  return 0;
+}
+
 long long pcba_batch_input_doubles(const pcba_batch* b) { return b ? b->mono_doubles : 0; }
 
 int pcba_batch_trace(const pcba_batch* b, int k, double* rows, int max_rows) {
@@ -1397,9 +1488,9 @@ int pcba_batch_stats(const pcba_batch* b, long long* loop_iters, long long* kern
   // per iteration: subdivision, k_pup, k3_classify, k4_index, k_move_control,
   // and k_refresh in FP32
   const long long per_it = 5 + (b->precision == PCBA_FP32 ? 1 : 0);
-  if (kernel_launches) *kernel_launches = 5 + per_it * it + b->extra_launches;
-  if (h2d_bytes) *h2d_bytes = b->h2d_bytes;
-  if (d2h_bytes) *d2h_bytes = b->d2h_bytes;
+  if (kernel_launches) *kernel_launches = 5 + per_it * it + b->extra_launches + b->prior_launches;
+  if (h2d_bytes) *h2d_bytes = b->h2d_bytes + b->prior_h2d;
+  if (d2h_bytes) *d2h_bytes = b->d2h_bytes + b->prior_d2h;
   return 0;
 }
 

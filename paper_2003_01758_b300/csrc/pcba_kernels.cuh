@@ -1,7 +1,8 @@
 // Kernels of one PCBA step (Algorithm 1) for many problems at once, plus the
 // monomial-to-Bernstein conversion and the point checks.  The subdivision
-// kernels live in pcba_subdivide.cuh and the point evaluations (warm start,
-// final check) in pcba_eval.cuh, both included below.
+// kernels live in pcba_subdivide.cuh, the point evaluations (warm start,
+// final check) in pcba_eval.cuh and the local polish of an incumbent in
+// pcba_polish.cuh, all included below.
 //
 //   k1_matrices / k1_convert  Alg. 1 line 1 (InitPatches, Sec. II-D): per axis
 //                             the matrix T_r = (power -> Bernstein on [0,1]) x
@@ -864,3 +865,4 @@ __global__ void k_init(Engine E) {
 }
 
 #include "pcba_eval.cuh"
+#include "pcba_polish.cuh"

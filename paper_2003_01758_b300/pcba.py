@@ -87,6 +87,8 @@ def lib():
         "pcba_batch_config": ([P, P, P, P, P], I),
         "pcba_batch_refresh_stats": ([P, P, P], I),
         "pcba_batch_set_stream": ([P, P], I),
+        "pcba_batch_polish": ([P, D, D, D, I, P], I),
+        "pcba_batch_solve_polished": ([P, D, D, D, I, P], I),
         "pcba_batch_destroy": ([P], None),
         "pcba_get_list": ([P, P, P, P, P, P, P, P], I),
         "pcba_root_patches": ([P, P, P, P], I),
@@ -128,6 +130,7 @@ def exported_symbols():
             "pcba_batch_solve_from_host", "pcba_batch_input_doubles", "pcba_batch_trace",
             "pcba_batch_timing", "pcba_batch_stats", "pcba_batch_launch_bytes",
             "pcba_batch_autotune", "pcba_batch_config", "pcba_batch_refresh_stats", "pcba_batch_set_stream", "pcba_batch_destroy",
+            "pcba_batch_polish", "pcba_batch_solve_polished",
             "pcba_get_list", "pcba_root_patches", "pcba_item_bytes", "pcba_set_stream",
             "pcba_set_warm_start", "pcba_destroy", "pcba_status_string", "pcba_last_error",
             "pcba_version", "pcba_bernstein_convert_noalloc", "pcba_batch_solve_guided",
@@ -355,6 +358,24 @@ class Batch:
         if _check(lib().pcba_batch_warm_point(self._b, k, _p(x), ctypes.byref(c))) == 0:
             return None
         return (x[:self.solvers[k].l].copy(), c.value) if with_cost else x[:self.solvers[k].l].copy()
+
+    def polish(self, mu0=1e-2, gap=1e-4, eq_tol=1e-4, iters=30):
+        """pcba_batch_polish: the locally polished point of every problem's last
+        solve (None where there is none), as a list of arrays."""
+        x = np.empty((self.n, MAX_DIM))
+        _check(lib().pcba_batch_polish(self._b, mu0, gap, eq_tol, iters, _p(x)))
+        return [None if not np.all(np.isfinite(x[k, :self.solvers[k].l]))
+                else x[k, :self.solvers[k].l].copy() for k in range(self.n)]
+
+    def solve_polished(self, opt_tol=1e-3, eq_tol=1e-4, relax_eq_tol=1e-2, max_iters=28,
+                       raw=False):
+        """pcba_batch_solve_polished: a solve at relax_eq_tol, the polish of its
+        points, then the certified solve at eq_tol seeded with them."""
+        _check(lib().pcba_batch_solve_polished(self._b, opt_tol, eq_tol, relax_eq_tol, max_iters,
+                                               self._results))
+        if raw:
+            return self._results
+        return [_result_dict(self._results[k], self.solvers[k].l) for k in range(self.n)]
 
     def set_refine_stencil(self, stencil, guess_dim=2, round=0):
         """pcba_batch_set_refine_stencil for one round (None or an empty array

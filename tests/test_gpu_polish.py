@@ -1,0 +1,125 @@
+"""Tight equality tolerances: pcba_batch_polish and pcba_batch_solve_polished.
+
+With equalities and a small eq_tol, no box is certified feasible until boxes
+are tiny, so p_up (Def. 4) stays infinite and the list outgrows memory.  The
+pipeline solves with a loose eq_tol, polishes the returned points with a
+log-barrier Newton method (FP64) and seeds the certified solve at the tight
+eq_tol with them.  The polish is a heuristic; what is checked here is that its
+points are what the certification needs (strictly feasible, FP32 coordinates,
+near the relaxed optimum), and that the pipeline's certified intervals agree
+with the oracle's."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2003_01758_b300 import pcba
+from paper_2003_01758_b300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def ev(a, x):
+    return oracle.eval_monomial(a, x)
+
+
+def test_pipeline_interval_matches_oracle():
+    # 8 inequalities, 2 equalities: the oracle certifies eq_tol 1e-3 in seconds
+    p = W.dim4(3000, n_ineq=8, n_eq=2)
+    o = oracle.solve(p.cost, p.ineq, p.eq, p.lo, p.hi, opt_tol=1e-3, eq_tol=1e-3, max_iters=28,
+                     max_items=1 << 18)
+    assert o["status"] == pcba.OPTIMAL
+    for prec in (pcba.FP32, pcba.FP64):
+        b = pcba.Batch([pcba.solver_from_problem(p, prec)], 4 << 30)
+        r = b.solve_polished(opt_tol=1e-3, eq_tol=1e-3, relax_eq_tol=1e-2)[0]
+        assert r["status"] == pcba.OPTIMAL, r
+        assert r["upper"] - r["lower"] <= 1e-3
+        assert r["lower"] <= o["upper"] and o["lower"] <= r["upper"], (r, o)
+        x = r["x"]
+        assert max(ev(g, x) for g in p.ineq) <= 0.0
+        assert max(abs(ev(h, x)) for h in p.eq) <= 1e-3
+        assert b.warm_point(0) is not None
+        b.close()
+
+
+def test_polished_points_are_strictly_feasible_fp32_points():
+    probs = [W.dim4(3000 + k) for k in range(3)]
+    b = pcba.Batch([pcba.solver_from_problem(q, pcba.FP32) for q in probs], 3 * (8 << 30))
+    rel = b.solve(opt_tol=1e-3, eq_tol=1e-2)
+    eq_tol = 1e-4
+    pts = b.polish(mu0=1e-2, gap=1e-4, eq_tol=eq_tol, iters=30)
+    for q, r, x in zip(probs, rel, pts):
+        assert r["status"] == pcba.OPTIMAL
+        assert x is not None
+        assert np.array_equal(x, x.astype(np.float32).astype(np.float64))
+        assert np.all(x >= q.lo) and np.all(x <= q.hi)
+        assert max(ev(g, x) for g in q.ineq) < 0.0
+        assert sum(abs(ev(h, x)) for h in q.eq) <= 0.5 * eq_tol
+        c = ev(q.cost, x)
+        # x is feasible for eq_tol 1e-2, so its cost is at least the relaxed
+        # certified lower bound; the barrier point is close to the optimum
+        assert c >= r["lower"] - 1e-12
+        assert c <= r["upper"] + 1e-3
+    res = b.solve_polished(opt_tol=1e-3, eq_tol=eq_tol, relax_eq_tol=1e-2)
+    for k, (q, r, rr, x) in enumerate(zip(probs, res, rel, pts)):
+        assert r["status"] == pcba.OPTIMAL, r
+        assert r["upper"] - r["lower"] <= 1e-3
+        # the strict minimum lies above the relaxed one and below the cost of
+        # the (strictly feasible) polished point
+        assert r["upper"] >= rr["lower"] - 1e-12
+        assert r["lower"] <= ev(q.cost, x) + 1e-9
+        assert max(abs(ev(h, r["x"])) for h in q.eq) <= eq_tol
+        assert b.warm_point(k) is not None
+    st = b.stats()
+    assert st["kernel_launches"] > 0 and st["loop_iters"] > 0
+    b.close()
+
+
+def test_plain_solve_cannot_certify_what_the_pipeline_does():
+    q = W.dim4(3001)
+    b = pcba.Batch([pcba.solver_from_problem(q, pcba.FP32)], 8 << 30)
+    plain = b.solve(opt_tol=1e-3, eq_tol=1e-4)[0]
+    assert plain["status"] == pcba.MEMCAP
+    r = b.solve_polished(opt_tol=1e-3, eq_tol=1e-4, relax_eq_tol=1e-2)[0]
+    assert r["status"] == pcba.OPTIMAL
+    # the stopped solve's lower bound still bounds the minimum from below
+    assert plain["lower"] <= r["upper"] + 1e-12
+    b.close()
+
+
+def test_polish_edge_cases_mixed_dimensions_and_infeasible():
+    # l = 1 (tiny-like), l = 2 without equalities, l = 4 with, and an
+    # infeasible problem (g = 1 + x^2 > 0 everywhere): one instantiation per l
+    one = W.Problem(np.array([0.0, -1.0, 0.0]), np.array([[-0.25, 0.0, 1.0]]), np.zeros((0, 1)),
+                    np.array([-1.0]), np.array([1.0]))
+    two = W.tiny(1000)
+    four = W.dim4(3002, n_ineq=8, n_eq=1)
+    bad = W.Problem(np.array([0.0, 1.0, 0.0]), np.array([[1.0, 0.0, 1.0]]), np.zeros((0, 1)),
+                    np.array([-1.0]), np.array([1.0]))
+    probs = [one, two, four, bad]
+    b = pcba.Batch([pcba.solver_from_problem(q, pcba.FP64) for q in probs], 4 << 30)
+    rel = b.solve(opt_tol=1e-3, eq_tol=1e-2)
+    assert rel[3]["status"] == pcba.INFEASIBLE
+    pts = b.polish(mu0=1e-2, gap=1e-4, eq_tol=1e-2, iters=30)
+    assert pts[3] is None
+    for q, r, x in zip(probs[:3], rel[:3], pts[:3]):
+        assert x is not None and x.shape == (q.l,)
+        assert max(ev(g, x) for g in q.ineq) < 0.0
+        assert sum(abs(ev(h, x)) for h in q.eq) <= 0.5e-2
+        assert ev(q.cost, x) >= r["lower"] - 1e-12
+    # min -x on [-1, 1] with x^2 <= 1/4: the barrier point at mu solves
+    # 1/4 - x^2 = 2 mu x, about mu below 1/2 (last mu = gap = 1e-4)
+    assert 0.5 - 1e-3 < pts[0][0] < 0.5
+    b.close()
+
+
+def test_polish_rejects_bad_arguments():
+    b = pcba.Batch([pcba.solver_from_problem(W.tiny(1000), pcba.FP64)], 1 << 28)
+    b.solve()
+    for kw in (dict(mu0=0.0), dict(gap=-1.0), dict(eq_tol=0.0), dict(iters=0), dict(iters=201)):
+        args = dict(mu0=1e-2, gap=1e-4, eq_tol=1e-4, iters=30)
+        args.update(kw)
+        with pytest.raises(pcba.PcbaError):
+            b.polish(**args)
+    with pytest.raises(pcba.PcbaError):
+        b.solve_polished(eq_tol=1e-2, relax_eq_tol=1e-3)
+    b.close()
