@@ -41,7 +41,7 @@ BATCH = 64
 OBSTACLES = 512
 OPT_TOL = 1e-3
 EQ_TOL = 1e-4
-RELAX_EQ_TOL = 1e-2   # first solve of the polished pipeline for equality-constrained problems
+RELAX_OPT_TOL, RELAX_EQ_TOL = 3e-2, 1e-1   # first solve of the polished pipeline (equalities)
 MAX_ITERS = 28
 BASE_SEED = 2000
 MEM_CAP = 64 << 30
@@ -302,7 +302,8 @@ def timed_steps(batch, steps, flush, polished=False):
         flush.zero_()
         torch.cuda.synchronize()
         if polished:
-            res = batch.solve_polished(OPT_TOL, EQ_TOL, RELAX_EQ_TOL, MAX_ITERS, raw=True)
+            res = batch.solve_polished(OPT_TOL, EQ_TOL, RELAX_OPT_TOL, RELAX_EQ_TOL, MAX_ITERS,
+                                       raw=True)
         else:
             res = batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS, raw=True)
         ms.append(batch.timing()["total_ms"])
@@ -497,15 +498,17 @@ def main():
         d4 = [W.dim4(3000 + k) for k in range(8)]
         dim4 = {"workload": "8 problems l=4, cost degree 4, 64 g_i degree 3, 2 h_j degree 2, "
                             "seeds 3000+k, eq_tol 1e-4, 8 GiB per problem",
-                "polished": "pcba_batch_solve_polished: solve at eq_tol %g, barrier-Newton "
-                            "polish of its points, certified solve at eq_tol 1e-4 seeded with "
-                            "them; time and launches of all three phases" % RELAX_EQ_TOL}
+                "polished": "pcba_batch_solve_polished: solve at opt_tol %g, eq_tol %g, "
+                            "barrier-Newton polish of its points, certified solve at opt_tol "
+                            "1e-3, eq_tol 1e-4 seeded with them; time and launches of all "
+                            "three phases" % (RELAX_OPT_TOL, RELAX_EQ_TOL)}
         legs = ((pcba.FP32, "fp32", False), (pcba.FP64, "fp64", False),
                 (pcba.FP32, "fp32_polished", True), (pcba.FP64, "fp64_polished", True))
         for prec, name, polished in legs:
             db = pcba.Batch([pcba.Solver(q.cost, q.ineq, q.eq, q.lo, q.hi, precision=prec)
                              for q in d4], 8 * (8 << 30))
-            run = ((lambda: db.solve_polished(OPT_TOL, EQ_TOL, RELAX_EQ_TOL, MAX_ITERS))
+            run = ((lambda: db.solve_polished(OPT_TOL, EQ_TOL, RELAX_OPT_TOL, RELAX_EQ_TOL,
+                                              MAX_ITERS))
                    if polished else (lambda: db.solve(OPT_TOL, EQ_TOL, MAX_ITERS)))
             run()
             dms, dtimes, dstatus = timed_steps(db, 2 if not polished else 5, flush, polished)

@@ -223,17 +223,19 @@ int pcba_batch_refresh_stats(const pcba_batch* b, long long* marked, long long* 
  * mu0, gap, eq_tol > 0 and 1 <= iters <= 200. */
 int pcba_batch_polish(pcba_batch* b, double mu0, double gap, double eq_tol, int iters,
                       double* x);
-/* Two solves for tight equality tolerances: a solve with eq_tol =
- * relax_eq_tol, then pcba_batch_polish of its points (mu0 = 1e-2,
- * gap = opt_tol / 10, 30 steps per level; the points stay on the device),
- * then a solve with eq_tol whose warm starts are the polished points.  Every
- * reported bound comes from the second solve, so the certificate is that of
- * pcba_batch_solve with eq_tol; time_ms and pcba_batch_timing's total count
- * from the start of the first solve, and pcba_batch_stats counts the kernel
- * launches and copies of all three phases.  PCBA_ERR_INVALID unless
- * 0 < eq_tol <= relax_eq_tol. */
-int pcba_batch_solve_polished(pcba_batch* b, double opt_tol, double eq_tol, double relax_eq_tol,
-                              int max_iters, pcba_result* out);
+/* Two solves for tight equality tolerances (not in the paper): a solve with
+ * (relax_opt_tol, relax_eq_tol), then pcba_batch_polish of its points
+ * (mu0 = 1e-2, gap = opt_tol / 10, 30 steps per level; the points stay on
+ * the device), then a solve with (opt_tol, eq_tol) whose warm starts are the
+ * polished points.  Every reported bound and point comes from the second
+ * solve, so the certificate is that of pcba_batch_solve with (opt_tol,
+ * eq_tol): the first solve and the polish only decide how early p_up becomes
+ * finite.  time_ms and pcba_batch_timing's total count from the start of the
+ * first solve, and pcba_batch_stats counts the kernel launches and copies of
+ * all three phases.  PCBA_ERR_INVALID unless 0 < eq_tol <= relax_eq_tol and
+ * both optimality tolerances are > 0. */
+int pcba_batch_solve_polished(pcba_batch* b, double opt_tol, double eq_tol, double relax_opt_tol,
+                              double relax_eq_tol, int max_iters, pcba_result* out);
 int pcba_batch_set_stream(pcba_batch* b, void* cuda_stream);
 void pcba_batch_destroy(pcba_batch* b);
 

@@ -1379,17 +1379,20 @@ int pcba_batch_polish(pcba_batch* b, double mu0, double gap, double eq_tol, int 
   return 0;
 }
 
-int pcba_batch_solve_polished(pcba_batch* b, double opt_tol, double eq_tol, double relax_eq_tol,
-                              int max_iters, pcba_result* out) {
+int pcba_batch_solve_polished(pcba_batch* b, double opt_tol, double eq_tol, double relax_opt_tol,
+                              double relax_eq_tol, int max_iters, pcba_result* out) {
   if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
   if (!(eq_tol > 0) || !(relax_eq_tol >= eq_tol))
     return fail(PCBA_ERR_INVALID, "need 0 < eq_tol <= relax_eq_tol");
+  if (!(opt_tol > 0) || !(relax_opt_tol > 0))
+    return fail(PCBA_ERR_INVALID, "tolerances must be > 0");
   if (!b->ev_pipe && cudaEventCreate(&b->ev_pipe) != cudaSuccess) {
     b->ev_pipe = nullptr;
     return fail(PCBA_ERR_CUDA, "event creation failed");
   }
   PCBA_CK(cudaEventRecord(b->ev_pipe, b->stream));
-  int rc = batch_solve_impl(b, nullptr, opt_tol, relax_eq_tol, max_iters, 0, nullptr, nullptr);
+  int rc = batch_solve_impl(b, nullptr, relax_opt_tol, relax_eq_tol, max_iters, 0, nullptr,
+                            nullptr);
   if (rc) return rc;
   long long l1 = 0, h1 = 0, d1 = 0;
   pcba_batch_stats(b, nullptr, &l1, &h1, &d1);

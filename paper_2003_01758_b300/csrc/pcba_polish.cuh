@@ -32,7 +32,7 @@
 
 #include "pcba_device.cuh"
 
-#define PCBA_POLISH_TPB 128
+#define PCBA_POLISH_TPB 256
 
 // Value, gradient and (HESS) Hessian of a dense monomial tensor a (row-major,
 // last axis fastest; degrees deg[0..L), strides stride[0..L)) at x: nested
@@ -278,18 +278,29 @@ __device__ __forceinline__ void cost_row_any(int K, const double* a, const int* 
 // most l - 1), then one item per inequality and per equality.  Problems with
 // more than PCBA_MAXD equality constraints, infeasible ones and ones without
 // a point get a NaN row.  out: [np][PCBA_MAXD] doubles.
+//
+// One full evaluation at a point gives, summed over the block: the cost's
+// gradient and Hessian, B1 = sum_i grad g_i / g_i and B2 = sum_i grad g_i
+// grad g_i^T / g_i^2 (so that the barrier gradient and Gauss-Newton Hessian
+// at any mu are grad p - mu B1 and hess p + mu B2), the merit pieces
+// p, -sum_i log(-g_i), sum_j |h_j|, and h_j with its gradient.  The full step
+// of every Newton iteration is evaluated this way (if it is accepted, the
+// next iteration needs no other evaluation); shorter steps of the backtracking
+// search evaluate values only.
 template <int L>
-__global__ void __launch_bounds__(PCBA_POLISH_TPB)
+__global__ void __launch_bounds__(PCBA_POLISH_TPB, 1)
     k_polish(Engine E, double* out, double mu0, double gap, double eq_tol, int iters) {
   constexpr int NS = L + L * (L + 1) / 2;  // gradient + packed Hessian
+  constexpr int ND = 2 * NS + 3;           // cost part, barrier part, merit pieces
   __shared__ double sx[L], sxt[L], sdx[L], sbest[L];
   __shared__ double spw[L * 17], sdpw[L * 17], sddpw[L * 17];
-  __shared__ double sred[(PCBA_POLISH_TPB / 32) * NS];
-  __shared__ double shv[PCBA_MAXD], shg[PCBA_MAXD * L];
+  __shared__ double sred[(PCBA_POLISH_TPB / 32) * ND];
+  __shared__ double sdata[2][ND];
+  __shared__ double shv[2][PCBA_MAXD], shg[2][PCBA_MAXD * L];
   __shared__ double sK[(L + PCBA_MAXD) * (L + PCBA_MAXD + 1)];
   __shared__ double s_m[3];
   __shared__ double s_rho, s_rel;
-  __shared__ int s_ok, s_stop, s_best, s_has;
+  __shared__ int s_ok, s_stop, s_best, s_has, s_okd[2];
   const int p = blockIdx.x;
   const ProbDesc* D = E.desc + p;
   if (D->l != L) return;
@@ -343,7 +354,7 @@ __global__ void __launch_bounds__(PCBA_POLISH_TPB)
     }
     __syncthreads();
   };
-  // s_m = (p, -sum log(-g_i), sum |h_j|) at xv; s_ok = every g_i < 0
+  // values only: s_m = (p, -sum log(-g_i), sum |h_j|) at xv; s_ok = every g_i < 0
   auto merit = [&](const double* xv) {
     powers(xv);
     double m[3] = {0.0, 0.0, 0.0};
@@ -369,53 +380,69 @@ __global__ void __launch_bounds__(PCBA_POLISH_TPB)
     }
     __syncthreads();
   };
+  // full evaluation at xv into sdata[d], shv[d], shg[d], s_okd[d]
+  auto evaluate = [&](const double* xv, int d) {
+    powers(xv);
+    double acc[ND];
+#pragma unroll
+    for (int q = 0; q < ND; ++q) acc[q] = 0.0;
+    int feas = 1;
+    for (int q = threadIdx.x; q < items; q += PCBA_POLISH_TPB) {
+      if (q < R) {
+        cost_row_any<L, true>(K, base, dP, tP, xv, spw, sdpw, sddpw, q, acc[2 * NS], acc);
+      } else if (q < R + alpha) {
+        double v, g[L], Hd[1];
+        PolyDiff<L, false>::eval(gbase + (long long)(q - R) * D->cg, dG, tG, xv, v, g, Hd);
+        if (v < 0.0) {
+          acc[2 * NS + 1] -= log(-v);
+          const double inv = 1.0 / v;
+#pragma unroll
+          for (int s = 0; s < L; ++s) {
+            acc[NS + s] += g[s] * inv;
+#pragma unroll
+            for (int t = s; t < L; ++t) acc[NS + L + polish_tri(L, s, t)] += g[s] * g[t] * inv * inv;
+          }
+        } else {
+          feas = 0;
+        }
+      } else {
+        double v, g[L], Hd[1];
+        const int jh = q - R - alpha;
+        PolyDiff<L, false>::eval(hbase + (long long)jh * D->ch, dH, tH, xv, v, g, Hd);
+        acc[2 * NS + 2] += fabs(v);
+        shv[d][jh] = v;
+#pragma unroll
+        for (int s = 0; s < L; ++s) shg[d][jh * L + s] = g[s];
+      }
+    }
+    feas = __syncthreads_and(feas);
+    polish_block_sum(acc, ND, sred);
+    if (threadIdx.x == 0) {
+      for (int q = 0; q < ND; ++q) sdata[d][q] = acc[q];
+      s_okd[d] = feas;
+    }
+    __syncthreads();
+  };
 
-  merit(sx);
-  if (!s_ok) return;  // the start point must be strictly inside every g_i < 0
-  double mu = mu0 * fmax(1.0, fabs(s_m[0]));
+  int cur = 0;
+  evaluate(sx, cur);
+  if (!s_okd[cur]) return;  // the start point must be strictly inside every g_i < 0
+  double mu = mu0 * fmax(1.0, fabs(sdata[cur][2 * NS]));
   const double mu_end = fmin(mu, gap / fmax(1.0, (double)alpha));
   double rho = 10.0;
   for (int lev = 0; lev < 24; ++lev) {
     // centring tolerance on the Newton step: loose on the way, tight at the end
     const double tol = mu <= mu_end ? 1e-11 : 1e-7;
     for (int it = 0; it < iters; ++it) {
-      // gradient and Hessian of the barrier problem, h_j and grad h_j
-      double acc[NS];
-#pragma unroll
-      for (int q = 0; q < NS; ++q) acc[q] = 0.0;
-      powers(sx);
-      for (int q = threadIdx.x; q < items; q += PCBA_POLISH_TPB) {
-        if (q < R) {
-          double vdummy = 0.0;
-          cost_row_any<L, true>(K, base, dP, tP, sx, spw, sdpw, sddpw, q, vdummy, acc);
-        } else if (q < R + alpha) {
-          double v, g[L], Hd[1];
-          PolyDiff<L, false>::eval(gbase + (long long)(q - R) * D->cg, dG, tG, sx, v, g, Hd);
-          const double inv = 1.0 / v;  // v < 0: the iterate is strictly feasible
-#pragma unroll
-          for (int s = 0; s < L; ++s) {
-            acc[s] -= mu * g[s] * inv;
-#pragma unroll
-            for (int t = s; t < L; ++t)
-              acc[L + polish_tri(L, s, t)] += mu * g[s] * g[t] * inv * inv;
-          }
-        } else {
-          double v, g[L], Hd[1];
-          const int jh = q - R - alpha;
-          PolyDiff<L, false>::eval(hbase + (long long)jh * D->ch, dH, tH, sx, v, g, Hd);
-          shv[jh] = v;
-#pragma unroll
-          for (int s = 0; s < L; ++s) shg[jh * L + s] = g[s];
-        }
-      }
-      polish_block_sum(acc, NS, sred);
-      merit(sx);
-      bool moved = false;
+      bool moved = false, stop = false;
       // Newton step; if its line search fails, once more with H shifted to
       // diagonal dominance (Gershgorin), which makes the step a descent one
-      for (int attempt = 0; attempt < 2 && !moved; ++attempt) {
+      for (int attempt = 0; attempt < 2 && !moved && !stop; ++attempt) {
         if (threadIdx.x == 0) {
-          double xm = 0.0, step = 0.0;
+          const double* dc = sdata[cur];
+          double acc[NS];
+          for (int q = 0; q < L; ++q) acc[q] = dc[q] - mu * dc[NS + q];
+          for (int q = L; q < NS; ++q) acc[q] = dc[q] + mu * dc[NS + q];
           double shift = 0.0;
           if (attempt == 1)
             for (int r = 0; r < L; ++r) {
@@ -425,8 +452,8 @@ __global__ void __launch_bounds__(PCBA_POLISH_TPB)
                   off += fabs(acc[L + (r <= c ? polish_tri(L, r, c) : polish_tri(L, c, r))]);
               shift = fmax(shift, off - acc[L + polish_tri(L, r, r)]);
             }
-          double numax = 0.0;
-          const bool ok = polish_kkt<L>(acc, shv, shg, beta, shift, sK, sdx, &numax);
+          double numax = 0.0, xm = 0.0, step = 0.0;
+          const bool ok = polish_kkt<L>(acc, shv[cur], shg[cur], beta, shift, sK, sdx, &numax);
           for (int r = 0; r < L; ++r) {
             if (!ok) sdx[r] = 0.0;
             step = fmax(step, fabs(sdx[r]));
@@ -436,15 +463,31 @@ __global__ void __launch_bounds__(PCBA_POLISH_TPB)
           s_rho = rho;
           s_stop = !ok || step <= tol * (1.0 + xm);
           s_rel = step / (1.0 + xm);
+          for (int q = 0; q < L; ++q) sxt[q] = fmin(fmax(sx[q] + sdx[q], D->lo[q]), D->hi[q]);
         }
         __syncthreads();
         rho = s_rho;
         const double rel = s_rel;
-        if (s_stop) break;
-        const double phi0 = s_m[0] + mu * s_m[1] + rho * s_m[2];
-        double t = 1.0;
-        for (int ls = 0; ls < 30 && t * rel > 1e-15; ++ls, t *= 0.5) {
+        if (s_stop) {
+          stop = true;
+          break;
+        }
+        const double* dc = sdata[cur];
+        const double phi0 = dc[2 * NS] + mu * dc[2 * NS + 1] + rho * dc[2 * NS + 2];
+        // the full step, evaluated in full
+        evaluate(sxt, 1 - cur);
+        const double* dn = sdata[1 - cur];
+        if (s_okd[1 - cur] && dn[2 * NS] + mu * dn[2 * NS + 1] + rho * dn[2 * NS + 2] <= phi0) {
+          if (threadIdx.x == 0)
+            for (int q = 0; q < L; ++q) sx[q] = sxt[q];
+          cur = 1 - cur;
+          moved = true;
           __syncthreads();
+          break;
+        }
+        // shorter steps, values only
+        double t = 0.5;
+        for (int ls = 1; ls < 30 && t * rel > 1e-15; ++ls, t *= 0.5) {
           if (threadIdx.x == 0)
             for (int q = 0; q < L; ++q) sxt[q] = fmin(fmax(sx[q] + t * sdx[q], D->lo[q]), D->hi[q]);
           __syncthreads();
@@ -458,8 +501,7 @@ __global__ void __launch_bounds__(PCBA_POLISH_TPB)
           if (threadIdx.x == 0)
             for (int q = 0; q < L; ++q) sx[q] = sxt[q];
           __syncthreads();
-        } else {
-          merit(sx);  // s_m back to the values at x for the second attempt
+          evaluate(sx, cur);
         }
       }
       if (!moved) break;

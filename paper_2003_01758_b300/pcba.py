@@ -88,7 +88,7 @@ def lib():
         "pcba_batch_refresh_stats": ([P, P, P], I),
         "pcba_batch_set_stream": ([P, P], I),
         "pcba_batch_polish": ([P, D, D, D, I, P], I),
-        "pcba_batch_solve_polished": ([P, D, D, D, I, P], I),
+        "pcba_batch_solve_polished": ([P, D, D, D, D, I, P], I),
         "pcba_batch_destroy": ([P], None),
         "pcba_get_list": ([P, P, P, P, P, P, P, P], I),
         "pcba_root_patches": ([P, P, P, P], I),
@@ -367,12 +367,13 @@ class Batch:
         return [None if not np.all(np.isfinite(x[k, :self.solvers[k].l]))
                 else x[k, :self.solvers[k].l].copy() for k in range(self.n)]
 
-    def solve_polished(self, opt_tol=1e-3, eq_tol=1e-4, relax_eq_tol=1e-2, max_iters=28,
-                       raw=False):
-        """pcba_batch_solve_polished: a solve at relax_eq_tol, the polish of its
-        points, then the certified solve at eq_tol seeded with them."""
-        _check(lib().pcba_batch_solve_polished(self._b, opt_tol, eq_tol, relax_eq_tol, max_iters,
-                                               self._results))
+    def solve_polished(self, opt_tol=1e-3, eq_tol=1e-4, relax_opt_tol=3e-2, relax_eq_tol=1e-1,
+                       max_iters=28, raw=False):
+        """pcba_batch_solve_polished: a solve at (relax_opt_tol, relax_eq_tol),
+        the polish of its points, then the certified solve at (opt_tol, eq_tol)
+        seeded with them."""
+        _check(lib().pcba_batch_solve_polished(self._b, opt_tol, eq_tol, relax_opt_tol,
+                                               relax_eq_tol, max_iters, self._results))
         if raw:
             return self._results
         return [_result_dict(self._results[k], self.solvers[k].l) for k in range(self.n)]

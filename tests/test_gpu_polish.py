@@ -122,4 +122,6 @@ def test_polish_rejects_bad_arguments():
             b.polish(**args)
     with pytest.raises(pcba.PcbaError):
         b.solve_polished(eq_tol=1e-2, relax_eq_tol=1e-3)
+    with pytest.raises(pcba.PcbaError):
+        b.solve_polished(relax_opt_tol=0.0)
     b.close()
