@@ -272,10 +272,50 @@ __device__ __forceinline__ void cost_row_any(int K, const double* a, const int* 
   }
 }
 
+// Slice i of a constraint polynomial along axis 0 (the terms with x_0^i):
+// its value and (GRAD) gradient, x_0^i q_i(x_1..) and its derivatives, with
+// pw / dpw the tables of x_0^j and j x_0^(j-1).  The slices of a polynomial
+// add up to it; l = 1 has a single slice (the whole polynomial).
+template <int L, bool GRAD>
+__device__ __forceinline__ void poly_slice(const double* a, const int* deg, const int* stride,
+                                           const double* x, const double* pw, const double* dpw,
+                                           int i, double& v, double* g) {
+  if constexpr (L == 1) {
+    double Hd[1];
+    if (GRAD) PolyDiff<1, false>::eval(a, deg, stride, x, v, g, Hd);
+    else v = PolyVal<1>::eval(a, deg, stride, x);
+  } else {
+    const double* ai = a + (long long)i * stride[0];
+    if (GRAD) {
+      double vq, gq[L - 1], Hd[1];
+      PolyDiff<L - 1, false>::eval(ai, deg + 1, stride + 1, x + 1, vq, gq, Hd);
+      v = pw[i] * vq;
+      g[0] = dpw[i] * vq;
+#pragma unroll
+      for (int s = 0; s < L - 1; ++s) g[1 + s] = pw[i] * gq[s];
+    } else {
+      v = pw[i] * PolyVal<L - 1>::eval(ai, deg + 1, stride + 1, x + 1);
+    }
+  }
+}
+
+// lanes per constraint: the slices along axis 0, rounded up to a power of two
+__device__ __forceinline__ int polish_group(int L, int d0) {
+  if (L == 1) return 1;
+  int gs = 1;
+  while (gs < d0 + 1) gs <<= 1;
+  return gs;
+}
+
 // One block per problem; blocks of problems with l != L return at once (the
 // host launches one instantiation per dimension present).  Work items of a
 // block: the R rows of the cost (K outer axes, the fewest with R >= 32, at
-// most l - 1), then one item per inequality and per equality.  Problems with
+// most l - 1), then, for every inequality and every equality, a group of
+// lanes (a power of two) that evaluate its slices along axis 0 and add them
+// with warp shuffles; the three segments start at multiples of 32 so that a
+// warp never spans two of them, and the group's first lane takes the sum
+// (short dependency chains: the latency of FP64 FMAs, not their rate, bounds
+// this kernel).  Problems with
 // more than PCBA_MAXD equality constraints, infeasible ones and ones without
 // a point get a NaN row.  out: [np][PCBA_MAXD] doubles.
 //
@@ -325,7 +365,10 @@ __global__ void __launch_bounds__(PCBA_POLISH_TPB, 1)
   }
   int K = 0, R = 1;
   while (K < L - 1 && R < 32) R *= dP[K++] + 1;
-  const int items = R + alpha + beta;
+  const int gG = polish_group(L, dG[0]), gH = polish_group(L, dH[0]);
+  const int seg_g = (R + 31) & ~31;
+  const int seg_h = seg_g + ((alpha * gG + 31) & ~31);
+  const int items = seg_h + ((beta * gH + 31) & ~31);
   double* res = out + (long long)p * PCBA_MAXD;
   if (threadIdx.x == 0) {
     double x0[PCBA_MAXD];
@@ -338,6 +381,7 @@ __global__ void __launch_bounds__(PCBA_POLISH_TPB, 1)
   if (!s_has) return;
 
   // x_r^j, j x_r^(j-1), j (j-1) x_r^(j-2) for the outer axes of the cost rows
+  // (axis 0 among them whenever l > 1, which the constraint slices use)
   auto powers = [&](const double* xv) {
     for (int t = threadIdx.x; t < K * 17; t += PCBA_POLISH_TPB) {
       const int r = t / 17, jj = t - r * 17;
@@ -360,14 +404,27 @@ __global__ void __launch_bounds__(PCBA_POLISH_TPB, 1)
     double m[3] = {0.0, 0.0, 0.0};
     int feas = 1;
     for (int q = threadIdx.x; q < items; q += PCBA_POLISH_TPB) {
-      if (q < R) {
-        cost_row_any<L, false>(K, base, dP, tP, xv, spw, sdpw, sddpw, q, m[0], nullptr);
-      } else if (q < R + alpha) {
-        const double v = PolyVal<L>::eval(gbase + (long long)(q - R) * D->cg, dG, tG, xv);
-        if (v < 0.0) m[1] -= log(-v);
-        else feas = 0;
+      if (q < seg_g) {
+        if (q < R) cost_row_any<L, false>(K, base, dP, tP, xv, spw, sdpw, sddpw, q, m[0], nullptr);
       } else {
-        m[2] += fabs(PolyVal<L>::eval(hbase + (long long)(q - R - alpha) * D->ch, dH, tH, xv));
+        const bool is_g = q < seg_h;
+        const int gs = is_g ? gG : gH, u = q - (is_g ? seg_g : seg_h);
+        const int c = u / gs, sl = u - c * gs;
+        const bool live = c < (is_g ? alpha : beta) && sl <= (is_g ? dG[0] : dH[0]);
+        double v = 0.0;
+        if (live) {
+          double gd[1];
+          if (is_g)
+            poly_slice<L, false>(gbase + (long long)c * D->cg, dG, tG, xv, spw, sdpw, sl, v, gd);
+          else
+            poly_slice<L, false>(hbase + (long long)c * D->ch, dH, tH, xv, spw, sdpw, sl, v, gd);
+        }
+        for (int o = gs >> 1; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (sl == 0 && c < (is_g ? alpha : beta)) {
+          if (!is_g) m[2] += fabs(v);
+          else if (v < 0.0) m[1] -= log(-v);
+          else feas = 0;
+        }
       }
     }
     feas = __syncthreads_and(feas);
@@ -388,31 +445,49 @@ __global__ void __launch_bounds__(PCBA_POLISH_TPB, 1)
     for (int q = 0; q < ND; ++q) acc[q] = 0.0;
     int feas = 1;
     for (int q = threadIdx.x; q < items; q += PCBA_POLISH_TPB) {
-      if (q < R) {
-        cost_row_any<L, true>(K, base, dP, tP, xv, spw, sdpw, sddpw, q, acc[2 * NS], acc);
-      } else if (q < R + alpha) {
-        double v, g[L], Hd[1];
-        PolyDiff<L, false>::eval(gbase + (long long)(q - R) * D->cg, dG, tG, xv, v, g, Hd);
-        if (v < 0.0) {
-          acc[2 * NS + 1] -= log(-v);
-          const double inv = 1.0 / v;
-#pragma unroll
-          for (int s = 0; s < L; ++s) {
-            acc[NS + s] += g[s] * inv;
-#pragma unroll
-            for (int t = s; t < L; ++t) acc[NS + L + polish_tri(L, s, t)] += g[s] * g[t] * inv * inv;
-          }
-        } else {
-          feas = 0;
-        }
+      if (q < seg_g) {
+        if (q < R) cost_row_any<L, true>(K, base, dP, tP, xv, spw, sdpw, sddpw, q, acc[2 * NS], acc);
       } else {
-        double v, g[L], Hd[1];
-        const int jh = q - R - alpha;
-        PolyDiff<L, false>::eval(hbase + (long long)jh * D->ch, dH, tH, xv, v, g, Hd);
-        acc[2 * NS + 2] += fabs(v);
-        shv[d][jh] = v;
+        const bool is_g = q < seg_h;
+        const int gs = is_g ? gG : gH, u = q - (is_g ? seg_g : seg_h);
+        const int c = u / gs, sl = u - c * gs;
+        const bool live = c < (is_g ? alpha : beta) && sl <= (is_g ? dG[0] : dH[0]);
+        double v = 0.0, g[L];
 #pragma unroll
-        for (int s = 0; s < L; ++s) shg[d][jh * L + s] = g[s];
+        for (int r = 0; r < L; ++r) g[r] = 0.0;
+        if (live) {
+          if (is_g)
+            poly_slice<L, true>(gbase + (long long)c * D->cg, dG, tG, xv, spw, sdpw, sl, v, g);
+          else
+            poly_slice<L, true>(hbase + (long long)c * D->ch, dH, tH, xv, spw, sdpw, sl, v, g);
+        }
+        for (int o = gs >> 1; o > 0; o >>= 1) {
+          v += __shfl_xor_sync(0xffffffffu, v, o);
+#pragma unroll
+          for (int r = 0; r < L; ++r) g[r] += __shfl_xor_sync(0xffffffffu, g[r], o);
+        }
+        if (sl == 0 && c < (is_g ? alpha : beta)) {
+          if (is_g) {
+            if (v < 0.0) {
+              acc[2 * NS + 1] -= log(-v);
+              const double inv = 1.0 / v;
+#pragma unroll
+              for (int s2 = 0; s2 < L; ++s2) {
+                acc[NS + s2] += g[s2] * inv;
+#pragma unroll
+                for (int t = s2; t < L; ++t)
+                  acc[NS + L + polish_tri(L, s2, t)] += g[s2] * g[t] * inv * inv;
+              }
+            } else {
+              feas = 0;
+            }
+          } else {
+            acc[2 * NS + 2] += fabs(v);
+            shv[d][c] = v;
+#pragma unroll
+            for (int r = 0; r < L; ++r) shg[d][c * L + r] = g[r];
+          }
+        }
       }
     }
     feas = __syncthreads_and(feas);
