@@ -31,6 +31,11 @@ static_assert(PCBA_MAX_DIM == PCBA_MAXD, "dimension limits differ");
 
 namespace {
 
+// largest shared-memory copy of a problem's constraint coefficients made by
+// the candidate certification (k_cand_first); larger problems read them from
+// global memory
+constexpr size_t kCandStageMax = 200 * 1024;
+
 thread_local std::string g_err;
 
 int fail(int code, const std::string& msg) {
@@ -135,11 +140,10 @@ struct pcba_batch {
   EvalOut* d_eval = nullptr;
   double* d_cand = nullptr;     // guided solves: [np][cand_cap][PCBA_MAXD]
   float* d_ckey = nullptr;      // warm starts: [np][ckey_cap] FP32 cost bounds of candidates
-  unsigned* d_cviol = nullptr;  // warm starts: [np][ckey_cap] violation flags (by rank)
   int* d_corder = nullptr;      // warm starts: [np][ckey_cap] candidates in rank order
-  int* d_cres = nullptr;        // warm starts: [np] resolved flags
+  int* d_cres = nullptr;        // warm starts: [np] lowest certified-feasible rank
   long long ckey_cap = 0;
-  int cand_cmax = 0, cand_tiles = 1;  // largest constraint patch, constraint tiles of 32
+  long long cand_floats = 0;    // largest constraint coefficient count (alpha cg + beta ch)
   double* d_stencil = nullptr;  // guided solves: [stencil_cap] doubles
   double* d_polish = nullptr;   // pcba_batch_polish output: [np][PCBA_MAXD]
   // pcba_batch_solve_polished: the warm points are already in d_warm (written
@@ -179,6 +183,7 @@ struct pcba_batch {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaStream_t side = nullptr;                        // k_refresh beside k_pup..k4_index
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_k1f = nullptr, ev_k1j = nullptr;  // K1 on the side stream beside the warm start
   std::vector<cudaEvent_t> kev;
   Engine E{};
   Grids g;
@@ -315,12 +320,14 @@ void free_batch(pcba_batch* b) {
   if (b->ev1) cudaEventDestroy(b->ev1);
   if (b->ev_fork) cudaEventDestroy(b->ev_fork);
   if (b->ev_join) cudaEventDestroy(b->ev_join);
+  if (b->ev_k1f) cudaEventDestroy(b->ev_k1f);
+  if (b->ev_k1j) cudaEventDestroy(b->ev_k1j);
   if (b->ev_pipe) cudaEventDestroy(b->ev_pipe);
   if (b->side) cudaStreamDestroy(b->side);
   void* dev[] = {b->d_desc, b->d_state, b->d_plan, b->d_params, b->d_pre, b->d_arena, b->d_rec,
                  b->d_slots, b->d_tilecnt, b->d_mono, b->d_trace, b->d_warm, b->d_mat,
                  b->d_raw, b->d_eval, b->d_tmaps, b->d_marks, b->d_cand, b->d_stencil,
-                 b->d_mono32, b->d_ckey, b->d_cviol, b->d_corder, b->d_cres, b->d_polish};
+                 b->d_mono32, b->d_ckey, b->d_corder, b->d_cres, b->d_polish};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {b->h_state, b->h_eval, b->h_plan, b->h_params, b->h_running};
@@ -514,8 +521,8 @@ int setup_kernels(pcba_batch* b) {
     PCBA_CK(cudaMemcpyToSymbol(c_binom, binom, sizeof(binom)));
     PCBA_CK(cudaMemcpyToSymbol(c_binom_inv, binom_inv, sizeof(binom_inv)));
   }
-  PCBA_CK(cudaFuncSetAttribute(k_cand_feas, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               96 * 1024));
+  PCBA_CK(cudaFuncSetAttribute(k_cand_first<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)kCandStageMax));
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_classify, PCBA_TPB, 0));
   g.k3_grid = std::max(1, occ) * g.sms;
 
@@ -742,14 +749,11 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   PCBA_ALLOC(b->d_mono, sizeof(double) * mono);
   PCBA_ALLOC(b->d_mono32, sizeof(float) * mono);
   PCBA_ALLOC(b->d_ckey, sizeof(float) * n);
-  PCBA_ALLOC(b->d_cviol, sizeof(unsigned) * n);
   PCBA_ALLOC(b->d_corder, sizeof(int) * n);
   PCBA_ALLOC(b->d_cres, sizeof(int) * n);
   b->ckey_cap = 1;
-  for (const ProbDesc& d : b->desc) {
-    b->cand_cmax = std::max(b->cand_cmax, std::max(d.alpha ? d.cg : 0, d.beta ? d.ch : 0));
-    b->cand_tiles = std::max(b->cand_tiles, (d.alpha + d.beta + 31) / 32);
-  }
+  for (const ProbDesc& d : b->desc)
+    b->cand_floats = std::max(b->cand_floats, (long long)d.alpha * d.cg + (long long)d.beta * d.ch);
   PCBA_ALLOC(b->d_trace, sizeof(double) * 4 * trace_rows);
   PCBA_ALLOC(b->d_warm, sizeof(double) * PCBA_MAXD * n);
   PCBA_ALLOC(b->d_mat, sizeof(double) * 3 * PCBA_MAXD * 578 * n);
@@ -805,6 +809,10 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   if ((rc = cleanup_ck(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming), "event")))
     return rc;
   if ((rc = cleanup_ck(cudaEventCreateWithFlags(&b->ev_join, cudaEventDisableTiming), "event")))
+    return rc;
+  if ((rc = cleanup_ck(cudaEventCreateWithFlags(&b->ev_k1f, cudaEventDisableTiming), "event")))
+    return rc;
+  if ((rc = cleanup_ck(cudaEventCreateWithFlags(&b->ev_k1j, cudaEventDisableTiming), "event")))
     return rc;
   if ((rc = cleanup_ck(cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking), "stream")))
     return rc;
@@ -891,6 +899,16 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
     PCBA_CK(cudaMemsetAsync(b->d_warm, 0xFF, sizeof(double) * PCBA_MAXD * n, s));  // NaN
   Engine E1 = b->E;
   E1.root_raw = want_raw ? b->d_raw : nullptr;
+  // InitPatches (Alg. 1 line 1) writes only the root items; the warm-start
+  // kernels read the monomials and write candidate buffers and the seed
+  // fields of the state, so K1 runs on the side stream beside them and
+  // joins before k_init
+  PCBA_CK(cudaEventRecord(b->ev_k1f, s));
+  PCBA_CK(cudaStreamWaitEvent(b->side, b->ev_k1f, 0));
+  const int nmat = n * 3 * PCBA_MAXD * 17;
+  k1_matrices<<<(nmat + 255) / 256, 256, 0, b->side>>>(E1, b->d_mat);
+  k1_convert<T><<<b->g.k1_grid, 32 * b->g.k1_wpb, b->g.k1_smem, b->side>>>(E1, b->d_mat, b->g.k1_cmax,
+                                                                   b->g.k1_wpb);
   if (guide || have_warm) {
     const unsigned cg = (unsigned)std::min<long long>((b->mono_doubles + 255) / 256, 4LL * b->g.sms);
     k_mono32<<<cg, 256, 0, s>>>(b->d_mono, b->d_mono32, b->mono_doubles);
@@ -904,42 +922,25 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
     E1.warm = b->d_cand;
     E1.n_warm = guide->n;
   }
-  const int nmat = n * 3 * PCBA_MAXD * 17;
-  k1_matrices<<<(nmat + 255) / 256, 256, 0, s>>>(E1, b->d_mat);
-  k1_convert<T><<<b->g.k1_grid, 32 * b->g.k1_wpb, b->g.k1_smem, s>>>(E1, b->d_mat, b->g.k1_cmax,
-                                                                   b->g.k1_wpb);
-  // ranks [0, head) are certified first; later ranks only for problems that
-  // found no feasible candidate among the earlier ones
+  // candidates ranked by their FP32 cost bound; the lowest certified-feasible
+  // rank seeds p_up (the constraint coefficients staged in shared memory when
+  // they fit)
   auto certify = [&](const Engine& Ec) -> int {
-    const int head = std::min(Ec.n_warm, 32);
-    const size_t cand_smem = sizeof(float) * ((size_t)32 * b->cand_cmax +
-                                              (size_t)std::min(Ec.n_warm, 1024) * b->max_l);
-    const bool cand_fast =
-        b->cand_cmax <= 512 && cand_smem <= 96 * 1024 && b->ckey_cap >= Ec.n_warm;
-    if (!cand_fast) {
+    if (b->ckey_cap < Ec.n_warm || Ec.n_warm > PCBA_MAX_CAND) {
       k_eval<<<n, PCBA_TPB, 0, s>>>(Ec, 0, nullptr);
       return 0;
     }
     const long long nc = (long long)n * Ec.n_warm;
-    const dim3 fgrid((unsigned)b->cand_tiles, (unsigned)n);
-    PCBA_CK(cudaMemsetAsync(b->d_cviol, 0, sizeof(unsigned) * (size_t)nc, s));
     k_cand_cost<<<(unsigned)std::min<long long>((nc + 255) / 256, 8LL * b->g.sms), 256, 0, s>>>(
         Ec, b->d_ckey);
-    k_cand_rank<<<n, PCBA_TPB, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres);
-    k_cand_feas<<<fgrid, 256, cand_smem, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres, b->d_cviol,
-                                              b->cand_cmax, 0, head);
+    k_cand_rank<<<n, PCBA_TPB, 0, s>>>(Ec, b->d_ckey, b->d_corder);
+    const size_t stage = sizeof(float) * (size_t)b->cand_floats;
+    if (stage <= kCandStageMax)
+      k_cand_first<true><<<n, 256, stage, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres);
+    else
+      k_cand_first<false><<<n, 256, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres);
+    k_cand_pick<<<(n + 127) / 128, 128, 0, s>>>(Ec, b->d_corder, b->d_cres);
     b->extra_launches += 3;
-    // later ranks in geometrically growing groups, each only for the problems
-    // still without a certified-feasible candidate
-    for (int r0 = head; r0 < Ec.n_warm;) {
-      const int r1 = std::min(Ec.n_warm, 4 * r0);
-      k_cand_check<<<n, 128, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cviol, b->d_cres, r0);
-      k_cand_feas<<<fgrid, 256, cand_smem, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres,
-                                                b->d_cviol, b->cand_cmax, r0, r1);
-      b->extra_launches += 2;
-      r0 = r1;
-    }
-    k_cand_pick<<<n, PCBA_TPB, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cviol);
     return 0;
   };
   if (guide || have_warm) {
@@ -963,6 +964,8 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   } else {
     k_eval<<<n, PCBA_TPB, 0, s>>>(E1, 0, nullptr);
   }
+  PCBA_CK(cudaEventRecord(b->ev_k1j, b->side));
+  PCBA_CK(cudaStreamWaitEvent(s, b->ev_k1j, 0));
   k_init<<<1, PCBA_TPB, 0, s>>>(E1);
   PCBA_CK(cudaGetLastError());
   b->subdiv_ms = 0;
@@ -1294,15 +1297,11 @@ int pcba_batch_solve_guided(pcba_batch* b, double opt_tol, double eq_tol, int ma
   }
   if (b->ckey_cap < n_cap) {
     if (b->d_ckey) cudaFree(b->d_ckey);
-    if (b->d_cviol) cudaFree(b->d_cviol);
     if (b->d_corder) cudaFree(b->d_corder);
     b->d_ckey = nullptr;
-    b->d_cviol = nullptr;
     b->d_corder = nullptr;
     b->ckey_cap = 0;
     if (cudaMalloc((void**)&b->d_ckey, sizeof(float) * (size_t)b->np * n_cap) != cudaSuccess ||
-        cudaMalloc((void**)&b->d_cviol, sizeof(unsigned) * (size_t)b->np * n_cap) !=
-            cudaSuccess ||
         cudaMalloc((void**)&b->d_corder, sizeof(int) * (size_t)b->np * n_cap) != cudaSuccess)
       return fail(PCBA_ERR_OOM, "candidate key allocation failed");
     b->ckey_cap = n_cap;

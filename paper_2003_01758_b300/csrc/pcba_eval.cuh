@@ -388,12 +388,12 @@ __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* res
 }
 
 // ---------------------------------------------------------------------------
-// Warm start over many candidates, spread over the whole GPU: the same choice
-// as k_eval mode 0 (the certified-feasible candidate with the lowest FP32
-// cost bound, ties to the lower index, its FP64 cost bound as p_up), computed
-// as (1) every candidate's FP32 cost bound, (2) every (candidate, constraint)
-// pair in FP32 with its error bound, one block per (problem, 32 constraints)
-// with the coefficients in shared memory, and (3) a per-problem argmin.
+// Warm start over many candidates: the same choice as k_eval mode 0 (the
+// certified-feasible candidate with the lowest FP32 cost bound, ties to the
+// lower index, its FP64 cost bound as p_up), computed as (1) every
+// candidate's FP32 cost bound, (2) the candidates ranked by it, (3) the lowest
+// feasible rank per problem, candidates dropped at their first violated
+// bound, and (4) the FP64 cost bound of that candidate.
 // ---------------------------------------------------------------------------
 __global__ void k_cand_cost(Engine E, float* key) {
   const long long total = (long long)E.np * E.n_warm;
@@ -417,9 +417,8 @@ __global__ void k_cand_cost(Engine E, float* key) {
 
 // Ranks the candidates of problem p by (FP32 cost bound, index): one block per
 // problem, bitonic sort in shared memory (at most PCBA_MAX_CAND candidates);
-// order[p][rank] = candidate index.  resolved[p] is cleared.
-__global__ void __launch_bounds__(PCBA_TPB) k_cand_rank(Engine E, const float* key, int* order,
-                                                        int* resolved) {
+// order[p][rank] = candidate index.
+__global__ void __launch_bounds__(PCBA_TPB) k_cand_rank(Engine E, const float* key, int* order) {
   __shared__ float s_key[PCBA_MAX_CAND];
   __shared__ int s_id[PCBA_MAX_CAND];
   const int p = blockIdx.x;
@@ -430,7 +429,6 @@ __global__ void __launch_bounds__(PCBA_TPB) k_cand_rank(Engine E, const float* k
     s_key[c] = c < n_c ? key[(long long)p * E.n_warm + c] : INFINITY;
     s_id[c] = c < n_c ? c : 0x7fffffff;
   }
-  if (threadIdx.x == 0) resolved[p] = 0;
   __syncthreads();
   for (int k = 2; k <= n2; k <<= 1)
     for (int j = k >> 1; j > 0; j >>= 1) {
@@ -449,108 +447,115 @@ __global__ void __launch_bounds__(PCBA_TPB) k_cand_rank(Engine E, const float* k
   for (int c = threadIdx.x; c < n_c; c += PCBA_TPB) order[(long long)p * E.n_warm + c] = s_id[c];
 }
 
-// Certifies the candidates of ranks [r0, r1) of every problem not yet
-// resolved: grid (constraint tiles, problems); dynamic shared memory: 32 * cmax
-// floats of coefficients, then (r1 - r0) * l floats of coordinates.
-// viol[p][rank] is set when a constraint bound exceeds its limit.
-__global__ void __launch_bounds__(256) k_cand_feas(Engine E, const float* key, const int* order,
-                                                   const int* resolved, unsigned* viol, int cmax,
-                                                   int r0, int r1) {
-  extern __shared__ float kcs[];
-  const int p = blockIdx.y;
-  if (resolved[p]) return;
+// The lowest rank whose candidate is certified feasible, per problem: one
+// block per problem.  Warps take ranks in increasing order from a shared
+// counter; a warp checks its candidate against 32 constraints at a time (lane
+// i: constraint 32 t + i, FP32 Horner with its error bound, FP64 where that
+// is undecided) and drops it at the first tile with a violated bound.  The
+// tiles that dropped recent candidates (a ring of 4) are tried first:
+// candidates of neighbouring cost tend to fail on the same constraints.  A
+// rank is skipped once a lower one is known feasible, so the result is the
+// minimum feasible rank whatever the order in which warps finish.  STAGE: the
+// constraint coefficients (FP32) are first copied to shared memory.
+// first[p] = that rank, or INT_MAX.
+template <bool STAGE>
+__global__ void __launch_bounds__(256) k_cand_first(Engine E, const float* key, const int* order,
+                                                    int* first) {
+  extern __shared__ float kcf[];
+  __shared__ int s_next, s_best, s_kpos;
+  __shared__ int s_killer[4];
+  const int p = blockIdx.x;
   const ProbDesc* D = E.desc + p;
-  const int total = D->alpha + D->beta;
-  const int q0 = blockIdx.x * 32;
-  if (q0 >= total) return;
+  const int l = D->l, alpha = D->alpha, total = D->alpha + D->beta;
+  const int tiles = (total + 31) >> 5;
   const int n_c = min(E.n_warm, PCBA_MAX_CAND);
-  r1 = min(r1, n_c);
-  if (r0 >= r1) return;
-  const int nr = r1 - r0;
-  const int nq = min(32, total - q0);
-  const int l = D->l;
-  float* sa = kcs;
-  float* sx = kcs + 32 * cmax;
   const long long base = (long long)p * E.n_warm;
-  const float* mono32 = E.mono32 + D->mono_off;
-  for (int t = threadIdx.x; t < nq * cmax; t += blockDim.x) {
-    const int qi = t / cmax, j = t - qi * cmax;
-    const int q = q0 + qi;
-    const bool is_g = q < D->alpha;
-    const int C = is_g ? D->cg : D->ch;
-    if (j < C) {
-      const float* a = is_g ? mono32 + D->cp + (long long)q * D->cg
-                            : mono32 + D->cp + (long long)D->alpha * D->cg +
-                                  (long long)(q - D->alpha) * D->ch;
-      sa[qi * cmax + j] = a[j];
-    }
-  }
-  for (int t = threadIdx.x; t < nr * l; t += blockDim.x) {
-    const int rr = t / l, r = t - rr * l;
-    const int c = order[base + r0 + rr];
-    sx[t] = (float)E.warm[(base + c) * PCBA_MAXD + r];
+  const long long nf = (long long)alpha * D->cg + (long long)D->beta * D->ch;
+  const float* src = E.mono32 + D->mono_off + D->cp;
+  if (STAGE)
+    for (long long t = threadIdx.x; t < nf; t += blockDim.x) kcf[t] = src[t];
+  const float* coef = STAGE ? kcf : src;
+  if (threadIdx.x == 0) {
+    s_next = 0;
+    s_best = 0x7fffffff;
+    s_kpos = 0;
+    for (int k = 0; k < 4; ++k) s_killer[k] = -1;
   }
   __syncthreads();
+  const int lane = threadIdx.x & 31;
   const float eq_tol = __double2float_rd(E.params->eq_tol);  // never above eq_tol
-  for (int t = threadIdx.x; t < nr * nq; t += blockDim.x) {
-    const int rr = t / nq, qi = t - rr * nq;
-    const int rank = r0 + rr;
-    if (!(key[base + order[base + rank]] < INFINITY)) continue;
-    const int q = q0 + qi;
-    const bool is_g = q < D->alpha;
-    float val, err;
-    horner_f32(sa + qi * cmax, l, is_g ? D->G : D->H, sx + rr * l, &val, &err);
-    const float lim = is_g ? 0.0f : eq_tol;
-    if (__fadd_ru(is_g ? val : fabsf(val), err) <= lim) continue;  // certified in FP32
-    bool bad = true;
-    if (__fsub_rd(is_g ? val : fabsf(val), err) <= lim) {
-      // undecided in FP32 (the point is within the bound of the limit): decide
-      // in FP64 on the FP64 coefficients at the same (FP32) point
-      double xd[PCBA_MAXD];
-      for (int r = 0; r < l; ++r) xd[r] = (double)sx[rr * l + r];
-      const double* a = is_g ? E.mono + D->mono_off + D->cp + (long long)q * D->cg
-                             : E.mono + D->mono_off + D->cp + (long long)D->alpha * D->cg +
-                                   (long long)(q - D->alpha) * D->ch;
-      double v64, e64;
-      horner_f64(a, l, is_g ? D->G : D->H, xd, &v64, &e64);
-      bad = !(__dadd_ru(is_g ? v64 : fabs(v64), e64) <= (is_g ? 0.0 : E.params->eq_tol));
+  for (;;) {
+    // lane 0 reads the shared state and broadcasts it, so that the warp stays
+    // converged for its vote
+    int rank = 0, stop = 0;
+    if (lane == 0) {
+      rank = atomicAdd(&s_next, 1);
+      stop = rank >= n_c || rank >= *(volatile int*)&s_best;
     }
-    if (bad) viol[base + rank] = 1u;
+    rank = __shfl_sync(0xffffffffu, rank, 0);
+    if (__shfl_sync(0xffffffffu, stop, 0)) break;
+    const int c = order[base + rank];
+    if (!(key[base + c] < INFINITY)) continue;  // no candidate point
+    float xf[PCBA_MAXD];
+    for (int r = 0; r < l; ++r) xf[r] = (float)E.warm[(base + c) * PCBA_MAXD + r];
+    int kill[4];
+    for (int k = 0; k < 4; ++k)
+      kill[k] = __shfl_sync(0xffffffffu, lane == 0 ? *(volatile int*)&s_killer[k] : 0, 0);
+    bool bad = false;
+    for (int step = 0; step < 4 + tiles && !bad; ++step) {
+      int t;
+      if (step < 4) {
+        t = kill[step];
+        bool dup = t < 0;
+        for (int k = 0; k < step; ++k) dup = dup || kill[k] == t;
+        if (dup) continue;
+      } else {
+        t = step - 4;
+        if (t == kill[0] || t == kill[1] || t == kill[2] || t == kill[3]) continue;
+      }
+      const int q = t * 32 + lane;
+      bool lane_bad = false;
+      if (q < total) {
+        const bool is_g = q < alpha;
+        const long long off = is_g ? (long long)q * D->cg
+                                   : (long long)alpha * D->cg + (long long)(q - alpha) * D->ch;
+        float val, err;
+        horner_f32(coef + off, l, is_g ? D->G : D->H, xf, &val, &err);
+        const float lim = is_g ? 0.0f : eq_tol;
+        if (!(__fadd_ru(is_g ? val : fabsf(val), err) <= lim)) {
+          lane_bad = true;
+          if (__fsub_rd(is_g ? val : fabsf(val), err) <= lim) {
+            // undecided in FP32: decide in FP64 on the FP64 coefficients at
+            // the same (FP32) point
+            double xd[PCBA_MAXD];
+            for (int r = 0; r < l; ++r) xd[r] = (double)xf[r];
+            double v64, e64;
+            horner_f64(E.mono + D->mono_off + D->cp + off, l, is_g ? D->G : D->H, xd, &v64, &e64);
+            lane_bad = !(__dadd_ru(is_g ? v64 : fabs(v64), e64) <= (is_g ? 0.0 : E.params->eq_tol));
+          }
+        }
+      }
+      if (__any_sync(0xffffffffu, lane_bad)) {
+        bad = true;
+        if (lane == 0) s_killer[atomicAdd(&s_kpos, 1) & 3] = t;
+      }
+    }
+    if (!bad && lane == 0) atomicMin(&s_best, rank);
   }
-}
-
-// After the ranks [0, r1) were checked: a problem is resolved when one of
-// them is certified feasible (a lower rank always wins).
-__global__ void k_cand_check(Engine E, const float* key, const int* order, const unsigned* viol,
-                             int* resolved, int r1) {
-  const int p = blockIdx.x;
-  const int n_c = min(E.n_warm, PCBA_MAX_CAND);
-  const long long base = (long long)p * E.n_warm;
-  int ok = 0;
-  for (int r = threadIdx.x; r < min(r1, n_c); r += blockDim.x)
-    if (key[base + order[base + r]] < INFINITY && viol[base + r] == 0u) ok = 1;
-  ok = __syncthreads_or(ok);
-  if (threadIdx.x == 0) resolved[p] = ok;
+  __syncthreads();
+  if (threadIdx.x == 0) first[p] = s_best;
 }
 
 // The first certified-feasible candidate in rank order seeds p_up with its
 // FP64 cost bound.
-__global__ void __launch_bounds__(PCBA_TPB) k_cand_pick(Engine E, const float* key,
-                                                        const int* order, const unsigned* viol) {
-  __shared__ int s_r[PCBA_TPB / 32];
-  const int p = blockIdx.x;
+__global__ void k_cand_pick(Engine E, const int* order, const int* first) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= E.np) return;
   const ProbDesc* D = E.desc + p;
   ProbState* S = E.state + p;
   const int n_c = min(E.n_warm, PCBA_MAX_CAND);
   const long long base = (long long)p * E.n_warm;
-  int br = 0x7fffffff;
-  for (int r = threadIdx.x; r < n_c; r += PCBA_TPB)
-    if (r < br && key[base + order[base + r]] < INFINITY && viol[base + r] == 0u) br = r;
-  for (int o = 16; o > 0; o >>= 1) br = min(br, __shfl_xor_sync(0xffffffffu, br, o));
-  if ((threadIdx.x & 31) == 0) s_r[threadIdx.x >> 5] = br;
-  __syncthreads();
-  if (threadIdx.x != 0) return;
-  for (int w = 1; w < PCBA_TPB / 32; ++w) br = min(br, s_r[w]);
+  const int br = first[p];
   const int l = D->l;
   double x[PCBA_MAXD];
   double offer = INFINITY;
