@@ -259,7 +259,8 @@ __constant__ double c_binom_inv[17 * 17];
 
 // T_r[i][j] = sum_k C(i,k) C(j,k) / C(n,k) lo^(j-k) w^k (power basis on the
 // box -> Bernstein basis), and A_r its absolute-value sum widened by 2^-40,
-// which covers the few roundings of every term (the reciprocal included).
+// which covers the few roundings of every term (the reciprocal included),
+// stored as floats rounded up (the 289 floats after T_r's 289 doubles).
 __device__ __forceinline__ void refresh_matrices(const double* binom, int l, const int* deg,
                                                  const double* blo, const double* bhi,
                                                  double* sT, int lane) {
@@ -276,7 +277,7 @@ __device__ __forceinline__ void refresh_matrices(const double* binom, int l, con
       wp[e] = wp[e - 1] * w;
     }
     double* T = sT + r * 578;
-    double* A = T + 289;
+    float* A = (float*)(T + 289);
     for (int e = lane; e < (n + 1) * (n + 1); e += 32) {
       const int i = e / (n + 1), j = e - (e / (n + 1)) * (n + 1);
       double t = 0.0, ta = 0.0;
@@ -288,7 +289,7 @@ __device__ __forceinline__ void refresh_matrices(const double* binom, int l, con
         ta += fabs(term);
       }
       T[e] = t;
-      A[e] = ta * (1.0 + 0x1p-40);
+      A[e] = __double2float_ru(ta * (1.0 + 0x1p-40));
     }
   }
   __syncwarp();
@@ -296,13 +297,17 @@ __device__ __forceinline__ void refresh_matrices(const double* binom, int l, con
 
 // Warp-cooperative conversion of one monomial tensor a (C coefficients,
 // multi-degree deg) with the matrices in sT; result in *sA, bound base in *sX.
+// The bound base (|A_1| x ... x |A_l|) |a| is carried in FP32 with every
+// input and every fused multiply-add rounded up, so it stays an upper bound
+// of the exact product and costs no FP64 operations (a value beyond the FP32
+// range gives an infinite bound: the patch is then never decided on).
 __device__ __forceinline__ double refresh_convert(const double* a, int C, int l, const int* deg,
                                                   const double* sT, double*& sA, double*& sB,
-                                                  double*& sX, double*& sY, int lane) {
+                                                  float*& sX, float*& sY, int lane) {
   for (int j = lane; j < C; j += 32) {
     const double v = a[j];
     sA[j] = v;
-    sX[j] = fabs(v);
+    sX[j] = __double2float_ru(fabs(v));
   }
   __syncwarp();
   double gterms = 0.0;
@@ -311,7 +316,7 @@ __device__ __forceinline__ double refresh_convert(const double* a, int C, int l,
     int stride = 1;
     for (int q = r + 1; q < l; ++q) stride *= deg[q] + 1;
     const double* T = sT + r * 578;
-    const double* A = T + 289;
+    const float* A = (const float*)(T + 289);
     gterms += 4.0 * n + 8.0;
     const int blk = (n + 1) * stride;
     for (int o = lane; o < C; o += 32) {
@@ -320,23 +325,24 @@ __device__ __forceinline__ double refresh_convert(const double* a, int C, int l,
       const int i = rem / stride;
       const int in = rem - i * stride;
       const double* src = sA + hp * blk + in;
-      const double* srcx = sX + hp * blk + in;
-      double s = 0.0, sx = 0.0;
+      const float* srcx = sX + hp * blk + in;
+      double s = 0.0;
+      float sx = 0.0f;
       for (int j = 0; j <= n; ++j) {
         s = fma(T[i * (n + 1) + j], src[j * stride], s);
-        sx = __dadd_ru(sx, __dmul_ru(A[i * (n + 1) + j], srcx[j * stride]));
+        sx = __fmaf_ru(A[i * (n + 1) + j], srcx[j * stride], sx);
       }
       sB[o] = s;
       sY[o] = sx;
     }
     __syncwarp();
     double* t = sA; sA = sB; sB = t;
-    t = sX; sX = sY; sY = t;
+    float* tf = sX; sX = sY; sY = tf;
   }
-  double amax = 0.0;
-  for (int j = lane; j < C; j += 32) amax = fmax(amax, sX[j]);
-  for (int o = 16; o > 0; o >>= 1) amax = fmax(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  return __dmul_ru(__dmul_ru(2.0 * gterms, 0x1p-53), amax);
+  float amax = 0.0f;
+  for (int j = lane; j < C; j += 32) amax = fmaxf(amax, sX[j]);
+  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
+  return __dmul_ru(__dmul_ru(2.0 * gterms, 0x1p-53), (double)amax);
 }
 
 __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
@@ -349,11 +355,14 @@ __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
   double* wbase = krs + (size_t)warp * (4 * cmax + 2 * 289 * lmax);
   double* sA = wbase;
   double* sB = sA + cmax;
-  double* sX = sB + cmax;
-  double* sY = sX + cmax;
-  double* sT = sY + cmax;
+  float* sX = (float*)(sB + cmax);
+  float* sY = (float*)(sB + 2 * cmax);
+  double* sT = sB + 3 * cmax;
   const uint4* list = E.marks + (size_t)par * E.mark_cap;
-  for (unsigned q = blockIdx.x * wpb + warp; q < count; q += gridDim.x * wpb) {
+  // marks are few (tens to hundreds per step) and each is a chain of FP64
+  // work: warp-major numbering spreads consecutive marks over blocks (SMs)
+  // instead of stacking them on the FP64 units of one SM
+  for (unsigned q = warp * gridDim.x + blockIdx.x; q < count; q += gridDim.x * wpb) {
     const uint4 m = list[q];
     const int p = (int)m.x, fam = (int)m.z, ip = (int)m.w;
     const ProbDesc* D = E.desc + p;
