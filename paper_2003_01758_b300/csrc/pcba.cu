@@ -933,13 +933,15 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
     const long long nc = (long long)n * Ec.n_warm;
     k_cand_cost<<<(unsigned)std::min<long long>((nc + 255) / 256, 8LL * b->g.sms), 256, 0, s>>>(
         Ec, b->d_ckey);
-    k_cand_rank<<<n, PCBA_TPB, 0, s>>>(Ec, b->d_ckey, b->d_corder);
+    k_cand_rank<<<n, PCBA_TPB, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres);
     const size_t stage = sizeof(float) * (size_t)b->cand_floats;
+    // blocks per problem: enough to cover about twice the SMs, at most 4
+    const dim3 fgrid((unsigned)n, (unsigned)std::max(1, std::min(4, 2 * b->g.sms / std::max(1, n))));
     if (stage <= kCandStageMax)
-      k_cand_first<true><<<n, 256, stage, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres);
+      k_cand_first<true><<<fgrid, PCBA_CAND_TPB, stage, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres);
     else
-      k_cand_first<false><<<n, 256, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres);
-    k_cand_pick<<<(n + 127) / 128, 128, 0, s>>>(Ec, b->d_corder, b->d_cres);
+      k_cand_first<false><<<fgrid, PCBA_CAND_TPB, 0, s>>>(Ec, b->d_ckey, b->d_corder, b->d_cres);
+    k_cand_pick<<<n, 32, 0, s>>>(Ec, b->d_corder, b->d_cres);
     b->extra_launches += 3;
     return 0;
   };

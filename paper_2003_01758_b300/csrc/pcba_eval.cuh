@@ -34,6 +34,7 @@ __global__ void k_mono32(const double* mono, float* out, long long n) {
 
 #define PCBA_EVAL_CHUNK 8
 #define PCBA_MAX_CAND 1024
+#define PCBA_CAND_TPB 512  // threads of k_cand_first
 
 // Nested Horner evaluation in FP32 of a dense monomial tensor (coefficients
 // a = the FP64 ones rounded to nearest FP32, row-major, last axis fastest) at
@@ -417,8 +418,9 @@ __global__ void k_cand_cost(Engine E, float* key) {
 
 // Ranks the candidates of problem p by (FP32 cost bound, index): one block per
 // problem, bitonic sort in shared memory (at most PCBA_MAX_CAND candidates);
-// order[p][rank] = candidate index.
-__global__ void __launch_bounds__(PCBA_TPB) k_cand_rank(Engine E, const float* key, int* order) {
+// order[p][rank] = candidate index; first[p] is reset to INT_MAX.
+__global__ void __launch_bounds__(PCBA_TPB) k_cand_rank(Engine E, const float* key, int* order,
+                                                        int* first) {
   __shared__ float s_key[PCBA_MAX_CAND];
   __shared__ int s_id[PCBA_MAX_CAND];
   const int p = blockIdx.x;
@@ -445,6 +447,7 @@ __global__ void __launch_bounds__(PCBA_TPB) k_cand_rank(Engine E, const float* k
       __syncthreads();
     }
   for (int c = threadIdx.x; c < n_c; c += PCBA_TPB) order[(long long)p * E.n_warm + c] = s_id[c];
+  if (threadIdx.x == 0) first[p] = 0x7fffffff;
 }
 
 // The lowest rank whose candidate is certified feasible, per problem: one
@@ -459,12 +462,15 @@ __global__ void __launch_bounds__(PCBA_TPB) k_cand_rank(Engine E, const float* k
 // constraint coefficients (FP32) are first copied to shared memory.
 // first[p] = that rank, or INT_MAX.
 template <bool STAGE>
-__global__ void __launch_bounds__(256) k_cand_first(Engine E, const float* key, const int* order,
-                                                    int* first) {
+__global__ void __launch_bounds__(PCBA_CAND_TPB, 1) k_cand_first(Engine E, const float* key,
+                                                              const int* order, int* first) {
   extern __shared__ float kcf[];
   __shared__ int s_next, s_best, s_kpos;
   __shared__ int s_killer[4];
   const int p = blockIdx.x;
+  // gridDim.y blocks share a problem: block y takes ranks y, y + gridDim.y, ...
+  // and all of them lower first[p] (set to INT_MAX by k_cand_rank)
+  const int nb = gridDim.y, by = blockIdx.y;
   const ProbDesc* D = E.desc + p;
   const int l = D->l, alpha = D->alpha, total = D->alpha + D->beta;
   const int tiles = (total + 31) >> 5;
@@ -489,7 +495,9 @@ __global__ void __launch_bounds__(256) k_cand_first(Engine E, const float* key, 
     // converged for its vote
     int rank = 0, stop = 0;
     if (lane == 0) {
-      rank = atomicAdd(&s_next, 1);
+      rank = atomicAdd(&s_next, 1) * nb + by;
+      if (nb > 1 && rank < *(volatile int*)&s_best)
+        atomicMin(&s_best, *(volatile int*)&first[p]);  // ranks found by the other blocks
       stop = rank >= n_c || rank >= *(volatile int*)&s_best;
     }
     rank = __shfl_sync(0xffffffffu, rank, 0);
@@ -540,17 +548,20 @@ __global__ void __launch_bounds__(256) k_cand_first(Engine E, const float* key, 
         if (lane == 0) s_killer[atomicAdd(&s_kpos, 1) & 3] = t;
       }
     }
-    if (!bad && lane == 0) atomicMin(&s_best, rank);
+    if (!bad && lane == 0) {
+      atomicMin(&s_best, rank);
+      atomicMin(&first[p], rank);
+    }
   }
-  __syncthreads();
-  if (threadIdx.x == 0) first[p] = s_best;
 }
 
 // The first certified-feasible candidate in rank order seeds p_up with its
 // FP64 cost bound.
 __global__ void k_cand_pick(Engine E, const int* order, const int* first) {
-  const int p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= E.np) return;
+  // one problem per block: the FP64 evaluation is a long chain of slow
+  // dependent operations, best kept on SMs of its own
+  const int p = blockIdx.x;
+  if (p >= E.np || threadIdx.x != 0) return;
   const ProbDesc* D = E.desc + p;
   ProbState* S = E.state + p;
   const int n_c = min(E.n_warm, PCBA_MAX_CAND);
