@@ -86,32 +86,34 @@ __device__ __forceinline__ void constraint_fibres(T* src, T* dR, size_t pad, int
   }
 }
 
-// One cost fibre into shared staging buffers (same in-place triangle).
+// One cost fibre into shared staging buffers (same in-place triangle).  The
+// extremes are kept in the patch's own type (a min or max of stored values is
+// exact in it): in FP32 this keeps the long per-fibre chains off the FP64 units.
 template <typename T, int N>
 __device__ __forceinline__ void cost_fibre(const T* src, T* sL, T* sR, int base, int stride,
-                                           double (&v)[5]) {
+                                           T (&v)[5]) {
   T q[N + 1];
 #pragma unroll
   for (int j = 0; j <= N; ++j) {
     q[j] = src[base + j * stride];
-    v[4] = fmax(v[4], (double)fabs(q[j]));
+    v[4] = max(v[4], abs(q[j]));
   }
   sL[base] = q[0];
   sR[base + N * stride] = q[N];
-  v[0] = fmax(v[0], -(double)q[0]);
-  v[1] = fmax(v[1], (double)q[0]);
-  v[2] = fmax(v[2], -(double)q[N]);
-  v[3] = fmax(v[3], (double)q[N]);
+  v[0] = max(v[0], -q[0]);
+  v[1] = max(v[1], q[0]);
+  v[2] = max(v[2], -q[N]);
+  v[3] = max(v[3], q[N]);
 #pragma unroll
   for (int k = 1; k <= N; ++k) {
 #pragma unroll
     for (int j = 0; j <= N - k; ++j) q[j] = mulrn(addrn(q[j], q[j + 1]), T(0.5));
     sL[base + k * stride] = q[0];
     sR[base + (N - k) * stride] = q[N - k];
-    v[0] = fmax(v[0], -(double)q[0]);
-    v[1] = fmax(v[1], (double)q[0]);
-    v[2] = fmax(v[2], -(double)q[N - k]);
-    v[3] = fmax(v[3], (double)q[N - k]);
+    v[0] = max(v[0], -q[0]);
+    v[1] = max(v[1], q[0]);
+    v[2] = max(v[2], -q[N - k]);
+    v[3] = max(v[3], q[N - k]);
   }
 }
 
@@ -245,15 +247,21 @@ __device__ void cost_part(const ProbDesc* D, const char* head, char* parent, cha
     O = *(const double*)(head + 32);
     ep = (double)*(const float*)(head + 40);
   }
-  double v[5] = {-INFINITY, -INFINITY, -INFINITY, -INFINITY, 0.0};
+  T vt[5] = {T(-INFINITY), T(-INFINITY), T(-INFINITY), T(-INFINITY), T(0)};
   for (int f = lane; f < nf; f += 32) {
     const int o = f / stride;
     const int base = o * blk + (f - o * stride);
     dispatch_fixed<NMAX, NFIX>(n, [&](auto nc) {
-      cost_fibre<T, decltype(nc)::value>(src, sL, sR, base, stride, v);
+      cost_fibre<T, decltype(nc)::value>(src, sL, sR, base, stride, vt);
     });
   }
-  warp_max_d<5>(v);
+#pragma unroll
+  for (int q = 0; q < 5; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) vt[q] = max(vt[q], __shfl_xor_sync(0xffffffffu, vt[q], o));
+  double v[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) v[q] = (double)vt[q];
   __syncwarp();
   const double minL = -v[0], maxL = v[1], minR = -v[2], maxR = v[3];
   if constexpr (sizeof(T) == 8) {
