@@ -218,6 +218,25 @@ __device__ __forceinline__ void warp_max_d(double (&v)[NV]) {
   }
 }
 
+// Layout of the cost patch along the bisection axis r: coefficient count,
+// degree, stride of the axis, fibre count, block of one outer index, offset
+// in the item.  The TMA kernel loads it with the per-problem context, before
+// the wait for the unit's copies, so its reads overlap that wait.
+struct CostGeom {
+  int cp, n, stride, nf, blk;
+  long long off;
+};
+__device__ __forceinline__ CostGeom cost_geom(const ProbDesc* D, int r) {
+  CostGeom g;
+  g.cp = D->cp;
+  g.n = D->P[r];
+  g.stride = axis_stride(D->P, D->l, r);
+  g.nf = g.cp / (g.n + 1);
+  g.blk = (g.n + 1) * g.stride;
+  g.off = D->off_cost;
+  return g;
+}
+
 // Cost patch of one parent, processed by one warp (tile 0, warp 0).
 // FP64: children stored as computed.  FP32: each child is re-centred on the
 // middle of its stored range, and its error bound grows by
@@ -228,18 +247,14 @@ __device__ __forceinline__ void warp_max_d(double (&v)[NV]) {
 // head: where the parent's head bytes (box, meta, cost) are read from: the
 // parent item itself, or a shared-memory copy of them.
 template <typename T, int NMAX, int NFIX = 0>
-__device__ void cost_part(const ProbDesc* D, const char* head, char* parent, char* right, int r,
+__device__ void cost_part(const CostGeom& cg, const char* head, char* parent, char* right,
                           ChildRec* recL, ChildRec* recR, T* stage, const MarkCtx& mk,
                           double cost_thr) {
   const int lane = threadIdx.x & 31;
-  const int cp = D->cp;
-  const int n = D->P[r];
-  const int stride = axis_stride(D->P, D->l, r);
-  const int nf = cp / (n + 1);
-  const int blk = (n + 1) * stride;
-  const T* src = (const T*)(head + D->off_cost);
-  T* dstL = (T*)(parent + D->off_cost);
-  T* dstR = (T*)(right + D->off_cost);
+  const int cp = cg.cp, n = cg.n, stride = cg.stride, nf = cg.nf, blk = cg.blk;
+  const T* src = (const T*)(head + cg.off);
+  T* dstL = (T*)(parent + cg.off);
+  T* dstR = (T*)(right + cg.off);
   T* sL = stage;
   T* sR = stage + cp;
   double O = 0.0, ep = 0.0;
@@ -500,7 +515,8 @@ __global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
     const MarkCtx mk{p, k, k + K, E.marks + (size_t)mpar * E.mark_cap, &E.plan->mark_count[mpar],
                      E.mark_cap};
     if (t == 0 && warp == 0) {
-      cost_part<T, NMAX>(D, parent, parent, right, r, recL, recR, (T*)k2stage, mk, cost_thr);
+      cost_part<T, NMAX>(cost_geom(D, r), parent, parent, right, recL, recR, (T*)k2stage, mk,
+                         cost_thr);
       if (lane == 0) {
         E.map[D->slot_off + k + K] = rslot;
         unsigned* iL = (unsigned*)parent;
@@ -834,6 +850,7 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
   __syncwarp();
   // per-problem context, reloaded only when the unit's problem changes
   int cx_p = -1, cx_K = 0, cx_r = 0;
+  CostGeom cx_cost{};
   char* cx_list = nullptr;
   long long cx_ib = 0, cx_slot = 0;
   // family fields of the unit's family (units of one problem are ordered
@@ -858,6 +875,7 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
       cx_ib = D->item_bytes;
       cx_slot = D->slot_off;
       cx_fam = -1;
+      cx_cost = cost_geom(D, cx_r);
     }
     if (w.fam >= 0 && w.fam != cx_fam) {
       const int fam = w.fam;
@@ -893,7 +911,7 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
     }
     if (w.g == 0) {
       const unsigned char* head = st + (size_t)stage_elems * sizeof(T) + 128;
-      cost_part<T, NMAX, NFIX>(D, (const char*)head, parent, right, r, recL, recR, cost_stage,
+      cost_part<T, NMAX, NFIX>(cx_cost, (const char*)head, parent, right, recL, recR, cost_stage,
                                mk, cost_thr);
       if (lane == 0) {
         E.map[cx_slot + w.k + K] = rslot;
