@@ -486,42 +486,62 @@ __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
   __threadfence();
   const SolveParams* P = E.params;
   const int K_save = (int)run;
+  // every independent load first (the state, the returned box's slot, the
+  // hole count's inputs), so that their latencies overlap; the stores follow
   const int l = D->l;
   const int r = S->r;
-  S->level[r] += 1;
-  const double p_up_step = okey_dec_min(S->pup_key);
+  const unsigned long long pup_key = S->pup_key, plo_key = S->plo_key;
   const double carry = S->p_up_carry;
-  const double p_up = fmin(p_up_step, carry);
   const unsigned bs = S->best_slot;
+  const int steps = S->steps, Kpar = S->K, ftop0 = S->ftop, hw0 = S->hw, nsweep = S->n;
+  const long long peak = S->peak_items;
+  const int trace_rows = D->trace_rows;
+  const long long trace_off = D->trace_off, Mcap = D->M;
+  const double opt_tol = P->opt_tol;
+  const int max_iters = P->max_iters;
+  const unsigned fr_ks = K_save < twoK ? __ldcg(E.flagrank + D->slot_off + K_save) : 0u;
+  const unsigned tc_ks = K_save < twoK ? __ldcg(tc + K_save / PCBA_TPB) : 0u;
+  const unsigned phys = bs != PCBA_NONE ? __ldcg(E.map + D->slot_off + bs) : 0u;
+  int level[PCBA_MAXD];
+#pragma unroll
+  for (int q = 0; q < PCBA_MAXD; ++q) level[q] = q < l ? S->level[q] : 0;
+  unsigned bidx[PCBA_MAXD];
   if (bs != PCBA_NONE) {
-    const unsigned* idx = (const unsigned*)(E.arena + D->list_off +
-                                            (size_t)__ldcg(E.map + D->slot_off + bs) * D->item_bytes);
+    const unsigned* idx =
+        (const unsigned*)(E.arena + D->list_off + (size_t)phys * D->item_bytes);
+#pragma unroll
+    for (int q = 0; q < PCBA_MAXD; ++q) bidx[q] = q < l ? __ldcg(idx + q) : 0u;
+  }
+  level[r] += 1;
+  S->level[r] = level[r];
+  const double p_up_step = okey_dec_min(pup_key);
+  const double p_up = fmin(p_up_step, carry);
+  if (bs != PCBA_NONE) {
     for (int q = 0; q < l; ++q) {
-      S->best_index[q] = __ldcg(idx + q);
-      S->best_level[q] = S->level[q];
+      S->best_index[q] = bidx[q];
+      S->best_level[q] = level[q];
     }
     S->have_box = 1;
     S->from_warm = 0;
     S->p_up_carry = p_up_step;
   }
-  const double p_lo = okey_dec_min(S->plo_key);
+  const double p_lo = okey_dec_min(plo_key);
   S->p_up = p_up;
   S->p_lo = p_lo;
-  if (S->steps < D->trace_rows) {
-    double* row = E.trace + (D->trace_off + S->steps) * 4;
-    row[0] = (double)S->K;
+  if (steps < trace_rows) {
+    double* row = E.trace + (trace_off + steps) * 4;
+    row[0] = (double)Kpar;
     row[1] = (double)K_save;
     row[2] = p_up;
     row[3] = p_lo;
   }
-  S->steps += 1;
-  if ((long long)twoK > S->peak_items) S->peak_items = twoK;
+  S->steps = steps + 1;
+  if ((long long)twoK > peak) S->peak_items = twoK;
   // free slots: this step popped K = twoK / 2 (stack first, then fresh slots);
   // k4_index pushes the slots of the twoK - K_save eliminated children
   {
-    const int Kpar = twoK / 2, ftop0 = S->ftop;
     const int ftop1 = ftop0 > Kpar ? ftop0 - Kpar : 0;
-    S->hw += Kpar > ftop0 ? Kpar - ftop0 : 0;
+    S->hw = hw0 + (Kpar > ftop0 ? Kpar - ftop0 : 0);
     S->ftop_push = ftop1;
     S->ftop = ftop1 + (twoK - K_save);
   }
@@ -532,26 +552,21 @@ __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
   if (K_save == 0) {
     status = 1;  // INFEASIBLE (Alg. 1 line 8)
     S->K = twoK;
-  } else if (p_up - p_lo <= P->opt_tol) {
+  } else if (p_up - p_lo <= opt_tol) {
     status = 0;  // OPTIMAL (Alg. 1 line 9)
     S->K = twoK;
   } else {
     // holes below K_save = K_save - (kept items below K_save)
-    unsigned grank;
-    if (K_save < twoK) {
-      const unsigned fr = __ldcg(E.flagrank + D->slot_off + K_save);
-      grank = __ldcg(tc + K_save / PCBA_TPB) + (fr & 0x7FFFFFFFu);
-    } else {
-      grank = (unsigned)K_save;
-    }
+    const unsigned grank = K_save < twoK ? tc_ks + (fr_ks & 0x7FFFFFFFu) : (unsigned)K_save;
     F = K_save - (int)grank;
     S->K = K_save;
     int rn = r + 1;
-    if (rn == l) { rn = 0; S->n += 1; }
+    int n_new = nsweep;
+    if (rn == l) { rn = 0; n_new += 1; S->n = n_new; }
     S->r = rn;
-    if (S->n >= P->max_iters) status = 3;                       // MAXITER (line 11)
-    else if (S->level[rn] >= 31) status = 3;                    // 32-bit dyadic indices
-    else if (2LL * K_save > D->M) status = 2;                   // MEMCAP (line 4)
+    if (n_new >= max_iters) status = 3;                         // MAXITER (line 11)
+    else if (level[rn] >= 31) status = 3;                       // 32-bit dyadic indices
+    else if (2LL * K_save > Mcap) status = 2;                   // MEMCAP (line 4)
   }
   S->F = F;
   S->status = status;
