@@ -549,7 +549,11 @@ int build_graph(pcba_batch* b) {
   cudaGraph_t body = cp->conditional.phGraph_out[0];
   PCBA_CK(cudaStreamBeginCaptureToGraph(b->cap_stream, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal));
+  // two iterations per body: the conditional node's relaunch between bodies
+  // costs a few microseconds; a second iteration after the loop's end finds
+  // no work in any kernel (and is not counted as a step)
   int rc = launch_loop_body<T>(b, b->cap_stream, 1);
+  if (!rc) rc = launch_loop_body<T>(b, b->cap_stream, 1);
   cudaGraph_t captured = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->cap_stream, &captured);
   if (rc) return rc;
@@ -1492,7 +1496,9 @@ int pcba_batch_stats(const pcba_batch* b, long long* loop_iters, long long* kern
   // per iteration: subdivision, k_pup, k3_classify, k4_index, k_move_control,
   // and k_refresh in FP32
   const long long per_it = 5 + (b->precision == PCBA_FP32 ? 1 : 0);
-  if (kernel_launches) *kernel_launches = 5 + per_it * it + b->extra_launches + b->prior_launches;
+  // the graph runs iterations in pairs: an odd count adds one empty iteration
+  const long long it_run = (b->flags & 3) == 0 ? it + (it & 1) : it;
+  if (kernel_launches) *kernel_launches = 5 + per_it * it_run + b->extra_launches + b->prior_launches;
   if (h2d_bytes) *h2d_bytes = b->h2d_bytes + b->prior_h2d;
   if (d2h_bytes) *d2h_bytes = b->d2h_bytes + b->prior_d2h;
   return 0;

@@ -751,16 +751,27 @@ __device__ __forceinline__ void control_phase(const Engine& E, cudaGraphConditio
   Plan* pl = E.plan;
   for (int q = threadIdx.x; q <= E.np; q += blockDim.x) E.k3_pre[q] = E.k3_pre_next[q];
   if (threadIdx.x == 0) {
+    // the graph's loop body holds two iterations; one that runs after the
+    // loop's end has no classify tiles, does no work and is not a step
+    const bool did = pl->k3_tiles > 0;
     pl->k3_tiles = pl->k3_tiles_next;
     // the refresh of this iteration consumed this step's list
     pl->marks_total += min(pl->mark_count[pl->steps_global & 1], E.mark_cap);
     pl->mark_count[pl->steps_global & 1] = 0u;
-    pl->steps_global += 1;
+    if (did) pl->steps_global += 1;
     const int running = pl->any_running;
     const SolveParams* P = E.params;
     int code = 0;
     if (running && P->max_steps > 0 && pl->steps_global >= P->max_steps) code = 5;
     else if (running && pl->steps_global >= P->step_guard) { code = PCBA_RUNNING + 1; pl->guard_hit = 1; }
+    if (code) {
+      // the plan was made for problems that are now stopped: leave the
+      // iteration that may follow in the loop body nothing to do
+      pl->k2_units = 0u;
+      pl->k3_tiles = 0u;
+      pl->k4_units = 0u;
+      pl->kr_units = 0u;
+    }
     s_code = code;
     s_run = code ? 0 : running;
   }
@@ -793,7 +804,7 @@ __global__ void __launch_bounds__(PCBA_TPB) k_move_control(Engine E,
                                                            cudaGraphConditionalHandle handle,
                                                            int use_graph) {
   __shared__ int s_last, s_code, s_run;
-  move_phase(E);
+  if (E.plan->k3_tiles > 0) move_phase(E);  // no moves after the loop's end
   __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
