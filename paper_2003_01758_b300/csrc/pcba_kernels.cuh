@@ -627,6 +627,31 @@ __device__ void plan_next(const Engine& E, unsigned* sscan) {
   }
 }
 
+// block-wide minimum of two unsigned 64-bit values (sm: 16 entries); the
+// result is valid in thread 0
+__device__ __forceinline__ void block_min2_u64(unsigned long long& a, unsigned long long& b,
+                                               unsigned long long* sm) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long oa = __shfl_xor_sync(0xffffffffu, a, o);
+    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, b, o);
+    a = oa < a ? oa : a;
+    b = ob < b ? ob : b;
+  }
+  if (lane == 0) {
+    sm[2 * wid] = a;
+    sm[2 * wid + 1] = b;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0)
+    for (int w = 1; w < PCBA_TPB / 32; ++w) {
+      a = sm[2 * w] < a ? sm[2 * w] : a;
+      b = sm[2 * w + 1] < b ? sm[2 * w + 1] : b;
+    }
+  __syncthreads();
+}
+
 __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan, double* sred,
                                                int& s_last, int& s_glast) {
   const unsigned tiles_total = E.plan->k3_tiles;
@@ -643,7 +668,10 @@ __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan,
     const double carry = S->p_up_carry;
     const double p_up = fmin(p_up_step, carry);
     unsigned keep = 0;
-    double v[2] = {-INFINITY, -INFINITY};  // -min kept pmin, -best slot
+    // least key of a kept child's pmin (the keys order like the values) and
+    // least slot of a child that attains p_up: integer reductions, no FP64
+    unsigned long long kmin = ~0ull;
+    unsigned long long smin = ~0ull;
     if (c < twoK) {
       ChildRec* R = E.rec + D->slot_off + c;
       const ChildRec rc = load_rec_cg(R);
@@ -657,17 +685,18 @@ __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan,
       const double hmaxmin = -okey_dec_max(rc.hnegmaxmin);
       const bool infeasible = gminmax > 0.0 || hminmax > 0.0 || hmaxmin < 0.0;
       keep = (!infeasible && pmin <= p_up) ? 1u : 0u;
-      if (keep) v[0] = -pmin;
-      if (p_up_step <= carry && pmax == p_up_step && rec_feasible(rc, eq_tol)) v[1] = -(double)c;
+      if (keep) kmin = rc.pmin;
+      if (p_up_step <= carry && pmax == p_up_step && rec_feasible(rc, eq_tol))
+        smin = (unsigned long long)c;
     }
     unsigned cnt;
     const unsigned rank = block_exclusive_scan(keep, sscan, &cnt);
     if (c < twoK) E.flagrank[D->slot_off + c] = (keep << 31) | rank;
-    block_max<2>(v, sred);
+    block_min2_u64(kmin, smin, (unsigned long long*)sred);
     if (threadIdx.x == 0) {
       E.tilecnt[D->tile_off + tile] = cnt;
-      if (v[0] > -INFINITY) atomicMin(&S->plo_key, okey(-v[0]));
-      if (v[1] > -INFINITY) atomicMin(&S->best_slot, (unsigned)(-v[1]));
+      if (kmin != ~0ull) atomicMin(&S->plo_key, kmin);
+      if (smin != ~0ull) atomicMin(&S->best_slot, (unsigned)smin);
       __threadfence();
       const unsigned old = atomicAdd(&S->k3_arrive, 1u);
       s_last = old == (unsigned)ntiles - 1;
