@@ -432,6 +432,15 @@ __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
   }
 }
 
+// rec_feasible on the keys (integer compares, no FP64): for a max-reduced
+// field k (0 = nothing reduced, i.e. minus infinity), "value <= 0" holds
+// exactly when k <= okey(+0.0) (both zeros included), and "value <= t" for
+// t > 0 when k <= okey(t).  k_eq = okey(eq_tol).
+__device__ __forceinline__ bool rec_feasible_key(const ChildRec& c, unsigned long long k_eq) {
+  constexpr unsigned long long k0 = 0x8000000000000000ull;  // okey(+0.0)
+  return c.gmaxmax <= k0 && c.hminmax <= k0 && c.hnegmaxmin <= k0 && c.habsmax <= k_eq;
+}
+
 // ---------------------------------------------------------------------------
 // Def. 4: p_up over the feasible children, from the finished records
 // ---------------------------------------------------------------------------
@@ -440,7 +449,7 @@ __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
 // warp lowers the problem's p_up key.
 __device__ __forceinline__ void pup_phase(const Engine& E) {
   const unsigned tiles_total = E.plan->k3_tiles;
-  const double eq_tol = E.params->eq_tol;
+  const unsigned long long k_eq = okey(E.params->eq_tol);
   for (unsigned u = blockIdx.x; u < tiles_total; u += gridDim.x) {
     const int p = find_problem(E.k3_pre, E.np, u);
     const ProbDesc* D = E.desc + p;
@@ -450,7 +459,7 @@ __device__ __forceinline__ void pup_phase(const Engine& E) {
     unsigned long long best = ~0ull;
     if (c < twoK) {
       const ChildRec rc = load_rec_cg(E.rec + D->slot_off + c);
-      if (rec_feasible(rc, eq_tol)) best = rc.pmax;
+      if (rec_feasible_key(rc, k_eq)) best = rc.pmax;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -655,7 +664,7 @@ __device__ __forceinline__ void block_min2_u64(unsigned long long& a, unsigned l
 __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan, double* sred,
                                                int& s_last, int& s_glast) {
   const unsigned tiles_total = E.plan->k3_tiles;
-  const double eq_tol = E.params->eq_tol;
+  const unsigned long long k_eq = okey(E.params->eq_tol);
   for (unsigned u = blockIdx.x; u < tiles_total; u += gridDim.x) {
     const int p = find_problem(E.k3_pre, E.np, u);
     const int tile = (int)(u - E.k3_pre[p]);
@@ -667,6 +676,7 @@ __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan,
     const double p_up_step = okey_dec_min(S->pup_key);
     const double carry = S->p_up_carry;
     const double p_up = fmin(p_up_step, carry);
+    const unsigned long long k_pup = okey(p_up + 0.0);  // p_up = -0.0 becomes +0.0
     unsigned keep = 0;
     // least key of a kept child's pmin (the keys order like the values) and
     // least slot of a child that attains p_up: integer reductions, no FP64
@@ -678,15 +688,14 @@ __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan,
       unsigned long long* w = (unsigned long long*)R;
 #pragma unroll
       for (int q = 0; q < 8; ++q) w[q] = 0ull;  // identity for the next step
-      const double pmin = okey_dec(rc.pmin);
-      const double pmax = okey_dec(rc.pmax);
-      const double gminmax = okey_dec_max(rc.gminmax);
-      const double hminmax = okey_dec_max(rc.hminmax);
-      const double hmaxmin = -okey_dec_max(rc.hnegmaxmin);
-      const bool infeasible = gminmax > 0.0 || hminmax > 0.0 || hmaxmin < 0.0;
-      keep = (!infeasible && pmin <= p_up) ? 1u : 0u;
+      // Def. 3 and the cut-off on the keys: "value > 0" for a max-reduced
+      // field is key > okey(+0.0); pmin <= p_up is a key compare once a zero
+      // p_up is taken as +0.0 (-0.0 <= +0.0 either way)
+      constexpr unsigned long long k0 = 0x8000000000000000ull;  // okey(+0.0)
+      const bool infeasible = rc.gminmax > k0 || rc.hminmax > k0 || rc.hnegmaxmin > k0;
+      keep = (!infeasible && rc.pmin <= k_pup) ? 1u : 0u;
       if (keep) kmin = rc.pmin;
-      if (p_up_step <= carry && pmax == p_up_step && rec_feasible(rc, eq_tol))
+      if (p_up_step <= carry && okey_dec(rc.pmax) == p_up_step && rec_feasible_key(rc, k_eq))
         smin = (unsigned long long)c;
     }
     unsigned cnt;
