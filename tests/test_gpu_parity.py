@@ -5,7 +5,7 @@ exact halvings in the de Casteljau triangle, the same list order from Alg. 2
 and Alg. 5), so starting both from the same Bernstein patches the whole list
 must agree bit for bit after every step.  From monomial inputs the two
 conversions round differently (the library applies per-axis matrices, the
-oracle sums the definition), so there the bar is the spec one:
+oracle sums the definition), so there the bar is the stated tolerance:
 root patches within 1e-12 of max|b| per patch, and certified intervals that
 overlap with width <= opt_tol.  FP32 mode carries a rigorous error bound per
 patch, so its intervals must contain the optimum the oracle brackets."""
