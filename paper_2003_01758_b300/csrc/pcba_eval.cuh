@@ -116,6 +116,59 @@ __device__ __forceinline__ void horner_f32(const float* a, int l, const int* deg
   }
 }
 
+// horner_f32 for l = 2 and degree (N, N) known at compile time: the same
+// operations in the same order (so the same value and bound, bit for bit),
+// with the loops unrolled so that the coefficient loads are not each waited
+// for in turn.
+template <int N>
+__device__ __forceinline__ void horner_f32_sq2(const float* a, const float* xin, float* val,
+                                               float* err) {
+  const float x0 = xin[0], x1 = xin[1];
+  const float ax0 = fabsf(x0), ax1 = fabsf(x1);
+  float M = 1.0f;
+  const float m1 = fmaxf(1.0f, ax1), m0 = fmaxf(1.0f, ax0);
+#pragma unroll
+  for (int k = 0; k < N; ++k) M = __fmul_ru(M, m1);
+#pragma unroll
+  for (int k = 0; k < N; ++k) M = __fmul_ru(M, m0);
+  float c[(N + 1) * (N + 1)];
+#pragma unroll
+  for (int j = 0; j < (N + 1) * (N + 1); ++j) c[j] = a[j];
+  float v = 0.0f, S = 0.0f;
+#pragma unroll
+  for (int i = N; i >= 0; --i) {
+    float vi = 0.0f, si = 0.0f;
+#pragma unroll
+    for (int j = N; j >= 0; --j) {
+      const float af = c[i * (N + 1) + j];
+      vi = fmaf(vi, x1, af);
+      si = __fmaf_ru(si, ax1, fabsf(af));
+    }
+    v = fmaf(v, x0, vi);
+    S = __fmaf_ru(S, ax0, si);
+  }
+  *val = v;
+  constexpr int dsum = 2 * N, C = (N + 1) * (N + 1);
+  const float rel = __fmul_ru((float)(2 * (2 * dsum + 2 + 4)), 0x1p-24f);
+  *err = __fadd_ru(__fmul_ru(rel, S), __fmul_ru(__fmul_ru((float)(C + dsum), 0x1p-149f), M));
+}
+
+// horner_f32, with the unrolled form for l = 2 and equal degrees up to 8
+__device__ __forceinline__ void horner_f32_any(const float* a, int l, const int* deg,
+                                               const float* x, float* val, float* err) {
+  if (l == 2 && deg[0] == deg[1]) {
+    switch (deg[0]) {
+      case 2: horner_f32_sq2<2>(a, x, val, err); return;
+      case 3: horner_f32_sq2<3>(a, x, val, err); return;
+      case 4: horner_f32_sq2<4>(a, x, val, err); return;
+      case 6: horner_f32_sq2<6>(a, x, val, err); return;
+      case 8: horner_f32_sq2<8>(a, x, val, err); return;
+      default: break;
+    }
+  }
+  horner_f32(a, l, deg, x, val, err);
+}
+
 // The same nested Horner scheme in FP64 on the FP64 coefficients at an FP64
 // point: |v - p(x)| <= 2 (2 dsum + l + 2) 2^-53 S + (C + dsum) 2^-1074 M.
 template <int L>
@@ -528,7 +581,7 @@ __global__ void __launch_bounds__(PCBA_CAND_TPB, 1) k_cand_first(Engine E, const
         const long long off = is_g ? (long long)q * D->cg
                                    : (long long)alpha * D->cg + (long long)(q - alpha) * D->ch;
         float val, err;
-        horner_f32(coef + off, l, is_g ? D->G : D->H, xf, &val, &err);
+        horner_f32_any(coef + off, l, is_g ? D->G : D->H, xf, &val, &err);
         const float lim = is_g ? 0.0f : eq_tol;
         if (!(__fadd_ru(is_g ? val : fabsf(val), err) <= lim)) {
           lane_bad = true;
