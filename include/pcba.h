@@ -50,6 +50,7 @@ enum {
   PCBA_INFEASIBLE = 1,   /* every item infeasible: certified (Alg. 1 line 8)    */
   PCBA_MEMCAP = 2,       /* 2 * length(L) > M (Alg. 1 line 4); best so far      */
   PCBA_MAXITER = 3,      /* the sweep counter reached max_iters (Alg. 1 line 11) */
+  PCBA_TIMEOUT = 4,      /* the time limit ran out (pcba_set_time_limit); best so far */
   PCBA_STEPLIMIT = 5,    /* stopped after max_steps steps (pcba_solve_steps)     */
   PCBA_ERR_INVALID = -1, /* bad argument                                         */
   PCBA_ERR_CUDA = -2,    /* a CUDA runtime call failed                           */
@@ -101,6 +102,10 @@ typedef struct {
   double verify_max_g;      /* max_i g_i(x) + its FP64 rounding bound              */
   double verify_max_abs_h;  /* max_j |h_j(x)| + its FP64 rounding bound            */
   double time_ms;           /* device time from the batch start to this problem's end */
+  double upper_err;         /* the rounding-error bound included in 'upper': FP32, the
+                               bound e_p of the returned box's cost patch (upper = its
+                               largest stored coefficient + e_p); a warm point, the FP64
+                               bound of its cost evaluation; FP64 boxes: 0             */
 } pcba_result;
 
 /* Builds a problem: cost p (Eq. (P)), n_ineq inequality constraints g_i <= 0,
@@ -237,6 +242,10 @@ int pcba_batch_polish(pcba_batch* b, double mu0, double gap, double eq_tol, int 
 int pcba_batch_solve_polished(pcba_batch* b, double opt_tol, double eq_tol, double relax_opt_tol,
                               double relax_eq_tol, int max_iters, pcba_result* out);
 int pcba_batch_set_stream(pcba_batch* b, void* cuda_stream);
+/* The time limit of pcba_set_time_limit for the solves of a batch: every
+ * problem still running when it runs out stops with PCBA_TIMEOUT.  In
+ * pcba_batch_solve_polished it applies to each of the two solves. */
+int pcba_batch_set_time_limit(pcba_batch* b, double seconds);
 void pcba_batch_destroy(pcba_batch* b);
 
 /* Copies the list of the last pcba_solve / pcba_solve_steps to the host in the
@@ -258,6 +267,16 @@ long long pcba_item_bytes(const pcba_handle* h);
 
 int pcba_set_stream(pcba_handle* h, void* cuda_stream);
 int pcba_set_warm_start(pcba_handle* h, const double* x);  /* NULL clears */
+
+/* Time limit of the solves of this handle (pcba_solve, pcba_solve_steps), in
+ * seconds of device time from the start of the solve's device work; 0 (the
+ * default) means none.  The robot of Sec. VI gives PCBA 0.4 s per problem.
+ * The limit is checked on the device between two bisection steps: a problem
+ * still running then stops with status PCBA_TIMEOUT and returns the interval
+ * [lower, upper] certified by the last finished step (and its point, if a
+ * feasible item was found), like PCBA_MAXITER.  A solve can therefore run one
+ * step past the limit.  PCBA_ERR_INVALID if seconds is negative or not finite. */
+int pcba_set_time_limit(pcba_handle* h, double seconds);
 void pcba_destroy(pcba_handle* h);
 
 /* Monomial-to-Bernstein conversion (the step pcba_root_patches runs) that
@@ -276,10 +295,11 @@ void pcba_destroy(pcba_handle* h);
  * returns PCBA_ERR_INVALID.
  * The per-axis matrices live in one fixed 18.5 KB device array in the library,
  * kept by every GPU that loads the library until the process exits.  The first
- * call on a device looks up that array's device address, so make the first
- * call on each device before capturing a stream into a CUDA graph.  All calls
- * share the array: two calls that overlap on the GPU (for instance on two
- * streams) race on it. */
+ * call in each CUDA context of a device (the first call on the device, and the
+ * first after cudaDeviceReset or in another context of it) looks up that
+ * array's device address, so make that call before capturing a stream into a
+ * CUDA graph.  All calls share the array: two calls that overlap on the GPU
+ * (for instance on two streams) race on it. */
 int pcba_bernstein_convert_noalloc(const double* d_mono, int n_patches, int nvars,
                                    const int* degree, const double* lo, const double* hi,
                                    double* d_out, void* stream);

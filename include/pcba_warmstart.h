@@ -135,6 +135,22 @@ int pcba_batch_warm_point(const pcba_batch* b, int k, double* x, double* cost);
  * (device floats).  2 <= G <= 32, ld >= col0 + G * G. */
 int pcba_batch_cost_grid(pcba_batch* b, int G, float* d_out, int ld, int col0);
 
+/* The FP32 point check of the certification above, on its own: the value of
+ * one polynomial at n_points points with a rigorous rounding-error bound,
+ * |d_val[i] - p(x_i)| <= d_err[i], where p has the FP64 coefficients whose
+ * round-to-nearest FP32 copies are d_coeff (device, dense monomial tensor of
+ * multi-degree degree[0..nvars), row-major) and x_i is row i of d_points
+ * (device, [n_points][nvars] floats).  The bound is the nested-Horner bound of
+ * Higham (Accuracy and Stability of Numerical Algorithms, Sec. 5.1) with a
+ * factor-2 margin plus the subnormal range.  unrolled = 0: the generic nested
+ * Horner; 1: the fully unrolled form the certification uses for two variables
+ * of equal degree 2, 3, 4, 6 or 8 (the same operations in the same order, so
+ * the same bits), the generic one for other shapes.  Queued on the stream;
+ * PCBA_ERR_INVALID for shapes beyond the limits of pcba.h. */
+int pcba_eval_points_f32(const float* d_coeff, int nvars, const int* degree,
+                         const float* d_points, int n_points, int unrolled, float* d_val,
+                         float* d_err, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

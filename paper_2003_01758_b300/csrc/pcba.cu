@@ -111,6 +111,7 @@ struct Grids {
 struct pcba_batch {
   int np = 0;
   bool want_tma = true;
+  double time_limit_s = 0.0;   // pcba_batch_set_time_limit (0: none)
   int precision = 64;
   int flags = 0;
   std::vector<ProbDesc> desc;
@@ -203,6 +204,7 @@ struct pcba_handle {
   double warm[PCBA_MAXD];
   pcba_batch* own = nullptr;
   size_t own_cap = 0;
+  double time_limit_s = 0.0;   // pcba_set_time_limit (0: none)
 };
 
 namespace {
@@ -882,7 +884,14 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   P.max_iters = max_iters;
   P.max_steps = max_steps;
   P.step_guard = b->max_l * max_iters + 4;
+  {
+    // test hook: a smaller guard makes the device loop stop before max_iters
+    // does, so that PCBA_ERR_DEVICE_TIMEOUT can be exercised without a fault
+    const char* g = std::getenv("PCBA_TEST_STEP_GUARD");
+    if (g && std::atoi(g) > 0) P.step_guard = std::min(P.step_guard, std::atoi(g));
+  }
   P.np = n;
+  P.time_limit_ns = b->time_limit_s > 0.0 ? (unsigned long long)(b->time_limit_s * 1e9) : 0ull;
   PCBA_CK(cudaEventRecord(b->ev0, s));
   b->h2d_bytes = (long long)sizeof(SolveParams) + (host_coeffs ? 8LL * b->mono_doubles : 0) +
                  (warm ? 8LL * PCBA_MAXD * n : 0) +
@@ -1085,6 +1094,7 @@ void fill_results(const pcba_batch* b, pcba_result* out) {
     }
     const unsigned long long t0 = b->h_plan->t0;
     R.time_ms = S.t_end >= t0 ? (double)(S.t_end - t0) * 1e-6 : 0.0;
+    R.upper_err = !point ? 0.0 : (S.have_box ? (double)S.box_err : S.warm_err);
   }
 }
 
@@ -1175,6 +1185,7 @@ const char* pcba_status_string(int s) {
     case PCBA_INFEASIBLE: return "INFEASIBLE";
     case PCBA_MEMCAP: return "MEMCAP";
     case PCBA_MAXITER: return "MAXITER";
+    case PCBA_TIMEOUT: return "TIMEOUT";
     case PCBA_STEPLIMIT: return "STEPLIMIT";
     case PCBA_ERR_INVALID: return "ERR_INVALID";
     case PCBA_ERR_CUDA: return "ERR_CUDA";
@@ -1224,6 +1235,22 @@ int pcba_set_warm_start(pcba_handle* h, const double* x) {
   return 0;
 }
 
+int pcba_set_time_limit(pcba_handle* h, double seconds) {
+  if (!h) return fail(PCBA_ERR_INVALID, "handle is null");
+  if (!(seconds >= 0.0) || !std::isfinite(seconds))
+    return fail(PCBA_ERR_INVALID, "time limit must be finite and >= 0");
+  h->time_limit_s = seconds;
+  return 0;
+}
+
+int pcba_batch_set_time_limit(pcba_batch* b, double seconds) {
+  if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
+  if (!(seconds >= 0.0) || !std::isfinite(seconds))
+    return fail(PCBA_ERR_INVALID, "time limit must be finite and >= 0");
+  b->time_limit_s = seconds;
+  return 0;
+}
+
 long long pcba_item_bytes(const pcba_handle* h) {
   if (!h) return fail(PCBA_ERR_INVALID, "handle is null");
   const HostProblem& P = h->prob;
@@ -1243,6 +1270,7 @@ int pcba_solve_steps(pcba_handle* h, double opt_tol, double eq_tol, int max_iter
   pcba_batch* b = nullptr;
   int rc = own_batch(h, mem_cap, &b);
   if (rc) return rc;
+  b->time_limit_s = h->time_limit_s;
   return batch_solve_impl(b, nullptr, opt_tol, eq_tol, max_iters, max_steps,
                           h->has_warm ? h->warm : nullptr, out);
 }
@@ -1363,6 +1391,31 @@ int pcba_batch_cost_grid(pcba_batch* b, int G, float* d_out, int ld, int col0) {
   if (G < 2 || G > 32) return fail(PCBA_ERR_INVALID, "G must be in [2, 32]");
   if (col0 < 0 || ld < col0 + G * G) return fail(PCBA_ERR_INVALID, "need ld >= col0 + G * G");
   k_cost_grid<<<b->np, PCBA_TPB, 0, b->stream>>>(b->E, G, d_out, ld, col0);
+  PCBA_CK(cudaGetLastError());
+  return 0;
+}
+
+int pcba_eval_points_f32(const float* d_coeff, int nvars, const int* degree,
+                         const float* d_points, int n_points, int unrolled, float* d_val,
+                         float* d_err, void* stream) {
+  if (!d_coeff || !degree || !d_val || !d_err || (n_points > 0 && !d_points))
+    return fail(PCBA_ERR_INVALID, "point evaluation: null argument");
+  if (nvars < 1 || nvars > PCBA_MAX_DIM || n_points < 0)
+    return fail(PCBA_ERR_INVALID, "point evaluation: nvars must be 1..8 and n_points >= 0");
+  PointPoly q;
+  std::memset(&q, 0, sizeof(q));
+  q.l = nvars;
+  long long C = 1;
+  for (int r = 0; r < nvars; ++r) {
+    if (degree[r] < 0 || degree[r] > PCBA_MAX_DEGREE)
+      return fail(PCBA_ERR_INVALID, "point evaluation: degree out of range");
+    q.deg[r] = degree[r];
+    C *= degree[r] + 1;
+  }
+  if (C > PCBA_MAX_PATCH) return fail(PCBA_ERR_INVALID, "point evaluation: patch too large");
+  if (n_points == 0) return 0;
+  k_eval_points_f32<<<(n_points + 255) / 256, 256, 0, (cudaStream_t)stream>>>(
+      d_coeff, q, d_points, n_points, unrolled ? 1 : 0, d_val, d_err);
   PCBA_CK(cudaGetLastError());
   return 0;
 }

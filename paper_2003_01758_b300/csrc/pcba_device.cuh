@@ -67,7 +67,7 @@ struct ChildRec {
   unsigned long long hminmax;         // max_j min B_hj
   unsigned long long hnegmaxmin;      // max_j (-max B_hj) = -(min_j max B_hj)
   unsigned long long habsmax;         // max_j max(max B_hj, -min B_hj)
-  unsigned long long pad;
+  unsigned long long perr;            // FP32: bits of the cost patch's error bound e_p
 };
 
 struct ProbState {
@@ -80,7 +80,7 @@ struct ProbState {
   int n;            // iteration counter n of Alg. 1 (sweeps)
   int steps;
   int level[PCBA_MAXD];
-  unsigned best_slot;
+  unsigned long long best_key;  // (slot << 32) | e_p bits of the least slot attaining p_up
   unsigned k3_arrive;
   int have_box;
   int from_warm;
@@ -102,6 +102,8 @@ struct ProbState {
   int seeded;                   // a warm-start candidate was certified feasible
   double seed_cost;             // its certified cost bound (the initial p_up)
   double seed_x[PCBA_MAXD];     // the candidate
+  float box_err;                // FP32: e_p of the returned box's cost patch (in p_up)
+  double warm_err;              // FP64 rounding bound of the warm point's cost (in p_up)
 };
 
 struct SolveParams {
@@ -110,6 +112,7 @@ struct SolveParams {
   int max_steps;      // 0: no step limit
   int step_guard;     // hard bound on device loop iterations
   int np;
+  unsigned long long time_limit_ns;  // 0: none; else stop running problems (TIMEOUT)
 };
 
 struct Plan {

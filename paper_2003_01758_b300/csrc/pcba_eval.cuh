@@ -421,15 +421,17 @@ __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* res
     if (s_done) break;
   }
   if (threadIdx.x == 0) {
-    double offer = INFINITY;
+    double offer = INFINITY, perr = 0.0;
     if (chosen >= 0) {
       double pc, pe;
       horner_f64(base, l, D->P, sx[chosen], &pc, &pe);
       offer = __dadd_ru(pc, pe);
+      perr = pe;
       if (!(offer < INFINITY)) chosen = -1;
     }
     const int found = chosen >= 0;
     S->from_warm = found;
+    S->warm_err = found ? perr : 0.0;
     S->p_up_carry = found ? offer : INFINITY;
     S->seeded = found;
     S->seed_cost = found ? offer : INFINITY;
@@ -622,15 +624,17 @@ __global__ void k_cand_pick(Engine E, const int* order, const int* first) {
   const int br = first[p];
   const int l = D->l;
   double x[PCBA_MAXD];
-  double offer = INFINITY;
+  double offer = INFINITY, perr = 0.0;
   int found = 0;
   if (br < n_c && eval_candidate(E, 0, p, order[base + br], x)) {
     double pc, pe;
     horner_f64(E.mono + D->mono_off, l, D->P, x, &pc, &pe);
     offer = __dadd_ru(pc, pe);
+    perr = pe;
     found = offer < INFINITY;
   }
   S->from_warm = found;
+  S->warm_err = found ? perr : 0.0;
   S->p_up_carry = found ? offer : INFINITY;
   S->seeded = found;
   S->seed_cost = found ? offer : INFINITY;
@@ -673,6 +677,24 @@ __global__ void __launch_bounds__(PCBA_TPB) k_cost_grid(Engine E, int G, float* 
   for (int w = 1; w < PCBA_TPB / 32; ++w) mn = fmin(mn, red[w]);
   for (int node = threadIdx.x; node < nodes; node += PCBA_TPB)
     out[(long long)p * ld + col0 + node] = (float)log(s_c[node] - mn + 1e-3);
+}
+
+// pcba_eval_points_f32: one thread per point, the certification's FP32 Horner.
+struct PointPoly {
+  int l;
+  int deg[PCBA_MAXD];
+};
+__global__ void k_eval_points_f32(const float* a, PointPoly q, const float* x, int n,
+                                  int unrolled, float* val, float* err) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  float xf[PCBA_MAXD];
+  for (int r = 0; r < q.l; ++r) xf[r] = x[(long long)i * q.l + r];
+  float v, e;
+  if (unrolled) horner_f32_any(a, q.l, q.deg, xf, &v, &e);
+  else horner_f32(a, q.l, q.deg, xf, &v, &e);
+  val[i] = v;
+  err[i] = e;
 }
 
 // Candidate points of guided solves: candidate c of problem p is the guess of

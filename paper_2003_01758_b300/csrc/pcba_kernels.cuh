@@ -501,7 +501,8 @@ __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
   const int r = S->r;
   const unsigned long long pup_key = S->pup_key, plo_key = S->plo_key;
   const double carry = S->p_up_carry;
-  const unsigned bs = S->best_slot;
+  const unsigned long long bkey = S->best_key;
+  const unsigned bs = bkey == ~0ull ? PCBA_NONE : (unsigned)(bkey >> 32);
   const int steps = S->steps, Kpar = S->K, ftop0 = S->ftop, hw0 = S->hw, nsweep = S->n;
   const long long peak = S->peak_items;
   const int trace_rows = D->trace_rows;
@@ -533,6 +534,7 @@ __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
     S->have_box = 1;
     S->from_warm = 0;
     S->p_up_carry = p_up_step;
+    S->box_err = __uint_as_float((unsigned)(bkey & 0xFFFFFFFFull));
   }
   const double p_lo = okey_dec_min(plo_key);
   S->p_up = p_up;
@@ -581,7 +583,7 @@ __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
   S->status = status;
   S->pup_key = ~0ull;
   S->plo_key = ~0ull;
-  S->best_slot = PCBA_NONE;
+  S->best_key = ~0ull;
   S->k3_arrive = 0u;
   if (status != PCBA_RUNNING) S->t_end = globaltimer();
 }
@@ -696,7 +698,7 @@ __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan,
       keep = (!infeasible && rc.pmin <= k_pup) ? 1u : 0u;
       if (keep) kmin = rc.pmin;
       if (p_up_step <= carry && okey_dec(rc.pmax) == p_up_step && rec_feasible_key(rc, k_eq))
-        smin = (unsigned long long)c;
+        smin = ((unsigned long long)c << 32) | (rc.perr & 0xFFFFFFFFull);
     }
     unsigned cnt;
     const unsigned rank = block_exclusive_scan(keep, sscan, &cnt);
@@ -705,7 +707,7 @@ __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan,
     if (threadIdx.x == 0) {
       E.tilecnt[D->tile_off + tile] = cnt;
       if (kmin != ~0ull) atomicMin(&S->plo_key, kmin);
-      if (smin != ~0ull) atomicMin(&S->best_slot, (unsigned)smin);
+      if (smin != ~0ull) atomicMin(&S->best_key, smin);
       __threadfence();
       const unsigned old = atomicAdd(&S->k3_arrive, 1u);
       s_last = old == (unsigned)ntiles - 1;
@@ -801,6 +803,8 @@ __device__ __forceinline__ void control_phase(const Engine& E, cudaGraphConditio
     const SolveParams* P = E.params;
     int code = 0;
     if (running && P->max_steps > 0 && pl->steps_global >= P->max_steps) code = 5;
+    else if (running && P->time_limit_ns > 0ull && globaltimer() - pl->t0 >= P->time_limit_ns)
+      code = 4;  // TIMEOUT: the time limit ran out between two steps
     else if (running && pl->steps_global >= P->step_guard) { code = PCBA_RUNNING + 1; pl->guard_hit = 1; }
     if (code) {
       // the plan was made for problems that are now stopped: leave the
@@ -882,7 +886,8 @@ __global__ void k_init(Engine E) {
       S->ftop_push = 0;
       S->hw = 1;
       E.map[D->slot_off] = 0u;
-      S->best_slot = PCBA_NONE;
+      S->best_key = ~0ull;
+      S->box_err = 0.0f;
       S->k3_arrive = 0;
       S->have_box = 0;
       S->pup_key = ~0ull;

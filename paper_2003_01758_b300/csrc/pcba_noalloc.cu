@@ -5,6 +5,8 @@
 // transform matrices in a buffer the library allocates.  Here they live in a
 // fixed file-scope device array instead, so the call only needs the caller's
 // input and output buffers.
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -27,8 +29,16 @@ constexpr int kScratchDoubles = PCBA_MAX_DIM * kMatDoubles;
 // this name to a kernel: in host code it is only a stand-in for the symbol.
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
+// The array's device address, per device, together with the unique ID of the
+// CUDA context it was looked up in: a module is loaded once per context, so
+// after cudaDeviceReset (a new primary context) or in another context of the
+// same device the address is looked up again.
 constexpr int kMaxDevices = 64;
-double* g_scratch_ptr[kMaxDevices] = {nullptr};
+struct ScratchAddr {
+  unsigned long long ctx_id;
+  double* ptr;
+};
+ScratchAddr g_scratch[kMaxDevices] = {};
 std::mutex g_scratch_mu;
 
 struct ConvArgs {
@@ -112,8 +122,36 @@ __global__ void nb_convert(ConvArgs a, const double* scratch, const double* mono
   }
 }
 
-// Resolves the device address of the scratch array once per device, with that
-// device current.
+// Unique ID of the calling thread's current CUDA context (0 if there is none
+// yet), through the driver entry points of the runtime (no link to libcuda).
+int current_context_id(unsigned long long* id) {
+  static PFN_cuCtxGetCurrent_v4000 get_current = nullptr;
+  static PFN_cuCtxGetId_v12000 get_id = nullptr;
+  if (!get_current || !get_id) {
+    void* f1 = nullptr;
+    void* f2 = nullptr;
+    cudaDriverEntryPointQueryResult q1, q2;
+    cudaError_t e1 = cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f1, 4000,
+                                                      cudaEnableDefault, &q1);
+    cudaError_t e2 = cudaGetDriverEntryPointByVersion("cuCtxGetId", &f2, 12000,
+                                                      cudaEnableDefault, &q2);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || !f1 || !f2 ||
+        q1 != cudaDriverEntryPointSuccess || q2 != cudaDriverEntryPointSuccess)
+      return pcba_internal_fail(PCBA_ERR_CUDA, "cuCtxGetCurrent / cuCtxGetId are not available");
+    get_current = (PFN_cuCtxGetCurrent_v4000)f1;
+    get_id = (PFN_cuCtxGetId_v12000)f2;
+  }
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS)
+    return pcba_internal_fail(PCBA_ERR_CUDA, "cuCtxGetCurrent failed");
+  *id = 0;
+  if (ctx && get_id(ctx, id) != CUDA_SUCCESS)
+    return pcba_internal_fail(PCBA_ERR_CUDA, "cuCtxGetId failed");
+  return 0;
+}
+
+// Resolves the device address of the scratch array with the device current:
+// once per device and CUDA context, cached for the later calls.
 int scratch_for_current_device(double** ptr) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -122,15 +160,24 @@ int scratch_for_current_device(double** ptr) {
   if (dev < 0 || dev >= kMaxDevices)
     return pcba_internal_fail(PCBA_ERR_INVALID, "device ordinal beyond the supported 64");
   std::lock_guard<std::mutex> lock(g_scratch_mu);
-  if (!g_scratch_ptr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess || !p)
-      return pcba_internal_fail(PCBA_ERR_CUDA,
-                                std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-    g_scratch_ptr[dev] = (double*)p;
+  unsigned long long id = 0;
+  int rc = current_context_id(&id);
+  if (rc) return rc;
+  if (id != 0 && g_scratch[dev].ptr && g_scratch[dev].ctx_id == id) {
+    *ptr = g_scratch[dev].ptr;
+    return 0;
   }
-  *ptr = g_scratch_ptr[dev];
+  // the lookup makes the device's primary context current if none was
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || !p)
+    return pcba_internal_fail(PCBA_ERR_CUDA,
+                              std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  rc = current_context_id(&id);
+  if (rc) return rc;
+  g_scratch[dev].ctx_id = id;
+  g_scratch[dev].ptr = (double*)p;
+  *ptr = (double*)p;
   return 0;
 }
 

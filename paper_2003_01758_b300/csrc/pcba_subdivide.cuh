@@ -330,6 +330,8 @@ __device__ void cost_part(const CostGeom& cg, const char* head, char* parent, ch
       recL->pmax = okey(highs[0]);
       recR->pmin = okey(lows[1]);
       recR->pmax = okey(highs[1]);
+      recL->perr = __float_as_uint((float)efs[0]);
+      recR->perr = __float_as_uint((float)efs[1]);
     }
     // the cost bound is refreshed once it is a visible part of opt_tol
     append_marks(mk, lane == 0 && efs[0] > cost_thr, lane == 0 && efs[1] > cost_thr, 2, 0);
@@ -448,7 +450,7 @@ __device__ __forceinline__ ChildRec load_rec_cg(const ChildRec* p) {
   c.hminmax = __ldcg(s + 4);
   c.hnegmaxmin = __ldcg(s + 5);
   c.habsmax = __ldcg(s + 6);
-  c.pad = 0;
+  c.perr = __ldcg(s + 7);
   return c;
 }
 

@@ -18,9 +18,10 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libpcba.so")
 MAX_DIM = 8
 
-OPTIMAL, INFEASIBLE, MEMCAP, MAXITER, STEPLIMIT = 0, 1, 2, 3, 5
+OPTIMAL, INFEASIBLE, MEMCAP, MAXITER, TIMEOUT, STEPLIMIT = 0, 1, 2, 3, 4, 5
 FP64, FP32 = 64, 32
-STATUS_NAMES = {0: "OPTIMAL", 1: "INFEASIBLE", 2: "MEMCAP", 3: "MAXITER", 5: "STEPLIMIT"}
+STATUS_NAMES = {0: "OPTIMAL", 1: "INFEASIBLE", 2: "MEMCAP", 3: "MAXITER", 4: "TIMEOUT",
+                5: "STEPLIMIT"}
 
 
 class PcbaError(RuntimeError):
@@ -52,7 +53,8 @@ class pcba_result(ctypes.Structure):
                 ("box_hi", ctypes.c_double * MAX_DIM),
                 ("peak_items", ctypes.c_longlong), ("peak_bytes", ctypes.c_longlong),
                 ("verify_cost", ctypes.c_double), ("verify_max_g", ctypes.c_double),
-                ("verify_max_abs_h", ctypes.c_double), ("time_ms", ctypes.c_double)]
+                ("verify_max_abs_h", ctypes.c_double), ("time_ms", ctypes.c_double),
+                ("upper_err", ctypes.c_double)]
 
 
 _lib = None
@@ -87,6 +89,9 @@ def lib():
         "pcba_batch_config": ([P, P, P, P, P], I),
         "pcba_batch_refresh_stats": ([P, P, P], I),
         "pcba_batch_set_stream": ([P, P], I),
+        "pcba_batch_set_time_limit": ([P, D], I),
+        "pcba_set_time_limit": ([P, D], I),
+        "pcba_eval_points_f32": ([P, I, P, P, I, I, P, P, P], I),
         "pcba_batch_polish": ([P, D, D, D, I, P], I),
         "pcba_batch_solve_polished": ([P, D, D, D, D, I, P], I),
         "pcba_batch_destroy": ([P], None),
@@ -138,7 +143,8 @@ def exported_symbols():
             "pcba_mlp_kernel_launches",
             "pcba_mlp_create", "pcba_mlp_destroy", "pcba_mlp_num_params", "pcba_mlp_set_params",
             "pcba_mlp_get_params", "pcba_mlp_forward", "pcba_mlp_gradient",
-            "pcba_mlp_train_step"]
+            "pcba_mlp_train_step", "pcba_set_time_limit", "pcba_batch_set_time_limit",
+            "pcba_eval_points_f32"]
 
 
 def _check(rc):
@@ -159,7 +165,7 @@ def _result_dict(r: pcba_result, l: int) -> dict:
         "x": np.array(r.x[:l]), "box_lo": np.array(r.box_lo[:l]), "box_hi": np.array(r.box_hi[:l]),
         "peak_items": r.peak_items, "peak_bytes": r.peak_bytes, "verify_cost": r.verify_cost,
         "verify_max_g": r.verify_max_g, "verify_max_abs_h": r.verify_max_abs_h,
-        "time_ms": r.time_ms,
+        "time_ms": r.time_ms, "upper_err": r.upper_err,
     }
 
 
@@ -236,6 +242,10 @@ class Solver:
             x = np.ascontiguousarray(x, dtype=np.float64)
             _check(lib().pcba_set_warm_start(self._h, _p(x)))
 
+    def set_time_limit(self, seconds):
+        """pcba_set_time_limit: device-time limit of this handle's solves (0: none)."""
+        _check(lib().pcba_set_time_limit(self._h, float(seconds)))
+
     def solve(self, opt_tol=1e-3, eq_tol=1e-4, max_iters=28, mem_cap=1 << 30, max_steps=0):
         r = pcba_result()
         _check(lib().pcba_solve_steps(self._h, opt_tol, eq_tol, max_iters, mem_cap, max_steps,
@@ -290,6 +300,16 @@ def bernstein_convert_noalloc(d_mono_ptr: int, n_patches: int, degree, lo, hi, d
                                                 _p(degree), _p(lo), _p(hi),
                                                 ctypes.c_void_p(d_out_ptr),
                                                 ctypes.c_void_p(stream_ptr)))
+
+
+def eval_points_f32(d_coeff_ptr: int, degree, d_points_ptr: int, n_points: int, unrolled: bool,
+                    d_val_ptr: int, d_err_ptr: int, stream_ptr: int = 0):
+    """pcba_eval_points_f32 on caller-owned device buffers (raw device pointers)."""
+    degree = np.ascontiguousarray(degree, dtype=np.int32)
+    _check(lib().pcba_eval_points_f32(ctypes.c_void_p(d_coeff_ptr), degree.size, _p(degree),
+                                      ctypes.c_void_p(d_points_ptr), int(n_points),
+                                      1 if unrolled else 0, ctypes.c_void_p(d_val_ptr),
+                                      ctypes.c_void_p(d_err_ptr), ctypes.c_void_p(stream_ptr)))
 
 
 def solver_from_problem(prob, precision=FP32):
@@ -463,6 +483,10 @@ class Batch:
 
     def set_stream(self, stream_ptr: int):
         _check(lib().pcba_batch_set_stream(self._b, ctypes.c_void_p(stream_ptr)))
+
+    def set_time_limit(self, seconds):
+        """pcba_batch_set_time_limit: device-time limit of every solve (0: none)."""
+        _check(lib().pcba_batch_set_time_limit(self._b, float(seconds)))
 
 
 def solve_batch(solvers, opt_tol=1e-3, eq_tol=1e-4, max_iters=28, mem_cap_total=1 << 32,

@@ -25,7 +25,7 @@ def declared_functions():
     text = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc))
                    if f.endswith(".h"))
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(pcba_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(pcba_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_every_declared_symbol_is_exported(lib):
@@ -80,3 +80,28 @@ def test_network_create_validates_on_host(lib):
         pcba.Mlp(0, 34, 128)
     with pytest.raises(pcba.PcbaError, match="shape"):
         pcba.Mlp(2, 34, 0)
+
+
+def test_time_limit_is_validated_on_host(lib):
+    p = W.tiny(1000)
+    s = pcba.Solver(p.cost, p.ineq, p.eq, p.lo, p.hi, precision=pcba.FP32)
+    s.set_time_limit(0.4)
+    s.set_time_limit(0.0)
+    for bad in (-1.0, float("nan"), float("inf")):
+        with pytest.raises(pcba.PcbaError, match="time limit"):
+            s.set_time_limit(bad)
+    assert lib.pcba_status_string(pcba.TIMEOUT) == b"TIMEOUT"
+
+
+def test_failed_device_allocation_reports_oom(lib, monkeypatch):
+    """The allocation-failure hook makes every device allocation of a batch
+    fail before any other CUDA call, so the out-of-memory path returns
+    PCBA_ERR_OOM with the handle intact, on any machine."""
+    p = W.tiny(1000)
+    s = pcba.Solver(p.cost, p.ineq, p.eq, p.lo, p.hi, precision=pcba.FP64)
+    monkeypatch.setenv("PCBA_TEST_FAIL_ALLOC", "1")
+    with pytest.raises(pcba.PcbaError, match="ERR_OOM"):
+        s.solve(opt_tol=1e-3, mem_cap=1 << 24)
+    with pytest.raises(pcba.PcbaError, match="ERR_OOM"):
+        pcba.Batch([s], 1 << 24)
+    assert s.item_bytes() > 0

@@ -125,3 +125,30 @@ def test_polish_rejects_bad_arguments():
     with pytest.raises(pcba.PcbaError):
         b.solve_polished(relax_opt_tol=0.0)
     b.close()
+
+
+def test_full_size_dim4_pipeline_against_relaxed_oracle():
+    """The 4-D configuration at its stated size (64 inequalities of degree 3,
+    2 equalities of degree 2, eq_tol 1e-4, 8 GiB per problem).  The oracle
+    certifies eq_tol 1e-2 in seconds, not 1e-4; the pipeline's tight interval
+    must be consistent with the relaxed one: every point feasible for 1e-4 is
+    feasible for 1e-2, so the tight p_up is at least the relaxed lower bound
+    (up to the oracle's FP64 rounding), and the returned point must be
+    feasible in the oracle's FP64 evaluation with its cost at or above the
+    tight lower bound."""
+    probs = [W.dim4(3000 + k) for k in range(8)]
+    b = pcba.Batch([pcba.solver_from_problem(q, pcba.FP32) for q in probs], 8 * (8 << 30))
+    res = b.solve_polished(opt_tol=1e-3, eq_tol=1e-4, relax_opt_tol=3e-2, relax_eq_tol=1e-1)
+    for k, (q, r) in enumerate(zip(probs, res)):
+        assert r["status"] == pcba.OPTIMAL, (k, r)
+        assert r["upper"] - r["lower"] <= 1e-3
+        x = r["x"]
+        assert max(ev(g, x) for g in q.ineq) <= 0.0
+        assert max(abs(ev(h, x)) for h in q.eq) <= 1e-4
+        assert r["lower"] <= ev(q.cost, x) + 1e-9
+        if k < 3:
+            o = oracle.solve(q.cost, q.ineq, q.eq, q.lo, q.hi, opt_tol=1e-3, eq_tol=1e-2,
+                             max_iters=28, max_items=1 << 18)
+            assert o["status"] == pcba.OPTIMAL
+            assert r["upper"] >= o["lower"] - 1e-9, (k, r, o)
+    b.close()

@@ -10,6 +10,7 @@ to be collected last."""
 import numpy as np
 import pytest
 
+import oracle
 from paper_2003_01758_b300 import pcba
 from paper_2003_01758_b300 import workloads as W
 
@@ -49,6 +50,9 @@ def test_noalloc_conversion_matches_root_patches_on_consecutive_calls():
     got2 = noalloc_convert(second.ineq, second.lo, second.hi)
     assert_close_per_patch(got1, reference_ineq_patches(first))
     assert_close_per_patch(got2, reference_ineq_patches(second))
+    # and against the oracle's direct-summation conversion of each patch
+    for got, p in ((got1, first), (got2, second)):
+        assert_close_per_patch(got, [oracle.bernstein_from_monomial(g, p.lo, p.hi) for g in p.ineq])
     # the scratch now holds the second call's matrices; a repeat of the first
     # call must not see them
     again = noalloc_convert(first.ineq, first.lo, first.hi)
