@@ -43,6 +43,7 @@ extern "C" {
 #define PCBA_MAX_DIM 8
 #define PCBA_MAX_DEGREE 16
 #define PCBA_MAX_PATCH 8192
+#define PCBA_MAX_SHARED 4
 
 /* Solver outcomes (result.status) and error codes (return values). */
 enum {
@@ -125,6 +126,51 @@ int pcba_create(pcba_handle** out, const pcba_poly* cost, const pcba_poly* ineq,
 int pcba_create_bernstein(pcba_handle** out, const pcba_poly* cost, const pcba_poly* ineq,
                           int n_ineq, const pcba_poly* eq, int n_eq, const pcba_box* box,
                           int precision);
+
+/* A family of inequality constraints that are affine in a few shared
+ * polynomials:
+ *
+ *     g_i(x) = offset[i] + sum_{m < n_shared} weight[i * n_shared + m] s_m(x) <= 0,
+ *     i = 0 .. n_constraints - 1.
+ *
+ * The Bernstein transform is linear (Sec. II-D, Eq. (BF): the coefficients of a
+ * constant are that constant, Thm. 1's partition of unity), so on every box
+ * B(g_i) = offset[i] + sum_m weight[i][m] B(s_m), coefficient by coefficient.
+ * A list item then stores the n_shared patches B(s_m) instead of one patch
+ * per constraint, and every constraint's bounds are computed from them when
+ * its box is bounded; in exact arithmetic the coefficients, and therefore the
+ * whole branch and bound, are those of the expanded constraints.  Obstacle
+ * constraints of the trajectory-planning POPs (Sec. II-C, Sec. VI) have this
+ * form: r^2 - ||F(q) - o_i||^2 = (r^2 - ||o_i||^2) - ||F||^2 + 2 o_i . F.
+ *   n_shared       1 .. PCBA_MAX_SHARED
+ *   shared         n_shared polynomials (zero-padded to one common degree)
+ *   n_constraints  alpha >= 0
+ *   weight         [alpha][n_shared] doubles, row-major
+ *   offset         [alpha] doubles */
+typedef struct {
+  int n_shared;
+  const pcba_poly* shared;
+  int n_constraints;
+  const double* weight;
+  const double* offset;
+} pcba_linear_family;
+
+/* Builds a problem whose inequalities are a linear family (no equality
+ * constraints): cost p, the family and the box, as pcba_create.  Each item
+ * also keeps one bit per constraint: a constraint whose bound proves
+ * g_i <= 0 on a box is dropped from that box and all its descendants (the
+ * Bernstein range of a sub-box lies in that of the box, Thm. 1 and Sec. II-E),
+ * so later bisections bound only the constraints still undecided there.
+ * Batches must not mix linear and dense problems. */
+int pcba_create_linear(pcba_handle** out, const pcba_poly* cost,
+                       const pcba_linear_family* ineq, const pcba_box* box, int precision);
+
+/* Per-item activity bits of the list of the last pcba_solve_steps on a
+ * linear-family problem: bits[k * words + w] holds constraints 32 w .. 32 w + 31
+ * of list item k (bit set: still undecided or violated on that box; clear:
+ * proven g_i <= 0 there), words = ceil(n_constraints / 32).  Returns the
+ * number of words per item (0 for a dense problem). */
+int pcba_get_active(pcba_handle* h, unsigned* bits, long long max_words);
 
 /* Runs Algorithm 1 to completion on one problem.
  *   opt_tol   optimality tolerance epsilon > 0 (Def. 2): stop when p_up - p_lo <= opt_tol

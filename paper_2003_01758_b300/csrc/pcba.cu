@@ -72,13 +72,55 @@ long long family_pad(long long n) { return n >= 32 ? round_up(n, 32) : round_up(
 struct HostProblem {
   int l = 0, precision = 64, form = 0;
   int P[PCBA_MAXD] = {0}, G[PCBA_MAXD] = {0}, H[PCBA_MAXD] = {0};
-  int alpha = 0, beta = 0;
+  int alpha = 0, beta = 0;   // stored inequality / equality patches
   long long cp = 1, cg = 0, ch = 0;
   double lo[PCBA_MAXD] = {0}, hi[PCBA_MAXD] = {0};
   std::vector<double> mono;  // cost | ineq (alpha * cg) | eq (beta * ch)
+  // linear family (pcba_create_linear): the stored inequality patches are the
+  // alpha = n_shared shared polynomials; nlin constraints g_i = c_i + w_i . s
+  int lin = 0, nlin = 0;
+  std::vector<double> lin_c, lin_w;  // [nlin], [nlin][alpha]
 };
 
+// Item layout of one problem (see pcba_device.cuh): offsets, stride and the
+// algorithmic bytes of one item.  Linear-family items hold two copies of the
+// shared patches and their error bounds (read from one, written to the other,
+// alternating by step) and one activity bit per constraint.
+void layout_item(const HostProblem& P, int prec, ProbDesc& d) {
+  const int w = prec == PCBA_FP32 ? 4 : 8;
+  d.apad = (int)family_pad(P.alpha);
+  d.bpad = (int)family_pad(P.beta);
+  d.lin = P.lin;
+  d.nlin = P.nlin;
+  d.mwords = P.lin ? (P.nlin + 31) / 32 : 0;
+  d.lin_chunks = P.lin ? std::max(1, (d.mwords + PCBA_LIN_WORDS - 1) / PCBA_LIN_WORDS) : 0;
+  const int copies = P.lin ? 2 : 1;
+  long long off = 64;
+  d.off_cost = off;
+  off = round_up(off + P.cp * w, 128);
+  d.off_eg = off;
+  // FP32 linear families: per copy the error bounds (apad floats) and the FP64
+  // offsets the shared patches are stored relative to (apad doubles)
+  d.copy_e = prec == PCBA_FP32 && P.lin ? 12LL * d.apad : 0;
+  if (prec == PCBA_FP32)
+    off = round_up(off + (P.lin ? copies * d.copy_e : d.apad * 4LL), 128);
+  d.off_eh = off;
+  if (prec == PCBA_FP32) off = round_up(off + d.bpad * 4LL, 128);
+  d.off_g = off;
+  d.copy_g = P.lin ? round_up(P.cg * d.apad * w, 128) : 0;
+  off = P.lin ? off + 2 * d.copy_g : round_up(off + P.cg * d.apad * w, 128);
+  d.off_h = off;
+  off = off + P.ch * d.bpad * w;
+  d.off_mask = off;
+  off += 4LL * d.mwords;
+  d.item_bytes = round_up(off, 256);
+  d.payload_bytes = 4LL * P.l + (P.cp + P.alpha * P.cg + P.beta * P.ch) * w +
+                    (prec == PCBA_FP32 ? 12LL + 4LL * (P.alpha + P.beta) : 0) + 4LL * d.mwords;
+}
+
 struct Grids {
+  int lin_k = 0;                     // linear families: shared patches per item (0: dense)
+  int lin_cgmax = 1, lin_cpmax = 1;  // largest shared / cost patch of the batch
   int nmax = 16;  // degree class of the subdivision kernel (4, 8 or 16)
   int nfix = 0;   // every patch of the batch has this degree on every axis (4 or 6), else 0
   bool tma = false;  // TMA-staged subdivision kernel
@@ -110,6 +152,9 @@ struct Grids {
 
 struct pcba_batch {
   int np = 0;
+  int lin = 0;                 // linear-family problems (pcba_create_linear)
+  long long nslots_total = 0;  // entries of each per-slot scratch array
+  long long lin_rows = 0;      // constraints of all linear-family problems
   bool want_tma = true;
   double time_limit_s = 0.0;   // pcba_batch_set_time_limit (0: none)
   int precision = 64;
@@ -147,6 +192,8 @@ struct pcba_batch {
   long long cand_floats = 0;    // largest constraint coefficient count (alpha cg + beta ch)
   double* d_stencil = nullptr;  // guided solves: [stencil_cap] doubles
   double* d_polish = nullptr;   // pcba_batch_polish output: [np][PCBA_MAXD]
+  float* d_lin32 = nullptr;     // linear families: [lin_rows][PCBA_LIN_STRIDE] (c, w_0..w_K-1) in FP32
+  double* d_lin64 = nullptr;    // the same in FP64
   // pcba_batch_solve_polished: the warm points are already in d_warm (written
   // by the polish kernel), and the counts of the phases before the last solve
   bool warm_on_device = false;
@@ -329,7 +376,8 @@ void free_batch(pcba_batch* b) {
   void* dev[] = {b->d_desc, b->d_state, b->d_plan, b->d_params, b->d_pre, b->d_arena, b->d_rec,
                  b->d_slots, b->d_tilecnt, b->d_mono, b->d_trace, b->d_warm, b->d_mat,
                  b->d_raw, b->d_eval, b->d_tmaps, b->d_marks, b->d_cand, b->d_stencil,
-                 b->d_mono32, b->d_ckey, b->d_corder, b->d_cres, b->d_polish};
+                 b->d_mono32, b->d_ckey, b->d_corder, b->d_cres, b->d_polish, b->d_lin32,
+                 b->d_lin64};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {b->h_state, b->h_eval, b->h_plan, b->h_params, b->h_running};
@@ -351,6 +399,17 @@ const void* tma_kernel(int nmax, int nfix) {
 template <typename T>
 void launch_k2(const pcba_batch* b, cudaStream_t s) {
   const Grids& g = b->g;
+  if (g.lin_k > 0) {
+    const Grids::K2Cfg& c = g.cfgs[g.cfg];
+    const dim3 blk(32 * c.wpb);
+    switch (g.lin_k) {
+      case 1: k2_subdivide_lin<T, 1><<<c.grid, blk, c.smem, s>>>(b->E, g.lin_cgmax, g.lin_cpmax); break;
+      case 2: k2_subdivide_lin<T, 2><<<c.grid, blk, c.smem, s>>>(b->E, g.lin_cgmax, g.lin_cpmax); break;
+      case 3: k2_subdivide_lin<T, 3><<<c.grid, blk, c.smem, s>>>(b->E, g.lin_cgmax, g.lin_cpmax); break;
+      default: k2_subdivide_lin<T, 4><<<c.grid, blk, c.smem, s>>>(b->E, g.lin_cgmax, g.lin_cpmax); break;
+    }
+    return;
+  }
   if (g.tma) {
     const dim3 blk(32 * g.tma_wpb);
     const int st = g.tma_stages, se = g.tma_stage_elems, cp = g.tma_cpmax;
@@ -369,6 +428,27 @@ void launch_k2(const pcba_batch* b, cudaStream_t s) {
   if (g.nmax <= 4) k2_subdivide<T, 4><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
   else if (g.nmax <= 8) k2_subdivide<T, 8><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
   else k2_subdivide<T, 16><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
+}
+
+// The linear-family subdivision kernel for K shared patches, and the shared
+// memory one of its warps uses.
+template <typename T>
+const void* lin_kernel(int K) {
+  switch (K) {
+    case 1: return (const void*)k2_subdivide_lin<T, 1>;
+    case 2: return (const void*)k2_subdivide_lin<T, 2>;
+    case 3: return (const void*)k2_subdivide_lin<T, 3>;
+    default: return (const void*)k2_subdivide_lin<T, 4>;
+  }
+}
+template <typename T>
+size_t lin_warp_smem(int K, int cgmax, int cpmax) {
+  switch (K) {
+    case 1: return lin_warp_bytes<T, 1>(cgmax, cpmax);
+    case 2: return lin_warp_bytes<T, 2>(cgmax, cpmax);
+    case 3: return lin_warp_bytes<T, 3>(cgmax, cpmax);
+    default: return lin_warp_bytes<T, 4>(cgmax, cpmax);
+  }
 }
 
 // The kernels of one device-loop iteration after the subdivision: the FP32
@@ -490,6 +570,23 @@ int setup_kernels(pcba_batch* b) {
         c.grid = std::max(1, occ) * g.sms;
       }
     }
+  }
+  if (b->lin) {
+    // linear families: one subdivision kernel (warp per unit), no TMA staging
+    g.lin_k = b->desc[0].alpha;
+    g.lin_cpmax = (int)cpmax;
+    g.lin_cgmax = 1;
+    for (const ProbDesc& d : b->desc) g.lin_cgmax = std::max(g.lin_cgmax, d.cg);
+    const size_t wb = lin_warp_smem<T>(g.lin_k, g.lin_cgmax, g.lin_cpmax);
+    int wpb = 8;
+    while (wpb > 1 && (size_t)wpb * wb > (size_t)smem_optin) wpb /= 2;
+    if (wb > (size_t)smem_optin) return fail(PCBA_ERR_INVALID, "shared patches too large");
+    const void* kl = lin_kernel<T>(g.lin_k);
+    PCBA_CK(cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)(wpb * wb)));
+    PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kl, 32 * wpb, wpb * wb));
+    g.cfgs.clear();
+    g.cfgs.push_back({false, wpb, 1, wpb * wb, std::max(1, occ) * g.sms});
   }
   // FP32 refresh: per warp 4 patch buffers of the largest patch and the
   // per-axis matrices; warps per block limited by shared memory
@@ -628,7 +725,8 @@ int apply_k2_config(pcba_batch* b, int idx) {
     }
   }
   for (ProbDesc& d : b->desc)
-    d.tiles = c.tma ? std::max(1, d.groups_g + d.groups_h) : std::max(1, d.tiles_g + d.tiles_h);
+    d.tiles = d.lin ? d.lin_chunks
+                    : (c.tma ? std::max(1, d.groups_g + d.groups_h) : std::max(1, d.tiles_g + d.tiles_h));
   PCBA_CK(cudaMemcpy(b->d_desc, b->desc.data(), sizeof(ProbDesc) * b->np, cudaMemcpyHostToDevice));
   return 0;
 }
@@ -661,9 +759,15 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
     b->want_tma = !(flags & 4) && !(nt && nt[0] == '1');
   }
   b->stream = hs[0]->stream;
-  const int w = prec == PCBA_FP32 ? 4 : 8;
+  b->lin = hs[0]->prob.lin;
+  for (int k = 0; k < n; ++k)
+    if (hs[k]->prob.lin != b->lin || (b->lin && hs[k]->prob.alpha != hs[0]->prob.alpha)) {
+      delete b;
+      return fail(PCBA_ERR_INVALID, "a batch must not mix linear-family and dense problems, "
+                                    "and its linear families must share n_shared");
+    }
   b->desc.resize(n);
-  long long mono = 0, sum_item = 0, trace_rows = 0;
+  long long mono = 0, sum_item = 0, trace_rows = 0, lin_rows = 0;
   for (int k = 0; k < n; ++k) {
     const HostProblem& P = hs[k]->prob;
     b->probs.push_back(&P);
@@ -676,8 +780,6 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
     d.ch = (int)P.ch;
     d.alpha = P.alpha;
     d.beta = P.beta;
-    d.apad = (int)family_pad(P.alpha);
-    d.bpad = (int)family_pad(P.beta);
     d.tiles_g = (P.alpha + PCBA_TPB - 1) / PCBA_TPB;
     d.tiles_h = (P.beta + PCBA_TPB - 1) / PCBA_TPB;
     d.tiles = std::max(1, d.tiles_g + d.tiles_h);
@@ -691,20 +793,9 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
       d.lo[r] = P.lo[r];
       d.hi[r] = P.hi[r];
     }
-    long long off = 64;
-    d.off_cost = off;
-    off = round_up(off + P.cp * w, 128);
-    d.off_eg = off;
-    if (prec == PCBA_FP32) off = round_up(off + d.apad * 4LL, 128);
-    d.off_eh = off;
-    if (prec == PCBA_FP32) off = round_up(off + d.bpad * 4LL, 128);
-    d.off_g = off;
-    off = round_up(off + P.cg * d.apad * w, 128);
-    d.off_h = off;
-    off = off + P.ch * d.bpad * w;
-    d.item_bytes = round_up(off, 256);
-    d.payload_bytes = 4LL * P.l + (P.cp + P.alpha * P.cg + P.beta * P.ch) * w +
-                      (prec == PCBA_FP32 ? 12LL + 4LL * (P.alpha + P.beta) : 0);
+    layout_item(P, prec, d);
+    d.lin_off = lin_rows;
+    lin_rows += P.nlin;
     d.move_chunks = 1;  // Eliminate moves one map entry per hole
     d.mono_off = mono;
     mono += (long long)P.mono.size();
@@ -719,6 +810,7 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   b->M = M;
   b->sum_item_bytes = sum_item;
   b->mono_doubles = mono;
+  b->lin_rows = lin_rows;
   b->trace_rows_total = trace_rows;
   const long long Mslots = std::max<long long>(M, 2);
   const long long tiles_per = (Mslots + PCBA_TPB - 1) / PCBA_TPB + 1;
@@ -733,6 +825,7 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   }
   const long long arena_bytes = list_off;
   const long long nslots = (long long)n * Mslots;
+  b->nslots_total = nslots;
   int rc = 0;
 #define PCBA_ALLOC(ptr, bytes)                                                        \
   do {                                                                                \
@@ -765,6 +858,8 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   PCBA_ALLOC(b->d_mat, sizeof(double) * 3 * PCBA_MAXD * 578 * n);
   PCBA_ALLOC(b->d_raw, sizeof(double) * mono);
   PCBA_ALLOC(b->d_eval, sizeof(EvalOut) * n);
+  PCBA_ALLOC(b->d_lin32, sizeof(float) * PCBA_LIN_STRIDE * std::max<long long>(lin_rows, 1));
+  PCBA_ALLOC(b->d_lin64, sizeof(double) * PCBA_LIN_STRIDE * std::max<long long>(lin_rows, 1));
   const unsigned mark_cap = 1u << 20;  // marked patches per step (extra marks are dropped)
   PCBA_ALLOC(b->d_marks, sizeof(uint4) * 2 * (prec == PCBA_FP32 ? mark_cap : 1));
 #undef PCBA_ALLOC
@@ -799,6 +894,26 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
                 all.begin() + b->desc[k].mono_off);
     if ((rc = cleanup_ck(cudaMemcpy(b->d_mono, all.data(), sizeof(double) * mono,
                                     cudaMemcpyHostToDevice), "mono upload")))
+      return rc;
+  }
+  if (lin_rows > 0) {
+    // constraint rows (c_i, w_i0 .. w_i,K-1), in FP64 and rounded to nearest FP32
+    std::vector<double> t64((size_t)(PCBA_LIN_STRIDE * lin_rows), 0.0);
+    std::vector<float> t32(t64.size(), 0.0f);
+    for (int k = 0; k < n; ++k) {
+      const HostProblem& P = *b->probs[k];
+      for (int i = 0; i < P.nlin; ++i) {
+        double* row = t64.data() + (size_t)(b->desc[k].lin_off + i) * PCBA_LIN_STRIDE;
+        row[0] = P.lin_c[i];
+        for (int m = 0; m < P.alpha; ++m) row[1 + m] = P.lin_w[(size_t)i * P.alpha + m];
+      }
+    }
+    for (size_t q = 0; q < t64.size(); ++q) t32[q] = (float)t64[q];
+    if ((rc = cleanup_ck(cudaMemcpy(b->d_lin64, t64.data(), sizeof(double) * t64.size(),
+                                    cudaMemcpyHostToDevice), "linear rows upload")))
+      return rc;
+    if ((rc = cleanup_ck(cudaMemcpy(b->d_lin32, t32.data(), sizeof(float) * t32.size(),
+                                    cudaMemcpyHostToDevice), "linear rows upload")))
       return rc;
   }
   std::vector<unsigned> k1pre(n + 1, 0);
@@ -852,6 +967,8 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   E.warm = b->d_warm;
   E.n_warm = 1;
   E.root_raw = nullptr;
+  E.lin32 = b->d_lin32;
+  E.lin64 = b->d_lin64;
   rc = prec == PCBA_FP32 ? setup_kernels<float>(b) : setup_kernels<double>(b);
   if (!rc) rc = apply_k2_config(b, (b->want_tma && b->g.cfgs.size() > 1) ? 1 : 0);
   if (!rc && (flags & 3) == 0) rc = prec == PCBA_FP32 ? build_graph<float>(b) : build_graph<double>(b);
@@ -1106,6 +1223,7 @@ constexpr int kPolishIters = 30;
 // k_polish for every dimension present in the batch, on the batch's stream
 int launch_polish(pcba_batch* b, double* d_out, double mu0, double gap, double eq_tol, int iters,
                   int* launches) {
+  if (b->lin) return fail(PCBA_ERR_INVALID, "the polish needs dense constraints (no linear family)");
   if (!(mu0 > 0.0) || !(gap > 0.0) || !(eq_tol > 0.0) || iters < 1 || iters > 200)
     return fail(PCBA_ERR_INVALID, "need mu0, gap, eq_tol > 0 and 1 <= iters <= 200");
   bool seen[PCBA_MAXD + 1] = {};
@@ -1206,6 +1324,54 @@ int pcba_create_bernstein(pcba_handle** out, const pcba_poly* cost, const pcba_p
   return create_impl(out, cost, ineq, n_ineq, eq, n_eq, box, precision, 1);
 }
 
+int pcba_create_linear(pcba_handle** out, const pcba_poly* cost,
+                       const pcba_linear_family* fam, const pcba_box* box, int precision) {
+  if (out) *out = nullptr;
+  if (!fam) return fail(PCBA_ERR_INVALID, "linear family is null");
+  if (fam->n_shared < 1 || fam->n_shared > PCBA_MAX_SHARED || !fam->shared)
+    return fail(PCBA_ERR_INVALID, "linear family: n_shared must be 1..4");
+  if (fam->n_constraints < 0 || fam->n_constraints > (1 << 20))
+    return fail(PCBA_ERR_INVALID, "linear family: n_constraints must be 0..2^20");
+  if (fam->n_constraints > 0 && (!fam->weight || !fam->offset))
+    return fail(PCBA_ERR_INVALID, "linear family: weight or offset is null");
+  const long long nw = (long long)fam->n_constraints * fam->n_shared;
+  for (long long q = 0; q < nw; ++q)
+    if (!std::isfinite(fam->weight[q])) return fail(PCBA_ERR_INVALID, "non-finite weight");
+  for (int i = 0; i < fam->n_constraints; ++i)
+    if (!std::isfinite(fam->offset[i])) return fail(PCBA_ERR_INVALID, "non-finite offset");
+  // the shared polynomials are stored as the inequality family of the handle
+  int rc = create_impl(out, cost, fam->shared, fam->n_shared, nullptr, 0, box, precision, 0);
+  if (rc) return rc;
+  HostProblem& P = (*out)->prob;
+  P.lin = 1;
+  P.nlin = fam->n_constraints;
+  P.lin_c.assign(fam->offset, fam->offset + fam->n_constraints);
+  P.lin_w.assign(fam->weight, fam->weight + nw);
+  return 0;
+}
+
+int pcba_get_active(pcba_handle* h, unsigned* bits, long long max_words) {
+  if (!h) return fail(PCBA_ERR_INVALID, "handle is null");
+  if (!h->prob.lin) return 0;
+  if (!h->own) return fail(PCBA_ERR_INVALID, "no solve has run on this handle");
+  pcba_batch* b = h->own;
+  const ProbDesc& d = b->desc[0];
+  const long long K = b->h_state[0].K;
+  if (bits) {
+    if (max_words < K * d.mwords) return fail(PCBA_ERR_INVALID, "activity buffer too small");
+    const long long nslots_total = b->nslots_total;
+    std::vector<unsigned> slot((size_t)std::max<long long>(K, 1));
+    PCBA_CK(cudaMemcpy(slot.data(), b->d_slots + 3 * nslots_total + d.slot_off,
+                       sizeof(unsigned) * (size_t)K, cudaMemcpyDeviceToHost));
+    for (long long k = 0; k < K; ++k)
+      PCBA_CK(cudaMemcpy(bits + k * d.mwords,
+                         b->d_arena + d.list_off + (size_t)slot[(size_t)k] * d.item_bytes +
+                             d.off_mask,
+                         sizeof(unsigned) * (size_t)d.mwords, cudaMemcpyDeviceToHost));
+  }
+  return d.mwords;
+}
+
 void pcba_destroy(pcba_handle* h) {
   if (!h) return;
   free_batch(h->own);
@@ -1253,15 +1419,10 @@ int pcba_batch_set_time_limit(pcba_batch* b, double seconds) {
 
 long long pcba_item_bytes(const pcba_handle* h) {
   if (!h) return fail(PCBA_ERR_INVALID, "handle is null");
-  const HostProblem& P = h->prob;
-  const int w = P.precision == PCBA_FP32 ? 4 : 8;
-  long long off = 64;
-  off = round_up(off + P.cp * w, 128);
-  if (P.precision == PCBA_FP32) off = round_up(off + family_pad(P.alpha) * 4LL, 128);
-  if (P.precision == PCBA_FP32) off = round_up(off + family_pad(P.beta) * 4LL, 128);
-  off = round_up(off + P.cg * family_pad(P.alpha) * w, 128);
-  off = off + P.ch * family_pad(P.beta) * w;
-  return round_up(off, 256);
+  ProbDesc d;
+  std::memset(&d, 0, sizeof(d));
+  layout_item(h->prob, h->prob.precision, d);
+  return d.item_bytes;
 }
 
 int pcba_solve_steps(pcba_handle* h, double opt_tol, double eq_tol, int max_iters, size_t mem_cap,
@@ -1600,7 +1761,7 @@ int pcba_get_list(pcba_handle* h, long long* K_out, double* cost, double* ineq, 
   if (!cost && !ineq && !eq && !err && !index) return 0;
   std::vector<char> buf((size_t)(K * d.item_bytes));
   std::vector<unsigned> slot((size_t)std::max<long long>(K, 1));
-  const long long nslots_total = (long long)b->np * std::max<long long>(b->M, 2);
+  const long long nslots_total = b->nslots_total;
   PCBA_CK(cudaMemcpy(slot.data(), b->d_slots + 3 * nslots_total + d.slot_off,
                      sizeof(unsigned) * (size_t)K, cudaMemcpyDeviceToHost));
   for (long long k = 0; k < K; ++k)
@@ -1609,6 +1770,9 @@ int pcba_get_list(pcba_handle* h, long long* K_out, double* cost, double* ineq, 
                        (size_t)d.item_bytes, cudaMemcpyDeviceToHost));
   const bool f32 = b->precision == PCBA_FP32;
   const int nerr = 1 + d.alpha + d.beta;
+  // linear families: the copy of the shared patches the next step would read
+  const int cpy = b->h_plan->steps_global & 1;
+  const long long off_g = d.off_g + cpy * d.copy_g, off_eg = d.off_eg + cpy * d.copy_e;
   for (long long k = 0; k < K; ++k) {
     const char* it = buf.data() + k * d.item_bytes;
     if (index)
@@ -1620,9 +1784,12 @@ int pcba_get_list(pcba_handle* h, long long* K_out, double* cost, double* ineq, 
     if (cost)
       for (int j = 0; j < d.cp; ++j) cost[k * d.cp + j] = f32 ? O + val(d.off_cost, j) : val(d.off_cost, j);
     if (ineq)
-      for (int i = 0; i < d.alpha; ++i)
+      for (int i = 0; i < d.alpha; ++i) {
+        // FP32 linear families store each shared patch relative to an offset
+        const double Oi = f32 && d.lin ? ((const double*)(it + off_eg + 4LL * d.apad))[i] : 0.0;
         for (int j = 0; j < d.cg; ++j)
-          ineq[(k * d.alpha + i) * d.cg + j] = val(d.off_g, (long long)j * d.apad + i);
+          ineq[(k * d.alpha + i) * d.cg + j] = Oi + val(off_g, (long long)j * d.apad + i);
+      }
     if (eq)
       for (int i = 0; i < d.beta; ++i)
         for (int j = 0; j < d.ch; ++j)
@@ -1632,7 +1799,7 @@ int pcba_get_list(pcba_handle* h, long long* K_out, double* cost, double* ineq, 
       if (f32) {
         e[0] = *(const float*)(it + 40);
         // the sign bit marks refresh candidates; the bound is the magnitude
-        for (int i = 0; i < d.alpha; ++i) e[1 + i] = std::fabs(((const float*)(it + d.off_eg))[i]);
+        for (int i = 0; i < d.alpha; ++i) e[1 + i] = std::fabs(((const float*)(it + off_eg))[i]);
         for (int i = 0; i < d.beta; ++i)
           e[1 + d.alpha + i] = std::fabs(((const float*)(it + d.off_eh))[i]);
       } else {

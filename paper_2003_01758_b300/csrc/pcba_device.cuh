@@ -12,6 +12,13 @@
 //                      so patch i is the column i ("constraint-minor")
 //   off_h              equality patches, [ch][bpad] of T
 //
+// A linear-family item (pcba_create_linear) stores the K shared patches in the
+// inequality block twice (copy_g apart; their error bounds twice, copy_e
+// apart): a bisection step reads the copy of its parity and writes the
+// children into the other one, so that the several work units of one parent
+// can all read it while the left child takes its slot.  After the patches,
+// off_mask holds one activity bit per constraint (mwords words).
+//
 // Constraint-minor storage makes every load and store of the subdivision
 // kernel unit-stride across the threads of a warp for every bisection
 // direction: thread i owns patch i and walks its fibres.
@@ -32,6 +39,8 @@
 #define PCBA_NONE 0xFFFFFFFFu
 #define PCBA_RUNNING 10
 #define PCBA_TRACE_PER_DIM 40
+#define PCBA_LIN_WORDS 8     // activity words (256 constraints) per linear subdivision unit
+#define PCBA_LIN_STRIDE 8    // floats / doubles per linear constraint row (c, w_0 .. w_K-1)
 
 struct ProbDesc {
   int l;
@@ -55,6 +64,15 @@ struct ProbDesc {
   long long trace_off;       // offset (rows) in the trace buffer
   int trace_rows;
   int units_k1;              // 1 + alpha + beta patches to convert
+  // linear families (pcba_create_linear): alpha = K shared patches, nlin
+  // constraints g_i = c_i + sum_m w_im s_m with rows at lin_off of the tables
+  int lin, nlin;
+  int mwords;                // activity words per item (32 constraints each)
+  int lin_chunks;            // subdivision units per item (PCBA_LIN_WORDS words each)
+  long long off_mask;        // activity bits of the item
+  long long copy_g, copy_e;  // byte distance between the two copies of the shared
+                             // patches / of their error bounds (0: one copy)
+  long long lin_off;         // first row of this problem in the constraint tables
 };
 
 // Per-child bound record, each field an order-preserving 64-bit key of a
@@ -162,6 +180,8 @@ struct Engine {
   double* root_raw;        // optional FP64 root patch dump
   const unsigned* k1_pre;  // [np + 1] patches per problem prefix
   const void* tmaps;       // [np][2] tensor maps (CUtensorMap) of the g / h blocks, or null
+  const float* lin32;      // linear families: constraint rows in FP32 (round to nearest)
+  const double* lin64;     // the same in FP64
 };
 
 // ---------------------------------------------------------------------------
@@ -251,3 +271,48 @@ __device__ __forceinline__ unsigned block_exclusive_scan(unsigned x, unsigned* s
   *total = tot;
   return woff + inc - x;
 }
+
+// ---------------------------------------------------------------------------
+// small exact helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double dev_binom(int n, int k) {
+  if (k < 0 || k > n) return 0.0;
+  if (k > n - k) k = n - k;
+  double c = 1.0;
+  for (int i = 1; i <= k; ++i) c = c * (double)(n - k + i) / (double)i;
+  return c;
+}
+__device__ __forceinline__ double dev_pow(double x, int e) {
+  double r = 1.0;
+  for (int i = 0; i < e; ++i) r *= x;
+  return r;
+}
+
+__device__ __forceinline__ float addrn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double addrn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mulrn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mulrn(double a, double b) { return __dmul_rn(a, b); }
+
+// order-preserving 32-bit key of a float (0 = below everything)
+__device__ __forceinline__ unsigned okey32(float x) {
+  const unsigned b = __float_as_uint(x);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+__device__ __forceinline__ float okey32_dec(unsigned k) {
+  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+__device__ __forceinline__ ChildRec load_rec_cg(const ChildRec* p) {
+  ChildRec c;
+  const unsigned long long* s = (const unsigned long long*)p;
+  c.pmin = __ldcg(s + 0);
+  c.pmax = __ldcg(s + 1);
+  c.gminmax = __ldcg(s + 2);
+  c.gmaxmax = __ldcg(s + 3);
+  c.hminmax = __ldcg(s + 4);
+  c.hnegmaxmin = __ldcg(s + 5);
+  c.habsmax = __ldcg(s + 6);
+  c.perr = __ldcg(s + 7);
+  return c;
+}
+

@@ -240,6 +240,60 @@ __device__ __forceinline__ void horner_f64(const double* a, int l, const int* de
   }
 }
 
+// Linear families (pcba_create_linear): inequality q is g_q = c_q + sum_m
+// w_qm s_m.  From the shared polynomials' values sv[m] at a point, each with
+// |sv[m] - s_m(x)| <= se[m]:
+//   FP32 (rows rounded to nearest FP32): the fused chain has K roundings and
+//   the rows one each, so with A = |c| + sum |w_m| |sv_m|,
+//     |val - g_q(x)| <= (2K + 2) 2^-24 A + (1 + 2^-20) sum |w_m| se_m + (2K + 2) 2^-149;
+//   FP64 (exact rows): K roundings,
+//     |val - g_q(x)| <= (K + 1) 2^-53 A + (1 + 2^-50) sum |w_m| se_m + (K + 1) 2^-1074.
+__device__ __forceinline__ void lin_value_f32(const Engine& E, const ProbDesc* D, int q,
+                                              const float* sv, const float* se, float* val,
+                                              float* err) {
+  const float* row = E.lin32 + (D->lin_off + q) * PCBA_LIN_STRIDE;
+  const int K = D->alpha;
+  float v = row[0], A = fabsf(row[0]), Ee = 0.0f;
+  for (int m = 0; m < K; ++m) {
+    const float w = row[1 + m];
+    v = fmaf(w, sv[m], v);
+    A = __fmaf_ru(fabsf(w), fabsf(sv[m]), A);
+    Ee = __fmaf_ru(fabsf(w), se[m], Ee);
+  }
+  const float kk = (float)(2 * K + 2);
+  *val = v;
+  *err = __fadd_ru(__fadd_ru(__fmul_ru(kk * 0x1p-24f, A), __fmul_ru(Ee, 1.0f + 0x1p-20f)),
+                   kk * 0x1p-149f);
+}
+__device__ __forceinline__ void lin_value_f64(const Engine& E, const ProbDesc* D, int q,
+                                              const double* sv, const double* se, double* val,
+                                              double* err) {
+  const double* row = E.lin64 + (D->lin_off + q) * PCBA_LIN_STRIDE;
+  const int K = D->alpha;
+  double v = row[0], A = fabs(row[0]), Ee = 0.0;
+  for (int m = 0; m < K; ++m) {
+    const double w = row[1 + m];
+    v = fma(w, sv[m], v);
+    A = __fma_ru(fabs(w), fabs(sv[m]), A);
+    Ee = __fma_ru(fabs(w), se[m], Ee);
+  }
+  const double kk = (double)(K + 1);
+  *val = v;
+  *err = __dadd_ru(__dadd_ru(__dmul_ru(kk * 0x1p-53, A), __dmul_ru(Ee, 1.0 + 0x1p-50)),
+                   kk * 0x1p-1074);
+}
+// Values and bounds of the K shared polynomials of a linear family at a point.
+__device__ __forceinline__ void lin_shared_f64(const Engine& E, const ProbDesc* D, const double* x,
+                                               double* sv, double* se) {
+  const double* sh = E.mono + D->mono_off + D->cp;
+  for (int m = 0; m < D->alpha; ++m) horner_f64(sh + (long long)m * D->cg, D->l, D->G, x, &sv[m], &se[m]);
+}
+__device__ __forceinline__ void lin_shared_f32(const Engine& E, const ProbDesc* D, const float* coef,
+                                               const float* x, float* sv, float* se) {
+  for (int m = 0; m < D->alpha; ++m)
+    horner_f32_any(coef + (long long)m * D->cg, D->l, D->G, x, &sv[m], &se[m]);
+}
+
 // candidate c of problem p: mode 0 a warm-start row (NaN first coordinate:
 // none), mode 1 the point the solve returns; false if there is none
 __device__ __forceinline__ bool eval_candidate(const Engine& E, int mode, int p, int c, double* x) {
@@ -275,6 +329,7 @@ __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* res
   __shared__ int s_id[PCBA_MAX_CAND];
   __shared__ double sx[PCBA_EVAL_CHUNK][PCBA_MAXD];
   __shared__ float sxf[PCBA_EVAL_CHUNK][PCBA_MAXD];
+  __shared__ float s_lsv[PCBA_EVAL_CHUNK][PCBA_MAX_SHARED], s_lse[PCBA_EVAL_CHUNK][PCBA_MAX_SHARED];
   __shared__ unsigned long long s_max[2];
   __shared__ int s_has[PCBA_EVAL_CHUNK];
   __shared__ int s_viol[PCBA_EVAL_CHUNK];
@@ -286,7 +341,8 @@ __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* res
   ProbState* S = E.state + p;
   const int l = D->l;
   const double* base = E.mono + D->mono_off;
-  const int total = D->alpha + D->beta;
+  // constraints to check: every g_i and h_j, or the rows of a linear family
+  const int total = D->lin ? D->nlin : D->alpha + D->beta;
 
   if (mode == 1) {
     // final check of one point, FP64
@@ -303,7 +359,18 @@ __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* res
       }
       return;
     }
-    for (int q = threadIdx.x; q < total; q += PCBA_TPB) {
+    if (D->lin) {
+      // the shared polynomials once, then every constraint from them
+      __shared__ double s_sv[PCBA_MAX_SHARED], s_se[PCBA_MAX_SHARED];
+      if (threadIdx.x == 0) lin_shared_f64(E, D, sx[0], s_sv, s_se);
+      __syncthreads();
+      for (int q = threadIdx.x; q < D->nlin; q += PCBA_TPB) {
+        double val, err;
+        lin_value_f64(E, D, q, s_sv, s_se, &val, &err);
+        atomicMax(&s_max[0], okey(__dadd_ru(val, err)));
+      }
+    }
+    for (int q = threadIdx.x; !D->lin && q < total; q += PCBA_TPB) {
       const bool is_g = q < D->alpha;
       const double* a = is_g ? base + D->cp + (long long)q * D->cg
                              : base + D->cp + (long long)D->alpha * D->cg +
@@ -376,8 +443,10 @@ __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* res
         has = eval_candidate(E, 0, p, s_id[c0 + c], sx[c]) ? 1 : 0;
       s_has[c] = has;
       s_viol[c] = 0;
-      if (has)
+      if (has) {
         for (int q = 0; q < l; ++q) sxf[c][q] = (float)sx[c][q];
+        if (D->lin) lin_shared_f32(E, D, mono32 + D->cp, sxf[c], s_lsv[c], s_lse[c]);
+      }
     }
     __syncthreads();
     const int nk = (int)min(s_nkill, (unsigned)PCBA_KILLERS);
@@ -386,12 +455,16 @@ __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* res
         const int c = it / nk;
         const int q = s_kill[it - c * nk];
         if (!s_has[c] || s_viol[c]) continue;
-        const bool is_g = q < D->alpha;
-        const float* a = is_g ? mono32 + D->cp + (long long)q * D->cg
-                              : mono32 + D->cp + (long long)D->alpha * D->cg +
-                                    (long long)(q - D->alpha) * D->ch;
+        const bool is_g = D->lin || q < D->alpha;
         float val, err;
-        horner_f32(a, l, is_g ? D->G : D->H, sxf[c], &val, &err);
+        if (D->lin) {
+          lin_value_f32(E, D, q, s_lsv[c], s_lse[c], &val, &err);
+        } else {
+          const float* a = is_g ? mono32 + D->cp + (long long)q * D->cg
+                                : mono32 + D->cp + (long long)D->alpha * D->cg +
+                                      (long long)(q - D->alpha) * D->ch;
+          horner_f32(a, l, is_g ? D->G : D->H, sxf[c], &val, &err);
+        }
         if (!(__fadd_ru(is_g ? val : fabsf(val), err) <= (is_g ? 0.0f : eq_tol))) s_viol[c] = 1;
       }
       __syncthreads();
@@ -400,12 +473,16 @@ __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* res
       const int c = it / total;
       const int q = it - c * total;
       if (!s_has[c] || s_viol[c]) continue;
-      const bool is_g = q < D->alpha;
-      const float* a = is_g ? mono32 + D->cp + (long long)q * D->cg
-                            : mono32 + D->cp + (long long)D->alpha * D->cg +
-                                  (long long)(q - D->alpha) * D->ch;
+      const bool is_g = D->lin || q < D->alpha;
       float val, err;
-      horner_f32(a, l, is_g ? D->G : D->H, sxf[c], &val, &err);
+      if (D->lin) {
+        lin_value_f32(E, D, q, s_lsv[c], s_lse[c], &val, &err);
+      } else {
+        const float* a = is_g ? mono32 + D->cp + (long long)q * D->cg
+                              : mono32 + D->cp + (long long)D->alpha * D->cg +
+                                    (long long)(q - D->alpha) * D->ch;
+        horner_f32(a, l, is_g ? D->G : D->H, sxf[c], &val, &err);
+      }
       if (!(__fadd_ru(is_g ? val : fabsf(val), err) <= (is_g ? 0.0f : eq_tol))) {
         s_viol[c] = 1;
         s_kill[atomicAdd(&s_nkill, 1u) % PCBA_KILLERS] = q;
@@ -527,7 +604,8 @@ __global__ void __launch_bounds__(PCBA_CAND_TPB, 1) k_cand_first(Engine E, const
   // and all of them lower first[p] (set to INT_MAX by k_cand_rank)
   const int nb = gridDim.y, by = blockIdx.y;
   const ProbDesc* D = E.desc + p;
-  const int l = D->l, alpha = D->alpha, total = D->alpha + D->beta;
+  const int l = D->l, alpha = D->alpha;
+  const int total = D->lin ? D->nlin : D->alpha + D->beta;
   const int tiles = (total + 31) >> 5;
   const int n_c = min(E.n_warm, PCBA_MAX_CAND);
   const long long base = (long long)p * E.n_warm;
@@ -564,6 +642,9 @@ __global__ void __launch_bounds__(PCBA_CAND_TPB, 1) k_cand_first(Engine E, const
     int kill[4];
     for (int k = 0; k < 4; ++k)
       kill[k] = __shfl_sync(0xffffffffu, lane == 0 ? *(volatile int*)&s_killer[k] : 0, 0);
+    // linear family: the shared polynomials at the point, once per candidate
+    float lsv[PCBA_MAX_SHARED], lse[PCBA_MAX_SHARED];
+    if (D->lin) lin_shared_f32(E, D, coef, xf, lsv, lse);
     bool bad = false;
     for (int step = 0; step < 4 + tiles && !bad; ++step) {
       int t;
@@ -578,7 +659,22 @@ __global__ void __launch_bounds__(PCBA_CAND_TPB, 1) k_cand_first(Engine E, const
       }
       const int q = t * 32 + lane;
       bool lane_bad = false;
-      if (q < total) {
+      if (q < total && D->lin) {
+        float val, err;
+        lin_value_f32(E, D, q, lsv, lse, &val, &err);
+        if (!(__fadd_ru(val, err) <= 0.0f)) {
+          lane_bad = true;
+          if (__fsub_rd(val, err) <= 0.0f) {
+            // undecided in FP32: the shared polynomials and the row in FP64
+            double xd[PCBA_MAXD], sv[PCBA_MAX_SHARED], se[PCBA_MAX_SHARED];
+            for (int r = 0; r < l; ++r) xd[r] = (double)xf[r];
+            lin_shared_f64(E, D, xd, sv, se);
+            double v64, e64;
+            lin_value_f64(E, D, q, sv, se, &v64, &e64);
+            lane_bad = !(__dadd_ru(v64, e64) <= 0.0);
+          }
+        }
+      } else if (q < total) {
         const bool is_g = q < alpha;
         const long long off = is_g ? (long long)q * D->cg
                                    : (long long)alpha * D->cg + (long long)(q - alpha) * D->ch;

@@ -45,23 +45,6 @@
 // ---------------------------------------------------------------------------
 // small exact helpers
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double dev_binom(int n, int k) {
-  if (k < 0 || k > n) return 0.0;
-  if (k > n - k) k = n - k;
-  double c = 1.0;
-  for (int i = 1; i <= k; ++i) c = c * (double)(n - k + i) / (double)i;
-  return c;
-}
-__device__ __forceinline__ double dev_pow(double x, int e) {
-  double r = 1.0;
-  for (int i = 0; i < e; ++i) r *= x;
-  return r;
-}
-
-__device__ __forceinline__ float addrn(float a, float b) { return __fadd_rn(a, b); }
-__device__ __forceinline__ double addrn(double a, double b) { return __dadd_rn(a, b); }
-__device__ __forceinline__ float mulrn(float a, float b) { return __fmul_rn(a, b); }
-__device__ __forceinline__ double mulrn(double a, double b) { return __dmul_rn(a, b); }
 
 // ---------------------------------------------------------------------------
 // K1: monomial -> Bernstein
@@ -233,6 +216,7 @@ __global__ void __launch_bounds__(128) k1_convert(Engine E, const double* mat, i
 }
 
 #include "pcba_subdivide.cuh"
+#include "pcba_linear.cuh"
 
 // ---------------------------------------------------------------------------
 // FP32 mode: refresh of marked patches from the FP64 monomials
@@ -412,17 +396,34 @@ __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
     const int* deg = fam ? D->H : D->G;
     refresh_matrices(binom, D->l, deg, blo, bhi, sT, lane);
     const size_t pad = fam ? D->bpad : D->apad;
-    float* block = (float*)(item + (fam ? D->off_h : D->off_g));
-    float* earr = (float*)(item + (fam ? D->off_eh : D->off_eg));
+    // linear-family items: the copy of the shared patches the next step reads
+    const int nxt = (E.plan->steps_global + 1) & 1;
+    float* block = (float*)(item + (fam ? D->off_h : D->off_g + nxt * D->copy_g));
+    float* earr = (float*)(item + (fam ? D->off_eh : D->off_eg + nxt * D->copy_e));
     const double* fam_mono = mono + D->cp + (fam ? (long long)D->alpha * D->cg : 0);
     const double err64 =
         refresh_convert(fam_mono + (long long)ip * C, C, D->l, deg, sT, sA, sB, sX, sY, lane);
+    // a linear family's shared patch is stored relative to the middle of its
+    // range, as the cost patch (the offset is an FP64 value kept exactly)
+    double O = 0.0;
+    if (D->lin) {
+      double bmin = INFINITY, bmax = -INFINITY;
+      for (int j = lane; j < C; j += 32) { bmin = fmin(bmin, sA[j]); bmax = fmax(bmax, sA[j]); }
+      for (int o = 16; o > 0; o >>= 1) {
+        bmin = fmin(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
+        bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+      }
+      O = 0.5 * (bmin + bmax);
+    }
     double emax = 0.0;
     for (int j = lane; j < C; j += 32) {
-      const float sv = __double2float_rn(sA[j]);
+      const double d = sA[j] - O;                 // |d - (b - O)| <= |d| 2^-53
+      const float sv = __double2float_rn(d);
       block[(size_t)j * pad + ip] = sv;
-      emax = fmax(emax, fabs((double)sv - sA[j]));
+      emax = fmax(emax, D->lin ? __dadd_ru(fabs((double)sv - d), __dmul_ru(fabs(d), 0x1p-52))
+                               : fabs((double)sv - sA[j]));
     }
+    if (D->lin && lane == 0) ((double*)(earr + D->apad))[ip] = O;
     for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
     if (lane == 0) {
       earr[ip] = __double2float_ru(__dadd_ru(emax, err64));
@@ -898,6 +899,16 @@ __global__ void k_init(Engine E) {
       S->t_end = 0;
       unsigned* idx = (unsigned*)(E.arena + D->list_off);
       for (int q = 0; q < D->l; ++q) idx[q] = 0u;
+      // linear families: every constraint is active on the root box, whose
+      // FP32 shared patches are stored relative to offsets 0
+      if (D->lin && E.precision == 32)
+        for (int q = 0; q < D->apad; ++q)
+          ((double*)(E.arena + D->list_off + D->off_eg + 4LL * D->apad))[q] = 0.0;
+      unsigned* mw = (unsigned*)(E.arena + D->list_off + D->off_mask);
+      for (int q = 0; q < D->mwords; ++q) {
+        const int rem = D->nlin - 32 * q;
+        mw[q] = rem >= 32 ? 0xFFFFFFFFu : ((1u << rem) - 1u);
+      }
       if (D->M < 2) {
         S->status = 2;  // MEMCAP before the first subdivision
         S->t_end = globaltimer();

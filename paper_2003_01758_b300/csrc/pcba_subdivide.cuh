@@ -149,14 +149,6 @@ __device__ __forceinline__ int axis_stride(const int* deg, int l, int r) {
   return s;
 }
 
-// order-preserving 32-bit key of a float (0 = below everything)
-__device__ __forceinline__ unsigned okey32(float x) {
-  const unsigned b = __float_as_uint(x);
-  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
-}
-__device__ __forceinline__ float okey32_dec(unsigned k) {
-  return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
-}
 
 // FP32 error bounds are stored with a mark in the sign bit, set when the bound
 // itself changes a decision of Def. 3 for this patch: the stored coefficients
@@ -440,19 +432,6 @@ __device__ __forceinline__ bool rec_feasible(const ChildRec& c, double eq_tol) {
   return gmaxmax <= 0.0 && hminmax <= 0.0 && hmaxmin >= 0.0 && habsmax <= eq_tol;
 }
 
-__device__ __forceinline__ ChildRec load_rec_cg(const ChildRec* p) {
-  ChildRec c;
-  const unsigned long long* s = (const unsigned long long*)p;
-  c.pmin = __ldcg(s + 0);
-  c.pmax = __ldcg(s + 1);
-  c.gminmax = __ldcg(s + 2);
-  c.gmaxmax = __ldcg(s + 3);
-  c.hminmax = __ldcg(s + 4);
-  c.hnegmaxmin = __ldcg(s + 5);
-  c.habsmax = __ldcg(s + 6);
-  c.perr = __ldcg(s + 7);
-  return c;
-}
 
 // Work unit = (problem, parent item k, tile t).  Tile 0 also splits the cost
 // patch (warp 0) and the box; every tile splits up to PCBA_TPB constraint

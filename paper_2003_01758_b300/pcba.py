@@ -45,6 +45,12 @@ class pcba_box(ctypes.Structure):
                 ("hi", ctypes.POINTER(ctypes.c_double))]
 
 
+class pcba_linear_family(ctypes.Structure):
+    _fields_ = [("n_shared", ctypes.c_int), ("shared", ctypes.c_void_p),
+                ("n_constraints", ctypes.c_int), ("weight", ctypes.POINTER(ctypes.c_double)),
+                ("offset", ctypes.POINTER(ctypes.c_double))]
+
+
 class pcba_result(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int), ("steps", ctypes.c_int), ("sweeps", ctypes.c_int),
                 ("from_warm_start", ctypes.c_int),
@@ -92,6 +98,8 @@ def lib():
         "pcba_batch_set_time_limit": ([P, D], I),
         "pcba_set_time_limit": ([P, D], I),
         "pcba_eval_points_f32": ([P, I, P, P, I, I, P, P, P], I),
+        "pcba_create_linear": ([P, P, P, P, I], I),
+        "pcba_get_active": ([P, P, LL], I),
         "pcba_batch_polish": ([P, D, D, D, I, P], I),
         "pcba_batch_solve_polished": ([P, D, D, D, D, I, P], I),
         "pcba_batch_destroy": ([P], None),
@@ -144,7 +152,7 @@ def exported_symbols():
             "pcba_mlp_create", "pcba_mlp_destroy", "pcba_mlp_num_params", "pcba_mlp_set_params",
             "pcba_mlp_get_params", "pcba_mlp_forward", "pcba_mlp_gradient",
             "pcba_mlp_train_step", "pcba_set_time_limit", "pcba_batch_set_time_limit",
-            "pcba_eval_points_f32"]
+            "pcba_eval_points_f32", "pcba_create_linear", "pcba_get_active"]
 
 
 def _check(rc):
@@ -286,6 +294,69 @@ class Solver:
         return (cost.reshape(tuple(self.P + 1)),
                 ineq[:self.n_ineq * cg].reshape((self.n_ineq,) + tuple(self.G + 1)),
                 eq[:self.n_eq * ch].reshape((self.n_eq,) + tuple(self.H + 1)))
+
+
+class LinearSolver(Solver):
+    """A problem whose inequalities are affine in K shared polynomials
+    (pcba_create_linear): g_i = offset[i] + sum_m weight[i, m] shared[m].
+
+    shared is an array (K, G+1...) of monomial tensors at one common
+    multi-degree, weight (alpha, K), offset (alpha,).  The list's "ineq"
+    patches (get_list, root_patches) are the K shared patches."""
+
+    def __init__(self, cost, shared, weight, offset, lo=-1.0, hi=1.0, precision=FP32):
+        cost = np.ascontiguousarray(cost, dtype=np.float64)
+        shared = np.ascontiguousarray(shared, dtype=np.float64)
+        l = cost.ndim
+        self.l = l
+        K = int(shared.shape[0])
+        weight = np.ascontiguousarray(weight, dtype=np.float64).reshape(-1, K)
+        offset = np.ascontiguousarray(offset, dtype=np.float64).reshape(-1)
+        assert weight.shape[0] == offset.shape[0]
+        self.n_ineq, self.n_eq, self.n_lin = K, 0, int(offset.shape[0])
+        self.precision = precision
+        lo = np.ascontiguousarray(np.broadcast_to(lo, (l,)), dtype=np.float64)
+        hi = np.ascontiguousarray(np.broadcast_to(hi, (l,)), dtype=np.float64)
+        cdeg = np.ascontiguousarray(np.array(cost.shape) - 1, dtype=np.int32)
+        sdeg = np.ascontiguousarray(np.array(shared.shape[1:]) - 1, dtype=np.int32)
+        rec = np.zeros(K, dtype=_POLY_DTYPE)
+        rec["nvars"] = l
+        rec["degree"] = sdeg.ctypes.data
+        rec["coeff"] = shared.ctypes.data + shared.strides[0] * np.arange(K, dtype=np.uint64)
+        self._keep = [cost, shared, weight, offset, lo, hi, cdeg, sdeg, rec]
+        c = pcba_poly(l, cdeg.ctypes.data_as(ctypes.POINTER(ctypes.c_int)),
+                      cost.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        fam = pcba_linear_family(K, rec.ctypes.data_as(ctypes.c_void_p), self.n_lin,
+                                 weight.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                 offset.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        box = pcba_box(l, lo.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                       hi.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        h = ctypes.c_void_p()
+        _check(lib().pcba_create_linear(ctypes.byref(h), ctypes.byref(c), ctypes.byref(fam),
+                                        ctypes.byref(box), precision))
+        self._h = h
+        self.P = np.array(cost.shape) - 1
+        self.G = np.array(shared.shape[1:]) - 1
+        self.H = np.zeros(l, int)
+
+    def get_active(self):
+        """Activity bits of the last solve's list as a bool array (K, alpha):
+        True where constraint i is still undecided (or violated) on item k."""
+        words = _check(lib().pcba_get_active(self._h, None, 0))
+        K = ctypes.c_longlong()
+        _check(lib().pcba_get_list(self._h, ctypes.byref(K), None, None, None, None, None, None))
+        K = K.value
+        bits = np.zeros(max(1, K * words), dtype=np.uint32)
+        _check(lib().pcba_get_active(self._h, _p(bits), bits.size))
+        b = np.unpackbits(bits[:K * words].view(np.uint8), bitorder="little").reshape(K, -1)
+        return b[:, :self.n_lin].astype(bool)
+
+
+def linear_solver_from_problem(prob, precision=FP32):
+    """LinearSolver of a workloads problem that carries its linear form
+    (meta["linear"] = (shared, weight, offset))."""
+    shared, weight, offset = prob.meta["linear"]
+    return LinearSolver(prob.cost, shared, weight, offset, prob.lo, prob.hi, precision=precision)
 
 
 def bernstein_convert_noalloc(d_mono_ptr: int, n_patches: int, degree, lo, hi, d_out_ptr: int,

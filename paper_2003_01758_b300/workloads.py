@@ -21,7 +21,9 @@ Workloads (numpy ``default_rng(seed)``):
             g_i = r^2 - ||F(q) - o_i||^2 (degree (6,6), r = 0.15), cost
             ||F(q) - goal||^2 with goal ~ U([-2,2]^2).  This stands in for the
             reachability-based trajectory design POP of Sec. II-C, whose FRS
-            polynomial w is not available.
+            polynomial w is not available.  The constraints are also given
+            as a linear family in the shared polynomials (||F||^2, F_1, F_2)
+            (meta["linear"] = (shared, weight, offset)).
   dim4      l=4 on [-1,1]^4, cost degree 4 per axis ~ N(0,1), 64 inequalities of
             degree 3 per axis shifted so g_i(q*) = -0.1, 2 equalities of degree 2
             per axis with h_j(q*) = 0.
@@ -131,10 +133,14 @@ def rtd(seed: int, n_obstacles: int = 512, radius: float = 0.15, f_degree: int =
     sl = (slice(None),) + tuple(slice(0, s) for s in shape)
     ineq[sl] += (2.0 * obstacles[:, 0])[:, None, None] * F[0] \
         + (2.0 * obstacles[:, 1])[:, None, None] * F[1]
-    ineq[:, 0, 0] += np.array([radius * radius - float(o @ o) for o in obstacles])
+    offset = np.array([radius * radius - float(o @ o) for o in obstacles])
+    ineq[:, 0, 0] += offset
+    # the same constraints as a linear family: g_i = offset_i + w_i . (||F||^2, F_1, F_2)
+    shared = np.stack([FF, pad_to(F[0], FF.shape), pad_to(F[1], FF.shape)])
+    weight = np.stack([-np.ones(n_obstacles), 2.0 * obstacles[:, 0], 2.0 * obstacles[:, 1]], 1)
     return Problem(pad_to(cost, FF.shape), ineq, _empty_family(2), -np.ones(2), np.ones(2),
                    {"F": F, "obstacles": obstacles, "goal": goal, "radius": radius,
-                    "workload": "rtd", "seed": seed})
+                    "workload": "rtd", "seed": seed, "linear": (shared, weight, offset)})
 
 
 def dim4(seed: int, n_ineq: int = 64, n_eq: int = 2) -> Problem:

@@ -335,3 +335,20 @@ def test_evd_shows_plain_fp64_conditioning_limit():
                        opt_tol=1e-7 * p["optimum"], max_iters=40, max_items=1 << 22)
     miss = max(res["lower"] - p["optimum"], p["optimum"] - res["upper"], 0.0)
     assert miss <= 1e3 * scale
+
+
+def test_rtd_linear_form_expands_to_the_dense_constraints():
+    """The linear-family form of the rtd constraints, offset_i + sum_m w_im
+    s_m, is the same polynomial as the dense tensor the oracle receives."""
+    from paper_2003_01758_b300 import workloads as W
+    p = W.rtd(2000, n_obstacles=40)
+    shared, weight, offset = p.meta["linear"]
+    dense = np.einsum("im,mab->iab", weight, shared)
+    dense[:, 0, 0] += offset
+    assert np.abs(dense - p.ineq).max() <= 1e-13 * np.abs(p.ineq).max()
+    # and a spot value: g_0 = r^2 - ||F(q) - o_0||^2 at a point
+    q = np.array([0.3, -0.7])
+    F = [W.poly_value(f, q) for f in p.meta["F"]]
+    o = p.meta["obstacles"][0]
+    g0 = p.meta["radius"] ** 2 - ((F[0] - o[0]) ** 2 + (F[1] - o[1]) ** 2)
+    assert abs(oracle.eval_monomial(p.ineq[0], q) - g0) <= 1e-12
