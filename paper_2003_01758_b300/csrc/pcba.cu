@@ -24,6 +24,7 @@
 #include <vector>
 
 #include "pcba.h"
+#include "pcba_host.h"
 #include "pcba_kernels.cuh"
 #include "pcba_warmstart.h"
 
@@ -119,29 +120,12 @@ void layout_item(const HostProblem& P, int prec, ProbDesc& d) {
 }
 
 struct Grids {
-  int lin_k = 0;                     // linear families: shared patches per item (0: dense)
-  int lin_cgmax = 1, lin_cpmax = 1;  // largest shared / cost patch of the batch
-  int nmax = 16;  // degree class of the subdivision kernel (4, 8 or 16)
-  int nfix = 0;   // every patch of the batch has this degree on every axis (4 or 6), else 0
-  bool tma = false;  // TMA-staged subdivision kernel
-  int tma_wpb = 8, tma_stages = 2, tma_stage_elems = 0, tma_cpmax = 1;
-  size_t tma_smem = 0;
-  int tma_grid = 1;
-  // feasible subdivision configurations: index 0 = direct loads, then TMA
-  // (warps per block, stages, shared bytes, grid)
-  struct K2Cfg {
-    bool tma;
-    int wpb, stages;
-    size_t smem;
-    int grid;
-  };
-  std::vector<K2Cfg> cfgs;
-  int cfg = 0;
+  K2Plan k2;          // subdivision kernels (pcba_k2.cu): variant and configurations
+  int cfg = 0;        // configuration in use (index into k2.cfgs)
+  bool tma = false;   // it stages parents with TMA (tensor maps needed)
   int sms = 148;
   int k1_grid = 1, k1_wpb = 1, k1_cmax = 1;
   size_t k1_smem = 0;
-  int k2_grid = 1;
-  size_t k2_smem = 0;
   int k3_grid = 1, k4_grid = 1;
   // FP32 refresh kernel
   int kr_grid = 1, kr_wpb = 4, kr_cmax = 1, kr_lmax = 1;
@@ -386,69 +370,10 @@ void free_batch(pcba_batch* b) {
   delete b;
 }
 
-// The TMA subdivision kernel instantiation for a degree class / fixed degree.
-template <typename T>
-const void* tma_kernel(int nmax, int nfix) {
-  if (nfix == 6) return (const void*)k2_subdivide_tma<T, 8, 6>;
-  if (nfix == 4) return (const void*)k2_subdivide_tma<T, 4, 4>;
-  if (nmax <= 4) return (const void*)k2_subdivide_tma<T, 4>;
-  if (nmax <= 8) return (const void*)k2_subdivide_tma<T, 8>;
-  return (const void*)k2_subdivide_tma<T, 16>;
-}
-
 template <typename T>
 void launch_k2(const pcba_batch* b, cudaStream_t s) {
-  const Grids& g = b->g;
-  if (g.lin_k > 0) {
-    const Grids::K2Cfg& c = g.cfgs[g.cfg];
-    const dim3 blk(32 * c.wpb);
-    switch (g.lin_k) {
-      case 1: k2_subdivide_lin<T, 1><<<c.grid, blk, c.smem, s>>>(b->E, g.lin_cgmax, g.lin_cpmax); break;
-      case 2: k2_subdivide_lin<T, 2><<<c.grid, blk, c.smem, s>>>(b->E, g.lin_cgmax, g.lin_cpmax); break;
-      case 3: k2_subdivide_lin<T, 3><<<c.grid, blk, c.smem, s>>>(b->E, g.lin_cgmax, g.lin_cpmax); break;
-      default: k2_subdivide_lin<T, 4><<<c.grid, blk, c.smem, s>>>(b->E, g.lin_cgmax, g.lin_cpmax); break;
-    }
-    return;
-  }
-  if (g.tma) {
-    const dim3 blk(32 * g.tma_wpb);
-    const int st = g.tma_stages, se = g.tma_stage_elems, cp = g.tma_cpmax;
-    if (g.nfix == 6)
-      k2_subdivide_tma<T, 8, 6><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, st, se, cp);
-    else if (g.nfix == 4)
-      k2_subdivide_tma<T, 4, 4><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, st, se, cp);
-    else if (g.nmax <= 4)
-      k2_subdivide_tma<T, 4><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, st, se, cp);
-    else if (g.nmax <= 8)
-      k2_subdivide_tma<T, 8><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, st, se, cp);
-    else
-      k2_subdivide_tma<T, 16><<<g.tma_grid, blk, g.tma_smem, s>>>(b->E, st, se, cp);
-    return;
-  }
-  if (g.nmax <= 4) k2_subdivide<T, 4><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
-  else if (g.nmax <= 8) k2_subdivide<T, 8><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
-  else k2_subdivide<T, 16><<<g.k2_grid, PCBA_TPB, g.k2_smem, s>>>(b->E);
-}
-
-// The linear-family subdivision kernel for K shared patches, and the shared
-// memory one of its warps uses.
-template <typename T>
-const void* lin_kernel(int K) {
-  switch (K) {
-    case 1: return (const void*)k2_subdivide_lin<T, 1>;
-    case 2: return (const void*)k2_subdivide_lin<T, 2>;
-    case 3: return (const void*)k2_subdivide_lin<T, 3>;
-    default: return (const void*)k2_subdivide_lin<T, 4>;
-  }
-}
-template <typename T>
-size_t lin_warp_smem(int K, int cgmax, int cpmax) {
-  switch (K) {
-    case 1: return lin_warp_bytes<T, 1>(cgmax, cpmax);
-    case 2: return lin_warp_bytes<T, 2>(cgmax, cpmax);
-    case 3: return lin_warp_bytes<T, 3>(cgmax, cpmax);
-    default: return lin_warp_bytes<T, 4>(cgmax, cpmax);
-  }
+  if (sizeof(T) == 4) pcba_k2_launch_f32(b->g.k2, b->g.cfg, b->E, s);
+  else pcba_k2_launch_f64(b->g.k2, b->g.cfg, b->E, s);
 }
 
 // The kernels of one device-loop iteration after the subdivision: the FP32
@@ -505,88 +430,11 @@ int setup_kernels(pcba_batch* b) {
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k1_convert<T>, 32 * g.k1_wpb,
                                                         g.k1_smem));
   g.k1_grid = std::max(1, occ) * g.sms;
-  // K2: cost staging in shared memory; kernel variant by the largest degree
-  int dmax = 0;
-  for (const ProbDesc& d : b->desc)
-    for (int r = 0; r < d.l; ++r) dmax = std::max(dmax, std::max(d.P[r], std::max(d.G[r], d.H[r])));
-  g.nmax = dmax <= 4 ? 4 : (dmax <= 8 ? 8 : 16);
+  // K2: the subdivision kernel variant and its configurations
   {
-    // a single degree on every axis of every patch of the batch: fixed-degree kernel
-    int fixed = -1;
-    bool uniform = true;
-    auto see = [&](int n) {
-      if (fixed < 0) fixed = n;
-      else if (fixed != n) uniform = false;
-    };
-    for (const ProbDesc& d : b->desc)
-      for (int r = 0; r < d.l; ++r) {
-        see(d.P[r]);
-        if (d.alpha > 0) see(d.G[r]);
-        if (d.beta > 0) see(d.H[r]);
-      }
-    g.nfix = (uniform && (fixed == 4 || fixed == 6) && !std::getenv("PCBA_NO_FIXED_DEGREE"))
-                 ? fixed : 0;
-  }
-  g.k2_smem = (size_t)(2 * cpmax) * sizeof(T);
-  const void* k2 = g.nmax == 4 ? (const void*)k2_subdivide<T, 4>
-                               : (g.nmax == 8 ? (const void*)k2_subdivide<T, 8>
-                                              : (const void*)k2_subdivide<T, 16>);
-  PCBA_CK(cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)std::max<size_t>(g.k2_smem, 1)));
-  PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k2, PCBA_TPB, g.k2_smem));
-  g.k2_grid = std::max(1, occ) * g.sms;
-  // candidate configurations: direct loads, then TMA-staged with per warp
-  // 'stages' copies of a [C][32] column block (C <= 256, the TMA box limit)
-  g.cfgs.clear();
-  g.cfgs.push_back({false, 8, 1, g.k2_smem, g.k2_grid});
-  {
-    long long cstage = 1;
-    bool fits = true;
-    for (const ProbDesc& d : b->desc) {
-      if (d.alpha > 0) cstage = std::max<long long>(cstage, d.cg);
-      if (d.beta > 0) cstage = std::max<long long>(cstage, d.ch);
-      if ((d.alpha > 0 && d.cg > 256) || (d.beta > 0 && d.ch > 256)) fits = false;
-    }
-    g.tma_stage_elems = (int)(cstage * 32);
-    g.tma_cpmax = (int)cpmax;
-    const size_t head_cap = ((size_t)64 + (size_t)cpmax * sizeof(T) + 32 + 127) / 128 * 128;
-    const size_t stage_bytes = (size_t)g.tma_stage_elems * sizeof(T) + 128 + head_cap;
-    const int cand[][2] = {{8, 2}, {8, 3}, {4, 2}, {4, 3}, {2, 2}};
-    const void* kt = tma_kernel<T>(g.nmax, g.nfix);
-    size_t smem_max = 0;
-    for (const auto& c : cand) {
-      const size_t wb = ((size_t)c[1] * stage_bytes + 2 * (size_t)cpmax * sizeof(T) + 127) / 128 * 128;
-      const size_t total = (size_t)c[0] * wb + (size_t)c[0] * c[1] * 8;
-      if (fits && total <= (size_t)smem_optin) {
-        g.cfgs.push_back({true, c[0], c[1], total, 0});
-        smem_max = std::max(smem_max, total);
-      }
-    }
-    if (g.cfgs.size() > 1) {
-      PCBA_CK(cudaFuncSetAttribute(kt, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max));
-      for (auto& c : g.cfgs) {
-        if (!c.tma) continue;
-        PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kt, 32 * c.wpb, c.smem));
-        c.grid = std::max(1, occ) * g.sms;
-      }
-    }
-  }
-  if (b->lin) {
-    // linear families: one subdivision kernel (warp per unit), no TMA staging
-    g.lin_k = b->desc[0].alpha;
-    g.lin_cpmax = (int)cpmax;
-    g.lin_cgmax = 1;
-    for (const ProbDesc& d : b->desc) g.lin_cgmax = std::max(g.lin_cgmax, d.cg);
-    const size_t wb = lin_warp_smem<T>(g.lin_k, g.lin_cgmax, g.lin_cpmax);
-    int wpb = 8;
-    while (wpb > 1 && (size_t)wpb * wb > (size_t)smem_optin) wpb /= 2;
-    if (wb > (size_t)smem_optin) return fail(PCBA_ERR_INVALID, "shared patches too large");
-    const void* kl = lin_kernel<T>(g.lin_k);
-    PCBA_CK(cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)(wpb * wb)));
-    PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kl, 32 * wpb, wpb * wb));
-    g.cfgs.clear();
-    g.cfgs.push_back({false, wpb, 1, wpb * wb, std::max(1, occ) * g.sms});
+    const int rc = sizeof(T) == 4 ? pcba_k2_prepare_f32(g.k2, b->desc, b->lin != 0, g.sms, smem_optin)
+                                  : pcba_k2_prepare_f64(g.k2, b->desc, b->lin != 0, g.sms, smem_optin);
+    if (rc) return rc;
   }
   // FP32 refresh: per warp 4 patch buffers of the largest patch and the
   // per-axis matrices; warps per block limited by shared memory
@@ -710,15 +558,11 @@ int build_tensor_maps(pcba_batch* b) {
 // groups), so the descriptors are re-uploaded.
 int apply_k2_config(pcba_batch* b, int idx) {
   Grids& g = b->g;
-  if (idx < 0 || idx >= (int)g.cfgs.size()) return fail(PCBA_ERR_INVALID, "no such configuration");
-  const Grids::K2Cfg& c = g.cfgs[idx];
+  if (idx < 0 || idx >= (int)g.k2.cfgs.size()) return fail(PCBA_ERR_INVALID, "no such configuration");
+  const K2Cfg& c = g.k2.cfgs[idx];
   g.cfg = idx;
   g.tma = c.tma;
   if (c.tma) {
-    g.tma_wpb = c.wpb;
-    g.tma_stages = c.stages;
-    g.tma_smem = c.smem;
-    g.tma_grid = c.grid;
     if (!b->d_tmaps) {
       const int rc = build_tensor_maps(b);
       if (rc) return rc;
@@ -970,7 +814,7 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   E.lin32 = b->d_lin32;
   E.lin64 = b->d_lin64;
   rc = prec == PCBA_FP32 ? setup_kernels<float>(b) : setup_kernels<double>(b);
-  if (!rc) rc = apply_k2_config(b, (b->want_tma && b->g.cfgs.size() > 1) ? 1 : 0);
+  if (!rc) rc = apply_k2_config(b, (b->want_tma && b->g.k2.cfgs.size() > 1) ? 1 : 0);
   if (!rc && (flags & 3) == 0) rc = prec == PCBA_FP32 ? build_graph<float>(b) : build_graph<double>(b);
   if (rc) {
     std::string msg = g_err;
@@ -1228,21 +1072,11 @@ int launch_polish(pcba_batch* b, double* d_out, double mu0, double gap, double e
     return fail(PCBA_ERR_INVALID, "need mu0, gap, eq_tol > 0 and 1 <= iters <= 200");
   bool seen[PCBA_MAXD + 1] = {};
   for (int k = 0; k < b->np; ++k) seen[b->desc[k].l] = true;
-  cudaStream_t s = b->stream;
-  const unsigned g = (unsigned)b->np;
   for (int L = 1; L <= PCBA_MAXD; ++L) {
     if (!seen[L]) continue;
-    switch (L) {
-      case 1: k_polish<1><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
-      case 2: k_polish<2><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
-      case 3: k_polish<3><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
-      case 4: k_polish<4><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
-      case 5: k_polish<5><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
-      case 6: k_polish<6><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
-      case 7: k_polish<7><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
-      default: k_polish<8><<<g, PCBA_POLISH_TPB, 0, s>>>(b->E, d_out, mu0, gap, eq_tol, iters); break;
-    }
-    PCBA_CK(cudaGetLastError());
+    const int rc = pcba_polish_launch(b->E, L, (unsigned)b->np, b->stream, d_out, mu0, gap,
+                                      eq_tol, iters);
+    if (rc) return rc;
     ++*launches;
   }
   return 0;
@@ -1659,11 +1493,11 @@ int pcba_batch_timing(const pcba_batch* b, double* total_ms, double* subdiv_ms,
 int pcba_batch_autotune(pcba_batch* b, double opt_tol, double eq_tol, int max_iters,
                         double* ms_per_config, int max_configs, int* chosen) {
   if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
-  const int ncfg = (int)b->g.cfgs.size();
+  const int ncfg = (int)b->g.k2.cfgs.size();
   double best = 1e300;
   int best_i = b->g.cfg;
   for (int i = 0; i < ncfg; ++i) {
-    if (b->g.cfgs[i].tma && !b->want_tma) continue;
+    if (b->g.k2.cfgs[i].tma && !b->want_tma) continue;
     int rc = apply_k2_config(b, i);
     if (!rc) rc = rebuild_graph(b);
     if (!rc) rc = batch_solve_impl(b, nullptr, opt_tol, eq_tol, max_iters, 0, nullptr, nullptr);
@@ -1685,7 +1519,7 @@ int pcba_batch_autotune(pcba_batch* b, double opt_tol, double eq_tol, int max_it
 int pcba_batch_config(const pcba_batch* b, int* tma, int* warps_per_block, int* stages,
                       int* grid) {
   if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
-  const Grids::K2Cfg& c = b->g.cfgs[b->g.cfg];
+  const K2Cfg& c = b->g.k2.cfgs[b->g.cfg];
   if (tma) *tma = c.tma ? 1 : 0;
   if (warps_per_block) *warps_per_block = c.wpb;
   if (stages) *stages = c.stages;

@@ -294,34 +294,6 @@ __device__ __forceinline__ void lin_shared_f32(const Engine& E, const ProbDesc* 
     horner_f32_any(coef + (long long)m * D->cg, D->l, D->G, x, &sv[m], &se[m]);
 }
 
-// candidate c of problem p: mode 0 a warm-start row (NaN first coordinate:
-// none), mode 1 the point the solve returns; false if there is none
-__device__ __forceinline__ bool eval_candidate(const Engine& E, int mode, int p, int c, double* x) {
-  const ProbDesc* D = E.desc + p;
-  const ProbState* S = E.state + p;
-  const int l = D->l;
-  if (mode == 0) {
-    const double* w = E.warm + ((long long)p * E.n_warm + c) * PCBA_MAXD;
-    if (isnan(w[0])) return false;
-    for (int q = 0; q < l; ++q) x[q] = (double)__double2float_rn(w[q]);  // FP32 coordinates
-    return true;
-  }
-  if (S->have_box) {
-    for (int q = 0; q < l; ++q) {
-      const double w = ldexp(D->hi[q] - D->lo[q], -S->best_level[q]);
-      const double blo = D->lo[q] + w * (double)S->best_index[q];
-      const double bhi = D->lo[q] + w * (double)(S->best_index[q] + 1u);
-      x[q] = 0.5 * (blo + bhi);
-    }
-    return true;
-  }
-  if (S->from_warm) {
-    for (int q = 0; q < l; ++q) x[q] = S->warm_x[q];
-    return true;
-  }
-  return false;
-}
-
 #define PCBA_KILLERS 32
 
 __global__ void __launch_bounds__(PCBA_TPB) k_eval(Engine E, int mode, void* results) {

@@ -1,8 +1,9 @@
 // Kernels of one PCBA step (Algorithm 1) for many problems at once, plus the
-// monomial-to-Bernstein conversion and the point checks.  The subdivision
-// kernels live in pcba_subdivide.cuh, the point evaluations (warm start,
-// final check) in pcba_eval.cuh and the local polish of an incumbent in
-// pcba_polish.cuh, all included below.
+// monomial-to-Bernstein conversion and the point checks.  The point
+// evaluations (warm start, final check) live in pcba_eval.cuh, included
+// below; the subdivision kernels (pcba_subdivide.cuh, pcba_linear.cuh) and
+// the local polish of an incumbent (pcba_polish.cuh) are compiled in their
+// own translation units (pcba_k2.cu, pcba_polish.cu).
 //
 //   k1_matrices / k1_convert  Alg. 1 line 1 (InitPatches, Sec. II-D): per axis
 //                             the matrix T_r = (power -> Bernstein on [0,1]) x
@@ -215,8 +216,6 @@ __global__ void __launch_bounds__(128) k1_convert(Engine E, const double* mat, i
   }
 }
 
-#include "pcba_subdivide.cuh"
-#include "pcba_linear.cuh"
 
 // ---------------------------------------------------------------------------
 // FP32 mode: refresh of marked patches from the FP64 monomials
@@ -954,4 +953,4 @@ __global__ void k_init(Engine E) {
 }
 
 #include "pcba_eval.cuh"
-#include "pcba_polish.cuh"
+
