@@ -257,6 +257,13 @@ int pcba_batch_stats(const pcba_batch* b, long long* loop_iters, long long* kern
  * last solve (their error bound changed a classification) and patches actually
  * refreshed (marked children that survived the cut-off). */
 int pcba_batch_refresh_stats(const pcba_batch* b, long long* marked, long long* refreshed);
+/* Linear families: constraint bounds computed by the last solve - pairs of
+ * (child box, active constraint), and how many of them needed the range of
+ * the constraint's coefficients rather than the interval bound from the
+ * shared patches' ranges - and the coefficients per shared patch (of the
+ * first problem).  All 0 for dense batches. */
+int pcba_batch_linear_stats(const pcba_batch* b, long long* pairs, long long* full,
+                            long long* coeffs);
 /* Local polish of the point each problem's last solve returned (not in the
  * paper).  From the centre of the last solve's best box (or its certified
  * warm point): a log-barrier Newton method in FP64 on

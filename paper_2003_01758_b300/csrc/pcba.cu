@@ -112,6 +112,10 @@ void layout_item(const HostProblem& P, int prec, ProbDesc& d) {
   off = P.lin ? off + 2 * d.copy_g : round_up(off + P.cg * d.apad * w, 128);
   d.off_h = off;
   off = off + P.ch * d.bpad * w;
+  // linear families: two 64-bit summaries of the non-empty activity chunks
+  // (read from one, written to the other, alternating by step), then the bits
+  d.off_sum = off;
+  if (P.lin) off += 16;
   d.off_mask = off;
   off += 4LL * d.mwords;
   d.item_bytes = round_up(off, 256);
@@ -853,6 +857,11 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   }
   P.np = n;
   P.time_limit_ns = b->time_limit_s > 0.0 ? (unsigned long long)(b->time_limit_s * 1e9) : 0ull;
+  {
+    // tuning knob of the linear-family kernel (units per item), for experiments
+    const char* ls = std::getenv("PCBA_LIN_SPLIT");
+    P.lin_split = ls ? std::atoi(ls) : PCBA_LIN_SPLIT;
+  }
   PCBA_CK(cudaEventRecord(b->ev0, s));
   b->h2d_bytes = (long long)sizeof(SolveParams) + (host_coeffs ? 8LL * b->mono_doubles : 0) +
                  (warm ? 8LL * PCBA_MAXD * n : 0) +
@@ -1556,6 +1565,15 @@ int pcba_batch_refresh_stats(const pcba_batch* b, long long* marked, long long* 
   if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
   if (marked) *marked = (long long)b->h_plan->marks_total;
   if (refreshed) *refreshed = (long long)b->h_plan->refreshed_total;
+  return 0;
+}
+
+int pcba_batch_linear_stats(const pcba_batch* b, long long* pairs, long long* full,
+                            long long* coeffs) {
+  if (!b) return fail(PCBA_ERR_INVALID, "batch is null");
+  if (pairs) *pairs = (long long)b->h_plan->lin_pairs;
+  if (full) *full = (long long)b->h_plan->lin_full;
+  if (coeffs) *coeffs = b->lin ? (long long)b->desc[0].cg : 0;
   return 0;
 }
 

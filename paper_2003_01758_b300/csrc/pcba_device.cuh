@@ -17,7 +17,10 @@
 // apart): a bisection step reads the copy of its parity and writes the
 // children into the other one, so that the several work units of one parent
 // can all read it while the left child takes its slot.  After the patches,
-// off_mask holds one activity bit per constraint (mwords words).
+// off_sum holds two 64-bit summaries (bit t: chunk t of the activity bits is
+// not empty; same alternation) and off_mask one activity bit per constraint
+// (mwords words).  An item whose summary is empty - every constraint proven
+// to hold on its box - no longer carries its shared patches.
 //
 // Constraint-minor storage makes every load and store of the subdivision
 // kernel unit-stride across the threads of a warp for every bisection
@@ -41,6 +44,8 @@
 #define PCBA_TRACE_PER_DIM 40
 #define PCBA_LIN_WORDS 8     // activity words (256 constraints) per linear subdivision unit
 #define PCBA_LIN_STRIDE 8    // floats / doubles per linear constraint row (c, w_0 .. w_K-1)
+#define PCBA_LIN_BATCH 4     // units a warp of the linear subdivision kernel fetches at once
+#define PCBA_LIN_SPLIT (1 << 30)  // default of SolveParams::lin_split (always one unit per chunk)
 
 struct ProbDesc {
   int l;
@@ -70,6 +75,7 @@ struct ProbDesc {
   int mwords;                // activity words per item (32 constraints each)
   int lin_chunks;            // subdivision units per item (PCBA_LIN_WORDS words each)
   long long off_mask;        // activity bits of the item
+  long long off_sum;         // two u64: bit t set iff chunk t has an active constraint
   long long copy_g, copy_e;  // byte distance between the two copies of the shared
                              // patches / of their error bounds (0: one copy)
   long long lin_off;         // first row of this problem in the constraint tables
@@ -121,6 +127,7 @@ struct ProbState {
   double seed_cost;             // its certified cost bound (the initial p_up)
   double seed_x[PCBA_MAXD];     // the candidate
   float box_err;                // FP32: e_p of the returned box's cost patch (in p_up)
+  int lin_tiles;                // linear families: subdivision units per item this step
   double warm_err;              // FP64 rounding bound of the warm point's cost (in p_up)
 };
 
@@ -131,6 +138,7 @@ struct SolveParams {
   int step_guard;     // hard bound on device loop iterations
   int np;
   unsigned long long time_limit_ns;  // 0: none; else stop running problems (TIMEOUT)
+  int lin_split;      // linear families: chunk units while K * chunks <= lin_split
 };
 
 struct Plan {
@@ -141,6 +149,9 @@ struct Plan {
   unsigned kr_units;
   unsigned mark_count[2];  // marked patches appended by the subdivision of even / odd steps
   unsigned long long marks_total, refreshed_total;
+  unsigned long long lin_pairs;  // linear families: (child, active constraint) bounds of the solve
+  unsigned long long lin_full;   // of which bounded from the coefficient range (not the interval)
+  unsigned lin_next;             // next unit of the linear subdivision kernel to hand out
   unsigned k3_done;
   unsigned k4_done;             // blocks of k_move_control finished (the last one runs the control)
   int any_running;

@@ -50,12 +50,15 @@ const void* direct_kernel(int nmax) {
 
 // The linear-family subdivision kernel for K shared patches, and the shared
 // memory one of its warps uses.
-const void* lin_kernel(int K) {
+// (K = 3 with every patch of degree 6 on every axis - the obstacle
+// constraints of degree-(3,3) maps - has a fixed-degree instance.)
+const void* lin_kernel(int K, int nfix) {
+  if (K == 3 && nfix == 6) return (const void*)k2_subdivide_lin<T, 3, 6>;
   switch (K) {
-    case 1: return (const void*)k2_subdivide_lin<T, 1>;
-    case 2: return (const void*)k2_subdivide_lin<T, 2>;
-    case 3: return (const void*)k2_subdivide_lin<T, 3>;
-    default: return (const void*)k2_subdivide_lin<T, 4>;
+    case 1: return (const void*)k2_subdivide_lin<T, 1, 0>;
+    case 2: return (const void*)k2_subdivide_lin<T, 2, 0>;
+    case 3: return (const void*)k2_subdivide_lin<T, 3, 0>;
+    default: return (const void*)k2_subdivide_lin<T, 4, 0>;
   }
 }
 size_t lin_warp_smem(int K, int cgmax, int cpmax) {
@@ -70,27 +73,7 @@ size_t lin_warp_smem(int K, int cgmax, int cpmax) {
 int prepare(K2Plan& g, const std::vector<ProbDesc>& desc, bool lin, int sms, int smem_optin) {
   long long cpmax = 1;
   for (const ProbDesc& d : desc) cpmax = std::max<long long>(cpmax, d.cp);
-  int occ = 0;
-  g.cfgs.clear();
-  if (lin) {
-    // linear families: one subdivision kernel (a warp per unit), no TMA staging
-    g.lin_k = desc[0].alpha;
-    g.lin_cpmax = (int)cpmax;
-    g.lin_cgmax = 1;
-    for (const ProbDesc& d : desc) g.lin_cgmax = std::max(g.lin_cgmax, d.cg);
-    const size_t wb = lin_warp_smem(g.lin_k, g.lin_cgmax, g.lin_cpmax);
-    if (wb > (size_t)smem_optin)
-      return pcba_internal_fail(PCBA_ERR_INVALID, "shared patches too large");
-    int wpb = 8;
-    while (wpb > 1 && (size_t)wpb * wb > (size_t)smem_optin) wpb /= 2;
-    const void* kl = lin_kernel(g.lin_k);
-    K2_CK(cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(wpb * wb)));
-    K2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kl, 32 * wpb, wpb * wb));
-    g.cfgs.push_back({false, wpb, 1, wpb * wb, std::max(1, occ) * sms});
-    return 0;
-  }
-  g.lin_k = 0;
-  // dense: cost staging in shared memory; kernel variant by the largest degree
+  // kernel variant by the largest degree
   int dmax = 0;
   for (const ProbDesc& d : desc)
     for (int r = 0; r < d.l; ++r) dmax = std::max(dmax, std::max(d.P[r], std::max(d.G[r], d.H[r])));
@@ -112,6 +95,26 @@ int prepare(K2Plan& g, const std::vector<ProbDesc>& desc, bool lin, int sms, int
     g.nfix = (uniform && (fixed == 4 || fixed == 6) && !std::getenv("PCBA_NO_FIXED_DEGREE"))
                  ? fixed : 0;
   }
+  int occ = 0;
+  g.cfgs.clear();
+  if (lin) {
+    // linear families: one subdivision kernel (a warp per unit), no TMA staging
+    g.lin_k = desc[0].alpha;
+    g.lin_cpmax = (int)cpmax;
+    g.lin_cgmax = 1;
+    for (const ProbDesc& d : desc) g.lin_cgmax = std::max(g.lin_cgmax, d.cg);
+    const size_t wb = lin_warp_smem(g.lin_k, g.lin_cgmax, g.lin_cpmax);
+    if (wb > (size_t)smem_optin)
+      return pcba_internal_fail(PCBA_ERR_INVALID, "shared patches too large");
+    int wpb = 8;
+    while (wpb > 1 && (size_t)wpb * wb > (size_t)smem_optin) wpb /= 2;
+    const void* kl = lin_kernel(g.lin_k, g.nfix);
+    K2_CK(cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(wpb * wb)));
+    K2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kl, 32 * wpb, wpb * wb));
+    g.cfgs.push_back({false, wpb, 1, wpb * wb, std::max(1, occ) * sms});
+    return 0;
+  }
+  g.lin_k = 0;
   const size_t k2_smem = (size_t)(2 * cpmax) * sizeof(T);
   const void* k2 = direct_kernel(g.nmax);
   K2_CK(cudaFuncSetAttribute(k2, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -157,11 +160,16 @@ void launch(const K2Plan& g, int cfg, const Engine& E, cudaStream_t s) {
   const K2Cfg& c = g.cfgs[cfg];
   const dim3 blk(32 * c.wpb);
   if (g.lin_k > 0) {
+    const int cg = g.lin_cgmax, cp = g.lin_cpmax;
+    if (g.lin_k == 3 && g.nfix == 6) {
+      k2_subdivide_lin<T, 3, 6><<<c.grid, blk, c.smem, s>>>(E, cg, cp);
+      return;
+    }
     switch (g.lin_k) {
-      case 1: k2_subdivide_lin<T, 1><<<c.grid, blk, c.smem, s>>>(E, g.lin_cgmax, g.lin_cpmax); break;
-      case 2: k2_subdivide_lin<T, 2><<<c.grid, blk, c.smem, s>>>(E, g.lin_cgmax, g.lin_cpmax); break;
-      case 3: k2_subdivide_lin<T, 3><<<c.grid, blk, c.smem, s>>>(E, g.lin_cgmax, g.lin_cpmax); break;
-      default: k2_subdivide_lin<T, 4><<<c.grid, blk, c.smem, s>>>(E, g.lin_cgmax, g.lin_cpmax); break;
+      case 1: k2_subdivide_lin<T, 1, 0><<<c.grid, blk, c.smem, s>>>(E, cg, cp); break;
+      case 2: k2_subdivide_lin<T, 2, 0><<<c.grid, blk, c.smem, s>>>(E, cg, cp); break;
+      case 3: k2_subdivide_lin<T, 3, 0><<<c.grid, blk, c.smem, s>>>(E, cg, cp); break;
+      default: k2_subdivide_lin<T, 4, 0><<<c.grid, blk, c.smem, s>>>(E, cg, cp); break;
     }
     return;
   }

@@ -594,14 +594,21 @@ __device__ void plan_next(const Engine& E, unsigned* sscan) {
     const int p = base + threadIdx.x;
     unsigned a2 = 0, a3 = 0, a4 = 0, ar = 0;
     if (p < E.np) {
-      const ProbState* S = E.state + p;
+      ProbState* S = E.state + p;
       const ProbDesc* D = E.desc + p;
       const int st = *(volatile const int*)&S->status;
       const int K = *(volatile const int*)&S->K;
       const int F = *(volatile const int*)&S->F;
       const int steps = *(volatile const int*)&S->steps;
       if (st == PCBA_RUNNING) {
-        a2 = (unsigned)K * (unsigned)D->tiles;
+        // linear families: chunk units while the list is short (most
+        // constraints still active), one unit per item after that
+        int tl = D->tiles;
+        if (D->lin) {
+          tl = (long long)K * D->lin_chunks <= E.params->lin_split ? D->lin_chunks : 1;
+          S->lin_tiles = tl;
+        }
+        a2 = (unsigned)K * (unsigned)tl;
         a3 = (unsigned)((2 * K + PCBA_TPB - 1) / PCBA_TPB);
         (void)steps;
       }
@@ -797,6 +804,7 @@ __device__ __forceinline__ void control_phase(const Engine& E, cudaGraphConditio
     pl->k3_tiles = pl->k3_tiles_next;
     // the refresh of this iteration consumed this step's list
     pl->marks_total += min(pl->mark_count[pl->steps_global & 1], E.mark_cap);
+    pl->lin_next = 0u;
     pl->mark_count[pl->steps_global & 1] = 0u;
     if (did) pl->steps_global += 1;
     const int running = pl->any_running;
@@ -903,6 +911,10 @@ __global__ void k_init(Engine E) {
       if (D->lin && E.precision == 32)
         for (int q = 0; q < D->apad; ++q)
           ((double*)(E.arena + D->list_off + D->off_eg + 4LL * D->apad))[q] = 0.0;
+      S->lin_tiles = D->tiles;
+      if (D->lin)
+        *(unsigned long long*)(E.arena + D->list_off + D->off_sum) =
+            D->lin_chunks >= 64 ? ~0ull : ((1ull << D->lin_chunks) - 1ull);
       unsigned* mw = (unsigned*)(E.arena + D->list_off + D->off_mask);
       for (int q = 0; q < D->mwords; ++q) {
         const int rem = D->nlin - 32 * q;
@@ -943,6 +955,9 @@ __global__ void k_init(Engine E) {
     pl->mark_count[1] = 0u;
     pl->marks_total = 0ull;
     pl->refreshed_total = 0ull;
+    pl->lin_pairs = 0ull;
+    pl->lin_full = 0ull;
+    pl->lin_next = 0u;
     E.kr_pre[E.np] = 0;
     pl->k3_done = 0;
     pl->k4_done = 0u;

@@ -101,27 +101,70 @@ __device__ __forceinline__ double lin_wmin(double v) {
 
 // Coefficient range of c + sum_m w_m s_mj over the C coefficients of one
 // child (coefficient-major, 4 slots per coefficient).
+// (Two partial extremes per bound, for independent dependency chains.)
+template <typename T, int K>
+__device__ __forceinline__ T lin_coef(const T* s, T c, const T (&w)[K]) {
+  T v = c;
+#pragma unroll
+  for (int m = 0; m < K; ++m) v = fma(w[m], s[m], v);
+  return v;
+}
 template <typename T, int K>
 __device__ __forceinline__ void lin_full_range(const T* sc, int C, T c, const T (&w)[K], T& lo,
                                                T& hi) {
-  lo = T(INFINITY);
-  hi = T(-INFINITY);
-#pragma unroll 4
-  for (int j = 0; j < C; ++j) {
-    const T* s = sc + (size_t)j * 4;
-    T v = c;
-#pragma unroll
-    for (int m = 0; m < K; ++m) v = fma(w[m], s[m], v);
-    lo = min(lo, v);
-    hi = max(hi, v);
+  T lo0 = T(INFINITY), hi0 = T(-INFINITY), lo1 = T(INFINITY), hi1 = T(-INFINITY);
+  int j = 0;
+#pragma unroll 2
+  for (; j + 1 < C; j += 2) {
+    const T v0 = lin_coef<T, K>(sc + (size_t)j * 4, c, w);
+    const T v1 = lin_coef<T, K>(sc + (size_t)(j + 1) * 4, c, w);
+    lo0 = min(lo0, v0);
+    hi0 = max(hi0, v0);
+    lo1 = min(lo1, v1);
+    hi1 = max(hi1, v1);
   }
+  if (j < C) {
+    const T v0 = lin_coef<T, K>(sc + (size_t)j * 4, c, w);
+    lo0 = min(lo0, v0);
+    hi0 = max(hi0, v0);
+  }
+  lo = min(lo0, lo1);
+  hi = max(hi0, hi1);
+}
+// Both children at once (the same constraint on the two halves of a box).
+template <typename T, int K>
+__device__ __forceinline__ void lin_full_range2(const T* sl, const T* sr, int C, T c,
+                                                const T (&w)[K], T& loL, T& hiL, T& loR,
+                                                T& hiR) {
+  T a0 = T(INFINITY), b0 = T(-INFINITY), a1 = T(INFINITY), b1 = T(-INFINITY);
+#pragma unroll 2
+  for (int j = 0; j < C; ++j) {
+    const T v0 = lin_coef<T, K>(sl + (size_t)j * 4, c, w);
+    const T v1 = lin_coef<T, K>(sr + (size_t)j * 4, c, w);
+    a0 = min(a0, v0);
+    b0 = max(b0, v0);
+    a1 = min(a1, v1);
+    b1 = max(b1, v1);
+  }
+  loL = a0;
+  hiL = b0;
+  loR = a1;
+  hiR = b1;
 }
 
-template <typename T, int K>
-__global__ void __launch_bounds__(256) k2_subdivide_lin(Engine E, int cgmax, int cpmax) {
+// NFIX > 0: every patch of the batch has degree NFIX along every axis (a
+// smaller kernel body); 0: any degree up to 16.
+//
+// Work units per item (ProbState::lin_tiles, set when the step is planned):
+// while a problem's list is short its items are split into one unit per chunk
+// of PCBA_LIN_WORDS activity words (near the root most constraints are still
+// active); later one unit takes the whole item and skips the chunks whose
+// summary bit is clear without reading them.
+template <typename T, int K, int NFIX>
+__global__ void __launch_bounds__(256, 3) k2_subdivide_lin(Engine E, int cgmax, int cpmax) {
   constexpr bool RIG = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char kls[];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   unsigned char* wb = kls + (size_t)warp * lin_warp_bytes<T, K>(cgmax, cpmax);
   T* sP = (T*)wb;                                   // parent patches [K][C]
   T* sC = sP + (size_t)K * cgmax;                   // children [2][C][4]
@@ -131,15 +174,21 @@ __global__ void __launch_bounds__(256) k2_subdivide_lin(Engine E, int cgmax, int
   const unsigned units = E.plan->k2_units;
   const int par = E.plan->steps_global & 1;  // copy read this step; children go to par ^ 1
   const double cost_thr = E.params->opt_tol * (1.0 / 64.0);
-  const unsigned per = (units + gridDim.x - 1) / gridDim.x;
-  const unsigned u0 = blockIdx.x * per;
-  const unsigned u1 = min(units, u0 + per);
   constexpr float u24 = 0x1p-24f;
   // per-problem context, reloaded when the unit's problem changes
-  int cx_p = -1, cx_K = 0, cx_r = 0, cx_ftop = 0, cx_hw = 0, cx_chunks = 1;
+  int cx_p = -1, cx_K = 0, cx_r = 0, cx_ftop = 0, cx_hw = 0, cx_chunks = 1, cx_tiles = 1;
   unsigned cx_beg = 0, cx_end = 0;
   const ProbDesc* D = nullptr;
-  for (unsigned u = u0 + warp; u < u1; u += wpb) {
+  // units are fetched in batches from a counter (reset before every step), so
+  // that the few heavy units - items with many active constraints - spread
+  // over the whole GPU instead of lengthening one block's range
+  for (;;) {
+  unsigned ubeg = 0;
+  if (lane == 0) ubeg = atomicAdd(&E.plan->lin_next, (unsigned)PCBA_LIN_BATCH);
+  ubeg = __shfl_sync(0xffffffffu, ubeg, 0);
+  if (ubeg >= units) break;
+  const unsigned uend = min(units, ubeg + (unsigned)PCBA_LIN_BATCH);
+  for (unsigned u = ubeg; u < uend; ++u) {
     if (u < cx_beg || u >= cx_end || cx_p < 0) {
       cx_p = find_problem(E.k2_pre, E.np, u);
       cx_beg = E.k2_pre[cx_p];
@@ -151,11 +200,14 @@ __global__ void __launch_bounds__(256) k2_subdivide_lin(Engine E, int cgmax, int
       cx_ftop = S->ftop;
       cx_hw = S->hw;
       cx_chunks = D->lin_chunks;
+      cx_tiles = S->lin_tiles;
     }
-    const int p = cx_p, Kl = cx_K, r = cx_r;
+    const int p = cx_p, Kl = cx_K, r = cx_r, chunks = cx_chunks, tiles = cx_tiles;
     const unsigned local = u - cx_beg;
-    const int k = (int)(local / (unsigned)cx_chunks);
-    const int t = (int)(local - (unsigned)k * cx_chunks);
+    const int k = (int)(local / (unsigned)tiles);
+    const int t = (int)(local - (unsigned)k * tiles);
+    // the chunks of this unit
+    const int c_beg = tiles == 1 ? 0 : t, c_end = tiles == 1 ? chunks : t + 1;
     const long long slot_off = D->slot_off;
     const unsigned pslot = E.map[slot_off + k];
     const unsigned rslot = right_slot(E, slot_off, k, cx_ftop, cx_hw);
@@ -164,14 +216,66 @@ __global__ void __launch_bounds__(256) k2_subdivide_lin(Engine E, int cgmax, int
     char* right = list + (size_t)rslot * D->item_bytes;
     ChildRec* recL = E.rec + slot_off + k;
     ChildRec* recR = E.rec + slot_off + k + Kl;
-    const int C = D->cg, apad = D->apad, l = D->l;
+    const int C = D->cg, apad = D->apad, l = D->l, mwords = D->mwords;
     const int n = D->G[r];
     const int stride = axis_stride(D->G, l, r);
     const int nf = C / (n + 1);
     const int blk = (n + 1) * stride;
     const MarkCtx mk{p, k, k + Kl, E.marks + (size_t)par * E.mark_cap, &E.plan->mark_count[par],
                      E.mark_cap};
-
+    unsigned* pmask = (unsigned*)(parent + D->off_mask);
+    unsigned* rmask = (unsigned*)(right + D->off_mask);
+    // summaries: bit c of the parent's says whether chunk c has an active
+    // constraint; the children's are written to the other word (kept only
+    // for up to 64 chunks; beyond that every chunk is read)
+    const bool summ = chunks <= 64;
+    unsigned long long* sumL = (unsigned long long*)(parent + D->off_sum) + (par ^ 1);
+    unsigned long long* sumR = (unsigned long long*)(right + D->off_sum) + (par ^ 1);
+    const unsigned long long range =
+        summ ? ((c_end >= 64 ? ~0ull : ((1ull << c_end) - 1ull)) & ~((1ull << c_beg) - 1ull)) : 0ull;
+    const unsigned long long psum =
+        summ ? *((const unsigned long long*)(parent + D->off_sum) + par) : ~0ull;
+    const unsigned long long live = summ ? (psum & range) : ~0ull;
+    // the unit holding chunk 0 writes the children's shared patches whenever
+    // any chunk of the item is live
+    const bool need_shared = c_beg == 0 ? psum != 0ull : live != 0ull;
+    // chunk 0 splits the cost patch and the box, and updates the slot map
+    auto split_cost_and_box = [&]() {
+      cost_part<T, 16, NFIX>(cost_geom(D, r), parent, parent, right, recL, recR, cstage, mk,
+                             cost_thr);
+      if (lane == 0) {
+        E.map[slot_off + k + Kl] = rslot;
+        unsigned* iL = (unsigned*)parent;
+        unsigned* iR = (unsigned*)right;
+        for (int s = 0; s < l; ++s) iR[s] = iL[s];
+        const unsigned v = iL[r];
+        iL[r] = 2u * v;
+        iR[r] = 2u * v + 1u;
+      }
+    };
+    // the children's words of a chunk with no active constraint: zero (the
+    // left child shares the parent's, already zero)
+    auto clear_right = [&](int c0, int c1) {
+      const int wb0 = c0 * PCBA_LIN_WORDS, wb1 = min(c1 * PCBA_LIN_WORDS, mwords);
+      for (int q = wb0 + lane; q < wb1; q += 32) rmask[q] = 0u;
+    };
+    if (!need_shared) {
+      // no active constraint in this unit's chunks (nor, for chunk 0, in the
+      // item): the shared patches are not needed any more
+      clear_right(c_beg, c_end);
+      if (lane == 0 && summ) {
+        if (tiles == 1) {
+          *sumL = 0ull;
+          *sumR = 0ull;
+        } else {
+          atomicAnd(sumL, ~range);
+          atomicAnd(sumR, ~range);
+        }
+      }
+      if (c_beg == 0) split_cost_and_box();
+      __syncwarp();
+      continue;
+    }
     // ---- the parent's shared patches into shared memory
     const T* gsrc = (const T*)(parent + D->off_g + par * D->copy_g);
     const char* pmeta = parent + D->off_eg + par * D->copy_e;  // FP32: errors, then offsets
@@ -205,7 +309,7 @@ __global__ void __launch_bounds__(256) k2_subdivide_lin(Engine E, int cgmax, int
       const int fi = f - m * nf;
       const int o = fi / stride;
       const int base = o * blk + (fi - o * stride);
-      dispatch_degree<16>(n, [&](auto nc) {
+      dispatch_fixed<16, NFIX>(n, [&](auto nc) {
         lin_fibre<T, decltype(nc)::value>(sP + (size_t)m * C, sL, sR, base, stride, m);
       });
     }
@@ -242,7 +346,7 @@ __global__ void __launch_bounds__(256) k2_subdivide_lin(Engine E, int cgmax, int
       }
     }
     // ---- chunk 0: the children's shared patches, the cost patch, box and map
-    if (t == 0) {
+    if (c_beg == 0) {
       T* dL = (T*)(parent + D->off_g + (par ^ 1) * D->copy_g);
       T* dR = (T*)(right + D->off_g + (par ^ 1) * D->copy_g);
       if constexpr (RIG) {
@@ -296,130 +400,173 @@ __global__ void __launch_bounds__(256) k2_subdivide_lin(Engine E, int cgmax, int
           dR[(size_t)j * apad + m] = sR[(size_t)j * 4 + m];
         }
       }
-      cost_part<T, 16>(cost_geom(D, r), parent, parent, right, recL, recR, cstage, mk, cost_thr);
-      if (lane == 0) {
-        E.map[slot_off + k + Kl] = rslot;
-        unsigned* iL = (unsigned*)parent;
-        unsigned* iR = (unsigned*)right;
-        for (int s = 0; s < l; ++s) iR[s] = iL[s];
-        const unsigned v = iL[r];
-        iL[r] = 2u * v;
-        iR[r] = 2u * v + 1u;
-      }
+      split_cost_and_box();
     }
-    // ---- the active constraints of this chunk
-    const int w0 = t * PCBA_LIN_WORDS;
-    const int nw = min(PCBA_LIN_WORDS, D->mwords - w0);
-    unsigned* pm = (unsigned*)(parent + D->off_mask) + w0;
-    unsigned* rm = (unsigned*)(right + D->off_mask) + w0;
-    const unsigned word = lane < nw ? pm[lane] : 0u;
-    const unsigned cnt = __popc(word);
-    unsigned incl = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-      if (lane >= o) incl += y;
-    }
-    const unsigned na = __shfl_sync(0xffffffffu, incl, 31);
-    {
-      unsigned pos = incl - cnt, bits = word;
-      while (bits) {
-        const int b = __ffs(bits) - 1;
-        bits &= bits - 1u;
-        sIdx[pos++] = (unsigned short)(lane * 32 + b);
-      }
-    }
-    if (lane < 2 * PCBA_LIN_WORDS) sMw[lane] = 0u;
-    __syncwarp();
     T gmax[2] = {T(-INFINITY), T(-INFINITY)}, gmin[2] = {T(-INFINITY), T(-INFINITY)};
     bool mark[2] = {false, false};
+    unsigned nfull = 0;      // coefficient-range evaluations of this lane
+    unsigned npairs = 0;     // (child, active constraint) bounds of this unit
     const int Kw = K;
-    for (unsigned q = lane; q < na; q += 32) {
-      const int li = sIdx[q];
-      const long long row = (D->lin_off + (long long)w0 * 32 + li) * PCBA_LIN_STRIDE;
-      T cc, w[K];
-      float E64 = 0.0f;  // FP32: bound of the FP64 rounding of the constant term
-      if constexpr (RIG) {
-        const float4 r0 = *(const float4*)(E.lin32 + row);
-        const float4 r1 = *(const float4*)(E.lin32 + row + 4);
-        const float rr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-#pragma unroll
-        for (int m = 0; m < K; ++m) w[m] = rr[1 + m];
-        // the constant term c_i + sum_m w_im O_m of the coefficients relative
-        // to the parent's offsets, in FP64 from the FP64 row: the large terms
-        // cancel here, exactly enough, and the FP32 part only carries the
-        // residuals (of the order of the box's range)
-        const double* rw = E.lin64 + row;
-        double kap = rw[0], a64 = fabs(rw[0]);
-#pragma unroll
-        for (int m = 0; m < K; ++m) {
-          kap = fma(rw[1 + m], Om[m], kap);
-          a64 = fma(fabs(rw[1 + m]), fabs(Om[m]), a64);
-        }
-        cc = (float)kap;
-        E64 = __double2float_ru(__dmul_ru(a64, 0x1p-50));
-      } else {
-        const double* rw = E.lin64 + row;
-        cc = rw[0];
-#pragma unroll
-        for (int m = 0; m < K; ++m) w[m] = rw[1 + m];
+    unsigned long long bitsL = 0ull, bitsR = 0ull;  // children's non-empty chunks here
+    for (int cc = c_beg; cc < c_end; ++cc) {
+      if (summ && !((live >> cc) & 1ull)) {
+        clear_right(cc, cc + 1);
+        continue;
       }
+      // ---- the active constraints of chunk cc, compacted
+      const int w0 = cc * PCBA_LIN_WORDS;
+      const int nw = min(PCBA_LIN_WORDS, mwords - w0);
+      unsigned* pm = pmask + w0;
+      unsigned* rm = rmask + w0;
+      __syncwarp();  // the previous chunk's readers of sIdx and sMw are done
+      const unsigned word = lane < nw ? pm[lane] : 0u;
+      const unsigned cnt = __popc(word);
+      unsigned incl = cnt;
 #pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        // E of the comment at the top of this file (0 in FP64 mode)
-        float Eb = 0.0f, Ee = 0.0f, Er = 0.0f;
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += y;
+      }
+      const unsigned na = __shfl_sync(0xffffffffu, incl, 31);
+      if (na == 0) {
+        if (lane < nw) rm[lane] = 0u;
+        continue;
+      }
+      {
+        unsigned pos = incl - cnt, bits = word;
+        while (bits) {
+          const int b = __ffs(bits) - 1;
+          bits &= bits - 1u;
+          sIdx[pos++] = (unsigned short)(lane * 32 + b);
+        }
+      }
+      if (lane < 2 * PCBA_LIN_WORDS) sMw[lane] = 0u;
+      __syncwarp();
+      npairs += 2u * na;
+      for (unsigned q = lane; q < na; q += 32) {
+        const int li = sIdx[q];
+        const long long row = (D->lin_off + (long long)w0 * 32 + li) * PCBA_LIN_STRIDE;
+        T cc, w[K];
+        float E64 = 0.0f;  // FP32: bound of the FP64 rounding of the constant term
         if constexpr (RIG) {
-          float A = fabsf((float)cc);
-#pragma unroll
+          const float4 r0 = *(const float4*)(E.lin32 + row);
+          const float4 r1 = *(const float4*)(E.lin32 + row + 4);
+          const float rr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+  #pragma unroll
+          for (int m = 0; m < K; ++m) w[m] = rr[1 + m];
+          // the constant term c_i + sum_m w_im O_m of the coefficients relative
+          // to the parent's offsets, in FP64 from the FP64 row: the large terms
+          // cancel here, exactly enough, and the FP32 part only carries the
+          // residuals (of the order of the box's range)
+          const double* rw = E.lin64 + row;
+          double kap = rw[0], a64 = fabs(rw[0]);
+  #pragma unroll
           for (int m = 0; m < K; ++m) {
-            A = __fmaf_ru(fabsf((float)w[m]), Mabs[c][m], A);
-            Ee = __fmaf_ru(fabsf((float)w[m]), ec[m], Ee);
+            kap = fma(rw[1 + m], Om[m], kap);
+            a64 = fma(fabs(rw[1 + m]), fabs(Om[m]), a64);
           }
-          const float kk = (float)(2 * Kw + 2);
-          Er = __fmul_ru((kk + 1.0f) * u24, A);
-          Eb = __fadd_ru(__fadd_ru(__fadd_ru(Er, __fmul_ru(Ee, 1.0f + 0x1p-20f)), E64),
-                         kk * 0x1p-149f);
+          cc = (float)kap;
+          E64 = __double2float_ru(__dmul_ru(a64, 0x1p-50));
+        } else {
+          const double* rw = E.lin64 + row;
+          cc = rw[0];
+  #pragma unroll
+          for (int m = 0; m < K; ++m) w[m] = rw[1 + m];
         }
-        // interval bound from the ranges of the shared patches
-        T lo = cc, hi = cc;
-#pragma unroll
-        for (int m = 0; m < K; ++m) {
-          const T a = w[m] * mn[c][m], b = w[m] * mx[c][m];
-          lo += min(a, b);
-          hi += max(a, b);
+        // E of the comment at the top of this file (0 in FP64 mode), and the
+        // interval bound from the ranges of the shared patches, per child
+        float Ee[2] = {0.0f, 0.0f}, Er[2] = {0.0f, 0.0f};
+        T lo[2], hi[2], Et[2];
+  #pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          float Eb = 0.0f;
+          if constexpr (RIG) {
+            float A = fabsf((float)cc), ee = 0.0f;
+  #pragma unroll
+            for (int m = 0; m < K; ++m) {
+              A = __fmaf_ru(fabsf((float)w[m]), Mabs[c][m], A);
+              ee = __fmaf_ru(fabsf((float)w[m]), ec[m], ee);
+            }
+            const float kk = (float)(2 * Kw + 2);
+            Er[c] = __fmul_ru((kk + 1.0f) * u24, A);
+            Ee[c] = ee;
+            Eb = __fadd_ru(__fadd_ru(__fadd_ru(Er[c], __fmul_ru(ee, 1.0f + 0x1p-20f)), E64),
+                           kk * 0x1p-149f);
+          }
+          Et[c] = T(Eb);
+          T a = cc, b = cc;
+  #pragma unroll
+          for (int m = 0; m < K; ++m) {
+            const T x = w[m] * mn[c][m], y = w[m] * mx[c][m];
+            a += min(x, y);
+            b += max(x, y);
+          }
+          lo[c] = a;
+          hi[c] = b;
         }
-        const T Et = T(Eb);
-        T up = add_up(hi, Et), dn = sub_dn(lo, Et);
-        bool sat = up <= T(0);
-        bool inf = dn > T(0);
-        if (!sat && !inf) {
-          // undecided: the coefficient range itself (Alg. 3)
-          lin_full_range<T, K>(c ? sR : sL, C, cc, w, lo, hi);
-          up = add_up(hi, Et);
-          dn = sub_dn(lo, Et);
-          sat = up <= T(0);
-          inf = dn > T(0);
+        // undecided by the interval: the coefficient range itself (Alg. 3)
+        const bool needL = !(add_up(hi[0], Et[0]) <= T(0)) && !(sub_dn(lo[0], Et[0]) > T(0));
+        const bool needR = !(add_up(hi[1], Et[1]) <= T(0)) && !(sub_dn(lo[1], Et[1]) > T(0));
+        if (needL && needR) {
+          lin_full_range2<T, K>(sL, sR, C, cc, w, lo[0], hi[0], lo[1], hi[1]);
+          nfull += 2;
+        } else if (needL) {
+          lin_full_range<T, K>(sL, C, cc, w, lo[0], hi[0]);
+          nfull += 1;
+        } else if (needR) {
+          lin_full_range<T, K>(sR, C, cc, w, lo[1], hi[1]);
+          nfull += 1;
         }
-        if (!sat) {
-          atomicOr(&sMw[c * PCBA_LIN_WORDS + (li >> 5)], 1u << (li & 31));
-          gmax[c] = max(gmax[c], up);
-          gmin[c] = max(gmin[c], dn);
-        }
-        if constexpr (RIG) {
-          // the bound changed a decision the stored coefficients make: mark
-          // the child's shared patches for a refresh if their errors are the
-          // larger part of the bound
-          const bool flip = (hi <= T(0)) != sat || (lo > T(0)) != inf;
-          if (flip && Ee > Er) mark[c] = true;
+  #pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          const T up = add_up(hi[c], Et[c]), dn = sub_dn(lo[c], Et[c]);
+          const bool sat = up <= T(0);
+          const bool inf = dn > T(0);
+          if (!sat) {
+            atomicOr(&sMw[c * PCBA_LIN_WORDS + (li >> 5)], 1u << (li & 31));
+            gmax[c] = max(gmax[c], up);
+            gmin[c] = max(gmin[c], dn);
+          }
+          if constexpr (RIG) {
+            // the bound changed a decision the stored coefficients make: mark
+            // the child's shared patches for a refresh if their errors are the
+            // larger part of the bound
+            const bool flip = (hi[c] <= T(0)) != sat || (lo[c] > T(0)) != inf;
+            if (flip && Ee[c] > Er[c]) mark[c] = true;
+          }
         }
       }
+
+      __syncwarp();
+      if (lane < nw) {
+        pm[lane] = sMw[lane];                      // left child: in place (this unit's words)
+        rm[lane] = sMw[PCBA_LIN_WORDS + lane];     // right child
+      }
+      const bool keepL = __any_sync(0xffffffffu, lane < nw && sMw[lane] != 0u);
+      const bool keepR = __any_sync(0xffffffffu, lane < nw && sMw[PCBA_LIN_WORDS + lane] != 0u);
+      if (cc < 64) {
+        if (keepL) bitsL |= 1ull << cc;
+        if (keepR) bitsR |= 1ull << cc;
+      }
     }
-    __syncwarp();
-    if (lane < nw) {
-      pm[lane] = sMw[lane];                      // left child: in place (this unit's words)
-      rm[lane] = sMw[PCBA_LIN_WORDS + lane];     // right child
+    // ---- the children's summaries for this unit's chunks
+    if (lane == 0 && summ) {
+      if (tiles == 1) {
+        *sumL = bitsL;
+        *sumR = bitsR;
+      } else {
+        const unsigned long long tb = 1ull << t;
+        if (bitsL) atomicOr(sumL, tb); else atomicAnd(sumL, ~tb);
+        if (bitsR) atomicOr(sumR, tb); else atomicAnd(sumR, ~tb);
+      }
     }
-    if (na > 0) {
+    // ---- bound maxima of the children, counters, refresh marks
+    if (npairs > 0) {
+      const unsigned full = __reduce_add_sync(0xffffffffu, nfull);
+      if (lane == 0) {
+        atomicAdd(&E.plan->lin_pairs, (unsigned long long)npairs);
+        atomicAdd(&E.plan->lin_full, (unsigned long long)full);
+      }
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const T gx = lin_wmax(gmax[c]);
@@ -437,5 +584,6 @@ __global__ void __launch_bounds__(256) k2_subdivide_lin(Engine E, int cgmax, int
       append_marks(mk, bl && lane < K, br && lane < K, 0, lane);
     }
     __syncwarp();
+  }
   }
 }

@@ -100,6 +100,7 @@ def lib():
         "pcba_eval_points_f32": ([P, I, P, P, I, I, P, P, P], I),
         "pcba_create_linear": ([P, P, P, P, I], I),
         "pcba_get_active": ([P, P, LL], I),
+        "pcba_batch_linear_stats": ([P, P, P, P], I),
         "pcba_batch_polish": ([P, D, D, D, I, P], I),
         "pcba_batch_solve_polished": ([P, D, D, D, D, I, P], I),
         "pcba_batch_destroy": ([P], None),
@@ -152,7 +153,8 @@ def exported_symbols():
             "pcba_mlp_create", "pcba_mlp_destroy", "pcba_mlp_num_params", "pcba_mlp_set_params",
             "pcba_mlp_get_params", "pcba_mlp_forward", "pcba_mlp_gradient",
             "pcba_mlp_train_step", "pcba_set_time_limit", "pcba_batch_set_time_limit",
-            "pcba_eval_points_f32", "pcba_create_linear", "pcba_get_active"]
+            "pcba_eval_points_f32", "pcba_create_linear", "pcba_get_active",
+            "pcba_batch_linear_stats"]
 
 
 def _check(rc):
@@ -551,6 +553,13 @@ class Batch:
         m, r = ctypes.c_longlong(), ctypes.c_longlong()
         _check(lib().pcba_batch_refresh_stats(self._b, ctypes.byref(m), ctypes.byref(r)))
         return {"marked": m.value, "refreshed": r.value}
+
+    def linear_stats(self):
+        """pcba_batch_linear_stats of the last solve."""
+        a, f, c = ctypes.c_longlong(), ctypes.c_longlong(), ctypes.c_longlong()
+        _check(lib().pcba_batch_linear_stats(self._b, ctypes.byref(a), ctypes.byref(f),
+                                             ctypes.byref(c)))
+        return {"pairs": a.value, "full": f.value, "coeffs": c.value}
 
     def set_stream(self, stream_ptr: int):
         _check(lib().pcba_batch_set_stream(self._b, ctypes.c_void_p(stream_ptr)))
