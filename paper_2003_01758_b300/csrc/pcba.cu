@@ -100,11 +100,12 @@ void layout_item(const HostProblem& P, int prec, ProbDesc& d) {
   d.off_cost = off;
   off = round_up(off + P.cp * w, 128);
   d.off_eg = off;
-  // FP32 linear families: per copy the error bounds (apad floats) and the FP64
-  // offsets the shared patches are stored relative to (apad doubles)
-  d.copy_e = prec == PCBA_FP32 && P.lin ? 12LL * d.apad : 0;
-  if (prec == PCBA_FP32)
-    off = round_up(off + (P.lin ? copies * d.copy_e : d.apad * 4LL), 128);
+  // linear families: per copy the metadata of the shared patches (FP32: error
+  // bounds, the FP64 offsets the patches are stored relative to, extremes of
+  // the stored values; FP64: the extremes)
+  d.copy_e = P.lin ? (prec == PCBA_FP32 ? 20LL : 16LL) * d.apad : 0;
+  if (P.lin) off = round_up(off + copies * d.copy_e, 128);
+  else if (prec == PCBA_FP32) off = round_up(off + d.apad * 4LL, 128);
   d.off_eh = off;
   if (prec == PCBA_FP32) off = round_up(off + d.bpad * 4LL, 128);
   d.off_g = off;
@@ -857,11 +858,7 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   }
   P.np = n;
   P.time_limit_ns = b->time_limit_s > 0.0 ? (unsigned long long)(b->time_limit_s * 1e9) : 0ull;
-  {
-    // tuning knob of the linear-family kernel (units per item), for experiments
-    const char* ls = std::getenv("PCBA_LIN_SPLIT");
-    P.lin_split = ls ? std::atoi(ls) : PCBA_LIN_SPLIT;
-  }
+
   PCBA_CK(cudaEventRecord(b->ev0, s));
   b->h2d_bytes = (long long)sizeof(SolveParams) + (host_coeffs ? 8LL * b->mono_doubles : 0) +
                  (warm ? 8LL * PCBA_MAXD * n : 0) +
@@ -1552,7 +1549,7 @@ int pcba_batch_stats(const pcba_batch* b, long long* loop_iters, long long* kern
   // kernels); epilogue: k_eval
   // per iteration: subdivision, k_pup, k3_classify, k4_index, k_move_control,
   // and k_refresh in FP32
-  const long long per_it = 5 + (b->precision == PCBA_FP32 ? 1 : 0);
+  const long long per_it = 5 + (b->precision == PCBA_FP32 ? 1 : 0) + (b->lin ? 1 : 0);
   // the graph runs iterations in pairs: an odd count adds one empty iteration
   const long long it_run = (b->flags & 3) == 0 ? it + (it & 1) : it;
   if (kernel_launches) *kernel_launches = 5 + per_it * it_run + b->extra_launches + b->prior_launches;

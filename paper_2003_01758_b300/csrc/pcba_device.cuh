@@ -45,7 +45,6 @@
 #define PCBA_LIN_WORDS 8     // activity words (256 constraints) per linear subdivision unit
 #define PCBA_LIN_STRIDE 8    // floats / doubles per linear constraint row (c, w_0 .. w_K-1)
 #define PCBA_LIN_BATCH 4     // units a warp of the linear subdivision kernel fetches at once
-#define PCBA_LIN_SPLIT (1 << 30)  // default of SolveParams::lin_split (always one unit per chunk)
 
 struct ProbDesc {
   int l;
@@ -127,7 +126,6 @@ struct ProbState {
   double seed_cost;             // its certified cost bound (the initial p_up)
   double seed_x[PCBA_MAXD];     // the candidate
   float box_err;                // FP32: e_p of the returned box's cost patch (in p_up)
-  int lin_tiles;                // linear families: subdivision units per item this step
   double warm_err;              // FP64 rounding bound of the warm point's cost (in p_up)
 };
 
@@ -138,7 +136,6 @@ struct SolveParams {
   int step_guard;     // hard bound on device loop iterations
   int np;
   unsigned long long time_limit_ns;  // 0: none; else stop running problems (TIMEOUT)
-  int lin_split;      // linear families: chunk units while K * chunks <= lin_split
 };
 
 struct Plan {
@@ -151,7 +148,8 @@ struct Plan {
   unsigned long long marks_total, refreshed_total;
   unsigned long long lin_pairs;  // linear families: (child, active constraint) bounds of the solve
   unsigned long long lin_full;   // of which bounded from the coefficient range (not the interval)
-  unsigned lin_next;             // next unit of the linear subdivision kernel to hand out
+  unsigned lin_next;             // next unit of the linear bound kernel to hand out
+  unsigned lin_next2;            // next item of the linear split kernel to hand out
   unsigned k3_done;
   unsigned k4_done;             // blocks of k_move_control finished (the last one runs the control)
   int any_running;
@@ -172,7 +170,7 @@ struct Engine {
   unsigned* k3_pre;        // [np + 1]
   unsigned* k3_pre_next;   // [np + 1]
   unsigned* k4_pre;        // [np + 1]
-  unsigned* kr_pre;        // [np + 1] (unused)
+  unsigned* kr_pre;        // [np + 1] parent items per problem (linear split kernel)
   uint4* marks;            // [2][mark_cap] (problem, child slot, family, patch) of marked patches
   unsigned mark_cap;
   char* arena;

@@ -30,6 +30,8 @@ struct K2Cfg {
 struct K2Plan {
   int lin_k = 0;                     // linear families: shared patches per item (0: dense)
   int lin_cgmax = 1, lin_cpmax = 1;  // largest shared / cost patch of the batch
+  int lin_split_grid = 1;            // blocks of the linear split kernel (256 threads)
+  size_t lin_split_smem = 0;         // its dynamic shared memory
   int nmax = 16;  // degree class of the dense kernels (4, 8 or 16)
   int nfix = 0;   // every patch of the batch has this degree on every axis (4 or 6), else 0
   int tma_stage_elems = 0, tma_cpmax = 1;

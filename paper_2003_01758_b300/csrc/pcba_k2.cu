@@ -48,25 +48,25 @@ const void* direct_kernel(int nmax) {
   return (const void*)k2_subdivide<T, 16>;
 }
 
-// The linear-family subdivision kernel for K shared patches, and the shared
-// memory one of its warps uses.
-// (K = 3 with every patch of degree 6 on every axis - the obstacle
-// constraints of degree-(3,3) maps - has a fixed-degree instance.)
-const void* lin_kernel(int K, int nfix) {
-  if (K == 3 && nfix == 6) return (const void*)k2_subdivide_lin<T, 3, 6>;
+// The linear-family kernels for K shared patches: the split (a thread per
+// item) and the bound (a warp per item chunk).  K = 3 with every patch of
+// degree 6 on every axis - the obstacle constraints of degree-(3,3) maps - has
+// a fixed-degree split.
+const void* lin_split_kernel(int K, int nfix) {
+  if (K == 3 && nfix == 6) return (const void*)k2_lin_split<T, 3, 6>;
   switch (K) {
-    case 1: return (const void*)k2_subdivide_lin<T, 1, 0>;
-    case 2: return (const void*)k2_subdivide_lin<T, 2, 0>;
-    case 3: return (const void*)k2_subdivide_lin<T, 3, 0>;
-    default: return (const void*)k2_subdivide_lin<T, 4, 0>;
+    case 1: return (const void*)k2_lin_split<T, 1, 0>;
+    case 2: return (const void*)k2_lin_split<T, 2, 0>;
+    case 3: return (const void*)k2_lin_split<T, 3, 0>;
+    default: return (const void*)k2_lin_split<T, 4, 0>;
   }
 }
-size_t lin_warp_smem(int K, int cgmax, int cpmax) {
+const void* lin_bound_kernel(int K) {
   switch (K) {
-    case 1: return lin_warp_bytes<T, 1>(cgmax, cpmax);
-    case 2: return lin_warp_bytes<T, 2>(cgmax, cpmax);
-    case 3: return lin_warp_bytes<T, 3>(cgmax, cpmax);
-    default: return lin_warp_bytes<T, 4>(cgmax, cpmax);
+    case 1: return (const void*)k2_lin_bound<T, 1>;
+    case 2: return (const void*)k2_lin_bound<T, 2>;
+    case 3: return (const void*)k2_lin_bound<T, 3>;
+    default: return (const void*)k2_lin_bound<T, 4>;
   }
 }
 
@@ -98,20 +98,24 @@ int prepare(K2Plan& g, const std::vector<ProbDesc>& desc, bool lin, int sms, int
   int occ = 0;
   g.cfgs.clear();
   if (lin) {
-    // linear families: one subdivision kernel (a warp per unit), no TMA staging
+    // linear families: the split and bound kernels, no TMA staging
     g.lin_k = desc[0].alpha;
     g.lin_cpmax = (int)cpmax;
     g.lin_cgmax = 1;
     for (const ProbDesc& d : desc) g.lin_cgmax = std::max(g.lin_cgmax, d.cg);
-    const size_t wb = lin_warp_smem(g.lin_k, g.lin_cgmax, g.lin_cpmax);
-    if (wb > (size_t)smem_optin)
+    const size_t ws = lin_split_warp_bytes<T>(g.lin_cgmax, g.lin_cpmax);
+    const size_t wbnd = lin_bound_warp_bytes<T>(g.lin_cgmax);
+    if (8 * ws > (size_t)smem_optin || 8 * wbnd > (size_t)smem_optin)
       return pcba_internal_fail(PCBA_ERR_INVALID, "shared patches too large");
-    int wpb = 8;
-    while (wpb > 1 && (size_t)wpb * wb > (size_t)smem_optin) wpb /= 2;
-    const void* kl = lin_kernel(g.lin_k, g.nfix);
-    K2_CK(cudaFuncSetAttribute(kl, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(wpb * wb)));
-    K2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kl, 32 * wpb, wpb * wb));
-    g.cfgs.push_back({false, wpb, 1, wpb * wb, std::max(1, occ) * sms});
+    const void* ks = lin_split_kernel(g.lin_k, g.nfix);
+    K2_CK(cudaFuncSetAttribute(ks, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * ws)));
+    K2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, ks, 256, 8 * ws));
+    g.lin_split_grid = std::max(1, occ) * sms;
+    g.lin_split_smem = 8 * ws;
+    const void* kb = lin_bound_kernel(g.lin_k);
+    K2_CK(cudaFuncSetAttribute(kb, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8 * wbnd)));
+    K2_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kb, 256, 8 * wbnd));
+    g.cfgs.push_back({false, 8, 1, 8 * wbnd, std::max(1, occ) * sms});
     return 0;
   }
   g.lin_k = 0;
@@ -160,16 +164,24 @@ void launch(const K2Plan& g, int cfg, const Engine& E, cudaStream_t s) {
   const K2Cfg& c = g.cfgs[cfg];
   const dim3 blk(32 * c.wpb);
   if (g.lin_k > 0) {
-    const int cg = g.lin_cgmax, cp = g.lin_cpmax;
+    // the split writes the children, then the bound reads them
+    const int gs = g.lin_split_grid, cg = g.lin_cgmax, cp = g.lin_cpmax;
+    const size_t ss = g.lin_split_smem;
     if (g.lin_k == 3 && g.nfix == 6) {
-      k2_subdivide_lin<T, 3, 6><<<c.grid, blk, c.smem, s>>>(E, cg, cp);
-      return;
+      k2_lin_split<T, 3, 6><<<gs, 256, ss, s>>>(E, cg, cp);
+    } else {
+      switch (g.lin_k) {
+        case 1: k2_lin_split<T, 1, 0><<<gs, 256, ss, s>>>(E, cg, cp); break;
+        case 2: k2_lin_split<T, 2, 0><<<gs, 256, ss, s>>>(E, cg, cp); break;
+        case 3: k2_lin_split<T, 3, 0><<<gs, 256, ss, s>>>(E, cg, cp); break;
+        default: k2_lin_split<T, 4, 0><<<gs, 256, ss, s>>>(E, cg, cp); break;
+      }
     }
     switch (g.lin_k) {
-      case 1: k2_subdivide_lin<T, 1, 0><<<c.grid, blk, c.smem, s>>>(E, cg, cp); break;
-      case 2: k2_subdivide_lin<T, 2, 0><<<c.grid, blk, c.smem, s>>>(E, cg, cp); break;
-      case 3: k2_subdivide_lin<T, 3, 0><<<c.grid, blk, c.smem, s>>>(E, cg, cp); break;
-      default: k2_subdivide_lin<T, 4, 0><<<c.grid, blk, c.smem, s>>>(E, cg, cp); break;
+      case 1: k2_lin_bound<T, 1><<<c.grid, blk, c.smem, s>>>(E, cg); break;
+      case 2: k2_lin_bound<T, 2><<<c.grid, blk, c.smem, s>>>(E, cg); break;
+      case 3: k2_lin_bound<T, 3><<<c.grid, blk, c.smem, s>>>(E, cg); break;
+      default: k2_lin_bound<T, 4><<<c.grid, blk, c.smem, s>>>(E, cg); break;
     }
     return;
   }

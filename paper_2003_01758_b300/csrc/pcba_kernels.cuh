@@ -601,14 +601,8 @@ __device__ void plan_next(const Engine& E, unsigned* sscan) {
       const int F = *(volatile const int*)&S->F;
       const int steps = *(volatile const int*)&S->steps;
       if (st == PCBA_RUNNING) {
-        // linear families: chunk units while the list is short (most
-        // constraints still active), one unit per item after that
-        int tl = D->tiles;
-        if (D->lin) {
-          tl = (long long)K * D->lin_chunks <= E.params->lin_split ? D->lin_chunks : 1;
-          S->lin_tiles = tl;
-        }
-        a2 = (unsigned)K * (unsigned)tl;
+        a2 = (unsigned)K * (unsigned)D->tiles;
+        ar = (unsigned)K;  // parent items (the linear split kernel's threads)
         a3 = (unsigned)((2 * K + PCBA_TPB - 1) / PCBA_TPB);
         (void)steps;
       }
@@ -805,6 +799,7 @@ __device__ __forceinline__ void control_phase(const Engine& E, cudaGraphConditio
     // the refresh of this iteration consumed this step's list
     pl->marks_total += min(pl->mark_count[pl->steps_global & 1], E.mark_cap);
     pl->lin_next = 0u;
+    pl->lin_next2 = 0u;
     pl->mark_count[pl->steps_global & 1] = 0u;
     if (did) pl->steps_global += 1;
     const int running = pl->any_running;
@@ -869,10 +864,10 @@ __global__ void __launch_bounds__(PCBA_TPB) k_move_control(Engine E,
 
 __global__ void k_init(Engine E) {
   __shared__ unsigned sscan[8];
-  unsigned run2 = 0, run3 = 0;
+  unsigned run2 = 0, run3 = 0, runr = 0;
   for (int base = 0; base < E.np; base += PCBA_TPB) {
     const int p = base + threadIdx.x;
-    unsigned a2 = 0, a3 = 0;
+    unsigned a2 = 0, a3 = 0, ar = 0;
     if (p < E.np) {
       const ProbDesc* D = E.desc + p;
       ProbState* S = E.state + p;
@@ -911,7 +906,6 @@ __global__ void k_init(Engine E) {
       if (D->lin && E.precision == 32)
         for (int q = 0; q < D->apad; ++q)
           ((double*)(E.arena + D->list_off + D->off_eg + 4LL * D->apad))[q] = 0.0;
-      S->lin_tiles = D->tiles;
       if (D->lin)
         *(unsigned long long*)(E.arena + D->list_off + D->off_sum) =
             D->lin_chunks >= 64 ? ~0ull : ((1ull << D->lin_chunks) - 1ull);
@@ -927,19 +921,23 @@ __global__ void k_init(Engine E) {
         S->status = PCBA_RUNNING;
         a2 = (unsigned)D->tiles;
         a3 = 1u;
+        ar = 1u;
       }
     }
     unsigned t2, t3;
     const unsigned e2 = block_exclusive_scan(a2, sscan, &t2);
     const unsigned e3 = block_exclusive_scan(a3, sscan, &t3);
+    unsigned tr;
+    const unsigned er = block_exclusive_scan(ar, sscan, &tr);
     if (p < E.np) {
       E.k2_pre[p] = run2 + e2;
       E.k3_pre[p] = run3 + e3;
       E.k4_pre[p] = 0;
-      E.kr_pre[p] = 0;
+      E.kr_pre[p] = runr + er;
     }
     run2 += t2;
     run3 += t3;
+    runr += tr;
   }
   if (threadIdx.x == 0) {
     E.k2_pre[E.np] = run2;
@@ -950,7 +948,7 @@ __global__ void k_init(Engine E) {
     pl->k3_tiles = run3;
     pl->k3_tiles_next = 0;
     pl->k4_units = 0;
-    pl->kr_units = 0;
+    pl->kr_units = runr;
     pl->mark_count[0] = 0u;
     pl->mark_count[1] = 0u;
     pl->marks_total = 0ull;
@@ -958,7 +956,8 @@ __global__ void k_init(Engine E) {
     pl->lin_pairs = 0ull;
     pl->lin_full = 0ull;
     pl->lin_next = 0u;
-    E.kr_pre[E.np] = 0;
+    pl->lin_next2 = 0u;
+    E.kr_pre[E.np] = runr;
     pl->k3_done = 0;
     pl->k4_done = 0u;
     pl->any_running = run2 > 0;

@@ -35,13 +35,22 @@
 // encloses the exact coefficient range of the constraint on the box.  (FP64
 // mode stores plain patches, O_m = 0, and is plain arithmetic as the paper's.)
 //
-// Work unit = (problem, parent item, chunk of PCBA_LIN_WORDS activity words),
-// one warp each.  Every unit subdivides the K shared patches of its parent in
-// shared memory (from the copy of this step's parity); chunk 0 also writes the
-// children's patches (to the other copy), splits the cost patch and the box
-// and updates the slot map.  A unit compacts the active constraints of its
-// chunk, bounds each on both children and writes the children's activity
-// words; the bound maxima go to the child records with one atomic per warp.
+// Two kernels per bisection step:
+//   k2_lin_split   one thread per parent item: splits the cost patch and the K
+//                  shared patches (de Casteljau at 1/2, Sec. II-E) into the two
+//                  children, re-centres every FP32 child patch on the middle of
+//                  its range, and stores per child and patch the extremes of
+//                  the stored values (with their error bound and offset), the
+//                  box and the slot map; the cost bounds go to the child
+//                  records.  The children's shared patches go to the copy of
+//                  the other parity, so the parent's stay readable.
+//   k2_lin_bound   one warp per (parent item, chunk of PCBA_LIN_WORDS activity
+//                  words): compacts the chunk's active constraints and bounds
+//                  each on both children from the stored extremes (interval
+//                  bound) or, where that is undecided, from the children's
+//                  coefficients; writes the children's activity words and the
+//                  chunk's summary bits, and publishes the bound maxima with
+//                  one atomic per warp.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -49,32 +58,22 @@
 
 #include "pcba_device.cuh"
 
-// Bytes of shared memory one warp of k2_subdivide_lin uses.
-template <typename T, int K>
-__host__ __device__ constexpr size_t lin_warp_bytes(int cgmax, int cpmax) {
-  return (((size_t)K * cgmax + 8 * (size_t)cgmax + 2 * (size_t)cpmax) * sizeof(T) +
-          32 * PCBA_LIN_WORDS * sizeof(unsigned short) + 2 * PCBA_LIN_WORDS * sizeof(unsigned) +
-          15) / 16 * 16;
-}
 
-// One fibre of shared patch m: parent coefficients base + j * stride of src,
-// children written to coefficient-major [C][4] buffers at slot m.
-template <typename T, int N>
-__device__ __forceinline__ void lin_fibre(const T* src, T* dL, T* dR, int base, int stride,
-                                          int m) {
-  T q[N + 1];
-#pragma unroll
-  for (int j = 0; j <= N; ++j) q[j] = src[base + j * stride];
-  dL[(size_t)base * 4 + m] = q[0];
-  dR[(size_t)(base + N * stride) * 4 + m] = q[N];
-#pragma unroll
-  for (int k = 1; k <= N; ++k) {
-#pragma unroll
-    for (int j = 0; j <= N - k; ++j) q[j] = mulrn(addrn(q[j], q[j + 1]), T(0.5));
-    dL[(size_t)(base + k * stride) * 4 + m] = q[0];
-    dR[(size_t)(base + (N - k) * stride) * 4 + m] = q[N - k];
+// Per-patch metadata of a linear item, one block per copy (copy_e bytes apart):
+//   FP32: error bound f32[apad] | offset f64[apad] | min f32[apad] | max f32[apad]
+//   FP64: min f64[apad] | max f64[apad]
+// (min and max are those of the stored values of each shared patch).
+template <typename T>
+struct LinMeta {
+  __device__ __forceinline__ static float* err(char* m, int) { return (float*)m; }
+  __device__ __forceinline__ static double* off(char* m, int a) { return (double*)(m + 4LL * a); }
+  __device__ __forceinline__ static T* mn(char* m, int a) {
+    return sizeof(T) == 4 ? (T*)(m + 12LL * a) : (T*)m;
   }
-}
+  __device__ __forceinline__ static T* mx(char* m, int a) {
+    return sizeof(T) == 4 ? (T*)(m + 16LL * a) : (T*)(m + 8LL * a);
+  }
+};
 
 // Directed sums of the FP32 bounds; FP64 mode is plain arithmetic (E = 0).
 __device__ __forceinline__ float add_up(float a, float b) { return __fadd_ru(a, b); }
@@ -99,151 +98,268 @@ __device__ __forceinline__ double lin_wmin(double v) {
   return v;
 }
 
-// Coefficient range of c + sum_m w_m s_mj over the C coefficients of one
-// child (coefficient-major, 4 slots per coefficient).
-// (Two partial extremes per bound, for independent dependency chains.)
-template <typename T, int K>
-__device__ __forceinline__ T lin_coef(const T* s, T c, const T (&w)[K]) {
-  T v = c;
+
+// ---------------------------------------------------------------------------
+// k2_lin_split: one warp per parent item
+// ---------------------------------------------------------------------------
+
+// NP coefficients of one position of NP patches stored coefficient-major
+// (patch m at p[m]): one 16-byte (FP32) or two (FP64) loads when NP > 1.
+template <typename T, int NP>
+__device__ __forceinline__ void lin_load(const T* p, T (&v)[NP]) {
+  if constexpr (NP == 1) {
+    v[0] = p[0];
+  } else if constexpr (sizeof(T) == 4) {
+    const float4 a = *(const float4*)p;
+    const float t[4] = {a.x, a.y, a.z, a.w};
 #pragma unroll
-  for (int m = 0; m < K; ++m) v = fma(w[m], s[m], v);
-  return v;
+    for (int m = 0; m < NP; ++m) v[m] = t[m];
+  } else {
+    const double2 a = *(const double2*)p;
+    const double2 b = *(const double2*)(p + 2);
+    const double t[4] = {a.x, a.y, b.x, b.y};
+#pragma unroll
+    for (int m = 0; m < NP; ++m) v[m] = t[m];
+  }
 }
-template <typename T, int K>
-__device__ __forceinline__ void lin_full_range(const T* sc, int C, T c, const T (&w)[K], T& lo,
-                                               T& hi) {
-  T lo0 = T(INFINITY), hi0 = T(-INFINITY), lo1 = T(INFINITY), hi1 = T(-INFINITY);
-  int j = 0;
-#pragma unroll 2
-  for (; j + 1 < C; j += 2) {
-    const T v0 = lin_coef<T, K>(sc + (size_t)j * 4, c, w);
-    const T v1 = lin_coef<T, K>(sc + (size_t)(j + 1) * 4, c, w);
-    lo0 = min(lo0, v0);
-    hi0 = max(hi0, v0);
-    lo1 = min(lo1, v1);
-    hi1 = max(hi1, v1);
+template <typename T, int NP>
+__device__ __forceinline__ void lin_store(T* p, const T (&v)[NP]) {
+  if constexpr (NP == 1) {
+    p[0] = v[0];
+  } else if constexpr (sizeof(T) == 4) {
+    float t[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+    for (int m = 0; m < NP; ++m) t[m] = v[m];
+    *(float4*)p = make_float4(t[0], t[1], t[2], t[3]);
+  } else {
+    double t[4] = {0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int m = 0; m < NP; ++m) t[m] = v[m];
+    *(double2*)p = make_double2(t[0], t[1]);
+    *(double2*)(p + 2) = make_double2(t[2], t[3]);
   }
-  if (j < C) {
-    const T v0 = lin_coef<T, K>(sc + (size_t)j * 4, c, w);
-    lo0 = min(lo0, v0);
-    hi0 = max(hi0, v0);
-  }
-  lo = min(lo0, lo1);
-  hi = max(hi0, hi1);
 }
-// Both children at once (the same constraint on the two halves of a box).
-template <typename T, int K>
-__device__ __forceinline__ void lin_full_range2(const T* sl, const T* sr, int C, T c,
-                                                const T (&w)[K], T& loL, T& hiL, T& loR,
-                                                T& hiR) {
-  T a0 = T(INFINITY), b0 = T(-INFINITY), a1 = T(INFINITY), b1 = T(-INFINITY);
-#pragma unroll 2
-  for (int j = 0; j < C; ++j) {
-    const T v0 = lin_coef<T, K>(sl + (size_t)j * 4, c, w);
-    const T v1 = lin_coef<T, K>(sr + (size_t)j * 4, c, w);
-    a0 = min(a0, v0);
-    b0 = max(b0, v0);
-    a1 = min(a1, v1);
-    b1 = max(b1, v1);
+
+// One mark (problem, child slot, family, patch) for k_refresh.
+__device__ __forceinline__ void lin_mark(const Engine& E, int mpar, int p, int slot, int fam,
+                                         int ip) {
+  const unsigned q = atomicAdd(&E.plan->mark_count[mpar], 1u);
+  if (q < E.mark_cap)
+    E.marks[(size_t)mpar * E.mark_cap + q] =
+        make_uint4((unsigned)p, (unsigned)slot, (unsigned)fam, (unsigned)ip);
+}
+
+
+// Bytes of shared memory one warp of k2_lin_split uses: the parent's cost
+// patch and its two children, the parent's shared patches and their two
+// children (coefficient-major, 4 slots per coefficient).
+template <typename T>
+__host__ __device__ constexpr size_t lin_split_warp_bytes(int cgmax, int cpmax) {
+  return ((3 * (size_t)cpmax + 12 * (size_t)cgmax) * sizeof(T) + 15) / 16 * 16;
+}
+
+// Extremes of the two children of one patch group (the cost, or one shared
+// patch) and the largest |parent value|, accumulated per lane.
+template <typename T>
+struct LinAcc {
+  T mnL, mxL, mnR, mxR, am;
+  __device__ __forceinline__ void init() {
+    mnL = mnR = T(INFINITY);
+    mxL = mxR = T(-INFINITY);
+    am = T(0);
   }
-  loL = a0;
-  hiL = b0;
-  loR = a1;
-  hiR = b1;
+};
+
+// One fibre (N + 1 values at src[j * sst], children to dL / dR at the same
+// positions): the de Casteljau triangle at 1/2 (Sec. II-E) in registers.
+template <typename T, int N>
+__device__ __forceinline__ void lin_fibre(const T* src, T* dL, T* dR, int sst, LinAcc<T>& a) {
+  T q[N + 1];
+#pragma unroll
+  for (int j = 0; j <= N; ++j) {
+    q[j] = src[j * sst];
+    a.am = max(a.am, abs(q[j]));
+  }
+  dL[0] = q[0];
+  dR[N * sst] = q[N];
+  a.mnL = min(a.mnL, q[0]);
+  a.mxL = max(a.mxL, q[0]);
+  a.mnR = min(a.mnR, q[N]);
+  a.mxR = max(a.mxR, q[N]);
+#pragma unroll
+  for (int k = 1; k <= N; ++k) {
+#pragma unroll
+    for (int j = 0; j <= N - k; ++j) q[j] = mulrn(addrn(q[j], q[j + 1]), T(0.5));
+    dL[k * sst] = q[0];
+    dR[(N - k) * sst] = q[N - k];
+    a.mnL = min(a.mnL, q[0]);
+    a.mxL = max(a.mxL, q[0]);
+    a.mnR = min(a.mnR, q[N - k]);
+    a.mxR = max(a.mxR, q[N - k]);
+  }
 }
 
 // NFIX > 0: every patch of the batch has degree NFIX along every axis (a
 // smaller kernel body); 0: any degree up to 16.
-//
-// Work units per item (ProbState::lin_tiles, set when the step is planned):
-// while a problem's list is short its items are split into one unit per chunk
-// of PCBA_LIN_WORDS activity words (near the root most constraints are still
-// active); later one unit takes the whole item and skips the chunks whose
-// summary bit is clear without reading them.
 template <typename T, int K, int NFIX>
-__global__ void __launch_bounds__(256, 3) k2_subdivide_lin(Engine E, int cgmax, int cpmax) {
+__global__ void __launch_bounds__(256, 3) k2_lin_split(Engine E, int cgmax, int cpmax) {
   constexpr bool RIG = sizeof(T) == 4;
+  constexpr float u24 = 0x1p-24f;
   extern __shared__ __align__(16) unsigned char kls[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  unsigned char* wb = kls + (size_t)warp * lin_warp_bytes<T, K>(cgmax, cpmax);
-  T* sP = (T*)wb;                                   // parent patches [K][C]
-  T* sC = sP + (size_t)K * cgmax;                   // children [2][C][4]
-  T* cstage = sC + (size_t)8 * cgmax;               // cost staging [2][cp]
-  unsigned short* sIdx = (unsigned short*)(cstage + (size_t)2 * cpmax);
-  unsigned* sMw = (unsigned*)(sIdx + 32 * PCBA_LIN_WORDS);  // child words [2][LIN_WORDS]
-  const unsigned units = E.plan->k2_units;
+  T* sc = (T*)(kls + (size_t)warp * lin_split_warp_bytes<T>(cgmax, cpmax));  // parent cost
+  T* scL = sc + cpmax;
+  T* scR = scL + cpmax;
+  T* sp = scR + cpmax;             // parent shared patches [C][4]
+  T* spL = sp + 4 * (size_t)cgmax;
+  T* spR = spL + 4 * (size_t)cgmax;
+  const unsigned items = E.plan->kr_units;
   const int par = E.plan->steps_global & 1;  // copy read this step; children go to par ^ 1
   const double cost_thr = E.params->opt_tol * (1.0 / 64.0);
-  constexpr float u24 = 0x1p-24f;
-  // per-problem context, reloaded when the unit's problem changes
-  int cx_p = -1, cx_K = 0, cx_r = 0, cx_ftop = 0, cx_hw = 0, cx_chunks = 1, cx_tiles = 1;
+  int cx_p = -1, cx_K = 0, cx_r = 0, cx_ftop = 0, cx_hw = 0;
   unsigned cx_beg = 0, cx_end = 0;
   const ProbDesc* D = nullptr;
-  // units are fetched in batches from a counter (reset before every step), so
-  // that the few heavy units - items with many active constraints - spread
-  // over the whole GPU instead of lengthening one block's range
+  // items are fetched in batches from a counter (reset before every step)
   for (;;) {
-  unsigned ubeg = 0;
-  if (lane == 0) ubeg = atomicAdd(&E.plan->lin_next, (unsigned)PCBA_LIN_BATCH);
-  ubeg = __shfl_sync(0xffffffffu, ubeg, 0);
-  if (ubeg >= units) break;
-  const unsigned uend = min(units, ubeg + (unsigned)PCBA_LIN_BATCH);
-  for (unsigned u = ubeg; u < uend; ++u) {
-    if (u < cx_beg || u >= cx_end || cx_p < 0) {
-      cx_p = find_problem(E.k2_pre, E.np, u);
-      cx_beg = E.k2_pre[cx_p];
-      cx_end = E.k2_pre[cx_p + 1];
-      D = E.desc + cx_p;
-      const ProbState* S = E.state + cx_p;
-      cx_K = S->K;
-      cx_r = S->r;
-      cx_ftop = S->ftop;
-      cx_hw = S->hw;
-      cx_chunks = D->lin_chunks;
-      cx_tiles = S->lin_tiles;
-    }
-    const int p = cx_p, Kl = cx_K, r = cx_r, chunks = cx_chunks, tiles = cx_tiles;
-    const unsigned local = u - cx_beg;
-    const int k = (int)(local / (unsigned)tiles);
-    const int t = (int)(local - (unsigned)k * tiles);
-    // the chunks of this unit
-    const int c_beg = tiles == 1 ? 0 : t, c_end = tiles == 1 ? chunks : t + 1;
-    const long long slot_off = D->slot_off;
-    const unsigned pslot = E.map[slot_off + k];
-    const unsigned rslot = right_slot(E, slot_off, k, cx_ftop, cx_hw);
-    char* list = E.arena + D->list_off;
-    char* parent = list + (size_t)pslot * D->item_bytes;
-    char* right = list + (size_t)rslot * D->item_bytes;
-    ChildRec* recL = E.rec + slot_off + k;
-    ChildRec* recR = E.rec + slot_off + k + Kl;
-    const int C = D->cg, apad = D->apad, l = D->l, mwords = D->mwords;
-    const int n = D->G[r];
-    const int stride = axis_stride(D->G, l, r);
-    const int nf = C / (n + 1);
-    const int blk = (n + 1) * stride;
-    const MarkCtx mk{p, k, k + Kl, E.marks + (size_t)par * E.mark_cap, &E.plan->mark_count[par],
-                     E.mark_cap};
-    unsigned* pmask = (unsigned*)(parent + D->off_mask);
-    unsigned* rmask = (unsigned*)(right + D->off_mask);
-    // summaries: bit c of the parent's says whether chunk c has an active
-    // constraint; the children's are written to the other word (kept only
-    // for up to 64 chunks; beyond that every chunk is read)
-    const bool summ = chunks <= 64;
-    unsigned long long* sumL = (unsigned long long*)(parent + D->off_sum) + (par ^ 1);
-    unsigned long long* sumR = (unsigned long long*)(right + D->off_sum) + (par ^ 1);
-    const unsigned long long range =
-        summ ? ((c_end >= 64 ? ~0ull : ((1ull << c_end) - 1ull)) & ~((1ull << c_beg) - 1ull)) : 0ull;
-    const unsigned long long psum =
-        summ ? *((const unsigned long long*)(parent + D->off_sum) + par) : ~0ull;
-    const unsigned long long live = summ ? (psum & range) : ~0ull;
-    // the unit holding chunk 0 writes the children's shared patches whenever
-    // any chunk of the item is live
-    const bool need_shared = c_beg == 0 ? psum != 0ull : live != 0ull;
-    // chunk 0 splits the cost patch and the box, and updates the slot map
-    auto split_cost_and_box = [&]() {
-      cost_part<T, 16, NFIX>(cost_geom(D, r), parent, parent, right, recL, recR, cstage, mk,
-                             cost_thr);
+    unsigned ubeg = 0;
+    if (lane == 0) ubeg = atomicAdd(&E.plan->lin_next2, (unsigned)PCBA_LIN_BATCH);
+    ubeg = __shfl_sync(0xffffffffu, ubeg, 0);
+    if (ubeg >= items) break;
+    const unsigned uend = min(items, ubeg + (unsigned)PCBA_LIN_BATCH);
+    for (unsigned u = ubeg; u < uend; ++u) {
+      if (u < cx_beg || u >= cx_end || cx_p < 0) {
+        cx_p = find_problem(E.kr_pre, E.np, u);
+        cx_beg = E.kr_pre[cx_p];
+        cx_end = E.kr_pre[cx_p + 1];
+        D = E.desc + cx_p;
+        const ProbState* S = E.state + cx_p;
+        cx_K = S->K;
+        cx_r = S->r;
+        cx_ftop = S->ftop;
+        cx_hw = S->hw;
+      }
+      const int p = cx_p, Kl = cx_K, r = cx_r, k = (int)(u - cx_beg);
+      const long long slot_off = D->slot_off;
+      const unsigned pslot = E.map[slot_off + k];
+      const unsigned rslot = right_slot(E, slot_off, k, cx_ftop, cx_hw);
+      char* list = E.arena + D->list_off;
+      char* parent = list + (size_t)pslot * D->item_bytes;
+      char* right = list + (size_t)rslot * D->item_bytes;
+      ChildRec* recL = E.rec + slot_off + k;
+      ChildRec* recR = E.rec + slot_off + k + Kl;
+      const int l = D->l, cp = D->cp, C = D->cg;
+      // shared patches only while a constraint is active in the item
+      const bool any = D->lin_chunks > 64 ||
+                       *((const unsigned long long*)(parent + D->off_sum) + par) != 0ull;
+      // ---- stage the parent (coalesced)
+      T* pc = (T*)(parent + D->off_cost);
+      T* rc = (T*)(right + D->off_cost);
+      for (int j = lane; j < cp; j += 32) sc[j] = pc[j];
+      const T* gs = (const T*)(parent + D->off_g + par * D->copy_g);
+      if (any)
+        for (int e = lane; e < 4 * C; e += 32) sp[e] = gs[e];
+      char* pm = parent + D->off_eg + par * D->copy_e;
+      double Oc = 0.0, Om[K];
+      float ecost = 0.0f, em[K];
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        Om[m] = 0.0;
+        em[m] = 0.0f;
+      }
+      if constexpr (RIG) {
+        Oc = *(const double*)(parent + 32);
+        ecost = *(const float*)(parent + 40);
+        if (any) {
+#pragma unroll
+          for (int m = 0; m < K; ++m) {
+            em[m] = fabsf(LinMeta<T>::err(pm, 4)[m]);
+            Om[m] = LinMeta<T>::off(pm, 4)[m];
+          }
+        }
+      }
+      __syncwarp();
+      // ---- every fibre of the cost patch and of the shared patches, a lane each
+      const int nc = D->P[r], stc = axis_stride(D->P, l, r), nfc = cp / (nc + 1);
+      const int blkc = (nc + 1) * stc;
+      const int ns = D->G[r], sts = axis_stride(D->G, l, r), nfs = C / (ns + 1);
+      const int blks = (ns + 1) * sts;
+      const int ntask = nfc + (any ? K * nfs : 0);
+      LinAcc<T> acc[K + 1];
+#pragma unroll
+      for (int g = 0; g <= K; ++g) acc[g].init();
+      for (int task = lane; task < ntask; task += 32) {
+        if (task < nfc) {
+          const int o = task / stc;
+          const int base = o * blkc + (task - o * stc);
+          dispatch_fixed<16, NFIX>(nc, [&](auto c) {
+            lin_fibre<T, decltype(c)::value>(sc + base, scL + base, scR + base, stc, acc[0]);
+          });
+        } else {
+          const int t2 = task - nfc;
+          const int m = t2 / nfs;
+          const int f = t2 - m * nfs;
+          const int o = f / sts;
+          const int base = (o * blks + (f - o * sts)) * 4;
+          dispatch_fixed<16, NFIX>(ns, [&](auto c) {
+#pragma unroll
+            for (int g = 0; g < K; ++g)
+              if (g == m)
+                lin_fibre<T, decltype(c)::value>(sp + base + g, spL + base + g, spR + base + g,
+                                                 4 * sts, acc[1 + g]);
+          });
+        }
+      }
+      // ---- extremes per patch group, over the warp
+#pragma unroll
+      for (int g = 0; g <= K; ++g) {
+        acc[g].mnL = lin_wmin(acc[g].mnL);
+        acc[g].mxL = lin_wmax(acc[g].mxL);
+        acc[g].mnR = lin_wmin(acc[g].mnR);
+        acc[g].mxR = lin_wmax(acc[g].mxR);
+        acc[g].am = lin_wmax(acc[g].am);
+      }
+      __syncwarp();
+      // ---- cost children: re-centred on the middle of each child's range
+      // (FP32), error bound grown by n (max |parent| 2^-24 + 2^-149) for the
+      // triangle and by max |stored| 2^-24 + 2^-149 + |O'| 2^-52 for the
+      // re-centring; the bounds go to the child records
+      T shc[2] = {T(0), T(0)};
+      if constexpr (RIG) {
+        shc[0] = __fmul_rn(__fadd_rn(acc[0].mnL, acc[0].mxL), 0.5f);
+        shc[1] = __fmul_rn(__fadd_rn(acc[0].mnR, acc[0].mxR), 0.5f);
+      }
+      for (int j = lane; j < cp; j += 32) {
+        pc[j] = addrn(scL[j], -shc[0]);
+        rc[j] = addrn(scR[j], -shc[1]);
+      }
       if (lane == 0) {
+        if constexpr (RIG) {
+          const float e1 = __fadd_ru(__fadd_ru(ecost, __fmul_ru(acc[0].am, (float)nc * u24)),
+                                     (float)nc * 0x1p-149f);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            const float smin = __fsub_rn(c ? acc[0].mnR : acc[0].mnL, shc[c]);
+            const float smax = __fsub_rn(c ? acc[0].mxR : acc[0].mxL, shc[c]);
+            const float Mr = fmaxf(fabsf(smin), fabsf(smax));
+            const double On = Oc + (double)shc[c];
+            const float e2 = __fadd_ru(__fadd_ru(__fadd_ru(e1, __fmul_ru(Mr, u24)), 0x1p-149f),
+                                       __double2float_ru(__dmul_ru(fabs(On), 0x1p-52)));
+            char* it = c ? right : parent;
+            *(double*)(it + 32) = On;
+            *(float*)(it + 40) = e2;
+            ChildRec* rec = c ? recR : recL;
+            rec->pmin = okey(__dsub_rd(__dadd_rd(On, (double)smin), (double)e2));
+            rec->pmax = okey(__dadd_ru(__dadd_ru(On, (double)smax), (double)e2));
+            rec->perr = __float_as_uint(e2);
+            if ((double)e2 > cost_thr) lin_mark(E, par, p, c ? k + Kl : k, 2, 0);
+          }
+        } else {
+          recL->pmin = okey((double)acc[0].mnL);
+          recL->pmax = okey((double)acc[0].mxL);
+          recR->pmin = okey((double)acc[0].mnR);
+          recR->pmax = okey((double)acc[0].mxR);
+        }
+        // box and slot map
         E.map[slot_off + k + Kl] = rslot;
         unsigned* iL = (unsigned*)parent;
         unsigned* iR = (unsigned*)right;
@@ -252,186 +368,191 @@ __global__ void __launch_bounds__(256, 3) k2_subdivide_lin(Engine E, int cgmax, 
         iL[r] = 2u * v;
         iR[r] = 2u * v + 1u;
       }
-    };
-    // the children's words of a chunk with no active constraint: zero (the
-    // left child shares the parent's, already zero)
-    auto clear_right = [&](int c0, int c1) {
-      const int wb0 = c0 * PCBA_LIN_WORDS, wb1 = min(c1 * PCBA_LIN_WORDS, mwords);
-      for (int q = wb0 + lane; q < wb1; q += 32) rmask[q] = 0u;
-    };
-    if (!need_shared) {
-      // no active constraint in this unit's chunks (nor, for chunk 0, in the
-      // item): the shared patches are not needed any more
-      clear_right(c_beg, c_end);
-      if (lane == 0 && summ) {
-        if (tiles == 1) {
-          *sumL = 0ull;
-          *sumR = 0ull;
-        } else {
-          atomicAnd(sumL, ~range);
-          atomicAnd(sumR, ~range);
+      // ---- shared children, re-centred likewise, to the other copy, with
+      // their metadata (error bound, offset, extremes of the stored values)
+      if (any) {
+        T sh[2][K];
+#pragma unroll
+        for (int g = 0; g < K; ++g) {
+          sh[0][g] = RIG ? T(__fmul_rn(__fadd_rn((float)acc[1 + g].mnL, (float)acc[1 + g].mxL), 0.5f))
+                         : T(0);
+          sh[1][g] = RIG ? T(__fmul_rn(__fadd_rn((float)acc[1 + g].mnR, (float)acc[1 + g].mxR), 0.5f))
+                         : T(0);
         }
-      }
-      if (c_beg == 0) split_cost_and_box();
-      __syncwarp();
-      continue;
-    }
-    // ---- the parent's shared patches into shared memory
-    const T* gsrc = (const T*)(parent + D->off_g + par * D->copy_g);
-    const char* pmeta = parent + D->off_eg + par * D->copy_e;  // FP32: errors, then offsets
-    float em[K];   // stored error bounds (FP32)
-    float am[K];   // max |parent residual| per patch (FP32)
-    double Om[K];  // FP64 offsets of the parent's stored patches (FP32; 0 in FP64)
+        T* gL = (T*)(parent + D->off_g + (par ^ 1) * D->copy_g);
+        T* gR = (T*)(right + D->off_g + (par ^ 1) * D->copy_g);
+        for (int e = lane; e < 4 * C; e += 32) {
+          const int m = e & 3;
+          T a0 = T(0), a1 = T(0);
 #pragma unroll
-    for (int m = 0; m < K; ++m) {
-      float a = 0.0f;
-      for (int j = lane; j < C; j += 32) {
-        const T v = gsrc[(size_t)j * apad + m];
-        sP[(size_t)m * C + j] = v;
-        if constexpr (RIG) a = fmaxf(a, fabsf((float)v));
-      }
-      if constexpr (RIG) {
-        am[m] = lin_wmax(a);
-        em[m] = fabsf(((const float*)pmeta)[m]);
-        Om[m] = ((const double*)(pmeta + 4LL * apad))[m];
-      } else {
-        am[m] = 0.0f;
-        em[m] = 0.0f;
-        Om[m] = 0.0;
-      }
-    }
-    __syncwarp();
-    // ---- de Casteljau at 1/2 on every fibre of every shared patch (Sec. II-E)
-    T* sL = sC;
-    T* sR = sC + (size_t)4 * cgmax;
-    for (int f = lane; f < K * nf; f += 32) {
-      const int m = f / nf;
-      const int fi = f - m * nf;
-      const int o = fi / stride;
-      const int base = o * blk + (fi - o * stride);
-      dispatch_fixed<16, NFIX>(n, [&](auto nc) {
-        lin_fibre<T, decltype(nc)::value>(sP + (size_t)m * C, sL, sR, base, stride, m);
-      });
-    }
-    __syncwarp();
-    // ---- extremes of the children's patches, and their error bounds
-    T mn[2][K], mx[2][K];
-    float Mabs[2][K], ec[K];
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const T* sc = c ? sR : sL;
-#pragma unroll
-      for (int m = 0; m < K; ++m) {
-        T a = T(INFINITY), b = T(-INFINITY);
-        for (int j = lane; j < C; j += 32) {
-          const T v = sc[(size_t)j * 4 + m];
-          a = min(a, v);
-          b = max(b, v);
-        }
-        mn[c][m] = lin_wmin(a);
-        mx[c][m] = lin_wmax(b);
-        if constexpr (RIG)
-          Mabs[c][m] = fmaxf(fabsf((float)mn[c][m]), fabsf((float)mx[c][m]));
-        else
-          Mabs[c][m] = 0.0f;
-      }
-    }
-#pragma unroll
-    for (int m = 0; m < K; ++m) {
-      if constexpr (RIG) {
-        const float fn = (float)n;
-        ec[m] = __fadd_ru(__fadd_ru(em[m], __fmul_ru(am[m], fn * u24)), fn * 0x1p-149f);
-      } else {
-        ec[m] = 0.0f;
-      }
-    }
-    // ---- chunk 0: the children's shared patches, the cost patch, box and map
-    if (c_beg == 0) {
-      T* dL = (T*)(parent + D->off_g + (par ^ 1) * D->copy_g);
-      T* dR = (T*)(right + D->off_g + (par ^ 1) * D->copy_g);
-      if constexpr (RIG) {
-        // FP32: each child patch re-centred on the middle of its range, as the
-        // cost patch: stored r' = fl(r - mid) (error <= u |r'|, and r' lies in
-        // [fl(mn - mid), fl(mx - mid)] since rounding is monotone), offset
-        // O' = O + mid in FP64 (error <= 2^-53 |O'|)
-        float mid[2][K];
-        float enew[2][K];
-        double On[2][K];
-#pragma unroll
-        for (int c = 0; c < 2; ++c)
-#pragma unroll
-          for (int m = 0; m < K; ++m) {
-            const float md = __fmul_rn(__fadd_rn((float)mn[c][m], (float)mx[c][m]), 0.5f);
-            const float Mr = fmaxf(fabsf(__fsub_rn((float)mn[c][m], md)),
-                                   fabsf(__fsub_rn((float)mx[c][m], md)));
-            mid[c][m] = md;
-            On[c][m] = Om[m] + (double)md;
-            const float eo = __double2float_ru(__dmul_ru(fabs(On[c][m]), 0x1p-52));
-            enew[c][m] = __fadd_ru(__fadd_ru(__fadd_ru(ec[m], __fmul_ru(Mr, u24)), 0x1p-149f), eo);
+          for (int g = 0; g < K; ++g)
+            if (g == m) {
+              a0 = sh[0][g];
+              a1 = sh[1][g];
+            }
+          if (m < K) {
+            gL[e] = addrn(spL[e], -a0);
+            gR[e] = addrn(spR[e], -a1);
           }
-        for (int e = lane; e < C * K; e += 32) {
-          const int j = e / K;
-          const int m = e - j * K;
-          float mL = mid[0][0], mR = mid[1][0];
-#pragma unroll
-          for (int q = 1; q < K; ++q)
-            if (m == q) { mL = mid[0][q]; mR = mid[1][q]; }
-          dL[(size_t)j * apad + m] = __fsub_rn((float)sL[(size_t)j * 4 + m], mL);
-          dR[(size_t)j * apad + m] = __fsub_rn((float)sR[(size_t)j * 4 + m], mR);
         }
-        if (lane < K) {
-          float eL = enew[0][0], eR = enew[1][0];
-          double oL = On[0][0], oR = On[1][0];
+        if (lane < 2 * K) {
+          const int c = lane / K, g0 = lane - c * K;
+          char* cm = (c ? right : parent) + D->off_eg + (par ^ 1) * D->copy_e;
 #pragma unroll
-          for (int m = 1; m < K; ++m)
-            if (lane == m) { eL = enew[0][m]; eR = enew[1][m]; oL = On[0][m]; oR = On[1][m]; }
-          char* mL = parent + D->off_eg + (par ^ 1) * D->copy_e;
-          char* mR = right + D->off_eg + (par ^ 1) * D->copy_e;
-          ((float*)mL)[lane] = eL;
-          ((float*)mR)[lane] = eR;
-          ((double*)(mL + 4LL * apad))[lane] = oL;
-          ((double*)(mR + 4LL * apad))[lane] = oR;
-        }
-      } else {
-        for (int e = lane; e < C * K; e += 32) {
-          const int j = e / K;
-          const int m = e - j * K;
-          dL[(size_t)j * apad + m] = sL[(size_t)j * 4 + m];
-          dR[(size_t)j * apad + m] = sR[(size_t)j * 4 + m];
+          for (int g = 0; g < K; ++g) {
+            if (g != g0) continue;
+            const T mn0 = c ? acc[1 + g].mnR : acc[1 + g].mnL;
+            const T mx0 = c ? acc[1 + g].mxR : acc[1 + g].mxL;
+            if constexpr (RIG) {
+              const float e1 = __fadd_ru(__fadd_ru(em[g], __fmul_ru((float)acc[1 + g].am, (float)ns * u24)),
+                                         (float)ns * 0x1p-149f);
+              const float smin = __fsub_rn((float)mn0, (float)sh[c][g]);
+              const float smax = __fsub_rn((float)mx0, (float)sh[c][g]);
+              const float Mr = fmaxf(fabsf(smin), fabsf(smax));
+              const double On = Om[g] + (double)sh[c][g];
+              LinMeta<T>::err(cm, 4)[g] =
+                  __fadd_ru(__fadd_ru(__fadd_ru(e1, __fmul_ru(Mr, u24)), 0x1p-149f),
+                            __double2float_ru(__dmul_ru(fabs(On), 0x1p-52)));
+              LinMeta<T>::off(cm, 4)[g] = On;
+              LinMeta<T>::mn(cm, 4)[g] = T(smin);
+              LinMeta<T>::mx(cm, 4)[g] = T(smax);
+            } else {
+              LinMeta<T>::mn(cm, 4)[g] = mn0;
+              LinMeta<T>::mx(cm, 4)[g] = mx0;
+            }
+          }
         }
       }
-      split_cost_and_box();
+      __syncwarp();  // the staging buffers are reused by the next item
     }
-    T gmax[2] = {T(-INFINITY), T(-INFINITY)}, gmin[2] = {T(-INFINITY), T(-INFINITY)};
-    bool mark[2] = {false, false};
-    unsigned nfull = 0;      // coefficient-range evaluations of this lane
-    unsigned npairs = 0;     // (child, active constraint) bounds of this unit
-    const int Kw = K;
-    unsigned long long bitsL = 0ull, bitsR = 0ull;  // children's non-empty chunks here
-    for (int cc = c_beg; cc < c_end; ++cc) {
-      if (summ && !((live >> cc) & 1ull)) {
-        clear_right(cc, cc + 1);
-        continue;
-      }
-      // ---- the active constraints of chunk cc, compacted
-      const int w0 = cc * PCBA_LIN_WORDS;
-      const int nw = min(PCBA_LIN_WORDS, mwords - w0);
-      unsigned* pm = pmask + w0;
-      unsigned* rm = rmask + w0;
-      __syncwarp();  // the previous chunk's readers of sIdx and sMw are done
-      const unsigned word = lane < nw ? pm[lane] : 0u;
-      const unsigned cnt = __popc(word);
-      unsigned incl = cnt;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k2_lin_bound: one warp per (parent item, chunk of activity words)
+// ---------------------------------------------------------------------------
+
+// Bytes of shared memory one warp of k2_lin_bound uses: both children's
+// shared patches ([C][4] each), the compacted constraint indices and the
+// children's activity words.
+template <typename T>
+__host__ __device__ constexpr size_t lin_bound_warp_bytes(int cgmax) {
+  return (8 * (size_t)cgmax * sizeof(T) + 32 * PCBA_LIN_WORDS * sizeof(unsigned short) +
+          2 * PCBA_LIN_WORDS * sizeof(unsigned) + 15) / 16 * 16;
+}
+
+// Coefficient range of cc + sum_m w_m s_mj over the C coefficients of one
+// child staged in shared memory ([C][4]); two partial extremes per bound.
+template <typename T, int K>
+__device__ __forceinline__ void lin_range(const T* s, int C, T cc, const T (&w)[K], T& lo, T& hi) {
+  T lo0 = T(INFINITY), hi0 = T(-INFINITY), lo1 = T(INFINITY), hi1 = T(-INFINITY);
+  int j = 0;
+#pragma unroll 2
+  for (; j + 1 < C; j += 2) {
+    T a[K], b[K];
+    lin_load<T, K>(s + (size_t)j * 4, a);
+    lin_load<T, K>(s + (size_t)(j + 1) * 4, b);
+    T v0 = cc, v1 = cc;
 #pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += y;
+    for (int m = 0; m < K; ++m) {
+      v0 = fma(w[m], a[m], v0);
+      v1 = fma(w[m], b[m], v1);
+    }
+    lo0 = min(lo0, v0);
+    hi0 = max(hi0, v0);
+    lo1 = min(lo1, v1);
+    hi1 = max(hi1, v1);
+  }
+  if (j < C) {
+    T a[K];
+    lin_load<T, K>(s + (size_t)j * 4, a);
+    T v0 = cc;
+#pragma unroll
+    for (int m = 0; m < K; ++m) v0 = fma(w[m], a[m], v0);
+    lo0 = min(lo0, v0);
+    hi0 = max(hi0, v0);
+  }
+  lo = min(lo0, lo1);
+  hi = max(hi0, hi1);
+}
+
+template <typename T, int K>
+__global__ void __launch_bounds__(256, 4) k2_lin_bound(Engine E, int cgmax) {
+  constexpr bool RIG = sizeof(T) == 4;
+  constexpr float u24 = 0x1p-24f;
+  extern __shared__ __align__(16) unsigned char klb[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  T* sS = (T*)(klb + (size_t)warp * lin_bound_warp_bytes<T>(cgmax));  // children [2][C][4]
+  unsigned short* sIdx = (unsigned short*)(sS + 8 * (size_t)cgmax);
+  unsigned* sMw = (unsigned*)(sIdx + 32 * PCBA_LIN_WORDS);  // child words [2][LIN_WORDS]
+  const unsigned units = E.plan->k2_units;
+  const int par = E.plan->steps_global & 1;  // the children's data is in copy par ^ 1
+  int cx_p = -1, cx_K = 0, cx_chunks = 1;
+  unsigned cx_beg = 0, cx_end = 0;
+  const ProbDesc* D = nullptr;
+  // units are fetched in batches from a counter (reset before every step), so
+  // that the few heavy units - chunks with many active constraints - spread
+  // over the whole GPU
+  for (;;) {
+    unsigned ubeg = 0;
+    if (lane == 0) ubeg = atomicAdd(&E.plan->lin_next, (unsigned)PCBA_LIN_BATCH);
+    ubeg = __shfl_sync(0xffffffffu, ubeg, 0);
+    if (ubeg >= units) break;
+    const unsigned uend = min(units, ubeg + (unsigned)PCBA_LIN_BATCH);
+    for (unsigned u = ubeg; u < uend; ++u) {
+      if (u < cx_beg || u >= cx_end || cx_p < 0) {
+        cx_p = find_problem(E.k2_pre, E.np, u);
+        cx_beg = E.k2_pre[cx_p];
+        cx_end = E.k2_pre[cx_p + 1];
+        D = E.desc + cx_p;
+        cx_K = E.state[cx_p].K;
+        cx_chunks = D->lin_chunks;
       }
-      const unsigned na = __shfl_sync(0xffffffffu, incl, 31);
+      const int p = cx_p, Kl = cx_K, chunks = cx_chunks;
+      const unsigned local = u - cx_beg;
+      const int k = (int)(local / (unsigned)chunks);
+      const int t = (int)(local - (unsigned)k * chunks);
+      const long long slot_off = D->slot_off;
+      char* list = E.arena + D->list_off;
+      char* left = list + (size_t)E.map[slot_off + k] * D->item_bytes;       // the parent's slot
+      char* right = list + (size_t)E.map[slot_off + k + Kl] * D->item_bytes;  // set by the split
+      const int C = D->cg, mwords = D->mwords;
+      const int w0 = t * PCBA_LIN_WORDS;
+      const int nw = min(PCBA_LIN_WORDS, mwords - w0);
+      unsigned* pm = (unsigned*)(left + D->off_mask) + w0;  // the parent's words, in place
+      unsigned* rm = (unsigned*)(right + D->off_mask) + w0;
+      // summaries: bit t of the parent's says whether chunk t has an active
+      // constraint; the children's are written to the other word (kept for up
+      // to 64 chunks)
+      const bool summ = chunks <= 64;
+      unsigned long long* sumL = (unsigned long long*)(left + D->off_sum) + (par ^ 1);
+      unsigned long long* sumR = (unsigned long long*)(right + D->off_sum) + (par ^ 1);
+      const unsigned long long tb = summ ? (1ull << t) : 0ull;
+      const bool live =
+          !summ || ((*((const unsigned long long*)(left + D->off_sum) + par) >> t) & 1ull);
+      unsigned word = 0u, cnt = 0u, incl = 0u, na = 0u;
+      if (live) {
+        word = lane < nw ? pm[lane] : 0u;
+        cnt = __popc(word);
+        incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += y;
+        }
+        na = __shfl_sync(0xffffffffu, incl, 31);
+      }
       if (na == 0) {
+        // no active constraint here: the children's words are zero (the
+        // left child shares the parent's, already zero)
         if (lane < nw) rm[lane] = 0u;
+        if (lane == 0 && tb) {
+          atomicAnd(sumL, ~tb);
+          atomicAnd(sumR, ~tb);
+        }
         continue;
       }
+      __syncwarp();  // the previous unit's readers of the staging buffers are done
       {
         unsigned pos = incl - cnt, bits = word;
         while (bits) {
@@ -441,83 +562,109 @@ __global__ void __launch_bounds__(256, 3) k2_subdivide_lin(Engine E, int cgmax, 
         }
       }
       if (lane < 2 * PCBA_LIN_WORDS) sMw[lane] = 0u;
+      // the children's shared patches (coalesced), extremes, error bounds and
+      // offsets (the same for every lane)
+      T cmn[2][K], cmx[2][K];
+      float Mabs[2][K], ec[2][K];
+      double Oc[2][K];
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        char* it = c ? right : left;
+        const T* cs = (const T*)(it + D->off_g + (par ^ 1) * D->copy_g);
+        for (int e = lane; e < 4 * C; e += 32) sS[(size_t)c * 4 * cgmax + e] = cs[e];
+        char* mc = it + D->off_eg + (par ^ 1) * D->copy_e;
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          cmn[c][m] = LinMeta<T>::mn(mc, 4)[m];
+          cmx[c][m] = LinMeta<T>::mx(mc, 4)[m];
+          if constexpr (RIG) {
+            Mabs[c][m] = fmaxf(fabsf((float)cmn[c][m]), fabsf((float)cmx[c][m]));
+            ec[c][m] = LinMeta<T>::err(mc, 4)[m];
+            Oc[c][m] = LinMeta<T>::off(mc, 4)[m];
+          } else {
+            Mabs[c][m] = 0.0f;
+            ec[c][m] = 0.0f;
+            Oc[c][m] = 0.0;
+          }
+        }
+      }
       __syncwarp();
-      npairs += 2u * na;
+      T gmax[2] = {T(-INFINITY), T(-INFINITY)}, gmin[2] = {T(-INFINITY), T(-INFINITY)};
+      bool mark[2] = {false, false};
+      unsigned nfull = 0;  // coefficient-range evaluations of this lane
+      const int Kw = K;
       for (unsigned q = lane; q < na; q += 32) {
         const int li = sIdx[q];
         const long long row = (D->lin_off + (long long)w0 * 32 + li) * PCBA_LIN_STRIDE;
-        T cc, w[K];
-        float E64 = 0.0f;  // FP32: bound of the FP64 rounding of the constant term
+        const double* rw = E.lin64 + row;
+        T w[K], cc[2];
+        float E64[2] = {0.0f, 0.0f};  // FP32: bound of the FP64 constant term
         if constexpr (RIG) {
           const float4 r0 = *(const float4*)(E.lin32 + row);
           const float4 r1 = *(const float4*)(E.lin32 + row + 4);
           const float rr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-  #pragma unroll
+#pragma unroll
           for (int m = 0; m < K; ++m) w[m] = rr[1 + m];
-          // the constant term c_i + sum_m w_im O_m of the coefficients relative
-          // to the parent's offsets, in FP64 from the FP64 row: the large terms
-          // cancel here, exactly enough, and the FP32 part only carries the
+          // the constant term c_i + sum_m w_im O_m of each child's
+          // coefficients relative to its offsets, in FP64 from the FP64 row:
+          // the large terms cancel here, and the FP32 part only carries the
           // residuals (of the order of the box's range)
-          const double* rw = E.lin64 + row;
-          double kap = rw[0], a64 = fabs(rw[0]);
-  #pragma unroll
-          for (int m = 0; m < K; ++m) {
-            kap = fma(rw[1 + m], Om[m], kap);
-            a64 = fma(fabs(rw[1 + m]), fabs(Om[m]), a64);
+#pragma unroll
+          for (int c = 0; c < 2; ++c) {
+            double kap = rw[0], a64 = fabs(rw[0]);
+#pragma unroll
+            for (int m = 0; m < K; ++m) {
+              kap = fma(rw[1 + m], Oc[c][m], kap);
+              a64 = fma(fabs(rw[1 + m]), fabs(Oc[c][m]), a64);
+            }
+            cc[c] = (T)kap;
+            E64[c] = __double2float_ru(__dmul_ru(a64, 0x1p-50));
           }
-          cc = (float)kap;
-          E64 = __double2float_ru(__dmul_ru(a64, 0x1p-50));
         } else {
-          const double* rw = E.lin64 + row;
-          cc = rw[0];
-  #pragma unroll
-          for (int m = 0; m < K; ++m) w[m] = rw[1 + m];
+#pragma unroll
+          for (int m = 0; m < K; ++m) w[m] = (T)rw[1 + m];
+          cc[0] = cc[1] = (T)rw[0];
         }
         // E of the comment at the top of this file (0 in FP64 mode), and the
-        // interval bound from the ranges of the shared patches, per child
+        // interval bound from the ranges of the stored patches, per child
         float Ee[2] = {0.0f, 0.0f}, Er[2] = {0.0f, 0.0f};
         T lo[2], hi[2], Et[2];
-  #pragma unroll
+#pragma unroll
         for (int c = 0; c < 2; ++c) {
           float Eb = 0.0f;
           if constexpr (RIG) {
-            float A = fabsf((float)cc), ee = 0.0f;
-  #pragma unroll
+            float A = fabsf((float)cc[c]), ee = 0.0f;
+#pragma unroll
             for (int m = 0; m < K; ++m) {
               A = __fmaf_ru(fabsf((float)w[m]), Mabs[c][m], A);
-              ee = __fmaf_ru(fabsf((float)w[m]), ec[m], ee);
+              ee = __fmaf_ru(fabsf((float)w[m]), ec[c][m], ee);
             }
             const float kk = (float)(2 * Kw + 2);
             Er[c] = __fmul_ru((kk + 1.0f) * u24, A);
             Ee[c] = ee;
-            Eb = __fadd_ru(__fadd_ru(__fadd_ru(Er[c], __fmul_ru(ee, 1.0f + 0x1p-20f)), E64),
+            Eb = __fadd_ru(__fadd_ru(__fadd_ru(Er[c], __fmul_ru(ee, 1.0f + 0x1p-20f)), E64[c]),
                            kk * 0x1p-149f);
           }
           Et[c] = T(Eb);
-          T a = cc, b = cc;
-  #pragma unroll
+          T x0 = cc[c], x1 = cc[c];
+#pragma unroll
           for (int m = 0; m < K; ++m) {
-            const T x = w[m] * mn[c][m], y = w[m] * mx[c][m];
-            a += min(x, y);
-            b += max(x, y);
+            const T x = w[m] * cmn[c][m], y = w[m] * cmx[c][m];
+            x0 += min(x, y);
+            x1 += max(x, y);
           }
-          lo[c] = a;
-          hi[c] = b;
+          lo[c] = x0;
+          hi[c] = x1;
         }
         // undecided by the interval: the coefficient range itself (Alg. 3)
-        const bool needL = !(add_up(hi[0], Et[0]) <= T(0)) && !(sub_dn(lo[0], Et[0]) > T(0));
-        const bool needR = !(add_up(hi[1], Et[1]) <= T(0)) && !(sub_dn(lo[1], Et[1]) > T(0));
-        if (needL && needR) {
-          lin_full_range2<T, K>(sL, sR, C, cc, w, lo[0], hi[0], lo[1], hi[1]);
-          nfull += 2;
-        } else if (needL) {
-          lin_full_range<T, K>(sL, C, cc, w, lo[0], hi[0]);
-          nfull += 1;
-        } else if (needR) {
-          lin_full_range<T, K>(sR, C, cc, w, lo[1], hi[1]);
-          nfull += 1;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+          if (!(add_up(hi[c], Et[c]) <= T(0)) && !(sub_dn(lo[c], Et[c]) > T(0))) {
+            lin_range<T, K>(sS + (size_t)c * 4 * cgmax, C, cc[c], w, lo[c], hi[c]);
+            ++nfull;
+          }
         }
-  #pragma unroll
+#pragma unroll
         for (int c = 0; c < 2; ++c) {
           const T up = add_up(hi[c], Et[c]), dn = sub_dn(lo[c], Et[c]);
           const bool sat = up <= T(0);
@@ -529,14 +676,13 @@ __global__ void __launch_bounds__(256, 3) k2_subdivide_lin(Engine E, int cgmax, 
           }
           if constexpr (RIG) {
             // the bound changed a decision the stored coefficients make: mark
-            // the child's shared patches for a refresh if their errors are the
-            // larger part of the bound
+            // the child's shared patches for a refresh if their errors are
+            // the larger part of the bound
             const bool flip = (hi[c] <= T(0)) != sat || (lo[c] > T(0)) != inf;
             if (flip && Ee[c] > Er[c]) mark[c] = true;
           }
         }
       }
-
       __syncwarp();
       if (lane < nw) {
         pm[lane] = sMw[lane];                      // left child: in place (this unit's words)
@@ -544,46 +690,32 @@ __global__ void __launch_bounds__(256, 3) k2_subdivide_lin(Engine E, int cgmax, 
       }
       const bool keepL = __any_sync(0xffffffffu, lane < nw && sMw[lane] != 0u);
       const bool keepR = __any_sync(0xffffffffu, lane < nw && sMw[PCBA_LIN_WORDS + lane] != 0u);
-      if (cc < 64) {
-        if (keepL) bitsL |= 1ull << cc;
-        if (keepR) bitsR |= 1ull << cc;
-      }
-    }
-    // ---- the children's summaries for this unit's chunks
-    if (lane == 0 && summ) {
-      if (tiles == 1) {
-        *sumL = bitsL;
-        *sumR = bitsR;
-      } else {
-        const unsigned long long tb = 1ull << t;
-        if (bitsL) atomicOr(sumL, tb); else atomicAnd(sumL, ~tb);
-        if (bitsR) atomicOr(sumR, tb); else atomicAnd(sumR, ~tb);
-      }
-    }
-    // ---- bound maxima of the children, counters, refresh marks
-    if (npairs > 0) {
-      const unsigned full = __reduce_add_sync(0xffffffffu, nfull);
       if (lane == 0) {
-        atomicAdd(&E.plan->lin_pairs, (unsigned long long)npairs);
-        atomicAdd(&E.plan->lin_full, (unsigned long long)full);
+        if (tb) {
+          if (keepL) atomicOr(sumL, tb); else atomicAnd(sumL, ~tb);
+          if (keepR) atomicOr(sumR, tb); else atomicAnd(sumR, ~tb);
+        }
+        atomicAdd(&E.plan->lin_pairs, 2ull * na);
       }
+      const unsigned full = __reduce_add_sync(0xffffffffu, nfull);
+      if (lane == 0) atomicAdd(&E.plan->lin_full, (unsigned long long)full);
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const T gx = lin_wmax(gmax[c]);
         const T gn = lin_wmax(gmin[c]);
-        ChildRec* rc = c ? recR : recL;
+        ChildRec* rc = E.rec + slot_off + k + (c ? Kl : 0);
         if (lane == 0 && gx > T(-INFINITY)) {
           atomicMax(&rc->gmaxmax, okey((double)gx));
           atomicMax(&rc->gminmax, okey((double)gn));
         }
       }
+      if constexpr (RIG) {
+        const MarkCtx mk{p, k, k + Kl, E.marks + (size_t)par * E.mark_cap,
+                         &E.plan->mark_count[par], E.mark_cap};
+        const bool bl = __any_sync(0xffffffffu, mark[0]);
+        const bool br = __any_sync(0xffffffffu, mark[1]);
+        append_marks(mk, bl && lane < K, br && lane < K, 0, lane);
+      }
     }
-    if constexpr (RIG) {
-      const bool bl = __any_sync(0xffffffffu, mark[0]);
-      const bool br = __any_sync(0xffffffffu, mark[1]);
-      append_marks(mk, bl && lane < K, br && lane < K, 0, lane);
-    }
-    __syncwarp();
-  }
   }
 }
