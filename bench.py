@@ -1,22 +1,27 @@
-"""Benchmark: certified-optimal PCBA solves per second on RTD-shaped problems.
+"""Benchmark: certified-optimal PCBA solves per second and time-to-certify.
 
-One step = one batched solve, through the C ABI, of B problems per GPU with the
-whole path: the learned warm start (cost-landscape features, the set-encoder
-network's forward pass, FP32-certified candidates seeding the incumbent), the
-FP64 monomial-to-Bernstein conversion, the branch and bound loop of subdivide /
-bound / incumbent / cut-off / compaction, and the FP64 check of the returned
-points, until every problem is certified or stops.  The same solve without
-the warm start, in FP32 and in FP64, is timed beside it.
+One step = one batched solve, through the C ABI, of the uneven 256-problem
+workload per GPU with the whole path: the learned warm start (cost-landscape
+features, the set-encoder network's forward pass, FP32-certified candidates
+seeding the incumbent), the FP64 monomial-to-Bernstein conversion, the branch
+and bound loop of subdivide / bound / incumbent / cut-off / compaction, and
+the FP64 check of the returned points, until every problem is certified or
+stops.  Only certified solves (OPTIMAL or INFEASIBLE) count.
 
   python bench.py [--gpus N --steps K --warmup W]      the CUDA library
   python bench.py --impl reference [...]               the CPU oracle on host cores
 
-Problems: l = 2 on [-1,1]^2, a degree-(3,3) map F with N(0, 0.5^2)
-coefficients, 512 obstacle points, constraints r^2 - ||F(q) - o_i||^2 <= 0 of
-degree (6,6), cost ||F(q) - goal||^2; rank k solves seeds 2000 + B*k + j.
-Patches are FP32 with directed-rounding error bounds (FP64 mode is timed
-beside it).  Inputs are resident in HBM when the timed region starts; L2 is
-flushed between timed steps by writing a 256 MiB buffer.
+Workload: 256 rtd problems per GPU (rank k: seeds 4000 + 256 k + j), obstacle
+counts floor(exp U(ln 16, ln 4096)); each is l = 2 on [-1,1]^2, a degree-(3,3)
+map F with N(0, 0.5^2) coefficients, obstacle constraints r^2 - ||F(q) - o_i||^2
+<= 0 (degree (6,6), r = 0.15, o_i ~ U([-2,2]^2)), cost ||F(q) - goal||^2.  The
+library receives the constraints as a linear family in (||F||^2, F_1, F_2)
+(pcba_create_linear); patches are FP32 with directed-rounding error bounds.
+Inputs are resident in HBM when the timed region starts; L2 is flushed
+between timed steps by writing a 256 MiB buffer.  Legs beside the headline:
+the same workload without warm start, in FP64 and with dense constraints; the
+64-problem 512-obstacle batch (linear, dense, dense FP64); the tiny problems
+one at a time; the 4-D problems with equalities; the warm-start A/B.
 """
 from __future__ import annotations
 
@@ -37,24 +42,34 @@ if ROOT not in sys.path:
 
 METRIC = "certified-optimal solves/sec and p50/p99 time-to-certify (opt_tol 1e-3), 1 B300"
 UNIT = "solves/s"
-BATCH = 64
-OBSTACLES = 512
+BATCH = 256
+BASE_SEED = 4000
+OBS_LO, OBS_HI = 16, 4096
 OPT_TOL = 1e-3
 EQ_TOL = 1e-4
 RELAX_OPT_TOL, RELAX_EQ_TOL = 3e-2, 1e-1   # first solve of the polished pipeline (equalities)
 MAX_ITERS = 28
-BASE_SEED = 2000
-MEM_CAP = 64 << 30
-UNEVEN_MEM = 200 << 30   # list memory shared by the 256 problems of the uneven batch
-WORKLOAD = ("rtd-shaped POPs: l=2 on [-1,1]^2, F degree (3,3) N(0,0.5^2), %d obstacles "
-            "U([-2,2]^2) r=0.15, constraints degree (6,6), cost ||F-goal||^2; batch of %d "
-            "problems per GPU (seeds %d+%d*rank+j); FP32 patches with directed-rounding "
-            "error bounds; opt_tol %g" % (OBSTACLES, BATCH, BASE_SEED, BATCH, OPT_TOL))
+MEM_CAP = 64 << 30        # list memory of the linear-family batch
+DENSE_MEM = 200 << 30     # list memory of the dense-constraint batch (same problems)
+WORKLOAD = ("uneven batch of %d rtd-shaped POPs per GPU (rank k: seeds %d+%d*k+j): l=2 on "
+            "[-1,1]^2, F degree (3,3) N(0,0.5^2), obstacles floor(exp U(ln %d, ln %d)) "
+            "U([-2,2]^2) r=0.15, constraints degree (6,6) given as a linear family in "
+            "(||F||^2, F_1, F_2), cost ||F-goal||^2; FP32 patches with directed-rounding error "
+            "bounds; learned warm start; opt_tol %g"
+            % (BATCH, BASE_SEED, BATCH, OBS_LO, OBS_HI, OPT_TOL))
 
 
 def shard_seeds(rank: int, batch: int = BATCH, base: int = BASE_SEED):
     """Seeds of the problems one rank solves (independent problems, no exchange)."""
     return [base + batch * rank + j for j in range(batch)]
+
+
+def shard_problems(rank: int, batch: int = BATCH):
+    """The rank's problems: obstacle counts drawn from the rank's first seed."""
+    from paper_2003_01758_b300 import workloads as W
+    seeds = shard_seeds(rank, batch)
+    counts = W.batch_obstacle_counts(batch, seeds[0], OBS_LO, OBS_HI)
+    return [W.rtd(s, n_obstacles=int(c)) for s, c in zip(seeds, counts)]
 
 
 def reduce_max(value: float, world: int) -> float:
@@ -65,6 +80,16 @@ def reduce_max(value: float, world: int) -> float:
     import torch.distributed as dist
     t = torch.tensor([value], dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def reduce_sum(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
     return float(t.item())
 
 
@@ -90,12 +115,12 @@ def kernel_code_hash(path):
     return hashlib.sha256(text.encode()).hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per subdivision launch from the committed ncu summary, or None
+def profiled_traffic(src_name, prof_name):
+    """DRAM bytes per subdivision step from a committed ncu summary, or None
     when the kernel code changed since that capture."""
     import re
-    src = os.path.join(ROOT, "paper_2003_01758_b300", "csrc", "pcba_subdivide.cuh")
-    prof = os.path.join(ROOT, "profiles", "k2_subdivide_rtd512_fp32.md")
+    src = os.path.join(ROOT, "paper_2003_01758_b300", "csrc", src_name)
+    prof = os.path.join(ROOT, "profiles", prof_name)
     try:
         text = open(prof).read()
         if "`%s`" % kernel_code_hash(src) not in text:
@@ -158,10 +183,12 @@ class ClockSampler:
 # CPU oracle (cpu_baseline leg and --impl reference)
 # ---------------------------------------------------------------------------
 
-def _oracle_one(seed):
+def _oracle_one(k):
+    """The oracle on problem k of the rank-0 workload (its dense constraints)."""
     import oracle
     from paper_2003_01758_b300 import workloads as W
-    p = W.rtd(seed, n_obstacles=OBSTACLES)
+    count = W.batch_obstacle_counts(BATCH, BASE_SEED, OBS_LO, OBS_HI)[k]
+    p = W.rtd(BASE_SEED + k, n_obstacles=int(count))
     t = time.perf_counter()
     r = oracle.solve(p.cost, p.ineq, p.eq, p.lo, p.hi, opt_tol=OPT_TOL, eq_tol=EQ_TOL,
                      max_iters=MAX_ITERS)
@@ -174,9 +201,9 @@ def oracle_pool(procs):
     return ProcessPoolExecutor(procs, mp_context=mp.get_context("spawn"))
 
 
-def run_oracle(pool, seeds):
+def run_oracle(pool, ks):
     t = time.perf_counter()
-    out = list(pool.map(_oracle_one, seeds))
+    out = list(pool.map(_oracle_one, ks))
     return out, time.perf_counter() - t
 
 
@@ -184,14 +211,18 @@ def cpu_procs():
     return max(1, min(os.cpu_count() or 1, 32))
 
 
-def cpu_baseline(pool, procs, per_proc=2):
-    seeds = [BASE_SEED + j for j in range(procs * per_proc)]
-    run_oracle(pool, seeds[:procs])  # start-up of the workers
-    out, dt = run_oracle(pool, seeds)
+# every 8th problem of the 256: the same spread of obstacle counts
+ORACLE_SAMPLE = list(range(0, BATCH, 8))
+
+
+def cpu_baseline(pool, procs):
+    run_oracle(pool, [0] * procs)  # start-up of the workers
+    out, dt = run_oracle(pool, ORACLE_SAMPLE)
     ok = sum(1 for s, _ in out if s in (0, 1))
     return {"value": ok / dt, "unit": UNIT, "cores": procs, "kind": "oracle",
-            "sample": "%d rtd problems (seeds %d..%d), FP64 oracle, one problem per process, "
-                      "%d processes, %.1f s wall" % (len(seeds), seeds[0], seeds[-1], procs, dt),
+            "sample": "%d of the 256 problems (every 8th), FP64 oracle with the dense "
+                      "constraints, one problem per process, %d processes, %.1f s wall"
+                      % (len(ORACLE_SAMPLE), procs, dt),
             "p50_ms": 1e3 * float(np.median([t for _, t in out])),
             "p99_ms": 1e3 * float(np.percentile([t for _, t in out], 99))}
 
@@ -202,12 +233,12 @@ def run_reference(args, rank, world):
     procs = cpu_procs()
     pool = oracle_pool(procs)
     per_step = procs
-    seeds = lambda s: [BASE_SEED + (s * per_step + j) % (BATCH * 16) for j in range(per_step)]
+    ks = lambda s: [(s * per_step + j) % BATCH for j in range(per_step)]
     for s in range(args.warmup):
-        run_oracle(pool, seeds(s))
+        run_oracle(pool, ks(s))
     total, solved, lat = 0.0, 0, []
     for s in range(args.steps):
-        out, dt = run_oracle(pool, seeds(args.warmup + s))
+        out, dt = run_oracle(pool, ks(args.warmup + s))
         total += dt
         solved += sum(1 for st, _ in out if st in (0, 1))
         lat += [t for _, t in out]
@@ -217,13 +248,13 @@ def run_reference(args, rank, world):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD.replace("FP32 patches with "
-                                                                     "directed-rounding error bounds",
-                                                                     "FP64 CPU oracle"),
-                                        "problems_per_step": per_step},
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD.split("; FP32")[0] + "; FP64 CPU oracle with the "
+                   "dense constraints", "problems_per_step": per_step},
         "p50_ms": 1e3 * float(np.median(lat)), "p99_ms": 1e3 * float(np.percentile(lat, 99)),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": procs, "kind": "oracle",
-                         "sample": "%d problems per step, one per process" % per_step},
+                         "sample": "%d problems of the workload per step, one per process"
+                                   % per_step},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -234,14 +265,22 @@ def run_reference(args, rank, world):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def make_batch(seeds, precision, flags=0, mem_cap=MEM_CAP):
+def make_batch(probs, precision, linear=True, flags=0, mem_cap=MEM_CAP):
     from paper_2003_01758_b300 import pcba
-    from paper_2003_01758_b300 import workloads as W
-    probs = [W.rtd(s, n_obstacles=OBSTACLES) for s in seeds]
-    solvers = [pcba.Solver(p.cost, p.ineq, p.eq, p.lo, p.hi, precision=precision) for p in probs]
-    host = np.concatenate([np.concatenate([p.cost.ravel(), p.ineq.ravel(), p.eq.ravel()])
-                           for p in probs])
-    return pcba.Batch(solvers, mem_cap, flags=flags), solvers, host, probs
+    mk = pcba.linear_solver_from_problem if linear else pcba.solver_from_problem
+    return pcba.Batch([mk(p, precision) for p in probs], mem_cap, flags=flags)
+
+
+def host_coeffs(probs, linear=True):
+    """The monomial coefficients of a batch as the library lays them out: per
+    problem the cost, then the shared polynomials (linear) or every constraint."""
+    parts = []
+    for p in probs:
+        parts.append(p.cost.ravel())
+        parts.append(p.meta["linear"][0].ravel() if linear else p.ineq.ravel())
+        if not linear:
+            parts.append(p.eq.ravel())
+    return np.concatenate(parts)
 
 
 class Learned:
@@ -271,7 +310,11 @@ class Learned:
                               raw=raw)
 
     def launches_per_step(self):
-        return self.batch.stats()["kernel_launches"] + 1 + 12
+        # the solve's kernels, the cost grid and the network's forward pass
+        before = self.model.kernel_launches()
+        self.step()
+        net = self.model.kernel_launches() - before
+        return self.batch.stats()["kernel_launches"] + 1 + net
 
     def timed(self, steps, flush):
         """K learned steps; device time from CUDA events on the step's stream."""
@@ -298,18 +341,31 @@ def timed_steps(batch, steps, flush, polished=False):
     polished: pcba_batch_solve_polished (relaxed solve, polish, certified solve)."""
     import torch
     ms, times, status = [], [], []
+    res = None
     for _ in range(steps):
         flush.zero_()
         torch.cuda.synchronize()
         if polished:
-            res = batch.solve_polished(OPT_TOL, EQ_TOL, RELAX_OPT_TOL, RELAX_EQ_TOL, MAX_ITERS,
-                                       raw=True)
+            res = batch.solve_polished(OPT_TOL, EQ_TOL, RELAX_OPT_TOL, RELAX_EQ_TOL, MAX_ITERS)
         else:
-            res = batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS, raw=True)
+            res = batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
         ms.append(batch.timing()["total_ms"])
-        times += [r.time_ms for r in res]
-        status += [r.status for r in res]
-    return ms, times, status
+        times += [r["time_ms"] for r in res]
+        status += [r["status"] for r in res]
+    return ms, times, status, res
+
+
+def certified(status):
+    return sum(1 for s in status if s in (0, 1))
+
+
+def leg_summary(ms, times, status, n_problems):
+    """Certified solves/s and latency of a timed leg."""
+    return {"value": certified(status) / (sum(ms) / 1e3), "unit": UNIT,
+            "ms_per_step": float(np.mean(ms)), "certified": certified(status),
+            "infeasible": sum(1 for s in status if s == 1), "solves": len(status),
+            "p50_ms": float(np.median(times)), "p99_ms": float(np.percentile(times, 99)),
+            "problems_per_step": n_problems}
 
 
 def main():
@@ -319,15 +375,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--problems", type=int, default=BATCH, help="problems per GPU and step")
-    ap.add_argument("--mem-gb", type=float, default=MEM_CAP / 2 ** 30)
     ap.add_argument("--loop", default="graph", choices=["graph", "host"],
                     help="device loop in a conditional CUDA graph, or driven from the host")
     ap.add_argument("--no-extras", action="store_true",
-                    help="timed solves only (no e2e, FP64, latency or roofline legs)")
-    ap.add_argument("--launch-bytes", action="store_true",
-                    help="with --no-extras: one instrumented solve, print the algorithmic "
-                         "bytes of each subdivision launch")
+                    help="timed headline steps only (no e2e, roofline or side legs)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
@@ -346,7 +397,6 @@ def main():
     args.warmup = max(args.warmup, 3)
 
     # the oracle pool starts before the first CUDA call (spawned workers)
-    base = None
     pool = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         pool = oracle_pool(cpu_procs())
@@ -355,11 +405,9 @@ def main():
     from paper_2003_01758_b300 import build, pcba
     build.build()
     torch.cuda.set_device(local)
-    seeds = shard_seeds(rank, batch=args.problems)
-    mem_cap = int(args.mem_gb * 2 ** 30)
+    probs = shard_problems(rank)
     loop_flag = 0 if args.loop == "graph" else pcba.Batch.HOST_LOOP
-    batch, solvers, host_np, probs = make_batch(seeds, pcba.FP32, flags=loop_flag,
-                                                mem_cap=mem_cap)
+    batch = make_batch(probs, pcba.FP32, linear=True, flags=loop_flag)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     learned = Learned(batch, probs)
 
@@ -379,22 +427,16 @@ def main():
     if world > 1:
         dist.barrier()
     total_ms = reduce_max(float(sum(ms)), world)
-    launches = learned.launches_per_step() * args.steps
-
-    value = world * len(seeds) * args.steps / (total_ms / 1e3)
+    cert_all = reduce_sum(float(certified(status)), world)
+    value = cert_all / (total_ms / 1e3)
     optimal = sum(1 for s in status if s == pcba.OPTIMAL)
     infeasible = sum(1 for s in status if s == pcba.INFEASIBLE)
+    launches = learned.launches_per_step() * args.steps
     if args.no_extras:
-        if args.launch_bytes and rank == 0:
-            ib, _, _, _ = make_batch(seeds, pcba.FP32, flags=pcba.Batch.INSTRUMENT,
-                                     mem_cap=mem_cap)
-            Learned(ib, probs).step()
-            print(json.dumps({"launch_bytes": ib.launch_bytes().tolist(), "timing": ib.timing()}))
-            ib.close()
         if rank == 0:
             print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                               "steps": args.steps, "ms_per_step": total_ms / args.steps,
-                              "problems_per_step": len(seeds), "loop": args.loop,
+                              "problems_per_step": len(probs), "loop": args.loop,
                               "certified": optimal + infeasible, "clocks": clk}))
         return 0
 
@@ -402,17 +444,18 @@ def main():
     # ---- the same solves without the warm start ----
     with torch.cuda.stream(learned.stream):
         batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
-        cms, ctimes, cstatus = timed_steps(batch, args.steps, flush)
-        cold_steps = [r["steps"] for r in batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)]
-    cold = {"value": world * len(seeds) * len(cms) / (reduce_max(float(sum(cms)), world) / 1e3),
-            "unit": UNIT, "p50_ms": float(np.median(ctimes)),
-            "p99_ms": float(np.percentile(ctimes, 99)),
-            "certified": sum(1 for s in cstatus if s in (0, 1)), "solves": len(cstatus),
-            "mean_bisection_steps": float(np.mean(cold_steps))}
+        cms, ctimes, cstatus, cres = timed_steps(batch, args.steps, flush)
+    cold = leg_summary(cms, ctimes, cstatus, len(probs))
+    cold["mean_bisection_steps"] = float(np.mean([r["steps"] for r in cres]))
+    cold["value"] = reduce_sum(float(certified(cstatus)), world) / (
+        reduce_max(float(sum(cms)), world) / 1e3)
 
-    # ---- end to end: host inputs in (coefficients, obstacle points, goal and map
-    # features), network, guided solve, results out; wall clock ----
-    host = torch.from_numpy(host_np).pin_memory().numpy()
+    # ---- end to end: host inputs in (monomial coefficients, constraint rows,
+    # obstacle points, goal and map features), network, guided solve, results
+    # out; wall clock ----
+    h_coeffs = torch.from_numpy(host_coeffs(probs)).pin_memory().numpy()
+    h_rows = torch.from_numpy(pcba.linear_rows(probs)).pin_memory().numpy()
+    assert h_coeffs.size == batch.input_doubles() and h_rows.size == batch.rows_doubles()
     h_points = torch.from_numpy(learned.points).pin_memory()
     h_offsets = torch.from_numpy(learned.offsets).pin_memory()
     h_glob = torch.from_numpy(learned.glob).pin_memory()
@@ -420,81 +463,135 @@ def main():
 
     def e2e_step():
         with torch.cuda.stream(learned.stream):
-            batch.upload(host)
+            batch.upload(h_coeffs)
+            batch.upload_rows(h_rows)
             learned.pk.points.copy_(h_points, non_blocking=True)
             learned.pk.offsets.copy_(h_offsets, non_blocking=True)
             learned.pk.glob.copy_(h_glob, non_blocking=True)
             return learned.step()
 
     e2e_step()
-    e2e_s = 0.0
+    e2e_s, e2e_status = 0.0, []
     for _ in range(args.steps):
         flush.zero_()
         torch.cuda.synchronize()
         t = time.perf_counter()
-        e2e_step()
+        res = e2e_step()
         e2e_s += time.perf_counter() - t
+        e2e_status += [r.status for r in res]
     e2e_stats = batch.stats()
-    e2e_total = reduce_max(e2e_s, world)
-    e2e_value = world * len(seeds) * args.steps / e2e_total
+    e2e_value = reduce_sum(float(certified(e2e_status)), world) / reduce_max(e2e_s, world)
 
-    # ---- roofline of the subdivide/bound kernel: CUDA events around each launch ----
-    ibatch, _, _, _ = make_batch(seeds, pcba.FP32, flags=pcba.Batch.INSTRUMENT, mem_cap=mem_cap)
+    # ---- roofline of the subdivision step (split + bound kernels): CUDA
+    # events around each launch pair in a host-driven loop ----
+    ibatch = make_batch(probs, pcba.FP32, linear=True, flags=pcba.Batch.INSTRUMENT)
     ilearned = Learned(ibatch, probs)
     ilearned.step()
     ilearned.step()
     it = ibatch.timing()
+    lin = ibatch.linear_stats()
     ibatch.close()
     peak, peak_kind = load_peaks()
     achieved = it["subdiv_bytes"] / (it["subdiv_ms"] * 1e-3) / 1e9 if it["subdiv_ms"] > 0 else 0.0
 
-    # ---- FP64 mode, same problems ----
-    b64, s64, _, _ = make_batch(seeds, pcba.FP64, mem_cap=mem_cap)
+    # ---- FP64 (plain arithmetic, no warm start), same problems: the FP32
+    # bounds against the FP64 ones, per result ----
+    fp32_res = [dict(lower=r.lower, upper=r.upper, status=r.status, upper_err=r.upper_err)
+                for r in learned.step()]
+    b64 = make_batch(probs, pcba.FP64, linear=True)
     b64.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
-    ms64, _, st64 = timed_steps(b64, max(1, args.steps // 2), flush)
-    fp64_value = len(seeds) * len(ms64) / (sum(ms64) / 1e3)
+    ms64, t64, st64, res64 = timed_steps(b64, 2, flush)
     b64.close()
+    both = [(a, b) for a, b in zip(fp32_res, res64)
+            if a["status"] == 0 and b["status"] == 0]
+    dlo = np.array([abs(a["lower"] - b["lower"]) for a, b in both])
+    dup = np.array([abs(a["upper"] - b["upper"]) for a, b in both])
+    uerr = np.array([a["upper_err"] for a, _ in both])
+    fp32_vs_fp64 = {
+        "problems_compared": len(both),
+        "status_equal": sum(1 for a, b in zip(fp32_res, res64) if a["status"] == b["status"]),
+        "abs_lower_diff": {"max": float(dlo.max()), "median": float(np.median(dlo))},
+        "abs_upper_diff": {"max": float(dup.max()), "median": float(np.median(dup))},
+        "fp32_upper_err": {"max": float(uerr.max()), "median": float(np.median(uerr))},
+        "fp64": leg_summary(ms64, t64, st64, len(probs)),
+    }
 
-    # the main batch's list memory is not needed any more
+    # the main batch's memory is not needed any more
     batch.close()
     torch.cuda.synchronize()
 
-    # ---- uneven batch: 256 problems, obstacle counts log-uniform in [16, 4096] ----
-    uneven = None
-    if rank == 0 and world == 1:
-        from paper_2003_01758_b300 import workloads as W
-        counts = W.batch_obstacle_counts(256, 4000)
-        up = [W.rtd(4000 + k, n_obstacles=int(c)) for k, c in enumerate(counts)]
-        ub = pcba.Batch([pcba.Solver(q.cost, q.ineq, q.eq, q.lo, q.hi, precision=pcba.FP32)
-                         for q in up], UNEVEN_MEM)
-        tune = ub.autotune(OPT_TOL, EQ_TOL, MAX_ITERS)
-        ums, utimes, ustatus = timed_steps(ub, 3, flush)
-        uneven = {"workload": "256 rtd problems, obstacles floor(exp U(ln 16, ln 4096)), "
-                              "seeds 4000+k, FP32, one batched solve per step, %d GiB of list "
-                              "memory shared (equal item capacity)" % (UNEVEN_MEM >> 30),
-                  "value": 256 * len(ums) / (sum(ums) / 1e3), "unit": UNIT,
-                  "ms_per_step": float(np.mean(ums)),
-                  "p50_ms": float(np.median(utimes)), "p99_ms": float(np.percentile(utimes, 99)),
-                  "certified": sum(1 for s_ in ustatus if s_ in (0, 1)),
-                  "infeasible": sum(1 for s_ in ustatus if s_ == 1), "solves": len(ustatus),
-                  "autotune": tune}
-        ub.close()
-
-    # ---- learned warm start A/B: 256 held-out problems, obstacles log-uniform in
-    # [64, 1024] (the training range), seeds 6000+k: cold / learned / fixed grid ----
-    ab = None
+    side = {}
     if rank == 0 and world == 1:
         from paper_2003_01758_b300 import train_warmstart
-        ab = train_warmstart.ab_compare(learned.model, train_warmstart.held_out(256))
-        ab["workload"] = ("256 held-out rtd problems, obstacles floor(exp U(ln 64, ln 1024)), "
-                          "seeds 6000+k, FP32, one batched solve per arm and repeat; network "
-                          "trained on 100k solutions of seeds 5000000+k")
-
-    # ---- 4-D problems: 64 inequalities of degree 3, 2 equalities of degree 2,
-    # eq_tol 1e-4, 8 GiB list cap per problem, FP32 (and FP64) ----
-    dim4 = None
-    if rank == 0 and world == 1:
         from paper_2003_01758_b300 import workloads as W
+        # ---- the same 256 problems with dense constraints (a patch per
+        # obstacle), learned warm start, autotuned subdivision kernel ----
+        db = make_batch(probs, pcba.FP32, linear=False, mem_cap=DENSE_MEM)
+        tune = db.autotune(OPT_TOL, EQ_TOL, MAX_ITERS)
+        dl = Learned(db, probs)
+        dl.step()
+        dms, dtimes, dstatus, _ = dl.timed(2, flush)
+        side["dense_constraints"] = leg_summary(dms, dtimes, dstatus, len(probs))
+        side["dense_constraints"]["autotune"] = tune
+        db.close()
+        torch.cuda.synchronize()
+
+        # ---- 64 problems with 512 obstacles: linear and dense constraints
+        # (learned warm start) and the paper's plain FP64 method (dense, no
+        # warm start) ----
+        c2 = [W.rtd(2000 + j) for j in range(64)]
+        for name, linear, prec, warm in (("linear_fp32_learned", True, pcba.FP32, True),
+                                         ("dense_fp32_learned", False, pcba.FP32, True),
+                                         ("dense_fp64_plain", False, pcba.FP64, False)):
+            b2 = make_batch(c2, prec, linear=linear, mem_cap=64 << 30)
+            if warm:
+                l2 = Learned(b2, c2)
+                l2.step()
+                m2, t2, s2, _ = l2.timed(3, flush)
+            else:
+                b2.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+                m2, t2, s2, _ = timed_steps(b2, 2, flush)
+            side.setdefault("batch64_obstacles512", {})[name] = leg_summary(m2, t2, s2, 64)
+            b2.close()
+
+        # ---- the tiny problems (degree 4, 10 constraints, FP64), one at a time ----
+        tiny_ms, tiny_status = [], []
+        for j in range(32):
+            q = W.tiny(1000 + j)
+            sb = pcba.Batch([pcba.solver_from_problem(q, pcba.FP64)], 1 << 28)
+            sb.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+            r = sb.solve(OPT_TOL, EQ_TOL, MAX_ITERS)[0]
+            tiny_ms.append(sb.timing()["total_ms"])
+            tiny_status.append(r["status"])
+            sb.close()
+        side["tiny_one_at_a_time"] = {
+            "p50_ms": float(np.median(tiny_ms)), "p99_ms": float(np.percentile(tiny_ms, 99)),
+            "certified": certified(tiny_status), "solves": len(tiny_status),
+            "workload": "32 tiny POPs (seeds 1000+k): l=2, cost and 10 constraints of degree "
+                        "(4,4), FP64, each solved alone"}
+
+        # ---- one problem of the workload at a time (linear, FP32, no warm start) ----
+        single = []
+        for q in probs[:16]:
+            sb = make_batch([q], pcba.FP32, linear=True, mem_cap=4 << 30)
+            sb.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+            sb.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+            single.append(sb.timing()["total_ms"])
+            sb.close()
+        side["single_problem_ms"] = {"p50": float(np.median(single)),
+                                     "p99": float(np.percentile(single, 99))}
+
+        # ---- learned warm start A/B: 256 held-out problems, obstacles
+        # log-uniform in [64, 1024] (the training range), seeds 6000+k ----
+        ab = train_warmstart.ab_compare(learned.model, train_warmstart.held_out(256),
+                                        maker=pcba.linear_solver_from_problem)
+        ab["workload"] = ("256 held-out rtd problems, obstacles floor(exp U(ln 64, ln 1024)), "
+                          "seeds 6000+k, linear families in FP32, one batched solve per arm and "
+                          "repeat; network trained on 100k solutions of seeds 5000000+k")
+        side["learned_warm_start_ab"] = ab
+
+        # ---- 4-D problems: 64 inequalities of degree 3, 2 equalities of
+        # degree 2, eq_tol 1e-4, 8 GiB list cap per problem ----
         d4 = [W.dim4(3000 + k) for k in range(8)]
         dim4 = {"workload": "8 problems l=4, cost degree 4, 64 g_i degree 3, 2 h_j degree 2, "
                             "seeds 3000+k, eq_tol 1e-4, 8 GiB per problem",
@@ -502,37 +599,17 @@ def main():
                             "barrier-Newton polish of its points, certified solve at opt_tol "
                             "1e-3, eq_tol 1e-4 seeded with them; time and launches of all "
                             "three phases" % (RELAX_OPT_TOL, RELAX_EQ_TOL)}
-        legs = ((pcba.FP32, "fp32", False), (pcba.FP64, "fp64", False),
-                (pcba.FP32, "fp32_polished", True), (pcba.FP64, "fp64_polished", True))
-        for prec, name, polished in legs:
-            db = pcba.Batch([pcba.Solver(q.cost, q.ineq, q.eq, q.lo, q.hi, precision=prec)
-                             for q in d4], 8 * (8 << 30))
-            run = ((lambda: db.solve_polished(OPT_TOL, EQ_TOL, RELAX_OPT_TOL, RELAX_EQ_TOL,
-                                              MAX_ITERS))
-                   if polished else (lambda: db.solve(OPT_TOL, EQ_TOL, MAX_ITERS)))
-            run()
-            dms, dtimes, dstatus = timed_steps(db, 2 if not polished else 5, flush, polished)
-            dres = run()
-            cert = sum(1 for s_ in dstatus if s_ in (0, 1))
-            dim4[name] = {"value": cert / (sum(dms) / 1e3), "unit": UNIT,
-                          "certified": cert, "solves": len(dstatus),
-                          "ms_per_step": float(np.mean(dms)),
-                          "p50_ms": float(np.median(dtimes)),
-                          "p99_ms": float(np.percentile(dtimes, 99)),
-                          "status": [pcba.STATUS_NAMES.get(r["status"], r["status"]) for r in dres],
-                          "max_width": float(max(r["upper"] - r["lower"] for r in dres)),
-                          "max_abs_h": float(max(r["verify_max_abs_h"] for r in dres))}
-            db.close()
+        for prec, name in ((pcba.FP32, "fp32_polished"), (pcba.FP64, "fp64_polished")):
+            dbt = pcba.Batch([pcba.solver_from_problem(q, prec) for q in d4], 8 * (8 << 30))
+            dbt.solve_polished(OPT_TOL, EQ_TOL, RELAX_OPT_TOL, RELAX_EQ_TOL, MAX_ITERS)
+            dms4, dt4, ds4, dres = timed_steps(dbt, 5, flush, polished=True)
+            dim4[name] = leg_summary(dms4, dt4, ds4, len(d4))
+            dim4[name]["max_width"] = float(max(r["upper"] - r["lower"] for r in dres))
+            dim4[name]["max_abs_h"] = float(max(r["verify_max_abs_h"] for r in dres))
+            dbt.close()
+        side["dim4"] = dim4
 
-    # ---- one problem at a time (latency of a single solve) ----
-    single = []
-    for s in solvers[:16]:
-        sb = pcba.Batch([s], mem_cap // 8)
-        sb.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
-        sb.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
-        single.append(sb.timing()["total_ms"])
-        sb.close()
-
+    base = None
     if pool is not None:
         base = cpu_baseline(pool, cpu_procs())
         pool.shutdown()
@@ -543,7 +620,7 @@ def main():
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "problems_per_step": len(seeds),
+        "config": {"workload": WORKLOAD, "problems_per_step": len(probs),
                    "warm_start": "learned (set-encoder network, BF16 on tcgen05; %d-candidate "
                                  "stencil, then %d around the seed, certified in FP32)"
                                  % (len(learned.stencil), len(warmstart.refine_stencil())),
@@ -555,27 +632,24 @@ def main():
                       "failed": len(status) - optimal - infeasible},
         "mean_bisection_steps": float(np.mean(nsteps)),
         "no_warm_start": cold,
-        "fp64_value": fp64_value,
-        "fp64_certified": sum(1 for s in st64 if s in (0, 1)),
-        "single_problem_ms": {"p50": float(np.median(single)),
-                              "p99": float(np.percentile(single, 99)),
-                              "solves_per_s": 1e3 / float(np.mean(single))},
+        "fp32_vs_fp64": fp32_vs_fp64,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": profiled_traffic(),
-                     "kernel": "k2_subdivide_tma<float>", "peak_kind": peak_kind,
-                     "launches": it["subdiv_launches"],
-                     "algorithmic_bytes_per_launch": it["subdiv_bytes"] / max(1, it["subdiv_launches"]),
-                     "avg_launch_ms": it["subdiv_ms"] / max(1, it["subdiv_launches"])},
+                     "frac": achieved / peak,
+                     "traffic": profiled_traffic("pcba_linear.cuh", "k2_lin_uneven256_fp32.md"),
+                     "kernel": "k2_lin_split + k2_lin_bound (one subdivision step)",
+                     "peak_kind": peak_kind, "launches": it["subdiv_launches"],
+                     "algorithmic_bytes_per_launch":
+                         it["subdiv_bytes"] / max(1, it["subdiv_launches"]),
+                     "avg_launch_ms": it["subdiv_ms"] / max(1, it["subdiv_launches"]),
+                     "constraint_bounds": lin["pairs"], "coefficient_ranges": lin["full"]},
         "cpu_baseline": base,
         "e2e": {"value": e2e_value, "unit": UNIT,
                 "h2d_bytes_per_step": e2e_stats["h2d_bytes"] + torch_h2d,
                 "d2h_bytes_per_step": e2e_stats["d2h_bytes"]},
-        "uneven_batch": uneven,
-        "learned_warm_start_ab": ab,
-        "dim4": dim4,
         "gpu_launches": launches,
         "clocks": clk,
     }
+    line.update(side)
     print(json.dumps(line))
     return 0
 

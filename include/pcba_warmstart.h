@@ -120,6 +120,16 @@ int pcba_batch_set_refine_stencil(pcba_batch* b, int round, const double* stenci
  * Pageable host memory makes the copy synchronous. */
 int pcba_batch_upload(pcba_batch* b, const double* host_coeffs);
 
+/* The same for the constraint rows of a batch of linear-family problems
+ * (pcba_create_linear): pcba_batch_rows_doubles(b) doubles, per problem in
+ * batch order and per constraint the row (offset, weight_0 .. weight_K-1)
+ * padded with zeros to PCBA_LIN_STRIDE (8) doubles.  The library keeps the
+ * FP64 rows and their FP32 roundings (made on the device); queued on the
+ * batch's stream, counted in the next solve's host-to-device bytes.
+ * PCBA_ERR_INVALID for a dense batch. */
+int pcba_batch_upload_rows(pcba_batch* b, const double* host_rows);
+long long pcba_batch_rows_doubles(const pcba_batch* b);
+
 /* The incumbent seed of problem k in the last solve of the batch: returns 1
  * if a candidate (or the warm start point) was certified feasible, writing it
  * (nvars coordinates) to x and its certified cost bound - the initial p_up -

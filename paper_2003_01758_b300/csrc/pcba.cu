@@ -230,6 +230,7 @@ struct pcba_batch {
   long long h2d_bytes = 0, d2h_bytes = 0;
   long long pending_h2d = 0;      // bytes queued by pcba_batch_upload since the last solve
   long long extra_launches = 0;   // prologue kernels of warm starts in the last solve
+  long long extra_launches_pending = 0;  // kernels queued by uploads since the last solve
   std::vector<double> launch_bytes;
 };
 
@@ -866,7 +867,8 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
                  (guide ? 8LL * b->refine_total() * b->refine_dim : 0) + b->pending_h2d;
   b->pending_h2d = 0;
   const bool have_warm = warm || b->warm_on_device;
-  b->extra_launches = (guide || have_warm ? 1 : 0) + (guide ? 1 : 0);
+  b->extra_launches = (guide || have_warm ? 1 : 0) + (guide ? 1 : 0) + b->extra_launches_pending;
+  b->extra_launches_pending = 0;
   b->d2h_bytes = (long long)(sizeof(ProbState) + sizeof(EvalOut)) * n + (long long)sizeof(Plan);
   if (host_coeffs)
     PCBA_CK(cudaMemcpyAsync(b->d_mono, host_coeffs, sizeof(double) * b->mono_doubles,
@@ -1375,6 +1377,25 @@ int pcba_batch_upload(pcba_batch* b, const double* host_coeffs) {
                           cudaMemcpyHostToDevice, b->stream));
   b->pending_h2d += 8LL * b->mono_doubles;
   return 0;
+}
+
+int pcba_batch_upload_rows(pcba_batch* b, const double* host_rows) {
+  if (!b || !host_rows) return fail(PCBA_ERR_INVALID, "batch or host_rows is null");
+  if (!b->lin) return fail(PCBA_ERR_INVALID, "the batch has no linear-family constraints");
+  const long long n = (long long)PCBA_LIN_STRIDE * b->lin_rows;
+  if (n == 0) return 0;
+  PCBA_CK(cudaMemcpyAsync(b->d_lin64, host_rows, sizeof(double) * n, cudaMemcpyHostToDevice,
+                          b->stream));
+  const unsigned g = (unsigned)std::min<long long>((n + 255) / 256, 4LL * b->g.sms);
+  k_rows32<<<g, 256, 0, b->stream>>>(b->d_lin64, b->d_lin32, n);
+  PCBA_CK(cudaGetLastError());
+  b->pending_h2d += 8LL * n;
+  b->extra_launches_pending += 1;
+  return 0;
+}
+
+long long pcba_batch_rows_doubles(const pcba_batch* b) {
+  return b ? (long long)PCBA_LIN_STRIDE * b->lin_rows : 0;
 }
 
 int pcba_batch_warm_point(const pcba_batch* b, int k, double* x, double* cost) {

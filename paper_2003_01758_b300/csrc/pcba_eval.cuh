@@ -32,6 +32,13 @@ __global__ void k_mono32(const double* mono, float* out, long long n) {
     out[i] = __double2float_rn(mono[i]);
 }
 
+// FP32 copy (round to nearest) of the linear-family constraint rows
+__global__ void k_rows32(const double* rows, float* out, long long n) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x)
+    out[i] = __double2float_rn(rows[i]);
+}
+
 #define PCBA_EVAL_CHUNK 8
 #define PCBA_MAX_CAND 1024
 #define PCBA_CAND_TPB 512  // threads of k_cand_first

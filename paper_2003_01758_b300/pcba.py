@@ -101,6 +101,8 @@ def lib():
         "pcba_create_linear": ([P, P, P, P, I], I),
         "pcba_get_active": ([P, P, LL], I),
         "pcba_batch_linear_stats": ([P, P, P, P], I),
+        "pcba_batch_upload_rows": ([P, P], I),
+        "pcba_batch_rows_doubles": ([P], LL),
         "pcba_batch_polish": ([P, D, D, D, I, P], I),
         "pcba_batch_solve_polished": ([P, D, D, D, D, I, P], I),
         "pcba_batch_destroy": ([P], None),
@@ -154,7 +156,7 @@ def exported_symbols():
             "pcba_mlp_get_params", "pcba_mlp_forward", "pcba_mlp_gradient",
             "pcba_mlp_train_step", "pcba_set_time_limit", "pcba_batch_set_time_limit",
             "pcba_eval_points_f32", "pcba_create_linear", "pcba_get_active",
-            "pcba_batch_linear_stats"]
+            "pcba_batch_linear_stats", "pcba_batch_upload_rows", "pcba_batch_rows_doubles"]
 
 
 def _check(rc):
@@ -354,6 +356,22 @@ class LinearSolver(Solver):
         return b[:, :self.n_lin].astype(bool)
 
 
+LIN_STRIDE = 8
+
+
+def linear_rows(problems):
+    """Host layout of pcba_batch_upload_rows for workloads problems with a
+    linear form: per constraint (offset, weights..., zero padding)."""
+    blocks = []
+    for prob in problems:
+        _, weight, offset = prob.meta["linear"]
+        r = np.zeros((offset.shape[0], LIN_STRIDE))
+        r[:, 0] = offset
+        r[:, 1:1 + weight.shape[1]] = weight
+        blocks.append(r.ravel())
+    return np.ascontiguousarray(np.concatenate(blocks), dtype=np.float64)
+
+
 def linear_solver_from_problem(prob, precision=FP32):
     """LinearSolver of a workloads problem that carries its linear form
     (meta["linear"] = (shared, weight, offset))."""
@@ -491,6 +509,15 @@ class Batch:
         """pcba_batch_upload: queue the host->device copy of all coefficients."""
         assert host_coeffs.dtype == np.float64 and host_coeffs.size == self.input_doubles()
         _check(lib().pcba_batch_upload(self._b, _p(host_coeffs)))
+
+    def upload_rows(self, host_rows):
+        """pcba_batch_upload_rows: queue the host->device copy of the linear
+        constraint rows (see linear_rows)."""
+        assert host_rows.dtype == np.float64 and host_rows.size == self.rows_doubles()
+        _check(lib().pcba_batch_upload_rows(self._b, _p(host_rows)))
+
+    def rows_doubles(self) -> int:
+        return int(lib().pcba_batch_rows_doubles(self._b))
 
     def cost_grid(self, G, out_ptr, ld, col0=0):
         """pcba_batch_cost_grid into a device float buffer (queued on the batch stream)."""

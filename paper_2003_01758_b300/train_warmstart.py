@@ -30,13 +30,14 @@ def held_out(n, lo=64, hi=1024):
     return [W.rtd(warmstart.EVAL_SEED0 + k, n_obstacles=int(c)) for k, c in enumerate(counts)]
 
 
-def ab_compare(mlp, probs, mem_cap_total=64 << 30, repeats=3):
+def ab_compare(mlp, probs, mem_cap_total=64 << 30, repeats=3, maker=None):
     """One batch solved three ways: cold (the plain solver), learned (network
     guess + default stencil, then the refinement stencil around the seed;
     device time includes the feature kernel and the network's forward pass) and
     grid (a fixed 25 x 25 grid of candidates, then the same refinement, no
     network: what the learned arm must beat to be worth its training)."""
-    b = pcba.Batch([pcba.solver_from_problem(p, pcba.FP32) for p in probs], mem_cap_total)
+    maker = maker or pcba.solver_from_problem
+    b = pcba.Batch([maker(p, pcba.FP32) for p in probs], mem_cap_total)
     stream = torch.cuda.Stream()
     refine = warmstart.refine_stencil()
     b.set_stream(stream.cuda_stream)

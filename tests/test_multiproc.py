@@ -35,7 +35,8 @@ def _worker(rank, world, port, out):
     try:
         seeds = bench.shard_seeds(rank)
         mx = bench.reduce_max(10.0 + rank, world)
-        out.put((rank, seeds, mx))
+        total = bench.reduce_sum(1.0 + rank, world)
+        out.put((rank, seeds, mx, total))
     finally:
         dist.destroy_process_group()
 
@@ -54,9 +55,11 @@ def test_two_ranks_shard_disjoint_problems_and_agree_on_the_max():
         assert p.exitcode == 0
     res.sort()
     s0, s1 = set(res[0][1]), set(res[1][1])
-    assert len(s0) == len(s1) == 64 and not (s0 & s1)
-    assert min(s0) == 2000 and min(s1) == 2064
+    assert len(s0) == len(s1) == 256 and not (s0 & s1)
+    assert min(s0) == 4000 and min(s1) == 4256
     assert res[0][2] == res[1][2] == 11.0
+    # certified solves are summed over ranks (the whole-job value)
+    assert res[0][3] == res[1][3] == 3.0
 
 
 _PORT = None
