@@ -182,6 +182,7 @@ struct pcba_batch {
   double* d_stencil = nullptr;  // guided solves: [stencil_cap] doubles
   double* d_polish = nullptr;   // pcba_batch_polish output: [np][PCBA_MAXD]
   float* d_lin32 = nullptr;     // linear families: [lin_rows][PCBA_LIN_STRIDE] (c, w_0..w_K-1) in FP32
+  uint2* d_lin_queue = nullptr; // linear families: heavy (item, chunk) units of a step
   double* d_lin64 = nullptr;    // the same in FP64
   // pcba_batch_solve_polished: the warm points are already in d_warm (written
   // by the polish kernel), and the counts of the phases before the last solve
@@ -367,7 +368,7 @@ void free_batch(pcba_batch* b) {
                  b->d_slots, b->d_tilecnt, b->d_mono, b->d_trace, b->d_warm, b->d_mat,
                  b->d_raw, b->d_eval, b->d_tmaps, b->d_marks, b->d_cand, b->d_stencil,
                  b->d_mono32, b->d_ckey, b->d_corder, b->d_cres, b->d_polish, b->d_lin32,
-                 b->d_lin64};
+                 b->d_lin64, b->d_lin_queue};
   for (void* p : dev)
     if (p) cudaFree(p);
   void* host[] = {b->h_state, b->h_eval, b->h_plan, b->h_params, b->h_running};
@@ -710,6 +711,14 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   PCBA_ALLOC(b->d_eval, sizeof(EvalOut) * n);
   PCBA_ALLOC(b->d_lin32, sizeof(float) * PCBA_LIN_STRIDE * std::max<long long>(lin_rows, 1));
   PCBA_ALLOC(b->d_lin64, sizeof(double) * PCBA_LIN_STRIDE * std::max<long long>(lin_rows, 1));
+  // queue of heavy (item, chunk) units: every item of every problem with all
+  // its chunks, at most 4 Mi entries (a full queue leaves units to the split)
+  long long qcap = 0;
+  if (b->lin)
+    for (int k = 0; k < n; ++k)
+      qcap = std::min<long long>(qcap + (long long)std::max<long long>(M, 2) *
+                                            b->desc[k].lin_chunks, 1LL << 22);
+  PCBA_ALLOC(b->d_lin_queue, sizeof(uint2) * std::max<long long>(qcap, 1));
   const unsigned mark_cap = 1u << 20;  // marked patches per step (extra marks are dropped)
   PCBA_ALLOC(b->d_marks, sizeof(uint4) * 2 * (prec == PCBA_FP32 ? mark_cap : 1));
 #undef PCBA_ALLOC
@@ -819,6 +828,8 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   E.root_raw = nullptr;
   E.lin32 = b->d_lin32;
   E.lin64 = b->d_lin64;
+  E.lin_queue = b->d_lin_queue;
+  E.lin_qcap = (unsigned)qcap;
   rc = prec == PCBA_FP32 ? setup_kernels<float>(b) : setup_kernels<double>(b);
   if (!rc) rc = apply_k2_config(b, (b->want_tma && b->g.k2.cfgs.size() > 1) ? 1 : 0);
   if (!rc && (flags & 3) == 0) rc = prec == PCBA_FP32 ? build_graph<float>(b) : build_graph<double>(b);

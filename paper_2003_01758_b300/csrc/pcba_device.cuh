@@ -45,6 +45,7 @@
 #define PCBA_LIN_WORDS 8     // activity words (256 constraints) per linear subdivision unit
 #define PCBA_LIN_STRIDE 8    // floats / doubles per linear constraint row (c, w_0 .. w_K-1)
 #define PCBA_LIN_BATCH 4     // units a warp of the linear subdivision kernel fetches at once
+#define PCBA_LIN_LIGHT 2     // items with at most this many live chunks are bounded by the split
 
 struct ProbDesc {
   int l;
@@ -150,6 +151,7 @@ struct Plan {
   unsigned long long lin_full;   // of which bounded from the coefficient range (not the interval)
   unsigned lin_next;             // next unit of the linear bound kernel to hand out
   unsigned lin_next2;            // next item of the linear split kernel to hand out
+  unsigned lin_qcount;           // (item, chunk) units queued for the linear bound kernel
   unsigned k3_done;
   unsigned k4_done;             // blocks of k_move_control finished (the last one runs the control)
   int any_running;
@@ -189,6 +191,8 @@ struct Engine {
   double* root_raw;        // optional FP64 root patch dump
   const unsigned* k1_pre;  // [np + 1] patches per problem prefix
   const void* tmaps;       // [np][2] tensor maps (CUtensorMap) of the g / h blocks, or null
+  uint2* lin_queue;        // linear families: (item, chunk) units of heavy items, this step
+  unsigned lin_qcap;       // its capacity (a full queue leaves the units to the split kernel)
   const float* lin32;      // linear families: constraint rows in FP32 (round to nearest)
   const double* lin64;     // the same in FP64
 };

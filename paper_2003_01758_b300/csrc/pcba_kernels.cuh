@@ -800,6 +800,7 @@ __device__ __forceinline__ void control_phase(const Engine& E, cudaGraphConditio
     pl->marks_total += min(pl->mark_count[pl->steps_global & 1], E.mark_cap);
     pl->lin_next = 0u;
     pl->lin_next2 = 0u;
+    pl->lin_qcount = 0u;
     pl->mark_count[pl->steps_global & 1] = 0u;
     if (did) pl->steps_global += 1;
     const int running = pl->any_running;
@@ -957,6 +958,7 @@ __global__ void k_init(Engine E) {
     pl->lin_full = 0ull;
     pl->lin_next = 0u;
     pl->lin_next2 = 0u;
+    pl->lin_qcount = 0u;
     E.kr_pre[E.np] = runr;
     pl->k3_done = 0;
     pl->k4_done = 0u;

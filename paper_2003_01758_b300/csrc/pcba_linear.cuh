@@ -36,21 +36,27 @@
 // mode stores plain patches, O_m = 0, and is plain arithmetic as the paper's.)
 //
 // Two kernels per bisection step:
-//   k2_lin_split   one thread per parent item: splits the cost patch and the K
-//                  shared patches (de Casteljau at 1/2, Sec. II-E) into the two
-//                  children, re-centres every FP32 child patch on the middle of
-//                  its range, and stores per child and patch the extremes of
-//                  the stored values (with their error bound and offset), the
-//                  box and the slot map; the cost bounds go to the child
-//                  records.  The children's shared patches go to the copy of
-//                  the other parity, so the parent's stay readable.
-//   k2_lin_bound   one warp per (parent item, chunk of PCBA_LIN_WORDS activity
-//                  words): compacts the chunk's active constraints and bounds
-//                  each on both children from the stored extremes (interval
-//                  bound) or, where that is undecided, from the children's
-//                  coefficients; writes the children's activity words and the
-//                  chunk's summary bits, and publishes the bound maxima with
-//                  one atomic per warp.
+//   k2_lin_split   one warp per parent item (items fetched in batches from a
+//                  counter): splits the cost patch and the K shared patches
+//                  (de Casteljau at 1/2, Sec. II-E) into the two children, a
+//                  lane per fibre, re-centres every FP32 child patch on the
+//                  middle of its range, and stores per child and patch the
+//                  extremes of the stored values (with their error bound and
+//                  offset), the box and the slot map; the cost bounds go to
+//                  the child records.  The children's shared patches go to the
+//                  copy of the other parity, so the parent's stay readable.
+//                  The constraints of an item with at most PCBA_LIN_LIGHT live
+//                  chunks (chunks of PCBA_LIN_WORDS activity words with an
+//                  active constraint) are bounded here from the children
+//                  still staged in shared memory; the live chunks of the other
+//                  items are queued as (item, chunk).
+//   k2_lin_bound   one warp per queued (item, chunk): stages both children and
+//                  bounds the chunk's constraints as the split kernel does.
+// Bounding a chunk compacts its active constraints and bounds each on both
+// children from the stored extremes (interval bound) or, where that is
+// undecided, from the children's coefficients; it writes the children's
+// activity words and the chunk's summary bits, and publishes the bound maxima
+// with one atomic per warp.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -150,12 +156,250 @@ __device__ __forceinline__ void lin_mark(const Engine& E, int mpar, int p, int s
 }
 
 
-// Bytes of shared memory one warp of k2_lin_split uses: the parent's cost
-// patch and its two children, the parent's shared patches and their two
-// children (coefficient-major, 4 slots per coefficient).
+// ---------------------------------------------------------------------------
+// k2_lin_bound: one warp per (parent item, chunk of activity words)
+// ---------------------------------------------------------------------------
+
+// Bytes of shared memory one warp of k2_lin_bound uses: both children's
+// shared patches ([C][4] each), the compacted constraint indices and the
+// children's activity words.
+template <typename T>
+__host__ __device__ constexpr size_t lin_bound_warp_bytes(int cgmax) {
+  return (8 * (size_t)cgmax * sizeof(T) + 32 * PCBA_LIN_WORDS * sizeof(unsigned short) +
+          2 * PCBA_LIN_WORDS * sizeof(unsigned) + 15) / 16 * 16;
+}
+
+// Coefficient range of cc + sum_m w_m s_mj over the C coefficients of one
+// child staged in shared memory ([C][4]); two partial extremes per bound.
+template <typename T, int K>
+__device__ __forceinline__ void lin_range(const T* s, int C, T cc, const T (&w)[K], T& lo, T& hi) {
+  T lo0 = T(INFINITY), hi0 = T(-INFINITY), lo1 = T(INFINITY), hi1 = T(-INFINITY);
+  int j = 0;
+#pragma unroll 2
+  for (; j + 1 < C; j += 2) {
+    T a[K], b[K];
+    lin_load<T, K>(s + (size_t)j * 4, a);
+    lin_load<T, K>(s + (size_t)(j + 1) * 4, b);
+    T v0 = cc, v1 = cc;
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+      v0 = fma(w[m], a[m], v0);
+      v1 = fma(w[m], b[m], v1);
+    }
+    lo0 = min(lo0, v0);
+    hi0 = max(hi0, v0);
+    lo1 = min(lo1, v1);
+    hi1 = max(hi1, v1);
+  }
+  if (j < C) {
+    T a[K];
+    lin_load<T, K>(s + (size_t)j * 4, a);
+    T v0 = cc;
+#pragma unroll
+    for (int m = 0; m < K; ++m) v0 = fma(w[m], a[m], v0);
+    lo0 = min(lo0, v0);
+    hi0 = max(hi0, v0);
+  }
+  lo = min(lo0, lo1);
+  hi = max(hi0, hi1);
+}
+
+// Both children's metadata (the same in every lane): extremes of the stored
+// values of each shared patch and, in FP32, their error bounds and offsets.
+template <typename T, int K>
+struct LinChildren {
+  T mn[2][K], mx[2][K];
+  float Mabs[2][K], ec[2][K];
+  double O[2][K];
+};
+
+// Chunk t of the activity words of parent item k (problem p, list length Kl):
+// its active constraints are compacted and bounded on both children (shared
+// patches staged at sL / sR, [C][4]), the children's words and the chunk's
+// summary bits are written and the bound maxima go to the child records.  One
+// warp; sIdx / sMw are its compaction and word buffers.
+template <typename T, int K>
+__device__ void lin_chunk(const Engine& E, const ProbDesc* D, int p, int k, int Kl, int t,
+                          char* left, char* right, const T* sL, const T* sR,
+                          const LinChildren<T, K>& ch, unsigned short* sIdx, unsigned* sMw,
+                          int par) {
+  constexpr bool RIG = sizeof(T) == 4;
+  constexpr float u24 = 0x1p-24f;
+  const int lane = threadIdx.x & 31;
+  const long long slot_off = D->slot_off;
+  const int C = D->cg, mwords = D->mwords;
+  const int w0 = t * PCBA_LIN_WORDS;
+  const int nw = min(PCBA_LIN_WORDS, mwords - w0);
+  unsigned* pm = (unsigned*)(left + D->off_mask) + w0;  // the parent's words, in place
+  unsigned* rm = (unsigned*)(right + D->off_mask) + w0;
+  unsigned long long* sumL = (unsigned long long*)(left + D->off_sum) + (par ^ 1);
+  unsigned long long* sumR = (unsigned long long*)(right + D->off_sum) + (par ^ 1);
+  const unsigned long long tb = D->lin_chunks <= 64 ? (1ull << t) : 0ull;
+  const unsigned word = lane < nw ? pm[lane] : 0u;
+  const unsigned cnt = __popc(word);
+  unsigned incl = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += y;
+  }
+  const unsigned na = __shfl_sync(0xffffffffu, incl, 31);
+  if (na == 0) {
+    // no active constraint here: the children's words are zero (the left
+    // child shares the parent's, already zero)
+    if (lane < nw) rm[lane] = 0u;
+    return;
+  }
+  __syncwarp();  // earlier readers of sIdx and sMw are done
+  {
+    unsigned pos = incl - cnt, bits = word;
+    while (bits) {
+      const int b = __ffs(bits) - 1;
+      bits &= bits - 1u;
+      sIdx[pos++] = (unsigned short)(lane * 32 + b);
+    }
+  }
+  if (lane < 2 * PCBA_LIN_WORDS) sMw[lane] = 0u;
+  __syncwarp();
+  T gmax[2] = {T(-INFINITY), T(-INFINITY)}, gmin[2] = {T(-INFINITY), T(-INFINITY)};
+  bool mark[2] = {false, false};
+  unsigned nfull = 0;  // coefficient-range evaluations of this lane
+  const int Kw = K;
+  for (unsigned q = lane; q < na; q += 32) {
+    const int li = sIdx[q];
+    const long long row = (D->lin_off + (long long)w0 * 32 + li) * PCBA_LIN_STRIDE;
+    const double* rw = E.lin64 + row;
+    T w[K], cc[2];
+    float E64[2] = {0.0f, 0.0f};  // FP32: bound of the FP64 constant term
+    if constexpr (RIG) {
+      const float4 r0 = *(const float4*)(E.lin32 + row);
+      const float4 r1 = *(const float4*)(E.lin32 + row + 4);
+      const float rr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+      for (int m = 0; m < K; ++m) w[m] = rr[1 + m];
+      // the constant term c_i + sum_m w_im O_m of each child's
+      // coefficients relative to its offsets, in FP64 from the FP64 row:
+      // the large terms cancel here, and the FP32 part only carries the
+      // residuals (of the order of the box's range)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) {
+        double kap = rw[0], a64 = fabs(rw[0]);
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          kap = fma(rw[1 + m], ch.O[c][m], kap);
+          a64 = fma(fabs(rw[1 + m]), fabs(ch.O[c][m]), a64);
+        }
+        cc[c] = (T)kap;
+        E64[c] = __double2float_ru(__dmul_ru(a64, 0x1p-50));
+      }
+    } else {
+#pragma unroll
+      for (int m = 0; m < K; ++m) w[m] = (T)rw[1 + m];
+      cc[0] = cc[1] = (T)rw[0];
+    }
+    // E of the comment at the top of this file (0 in FP64 mode), and the
+    // interval bound from the ranges of the stored patches, per child
+    float Ee[2] = {0.0f, 0.0f}, Er[2] = {0.0f, 0.0f};
+    T lo[2], hi[2], Et[2];
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      float Eb = 0.0f;
+      if constexpr (RIG) {
+        float A = fabsf((float)cc[c]), ee = 0.0f;
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+          A = __fmaf_ru(fabsf((float)w[m]), ch.Mabs[c][m], A);
+          ee = __fmaf_ru(fabsf((float)w[m]), ch.ec[c][m], ee);
+        }
+        const float kk = (float)(2 * Kw + 2);
+        Er[c] = __fmul_ru((kk + 1.0f) * u24, A);
+        Ee[c] = ee;
+        Eb = __fadd_ru(__fadd_ru(__fadd_ru(Er[c], __fmul_ru(ee, 1.0f + 0x1p-20f)), E64[c]),
+                       kk * 0x1p-149f);
+      }
+      Et[c] = T(Eb);
+      T x0 = cc[c], x1 = cc[c];
+#pragma unroll
+      for (int m = 0; m < K; ++m) {
+        const T x = w[m] * ch.mn[c][m], y = w[m] * ch.mx[c][m];
+        x0 += min(x, y);
+        x1 += max(x, y);
+      }
+      lo[c] = x0;
+      hi[c] = x1;
+    }
+    // undecided by the interval: the coefficient range itself (Alg. 3)
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      if (!(add_up(hi[c], Et[c]) <= T(0)) && !(sub_dn(lo[c], Et[c]) > T(0))) {
+        lin_range<T, K>(c ? sR : sL, C, cc[c], w, lo[c], hi[c]);
+        ++nfull;
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < 2; ++c) {
+      const T up = add_up(hi[c], Et[c]), dn = sub_dn(lo[c], Et[c]);
+      const bool sat = up <= T(0);
+      const bool inf = dn > T(0);
+      if (!sat) {
+        atomicOr(&sMw[c * PCBA_LIN_WORDS + (li >> 5)], 1u << (li & 31));
+        gmax[c] = max(gmax[c], up);
+        gmin[c] = max(gmin[c], dn);
+      }
+      if constexpr (RIG) {
+        // the bound changed a decision the stored coefficients make: mark
+        // the child's shared patches for a refresh if their errors are
+        // the larger part of the bound
+        const bool flip = (hi[c] <= T(0)) != sat || (lo[c] > T(0)) != inf;
+        if (flip && Ee[c] > Er[c]) mark[c] = true;
+      }
+    }
+  }
+  __syncwarp();
+  if (lane < nw) {
+    pm[lane] = sMw[lane];                      // left child: in place (this unit's words)
+    rm[lane] = sMw[PCBA_LIN_WORDS + lane];     // right child
+  }
+  const bool keepL = __any_sync(0xffffffffu, lane < nw && sMw[lane] != 0u);
+  const bool keepR = __any_sync(0xffffffffu, lane < nw && sMw[PCBA_LIN_WORDS + lane] != 0u);
+  if (lane == 0) {
+    if (tb) {
+      if (keepL) atomicOr(sumL, tb);
+      if (keepR) atomicOr(sumR, tb);
+    }
+    atomicAdd(&E.plan->lin_pairs, 2ull * na);
+  }
+  const unsigned full = __reduce_add_sync(0xffffffffu, nfull);
+  if (lane == 0) atomicAdd(&E.plan->lin_full, (unsigned long long)full);
+#pragma unroll
+  for (int c = 0; c < 2; ++c) {
+    const T gx = lin_wmax(gmax[c]);
+    const T gn = lin_wmax(gmin[c]);
+    ChildRec* rc = E.rec + slot_off + k + (c ? Kl : 0);
+    if (lane == 0 && gx > T(-INFINITY)) {
+      atomicMax(&rc->gmaxmax, okey((double)gx));
+      atomicMax(&rc->gminmax, okey((double)gn));
+    }
+  }
+  if constexpr (RIG) {
+    const MarkCtx mk{p, k, k + Kl, E.marks + (size_t)par * E.mark_cap,
+                     &E.plan->mark_count[par], E.mark_cap};
+    const bool bl = __any_sync(0xffffffffu, mark[0]);
+    const bool br = __any_sync(0xffffffffu, mark[1]);
+    append_marks(mk, bl && lane < K, br && lane < K, 0, lane);
+  }
+  __syncwarp();
+}
+
+// Bytes of shared memory one warp of k2_lin_split uses: the parent's shared
+// patches and their two children (coefficient-major, 4 slots per
+// coefficient), the parent's cost patch and its two children, then the
+// compacted constraint indices and the children's activity words of one chunk.
 template <typename T>
 __host__ __device__ constexpr size_t lin_split_warp_bytes(int cgmax, int cpmax) {
-  return ((3 * (size_t)cpmax + 12 * (size_t)cgmax) * sizeof(T) + 15) / 16 * 16;
+  return ((3 * (size_t)cpmax + 12 * (size_t)cgmax) * sizeof(T) +
+          32 * PCBA_LIN_WORDS * sizeof(unsigned short) + 2 * PCBA_LIN_WORDS * sizeof(unsigned) +
+          15) / 16 * 16;
 }
 
 // Extremes of the two children of one patch group (the cost, or one shared
@@ -207,12 +451,16 @@ __global__ void __launch_bounds__(256, 3) k2_lin_split(Engine E, int cgmax, int 
   constexpr float u24 = 0x1p-24f;
   extern __shared__ __align__(16) unsigned char kls[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  T* sc = (T*)(kls + (size_t)warp * lin_split_warp_bytes<T>(cgmax, cpmax));  // parent cost
-  T* scL = sc + cpmax;
-  T* scR = scL + cpmax;
-  T* sp = scR + cpmax;             // parent shared patches [C][4]
+  // the shared patches first: their 16-byte vector loads need the warp's
+  // (16-byte aligned) base, whatever the cost patch's size
+  T* sp = (T*)(kls + (size_t)warp * lin_split_warp_bytes<T>(cgmax, cpmax));  // [C][4]
   T* spL = sp + 4 * (size_t)cgmax;
   T* spR = spL + 4 * (size_t)cgmax;
+  T* sc = spR + 4 * (size_t)cgmax;  // parent cost patch and its children
+  T* scL = sc + cpmax;
+  T* scR = scL + cpmax;
+  unsigned short* sIdx = (unsigned short*)(scR + cpmax);
+  unsigned* sMw = (unsigned*)(sIdx + 32 * PCBA_LIN_WORDS);
   const unsigned items = E.plan->kr_units;
   const int par = E.plan->steps_global & 1;  // copy read this step; children go to par ^ 1
   const double cost_thr = E.params->opt_tol * (1.0 / 64.0);
@@ -370,6 +618,7 @@ __global__ void __launch_bounds__(256, 3) k2_lin_split(Engine E, int cgmax, int 
       }
       // ---- shared children, re-centred likewise, to the other copy, with
       // their metadata (error bound, offset, extremes of the stored values)
+      LinChildren<T, K> ch;
       if (any) {
         T sh[2][K];
 #pragma unroll
@@ -391,36 +640,94 @@ __global__ void __launch_bounds__(256, 3) k2_lin_split(Engine E, int cgmax, int 
               a1 = sh[1][g];
             }
           if (m < K) {
-            gL[e] = addrn(spL[e], -a0);
-            gR[e] = addrn(spR[e], -a1);
+            // the stored values, kept staged for the constraint bounds below
+            const T vl = addrn(spL[e], -a0), vr = addrn(spR[e], -a1);
+            gL[e] = vl;
+            gR[e] = vr;
+            spL[e] = vl;
+            spR[e] = vr;
           }
         }
+        // the children's metadata (every lane computes it; it is also what
+        // the bound of the constraints below uses)
+#pragma unroll
+        for (int c = 0; c < 2; ++c)
+#pragma unroll
+          for (int g = 0; g < K; ++g) {
+            const T mn0 = c ? acc[1 + g].mnR : acc[1 + g].mnL;
+            const T mx0 = c ? acc[1 + g].mxR : acc[1 + g].mxL;
+            if constexpr (RIG) {
+              const float e1 = __fadd_ru(
+                  __fadd_ru(em[g], __fmul_ru((float)acc[1 + g].am, (float)ns * u24)),
+                  (float)ns * 0x1p-149f);
+              const float smin = __fsub_rn((float)mn0, (float)sh[c][g]);
+              const float smax = __fsub_rn((float)mx0, (float)sh[c][g]);
+              const float Mr = fmaxf(fabsf(smin), fabsf(smax));
+              ch.O[c][g] = Om[g] + (double)sh[c][g];
+              ch.ec[c][g] = __fadd_ru(__fadd_ru(__fadd_ru(e1, __fmul_ru(Mr, u24)), 0x1p-149f),
+                                      __double2float_ru(__dmul_ru(fabs(ch.O[c][g]), 0x1p-52)));
+              ch.mn[c][g] = T(smin);
+              ch.mx[c][g] = T(smax);
+              ch.Mabs[c][g] = Mr;
+            } else {
+              ch.O[c][g] = 0.0;
+              ch.ec[c][g] = 0.0f;
+              ch.mn[c][g] = mn0;
+              ch.mx[c][g] = mx0;
+              ch.Mabs[c][g] = 0.0f;
+            }
+          }
         if (lane < 2 * K) {
           const int c = lane / K, g0 = lane - c * K;
           char* cm = (c ? right : parent) + D->off_eg + (par ^ 1) * D->copy_e;
 #pragma unroll
-          for (int g = 0; g < K; ++g) {
-            if (g != g0) continue;
-            const T mn0 = c ? acc[1 + g].mnR : acc[1 + g].mnL;
-            const T mx0 = c ? acc[1 + g].mxR : acc[1 + g].mxL;
-            if constexpr (RIG) {
-              const float e1 = __fadd_ru(__fadd_ru(em[g], __fmul_ru((float)acc[1 + g].am, (float)ns * u24)),
-                                         (float)ns * 0x1p-149f);
-              const float smin = __fsub_rn((float)mn0, (float)sh[c][g]);
-              const float smax = __fsub_rn((float)mx0, (float)sh[c][g]);
-              const float Mr = fmaxf(fabsf(smin), fabsf(smax));
-              const double On = Om[g] + (double)sh[c][g];
-              LinMeta<T>::err(cm, 4)[g] =
-                  __fadd_ru(__fadd_ru(__fadd_ru(e1, __fmul_ru(Mr, u24)), 0x1p-149f),
-                            __double2float_ru(__dmul_ru(fabs(On), 0x1p-52)));
-              LinMeta<T>::off(cm, 4)[g] = On;
-              LinMeta<T>::mn(cm, 4)[g] = T(smin);
-              LinMeta<T>::mx(cm, 4)[g] = T(smax);
-            } else {
-              LinMeta<T>::mn(cm, 4)[g] = mn0;
-              LinMeta<T>::mx(cm, 4)[g] = mx0;
+          for (int cc = 0; cc < 2; ++cc)
+#pragma unroll
+            for (int g = 0; g < K; ++g) {
+              if (g != g0 || cc != c) continue;
+              if constexpr (RIG) {
+                LinMeta<T>::err(cm, 4)[g] = ch.ec[cc][g];
+                LinMeta<T>::off(cm, 4)[g] = ch.O[cc][g];
+              }
+              LinMeta<T>::mn(cm, 4)[g] = ch.mn[cc][g];
+              LinMeta<T>::mx(cm, 4)[g] = ch.mx[cc][g];
+            }
+        }
+        __syncwarp();
+      }
+      // ---- the constraints.  The children's summaries start empty (each live
+      // chunk sets its bits) and their words of chunks without an active
+      // constraint are zero; an item with few live chunks is bounded here,
+      // from the staged children, the live chunks of the others go to the
+      // bound kernel's queue (or stay here when it is full)
+      {
+        // (more than 64 chunks keep no summaries: every chunk is read)
+        const int chunks = D->lin_chunks;
+        const bool summ = chunks <= 64;
+        const unsigned long long psum =
+            summ ? *((const unsigned long long*)(parent + D->off_sum) + par) : 0ull;
+        auto live = [&](int t) { return summ ? ((psum >> t) & 1ull) != 0ull : true; };
+        if (lane == 0 && summ) {
+          *((unsigned long long*)(parent + D->off_sum) + (par ^ 1)) = 0ull;
+          *((unsigned long long*)(right + D->off_sum) + (par ^ 1)) = 0ull;
+        }
+        unsigned* rmask = (unsigned*)(right + D->off_mask);
+        for (int q = lane; q < D->mwords; q += 32)
+          if (!live(q / PCBA_LIN_WORDS)) rmask[q] = 0u;
+        __syncwarp();
+        const bool light = summ && __popcll(psum) <= PCBA_LIN_LIGHT;
+        for (int t = 0; t < chunks; ++t) {
+          if (!live(t)) continue;
+          if (!light) {
+            unsigned q = 0;
+            if (lane == 0) q = atomicAdd(&E.plan->lin_qcount, 1u);
+            q = __shfl_sync(0xffffffffu, q, 0);
+            if (q < E.lin_qcap) {
+              if (lane == 0) E.lin_queue[q] = make_uint2(u, (unsigned)t);
+              continue;
             }
           }
+          lin_chunk<T, K>(E, D, p, k, Kl, t, parent, right, spL, spR, ch, sIdx, sMw, par);
         }
       }
       __syncwarp();  // the staging buffers are reused by the next item
@@ -428,145 +735,36 @@ __global__ void __launch_bounds__(256, 3) k2_lin_split(Engine E, int cgmax, int 
   }
 }
 
-// ---------------------------------------------------------------------------
-// k2_lin_bound: one warp per (parent item, chunk of activity words)
-// ---------------------------------------------------------------------------
-
-// Bytes of shared memory one warp of k2_lin_bound uses: both children's
-// shared patches ([C][4] each), the compacted constraint indices and the
-// children's activity words.
-template <typename T>
-__host__ __device__ constexpr size_t lin_bound_warp_bytes(int cgmax) {
-  return (8 * (size_t)cgmax * sizeof(T) + 32 * PCBA_LIN_WORDS * sizeof(unsigned short) +
-          2 * PCBA_LIN_WORDS * sizeof(unsigned) + 15) / 16 * 16;
-}
-
-// Coefficient range of cc + sum_m w_m s_mj over the C coefficients of one
-// child staged in shared memory ([C][4]); two partial extremes per bound.
-template <typename T, int K>
-__device__ __forceinline__ void lin_range(const T* s, int C, T cc, const T (&w)[K], T& lo, T& hi) {
-  T lo0 = T(INFINITY), hi0 = T(-INFINITY), lo1 = T(INFINITY), hi1 = T(-INFINITY);
-  int j = 0;
-#pragma unroll 2
-  for (; j + 1 < C; j += 2) {
-    T a[K], b[K];
-    lin_load<T, K>(s + (size_t)j * 4, a);
-    lin_load<T, K>(s + (size_t)(j + 1) * 4, b);
-    T v0 = cc, v1 = cc;
-#pragma unroll
-    for (int m = 0; m < K; ++m) {
-      v0 = fma(w[m], a[m], v0);
-      v1 = fma(w[m], b[m], v1);
-    }
-    lo0 = min(lo0, v0);
-    hi0 = max(hi0, v0);
-    lo1 = min(lo1, v1);
-    hi1 = max(hi1, v1);
-  }
-  if (j < C) {
-    T a[K];
-    lin_load<T, K>(s + (size_t)j * 4, a);
-    T v0 = cc;
-#pragma unroll
-    for (int m = 0; m < K; ++m) v0 = fma(w[m], a[m], v0);
-    lo0 = min(lo0, v0);
-    hi0 = max(hi0, v0);
-  }
-  lo = min(lo0, lo1);
-  hi = max(hi0, hi1);
-}
-
+// Heavy items' live chunks, queued by k2_lin_split as (item, chunk): the
+// children are staged from memory.
 template <typename T, int K>
 __global__ void __launch_bounds__(256, 4) k2_lin_bound(Engine E, int cgmax) {
   constexpr bool RIG = sizeof(T) == 4;
-  constexpr float u24 = 0x1p-24f;
   extern __shared__ __align__(16) unsigned char klb[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* sS = (T*)(klb + (size_t)warp * lin_bound_warp_bytes<T>(cgmax));  // children [2][C][4]
   unsigned short* sIdx = (unsigned short*)(sS + 8 * (size_t)cgmax);
-  unsigned* sMw = (unsigned*)(sIdx + 32 * PCBA_LIN_WORDS);  // child words [2][LIN_WORDS]
-  const unsigned units = E.plan->k2_units;
+  unsigned* sMw = (unsigned*)(sIdx + 32 * PCBA_LIN_WORDS);
+  const unsigned units = min(E.plan->lin_qcount, E.lin_qcap);
   const int par = E.plan->steps_global & 1;  // the children's data is in copy par ^ 1
-  int cx_p = -1, cx_K = 0, cx_chunks = 1;
-  unsigned cx_beg = 0, cx_end = 0;
-  const ProbDesc* D = nullptr;
-  // units are fetched in batches from a counter (reset before every step), so
-  // that the few heavy units - chunks with many active constraints - spread
-  // over the whole GPU
   for (;;) {
     unsigned ubeg = 0;
     if (lane == 0) ubeg = atomicAdd(&E.plan->lin_next, (unsigned)PCBA_LIN_BATCH);
     ubeg = __shfl_sync(0xffffffffu, ubeg, 0);
     if (ubeg >= units) break;
     const unsigned uend = min(units, ubeg + (unsigned)PCBA_LIN_BATCH);
-    for (unsigned u = ubeg; u < uend; ++u) {
-      if (u < cx_beg || u >= cx_end || cx_p < 0) {
-        cx_p = find_problem(E.k2_pre, E.np, u);
-        cx_beg = E.k2_pre[cx_p];
-        cx_end = E.k2_pre[cx_p + 1];
-        D = E.desc + cx_p;
-        cx_K = E.state[cx_p].K;
-        cx_chunks = D->lin_chunks;
-      }
-      const int p = cx_p, Kl = cx_K, chunks = cx_chunks;
-      const unsigned local = u - cx_beg;
-      const int k = (int)(local / (unsigned)chunks);
-      const int t = (int)(local - (unsigned)k * chunks);
-      const long long slot_off = D->slot_off;
+    for (unsigned q = ubeg; q < uend; ++q) {
+      const uint2 ent = E.lin_queue[q];
+      const int p = find_problem(E.kr_pre, E.np, ent.x);
+      const ProbDesc* D = E.desc + p;
+      const int k = (int)(ent.x - E.kr_pre[p]), t = (int)ent.y;
+      const int Kl = E.state[p].K;
       char* list = E.arena + D->list_off;
-      char* left = list + (size_t)E.map[slot_off + k] * D->item_bytes;       // the parent's slot
-      char* right = list + (size_t)E.map[slot_off + k + Kl] * D->item_bytes;  // set by the split
-      const int C = D->cg, mwords = D->mwords;
-      const int w0 = t * PCBA_LIN_WORDS;
-      const int nw = min(PCBA_LIN_WORDS, mwords - w0);
-      unsigned* pm = (unsigned*)(left + D->off_mask) + w0;  // the parent's words, in place
-      unsigned* rm = (unsigned*)(right + D->off_mask) + w0;
-      // summaries: bit t of the parent's says whether chunk t has an active
-      // constraint; the children's are written to the other word (kept for up
-      // to 64 chunks)
-      const bool summ = chunks <= 64;
-      unsigned long long* sumL = (unsigned long long*)(left + D->off_sum) + (par ^ 1);
-      unsigned long long* sumR = (unsigned long long*)(right + D->off_sum) + (par ^ 1);
-      const unsigned long long tb = summ ? (1ull << t) : 0ull;
-      const bool live =
-          !summ || ((*((const unsigned long long*)(left + D->off_sum) + par) >> t) & 1ull);
-      unsigned word = 0u, cnt = 0u, incl = 0u, na = 0u;
-      if (live) {
-        word = lane < nw ? pm[lane] : 0u;
-        cnt = __popc(word);
-        incl = cnt;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const unsigned y = __shfl_up_sync(0xffffffffu, incl, o);
-          if (lane >= o) incl += y;
-        }
-        na = __shfl_sync(0xffffffffu, incl, 31);
-      }
-      if (na == 0) {
-        // no active constraint here: the children's words are zero (the
-        // left child shares the parent's, already zero)
-        if (lane < nw) rm[lane] = 0u;
-        if (lane == 0 && tb) {
-          atomicAnd(sumL, ~tb);
-          atomicAnd(sumR, ~tb);
-        }
-        continue;
-      }
+      char* left = list + (size_t)E.map[D->slot_off + k] * D->item_bytes;
+      char* right = list + (size_t)E.map[D->slot_off + k + Kl] * D->item_bytes;
+      const int C = D->cg;
       __syncwarp();  // the previous unit's readers of the staging buffers are done
-      {
-        unsigned pos = incl - cnt, bits = word;
-        while (bits) {
-          const int b = __ffs(bits) - 1;
-          bits &= bits - 1u;
-          sIdx[pos++] = (unsigned short)(lane * 32 + b);
-        }
-      }
-      if (lane < 2 * PCBA_LIN_WORDS) sMw[lane] = 0u;
-      // the children's shared patches (coalesced), extremes, error bounds and
-      // offsets (the same for every lane)
-      T cmn[2][K], cmx[2][K];
-      float Mabs[2][K], ec[2][K];
-      double Oc[2][K];
+      LinChildren<T, K> ch;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         char* it = c ? right : left;
@@ -575,147 +773,22 @@ __global__ void __launch_bounds__(256, 4) k2_lin_bound(Engine E, int cgmax) {
         char* mc = it + D->off_eg + (par ^ 1) * D->copy_e;
 #pragma unroll
         for (int m = 0; m < K; ++m) {
-          cmn[c][m] = LinMeta<T>::mn(mc, 4)[m];
-          cmx[c][m] = LinMeta<T>::mx(mc, 4)[m];
+          ch.mn[c][m] = LinMeta<T>::mn(mc, 4)[m];
+          ch.mx[c][m] = LinMeta<T>::mx(mc, 4)[m];
           if constexpr (RIG) {
-            Mabs[c][m] = fmaxf(fabsf((float)cmn[c][m]), fabsf((float)cmx[c][m]));
-            ec[c][m] = LinMeta<T>::err(mc, 4)[m];
-            Oc[c][m] = LinMeta<T>::off(mc, 4)[m];
+            ch.Mabs[c][m] = fmaxf(fabsf((float)ch.mn[c][m]), fabsf((float)ch.mx[c][m]));
+            ch.ec[c][m] = LinMeta<T>::err(mc, 4)[m];
+            ch.O[c][m] = LinMeta<T>::off(mc, 4)[m];
           } else {
-            Mabs[c][m] = 0.0f;
-            ec[c][m] = 0.0f;
-            Oc[c][m] = 0.0;
+            ch.Mabs[c][m] = 0.0f;
+            ch.ec[c][m] = 0.0f;
+            ch.O[c][m] = 0.0;
           }
         }
       }
       __syncwarp();
-      T gmax[2] = {T(-INFINITY), T(-INFINITY)}, gmin[2] = {T(-INFINITY), T(-INFINITY)};
-      bool mark[2] = {false, false};
-      unsigned nfull = 0;  // coefficient-range evaluations of this lane
-      const int Kw = K;
-      for (unsigned q = lane; q < na; q += 32) {
-        const int li = sIdx[q];
-        const long long row = (D->lin_off + (long long)w0 * 32 + li) * PCBA_LIN_STRIDE;
-        const double* rw = E.lin64 + row;
-        T w[K], cc[2];
-        float E64[2] = {0.0f, 0.0f};  // FP32: bound of the FP64 constant term
-        if constexpr (RIG) {
-          const float4 r0 = *(const float4*)(E.lin32 + row);
-          const float4 r1 = *(const float4*)(E.lin32 + row + 4);
-          const float rr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-#pragma unroll
-          for (int m = 0; m < K; ++m) w[m] = rr[1 + m];
-          // the constant term c_i + sum_m w_im O_m of each child's
-          // coefficients relative to its offsets, in FP64 from the FP64 row:
-          // the large terms cancel here, and the FP32 part only carries the
-          // residuals (of the order of the box's range)
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            double kap = rw[0], a64 = fabs(rw[0]);
-#pragma unroll
-            for (int m = 0; m < K; ++m) {
-              kap = fma(rw[1 + m], Oc[c][m], kap);
-              a64 = fma(fabs(rw[1 + m]), fabs(Oc[c][m]), a64);
-            }
-            cc[c] = (T)kap;
-            E64[c] = __double2float_ru(__dmul_ru(a64, 0x1p-50));
-          }
-        } else {
-#pragma unroll
-          for (int m = 0; m < K; ++m) w[m] = (T)rw[1 + m];
-          cc[0] = cc[1] = (T)rw[0];
-        }
-        // E of the comment at the top of this file (0 in FP64 mode), and the
-        // interval bound from the ranges of the stored patches, per child
-        float Ee[2] = {0.0f, 0.0f}, Er[2] = {0.0f, 0.0f};
-        T lo[2], hi[2], Et[2];
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          float Eb = 0.0f;
-          if constexpr (RIG) {
-            float A = fabsf((float)cc[c]), ee = 0.0f;
-#pragma unroll
-            for (int m = 0; m < K; ++m) {
-              A = __fmaf_ru(fabsf((float)w[m]), Mabs[c][m], A);
-              ee = __fmaf_ru(fabsf((float)w[m]), ec[c][m], ee);
-            }
-            const float kk = (float)(2 * Kw + 2);
-            Er[c] = __fmul_ru((kk + 1.0f) * u24, A);
-            Ee[c] = ee;
-            Eb = __fadd_ru(__fadd_ru(__fadd_ru(Er[c], __fmul_ru(ee, 1.0f + 0x1p-20f)), E64[c]),
-                           kk * 0x1p-149f);
-          }
-          Et[c] = T(Eb);
-          T x0 = cc[c], x1 = cc[c];
-#pragma unroll
-          for (int m = 0; m < K; ++m) {
-            const T x = w[m] * cmn[c][m], y = w[m] * cmx[c][m];
-            x0 += min(x, y);
-            x1 += max(x, y);
-          }
-          lo[c] = x0;
-          hi[c] = x1;
-        }
-        // undecided by the interval: the coefficient range itself (Alg. 3)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          if (!(add_up(hi[c], Et[c]) <= T(0)) && !(sub_dn(lo[c], Et[c]) > T(0))) {
-            lin_range<T, K>(sS + (size_t)c * 4 * cgmax, C, cc[c], w, lo[c], hi[c]);
-            ++nfull;
-          }
-        }
-#pragma unroll
-        for (int c = 0; c < 2; ++c) {
-          const T up = add_up(hi[c], Et[c]), dn = sub_dn(lo[c], Et[c]);
-          const bool sat = up <= T(0);
-          const bool inf = dn > T(0);
-          if (!sat) {
-            atomicOr(&sMw[c * PCBA_LIN_WORDS + (li >> 5)], 1u << (li & 31));
-            gmax[c] = max(gmax[c], up);
-            gmin[c] = max(gmin[c], dn);
-          }
-          if constexpr (RIG) {
-            // the bound changed a decision the stored coefficients make: mark
-            // the child's shared patches for a refresh if their errors are
-            // the larger part of the bound
-            const bool flip = (hi[c] <= T(0)) != sat || (lo[c] > T(0)) != inf;
-            if (flip && Ee[c] > Er[c]) mark[c] = true;
-          }
-        }
-      }
-      __syncwarp();
-      if (lane < nw) {
-        pm[lane] = sMw[lane];                      // left child: in place (this unit's words)
-        rm[lane] = sMw[PCBA_LIN_WORDS + lane];     // right child
-      }
-      const bool keepL = __any_sync(0xffffffffu, lane < nw && sMw[lane] != 0u);
-      const bool keepR = __any_sync(0xffffffffu, lane < nw && sMw[PCBA_LIN_WORDS + lane] != 0u);
-      if (lane == 0) {
-        if (tb) {
-          if (keepL) atomicOr(sumL, tb); else atomicAnd(sumL, ~tb);
-          if (keepR) atomicOr(sumR, tb); else atomicAnd(sumR, ~tb);
-        }
-        atomicAdd(&E.plan->lin_pairs, 2ull * na);
-      }
-      const unsigned full = __reduce_add_sync(0xffffffffu, nfull);
-      if (lane == 0) atomicAdd(&E.plan->lin_full, (unsigned long long)full);
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const T gx = lin_wmax(gmax[c]);
-        const T gn = lin_wmax(gmin[c]);
-        ChildRec* rc = E.rec + slot_off + k + (c ? Kl : 0);
-        if (lane == 0 && gx > T(-INFINITY)) {
-          atomicMax(&rc->gmaxmax, okey((double)gx));
-          atomicMax(&rc->gminmax, okey((double)gn));
-        }
-      }
-      if constexpr (RIG) {
-        const MarkCtx mk{p, k, k + Kl, E.marks + (size_t)par * E.mark_cap,
-                         &E.plan->mark_count[par], E.mark_cap};
-        const bool bl = __any_sync(0xffffffffu, mark[0]);
-        const bool br = __any_sync(0xffffffffu, mark[1]);
-        append_marks(mk, bl && lane < K, br && lane < K, 0, lane);
-      }
+      lin_chunk<T, K>(E, D, p, k, Kl, t, left, right, sS, sS + 4 * (size_t)cgmax, ch, sIdx, sMw,
+                      par);
     }
   }
 }
