@@ -181,7 +181,7 @@ struct pcba_batch {
   long long cand_floats = 0;    // largest constraint coefficient count (alpha cg + beta ch)
   double* d_stencil = nullptr;  // guided solves: [stencil_cap] doubles
   double* d_polish = nullptr;   // pcba_batch_polish output: [np][PCBA_MAXD]
-  float* d_lin32 = nullptr;     // linear families: [lin_rows][PCBA_LIN_STRIDE] (c, w_0..w_K-1) in FP32
+  float* d_lin32 = nullptr;     // linear families: [lin_rows][PCBA_LIN32_STRIDE] FP32 pairs of the rows
   uint2* d_lin_queue = nullptr; // linear families: heavy (item, chunk) units of a step
   double* d_lin64 = nullptr;    // the same in FP64
   // pcba_batch_solve_polished: the warm points are already in d_warm (written
@@ -449,7 +449,7 @@ int setup_kernels(pcba_batch* b) {
     g.kr_lmax = b->max_l;
     g.kr_cmax = (int)cmax;
     auto need = [&](int wpb, long long c) {
-      return (size_t)wpb * (size_t)(4 * c + 2 * 289 * g.kr_lmax) * sizeof(double);
+      return (size_t)wpb * (size_t)(4 * c + 2 * 289 * g.kr_lmax + PCBA_KR_SCRATCH) * sizeof(double);
     };
     g.kr_wpb = 4;
     while (g.kr_wpb > 1 && need(g.kr_wpb, g.kr_cmax) > (size_t)smem_optin - 4096) g.kr_wpb /= 2;
@@ -459,8 +459,9 @@ int setup_kernels(pcba_batch* b) {
                                  (int)g.kr_smem));
     PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_refresh, 32 * g.kr_wpb,
                                                           g.kr_smem));
-    // marks are few (thousands per solve): two blocks per SM at most
-    g.kr_grid = std::max(1, std::min(occ, 2)) * g.sms;
+    // marks are tens to thousands per step, each a chain of FP64 work: as
+    // many resident blocks as fit (at most 4 per SM) to hide its latency
+    g.kr_grid = std::max(1, std::min(occ, 4)) * g.sms;
     double binom[17 * 17], binom_inv[17 * 17];
     for (int n = 0; n < 17; ++n)
       for (int k = 0; k < 17; ++k) {
@@ -709,7 +710,7 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   PCBA_ALLOC(b->d_mat, sizeof(double) * 3 * PCBA_MAXD * 578 * n);
   PCBA_ALLOC(b->d_raw, sizeof(double) * mono);
   PCBA_ALLOC(b->d_eval, sizeof(EvalOut) * n);
-  PCBA_ALLOC(b->d_lin32, sizeof(float) * PCBA_LIN_STRIDE * std::max<long long>(lin_rows, 1));
+  PCBA_ALLOC(b->d_lin32, sizeof(float) * PCBA_LIN32_STRIDE * std::max<long long>(lin_rows, 1));
   PCBA_ALLOC(b->d_lin64, sizeof(double) * PCBA_LIN_STRIDE * std::max<long long>(lin_rows, 1));
   // queue of heavy (item, chunk) units: every item of every problem with all
   // its chunks, at most 4 Mi entries (a full queue leaves units to the split)
@@ -756,9 +757,9 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
       return rc;
   }
   if (lin_rows > 0) {
-    // constraint rows (c_i, w_i0 .. w_i,K-1), in FP64 and rounded to nearest FP32
+    // constraint rows (c_i, w_i0 .. w_i,K-1), in FP64 and as FP32 pairs
     std::vector<double> t64((size_t)(PCBA_LIN_STRIDE * lin_rows), 0.0);
-    std::vector<float> t32(t64.size(), 0.0f);
+    std::vector<float> t32((size_t)(PCBA_LIN32_STRIDE * lin_rows), 0.0f);
     for (int k = 0; k < n; ++k) {
       const HostProblem& P = *b->probs[k];
       for (int i = 0; i < P.nlin; ++i) {
@@ -767,7 +768,13 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
         for (int m = 0; m < P.alpha; ++m) row[1 + m] = P.lin_w[(size_t)i * P.alpha + m];
       }
     }
-    for (size_t q = 0; q < t64.size(); ++q) t32[q] = (float)t64[q];
+    for (long long q = 0; q < lin_rows; ++q)
+      for (int j = 0; j < PCBA_LIN_STRIDE; ++j) {
+        const double x = t64[(size_t)q * PCBA_LIN_STRIDE + j];
+        const float hi = (float)x;
+        t32[(size_t)q * PCBA_LIN32_STRIDE + j] = hi;
+        t32[(size_t)q * PCBA_LIN32_STRIDE + PCBA_LIN_STRIDE + j] = (float)(x - (double)hi);
+      }
     if ((rc = cleanup_ck(cudaMemcpy(b->d_lin64, t64.data(), sizeof(double) * t64.size(),
                                     cudaMemcpyHostToDevice), "linear rows upload")))
       return rc;
@@ -1398,7 +1405,7 @@ int pcba_batch_upload_rows(pcba_batch* b, const double* host_rows) {
   PCBA_CK(cudaMemcpyAsync(b->d_lin64, host_rows, sizeof(double) * n, cudaMemcpyHostToDevice,
                           b->stream));
   const unsigned g = (unsigned)std::min<long long>((n + 255) / 256, 4LL * b->g.sms);
-  k_rows32<<<g, 256, 0, b->stream>>>(b->d_lin64, b->d_lin32, n);
+  k_rows32<<<g, 256, 0, b->stream>>>(b->d_lin64, b->d_lin32, b->lin_rows);
   PCBA_CK(cudaGetLastError());
   b->pending_h2d += 8LL * n;
   b->extra_launches_pending += 1;

@@ -43,7 +43,9 @@
 #define PCBA_RUNNING 10
 #define PCBA_TRACE_PER_DIM 40
 #define PCBA_LIN_WORDS 8     // activity words (256 constraints) per linear subdivision unit
-#define PCBA_LIN_STRIDE 8    // floats / doubles per linear constraint row (c, w_0 .. w_K-1)
+#define PCBA_LIN_STRIDE 8    // doubles per linear constraint row (c, w_0 .. w_K-1)
+#define PCBA_FAM_LIN 3        // refresh mark: every shared patch of a linear-family item
+#define PCBA_LIN32_STRIDE 16  // floats per FP32 row: the FP64 row rounded, then the remainders
 #define PCBA_LIN_BATCH 4     // units a warp of the linear subdivision kernel fetches at once
 #define PCBA_LIN_LIGHT 2     // items with at most this many live chunks are bounded by the split
 
@@ -193,7 +195,9 @@ struct Engine {
   const void* tmaps;       // [np][2] tensor maps (CUtensorMap) of the g / h blocks, or null
   uint2* lin_queue;        // linear families: (item, chunk) units of heavy items, this step
   unsigned lin_qcap;       // its capacity (a full queue leaves the units to the split kernel)
-  const float* lin32;      // linear families: constraint rows in FP32 (round to nearest)
+  const float* lin32;      // linear families: constraint rows in FP32, [rows][16]: the
+                           // FP64 row rounded to nearest (8), then the remainders
+                           // fl(x - hi) (8), so that hi + lo carries x to 2^-48
   const double* lin64;     // the same in FP64
 };
 

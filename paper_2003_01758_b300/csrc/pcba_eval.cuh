@@ -33,10 +33,18 @@ __global__ void k_mono32(const double* mono, float* out, long long n) {
 }
 
 // FP32 copy (round to nearest) of the linear-family constraint rows
-__global__ void k_rows32(const double* rows, float* out, long long n) {
+// FP32 pairs of the linear rows: x = hi + lo to 2^-48 relative (x - hi is
+// exact in FP64, lo its rounding to nearest FP32).
+__global__ void k_rows32(const double* rows, float* out, long long nrows) {
+  const long long n = nrows * PCBA_LIN_STRIDE;
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
-       i += (long long)gridDim.x * blockDim.x)
-    out[i] = __double2float_rn(rows[i]);
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long q = i / PCBA_LIN_STRIDE, j = i - q * PCBA_LIN_STRIDE;
+    const double x = rows[i];
+    const float hi = __double2float_rn(x);
+    out[q * PCBA_LIN32_STRIDE + j] = hi;
+    out[q * PCBA_LIN32_STRIDE + PCBA_LIN_STRIDE + j] = __double2float_rn(x - (double)hi);
+  }
 }
 
 #define PCBA_EVAL_CHUNK 8
@@ -258,7 +266,7 @@ __device__ __forceinline__ void horner_f64(const double* a, int l, const int* de
 __device__ __forceinline__ void lin_value_f32(const Engine& E, const ProbDesc* D, int q,
                                               const float* sv, const float* se, float* val,
                                               float* err) {
-  const float* row = E.lin32 + (D->lin_off + q) * PCBA_LIN_STRIDE;
+  const float* row = E.lin32 + (D->lin_off + q) * PCBA_LIN32_STRIDE;
   const int K = D->alpha;
   float v = row[0], A = fabsf(row[0]), Ee = 0.0f;
   for (int m = 0; m < K; ++m) {

@@ -240,25 +240,46 @@ __global__ void __launch_bounds__(128) k1_convert(Engine E, const double* mat, i
 __constant__ double c_binom[17 * 17];
 __constant__ double c_binom_inv[17 * 17];
 
+// Doubles of per-warp scratch of refresh_matrices: the factors U and V
+// ([17][17] each) and the powers lo^e, w^e ([17] each).
+#define PCBA_KR_SCRATCH (2 * 289 + 2 * 17)
+
 // T_r[i][j] = sum_k C(i,k) C(j,k) / C(n,k) lo^(j-k) w^k (power basis on the
-// box -> Bernstein basis), and A_r its absolute-value sum widened by 2^-40,
-// which covers the few roundings of every term (the reciprocal included),
-// stored as floats rounded up (the 289 floats after T_r's 289 doubles).
+// box -> Bernstein basis), formed as sum_k U[i][k] V[j][k] with U[i][k] =
+// C(i,k) / C(n,k) w^k and V[j][k] = C(j,k) lo^(j-k) (each factor computed
+// once, the powers by lane e with e products), and A_r its absolute-value sum
+// widened by 2^-40, which covers the roundings of every term (at most
+// (j + n + 5) 2^-53 relative, the reciprocal and the sum included), stored
+// as floats rounded up (the 289 floats after T_r's 289 doubles).  scr is the
+// warp's PCBA_KR_SCRATCH doubles.
 __device__ __forceinline__ void refresh_matrices(const double* binom, int l, const int* deg,
                                                  const double* blo, const double* bhi,
-                                                 double* sT, int lane) {
+                                                 double* sT, double* scr, int lane) {
+  double* U = scr;
+  double* V = scr + 289;
+  double* lp = scr + 578;
+  double* wp = lp + 17;
   for (int r = 0; r < l; ++r) {
     const int n = deg[r];
     const double lo = blo[r], w = bhi[r] - blo[r];
-    // powers lo^e and w^e (same products as dev_pow, kept in registers)
-    double lp[17], wp[17];
-    lp[0] = 1.0;
-    wp[0] = 1.0;
-#pragma unroll
-    for (int e = 1; e < 17; ++e) {
-      lp[e] = lp[e - 1] * lo;
-      wp[e] = wp[e - 1] * w;
+    if (lane <= n) {
+      double a = 1.0, b = 1.0;
+      for (int e = 0; e < lane; ++e) {
+        a *= lo;
+        b *= w;
+      }
+      lp[lane] = a;
+      wp[lane] = b;
     }
+    __syncwarp();
+    // U and V over the pairs k <= i (k <= j) of a (n+1) x (n+1) grid
+    for (int e = lane; e < (n + 1) * (n + 1); e += 32) {
+      const int i = e / (n + 1), k = e - (e / (n + 1)) * (n + 1);
+      if (k > i) continue;
+      U[i * 17 + k] = binom[i * 17 + k] * c_binom_inv[n * 17 + k] * wp[k];
+      V[i * 17 + k] = binom[i * 17 + k] * lp[i - k];
+    }
+    __syncwarp();
     double* T = sT + r * 578;
     float* A = (float*)(T + 289);
     for (int e = lane; e < (n + 1) * (n + 1); e += 32) {
@@ -266,16 +287,15 @@ __device__ __forceinline__ void refresh_matrices(const double* binom, int l, con
       double t = 0.0, ta = 0.0;
       const int kmax = i < j ? i : j;
       for (int k = 0; k <= kmax; ++k) {
-        const double term = binom[i * 17 + k] * c_binom_inv[n * 17 + k] * binom[j * 17 + k] *
-                            lp[j - k] * wp[k];
-        t += term;
-        ta += fabs(term);
+        const double u = U[i * 17 + k], v = V[j * 17 + k];
+        t = fma(u, v, t);
+        ta = fma(fabs(u), fabs(v), ta);
       }
       T[e] = t;
       A[e] = __double2float_ru(ta * (1.0 + 0x1p-40));
     }
+    __syncwarp();  // the next axis reuses U, V and the powers
   }
-  __syncwarp();
 }
 
 // Warp-cooperative conversion of one monomial tensor a (C coefficients,
@@ -328,6 +348,36 @@ __device__ __forceinline__ double refresh_convert(const double* a, int C, int l,
   return __dmul_ru(__dmul_ru(2.0 * gterms, 0x1p-53), (double)amax);
 }
 
+// Stores a converted patch (sA, C coefficients, bound base err64) as FP32
+// values at dst[j * pad] relative to the offset O (0, or the middle of its
+// range when centre is set), and returns its error bound (rounded up).
+__device__ __forceinline__ float refresh_store(const double* sA, int C, double err64, bool centre,
+                                               float* dst, size_t pad, double& O, int lane) {
+  O = 0.0;
+  if (centre) {
+    double bmin = INFINITY, bmax = -INFINITY;
+    for (int j = lane; j < C; j += 32) {
+      bmin = fmin(bmin, sA[j]);
+      bmax = fmax(bmax, sA[j]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      bmin = fmin(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
+      bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
+    }
+    O = 0.5 * (bmin + bmax);
+  }
+  double emax = 0.0;
+  for (int j = lane; j < C; j += 32) {
+    const double d = sA[j] - O;  // |d - (b - O)| <= |d| 2^-53 (exact when O = 0)
+    const float sv = __double2float_rn(d);
+    dst[(size_t)j * pad] = sv;
+    emax = fmax(emax, centre ? __dadd_ru(fabs((double)sv - d), __dmul_ru(fabs(d), 0x1p-52))
+                             : fabs((double)sv - sA[j]));
+  }
+  for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+  return __double2float_ru(__dadd_ru(emax, err64));
+}
+
 __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
   extern __shared__ double krs[];
   const int par = E.plan->steps_global & 1;  // the list this step's subdivision filled
@@ -335,14 +385,15 @@ __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
   if (count == 0) return;
   const double* binom = c_binom;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  double* wbase = krs + (size_t)warp * (4 * cmax + 2 * 289 * lmax);
+  double* wbase = krs + (size_t)warp * (4 * cmax + 2 * 289 * lmax + PCBA_KR_SCRATCH);
   double* sA = wbase;
   double* sB = sA + cmax;
   float* sX = (float*)(sB + cmax);
   float* sY = (float*)(sB + 2 * cmax);
   double* sT = sB + 3 * cmax;
+  double* scr = sT + 2 * 289 * lmax;
   const uint4* list = E.marks + (size_t)par * E.mark_cap;
-  // marks are few (tens to hundreds per step) and each is a chain of FP64
+  // marks are few (tens to thousands per step) and each is a chain of FP64
   // work: warp-major numbering spreads consecutive marks over blocks (SMs)
   // instead of stacking them on the FP64 units of one SM
   for (unsigned q = warp * gridDim.x + blockIdx.x; q < count; q += gridDim.x * wpb) {
@@ -364,68 +415,57 @@ __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
     if (fam == 2) {
       if (D->cp > cmax) continue;
       // the cost patch: recomputed and re-centred on its range
-      refresh_matrices(binom, D->l, D->P, blo, bhi, sT, lane);
+      refresh_matrices(binom, D->l, D->P, blo, bhi, sT, scr, lane);
       const double err64 = refresh_convert(mono, D->cp, D->l, D->P, sT, sA, sB, sX, sY, lane);
-      double bmin = INFINITY, bmax = -INFINITY;
-      for (int j = lane; j < D->cp; j += 32) { bmin = fmin(bmin, sA[j]); bmax = fmax(bmax, sA[j]); }
-      for (int o = 16; o > 0; o >>= 1) {
-        bmin = fmin(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
-        bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-      }
-      const double O = 0.5 * (bmin + bmax);
-      float* dst = (float*)(item + D->off_cost);
-      double emax = 0.0;
-      for (int j = lane; j < D->cp; j += 32) {
-        const double d = sA[j] - O;
-        const float sv = __double2float_rn(d);
-        dst[j] = sv;
-        emax = fmax(emax, __dadd_ru(fabs((double)sv - d), __dmul_ru(fabs(d), 0x1p-52)));
-      }
-      for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+      double O;
+      const float e = refresh_store(sA, D->cp, err64, true, (float*)(item + D->off_cost), 1, O,
+                                    lane);
       if (lane == 0) {
         *(double*)(item + 32) = O;
-        *(float*)(item + 40) = __double2float_ru(__dadd_ru(emax, err64));
+        *(float*)(item + 40) = e;
         atomicAdd(&E.plan->refreshed_total, 1ull);
       }
       __syncwarp();
       continue;
     }
+    if (fam == PCBA_FAM_LIN) {
+      // every shared patch of a linear-family item (one set of matrices),
+      // re-centred, to the copy the next step reads
+      const int C = D->cg;
+      if (C > cmax) continue;
+      refresh_matrices(binom, D->l, D->G, blo, bhi, sT, scr, lane);
+      const int nxt = (E.plan->steps_global + 1) & 1;
+      float* block = (float*)(item + D->off_g + nxt * D->copy_g);
+      float* earr = (float*)(item + D->off_eg + nxt * D->copy_e);
+      const double* sh_mono = mono + D->cp;
+      for (int g = 0; g < D->alpha; ++g) {
+        const double err64 =
+            refresh_convert(sh_mono + (long long)g * C, C, D->l, D->G, sT, sA, sB, sX, sY, lane);
+        double O;
+        const float e = refresh_store(sA, C, err64, true, block + g, D->apad, O, lane);
+        if (lane == 0) {
+          ((double*)(earr + D->apad))[g] = O;
+          earr[g] = e;
+        }
+        __syncwarp();
+      }
+      if (lane == 0) atomicAdd(&E.plan->refreshed_total, (unsigned long long)D->alpha);
+      continue;
+    }
     const int C = fam ? D->ch : D->cg;
     if (C > cmax) continue;
     const int* deg = fam ? D->H : D->G;
-    refresh_matrices(binom, D->l, deg, blo, bhi, sT, lane);
+    refresh_matrices(binom, D->l, deg, blo, bhi, sT, scr, lane);
     const size_t pad = fam ? D->bpad : D->apad;
-    // linear-family items: the copy of the shared patches the next step reads
-    const int nxt = (E.plan->steps_global + 1) & 1;
-    float* block = (float*)(item + (fam ? D->off_h : D->off_g + nxt * D->copy_g));
-    float* earr = (float*)(item + (fam ? D->off_eh : D->off_eg + nxt * D->copy_e));
+    float* block = (float*)(item + (fam ? D->off_h : D->off_g));
+    float* earr = (float*)(item + (fam ? D->off_eh : D->off_eg));
     const double* fam_mono = mono + D->cp + (fam ? (long long)D->alpha * D->cg : 0);
     const double err64 =
         refresh_convert(fam_mono + (long long)ip * C, C, D->l, deg, sT, sA, sB, sX, sY, lane);
-    // a linear family's shared patch is stored relative to the middle of its
-    // range, as the cost patch (the offset is an FP64 value kept exactly)
-    double O = 0.0;
-    if (D->lin) {
-      double bmin = INFINITY, bmax = -INFINITY;
-      for (int j = lane; j < C; j += 32) { bmin = fmin(bmin, sA[j]); bmax = fmax(bmax, sA[j]); }
-      for (int o = 16; o > 0; o >>= 1) {
-        bmin = fmin(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
-        bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-      }
-      O = 0.5 * (bmin + bmax);
-    }
-    double emax = 0.0;
-    for (int j = lane; j < C; j += 32) {
-      const double d = sA[j] - O;                 // |d - (b - O)| <= |d| 2^-53
-      const float sv = __double2float_rn(d);
-      block[(size_t)j * pad + ip] = sv;
-      emax = fmax(emax, D->lin ? __dadd_ru(fabs((double)sv - d), __dmul_ru(fabs(d), 0x1p-52))
-                               : fabs((double)sv - sA[j]));
-    }
-    if (D->lin && lane == 0) ((double*)(earr + D->apad))[ip] = O;
-    for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
+    double O;
+    const float e = refresh_store(sA, C, err64, false, block + ip, pad, O, lane);
     if (lane == 0) {
-      earr[ip] = __double2float_ru(__dadd_ru(emax, err64));
+      earr[ip] = e;
       atomicAdd(&E.plan->refreshed_total, 1ull);
     }
     __syncwarp();

@@ -17,20 +17,30 @@
 // an FP64 offset O_m (re-centred on the middle of its range at every
 // bisection, as the cost patch), with a bound e_m: |O_m + r_mj - b_mj| <= e_m.
 // Near an obstacle's boundary the terms c_i, ||F||^2 and 2 o_i . F are large
-// and cancel, so the constant part kappa_i = c_i + sum_m w_im O_m is formed in
-// FP64 from the FP64 row (error <= 2^-50 A64, A64 = |c| + sum_m |w_m| |O_m|,
-// for K <= 4) and rounded to FP32; the FP32 work only carries residuals.
+// and cancel, so the constant part kappa_i = c_i + sum_m w_im O_m is formed to
+// about 48 bits and then rounded to FP32; the FP32 work only carries
+// residuals.  It takes no FP64 operation (B300 issues FP64 at a small
+// fraction of the FP32 rate): c, w and O are each split into two FP32 values
+// (x = hi + lo to 2^-48 |x|), w_hi O_hi is formed exactly as p + e (fused
+// multiply-add), c_hi + sum p_m is summed error-free (TwoSum, Knuth), and the
+// small terms (c_lo, e, w_hi O_lo, w_lo O_hi, the TwoSum errors) in plain FP32.
+// With A64 = |c| + sum_m |w_m| |O_m| the splits and the dropped w_lo O_lo cost
+// at most (1 + 5K) 2^-48 A64 and the sum of the small terms (each at most
+// 2^-24 A64 in size, (K + 3) 2^-24 A64 together, 4K roundings) at most
+// 4K (K + 3) 2^-48 A64, so for K <= 4 the error before the final rounding is
+// below 134 2^-48 A64 < 2^-40 A64; products and sums that underflow add at
+// most (8K + 2) 2^-149.
 // With A = |kappa| + sum_m |w_m| max_j |r_mj| (the child's residuals), the
 // computed coefficient v_j = fma(w_K-1, r_K-1,j, ... fma(w_0, r_0j, kappa))
 // differs from the exact c_i + sum_m w_im b_mj by at most
 //     K u A (1 + u)^K            the K roundings of the fused chain,
 //   + 2.02 u A                   rounding of kappa and of w to FP32,
 //   + (1 + 1.01 u) sum |w_m| e_m stored-patch errors,
-//   + 2^-50 A64                  the FP64 constant term,
+//   + 2^-40 A64 + (8K+2) 2^-149  the two-float constant term,
 // and the interval bound kappa + sum_m min/max(w_m mn_m, w_m mx_m) (mn_m, mx_m
 // the exact extremes of the stored residuals) by at most 2K u A plus the same
 // other terms; subnormal results add at most 2^-149 each.  So
-//     E = (2K + 3) u A + (1 + 2^-20) sum |w_m| e_m + 2^-50 A64 + (2K + 2) 2^-149,
+//     E = (2K + 3) u A + (1 + 2^-20) sum |w_m| e_m + 2^-40 A64 + (10K + 4) 2^-149,
 // computed with upward rounding, bounds both, and [min_j v_j - E, max_j v_j + E]
 // encloses the exact coefficient range of the constraint on the box.  (FP64
 // mode stores plain patches, O_m = 0, and is plain arithmetic as the paper's.)
@@ -205,13 +215,70 @@ __device__ __forceinline__ void lin_range(const T* s, int C, T cc, const T (&w)[
 }
 
 // Both children's metadata (the same in every lane): extremes of the stored
-// values of each shared patch and, in FP32, their error bounds and offsets.
+// values of each shared patch and, in FP32, their error bounds and offsets
+// (the FP64 offset O split into FP32 values, O = Oh + Ol to 2^-48 |O|).
 template <typename T, int K>
 struct LinChildren {
   T mn[2][K], mx[2][K];
   float Mabs[2][K], ec[2][K];
-  double O[2][K];
+  float Oh[2][K], Ol[2][K];
 };
+
+// Lanes c K + g (c < 2, g < K) hold child c's values of shared patch g; every
+// lane receives all of them.
+template <typename T, int K>
+__device__ __forceinline__ void lin_children_bcast(LinChildren<T, K>& ch, T mn, T mx, float Mabs,
+                                                   float ec, float Oh, float Ol) {
+#pragma unroll
+  for (int c = 0; c < 2; ++c)
+#pragma unroll
+    for (int g = 0; g < K; ++g) {
+      const int src = c * K + g;
+      ch.mn[c][g] = __shfl_sync(0xffffffffu, mn, src);
+      ch.mx[c][g] = __shfl_sync(0xffffffffu, mx, src);
+      ch.Mabs[c][g] = __shfl_sync(0xffffffffu, Mabs, src);
+      ch.ec[c][g] = __shfl_sync(0xffffffffu, ec, src);
+      ch.Oh[c][g] = __shfl_sync(0xffffffffu, Oh, src);
+      ch.Ol[c][g] = __shfl_sync(0xffffffffu, Ol, src);
+    }
+}
+
+// An FP64 value as two FP32 values, x = hi + lo to 2^-48 |x| (x - hi is
+// exact in FP64).
+__device__ __forceinline__ void lin_split_f64(double x, float& hi, float& lo) {
+  hi = __double2float_rn(x);
+  lo = __double2float_rn(x - (double)hi);
+}
+
+// The constant term kappa = c + sum_m w_m O_m of a constraint's coefficients
+// relative to a child's offsets, in FP32 operations only (the two-float
+// scheme of the comment at the top of this file): hv / lv are the row's FP32
+// pairs (c, w_0 .. w_K-1).  kap is the result rounded to FP32, ekap a bound
+// of its error before that rounding (2^-40 A64 + (8K + 2) 2^-149).
+template <int K>
+__device__ __forceinline__ void lin_kappa(const float* hv, const float* lv, const float (&Oh)[K],
+                                          const float (&Ol)[K], float& kap, float& ekap) {
+  float s = hv[0];        // c_hi + sum p_m, carried error-free with the TwoSum errors
+  float sm = lv[0];       // the small terms
+  float A = fabsf(hv[0]);  // A64 from the high parts, rounded up
+#pragma unroll
+  for (int m = 0; m < K; ++m) {
+    const float wh = hv[1 + m], wl = lv[1 + m];
+    const float p = __fmul_rn(wh, Oh[m]);
+    const float e = __fmaf_rn(wh, Oh[m], -p);  // wh Oh = p + e exactly
+    const float t = __fadd_rn(s, p);           // TwoSum: s + p = t + er exactly
+    const float bv = __fsub_rn(t, s);
+    const float er = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bv)), __fsub_rn(p, bv));
+    s = t;
+    const float cross = __fadd_rn(__fmul_rn(wh, Ol[m]), __fmul_rn(wl, Oh[m]));
+    sm = __fadd_rn(sm, __fadd_rn(__fadd_rn(e, er), cross));
+    A = __fmaf_ru(fabsf(wh), fabsf(Oh[m]), A);
+  }
+  kap = __fadd_rn(s, sm);
+  // the high parts understate A64 by at most a factor (1 + 2^-24)^2, well
+  // inside the margin of 134 2^-48 < 2^-40
+  ekap = __fadd_ru(__fmul_ru(A, 0x1p-40f), (float)(8 * K + 2) * 0x1p-149f);
+}
 
 // Chunk t of the activity words of parent item k (problem p, list length Kl):
 // its active constraints are compacted and bounded on both children (shared
@@ -267,32 +334,33 @@ __device__ void lin_chunk(const Engine& E, const ProbDesc* D, int p, int k, int 
   const int Kw = K;
   for (unsigned q = lane; q < na; q += 32) {
     const int li = sIdx[q];
-    const long long row = (D->lin_off + (long long)w0 * 32 + li) * PCBA_LIN_STRIDE;
-    const double* rw = E.lin64 + row;
+    const long long row = D->lin_off + (long long)w0 * 32 + li;
     T w[K], cc[2];
-    float E64[2] = {0.0f, 0.0f};  // FP32: bound of the FP64 constant term
+    float E64[2] = {0.0f, 0.0f};  // FP32: bound of the error of the constant term
     if constexpr (RIG) {
-      const float4 r0 = *(const float4*)(E.lin32 + row);
-      const float4 r1 = *(const float4*)(E.lin32 + row + 4);
-      const float rr[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-#pragma unroll
-      for (int m = 0; m < K; ++m) w[m] = rr[1 + m];
-      // the constant term c_i + sum_m w_im O_m of each child's
-      // coefficients relative to its offsets, in FP64 from the FP64 row:
-      // the large terms cancel here, and the FP32 part only carries the
-      // residuals (of the order of the box's range)
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        double kap = rw[0], a64 = fabs(rw[0]);
-#pragma unroll
-        for (int m = 0; m < K; ++m) {
-          kap = fma(rw[1 + m], ch.O[c][m], kap);
-          a64 = fma(fabs(rw[1 + m]), fabs(ch.O[c][m]), a64);
+      // the row's FP32 pairs (the slots past K + 1 are zero and not read)
+      const float* r32 = E.lin32 + row * PCBA_LIN32_STRIDE;
+      float hv[8], lv[8];
+      {
+        const float4 h0 = *(const float4*)r32, l0 = *(const float4*)(r32 + PCBA_LIN_STRIDE);
+        hv[0] = h0.x; hv[1] = h0.y; hv[2] = h0.z; hv[3] = h0.w;
+        lv[0] = l0.x; lv[1] = l0.y; lv[2] = l0.z; lv[3] = l0.w;
+        if constexpr (K >= 4) {
+          const float4 h1 = *(const float4*)(r32 + 4);
+          const float4 l1 = *(const float4*)(r32 + PCBA_LIN_STRIDE + 4);
+          hv[4] = h1.x; hv[5] = h1.y; hv[6] = h1.z; hv[7] = h1.w;
+          lv[4] = l1.x; lv[5] = l1.y; lv[6] = l1.z; lv[7] = l1.w;
         }
-        cc[c] = (T)kap;
-        E64[c] = __double2float_ru(__dmul_ru(a64, 0x1p-50));
       }
+#pragma unroll
+      for (int m = 0; m < K; ++m) w[m] = hv[1 + m];
+      // the constant term c_i + sum_m w_im O_m of each child's coefficients
+      // relative to its offsets: the large terms cancel here, and the FP32
+      // part only carries the residuals (of the order of the box's range)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) lin_kappa<K>(hv, lv, ch.Oh[c], ch.Ol[c], cc[c], E64[c]);
     } else {
+      const double* rw = E.lin64 + row * PCBA_LIN_STRIDE;
 #pragma unroll
       for (int m = 0; m < K; ++m) w[m] = (T)rw[1 + m];
       cc[0] = cc[1] = (T)rw[0];
@@ -384,9 +452,16 @@ __device__ void lin_chunk(const Engine& E, const ProbDesc* D, int p, int k, int 
   if constexpr (RIG) {
     const MarkCtx mk{p, k, k + Kl, E.marks + (size_t)par * E.mark_cap,
                      &E.plan->mark_count[par], E.mark_cap};
-    const bool bl = __any_sync(0xffffffffu, mark[0]);
-    const bool br = __any_sync(0xffffffffu, mark[1]);
-    append_marks(mk, bl && lane < K, br && lane < K, 0, lane);
+    // one mark per child for all its shared patches (family PCBA_FAM_LIN),
+    // the first chunk to ask for it sets bit 32 of the child record's perr
+    // (the split kernel wrote the error bits below it this step)
+    bool ml = __any_sync(0xffffffffu, mark[0]), mr = __any_sync(0xffffffffu, mark[1]);
+    if (lane == 0) {
+      constexpr unsigned long long bit = 1ull << 32;
+      if (ml) ml = !(atomicOr(&E.rec[slot_off + k].perr, bit) & bit);
+      if (mr) mr = !(atomicOr(&E.rec[slot_off + k + Kl].perr, bit) & bit);
+    }
+    append_marks(mk, lane == 0 && ml, lane == 0 && mr, PCBA_FAM_LIN, 0);
   }
   __syncwarp();
 }
@@ -648,50 +723,54 @@ __global__ void __launch_bounds__(256, 3) k2_lin_split(Engine E, int cgmax, int 
             spR[e] = vr;
           }
         }
-        // the children's metadata (every lane computes it; it is also what
-        // the bound of the constraints below uses)
+        // the children's metadata, lane c K + g for child c and shared patch
+        // g (the FP64 offset arithmetic once per value), then broadcast: it
+        // is also what the bound of the constraints below uses
+        {
+          T mn0 = T(0), mx0 = T(0), shv = T(0);
+          float amv = 0.0f, emv = 0.0f;
+          double omv = 0.0;
 #pragma unroll
-        for (int c = 0; c < 2; ++c)
+          for (int c = 0; c < 2; ++c)
 #pragma unroll
-          for (int g = 0; g < K; ++g) {
-            const T mn0 = c ? acc[1 + g].mnR : acc[1 + g].mnL;
-            const T mx0 = c ? acc[1 + g].mxR : acc[1 + g].mxL;
-            if constexpr (RIG) {
-              const float e1 = __fadd_ru(
-                  __fadd_ru(em[g], __fmul_ru((float)acc[1 + g].am, (float)ns * u24)),
-                  (float)ns * 0x1p-149f);
-              const float smin = __fsub_rn((float)mn0, (float)sh[c][g]);
-              const float smax = __fsub_rn((float)mx0, (float)sh[c][g]);
-              const float Mr = fmaxf(fabsf(smin), fabsf(smax));
-              ch.O[c][g] = Om[g] + (double)sh[c][g];
-              ch.ec[c][g] = __fadd_ru(__fadd_ru(__fadd_ru(e1, __fmul_ru(Mr, u24)), 0x1p-149f),
-                                      __double2float_ru(__dmul_ru(fabs(ch.O[c][g]), 0x1p-52)));
-              ch.mn[c][g] = T(smin);
-              ch.mx[c][g] = T(smax);
-              ch.Mabs[c][g] = Mr;
-            } else {
-              ch.O[c][g] = 0.0;
-              ch.ec[c][g] = 0.0f;
-              ch.mn[c][g] = mn0;
-              ch.mx[c][g] = mx0;
-              ch.Mabs[c][g] = 0.0f;
+            for (int g = 0; g < K; ++g)
+              if (lane == c * K + g) {
+                mn0 = c ? acc[1 + g].mnR : acc[1 + g].mnL;
+                mx0 = c ? acc[1 + g].mxR : acc[1 + g].mxL;
+                shv = sh[c][g];
+                amv = (float)acc[1 + g].am;
+                emv = em[g];
+                omv = Om[g];
+              }
+          T vmn = mn0, vmx = mx0;
+          float vM = 0.0f, vec = 0.0f, vOh = 0.0f, vOl = 0.0f;
+          double vO = 0.0;
+          if constexpr (RIG) {
+            if (lane < 2 * K) {
+              const float e1 = __fadd_ru(__fadd_ru(emv, __fmul_ru(amv, (float)ns * u24)),
+                                         (float)ns * 0x1p-149f);
+              const float smin = __fsub_rn((float)mn0, (float)shv);
+              const float smax = __fsub_rn((float)mx0, (float)shv);
+              vM = fmaxf(fabsf(smin), fabsf(smax));
+              vO = omv + (double)shv;
+              lin_split_f64(vO, vOh, vOl);
+              vec = __fadd_ru(__fadd_ru(__fadd_ru(e1, __fmul_ru(vM, u24)), 0x1p-149f),
+                              __double2float_ru(__dmul_ru(fabs(vO), 0x1p-52)));
+              vmn = T(smin);
+              vmx = T(smax);
             }
           }
-        if (lane < 2 * K) {
-          const int c = lane / K, g0 = lane - c * K;
-          char* cm = (c ? right : parent) + D->off_eg + (par ^ 1) * D->copy_e;
-#pragma unroll
-          for (int cc = 0; cc < 2; ++cc)
-#pragma unroll
-            for (int g = 0; g < K; ++g) {
-              if (g != g0 || cc != c) continue;
-              if constexpr (RIG) {
-                LinMeta<T>::err(cm, 4)[g] = ch.ec[cc][g];
-                LinMeta<T>::off(cm, 4)[g] = ch.O[cc][g];
-              }
-              LinMeta<T>::mn(cm, 4)[g] = ch.mn[cc][g];
-              LinMeta<T>::mx(cm, 4)[g] = ch.mx[cc][g];
+          if (lane < 2 * K) {
+            const int c = lane / K, g = lane - c * K;
+            char* cm = (c ? right : parent) + D->off_eg + (par ^ 1) * D->copy_e;
+            if constexpr (RIG) {
+              LinMeta<T>::err(cm, 4)[g] = vec;
+              LinMeta<T>::off(cm, 4)[g] = vO;
             }
+            LinMeta<T>::mn(cm, 4)[g] = vmn;
+            LinMeta<T>::mx(cm, 4)[g] = vmx;
+          }
+          lin_children_bcast<T, K>(ch, vmn, vmx, vM, vec, vOh, vOl);
         }
         __syncwarp();
       }
@@ -764,27 +843,30 @@ __global__ void __launch_bounds__(256, 4) k2_lin_bound(Engine E, int cgmax) {
       char* right = list + (size_t)E.map[D->slot_off + k + Kl] * D->item_bytes;
       const int C = D->cg;
       __syncwarp();  // the previous unit's readers of the staging buffers are done
+      // the children's shared patches, and their metadata read by lane
+      // c K + g and broadcast
       LinChildren<T, K> ch;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
-        char* it = c ? right : left;
+        const char* it = c ? right : left;
         const T* cs = (const T*)(it + D->off_g + (par ^ 1) * D->copy_g);
         for (int e = lane; e < 4 * C; e += 32) sS[(size_t)c * 4 * cgmax + e] = cs[e];
-        char* mc = it + D->off_eg + (par ^ 1) * D->copy_e;
-#pragma unroll
-        for (int m = 0; m < K; ++m) {
-          ch.mn[c][m] = LinMeta<T>::mn(mc, 4)[m];
-          ch.mx[c][m] = LinMeta<T>::mx(mc, 4)[m];
+      }
+      {
+        T vmn = T(0), vmx = T(0);
+        float vM = 0.0f, vec = 0.0f, vOh = 0.0f, vOl = 0.0f;
+        if (lane < 2 * K) {
+          const int c = lane / K, g = lane - c * K;
+          char* mc = (c ? right : left) + D->off_eg + (par ^ 1) * D->copy_e;
+          vmn = LinMeta<T>::mn(mc, 4)[g];
+          vmx = LinMeta<T>::mx(mc, 4)[g];
           if constexpr (RIG) {
-            ch.Mabs[c][m] = fmaxf(fabsf((float)ch.mn[c][m]), fabsf((float)ch.mx[c][m]));
-            ch.ec[c][m] = LinMeta<T>::err(mc, 4)[m];
-            ch.O[c][m] = LinMeta<T>::off(mc, 4)[m];
-          } else {
-            ch.Mabs[c][m] = 0.0f;
-            ch.ec[c][m] = 0.0f;
-            ch.O[c][m] = 0.0;
+            vM = fmaxf(fabsf((float)vmn), fabsf((float)vmx));
+            vec = LinMeta<T>::err(mc, 4)[g];
+            lin_split_f64(LinMeta<T>::off(mc, 4)[g], vOh, vOl);
           }
         }
+        lin_children_bcast<T, K>(ch, vmn, vmx, vM, vec, vOh, vOl);
       }
       __syncwarp();
       lin_chunk<T, K>(E, D, p, k, Kl, t, left, right, sS, sS + 4 * (size_t)cgmax, ch, sIdx, sMw,
