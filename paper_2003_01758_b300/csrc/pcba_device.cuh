@@ -47,7 +47,10 @@
 #define PCBA_FAM_LIN 3        // refresh mark: every shared patch of a linear-family item
 #define PCBA_LIN32_STRIDE 16  // floats per FP32 row: the FP64 row rounded, then the remainders
 #define PCBA_LIN_BATCH 4     // units a warp of the linear subdivision kernel fetches at once
-#define PCBA_LIN_LIGHT 2     // items with at most this many live chunks are bounded by the split
+#define PCBA_LIN_LIGHT_MAX 96  // an item with <= 4 live chunks and at most this many active
+                               // constraints is bounded by the split kernel
+#define PCBA_LIN_WIN 64      // active constraints per queued window (unless a single chunk)
+#define PCBA_LIN_IDX 256     // compaction buffer of a warp (constraints per pass)
 
 struct ProbDesc {
   int l;

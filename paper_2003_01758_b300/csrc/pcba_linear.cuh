@@ -55,17 +55,19 @@
 //                  offset), the box and the slot map; the cost bounds go to
 //                  the child records.  The children's shared patches go to the
 //                  copy of the other parity, so the parent's stay readable.
-//                  The constraints of an item with at most PCBA_LIN_LIGHT live
-//                  chunks (chunks of PCBA_LIN_WORDS activity words with an
-//                  active constraint) are bounded here from the children
-//                  still staged in shared memory; the live chunks of the other
-//                  items are queued as (item, chunk).
-//   k2_lin_bound   one warp per queued (item, chunk): stages both children and
-//                  bounds the chunk's constraints as the split kernel does.
-// Bounding a chunk compacts its active constraints and bounds each on both
+//                  An item whose live chunks (chunks of PCBA_LIN_WORDS
+//                  activity words with an active constraint; at most 4) hold
+//                  at most PCBA_LIN_LIGHT_MAX active constraints is bounded
+//                  here from the children still staged in shared memory; the
+//                  live chunks of the other items are grouped into windows of
+//                  about PCBA_LIN_WIN active constraints, the first bounded
+//                  here and the others queued as (item, window).
+//   k2_lin_bound   one warp per queued (item, window): stages both children and
+//                  bounds the window's constraints as the split kernel does.
+// Bounding a window compacts its active constraints and bounds each on both
 // children from the stored extremes (interval bound) or, where that is
 // undecided, from the children's coefficients; it writes the children's
-// activity words and the chunk's summary bits, and publishes the bound maxima
+// activity words and its chunks' summary bits, and publishes the bound maxima
 // with one atomic per warp.
 #pragma once
 
@@ -170,13 +172,61 @@ __device__ __forceinline__ void lin_mark(const Engine& E, int mpar, int p, int s
 // k2_lin_bound: one warp per (parent item, chunk of activity words)
 // ---------------------------------------------------------------------------
 
+// Per-warp buffers of the constraint bounds, after the staged patches.
+struct LinScratch {
+  unsigned char* sCh;     // the children's metadata (a LinChildren), 256 bytes
+  unsigned* sMw;          // the children's words of a window, [2][32]
+  int* sWi;               // the window's word indices, [32]
+  unsigned* sWin;         // the windows of an item, [64]
+  unsigned short* sIdx;   // compacted constraints, [PCBA_LIN_IDX]
+  unsigned short* sCnt;   // active constraints per live chunk, [64]
+  unsigned char* sChunk;  // the live chunks, [64]
+};
+__host__ __device__ constexpr size_t lin_scratch_bytes() {
+  return 256 + 4 * 64 + 4 * 32 + 4 * 64 + 2 * PCBA_LIN_IDX + 2 * 64 + 64;
+}
+// base: 16-byte aligned
+__device__ __forceinline__ LinScratch lin_scratch(unsigned char* base) {
+  LinScratch s;
+  s.sCh = base;
+  s.sMw = (unsigned*)(base + 256);
+  s.sWi = (int*)(s.sMw + 64);
+  s.sWin = (unsigned*)(s.sWi + 32);
+  s.sIdx = (unsigned short*)(s.sWin + 64);
+  s.sCnt = s.sIdx + PCBA_LIN_IDX;
+  s.sChunk = (unsigned char*)(s.sCnt + 64);
+  return s;
+}
+
 // Bytes of shared memory one warp of k2_lin_bound uses: both children's
-// shared patches ([C][4] each), the compacted constraint indices and the
-// children's activity words.
+// shared patches ([C][4] each), then the constraint buffers.
 template <typename T>
 __host__ __device__ constexpr size_t lin_bound_warp_bytes(int cgmax) {
-  return (8 * (size_t)cgmax * sizeof(T) + 32 * PCBA_LIN_WORDS * sizeof(unsigned short) +
-          2 * PCBA_LIN_WORDS * sizeof(unsigned) + 15) / 16 * 16;
+  return (8 * (size_t)cgmax * sizeof(T) + 15) / 16 * 16 + lin_scratch_bytes();
+}
+
+// A window (first chunk t0 in bits 0..15, bit j of bits 16..31: chunk t0 + j
+// belongs to it; at most 4 chunks) as lane q's word: word q % 8 of the
+// window's (q / 8)-th chunk, its index wi (-1: none), value wv and summary
+// bit cb (0 without summaries).
+__device__ __forceinline__ void lin_window_words(const ProbDesc* D, const unsigned* pmask,
+                                                 unsigned win, bool summ, int& wi, unsigned& wv,
+                                                 unsigned long long& cb) {
+  const int lane = threadIdx.x & 31;
+  wi = -1;
+  wv = 0u;
+  cb = 0ull;
+  unsigned m = win >> 16;
+  for (int i = 0; i < (lane >> 3); ++i) m &= m - 1u;
+  if (m != 0u) {
+    const int t = (int)(win & 0xFFFFu) + __ffs(m) - 1;
+    const int w = t * PCBA_LIN_WORDS + (lane & 7);
+    if (w < D->mwords) {
+      wi = w;
+      wv = pmask[w];
+      cb = summ ? 1ull << t : 0ull;
+    }
+  }
 }
 
 // Coefficient range of cc + sum_m w_m s_mj over the C coefficients of one
@@ -214,34 +264,17 @@ __device__ __forceinline__ void lin_range(const T* s, int C, T cc, const T (&w)[
   hi = max(hi0, hi1);
 }
 
-// Both children's metadata (the same in every lane): extremes of the stored
-// values of each shared patch and, in FP32, their error bounds and offsets
-// (the FP64 offset O split into FP32 values, O = Oh + Ol to 2^-48 |O|).
+// Both children's metadata (kept in shared memory, written by lane c K + g
+// for child c and shared patch g): extremes of the stored values of each
+// shared patch and, in FP32, their error bounds and offsets (the FP64 offset
+// O split into FP32 values, O = Oh + Ol to 2^-48 |O|).  At most 256 bytes.
 template <typename T, int K>
 struct LinChildren {
   T mn[2][K], mx[2][K];
   float Mabs[2][K], ec[2][K];
   float Oh[2][K], Ol[2][K];
 };
-
-// Lanes c K + g (c < 2, g < K) hold child c's values of shared patch g; every
-// lane receives all of them.
-template <typename T, int K>
-__device__ __forceinline__ void lin_children_bcast(LinChildren<T, K>& ch, T mn, T mx, float Mabs,
-                                                   float ec, float Oh, float Ol) {
-#pragma unroll
-  for (int c = 0; c < 2; ++c)
-#pragma unroll
-    for (int g = 0; g < K; ++g) {
-      const int src = c * K + g;
-      ch.mn[c][g] = __shfl_sync(0xffffffffu, mn, src);
-      ch.mx[c][g] = __shfl_sync(0xffffffffu, mx, src);
-      ch.Mabs[c][g] = __shfl_sync(0xffffffffu, Mabs, src);
-      ch.ec[c][g] = __shfl_sync(0xffffffffu, ec, src);
-      ch.Oh[c][g] = __shfl_sync(0xffffffffu, Oh, src);
-      ch.Ol[c][g] = __shfl_sync(0xffffffffu, Ol, src);
-    }
-}
+static_assert(sizeof(LinChildren<double, PCBA_MAX_SHARED>) <= 256, "metadata area of a warp");
 
 // An FP64 value as two FP32 values, x = hi + lo to 2^-48 |x| (x - hi is
 // exact in FP64).
@@ -280,29 +313,34 @@ __device__ __forceinline__ void lin_kappa(const float* hv, const float* lv, cons
   ekap = __fadd_ru(__fmul_ru(A, 0x1p-40f), (float)(8 * K + 2) * 0x1p-149f);
 }
 
-// Chunk t of the activity words of parent item k (problem p, list length Kl):
-// its active constraints are compacted and bounded on both children (shared
-// patches staged at sL / sR, [C][4]), the children's words and the chunk's
-// summary bits are written and the bound maxima go to the child records.  One
-// warp; sIdx / sMw are its compaction and word buffers.
+// A window of up to 32 of parent item k's activity words (problem p, list
+// length Kl): lane q holds the index wi of one of the item's words (-1:
+// none), its value word and its chunk's summary bit cbit (0 without
+// summaries).  The window holds at most PCBA_LIN_IDX active constraints (a
+// single chunk at most PCBA_LIN_WORDS x 32, several at most PCBA_LIN_WIN, a
+// light item at most PCBA_LIN_LIGHT_MAX).  They are compacted and bounded on
+// both children (shared patches staged at sL / sR,
+// [C][4]); the children's words and their chunks' summary bits are written
+// and the bound maxima go to the child records.  One warp; sIdx, sMw (the
+// children's words, 2 x 32) and sWi (the 32 word indices) are its buffers.
+static_assert(PCBA_LIN_WORDS * 32 <= PCBA_LIN_IDX && PCBA_LIN_WIN <= PCBA_LIN_IDX &&
+                  PCBA_LIN_LIGHT_MAX <= PCBA_LIN_IDX,
+              "a window's active constraints fit the compaction buffer");
 template <typename T, int K>
-__device__ void lin_chunk(const Engine& E, const ProbDesc* D, int p, int k, int Kl, int t,
-                          char* left, char* right, const T* sL, const T* sR,
-                          const LinChildren<T, K>& ch, unsigned short* sIdx, unsigned* sMw,
-                          int par) {
+__device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int Kl, int wi,
+                           unsigned word, unsigned long long cbit, char* left, char* right,
+                           const T* sL, const T* sR, const LinChildren<T, K>& ch,
+                           unsigned short* sIdx, unsigned* sMw, int* sWi, int par) {
   constexpr bool RIG = sizeof(T) == 4;
   constexpr float u24 = 0x1p-24f;
   const int lane = threadIdx.x & 31;
   const long long slot_off = D->slot_off;
-  const int C = D->cg, mwords = D->mwords;
-  const int w0 = t * PCBA_LIN_WORDS;
-  const int nw = min(PCBA_LIN_WORDS, mwords - w0);
-  unsigned* pm = (unsigned*)(left + D->off_mask) + w0;  // the parent's words, in place
-  unsigned* rm = (unsigned*)(right + D->off_mask) + w0;
+  const int C = D->cg;
+  unsigned* pm = (unsigned*)(left + D->off_mask);  // the parent's words, in place
+  unsigned* rm = (unsigned*)(right + D->off_mask);
   unsigned long long* sumL = (unsigned long long*)(left + D->off_sum) + (par ^ 1);
   unsigned long long* sumR = (unsigned long long*)(right + D->off_sum) + (par ^ 1);
-  const unsigned long long tb = D->lin_chunks <= 64 ? (1ull << t) : 0ull;
-  const unsigned word = lane < nw ? pm[lane] : 0u;
+  if (wi < 0) word = 0u;
   const unsigned cnt = __popc(word);
   unsigned incl = cnt;
 #pragma unroll
@@ -314,10 +352,17 @@ __device__ void lin_chunk(const Engine& E, const ProbDesc* D, int p, int k, int 
   if (na == 0) {
     // no active constraint here: the children's words are zero (the left
     // child shares the parent's, already zero)
-    if (lane < nw) rm[lane] = 0u;
+    if (wi >= 0) rm[wi] = 0u;
     return;
   }
-  __syncwarp();  // earlier readers of sIdx and sMw are done
+  __syncwarp();  // earlier readers of the buffers are done
+  sWi[lane] = wi;
+  sMw[lane] = 0u;
+  sMw[32 + lane] = 0u;
+  T gmax[2] = {T(-INFINITY), T(-INFINITY)}, gmin[2] = {T(-INFINITY), T(-INFINITY)};
+  bool mark[2] = {false, false};
+  unsigned nfull = 0;  // coefficient-range evaluations of this lane
+  const int Kw = K;
   {
     unsigned pos = incl - cnt, bits = word;
     while (bits) {
@@ -326,15 +371,10 @@ __device__ void lin_chunk(const Engine& E, const ProbDesc* D, int p, int k, int 
       sIdx[pos++] = (unsigned short)(lane * 32 + b);
     }
   }
-  if (lane < 2 * PCBA_LIN_WORDS) sMw[lane] = 0u;
   __syncwarp();
-  T gmax[2] = {T(-INFINITY), T(-INFINITY)}, gmin[2] = {T(-INFINITY), T(-INFINITY)};
-  bool mark[2] = {false, false};
-  unsigned nfull = 0;  // coefficient-range evaluations of this lane
-  const int Kw = K;
   for (unsigned q = lane; q < na; q += 32) {
     const int li = sIdx[q];
-    const long long row = D->lin_off + (long long)w0 * 32 + li;
+    const long long row = D->lin_off + (long long)sWi[li >> 5] * 32 + (li & 31);
     T w[K], cc[2];
     float E64[2] = {0.0f, 0.0f};  // FP32: bound of the error of the constant term
     if constexpr (RIG) {
@@ -410,7 +450,7 @@ __device__ void lin_chunk(const Engine& E, const ProbDesc* D, int p, int k, int 
       const bool sat = up <= T(0);
       const bool inf = dn > T(0);
       if (!sat) {
-        atomicOr(&sMw[c * PCBA_LIN_WORDS + (li >> 5)], 1u << (li & 31));
+        atomicOr(&sMw[c * 32 + (li >> 5)], 1u << (li & 31));
         gmax[c] = max(gmax[c], up);
         gmin[c] = max(gmin[c], dn);
       }
@@ -423,18 +463,22 @@ __device__ void lin_chunk(const Engine& E, const ProbDesc* D, int p, int k, int 
       }
     }
   }
-  __syncwarp();
-  if (lane < nw) {
-    pm[lane] = sMw[lane];                      // left child: in place (this unit's words)
-    rm[lane] = sMw[PCBA_LIN_WORDS + lane];     // right child
+  if (wi >= 0) {
+    pm[wi] = sMw[lane];       // left child: in place (this window's words)
+    rm[wi] = sMw[32 + lane];  // right child
   }
-  const bool keepL = __any_sync(0xffffffffu, lane < nw && sMw[lane] != 0u);
-  const bool keepR = __any_sync(0xffffffffu, lane < nw && sMw[PCBA_LIN_WORDS + lane] != 0u);
+  // the summary bits of the chunks that keep an active constraint
+  const unsigned long long kl = (wi >= 0 && sMw[lane] != 0u) ? cbit : 0ull;
+  const unsigned long long kr = (wi >= 0 && sMw[32 + lane] != 0u) ? cbit : 0ull;
+  const unsigned long long keepL =
+      ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(kl >> 32)) << 32) |
+      __reduce_or_sync(0xffffffffu, (unsigned)kl);
+  const unsigned long long keepR =
+      ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(kr >> 32)) << 32) |
+      __reduce_or_sync(0xffffffffu, (unsigned)kr);
   if (lane == 0) {
-    if (tb) {
-      if (keepL) atomicOr(sumL, tb);
-      if (keepR) atomicOr(sumR, tb);
-    }
+    if (keepL) atomicOr(sumL, keepL);
+    if (keepR) atomicOr(sumR, keepR);
     atomicAdd(&E.plan->lin_pairs, 2ull * na);
   }
   const unsigned full = __reduce_add_sync(0xffffffffu, nfull);
@@ -453,7 +497,7 @@ __device__ void lin_chunk(const Engine& E, const ProbDesc* D, int p, int k, int 
     const MarkCtx mk{p, k, k + Kl, E.marks + (size_t)par * E.mark_cap,
                      &E.plan->mark_count[par], E.mark_cap};
     // one mark per child for all its shared patches (family PCBA_FAM_LIN),
-    // the first chunk to ask for it sets bit 32 of the child record's perr
+    // the first window to ask for it sets bit 32 of the child record's perr
     // (the split kernel wrote the error bits below it this step)
     bool ml = __any_sync(0xffffffffu, mark[0]), mr = __any_sync(0xffffffffu, mark[1]);
     if (lane == 0) {
@@ -472,9 +516,8 @@ __device__ void lin_chunk(const Engine& E, const ProbDesc* D, int p, int k, int 
 // compacted constraint indices and the children's activity words of one chunk.
 template <typename T>
 __host__ __device__ constexpr size_t lin_split_warp_bytes(int cgmax, int cpmax) {
-  return ((3 * (size_t)cpmax + 12 * (size_t)cgmax) * sizeof(T) +
-          32 * PCBA_LIN_WORDS * sizeof(unsigned short) + 2 * PCBA_LIN_WORDS * sizeof(unsigned) +
-          15) / 16 * 16;
+  return ((3 * (size_t)cpmax + 12 * (size_t)cgmax) * sizeof(T) + 15) / 16 * 16 +
+         lin_scratch_bytes();
 }
 
 // Extremes of the two children of one patch group (the cost, or one shared
@@ -520,8 +563,16 @@ __device__ __forceinline__ void lin_fibre(const T* src, T* dL, T* dR, int sst, L
 
 // NFIX > 0: every patch of the batch has degree NFIX along every axis (a
 // smaller kernel body); 0: any degree up to 16.
+// Resident blocks per SM the register allocation of the two kernels aims at.
+#ifndef PCBA_LIN_SPLIT_BLOCKS
+#define PCBA_LIN_SPLIT_BLOCKS 2
+#endif
+#ifndef PCBA_LIN_BOUND_BLOCKS
+#define PCBA_LIN_BOUND_BLOCKS 3
+#endif
+
 template <typename T, int K, int NFIX>
-__global__ void __launch_bounds__(256, 3) k2_lin_split(Engine E, int cgmax, int cpmax) {
+__global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engine E, int cgmax, int cpmax) {
   constexpr bool RIG = sizeof(T) == 4;
   constexpr float u24 = 0x1p-24f;
   extern __shared__ __align__(16) unsigned char kls[];
@@ -534,8 +585,10 @@ __global__ void __launch_bounds__(256, 3) k2_lin_split(Engine E, int cgmax, int 
   T* sc = spR + 4 * (size_t)cgmax;  // parent cost patch and its children
   T* scL = sc + cpmax;
   T* scR = scL + cpmax;
-  unsigned short* sIdx = (unsigned short*)(scR + cpmax);
-  unsigned* sMw = (unsigned*)(sIdx + 32 * PCBA_LIN_WORDS);
+  const LinScratch ls = lin_scratch(
+      (unsigned char*)sp + ((3 * (size_t)cpmax + 12 * (size_t)cgmax) * sizeof(T) + 15) / 16 * 16);
+  // the children's metadata, warp-uniform: read by broadcast from shared memory
+  LinChildren<T, K>& ch = *reinterpret_cast<LinChildren<T, K>*>(ls.sCh);
   const unsigned items = E.plan->kr_units;
   const int par = E.plan->steps_global & 1;  // copy read this step; children go to par ^ 1
   const double cost_thr = E.params->opt_tol * (1.0 / 64.0);
@@ -693,7 +746,6 @@ __global__ void __launch_bounds__(256, 3) k2_lin_split(Engine E, int cgmax, int 
       }
       // ---- shared children, re-centred likewise, to the other copy, with
       // their metadata (error bound, offset, extremes of the stored values)
-      LinChildren<T, K> ch;
       if (any) {
         T sh[2][K];
 #pragma unroll
@@ -769,44 +821,138 @@ __global__ void __launch_bounds__(256, 3) k2_lin_split(Engine E, int cgmax, int 
             }
             LinMeta<T>::mn(cm, 4)[g] = vmn;
             LinMeta<T>::mx(cm, 4)[g] = vmx;
+            ch.mn[c][g] = vmn;
+            ch.mx[c][g] = vmx;
+            ch.Mabs[c][g] = vM;
+            ch.ec[c][g] = vec;
+            ch.Oh[c][g] = vOh;
+            ch.Ol[c][g] = vOl;
           }
-          lin_children_bcast<T, K>(ch, vmn, vmx, vM, vec, vOh, vOl);
         }
         __syncwarp();
       }
-      // ---- the constraints.  The children's summaries start empty (each live
-      // chunk sets its bits) and their words of chunks without an active
-      // constraint are zero; an item with few live chunks is bounded here,
-      // from the staged children, the live chunks of the others go to the
-      // bound kernel's queue (or stay here when it is full)
+      // ---- the constraints.  The children's summaries start empty (each
+      // window sets the bits of its chunks that keep an active constraint)
+      // and their words of chunks without one are zero.  An item whose live
+      // chunks (at most 4) hold at most PCBA_LIN_LIGHT_MAX active
+      // constraints is bounded here, from the children still staged.  The
+      // live chunks of the other items are grouped into windows (at most 4
+      // chunks within 16 consecutive ones, at most PCBA_LIN_WIN active
+      // constraints unless a single chunk) and queued for k2_lin_bound; the
+      // first window, and those the full queue refuses, stay here.
       {
-        // (more than 64 chunks keep no summaries: every chunk is read)
-        const int chunks = D->lin_chunks;
-        const bool summ = chunks <= 64;
+        const int chunks = D->lin_chunks, mwords = D->mwords;
+        const bool summ = chunks <= 64;  // (more chunks keep no summaries: all are read)
         const unsigned long long psum =
             summ ? *((const unsigned long long*)(parent + D->off_sum) + par) : 0ull;
-        auto live = [&](int t) { return summ ? ((psum >> t) & 1ull) != 0ull : true; };
         if (lane == 0 && summ) {
           *((unsigned long long*)(parent + D->off_sum) + (par ^ 1)) = 0ull;
           *((unsigned long long*)(right + D->off_sum) + (par ^ 1)) = 0ull;
         }
+        const unsigned* pmask = (const unsigned*)(parent + D->off_mask);
         unsigned* rmask = (unsigned*)(right + D->off_mask);
-        for (int q = lane; q < D->mwords; q += 32)
-          if (!live(q / PCBA_LIN_WORDS)) rmask[q] = 0u;
+        if (summ)
+          for (int q = lane; q < mwords; q += 32)
+            if (!((psum >> (q / PCBA_LIN_WORDS)) & 1ull)) rmask[q] = 0u;
         __syncwarp();
-        const bool light = summ && __popcll(psum) <= PCBA_LIN_LIGHT;
-        for (int t = 0; t < chunks; ++t) {
-          if (!live(t)) continue;
-          if (!light) {
-            unsigned q = 0;
-            if (lane == 0) q = atomicAdd(&E.plan->lin_qcount, 1u);
-            q = __shfl_sync(0xffffffffu, q, 0);
-            if (q < E.lin_qcap) {
-              if (lane == 0) E.lin_queue[q] = make_uint2(u, (unsigned)t);
-              continue;
+        const int nlive = summ ? __popcll(psum) : chunks;
+        // what this warp bounds itself: mode 1 the light window (lane words
+        // lwi / lwv / lcb), 2 the windows in ls.sWin the queue refused (and
+        // the first), 3 the single-chunk windows the queue refused
+        int mode = 0, nwin = 0;
+        unsigned qb = 0u;
+        int lwi = -1;
+        unsigned lwv = 0u;
+        unsigned long long lcb = 0ull;
+        if (nlive > 0 && summ && nlive <= 4) {
+          // lane q: word q % 8 of the (q / 8)-th live chunk
+          const int j = lane >> 3;
+          if (j < nlive) {
+            unsigned long long m = psum;
+            for (int i2 = 0; i2 < j; ++i2) m &= m - 1ull;
+            const int t = __ffsll((long long)m) - 1;
+            const int w = t * PCBA_LIN_WORDS + (lane & 7);
+            if (w < mwords) {
+              lwi = w;
+              lwv = pmask[w];
+              lcb = 1ull << t;
             }
           }
-          lin_chunk<T, K>(E, D, p, k, Kl, t, parent, right, spL, spR, ch, sIdx, sMw, par);
+          if (__reduce_add_sync(0xffffffffu, (unsigned)__popc(lwv)) <= PCBA_LIN_LIGHT_MAX) mode = 1;
+        }
+        if (nlive > 0 && summ && mode == 0) {
+          // the live chunks in order and their active constraints
+          for (int t = lane; t < 64; t += 32)
+            if ((psum >> t) & 1ull)
+              ls.sChunk[__popcll(psum & ((1ull << t) - 1ull))] = (unsigned char)t;
+          __syncwarp();
+          for (int j0 = 0; j0 < nlive; j0 += 4) {
+            const int j = j0 + (lane >> 3);
+            unsigned c = 0u;
+            if (j < nlive) {
+              const int w = ls.sChunk[j] * PCBA_LIN_WORDS + (lane & 7);
+              if (w < mwords) c = __popc(pmask[w]);
+            }
+            c += __shfl_xor_sync(0xffffffffu, c, 1);
+            c += __shfl_xor_sync(0xffffffffu, c, 2);
+            c += __shfl_xor_sync(0xffffffffu, c, 4);
+            if ((lane & 7) == 0 && j < nlive) ls.sCnt[j] = (unsigned short)c;
+          }
+          __syncwarp();
+          // the windows, formed greedily by lane 0
+          if (lane == 0) {
+            int j = 0;
+            while (j < nlive) {
+              const int t0 = ls.sChunk[j];
+              unsigned mask = 1u, cw = ls.sCnt[j];
+              int nch = 1;
+              ++j;
+              while (j < nlive && nch < 4 && ls.sChunk[j] - t0 < 16 &&
+                     cw + ls.sCnt[j] <= (unsigned)PCBA_LIN_WIN) {
+                mask |= 1u << (ls.sChunk[j] - t0);
+                cw += ls.sCnt[j];
+                ++nch;
+                ++j;
+              }
+              ls.sWin[nwin++] = (unsigned)t0 | (mask << 16);
+            }
+          }
+          nwin = __shfl_sync(0xffffffffu, nwin, 0);
+          __syncwarp();
+          if (lane == 0 && nwin > 1) qb = atomicAdd(&E.plan->lin_qcount, (unsigned)(nwin - 1));
+          qb = __shfl_sync(0xffffffffu, qb, 0);
+          for (int i2 = 1 + lane; i2 < nwin; i2 += 32) {
+            const unsigned q = qb + (unsigned)(i2 - 1);
+            if (q < E.lin_qcap) E.lin_queue[q] = make_uint2(u, ls.sWin[i2]);
+          }
+          mode = 2;
+        }
+        if (nlive > 0 && !summ) {
+          // no summaries: every chunk is a window of its own, queued
+          if (lane == 0) qb = atomicAdd(&E.plan->lin_qcount, (unsigned)chunks);
+          qb = __shfl_sync(0xffffffffu, qb, 0);
+          for (int t = lane; t < chunks; t += 32)
+            if (qb + (unsigned)t < E.lin_qcap)
+              E.lin_queue[qb + (unsigned)t] = make_uint2(u, (unsigned)t | (1u << 16));
+          mode = 3;
+        }
+        for (int i2 = 0; mode != 0; ++i2) {
+          int wi = lwi;
+          unsigned wv = lwv;
+          unsigned long long cb = lcb;
+          if (mode == 1) {
+            if (i2 > 0) break;
+          } else if (mode == 2) {
+            while (i2 > 0 && i2 < nwin && qb + (unsigned)(i2 - 1) < E.lin_qcap) ++i2;
+            if (i2 >= nwin) break;
+            lin_window_words(D, pmask, ls.sWin[i2], true, wi, wv, cb);
+          } else {
+            while (i2 < chunks && qb + (unsigned)i2 < E.lin_qcap) ++i2;
+            if (i2 >= chunks) break;
+            lin_window_words(D, pmask, (unsigned)i2 | (1u << 16), false, wi, wv, cb);
+          }
+          lin_window<T, K>(E, D, p, k, Kl, wi, wv, cb, parent, right, spL, spR, ch, ls.sIdx,
+                           ls.sMw, ls.sWi, par);
         }
       }
       __syncwarp();  // the staging buffers are reused by the next item
@@ -817,13 +963,14 @@ __global__ void __launch_bounds__(256, 3) k2_lin_split(Engine E, int cgmax, int 
 // Heavy items' live chunks, queued by k2_lin_split as (item, chunk): the
 // children are staged from memory.
 template <typename T, int K>
-__global__ void __launch_bounds__(256, 4) k2_lin_bound(Engine E, int cgmax) {
+__global__ void __launch_bounds__(256, PCBA_LIN_BOUND_BLOCKS) k2_lin_bound(Engine E, int cgmax) {
   constexpr bool RIG = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char klb[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   T* sS = (T*)(klb + (size_t)warp * lin_bound_warp_bytes<T>(cgmax));  // children [2][C][4]
-  unsigned short* sIdx = (unsigned short*)(sS + 8 * (size_t)cgmax);
-  unsigned* sMw = (unsigned*)(sIdx + 32 * PCBA_LIN_WORDS);
+  const LinScratch ls =
+      lin_scratch((unsigned char*)sS + (8 * (size_t)cgmax * sizeof(T) + 15) / 16 * 16);
+  LinChildren<T, K>& ch = *reinterpret_cast<LinChildren<T, K>*>(ls.sCh);
   const unsigned units = min(E.plan->lin_qcount, E.lin_qcap);
   const int par = E.plan->steps_global & 1;  // the children's data is in copy par ^ 1
   for (;;) {
@@ -836,7 +983,7 @@ __global__ void __launch_bounds__(256, 4) k2_lin_bound(Engine E, int cgmax) {
       const uint2 ent = E.lin_queue[q];
       const int p = find_problem(E.kr_pre, E.np, ent.x);
       const ProbDesc* D = E.desc + p;
-      const int k = (int)(ent.x - E.kr_pre[p]), t = (int)ent.y;
+      const int k = (int)(ent.x - E.kr_pre[p]);
       const int Kl = E.state[p].K;
       char* list = E.arena + D->list_off;
       char* left = list + (size_t)E.map[D->slot_off + k] * D->item_bytes;
@@ -845,7 +992,6 @@ __global__ void __launch_bounds__(256, 4) k2_lin_bound(Engine E, int cgmax) {
       __syncwarp();  // the previous unit's readers of the staging buffers are done
       // the children's shared patches, and their metadata read by lane
       // c K + g and broadcast
-      LinChildren<T, K> ch;
 #pragma unroll
       for (int c = 0; c < 2; ++c) {
         const char* it = c ? right : left;
@@ -865,12 +1011,22 @@ __global__ void __launch_bounds__(256, 4) k2_lin_bound(Engine E, int cgmax) {
             vec = LinMeta<T>::err(mc, 4)[g];
             lin_split_f64(LinMeta<T>::off(mc, 4)[g], vOh, vOl);
           }
+          ch.mn[c][g] = vmn;
+          ch.mx[c][g] = vmx;
+          ch.Mabs[c][g] = vM;
+          ch.ec[c][g] = vec;
+          ch.Oh[c][g] = vOh;
+          ch.Ol[c][g] = vOl;
         }
-        lin_children_bcast<T, K>(ch, vmn, vmx, vM, vec, vOh, vOl);
       }
+      int wi;
+      unsigned wv;
+      unsigned long long cb;
+      lin_window_words(D, (const unsigned*)(left + D->off_mask), ent.y, D->lin_chunks <= 64, wi,
+                       wv, cb);
       __syncwarp();
-      lin_chunk<T, K>(E, D, p, k, Kl, t, left, right, sS, sS + 4 * (size_t)cgmax, ch, sIdx, sMw,
-                      par);
+      lin_window<T, K>(E, D, p, k, Kl, wi, wv, cb, left, right, sS, sS + 4 * (size_t)cgmax, ch,
+                       ls.sIdx, ls.sMw, ls.sWi, par);
     }
   }
 }
