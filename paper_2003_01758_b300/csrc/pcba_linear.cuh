@@ -229,17 +229,18 @@ __device__ __forceinline__ void lin_window_words(const ProbDesc* D, const unsign
   }
 }
 
-// Coefficient range of cc + sum_m w_m s_mj over the C coefficients of one
-// child staged in shared memory ([C][4]); two partial extremes per bound.
+// Range of cc + sum_m w_m s_mj over the coefficients j = j0, j0 + G, ... of
+// one child staged in shared memory ([C][4]); two partial extremes per bound.
 template <typename T, int K>
-__device__ __forceinline__ void lin_range(const T* s, int C, T cc, const T (&w)[K], T& lo, T& hi) {
+__device__ __forceinline__ void lin_range(const T* s, int C, T cc, const T (&w)[K], int j0, int G,
+                                          T& lo, T& hi) {
   T lo0 = T(INFINITY), hi0 = T(-INFINITY), lo1 = T(INFINITY), hi1 = T(-INFINITY);
-  int j = 0;
+  int j = j0;
 #pragma unroll 2
-  for (; j + 1 < C; j += 2) {
+  for (; j + G < C; j += 2 * G) {
     T a[K], b[K];
     lin_load<T, K>(s + (size_t)j * 4, a);
-    lin_load<T, K>(s + (size_t)(j + 1) * 4, b);
+    lin_load<T, K>(s + (size_t)(j + G) * 4, b);
     T v0 = cc, v1 = cc;
 #pragma unroll
     for (int m = 0; m < K; ++m) {
@@ -363,6 +364,11 @@ __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int
   bool mark[2] = {false, false};
   unsigned nfull = 0;  // coefficient-range evaluations of this lane
   const int Kw = K;
+  // lanes per constraint: G lanes share one constraint's coefficients when
+  // the window has few (G a power of 2, na G <= 32, at most 8)
+  const int G = na > 16 ? 1 : (na > 8 ? 2 : (na > 4 ? 4 : 8));
+  const int gsub = lane & (G - 1);
+  const unsigned per = 32u / (unsigned)G;
   {
     unsigned pos = incl - cnt, bits = word;
     while (bits) {
@@ -372,8 +378,11 @@ __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int
     }
   }
   __syncwarp();
-  for (unsigned q = lane; q < na; q += 32) {
-    const int li = sIdx[q];
+  for (unsigned q0 = 0; q0 < na; q0 += per) {
+    // (the lanes past the last constraint repeat the first one and drop it)
+    const unsigned q = q0 + (unsigned)lane / (unsigned)G;
+    const bool act = q < na;
+    const int li = sIdx[act ? q : 0u];
     const long long row = D->lin_off + (long long)sWi[li >> 5] * 32 + (li & 31);
     T w[K], cc[2];
     float E64[2] = {0.0f, 0.0f};  // FP32: bound of the error of the constant term
@@ -436,16 +445,26 @@ __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int
       lo[c] = x0;
       hi[c] = x1;
     }
-    // undecided by the interval: the coefficient range itself (Alg. 3)
+    // undecided by the interval: the coefficient range itself (Alg. 3), the
+    // G lanes of the constraint taking every G-th coefficient
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
-      if (!(add_up(hi[c], Et[c]) <= T(0)) && !(sub_dn(lo[c], Et[c]) > T(0))) {
-        lin_range<T, K>(c ? sR : sL, C, cc[c], w, lo[c], hi[c]);
-        ++nfull;
+      const bool need = !(add_up(hi[c], Et[c]) <= T(0)) && !(sub_dn(lo[c], Et[c]) > T(0));
+      T rl = T(INFINITY), rh = T(-INFINITY);
+      if (need) lin_range<T, K>(c ? sR : sL, C, cc[c], w, gsub, G, rl, rh);
+      for (int o = 1; o < G; o <<= 1) {
+        rl = min(rl, __shfl_xor_sync(0xffffffffu, rl, o));
+        rh = max(rh, __shfl_xor_sync(0xffffffffu, rh, o));
+      }
+      if (need) {
+        lo[c] = rl;
+        hi[c] = rh;
+        if (act && gsub == 0) ++nfull;
       }
     }
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
+      if (!act || gsub != 0) continue;
       const T up = add_up(hi[c], Et[c]), dn = sub_dn(lo[c], Et[c]);
       const bool sat = up <= T(0);
       const bool inf = dn > T(0);
