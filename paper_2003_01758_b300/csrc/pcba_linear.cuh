@@ -158,6 +158,36 @@ __device__ __forceinline__ void lin_store(T* p, const T (&v)[NP]) {
   }
 }
 
+// Copies n1 elements of T from s1 to d1 and n2 from s2 to d2 (global to
+// shared memory, all four 16-byte aligned) in 16-byte pieces, a lane's loads
+// issued before its stores (U at a time); one warp.
+template <typename T, int U>
+__device__ __forceinline__ void lin_copy2(T* d1, const T* s1, int n1, T* d2, const T* s2, int n2,
+                                          int lane) {
+  constexpr int V = 16 / (int)sizeof(T);
+  const int a = n1 / V, b = n2 / V, n = a + b;
+  const float4* x1 = (const float4*)s1;
+  const float4* x2 = (const float4*)s2;
+  for (int e0 = lane; e0 < n; e0 += 32 * U) {
+    float4 v[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + 32 * u;
+      if (e < n) v[u] = e < a ? x1[e] : x2[e - a];
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int e = e0 + 32 * u;
+      if (e < n) {
+        if (e < a) ((float4*)d1)[e] = v[u];
+        else ((float4*)d2)[e - a] = v[u];
+      }
+    }
+  }
+  for (int e = a * V + lane; e < n1; e += 32) d1[e] = s1[e];
+  for (int e = b * V + lane; e < n2; e += 32) d2[e] = s2[e];
+}
+
 // One mark (problem, child slot, family, patch) for k_refresh.
 __device__ __forceinline__ void lin_mark(const Engine& E, int mpar, int p, int slot, int fam,
                                          int ip) {
@@ -649,10 +679,8 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
       // ---- stage the parent (coalesced)
       T* pc = (T*)(parent + D->off_cost);
       T* rc = (T*)(right + D->off_cost);
-      for (int j = lane; j < cp; j += 32) sc[j] = pc[j];
       const T* gs = (const T*)(parent + D->off_g + par * D->copy_g);
-      if (any)
-        for (int e = lane; e < 4 * C; e += 32) sp[e] = gs[e];
+      lin_copy2<T, 4>(sc, pc, cp, sp, gs, any ? 4 * C : 0, lane);
       char* pm = parent + D->off_eg + par * D->copy_e;
       double Oc = 0.0, Om[K];
       float ecost = 0.0f, em[K];
@@ -727,34 +755,33 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
         pc[j] = addrn(scL[j], -shc[0]);
         rc[j] = addrn(scR[j], -shc[1]);
       }
-      if (lane == 0) {
+      // the cost records (lane c for child c) and the box and slot map (lane 2)
+      if (lane < 2) {
+        const int c = lane;
+        const T cmn = c ? acc[0].mnR : acc[0].mnL, cmx = c ? acc[0].mxR : acc[0].mxL;
+        ChildRec* rec = c ? recR : recL;
         if constexpr (RIG) {
           const float e1 = __fadd_ru(__fadd_ru(ecost, __fmul_ru(acc[0].am, (float)nc * u24)),
                                      (float)nc * 0x1p-149f);
-#pragma unroll
-          for (int c = 0; c < 2; ++c) {
-            const float smin = __fsub_rn(c ? acc[0].mnR : acc[0].mnL, shc[c]);
-            const float smax = __fsub_rn(c ? acc[0].mxR : acc[0].mxL, shc[c]);
-            const float Mr = fmaxf(fabsf(smin), fabsf(smax));
-            const double On = Oc + (double)shc[c];
-            const float e2 = __fadd_ru(__fadd_ru(__fadd_ru(e1, __fmul_ru(Mr, u24)), 0x1p-149f),
-                                       __double2float_ru(__dmul_ru(fabs(On), 0x1p-52)));
-            char* it = c ? right : parent;
-            *(double*)(it + 32) = On;
-            *(float*)(it + 40) = e2;
-            ChildRec* rec = c ? recR : recL;
-            rec->pmin = okey(__dsub_rd(__dadd_rd(On, (double)smin), (double)e2));
-            rec->pmax = okey(__dadd_ru(__dadd_ru(On, (double)smax), (double)e2));
-            rec->perr = __float_as_uint(e2);
-            if ((double)e2 > cost_thr) lin_mark(E, par, p, c ? k + Kl : k, 2, 0);
-          }
+          const float sh = c ? shc[1] : shc[0];
+          const float smin = __fsub_rn(cmn, sh);
+          const float smax = __fsub_rn(cmx, sh);
+          const float Mr = fmaxf(fabsf(smin), fabsf(smax));
+          const double On = Oc + (double)sh;
+          const float e2 = __fadd_ru(__fadd_ru(__fadd_ru(e1, __fmul_ru(Mr, u24)), 0x1p-149f),
+                                     __double2float_ru(__dmul_ru(fabs(On), 0x1p-52)));
+          char* it = c ? right : parent;
+          *(double*)(it + 32) = On;
+          *(float*)(it + 40) = e2;
+          rec->pmin = okey(__dsub_rd(__dadd_rd(On, (double)smin), (double)e2));
+          rec->pmax = okey(__dadd_ru(__dadd_ru(On, (double)smax), (double)e2));
+          rec->perr = __float_as_uint(e2);
+          if ((double)e2 > cost_thr) lin_mark(E, par, p, c ? k + Kl : k, 2, 0);
         } else {
-          recL->pmin = okey((double)acc[0].mnL);
-          recL->pmax = okey((double)acc[0].mxL);
-          recR->pmin = okey((double)acc[0].mnR);
-          recR->pmax = okey((double)acc[0].mxR);
+          rec->pmin = okey((double)cmn);
+          rec->pmax = okey((double)cmx);
         }
-        // box and slot map
+      } else if (lane == 2) {
         E.map[slot_off + k + Kl] = rslot;
         unsigned* iL = (unsigned*)parent;
         unsigned* iR = (unsigned*)right;
@@ -1009,14 +1036,10 @@ __global__ void __launch_bounds__(256, PCBA_LIN_BOUND_BLOCKS) k2_lin_bound(Engin
       char* right = list + (size_t)E.map[D->slot_off + k + Kl] * D->item_bytes;
       const int C = D->cg;
       __syncwarp();  // the previous unit's readers of the staging buffers are done
-      // the children's shared patches, and their metadata read by lane
-      // c K + g and broadcast
-#pragma unroll
-      for (int c = 0; c < 2; ++c) {
-        const char* it = c ? right : left;
-        const T* cs = (const T*)(it + D->off_g + (par ^ 1) * D->copy_g);
-        for (int e = lane; e < 4 * C; e += 32) sS[(size_t)c * 4 * cgmax + e] = cs[e];
-      }
+      // the children's shared patches, and their metadata (lane c K + g)
+      lin_copy2<T, 2>(sS, (const T*)(left + D->off_g + (par ^ 1) * D->copy_g), 4 * C,
+                   sS + 4 * (size_t)cgmax, (const T*)(right + D->off_g + (par ^ 1) * D->copy_g),
+                   4 * C, lane);
       {
         T vmn = T(0), vmx = T(0);
         float vM = 0.0f, vec = 0.0f, vOh = 0.0f, vOl = 0.0f;
