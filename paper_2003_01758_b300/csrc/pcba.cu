@@ -447,7 +447,11 @@ int setup_kernels(pcba_batch* b) {
   // per-axis matrices; warps per block limited by shared memory
   if (sizeof(T) == 4) {
     g.kr_lmax = b->max_l;
-    g.kr_cmax = (int)cmax;
+    // (a linear-family item's shared patches are refreshed together)
+    long long krc = cmax;
+    for (const ProbDesc& d : b->desc)
+      if (d.lin) krc = std::max<long long>(krc, (long long)d.alpha * d.cg);
+    g.kr_cmax = (int)krc;
     auto need = [&](int wpb, long long c) {
       return (size_t)wpb * (size_t)(4 * c + 2 * 289 * g.kr_lmax + PCBA_KR_SCRATCH) * sizeof(double);
     };

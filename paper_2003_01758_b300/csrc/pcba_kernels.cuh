@@ -348,6 +348,133 @@ __device__ __forceinline__ double refresh_convert(const double* a, int C, int l,
   return __dmul_ru(__dmul_ru(2.0 * gterms, 0x1p-53), (double)amax);
 }
 
+// refresh_convert for the nf (<= PCBA_MAX_SHARED) patches a[g C + j] of one
+// multi-degree at once: every pass runs over all nf C coefficients, so the
+// patches' FP64 dependency chains overlap, and each output is summed in two
+// partial sums (at most n + 1 roundings on any path, as a single chain).
+// err[g] receives patch g's bound (in every lane).
+__device__ __forceinline__ void refresh_convert_multi(const double* a, int nf, int C, int l,
+                                                      const int* deg, const double* sT,
+                                                      double*& sA, double*& sB, float*& sX,
+                                                      float*& sY, int lane, double* err) {
+  const int N = nf * C;
+  for (int j = lane; j < N; j += 32) {
+    const double v = a[j];
+    sA[j] = v;
+    sX[j] = __double2float_ru(fabs(v));
+  }
+  __syncwarp();
+  double gterms = 0.0;
+  for (int r = 0; r < l; ++r) {
+    const int n = deg[r];
+    int stride = 1;
+    for (int q = r + 1; q < l; ++q) stride *= deg[q] + 1;
+    const double* T = sT + r * 578;
+    const float* A = (const float*)(T + 289);
+    gterms += 4.0 * n + 8.0;
+    const int blk = (n + 1) * stride;
+    for (int o2 = lane; o2 < N; o2 += 32) {
+      const int g = o2 / C;
+      const int o = o2 - g * C;
+      const int hp = o / blk;
+      const int rem = o - hp * blk;
+      const int i = rem / stride;
+      const int in = rem - i * stride;
+      const double* src = sA + g * C + hp * blk + in;
+      const float* srcx = sX + g * C + hp * blk + in;
+      const double* Ti = T + i * (n + 1);
+      const float* Ai = A + i * (n + 1);
+      double s0 = 0.0, s1 = 0.0;
+      float x0 = 0.0f, x1 = 0.0f;
+      int j = 0;
+      for (; j < n; j += 2) {
+        s0 = fma(Ti[j], src[j * stride], s0);
+        s1 = fma(Ti[j + 1], src[(j + 1) * stride], s1);
+        x0 = __fmaf_ru(Ai[j], srcx[j * stride], x0);
+        x1 = __fmaf_ru(Ai[j + 1], srcx[(j + 1) * stride], x1);
+      }
+      if (j == n) {
+        s0 = fma(Ti[j], src[j * stride], s0);
+        x0 = __fmaf_ru(Ai[j], srcx[j * stride], x0);
+      }
+      sB[o2] = s0 + s1;
+      sY[o2] = __fadd_ru(x0, x1);
+    }
+    __syncwarp();
+    double* t = sA; sA = sB; sB = t;
+    float* tf = sX; sX = sY; sY = tf;
+  }
+  float am[PCBA_MAX_SHARED] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int j = lane; j < N; j += 32) {
+    const int g = j / C;
+#pragma unroll
+    for (int q = 0; q < PCBA_MAX_SHARED; ++q)
+      if (q == g) am[q] = fmaxf(am[q], sX[j]);
+  }
+#pragma unroll
+  for (int q = 0; q < PCBA_MAX_SHARED; ++q) {
+    for (int o = 16; o > 0; o >>= 1) am[q] = fmaxf(am[q], __shfl_xor_sync(0xffffffffu, am[q], o));
+    err[q] = __dmul_ru(__dmul_ru(2.0 * gterms, 0x1p-53), (double)am[q]);
+  }
+}
+
+// Stores the nf converted patches of refresh_convert_multi (sA, C each),
+// each re-centred on the middle of its range, as FP32 values at
+// block[j * pad + g], with offset and error bound (err64[g] added) in the
+// FP32 metadata earr of a linear-family item.
+__device__ __forceinline__ void refresh_store_multi(const double* sA, int nf, int C,
+                                                    const double* err64, float* block, size_t pad,
+                                                    float* earr, size_t apad, int lane) {
+  const int N = nf * C;
+  double bmin[PCBA_MAX_SHARED], bmax[PCBA_MAX_SHARED], O[PCBA_MAX_SHARED], em[PCBA_MAX_SHARED];
+#pragma unroll
+  for (int q = 0; q < PCBA_MAX_SHARED; ++q) {
+    bmin[q] = INFINITY;
+    bmax[q] = -INFINITY;
+    em[q] = 0.0;
+  }
+  for (int j = lane; j < N; j += 32) {
+    const int g = j / C;
+    const double v = sA[j];
+#pragma unroll
+    for (int q = 0; q < PCBA_MAX_SHARED; ++q)
+      if (q == g) {
+        bmin[q] = fmin(bmin[q], v);
+        bmax[q] = fmax(bmax[q], v);
+      }
+  }
+#pragma unroll
+  for (int q = 0; q < PCBA_MAX_SHARED; ++q) {
+    for (int o = 16; o > 0; o >>= 1) {
+      bmin[q] = fmin(bmin[q], __shfl_xor_sync(0xffffffffu, bmin[q], o));
+      bmax[q] = fmax(bmax[q], __shfl_xor_sync(0xffffffffu, bmax[q], o));
+    }
+    O[q] = 0.5 * (bmin[q] + bmax[q]);
+  }
+  for (int j = lane; j < N; j += 32) {
+    const int g = j / C;
+    double Og = 0.0;
+#pragma unroll
+    for (int q = 0; q < PCBA_MAX_SHARED; ++q)
+      if (q == g) Og = O[q];
+    const double d = sA[j] - Og;  // |d - (b - O)| <= |d| 2^-53
+    const float sv = __double2float_rn(d);
+    block[(size_t)(j - g * C) * pad + g] = sv;
+    const double e = __dadd_ru(fabs((double)sv - d), __dmul_ru(fabs(d), 0x1p-52));
+#pragma unroll
+    for (int q = 0; q < PCBA_MAX_SHARED; ++q)
+      if (q == g) em[q] = fmax(em[q], e);
+  }
+#pragma unroll
+  for (int q = 0; q < PCBA_MAX_SHARED; ++q) {
+    for (int o = 16; o > 0; o >>= 1) em[q] = fmax(em[q], __shfl_xor_sync(0xffffffffu, em[q], o));
+    if (lane == 0 && q < nf) {
+      ((double*)(earr + apad))[q] = O[q];
+      earr[q] = __double2float_ru(__dadd_ru(em[q], err64[q]));
+    }
+  }
+}
+
 // Stores a converted patch (sA, C coefficients, bound base err64) as FP32
 // values at dst[j * pad] relative to the offset O (0, or the middle of its
 // range when centre is set), and returns its error bound (rounded up).
@@ -432,23 +559,15 @@ __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
       // every shared patch of a linear-family item (one set of matrices),
       // re-centred, to the copy the next step reads
       const int C = D->cg;
-      if (C > cmax) continue;
+      if (D->alpha * C > cmax) continue;
       refresh_matrices(binom, D->l, D->G, blo, bhi, sT, scr, lane);
       const int nxt = (E.plan->steps_global + 1) & 1;
-      float* block = (float*)(item + D->off_g + nxt * D->copy_g);
-      float* earr = (float*)(item + D->off_eg + nxt * D->copy_e);
-      const double* sh_mono = mono + D->cp;
-      for (int g = 0; g < D->alpha; ++g) {
-        const double err64 =
-            refresh_convert(sh_mono + (long long)g * C, C, D->l, D->G, sT, sA, sB, sX, sY, lane);
-        double O;
-        const float e = refresh_store(sA, C, err64, true, block + g, D->apad, O, lane);
-        if (lane == 0) {
-          ((double*)(earr + D->apad))[g] = O;
-          earr[g] = e;
-        }
-        __syncwarp();
-      }
+      double err64[PCBA_MAX_SHARED];
+      refresh_convert_multi(mono + D->cp, D->alpha, C, D->l, D->G, sT, sA, sB, sX, sY, lane,
+                            err64);
+      refresh_store_multi(sA, D->alpha, C, err64, (float*)(item + D->off_g + nxt * D->copy_g),
+                          D->apad, (float*)(item + D->off_eg + nxt * D->copy_e), D->apad, lane);
+      __syncwarp();
       if (lane == 0) atomicAdd(&E.plan->refreshed_total, (unsigned long long)D->alpha);
       continue;
     }
