@@ -1,12 +1,14 @@
 """Benchmark: certified-optimal PCBA solves per second and time-to-certify.
 
 One step = one batched solve, through the C ABI, of the uneven 256-problem
-workload per GPU with the whole path: the learned warm start (cost-landscape
-features, the set-encoder network's forward pass, FP32-certified candidates
-seeding the incumbent), the FP64 monomial-to-Bernstein conversion, the branch
-and bound loop of subdivide / bound / incumbent / cut-off / compaction, and
-the FP64 check of the returned points, until every problem is certified or
-stops.  Only certified solves (OPTIMAL or INFEASIBLE) count.
+workload per GPU with the whole path of Alg. 1: the FP64 monomial-to-Bernstein
+conversion, the branch and bound loop of subdivide / bound / incumbent /
+cut-off / compaction, and the FP64 check of the returned points, until every
+problem is certified or stops.  Only certified solves (OPTIMAL or INFEASIBLE)
+count.  On this workload the learned warm start (cost-landscape features, the
+set-encoder network's forward pass, FP32-certified candidates seeding the
+incumbent) costs more per step than it saves, so it is a leg beside the
+headline, not the headline.
 
   python bench.py [--gpus N --steps K --warmup W]      the CUDA library
   python bench.py --impl reference [...]               the CPU oracle on host cores
@@ -19,9 +21,11 @@ library receives the constraints as a linear family in (||F||^2, F_1, F_2)
 (pcba_create_linear); patches are FP32 with directed-rounding error bounds.
 Inputs are resident in HBM when the timed region starts; L2 is flushed
 between timed steps by writing a 256 MiB buffer.  Legs beside the headline:
-the same workload without warm start, in FP64 and with dense constraints; the
-64-problem 512-obstacle batch (linear, dense, dense FP64); the tiny problems
-one at a time; the 4-D problems with equalities; the warm-start A/B.
+the same workload with the learned warm start, in FP64 and with dense
+constraints; the 64-problem 512-obstacle batch (linear, dense, dense FP64);
+the tiny problems one at a time; the 4-D problems with equalities; the
+warm-start A/B; the RTD* planning POPs (Sec. VI-A); the increasing-constraints
+problems (Sec. V-C).
 """
 from __future__ import annotations
 
@@ -55,7 +59,7 @@ WORKLOAD = ("uneven batch of %d rtd-shaped POPs per GPU (rank k: seeds %d+%d*k+j
             "[-1,1]^2, F degree (3,3) N(0,0.5^2), obstacles floor(exp U(ln %d, ln %d)) "
             "U([-2,2]^2) r=0.15, constraints degree (6,6) given as a linear family in "
             "(||F||^2, F_1, F_2), cost ||F-goal||^2; FP32 patches with directed-rounding error "
-            "bounds; learned warm start; opt_tol %g"
+            "bounds; no warm start (Alg. 1 from the root box); opt_tol %g"
             % (BATCH, BASE_SEED, BATCH, OBS_LO, OBS_HI, OPT_TOL))
 
 
@@ -379,6 +383,13 @@ def main():
                     help="device loop in a conditional CUDA graph, or driven from the host")
     ap.add_argument("--no-extras", action="store_true",
                     help="timed headline steps only (no e2e, roofline or side legs)")
+    ap.add_argument("--problems", type=int, default=0,
+                    help="profiling: only the first N problems of the workload (0: all)")
+    ap.add_argument("--mem-gb", type=int, default=MEM_CAP >> 30,
+                    help="list memory of the headline batch in GiB")
+    ap.add_argument("--launch-bytes", action="store_true",
+                    help="with --no-extras: also an instrumented host-loop solve, printing "
+                         "the algorithmic bytes of each subdivision step")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", str(args.gpus)))
@@ -406,23 +417,28 @@ def main():
     build.build()
     torch.cuda.set_device(local)
     probs = shard_problems(rank)
+    if args.problems > 0:
+        probs = probs[:args.problems]
     loop_flag = 0 if args.loop == "graph" else pcba.Batch.HOST_LOOP
-    batch = make_batch(probs, pcba.FP32, linear=True, flags=loop_flag)
+    batch = make_batch(probs, pcba.FP32, linear=True, flags=loop_flag,
+                       mem_cap=args.mem_gb << 30)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     learned = Learned(batch, probs)
 
     for _ in range(args.warmup):
-        learned.step()
+        batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
 
-    # ---- timed region: K learned-warm-start batched solves, inputs resident in HBM ----
+    # ---- timed region: K batched solves (Alg. 1, no warm start), inputs
+    # resident in HBM ----
     if world > 1:
         import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
-    ms, times, status, nsteps = learned.timed(args.steps, flush)
+    ms, times, status, last = timed_steps(batch, args.steps, flush)
     clk = clocks.stop()
+    nsteps = [r["steps"] for r in last]
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
@@ -431,44 +447,47 @@ def main():
     value = cert_all / (total_ms / 1e3)
     optimal = sum(1 for s in status if s == pcba.OPTIMAL)
     infeasible = sum(1 for s in status if s == pcba.INFEASIBLE)
-    launches = learned.launches_per_step() * args.steps
+    launches = batch.stats()["kernel_launches"] * args.steps
     if args.no_extras:
+        out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+               "steps": args.steps, "ms_per_step": total_ms / args.steps,
+               "problems_per_step": len(probs), "loop": args.loop,
+               "certified": optimal + infeasible, "clocks": clk}
+        if args.launch_bytes:
+            # after the timed solves: one instrumented host-loop solve
+            ib = make_batch(probs, pcba.FP32, linear=True, flags=pcba.Batch.INSTRUMENT,
+                            mem_cap=args.mem_gb << 30)
+            ib.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+            out["launch_bytes"] = [float(x) for x in ib.launch_bytes()]
+            ib.close()
         if rank == 0:
-            print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
-                              "steps": args.steps, "ms_per_step": total_ms / args.steps,
-                              "problems_per_step": len(probs), "loop": args.loop,
-                              "certified": optimal + infeasible, "clocks": clk}))
+            print(json.dumps(out))
         return 0
 
     from paper_2003_01758_b300 import warmstart
-    # ---- the same solves without the warm start ----
-    with torch.cuda.stream(learned.stream):
-        batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
-        cms, ctimes, cstatus, cres = timed_steps(batch, args.steps, flush)
-    cold = leg_summary(cms, ctimes, cstatus, len(probs))
-    cold["mean_bisection_steps"] = float(np.mean([r["steps"] for r in cres]))
-    cold["value"] = reduce_sum(float(certified(cstatus)), world) / (
-        reduce_max(float(sum(cms)), world) / 1e3)
+    # ---- the same solves with the learned warm start (network forward pass,
+    # candidates certified, guided solve; all in the step) ----
+    learned.step()
+    lms, ltimes, lstatus, lsteps = learned.timed(args.steps, flush)
+    learned_leg = leg_summary(lms, ltimes, lstatus, len(probs))
+    learned_leg["mean_bisection_steps"] = float(np.mean(lsteps))
+    learned_leg["value"] = reduce_sum(float(certified(lstatus)), world) / (
+        reduce_max(float(sum(lms)), world) / 1e3)
+    learned_leg["gpu_launches_per_step"] = learned.launches_per_step()
+    learned_leg["warm_start"] = ("set-encoder network, BF16 on tcgen05; %d-candidate stencil, "
+                                 "then %d around the seed, certified in FP32"
+                                 % (len(learned.stencil), len(warmstart.refine_stencil())))
 
-    # ---- end to end: host inputs in (monomial coefficients, constraint rows,
-    # obstacle points, goal and map features), network, guided solve, results
-    # out; wall clock ----
+    # ---- end to end: host inputs in (monomial coefficients and constraint
+    # rows), solve, results out; wall clock ----
     h_coeffs = torch.from_numpy(host_coeffs(probs)).pin_memory().numpy()
     h_rows = torch.from_numpy(pcba.linear_rows(probs)).pin_memory().numpy()
     assert h_coeffs.size == batch.input_doubles() and h_rows.size == batch.rows_doubles()
-    h_points = torch.from_numpy(learned.points).pin_memory()
-    h_offsets = torch.from_numpy(learned.offsets).pin_memory()
-    h_glob = torch.from_numpy(learned.glob).pin_memory()
-    torch_h2d = 4 * (learned.points.size + learned.offsets.size + learned.glob.size)
 
     def e2e_step():
-        with torch.cuda.stream(learned.stream):
-            batch.upload(h_coeffs)
-            batch.upload_rows(h_rows)
-            learned.pk.points.copy_(h_points, non_blocking=True)
-            learned.pk.offsets.copy_(h_offsets, non_blocking=True)
-            learned.pk.glob.copy_(h_glob, non_blocking=True)
-            return learned.step()
+        batch.upload(h_coeffs)
+        batch.upload_rows(h_rows)
+        return batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS, raw=True)
 
     e2e_step()
     e2e_s, e2e_status = 0.0, []
@@ -485,9 +504,8 @@ def main():
     # ---- roofline of the subdivision step (split + bound kernels): CUDA
     # events around each launch pair in a host-driven loop ----
     ibatch = make_batch(probs, pcba.FP32, linear=True, flags=pcba.Batch.INSTRUMENT)
-    ilearned = Learned(ibatch, probs)
-    ilearned.step()
-    ilearned.step()
+    ibatch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+    ibatch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
     it = ibatch.timing()
     lin = ibatch.linear_stats()
     ibatch.close()
@@ -496,8 +514,8 @@ def main():
 
     # ---- FP64 (plain arithmetic, no warm start), same problems: the FP32
     # bounds against the FP64 ones, per result ----
-    fp32_res = [dict(lower=r.lower, upper=r.upper, status=r.status, upper_err=r.upper_err)
-                for r in learned.step()]
+    fp32_res = [dict(lower=r["lower"], upper=r["upper"], status=r["status"],
+                     upper_err=r["upper_err"]) for r in batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)]
     b64 = make_batch(probs, pcba.FP64, linear=True)
     b64.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
     ms64, t64, st64, res64 = timed_steps(b64, 2, flush)
@@ -609,6 +627,60 @@ def main():
             dbt.close()
         side["dim4"] = dim4
 
+        # ---- RTD* planning POPs (Sec. VI-A): 64 problems, 30..300 degree-12
+        # obstacle constraints (log-uniform), one or two waypoints ----
+        rng = np.random.default_rng(9)
+        counts = np.floor(np.exp(rng.uniform(np.log(30), np.log(300), 64))).astype(int)
+        rs = [W.rtd_star(7000 + k, n_ineq=int(c), n_wp=1 + k % 2) for k, c in enumerate(counts)]
+        star = {"workload": "64 RTD* POPs (seeds 7000+k): Q = [0,1] x [-1,1], waypoint-product "
+                            "cost (degree 10 with one waypoint, 16 with two), 30..300 "
+                            "degree-12 obstacle constraints, no warm start"}
+        for name, linear, prec in (("linear_fp32", True, pcba.FP32),
+                                   ("dense_fp64_plain", False, pcba.FP64)):
+            bs = make_batch(rs, prec, linear=linear, mem_cap=32 << 30)
+            bs.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+            sm, st, ss, _ = timed_steps(bs, 3, flush)
+            star[name] = leg_summary(sm, st, ss, len(rs))
+            bs.close()
+        side["rtd_star"] = star
+
+        # ---- increasing constraints (Sec. V-C): per objective the paper's 20
+        # trials, 10, 20, ..., 200 random degree-2 constraints, one batch ----
+        from tests import benchmarks
+        inc = {"workload": "per appendix objective, the problems with 10, 20, .., 200 random constraints "
+                           "of total degree <= 2 (coefficients U[-5, 5], the optimizer kept "
+                           "feasible with margin 1), seeds 11+n; dense FP32; opt_tol 1e-3 "
+                           "max(1, |optimum|)"}
+        # list memory per problem: 1 GiB, Powell 5 GiB; Wood keeps ~1.9M boxes
+        # of dense patches (9.5 GB at 10 constraints, > 40 GB from 50 on), so
+        # only its trials with 10..40 constraints run, one at a time at 40 GiB
+        for name in ("EVD", "Powell", "Wood", "DixonPrice2", "DixonPrice3", "DixonPrice4",
+                     "Beale", "Bukin02", "DeckkersAarts"):
+            bm = benchmarks.load(name)
+            trials = range(10, 41, 10) if name == "Wood" else range(10, 201, 10)
+            per = {"Powell": 5 << 30, "Wood": 40 << 30}.get(name, 1 << 30)
+            ps = [W.increasing_constraints(bm["cost"], bm["lo"], bm["hi"], bm["x_opt"], n,
+                                           seed=11 + n) for n in trials]
+            tol = 1e-3 * max(1.0, abs(bm["optimum"]))
+            groups = [[q] for q in ps] if name == "Wood" else [ps]
+            ims, itimes, ist, ipeak = [0.0] * 3, [], [], 0
+            for grp in groups:
+                bi = pcba.Batch([pcba.solver_from_problem(q, pcba.FP32) for q in grp],
+                                len(grp) * per)
+                bi.solve(tol, EQ_TOL, MAX_ITERS)
+                for rep in range(3):
+                    flush.zero_()
+                    torch.cuda.synchronize()
+                    ires = bi.solve(tol, EQ_TOL, MAX_ITERS)
+                    ims[rep] += bi.timing()["total_ms"]
+                    itimes += [r["time_ms"] for r in ires]
+                    ist += [r["status"] for r in ires]
+                    ipeak = max(ipeak, max(r["peak_items"] for r in ires))
+                bi.close()
+            inc[name] = leg_summary(ims, itimes, ist, len(ps))
+            inc[name]["peak_items"] = int(ipeak)
+        side["increasing_constraints"] = inc
+
     base = None
     if pool is not None:
         base = cpu_baseline(pool, cpu_procs())
@@ -621,9 +693,8 @@ def main():
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "problems_per_step": len(probs),
-                   "warm_start": "learned (set-encoder network, BF16 on tcgen05; %d-candidate "
-                                 "stencil, then %d around the seed, certified in FP32)"
-                                 % (len(learned.stencil), len(warmstart.refine_stencil())),
+                   "warm_start": "none (Alg. 1 from the root box; the learned warm start is "
+                                 "the learned_warm_start leg)",
                    "l2": "flushed between timed steps (256 MiB write)",
                    "parallelism": "independent problems per GPU (dp%d)" % world,
                    "device_loop": args.loop},
@@ -631,7 +702,7 @@ def main():
         "certified": {"optimal": optimal, "infeasible": infeasible,
                       "failed": len(status) - optimal - infeasible},
         "mean_bisection_steps": float(np.mean(nsteps)),
-        "no_warm_start": cold,
+        "learned_warm_start": learned_leg,
         "fp32_vs_fp64": fp32_vs_fp64,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
@@ -644,7 +715,7 @@ def main():
                      "constraint_bounds": lin["pairs"], "coefficient_ranges": lin["full"]},
         "cpu_baseline": base,
         "e2e": {"value": e2e_value, "unit": UNIT,
-                "h2d_bytes_per_step": e2e_stats["h2d_bytes"] + torch_h2d,
+                "h2d_bytes_per_step": e2e_stats["h2d_bytes"],
                 "d2h_bytes_per_step": e2e_stats["d2h_bytes"]},
         "gpu_launches": launches,
         "clocks": clk,
