@@ -5,7 +5,9 @@ workload per GPU with the whole path of Alg. 1: the FP64 monomial-to-Bernstein
 conversion, the branch and bound loop of subdivide / bound / incumbent /
 cut-off / compaction, and the FP64 check of the returned points, until every
 problem is certified or stops.  Only certified solves (OPTIMAL or INFEASIBLE)
-count.  On this workload the learned warm start (cost-landscape features, the
+count.  The incumbent also takes certified box corners (vertex incumbents,
+batch flag 8: a corner coefficient is the polynomial's value at the corner,
+Sec. II-D); the plain Alg. 1-5 run is the no_vertex leg.  On this workload the learned warm start (cost-landscape features, the
 set-encoder network's forward pass, FP32-certified candidates seeding the
 incumbent) costs more per step than it saves, so it is a leg beside the
 headline, not the headline.
@@ -59,7 +61,8 @@ WORKLOAD = ("uneven batch of %d rtd-shaped POPs per GPU (rank k: seeds %d+%d*k+j
             "[-1,1]^2, F degree (3,3) N(0,0.5^2), obstacles floor(exp U(ln %d, ln %d)) "
             "U([-2,2]^2) r=0.15, constraints degree (6,6) given as a linear family in "
             "(||F||^2, F_1, F_2), cost ||F-goal||^2; FP32 patches with directed-rounding error "
-            "bounds; no warm start (Alg. 1 from the root box); opt_tol %g"
+            "bounds; vertex incumbents (corner coefficients, Sec. II-D); no warm start; "
+            "opt_tol %g"
             % (BATCH, BASE_SEED, BATCH, OBS_LO, OBS_HI, OPT_TOL))
 
 
@@ -420,7 +423,7 @@ def main():
     if args.problems > 0:
         probs = probs[:args.problems]
     loop_flag = 0 if args.loop == "graph" else pcba.Batch.HOST_LOOP
-    batch = make_batch(probs, pcba.FP32, linear=True, flags=loop_flag,
+    batch = make_batch(probs, pcba.FP32, linear=True, flags=loop_flag | pcba.Batch.VERTEX,
                        mem_cap=args.mem_gb << 30)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     learned = Learned(batch, probs)
@@ -455,7 +458,8 @@ def main():
                "certified": optimal + infeasible, "clocks": clk}
         if args.launch_bytes:
             # after the timed solves: one instrumented host-loop solve
-            ib = make_batch(probs, pcba.FP32, linear=True, flags=pcba.Batch.INSTRUMENT,
+            ib = make_batch(probs, pcba.FP32, linear=True,
+                            flags=pcba.Batch.INSTRUMENT | pcba.Batch.VERTEX,
                             mem_cap=args.mem_gb << 30)
             ib.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
             out["launch_bytes"] = [float(x) for x in ib.launch_bytes()]
@@ -465,6 +469,17 @@ def main():
         return 0
 
     from paper_2003_01758_b300 import warmstart
+    # ---- the same solves without vertex incumbents (Alg. 1-5 as printed) ----
+    nb = make_batch(probs, pcba.FP32, linear=True, mem_cap=args.mem_gb << 30)
+    nb.set_stream(learned.stream.cuda_stream)
+    nb.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
+    nms, ntimes, nstatus, nres = timed_steps(nb, args.steps, flush)
+    no_vertex = leg_summary(nms, ntimes, nstatus, len(probs))
+    no_vertex["mean_bisection_steps"] = float(np.mean([r["steps"] for r in nres]))
+    no_vertex["value"] = reduce_sum(float(certified(nstatus)), world) / (
+        reduce_max(float(sum(nms)), world) / 1e3)
+    nb.close()
+
     # ---- the same solves with the learned warm start (network forward pass,
     # candidates certified, guided solve; all in the step) ----
     learned.step()
@@ -503,7 +518,8 @@ def main():
 
     # ---- roofline of the subdivision step (split + bound kernels): CUDA
     # events around each launch pair in a host-driven loop ----
-    ibatch = make_batch(probs, pcba.FP32, linear=True, flags=pcba.Batch.INSTRUMENT)
+    ibatch = make_batch(probs, pcba.FP32, linear=True,
+                        flags=pcba.Batch.INSTRUMENT | pcba.Batch.VERTEX)
     ibatch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
     ibatch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
     it = ibatch.timing()
@@ -516,7 +532,7 @@ def main():
     # bounds against the FP64 ones, per result ----
     fp32_res = [dict(lower=r["lower"], upper=r["upper"], status=r["status"],
                      upper_err=r["upper_err"]) for r in batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS)]
-    b64 = make_batch(probs, pcba.FP64, linear=True)
+    b64 = make_batch(probs, pcba.FP64, linear=True, flags=pcba.Batch.VERTEX)
     b64.solve(OPT_TOL, EQ_TOL, MAX_ITERS)
     ms64, t64, st64, res64 = timed_steps(b64, 2, flush)
     b64.close()
@@ -702,6 +718,7 @@ def main():
         "certified": {"optimal": optimal, "infeasible": infeasible,
                       "failed": len(status) - optimal - infeasible},
         "mean_bisection_steps": float(np.mean(nsteps)),
+        "no_vertex": no_vertex,
         "learned_warm_start": learned_leg,
         "fp32_vs_fp64": fp32_vs_fp64,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

@@ -211,7 +211,18 @@ int pcba_solve_batch(pcba_handle** hs, int n, double opt_tol, double eq_tol, int
  *   1 = host loop that reads one status word per step;
  *   3 = host loop with CUDA events around every subdivision launch;
  *   4 = do not use the TMA-staged subdivision kernel (the direct-load one runs;
- *       it is also used when a constraint patch exceeds 256 coefficients). */
+ *       it is also used when a constraint patch exceeds 256 coefficients);
+ *   8 = vertex incumbents (linear-family batches only, else PCBA_ERR_INVALID):
+ *       the corner coefficients of a patch are the polynomial's values at the
+ *       box's corners (Sec. II-D), so a child box's corner at which every
+ *       active constraint's corner value plus its bound E is <= 0 is a
+ *       feasible point, and its corner cost coefficient plus e_p bounds p
+ *       there.  The least such bound lowers p_up in the same step (before the
+ *       cut-off test) and the corner becomes the returned point (FP32 and
+ *       FP64; up to 4 corners per box: those of the first two axes, the
+ *       other axes at their lower end).  Sound (Thm. 3 holds for any p_up
+ *       attained at a feasible point); without it the lists follow Alg. 1-5
+ *       exactly. */
 int pcba_batch_create(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_total,
                       int flags);
 int pcba_batch_solve(pcba_batch* b, double opt_tol, double eq_tol, int max_iters,

@@ -622,6 +622,10 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
       return fail(PCBA_ERR_INVALID, "a batch must not mix linear-family and dense problems, "
                                     "and its linear families must share n_shared");
     }
+  if ((flags & 8) && !b->lin) {
+    delete b;
+    return fail(PCBA_ERR_INVALID, "vertex incumbents (flag 8) need linear-family problems");
+  }
   b->desc.resize(n);
   long long mono = 0, sum_item = 0, trace_rows = 0, lin_rows = 0;
   for (int k = 0; k < n; ++k) {
@@ -881,6 +885,7 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
   }
   P.np = n;
   P.time_limit_ns = b->time_limit_s > 0.0 ? (unsigned long long)(b->time_limit_s * 1e9) : 0ull;
+  P.vertex = (b->flags & 8) ? 1 : 0;
 
   PCBA_CK(cudaEventRecord(b->ev0, s));
   b->h2d_bytes = (long long)sizeof(SolveParams) + (host_coeffs ? 8LL * b->mono_doubles : 0) +
@@ -1306,7 +1311,7 @@ int pcba_solve(pcba_handle* h, double opt_tol, double eq_tol, int max_iters, siz
 }
 
 int pcba_batch_create(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_total, int flags) {
-  if (flags < 0 || flags > 7) return fail(PCBA_ERR_INVALID, "flags must be 0..7");
+  if (flags < 0 || flags > 15) return fail(PCBA_ERR_INVALID, "flags must be 0..15");
   return batch_create_impl(out, hs, n, mem_cap_total, flags);
 }
 

@@ -97,6 +97,11 @@ struct ChildRec {
   unsigned long long hnegmaxmin;      // max_j (-max B_hj) = -(min_j max B_hj)
   unsigned long long habsmax;         // max_j max(max B_hj, -min B_hj)
   unsigned long long perr;            // FP32: bits of the cost patch's error bound e_p
+  // vertex incumbents (batch flag 8): per corner, the max over the child's
+  // active constraints of (corner value + bound), as okey32 (0: none), and
+  // an upper bound of the cost at the corner
+  unsigned vtxg[4];
+  float vtxc[4];
 };
 
 struct ProbState {
@@ -133,6 +138,7 @@ struct ProbState {
   double seed_x[PCBA_MAXD];     // the candidate
   float box_err;                // FP32: e_p of the returned box's cost patch (in p_up)
   double warm_err;              // FP64 rounding bound of the warm point's cost (in p_up)
+  unsigned long long vtx_key;   // this step: okey32(corner cost bound) << 32 | child << 2 | corner
 };
 
 struct SolveParams {
@@ -142,6 +148,7 @@ struct SolveParams {
   int step_guard;     // hard bound on device loop iterations
   int np;
   unsigned long long time_limit_ns;  // 0: none; else stop running problems (TIMEOUT)
+  int vertex;         // vertex incumbents (linear families)
 };
 
 struct Plan {
@@ -320,6 +327,16 @@ __device__ __forceinline__ unsigned okey32(float x) {
 }
 __device__ __forceinline__ float okey32_dec(unsigned k) {
   return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// Flat index of corner q of a patch of multi-degree deg (row-major, last
+// axis fastest): bit a of q (a < 2) selects the upper end of axis a, later
+// axes stay at their lower end.  The coefficient there is the polynomial's
+// value at that corner of the box (Sec. II-D).
+__device__ __forceinline__ int corner_index(const int* deg, int l, int q) {
+  int idx = 0;
+  for (int a = 0; a < l; ++a) idx = idx * (deg[a] + 1) + ((a < 2 && ((q >> a) & 1)) ? deg[a] : 0);
+  return idx;
 }
 
 __device__ __forceinline__ ChildRec load_rec_cg(const ChildRec* p) {

@@ -615,17 +615,32 @@ __device__ __forceinline__ void pup_phase(const Engine& E) {
     ProbState* S = E.state + p;
     const int twoK = 2 * S->K;
     const int c = (int)(u - E.k3_pre[p]) * PCBA_TPB + threadIdx.x;
-    unsigned long long best = ~0ull;
+    unsigned long long best = ~0ull, vbest = ~0ull;
     if (c < twoK) {
-      const ChildRec rc = load_rec_cg(E.rec + D->slot_off + c);
+      const ChildRec* R = E.rec + D->slot_off + c;
+      const ChildRec rc = load_rec_cg(R);
       if (rec_feasible_key(rc, k_eq)) best = rc.pmax;
+      if (E.params->vertex) {
+        // a corner at which every active constraint is certainly <= 0:
+        // its cost bound, with the child and the corner
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          if (__ldcg(&R->vtxg[q]) > 0x80000000u) continue;  // okey32(+0.0)
+          const unsigned long long key =
+              ((unsigned long long)okey32(__ldcg(&R->vtxc[q])) << 32) | ((unsigned)c << 2) | q;
+          vbest = key < vbest ? key : vbest;
+        }
+      }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const unsigned long long other = __shfl_xor_sync(0xffffffffu, best, o);
       best = other < best ? other : best;
+      const unsigned long long vo = __shfl_xor_sync(0xffffffffu, vbest, o);
+      vbest = vo < vbest ? vo : vbest;
     }
     if ((threadIdx.x & 31) == 0 && best != ~0ull) atomicMin(&S->pup_key, best);
+    if ((threadIdx.x & 31) == 0 && vbest != ~0ull) atomicMin(&S->vtx_key, vbest);
   }
 }
 
@@ -634,6 +649,11 @@ __global__ void __launch_bounds__(PCBA_TPB) k_pup(Engine E) { pup_phase(E); }
 // ---------------------------------------------------------------------------
 // K3: classify, scan, finalize, plan
 // ---------------------------------------------------------------------------
+// The least certified corner cost of this step (vertex incumbents), +inf if none.
+__device__ __forceinline__ double vertex_bound(unsigned long long vtx_key) {
+  return vtx_key == ~0ull ? INFINITY : (double)okey32_dec((unsigned)(vtx_key >> 32));
+}
+
 __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
   const ProbDesc* D = E.desc + p;
   ProbState* S = E.state + p;
@@ -658,7 +678,7 @@ __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
   // hole count's inputs), so that their latencies overlap; the stores follow
   const int l = D->l;
   const int r = S->r;
-  const unsigned long long pup_key = S->pup_key, plo_key = S->plo_key;
+  const unsigned long long pup_key = S->pup_key, plo_key = S->plo_key, vkey = S->vtx_key;
   const double carry = S->p_up_carry;
   const unsigned long long bkey = S->best_key;
   const unsigned bs = bkey == ~0ull ? PCBA_NONE : (unsigned)(bkey >> 32);
@@ -671,6 +691,10 @@ __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
   const unsigned fr_ks = K_save < twoK ? __ldcg(E.flagrank + D->slot_off + K_save) : 0u;
   const unsigned tc_ks = K_save < twoK ? __ldcg(tc + K_save / PCBA_TPB) : 0u;
   const unsigned phys = bs != PCBA_NONE ? __ldcg(E.map + D->slot_off + bs) : 0u;
+  // vertex incumbent: the child and corner of the least certified corner cost
+  const double vtx = vertex_bound(vkey);
+  const unsigned vslot = vkey == ~0ull ? PCBA_NONE : (unsigned)(vkey & 0xFFFFFFFFull) >> 2;
+  const unsigned vphys = vslot != PCBA_NONE ? __ldcg(E.map + D->slot_off + vslot) : 0u;
   int level[PCBA_MAXD];
 #pragma unroll
   for (int q = 0; q < PCBA_MAXD; ++q) level[q] = q < l ? S->level[q] : 0;
@@ -684,7 +708,22 @@ __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
   level[r] += 1;
   S->level[r] = level[r];
   const double p_up_step = okey_dec_min(pup_key);
-  const double p_up = fmin(p_up_step, carry);
+  const double p_up = fmin(fmin(p_up_step, carry), vtx);
+  if (bs == PCBA_NONE && vslot != PCBA_NONE && vtx < fmin(p_up_step, carry)) {
+    // the corner is the incumbent: an exact point of the child's box
+    const unsigned q = (unsigned)(vkey & 3ull);
+    const unsigned* idx =
+        (const unsigned*)(E.arena + D->list_off + (size_t)vphys * D->item_bytes);
+    for (int a = 0; a < l; ++a) {
+      const double w = ldexp(D->hi[a] - D->lo[a], -level[a]);
+      const unsigned bit = (a < 2) ? ((q >> a) & 1u) : 0u;
+      S->warm_x[a] = D->lo[a] + w * (double)(__ldcg(idx + a) + bit);
+    }
+    S->have_box = 0;
+    S->from_warm = 1;
+    S->p_up_carry = vtx;
+    S->warm_err = 0.0;
+  }
   if (bs != PCBA_NONE) {
     for (int q = 0; q < l; ++q) {
       S->best_index[q] = bidx[q];
@@ -743,6 +782,7 @@ __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
   S->pup_key = ~0ull;
   S->plo_key = ~0ull;
   S->best_key = ~0ull;
+  S->vtx_key = ~0ull;
   S->k3_arrive = 0u;
   if (status != PCBA_RUNNING) S->t_end = globaltimer();
 }
@@ -837,7 +877,8 @@ __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan,
     const int c = tile * PCBA_TPB + threadIdx.x;
     const double p_up_step = okey_dec_min(S->pup_key);
     const double carry = S->p_up_carry;
-    const double p_up = fmin(p_up_step, carry);
+    const double vtx = vertex_bound(S->vtx_key);
+    const double p_up = fmin(fmin(p_up_step, carry), vtx);
     const unsigned long long k_pup = okey(p_up + 0.0);  // p_up = -0.0 becomes +0.0
     unsigned keep = 0;
     // least key of a kept child's pmin (the keys order like the values) and
@@ -849,7 +890,7 @@ __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan,
       const ChildRec rc = load_rec_cg(R);
       unsigned long long* w = (unsigned long long*)R;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) w[q] = 0ull;  // identity for the next step
+      for (int q = 0; q < (int)(sizeof(ChildRec) / 8); ++q) w[q] = 0ull;  // identity for the next step
       // Def. 3 and the cut-off on the keys: "value > 0" for a max-reduced
       // field is key > okey(+0.0); pmin <= p_up is a key compare once a zero
       // p_up is taken as +0.0 (-0.0 <= +0.0 either way)
@@ -857,7 +898,8 @@ __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan,
       const bool infeasible = rc.gminmax > k0 || rc.hminmax > k0 || rc.hnegmaxmin > k0;
       keep = (!infeasible && rc.pmin <= k_pup) ? 1u : 0u;
       if (keep) kmin = rc.pmin;
-      if (p_up_step <= carry && okey_dec(rc.pmax) == p_up_step && rec_feasible_key(rc, k_eq))
+      if (p_up_step <= carry && p_up_step <= vtx && okey_dec(rc.pmax) == p_up_step &&
+          rec_feasible_key(rc, k_eq))
         smin = ((unsigned long long)c << 32) | (rc.perr & 0xFFFFFFFFull);
     }
     unsigned cnt;
@@ -1050,6 +1092,7 @@ __global__ void k_init(Engine E) {
       S->hw = 1;
       E.map[D->slot_off] = 0u;
       S->best_key = ~0ull;
+      S->vtx_key = ~0ull;
       S->box_err = 0.0f;
       S->k3_arrive = 0;
       S->have_box = 0;

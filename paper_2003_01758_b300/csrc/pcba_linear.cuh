@@ -399,6 +399,16 @@ __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int
   const int G = na > 16 ? 1 : (na > 8 ? 2 : (na > 4 ? 4 : 8));
   const int gsub = lane & (G - 1);
   const unsigned per = 32u / (unsigned)G;
+  // vertex incumbents: each child's corner values of its active constraints
+  // (the corner coefficient is the constraint's value there, Sec. II-D)
+  const bool vtx_on = E.params->vertex != 0;
+  int jc[4] = {0, 0, 0, 0};
+  T vmax[2][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (vtx_on) jc[q] = corner_index(D->G, D->l, q);
+    vmax[0][q] = vmax[1][q] = T(-INFINITY);
+  }
   {
     unsigned pos = incl - cnt, bits = word;
     while (bits) {
@@ -492,6 +502,19 @@ __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int
         if (act && gsub == 0) ++nfull;
       }
     }
+    if (vtx_on && act && gsub == 0) {
+#pragma unroll
+      for (int c = 0; c < 2; ++c)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          T a[K];
+          lin_load<T, K>((c ? sR : sL) + (size_t)jc[q] * 4, a);
+          T v = cc[c];
+#pragma unroll
+          for (int m = 0; m < K; ++m) v = fma(w[m], a[m], v);
+          vmax[c][q] = max(vmax[c][q], add_up(v, Et[c]));
+        }
+    }
 #pragma unroll
     for (int c = 0; c < 2; ++c) {
       if (!act || gsub != 0) continue;
@@ -529,6 +552,18 @@ __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int
     if (keepL) atomicOr(sumL, keepL);
     if (keepR) atomicOr(sumR, keepR);
     atomicAdd(&E.plan->lin_pairs, 2ull * na);
+  }
+  if (vtx_on) {
+#pragma unroll
+    for (int c = 0; c < 2; ++c)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const T m = lin_wmax(vmax[c][q]);
+        if (lane == 0 && m > T(-INFINITY)) {
+          const float mf = sizeof(T) == 4 ? (float)m : __double2float_ru((double)m);
+          atomicMax(&E.rec[slot_off + k + (c ? Kl : 0)].vtxg[q], okey32(mf));
+        }
+      }
   }
   const unsigned full = __reduce_add_sync(0xffffffffu, nfull);
   if (lane == 0) atomicAdd(&E.plan->lin_full, (unsigned long long)full);
@@ -617,7 +652,7 @@ __device__ __forceinline__ void lin_fibre(const T* src, T* dL, T* dR, int sst, L
 #define PCBA_LIN_SPLIT_BLOCKS 2
 #endif
 #ifndef PCBA_LIN_BOUND_BLOCKS
-#define PCBA_LIN_BOUND_BLOCKS 3
+#define PCBA_LIN_BOUND_BLOCKS 2
 #endif
 
 template <typename T, int K, int NFIX>
@@ -777,9 +812,25 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
           rec->pmax = okey(__dadd_ru(__dadd_ru(On, (double)smax), (double)e2));
           rec->perr = __float_as_uint(e2);
           if ((double)e2 > cost_thr) lin_mark(E, par, p, c ? k + Kl : k, 2, 0);
+          if (E.params->vertex) {
+            // the cost at the child's corners: offset + stored value + e_p
+            const T* st = c ? scR : scL;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const float rq = __fsub_rn(st[corner_index(D->P, l, q)], sh);
+              rec->vtxc[q] =
+                  __double2float_ru(__dadd_ru(__dadd_ru(On, (double)rq), (double)e2));
+            }
+          }
         } else {
           rec->pmin = okey((double)cmn);
           rec->pmax = okey((double)cmx);
+          if (E.params->vertex) {
+            const T* st = c ? scR : scL;
+#pragma unroll
+            for (int q = 0; q < 4; ++q)
+              rec->vtxc[q] = __double2float_ru((double)st[corner_index(D->P, l, q)]);
+          }
         }
       } else if (lane == 2) {
         E.map[slot_off + k + Kl] = rslot;

@@ -410,7 +410,7 @@ def solver_from_problem(prob, precision=FP32):
 class Batch:
     """A reusable batch of problems solved together (pcba_batch_*)."""
 
-    GRAPH, HOST_LOOP, INSTRUMENT, NO_TMA = 0, 1, 3, 4
+    GRAPH, HOST_LOOP, INSTRUMENT, NO_TMA, VERTEX = 0, 1, 3, 4, 8
 
     def __init__(self, solvers, mem_cap_total, flags=0):
         self.solvers = list(solvers)
