@@ -106,7 +106,9 @@ typedef struct {
   double upper_err;         /* the rounding-error bound included in 'upper': FP32, the
                                bound e_p of the returned box's cost patch (upper = its
                                largest stored coefficient + e_p); a warm point, the FP64
-                               bound of its cost evaluation; FP64 boxes: 0             */
+                               bound of its cost evaluation; a vertex incumbent (batch
+                               flag 8), the e_p of the cost patch whose corner it is;
+                               FP64 boxes and corners: 0                               */
 } pcba_result;
 
 /* Builds a problem: cost p (Eq. (P)), n_ineq inequality constraints g_i <= 0,

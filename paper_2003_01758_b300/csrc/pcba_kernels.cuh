@@ -722,7 +722,8 @@ __device__ void finalize_problem(const Engine& E, int p, unsigned* sscan) {
     S->have_box = 0;
     S->from_warm = 1;
     S->p_up_carry = vtx;
-    S->warm_err = 0.0;
+    // the bound in the corner's cost: the child's cost-patch bound e_p (FP32)
+    S->warm_err = E.precision == 32 ? (double)__ldcg((const float*)(idx) + 10) : 0.0;
   }
   if (bs != PCBA_NONE) {
     for (int q = 0; q < l; ++q) {
