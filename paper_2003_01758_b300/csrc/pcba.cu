@@ -104,10 +104,21 @@ void layout_item(const HostProblem& P, int prec, ProbDesc& d) {
   // bounds, the FP64 offsets the patches are stored relative to, extremes of
   // the stored values; FP64: the extremes)
   d.copy_e = P.lin ? (prec == PCBA_FP32 ? 20LL : 16LL) * d.apad : 0;
+  d.off_og = d.off_oh = 0;
   if (P.lin) off = round_up(off + copies * d.copy_e, 128);
-  else if (prec == PCBA_FP32) off = round_up(off + d.apad * 4LL, 128);
+  else if (prec == PCBA_FP32) {
+    // dense FP32 families: error bounds, then the per-patch offsets, each
+    // array at least 32 floats (the TMA kernel loads 32 of each per group)
+    const long long ea = 4LL * std::max(d.apad, 32);
+    d.off_og = off + ea;
+    off = round_up(off + 2 * ea, 128);
+  }
   d.off_eh = off;
-  if (prec == PCBA_FP32) off = round_up(off + d.bpad * 4LL, 128);
+  if (prec == PCBA_FP32) {
+    const long long eb = 4LL * std::max(d.bpad, 32);
+    d.off_oh = off + eb;
+    off = round_up(off + 2 * eb, 128);
+  }
   d.off_g = off;
   d.copy_g = P.lin ? round_up(P.cg * d.apad * w, 128) : 0;
   off = P.lin ? off + 2 * d.copy_g : round_up(off + P.cg * d.apad * w, 128);
@@ -121,7 +132,9 @@ void layout_item(const HostProblem& P, int prec, ProbDesc& d) {
   off += 4LL * d.mwords;
   d.item_bytes = round_up(off, 256);
   d.payload_bytes = 4LL * P.l + (P.cp + P.alpha * P.cg + P.beta * P.ch) * w +
-                    (prec == PCBA_FP32 ? 12LL + 4LL * (P.alpha + P.beta) : 0) + 4LL * d.mwords;
+                    (prec == PCBA_FP32 ? 12LL + 4LL * (P.alpha + P.beta) : 0) +
+                    (prec == PCBA_FP32 && !P.lin ? 4LL * (P.alpha + P.beta) : 0) +
+                    4LL * d.mwords;
 }
 
 struct Grids {
@@ -1682,15 +1695,20 @@ int pcba_get_list(pcba_handle* h, long long* K_out, double* cost, double* ineq, 
       for (int j = 0; j < d.cp; ++j) cost[k * d.cp + j] = f32 ? O + val(d.off_cost, j) : val(d.off_cost, j);
     if (ineq)
       for (int i = 0; i < d.alpha; ++i) {
-        // FP32 linear families store each shared patch relative to an offset
-        const double Oi = f32 && d.lin ? ((const double*)(it + off_eg + 4LL * d.apad))[i] : 0.0;
+        // FP32 patches are stored relative to an offset (linear families:
+        // FP64, dense families: FP32)
+        const double Oi = !f32 ? 0.0
+                          : d.lin ? ((const double*)(it + off_eg + 4LL * d.apad))[i]
+                                  : (double)((const float*)(it + d.off_og))[i];
         for (int j = 0; j < d.cg; ++j)
           ineq[(k * d.alpha + i) * d.cg + j] = Oi + val(off_g, (long long)j * d.apad + i);
       }
     if (eq)
-      for (int i = 0; i < d.beta; ++i)
+      for (int i = 0; i < d.beta; ++i) {
+        const double Oh = f32 && !d.lin ? (double)((const float*)(it + d.off_oh))[i] : 0.0;
         for (int j = 0; j < d.ch; ++j)
-          eq[(k * d.beta + i) * d.ch + j] = val(d.off_h, (long long)j * d.bpad + i);
+          eq[(k * d.beta + i) * d.ch + j] = Oh + val(d.off_h, (long long)j * d.bpad + i);
+      }
     if (err) {
       float* e = err + k * nerr;
       if (f32) {

@@ -7,7 +7,9 @@
 //                      is shared by all items of a problem and kept in its state
 //   [32, 48)           cost meta (FP32 mode): f64 offset O, f32 error bound e_p
 //   off_cost           cost patch B_p, cp values of T (FP32: stored = value - O)
-//   off_eg, off_eh     FP32 mode: error bound per inequality / equality patch
+//   off_eg, off_eh     FP32 mode: error bound per inequality / equality patch, then
+//                      (dense families) the patch's FP32 offset o (off_og = off_eg +
+//                      4 max(apad, 32), off_oh likewise): stored = value - o
 //   off_g              inequality patches, coefficient-major: [cg][apad] of T,
 //                      so patch i is the column i ("constraint-minor")
 //   off_h              equality patches, [ch][bpad] of T
@@ -44,6 +46,7 @@
 #define PCBA_TRACE_PER_DIM 40
 #define PCBA_LIN_WORDS 8     // activity words (256 constraints) per linear subdivision unit
 #define PCBA_LIN_STRIDE 8    // doubles per linear constraint row (c, w_0 .. w_K-1)
+#define PCBA_ESTAGE_BYTES 256  // TMA subdivision stage: 32 FP32 error bounds, then 32 offsets
 #define PCBA_FAM_LIN 3        // refresh mark: every shared patch of a linear-family item
 #define PCBA_LIN32_STRIDE 16  // floats per FP32 row: the FP64 row rounded, then the remainders
 #define PCBA_LIN_BATCH 4     // units a warp of the linear subdivision kernel fetches at once
@@ -66,6 +69,7 @@ struct ProbDesc {
   long long item_bytes;      // stride of the list
   long long payload_bytes;   // algorithmic bytes of one item (no padding)
   long long off_cost, off_eg, off_eh, off_g, off_h;
+  long long off_og, off_oh;  // FP32 dense families: per-patch offsets (0: none)
   long long list_off;        // byte offset of the list in the arena
   long long M;               // capacity in items (memory test of Alg. 1 line 4)
   long long slot_off;        // offset of this problem in the per-slot scratch arrays

@@ -137,7 +137,7 @@ int prepare(K2Plan& g, const std::vector<ProbDesc>& desc, bool lin, int sms, int
   g.tma_stage_elems = (int)(cstage * 32);
   g.tma_cpmax = (int)cpmax;
   const size_t head_cap = ((size_t)64 + (size_t)cpmax * sizeof(T) + 32 + 127) / 128 * 128;
-  const size_t stage_bytes = (size_t)g.tma_stage_elems * sizeof(T) + 128 + head_cap;
+  const size_t stage_bytes = (size_t)g.tma_stage_elems * sizeof(T) + PCBA_ESTAGE_BYTES + head_cap;
   const int cand[][2] = {{8, 2}, {8, 3}, {4, 2}, {4, 3}, {2, 2}};
   const void* kt = tma_kernel(g.nmax, g.nfix);
   size_t smem_max = 0;

@@ -179,16 +179,39 @@ __global__ void __launch_bounds__(128) k1_convert(Engine E, const double* mat, i
     } else if (fam != 0) {
       float* dst = (float*)(item0 + (fam == 1 ? D.off_g : D.off_h)) + idx;
       const size_t pad = fam == 1 ? D.apad : D.bpad;
+      // dense families: stored relative to an FP32 offset o, the middle of
+      // the coefficient range rounded to FP32, so that the rounding error
+      // scales with the range; linear families' shared patches are stored
+      // absolute here (k_init gives them their offsets)
+      double o = 0.0;
+      if (!D.lin) {
+        double bmin = INFINITY, bmax = -INFINITY;
+        for (int j = lane; j < C; j += 32) { bmin = fmin(bmin, sA[j]); bmax = fmax(bmax, sA[j]); }
+        for (int w = 16; w > 0; w >>= 1) {
+          bmin = fmin(bmin, __shfl_xor_sync(0xffffffffu, bmin, w));
+          bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, w));
+        }
+        o = (double)__double2float_rn(0.5 * (bmin + bmax));
+      }
       double emax = 0.0;
       for (int j = lane; j < C; j += 32) {
-        const float s = __double2float_rn(sA[j]);
-        dst[(size_t)j * pad] = s;
-        emax = fmax(emax, fabs((double)s - sA[j]));  // exact in double
+        if (D.lin) {
+          const float s = __double2float_rn(sA[j]);
+          dst[(size_t)j * pad] = s;
+          emax = fmax(emax, fabs((double)s - sA[j]));  // exact in double
+        } else {
+          const double d = sA[j] - o;  // |d - (b - o)| <= |d| 2^-53
+          const float s = __double2float_rn(d);
+          dst[(size_t)j * pad] = s;
+          emax = fmax(emax, __dadd_ru(fabs((double)s - d), __dmul_ru(fabs(d), 0x1p-52)));
+        }
       }
-      for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-      if (lane == 0)
+      for (int w = 16; w > 0; w >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, w));
+      if (lane == 0) {
         ((float*)(item0 + (fam == 1 ? D.off_eg : D.off_eh)))[idx] =
             __double2float_ru(__dadd_ru(emax, err64));
+        if (!D.lin) ((float*)(item0 + (fam == 1 ? D.off_og : D.off_oh)))[idx] = (float)o;
+      }
     } else {
       // cost: stored = value - O with O the centre of the coefficient range
       double bmin = INFINITY, bmax = -INFINITY;
@@ -477,9 +500,11 @@ __device__ __forceinline__ void refresh_store_multi(const double* sA, int nf, in
 
 // Stores a converted patch (sA, C coefficients, bound base err64) as FP32
 // values at dst[j * pad] relative to the offset O (0, or the middle of its
-// range when centre is set), and returns its error bound (rounded up).
+// range when centre is set; rounded to FP32 when o32 is set), and returns its
+// error bound (rounded up).
 __device__ __forceinline__ float refresh_store(const double* sA, int C, double err64, bool centre,
-                                               float* dst, size_t pad, double& O, int lane) {
+                                               float* dst, size_t pad, double& O, int lane,
+                                               bool o32 = false) {
   O = 0.0;
   if (centre) {
     double bmin = INFINITY, bmax = -INFINITY;
@@ -492,6 +517,7 @@ __device__ __forceinline__ float refresh_store(const double* sA, int C, double e
       bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
     }
     O = 0.5 * (bmin + bmax);
+    if (o32) O = (double)__double2float_rn(O);
   }
   double emax = 0.0;
   for (int j = lane; j < C; j += 32) {
@@ -581,10 +607,12 @@ __global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
     const double* fam_mono = mono + D->cp + (fam ? (long long)D->alpha * D->cg : 0);
     const double err64 =
         refresh_convert(fam_mono + (long long)ip * C, C, D->l, deg, sT, sA, sB, sX, sY, lane);
+    // dense families: re-centred on an FP32 offset
     double O;
-    const float e = refresh_store(sA, C, err64, false, block + ip, pad, O, lane);
+    const float e = refresh_store(sA, C, err64, true, block + ip, pad, O, lane, true);
     if (lane == 0) {
       earr[ip] = e;
+      ((float*)(item + (fam ? D->off_oh : D->off_og)))[ip] = (float)O;
       atomicAdd(&E.plan->refreshed_total, 1ull);
     }
     __syncwarp();

@@ -42,15 +42,63 @@ struct FibAcc {
   T minL, maxL, minR, maxR, m;
 };
 
+// FP32 re-centring of a dense constraint patch at a bisection.  The patch is
+// stored as residuals r relative to an FP32 offset o.  With s = r_0 (its first
+// stored coefficient): o + s = o' + t exactly (TwoSum, Knuth), d = fl(s - t),
+// and the parent's residuals are shifted to fl(r - d) before the de Casteljau
+// triangle, so the children are stored relative to o'.  Then
+// o' + fl(r - d) = o + r - (d - (s - t)) + (fl(r - d) - (r - d)): the patch
+// error grows by at most u |d| (1 + 2u) + u m' (m' = max |fl(r - d)|), which
+// scales with the patch's range, not with its magnitude.
+struct Recentre {
+  float o, d;
+};
+__device__ __forceinline__ Recentre recentre(float o, float s) {
+  const float on = __fadd_rn(o, s);
+  const float bv = __fsub_rn(on, o);
+  const float t = __fadd_rn(__fsub_rn(o, __fsub_rn(on, bv)), __fsub_rn(s, bv));
+  return Recentre{on, __fsub_rn(s, t)};
+}
+
+// FP32 bounds of a re-centred child: the parent bound e, the shift d, the
+// triangle over residuals of magnitude m (n levels), then [o + min - e,
+// o + max + e] with directed rounding, the stored values o + min / o + max
+// (round to nearest, for the mark) and the mark floor.
+struct ChildBound {
+  float ec, lo, hi, smin, smax, floor;
+};
+__device__ __forceinline__ ChildBound child_bound(float ep, float m, float d, int n, float o,
+                                                  float mn, float mx) {
+  ChildBound b;
+  const float fn = (float)n;
+  b.ec = __fadd_ru(__fadd_ru(__fadd_ru(fabsf(ep), __fmul_ru(m, (fn + 1.0f + 0x1p-10f) * 0x1p-24f)),
+                             __fmul_ru(fabsf(d), 0x1p-24f * (1.0f + 0x1p-20f))),
+                   (fn + 2.0f) * 0x1p-149f);
+  b.lo = __fadd_rd(o, __fsub_rd(mn, b.ec));
+  b.hi = __fadd_ru(o, __fadd_ru(mx, b.ec));
+  b.smin = __fadd_rn(o, mn);
+  b.smax = __fadd_rn(o, mx);
+  // a refresh stores residuals rounded to FP32 (~u max |r| / 2) and adds the
+  // FP64 conversion bound, which grows with the power-basis weights (up to
+  // ~3^12 |value| 2^-45 for degree 12 on [-1,1]): below 8 u max |r| +
+  // 2^-30 |value| a refresh would not pay
+  b.floor = __fadd_ru(__fmul_ru(fmaxf(fabsf(mn), fabsf(mx)), 8.0f * 0x1p-24f),
+                      __fmul_ru(fmaxf(fabsf(b.smin), fabsf(b.smax)), 0x1p-30f));
+  return b;
+}
+
 // Thread i walks every fibre of constraint patch i (column i of a
 // coefficient-major [C][pad] block); the left child overwrites the parent.
 // The de Casteljau triangle (see split_fibre) is evaluated in place: after
 // level k, q[0] is left_k and q[N-k] is right_(N-k), and both are stored at
 // once, so only the N+1 working values stay in registers.  Writing left_k over
 // the parent's coefficient k is safe: it was loaded before the first level.
+// FP32 (RIG): every parent coefficient is first shifted by d (the patch's
+// re-centring, see constraint_part), and the left child's coefficient 0 is
+// stored too.
 template <typename T, int N, bool RIG>
 __device__ __forceinline__ void constraint_fibres(T* src, T* dR, size_t pad, int C, int stride,
-                                                  int i, FibAcc<T>& a) {
+                                                  int i, FibAcc<T>& a, T d = T(0)) {
   const int nf = C / (N + 1);
   const int blk = (N + 1) * stride;
   const size_t st = (size_t)stride * pad;
@@ -65,7 +113,11 @@ __device__ __forceinline__ void constraint_fibres(T* src, T* dR, size_t pad, int
     for (int j = 0; j <= N; ++j) q[j] = colL[j * st];
     if constexpr (RIG) {
 #pragma unroll
-      for (int j = 0; j <= N; ++j) a.m = fmax(a.m, fabs(q[j]));
+      for (int j = 0; j <= N; ++j) {
+        q[j] = addrn(q[j], -d);
+        a.m = fmax(a.m, fabs(q[j]));
+      }
+      colL[0] = q[0];
     }
     colR[N * st] = q[N];
     a.minR = fmin(a.minR, q[N]);
@@ -151,15 +203,15 @@ __device__ __forceinline__ int axis_stride(const int* deg, int l, int r) {
 
 
 // FP32 error bounds are stored with a mark in the sign bit, set when the bound
-// itself changes a decision of Def. 3 for this patch: the stored coefficients
-// (min s, max s) would decide it (infeasible, feasible, or inside the
-// equality window) but the enclosure [s_min - e, s_max + e] does not.  The
-// magnitude is the bound; k_refresh recomputes marked patches.
+// itself changes a decision of Def. 3 for this patch: the stored values (min s,
+// max s, offset included) would decide it (infeasible, feasible, or inside
+// the equality window) but the enclosure [lo, hi] does not.  The magnitude is
+// the bound; k_refresh recomputes marked patches.  floor: about what a refresh
+// could reach (its rounding of the stored values and the FP64 conversion
+// bound) times 8; a patch whose bound is below it is left alone.
 __device__ __forceinline__ float mark_err(float e, float smin, float smax, float lo, float hi,
-                                          int fam, float eqt) {
-  // a refresh cannot go below about one rounding of the coefficients: leave
-  // patches whose bound is already close to that floor
-  if (e <= 8.0f * fmaxf(fabsf(smin), fabsf(smax)) * 0x1p-24f) return e;
+                                          int fam, float eqt, float floor) {
+  if (e <= floor) return e;
   bool flip;
   if (fam == 0) {
     flip = (lo <= 0.0f && hi >= 0.0f) && (smin > 0.0f || smax < 0.0f);
@@ -358,24 +410,33 @@ __device__ void constraint_part(const ProbDesc* D, char* parent, char* right, in
     a.minL = a.minR = T(INFINITY);
     a.maxL = a.maxR = T(-INFINITY);
     a.m = T(0);
+    Recentre rc{0.0f, 0.0f};
+    float* opp = nullptr;
+    if constexpr (RIG) {
+      opp = (float*)(parent + (fam ? D->off_oh : D->off_og));
+      rc = recentre(opp[i], (float)src[i]);  // src[i]: coefficient 0 of patch i
+    }
     dispatch_degree<NMAX>(n, [&](auto nc) {
-      constraint_fibres<T, decltype(nc)::value, RIG>(src, dR, pad, C, stride, i, a);
+      constraint_fibres<T, decltype(nc)::value, RIG>(src, dR, pad, C, stride, i, a, T(rc.d));
     });
     T loL, hiL, loR, hiR;
     if constexpr (RIG) {
       float* ep = (float*)(parent + (fam ? D->off_eh : D->off_eg));
       float* er = (float*)(right + (fam ? D->off_eh : D->off_eg));
-      const float fn = (float)n;
-      const float ec = __fadd_ru(__fadd_ru(fabsf(ep[i]), __fmul_ru((float)a.m, fn * 0x1p-24f)),
-                                 fn * 0x1p-149f);
-      loL = __fsub_rd((float)a.minL, ec);
-      hiL = __fadd_ru((float)a.maxL, ec);
-      loR = __fsub_rd((float)a.minR, ec);
-      hiR = __fadd_ru((float)a.maxR, ec);
-      const float eL = mark_err(ec, (float)a.minL, (float)a.maxL, loL, hiL, fam, eqt);
-      const float eR = mark_err(ec, (float)a.minR, (float)a.maxR, loR, hiR, fam, eqt);
+      const ChildBound bL = child_bound(ep[i], (float)a.m, rc.d, n, rc.o, (float)a.minL,
+                                        (float)a.maxL);
+      const ChildBound bR = child_bound(ep[i], (float)a.m, rc.d, n, rc.o, (float)a.minR,
+                                        (float)a.maxR);
+      loL = bL.lo;
+      hiL = bL.hi;
+      loR = bR.lo;
+      hiR = bR.hi;
+      const float eL = mark_err(bL.ec, bL.smin, bL.smax, loL, hiL, fam, eqt, bL.floor);
+      const float eR = mark_err(bR.ec, bR.smin, bR.smax, loR, hiR, fam, eqt, bR.floor);
       ep[i] = eL;
       er[i] = eR;
+      opp[i] = rc.o;
+      ((float*)(right + (fam ? D->off_oh : D->off_og)))[i] = rc.o;
       mL = __float_as_uint(eL) >> 31;
       mR = __float_as_uint(eR) >> 31;
     } else {
@@ -658,13 +719,16 @@ __device__ __forceinline__ void issue_unit(const Engine& E, const WarpUnit& w, T
   }
   const int C = w.fam ? D->ch : D->cg;
   unsigned bytes = (unsigned)C * 32u * (unsigned)sizeof(T) + hb;
-  if (sizeof(T) == 4) bytes += 128u;
+  if (sizeof(T) == 4) bytes += 256u;
   mbar_arrive_expect_tx(bar, bytes);
   if (hb) bulk_load(head, item, hb, bar);
   const char* tm = (const char*)E.tmaps + ((size_t)w.p * 2 + w.fam) * 128;
   tma_load_3d(stage, tm, w.x, 0, (int)w.pslot, bar);
-  if (sizeof(T) == 4)
+  if (sizeof(T) == 4) {
+    // the group's 32 error bounds, then its 32 offsets
     bulk_load(estage, item + (w.fam ? D->off_eh : D->off_eg) + (size_t)w.x * 4, 128u, bar);
+    bulk_load(estage + 32, item + (w.fam ? D->off_oh : D->off_og) + (size_t)w.x * 4, 128u, bar);
+  }
 }
 
 // Fibres of one column (lane) of a staged [C][32] block: loads from shared
@@ -680,7 +744,7 @@ __device__ __forceinline__ void issue_unit(const Engine& E, const WarpUnit& w, T
 template <typename T, int N, bool RIG, int NF>
 __device__ __forceinline__ void staged_fibre_group(const T* sl, T* gL, T* gR, size_t pad,
                                                    size_t st, int blk, int stride, int f,
-                                                   FibAcc<T>& a) {
+                                                   FibAcc<T>& a, T d) {
   int c0[NF];
   T q[NF][N + 1];
 #pragma unroll
@@ -695,10 +759,15 @@ __device__ __forceinline__ void staged_fibre_group(const T* sl, T* gL, T* gR, si
 #pragma unroll
   for (int h = 0; h < NF; ++h) {
     if constexpr (RIG) {
+      // FP32: the re-centring shift (see recentre); left_0 is stored shifted
 #pragma unroll
-      for (int j = 0; j <= N; ++j) a.m = fmax(a.m, fabs(q[h][j]));
+      for (int j = 0; j <= N; ++j) {
+        q[h][j] = addrn(q[h][j], -d);
+        a.m = fmax(a.m, fabs(q[h][j]));
+      }
+      gL[(size_t)c0[h] * pad] = q[h][0];
     }
-    // left_0 = f_0 already sits in the parent slot the left child overwrites
+    // (FP64: left_0 = f_0 already sits in the parent slot the left child overwrites)
     gR[(size_t)c0[h] * pad + N * st] = q[h][N];
     a.minL = fmin(a.minL, q[h][0]);
     a.maxL = fmax(a.maxL, q[h][0]);
@@ -729,15 +798,16 @@ __device__ __forceinline__ void staged_fibre_group(const T* sl, T* gL, T* gR, si
 
 template <typename T, int N, bool RIG>
 __device__ __forceinline__ void staged_fibres(const T* stage, T* gL, T* gR, size_t pad, int C,
-                                              int stride, int lane, FibAcc<T>& a) {
+                                              int stride, int lane, FibAcc<T>& a, T d = T(0)) {
   const int nf = C / (N + 1);
   const int blk = (N + 1) * stride;
   const size_t st = (size_t)stride * pad;
   const T* sl = stage + lane;
   int f = 0;
 #pragma unroll 1
-  for (; f + 1 < nf; f += 2) staged_fibre_group<T, N, RIG, 2>(sl, gL, gR, pad, st, blk, stride, f, a);
-  if (f < nf) staged_fibre_group<T, N, RIG, 1>(sl, gL, gR, pad, st, blk, stride, f, a);
+  for (; f + 1 < nf; f += 2)
+    staged_fibre_group<T, N, RIG, 2>(sl, gL, gR, pad, st, blk, stride, f, a, d);
+  if (f < nf) staged_fibre_group<T, N, RIG, 1>(sl, gL, gR, pad, st, blk, stride, f, a, d);
 }
 
 // The bound reductions of one warp's 32 patches, published with atomics
@@ -793,7 +863,7 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
   // staging; head = box, cost meta and cost patch of the parent (group 0),
   // with the unit's WarpUnit header in its last 32 bytes
   const size_t head_cap = ((size_t)64 + (size_t)cpmax * sizeof(T) + 32 + 127) / 128 * 128;
-  const size_t stage_bytes = (size_t)stage_elems * sizeof(T) + 128 + head_cap;
+  const size_t stage_bytes = (size_t)stage_elems * sizeof(T) + PCBA_ESTAGE_BYTES + head_cap;
   const size_t warp_bytes = (size_t)stages * stage_bytes + (size_t)2 * cpmax * sizeof(T);
   const size_t warp_bytes_al = (warp_bytes + 127) / 128 * 128;
   unsigned char* wb = k2t_smem + (size_t)warp * warp_bytes_al;
@@ -823,7 +893,7 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
     if (lane == 0) {
       const WarpUnit w = resolve_unit(E, first + (unsigned)j * wpb, ic);
       unsigned char* st = wb + (size_t)j * stage_bytes;
-      unsigned char* head = st + (size_t)stage_elems * sizeof(T) + 128;
+      unsigned char* head = st + (size_t)stage_elems * sizeof(T) + PCBA_ESTAGE_BYTES;
       *(WarpUnit*)(head + head_cap - 32) = w;
       issue_unit<T>(E, w, (T*)st, (float*)(st + (size_t)stage_elems * sizeof(T)), head, &bars[j]);
     }
@@ -838,14 +908,15 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
   // inequality groups first, then equality groups)
   int cx_fam = -1, cx_cnt = 0, cx_C = 0, cx_n = 0, cx_stride = 1;
   size_t cx_pad = 0;
-  long long cx_off = 0, cx_offe = 0;
+  long long cx_off = 0, cx_offe = 0, cx_offo = 0;
   for (int j = 0; j < J; ++j) {
     const int s = j % stages;
     const unsigned parity = (unsigned)(j / stages) & 1u;
     unsigned char* st = wb + (size_t)s * stage_bytes;
     const T* stage = (const T*)st;
     const float* estage = (const float*)(st + (size_t)stage_elems * sizeof(T));
-    const WarpUnit w = *(const WarpUnit*)(st + (size_t)stage_elems * sizeof(T) + 128 + head_cap - 32);
+    const WarpUnit w =
+        *(const WarpUnit*)(st + (size_t)stage_elems * sizeof(T) + PCBA_ESTAGE_BYTES + head_cap - 32);
     const ProbDesc* D = E.desc + w.p;
     if (w.p != cx_p) {
       const ProbState* S = E.state + w.p;
@@ -867,6 +938,7 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
       cx_pad = fam ? D->bpad : D->apad;
       cx_off = fam ? D->off_h : D->off_g;
       cx_offe = fam ? D->off_eh : D->off_eg;
+      cx_offo = fam ? D->off_oh : D->off_og;
       cx_n = deg[cx_r];
       cx_stride = axis_stride(deg, D->l, cx_r);
     }
@@ -891,7 +963,7 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
       return;
     }
     if (w.g == 0) {
-      const unsigned char* head = st + (size_t)stage_elems * sizeof(T) + 128;
+      const unsigned char* head = st + (size_t)stage_elems * sizeof(T) + PCBA_ESTAGE_BYTES;
       cost_part<T, NMAX, NFIX>(cx_cost, (const char*)head, parent, right, recL, recR, cost_stage,
                                mk, cost_thr);
       if (lane == 0) {
@@ -925,23 +997,29 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
         a.m = T(0);
         T* gL = (T*)(parent + off) + i;
         T* gR = (T*)(right + off) + i;
+        // FP32: re-centre on the staged coefficient 0 of this lane's patch
+        Recentre rc{0.0f, 0.0f};
+        if constexpr (RIG) rc = recentre(estage[32 + lane], (float)stage[lane]);
         dispatch_fixed<NMAX, NFIX>(n, [&](auto nc) {
-          staged_fibres<T, decltype(nc)::value, RIG>(stage, gL, gR, pad, C, stride, lane, a);
+          staged_fibres<T, decltype(nc)::value, RIG>(stage, gL, gR, pad, C, stride, lane, a,
+                                                     T(rc.d));
         });
         T loL, hiL, loR, hiR;
         if constexpr (RIG) {
-          const float fnn = (float)n;
-          const float ec = __fadd_ru(__fadd_ru(fabsf(estage[lane]),
-                                               __fmul_ru((float)a.m, fnn * 0x1p-24f)),
-                                     fnn * 0x1p-149f);
-          loL = __fsub_rd((float)a.minL, ec);
-          hiL = __fadd_ru((float)a.maxL, ec);
-          loR = __fsub_rd((float)a.minR, ec);
-          hiR = __fadd_ru((float)a.maxR, ec);
-          const float eL = mark_err(ec, (float)a.minL, (float)a.maxL, loL, hiL, fam, eqt);
-          const float eR = mark_err(ec, (float)a.minR, (float)a.maxR, loR, hiR, fam, eqt);
+          const ChildBound bL = child_bound(estage[lane], (float)a.m, rc.d, n, rc.o,
+                                            (float)a.minL, (float)a.maxL);
+          const ChildBound bR = child_bound(estage[lane], (float)a.m, rc.d, n, rc.o,
+                                            (float)a.minR, (float)a.maxR);
+          loL = bL.lo;
+          hiL = bL.hi;
+          loR = bR.lo;
+          hiR = bR.hi;
+          const float eL = mark_err(bL.ec, bL.smin, bL.smax, loL, hiL, fam, eqt, bL.floor);
+          const float eR = mark_err(bR.ec, bR.smin, bR.smax, loR, hiR, fam, eqt, bR.floor);
           ((float*)(parent + cx_offe))[i] = eL;
           ((float*)(right + cx_offe))[i] = eR;
+          ((float*)(parent + cx_offo))[i] = rc.o;
+          ((float*)(right + cx_offo))[i] = rc.o;
           mL = __float_as_uint(eL) >> 31;
           mR = __float_as_uint(eR) >> 31;
         } else {
@@ -965,7 +1043,7 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
     fence_proxy_async_smem();
     if (lane == 0 && j + stages < J) {
       const WarpUnit wn = resolve_unit(E, first + (unsigned)(j + stages) * wpb, ic);
-      unsigned char* head = st + (size_t)stage_elems * sizeof(T) + 128;
+      unsigned char* head = st + (size_t)stage_elems * sizeof(T) + PCBA_ESTAGE_BYTES;
       *(WarpUnit*)(head + head_cap - 32) = wn;
       issue_unit<T>(E, wn, (T*)st, (float*)(st + (size_t)stage_elems * sizeof(T)), head, &bars[s]);
     }

@@ -64,11 +64,12 @@ def test_create_validates_on_host(lib):
 def test_item_bytes_follow_memory_formula(lib):
     """Eq. (memory_per_item) counts 2l + Pi(P+1) + alpha Pi(G+1) + beta Pi(H+1)
     entries of 4 B; the FP32 layout stores the same coefficients in 4 B plus
-    one error bound per patch, the dyadic box and padding to 128 B rows."""
+    an error bound and an offset per constraint patch, the dyadic box and
+    padding to 128 B rows."""
     p = W.rtd(2000)
     s = pcba.Solver(p.cost, p.ineq, p.eq, p.lo, p.hi, precision=pcba.FP32)
     entries = 2 * 2 + 49 + 512 * 49
-    assert 4 * entries <= s.item_bytes() <= 4 * entries + 4 * 513 + 1024
+    assert 4 * entries <= s.item_bytes() <= 4 * entries + 8 * 513 + 1024
     s64 = pcba.Solver(p.cost, p.ineq, p.eq, p.lo, p.hi, precision=pcba.FP64)
     assert 8 * (49 + 512 * 49) <= s64.item_bytes() <= 8 * (49 + 512 * 49) + 1024
 
