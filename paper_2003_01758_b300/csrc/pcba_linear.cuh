@@ -60,8 +60,8 @@
 //                  at most PCBA_LIN_LIGHT_MAX active constraints is bounded
 //                  here from the children still staged in shared memory; the
 //                  live chunks of the other items are grouped into windows of
-//                  about PCBA_LIN_WIN active constraints, the first bounded
-//                  here and the others queued as (item, window).
+//                  about PCBA_LIN_WIN active constraints; a single window is
+//                  bounded here, several are queued as (item, window).
 //   k2_lin_bound   one warp per queued (item, window): stages both children and
 //                  bounds the window's constraints as the split kernel does.
 // Bounding a window compacts its active constraints and bounds each on both
@@ -679,13 +679,17 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
   int cx_p = -1, cx_K = 0, cx_r = 0, cx_ftop = 0, cx_hw = 0;
   unsigned cx_beg = 0, cx_end = 0;
   const ProbDesc* D = nullptr;
-  // items are fetched in batches from a counter (reset before every step)
+  // items are fetched in batches from a counter (reset before every step);
+  // one at a time while there are fewer than four per resident warp (the
+  // first steps: few items, each with many active constraints)
+  const unsigned bsz =
+      items < 4u * gridDim.x * (blockDim.x >> 5) ? 1u : (unsigned)PCBA_LIN_BATCH;
   for (;;) {
     unsigned ubeg = 0;
-    if (lane == 0) ubeg = atomicAdd(&E.plan->lin_next2, (unsigned)PCBA_LIN_BATCH);
+    if (lane == 0) ubeg = atomicAdd(&E.plan->lin_next2, bsz);
     ubeg = __shfl_sync(0xffffffffu, ubeg, 0);
     if (ubeg >= items) break;
-    const unsigned uend = min(items, ubeg + (unsigned)PCBA_LIN_BATCH);
+    const unsigned uend = min(items, ubeg + bsz);
     for (unsigned u = ubeg; u < uend; ++u) {
       if (u < cx_beg || u >= cx_end || cx_p < 0) {
         cx_p = find_problem(E.kr_pre, E.np, u);
@@ -935,8 +939,9 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
       // constraints is bounded here, from the children still staged.  The
       // live chunks of the other items are grouped into windows (at most 4
       // chunks within 16 consecutive ones, at most PCBA_LIN_WIN active
-      // constraints unless a single chunk) and queued for k2_lin_bound; the
-      // first window, and those the full queue refuses, stay here.
+      // constraints unless a single chunk); a single window stays here,
+      // several are queued for k2_lin_bound (those the full queue refuses
+      // stay here too).
       {
         const int chunks = D->lin_chunks, mwords = D->mwords;
         const bool summ = chunks <= 64;  // (more chunks keep no summaries: all are read)
@@ -954,9 +959,10 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
         __syncwarp();
         const int nlive = summ ? __popcll(psum) : chunks;
         // what this warp bounds itself: mode 1 the light window (lane words
-        // lwi / lwv / lcb), 2 the windows in ls.sWin the queue refused (and
-        // the first), 3 the single-chunk windows the queue refused
-        int mode = 0, nwin = 0;
+        // lwi / lwv / lcb), 2 the windows in ls.sWin not queued (a single
+        // one, or those the full queue refused), 3 the single-chunk windows
+        // the queue refused
+        int mode = 0, nwin = 0, nq = 0;
         unsigned qb = 0u;
         int lwi = -1;
         unsigned lwv = 0u;
@@ -1016,10 +1022,13 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
           }
           nwin = __shfl_sync(0xffffffffu, nwin, 0);
           __syncwarp();
-          if (lane == 0 && nwin > 1) qb = atomicAdd(&E.plan->lin_qcount, (unsigned)(nwin - 1));
+          // several windows: all go to the bound kernel's warps (a heavy
+          // item's windows would otherwise run one after another here)
+          nq = nwin > 1 ? nwin : 0;
+          if (lane == 0 && nq > 0) qb = atomicAdd(&E.plan->lin_qcount, (unsigned)nq);
           qb = __shfl_sync(0xffffffffu, qb, 0);
-          for (int i2 = 1 + lane; i2 < nwin; i2 += 32) {
-            const unsigned q = qb + (unsigned)(i2 - 1);
+          for (int i2 = lane; i2 < nq; i2 += 32) {
+            const unsigned q = qb + (unsigned)i2;
             if (q < E.lin_qcap) E.lin_queue[q] = make_uint2(u, ls.sWin[i2]);
           }
           mode = 2;
@@ -1040,7 +1049,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
           if (mode == 1) {
             if (i2 > 0) break;
           } else if (mode == 2) {
-            while (i2 > 0 && i2 < nwin && qb + (unsigned)(i2 - 1) < E.lin_qcap) ++i2;
+            while (i2 < nq && qb + (unsigned)i2 < E.lin_qcap) ++i2;  // queued
             if (i2 >= nwin) break;
             lin_window_words(D, pmask, ls.sWin[i2], true, wi, wv, cb);
           } else {
@@ -1070,12 +1079,14 @@ __global__ void __launch_bounds__(256, PCBA_LIN_BOUND_BLOCKS) k2_lin_bound(Engin
   LinChildren<T, K>& ch = *reinterpret_cast<LinChildren<T, K>*>(ls.sCh);
   const unsigned units = min(E.plan->lin_qcount, E.lin_qcap);
   const int par = E.plan->steps_global & 1;  // the children's data is in copy par ^ 1
+  const unsigned bsz =
+      units < 4u * gridDim.x * (blockDim.x >> 5) ? 1u : (unsigned)PCBA_LIN_BATCH;
   for (;;) {
     unsigned ubeg = 0;
-    if (lane == 0) ubeg = atomicAdd(&E.plan->lin_next, (unsigned)PCBA_LIN_BATCH);
+    if (lane == 0) ubeg = atomicAdd(&E.plan->lin_next, bsz);
     ubeg = __shfl_sync(0xffffffffu, ubeg, 0);
     if (ubeg >= units) break;
-    const unsigned uend = min(units, ubeg + (unsigned)PCBA_LIN_BATCH);
+    const unsigned uend = min(units, ubeg + bsz);
     for (unsigned q = ubeg; q < uend; ++q) {
       const uint2 ent = E.lin_queue[q];
       const int p = find_problem(E.kr_pre, E.np, ent.x);
