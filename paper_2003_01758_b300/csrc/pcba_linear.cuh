@@ -235,10 +235,16 @@ __host__ __device__ constexpr size_t lin_bound_warp_bytes(int cgmax) {
   return (8 * (size_t)cgmax * sizeof(T) + 15) / 16 * 16 + lin_scratch_bytes();
 }
 
-// A window (first chunk t0 in bits 0..15, bit j of bits 16..31: chunk t0 + j
-// belongs to it; at most 4 chunks) as lane q's word: word q % 8 of the
-// window's (q / 8)-th chunk, its index wi (-1: none), value wv and summary
-// bit cb (0 without summaries).
+// A window, as lane q's word: its index wi (-1: none), value wv and summary
+// bit cb (0 without summaries).  Two forms (chunk t0 in bits 0..15):
+//   bit 31 clear: bit j of bits 16..30 says chunk t0 + j belongs to it (at
+//     most 4 chunks); lane q takes word q % 8 of its (q / 8)-th chunk;
+//   bit 31 set: words a .. b-1 of chunk t0 (a in bits 16..18, b in bits
+//     19..22), for a chunk with more active constraints than one window
+//     takes; lane q takes word a + q.
+__device__ __forceinline__ unsigned lin_word_window(int t0, int a, int b) {
+  return (unsigned)t0 | ((unsigned)a << 16) | ((unsigned)b << 19) | 0x80000000u;
+}
 __device__ __forceinline__ void lin_window_words(const ProbDesc* D, const unsigned* pmask,
                                                  unsigned win, bool summ, int& wi, unsigned& wv,
                                                  unsigned long long& cb) {
@@ -246,7 +252,17 @@ __device__ __forceinline__ void lin_window_words(const ProbDesc* D, const unsign
   wi = -1;
   wv = 0u;
   cb = 0ull;
-  unsigned m = win >> 16;
+  if (win & 0x80000000u) {
+    const int t = (int)(win & 0xFFFFu), a = (int)((win >> 16) & 7u), b = (int)((win >> 19) & 15u);
+    const int w = t * PCBA_LIN_WORDS + a + lane;
+    if (lane < b - a && w < D->mwords) {
+      wi = w;
+      wv = pmask[w];
+      cb = summ ? 1ull << t : 0ull;
+    }
+    return;
+  }
+  unsigned m = (win >> 16) & 0x7FFFu;
   for (int i = 0; i < (lane >> 3); ++i) m &= m - 1u;
   if (m != 0u) {
     const int t = (int)(win & 0xFFFFu) + __ffs(m) - 1;
@@ -1002,15 +1018,34 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
             if ((lane & 7) == 0 && j < nlive) ls.sCnt[j] = (unsigned short)c;
           }
           __syncwarp();
-          // the windows, formed greedily by lane 0
+          // the windows, formed greedily by lane 0; a chunk with more than
+          // PCBA_LIN_WIN active constraints is cut into ranges of its words
+          // (while the window list has room)
           if (lane == 0) {
             int j = 0;
             while (j < nlive) {
               const int t0 = ls.sChunk[j];
+              if (ls.sCnt[j] > PCBA_LIN_WIN && nwin + PCBA_LIN_WORDS <= 64) {
+                int a = 0;
+                unsigned cw = 0u;
+                for (int b = 0; b < PCBA_LIN_WORDS; ++b) {
+                  const int w = t0 * PCBA_LIN_WORDS + b;
+                  const unsigned c = w < mwords ? (unsigned)__popc(pmask[w]) : 0u;
+                  if (b > a && cw + c > (unsigned)PCBA_LIN_WIN) {
+                    ls.sWin[nwin++] = lin_word_window(t0, a, b);
+                    a = b;
+                    cw = 0u;
+                  }
+                  cw += c;
+                }
+                ls.sWin[nwin++] = lin_word_window(t0, a, PCBA_LIN_WORDS);
+                ++j;
+                continue;
+              }
               unsigned mask = 1u, cw = ls.sCnt[j];
               int nch = 1;
               ++j;
-              while (j < nlive && nch < 4 && ls.sChunk[j] - t0 < 16 &&
+              while (j < nlive && nch < 4 && ls.sChunk[j] - t0 < 15 &&
                      cw + ls.sCnt[j] <= (unsigned)PCBA_LIN_WIN) {
                 mask |= 1u << (ls.sChunk[j] - t0);
                 cw += ls.sCnt[j];
@@ -1081,6 +1116,10 @@ __global__ void __launch_bounds__(256, PCBA_LIN_BOUND_BLOCKS) k2_lin_bound(Engin
   const int par = E.plan->steps_global & 1;  // the children's data is in copy par ^ 1
   const unsigned bsz =
       units < 4u * gridDim.x * (blockDim.x >> 5) ? 1u : (unsigned)PCBA_LIN_BATCH;
+  unsigned cur = 0xFFFFFFFFu;  // the item whose children are staged
+  int p = 0, k = 0, Kl = 0;
+  const ProbDesc* D = nullptr;
+  char *left = nullptr, *right = nullptr;
   for (;;) {
     unsigned ubeg = 0;
     if (lane == 0) ubeg = atomicAdd(&E.plan->lin_next, bsz);
@@ -1089,27 +1128,29 @@ __global__ void __launch_bounds__(256, PCBA_LIN_BOUND_BLOCKS) k2_lin_bound(Engin
     const unsigned uend = min(units, ubeg + bsz);
     for (unsigned q = ubeg; q < uend; ++q) {
       const uint2 ent = E.lin_queue[q];
-      const int p = find_problem(E.kr_pre, E.np, ent.x);
-      const ProbDesc* D = E.desc + p;
-      const int k = (int)(ent.x - E.kr_pre[p]);
-      const int Kl = E.state[p].K;
-      char* list = E.arena + D->list_off;
-      char* left = list + (size_t)E.map[D->slot_off + k] * D->item_bytes;
-      char* right = list + (size_t)E.map[D->slot_off + k + Kl] * D->item_bytes;
-      const int C = D->cg;
-      __syncwarp();  // the previous unit's readers of the staging buffers are done
-      // the children's shared patches, and their metadata (lane c K + g)
-      lin_copy2<T, 2>(sS, (const T*)(left + D->off_g + (par ^ 1) * D->copy_g), 4 * C,
-                   sS + 4 * (size_t)cgmax, (const T*)(right + D->off_g + (par ^ 1) * D->copy_g),
-                   4 * C, lane);
-      {
-        T vmn = T(0), vmx = T(0);
-        float vM = 0.0f, vec = 0.0f, vOh = 0.0f, vOl = 0.0f;
+      // an item's windows are queued one after another: the next window of
+      // the same item reuses the staged children
+      if (ent.x != cur) {
+        cur = ent.x;
+        p = find_problem(E.kr_pre, E.np, ent.x);
+        D = E.desc + p;
+        k = (int)(ent.x - E.kr_pre[p]);
+        Kl = E.state[p].K;
+        char* list = E.arena + D->list_off;
+        left = list + (size_t)E.map[D->slot_off + k] * D->item_bytes;
+        right = list + (size_t)E.map[D->slot_off + k + Kl] * D->item_bytes;
+        const int C = D->cg;
+        __syncwarp();  // the previous unit's readers of the staging buffers are done
+        // the children's shared patches, and their metadata (lane c K + g)
+        lin_copy2<T, 2>(sS, (const T*)(left + D->off_g + (par ^ 1) * D->copy_g), 4 * C,
+                        sS + 4 * (size_t)cgmax,
+                        (const T*)(right + D->off_g + (par ^ 1) * D->copy_g), 4 * C, lane);
         if (lane < 2 * K) {
           const int c = lane / K, g = lane - c * K;
           char* mc = (c ? right : left) + D->off_eg + (par ^ 1) * D->copy_e;
-          vmn = LinMeta<T>::mn(mc, 4)[g];
-          vmx = LinMeta<T>::mx(mc, 4)[g];
+          const T vmn = LinMeta<T>::mn(mc, 4)[g];
+          const T vmx = LinMeta<T>::mx(mc, 4)[g];
+          float vM = 0.0f, vec = 0.0f, vOh = 0.0f, vOl = 0.0f;
           if constexpr (RIG) {
             vM = fmaxf(fabsf((float)vmn), fabsf((float)vmx));
             vec = LinMeta<T>::err(mc, 4)[g];
