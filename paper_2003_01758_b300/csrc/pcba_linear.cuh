@@ -695,11 +695,12 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
   int cx_p = -1, cx_K = 0, cx_r = 0, cx_ftop = 0, cx_hw = 0;
   unsigned cx_beg = 0, cx_end = 0;
   const ProbDesc* D = nullptr;
-  // items are fetched in batches from a counter (reset before every step);
-  // one at a time while there are fewer than four per resident warp (the
-  // first steps: few items, each with many active constraints)
+  // items are fetched from a counter (reset before every step), one at a
+  // time unless there are many per resident warp: a step ends when its last
+  // warp does, so batches that leave some warps one batch more than others
+  // cost a whole batch of latency
   const unsigned bsz =
-      items < 4u * gridDim.x * (blockDim.x >> 5) ? 1u : (unsigned)PCBA_LIN_BATCH;
+      items < 16u * gridDim.x * (blockDim.x >> 5) ? 1u : (unsigned)PCBA_LIN_BATCH;
   for (;;) {
     unsigned ubeg = 0;
     if (lane == 0) ubeg = atomicAdd(&E.plan->lin_next2, bsz);
@@ -1115,7 +1116,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_BOUND_BLOCKS) k2_lin_bound(Engin
   const unsigned units = min(E.plan->lin_qcount, E.lin_qcap);
   const int par = E.plan->steps_global & 1;  // the children's data is in copy par ^ 1
   const unsigned bsz =
-      units < 4u * gridDim.x * (blockDim.x >> 5) ? 1u : (unsigned)PCBA_LIN_BATCH;
+      units < 16u * gridDim.x * (blockDim.x >> 5) ? 1u : (unsigned)PCBA_LIN_BATCH;
   unsigned cur = 0xFFFFFFFFu;  // the item whose children are staged
   int p = 0, k = 0, Kl = 0;
   const ProbDesc* D = nullptr;
