@@ -195,7 +195,7 @@ struct pcba_batch {
   double* d_stencil = nullptr;  // guided solves: [stencil_cap] doubles
   double* d_polish = nullptr;   // pcba_batch_polish output: [np][PCBA_MAXD]
   float* d_lin32 = nullptr;     // linear families: [lin_rows][PCBA_LIN32_STRIDE] FP32 pairs of the rows
-  uint2* d_lin_queue = nullptr; // linear families: heavy (item, chunk) units of a step
+  uint4* d_lin_queue = nullptr; // linear families: heavy (item, window, problem, k) units
   double* d_lin64 = nullptr;    // the same in FP64
   // pcba_batch_solve_polished: the warm points are already in d_warm (written
   // by the polish kernel), and the counts of the phases before the last solve
@@ -733,14 +733,14 @@ int batch_create_impl(pcba_batch** out, pcba_handle** hs, int n, size_t mem_cap_
   PCBA_ALLOC(b->d_eval, sizeof(EvalOut) * n);
   PCBA_ALLOC(b->d_lin32, sizeof(float) * PCBA_LIN32_STRIDE * std::max<long long>(lin_rows, 1));
   PCBA_ALLOC(b->d_lin64, sizeof(double) * PCBA_LIN_STRIDE * std::max<long long>(lin_rows, 1));
-  // queue of heavy (item, chunk) units: every item of every problem with all
+  // queue of heavy (item, window) units: every item of every problem with all
   // its chunks, at most 4 Mi entries (a full queue leaves units to the split)
   long long qcap = 0;
   if (b->lin)
     for (int k = 0; k < n; ++k)
       qcap = std::min<long long>(qcap + (long long)std::max<long long>(M, 2) *
                                             b->desc[k].lin_chunks, 1LL << 22);
-  PCBA_ALLOC(b->d_lin_queue, sizeof(uint2) * std::max<long long>(qcap, 1));
+  PCBA_ALLOC(b->d_lin_queue, sizeof(uint4) * std::max<long long>(qcap, 1));
   const unsigned mark_cap = 1u << 20;  // marked patches per step (extra marks are dropped)
   PCBA_ALLOC(b->d_marks, sizeof(uint4) * 2 * (prec == PCBA_FP32 ? mark_cap : 1));
 #undef PCBA_ALLOC

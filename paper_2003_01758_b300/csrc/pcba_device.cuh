@@ -50,9 +50,13 @@
 #define PCBA_FAM_LIN 3        // refresh mark: every shared patch of a linear-family item
 #define PCBA_LIN32_STRIDE 16  // floats per FP32 row: the FP64 row rounded, then the remainders
 #define PCBA_LIN_BATCH 4     // units a warp of the linear subdivision kernel fetches at once
-#define PCBA_LIN_LIGHT_MAX 96  // an item with <= 4 live chunks and at most this many active
+#ifndef PCBA_LIN_LIGHT_MAX
+#define PCBA_LIN_LIGHT_MAX 64  // an item with <= 4 live chunks and at most this many active
                                // constraints is bounded by the split kernel
+#endif
+#ifndef PCBA_LIN_WIN
 #define PCBA_LIN_WIN 64      // active constraints per queued window (unless a single chunk)
+#endif
 #define PCBA_LIN_IDX 256     // compaction buffer of a warp (constraints per pass)
 
 struct ProbDesc {
@@ -167,7 +171,7 @@ struct Plan {
   unsigned long long lin_full;   // of which bounded from the coefficient range (not the interval)
   unsigned lin_next;             // next unit of the linear bound kernel to hand out
   unsigned lin_next2;            // next item of the linear split kernel to hand out
-  unsigned lin_qcount;           // (item, chunk) units queued for the linear bound kernel
+  unsigned lin_qcount;           // (item, window) units queued for the linear bound kernel
   unsigned k3_done;
   unsigned k4_done;             // blocks of k_move_control finished (the last one runs the control)
   int any_running;
@@ -207,7 +211,7 @@ struct Engine {
   double* root_raw;        // optional FP64 root patch dump
   const unsigned* k1_pre;  // [np + 1] patches per problem prefix
   const void* tmaps;       // [np][2] tensor maps (CUtensorMap) of the g / h blocks, or null
-  uint2* lin_queue;        // linear families: (item, chunk) units of heavy items, this step
+  uint4* lin_queue;        // linear families: (item, window, problem, k) units of heavy items
   unsigned lin_qcap;       // its capacity (a full queue leaves the units to the split kernel)
   const float* lin32;      // linear families: constraint rows in FP32, [rows][16]: the
                            // FP64 row rounded to nearest (8), then the remainders
@@ -251,6 +255,22 @@ __device__ __forceinline__ int find_problem(const unsigned* pre, int np, unsigne
   while (hi - lo > 1) {
     int mid = (lo + hi) >> 1;
     if (__ldg(pre + mid) <= u) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// The same search by a whole warp (all 32 lanes, warp-uniform u): each round
+// splits [lo, hi) into 32 parts and reads one boundary per lane, so 1024
+// problems take two dependent loads instead of ten.
+__device__ __forceinline__ int find_problem_warp(const unsigned* pre, int np, unsigned u,
+                                                 int lane) {
+  int lo = 0, hi = np;  // pre[lo] <= u; the answer lies in [lo, hi)
+  while (hi - lo > 1) {
+    const int step = (hi - lo + 31) >> 5;
+    const int idx = lo + lane * step;
+    const unsigned b = __ballot_sync(0xffffffffu, idx < hi && __ldg(pre + idx) <= u);
+    lo += (31 - __clz(b)) * step;  // lane 0 reads pre[lo] <= u: b != 0
+    hi = min(hi, lo + step);
   }
   return lo;
 }

@@ -168,6 +168,12 @@ __device__ __forceinline__ void lin_copy2(T* d1, const T* s1, int n1, T* d2, con
   const int a = n1 / V, b = n2 / V, n = a + b;
   const float4* x1 = (const float4*)s1;
   const float4* x2 = (const float4*)s2;
+  // the ragged ends (fewer than V elements each, lanes 0.. and 8..) are read
+  // with the first pieces
+  const int r1 = n1 - a * V, r2 = n2 - b * V;
+  T t = T(0);
+  if (lane < r1) t = s1[a * V + lane];
+  else if (lane >= 8 && lane - 8 < r2) t = s2[b * V + lane - 8];
   for (int e0 = lane; e0 < n; e0 += 32 * U) {
     float4 v[U];
 #pragma unroll
@@ -184,8 +190,8 @@ __device__ __forceinline__ void lin_copy2(T* d1, const T* s1, int n1, T* d2, con
       }
     }
   }
-  for (int e = a * V + lane; e < n1; e += 32) d1[e] = s1[e];
-  for (int e = b * V + lane; e < n2; e += 32) d2[e] = s2[e];
+  if (lane < r1) d1[a * V + lane] = t;
+  else if (lane >= 8 && lane - 8 < r2) d2[b * V + lane - 8] = t;
 }
 
 // One mark (problem, child slot, family, patch) for k_refresh.
@@ -328,6 +334,20 @@ static_assert(sizeof(LinChildren<double, PCBA_MAX_SHARED>) <= 256, "metadata are
 __device__ __forceinline__ void lin_split_f64(double x, float& hi, float& lo) {
   hi = __double2float_rn(x);
   lo = __double2float_rn(x - (double)hi);
+}
+
+// An upper bound of |x| 2^-52 (so of the rounding error of an FP64 sum
+// whose result is x) from x's exponent field alone, without an FP64
+// instruction: |x| < 2^(E - 1022) for the biased exponent E.  At most twice
+// |x| 2^-52 when that is above 2^-126, +inf for a non-finite x.
+__device__ __forceinline__ float lin_f64_ulp_bound(double x) {
+  const int fe = max(((__double2hiint(x) >> 20) & 0x7ff) - 947, 1);
+  return fe >= 255 ? INFINITY : __int_as_float(fe << 23);
+}
+
+// -x when neg, by the sign bit (no FP64 instruction).
+__device__ __forceinline__ double lin_neg_if(double x, bool neg) {
+  return __hiloint2double(__double2hiint(x) ^ (neg ? (int)0x80000000 : 0), __double2loint(x));
 }
 
 // The constant term kappa = c + sum_m w_m O_m of a constraint's coefficients
@@ -630,6 +650,13 @@ struct LinAcc {
     mxL = mxR = T(-INFINITY);
     am = T(0);
   }
+  __device__ __forceinline__ void merge(const LinAcc& o) {
+    mnL = min(mnL, o.mnL);
+    mxL = max(mxL, o.mxL);
+    mnR = min(mnR, o.mnR);
+    mxR = max(mxR, o.mxR);
+    am = max(am, o.am);
+  }
 };
 
 // One fibre (N + 1 values at src[j * sst], children to dL / dR at the same
@@ -663,9 +690,11 @@ __device__ __forceinline__ void lin_fibre(const T* src, T* dL, T* dR, int sst, L
 
 // NFIX > 0: every patch of the batch has degree NFIX along every axis (a
 // smaller kernel body); 0: any degree up to 16.
-// Resident blocks per SM the register allocation of the two kernels aims at.
+// Resident blocks per SM the register allocation of the two kernels aims at
+// (the split kernel's latency chains gain more from a third block's warps
+// than its few spills cost).
 #ifndef PCBA_LIN_SPLIT_BLOCKS
-#define PCBA_LIN_SPLIT_BLOCKS 2
+#define PCBA_LIN_SPLIT_BLOCKS 3
 #endif
 #ifndef PCBA_LIN_BOUND_BLOCKS
 #define PCBA_LIN_BOUND_BLOCKS 2
@@ -691,7 +720,9 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
   LinChildren<T, K>& ch = *reinterpret_cast<LinChildren<T, K>*>(ls.sCh);
   const unsigned items = E.plan->kr_units;
   const int par = E.plan->steps_global & 1;  // copy read this step; children go to par ^ 1
-  const double cost_thr = E.params->opt_tol * (1.0 / 64.0);
+  // an FP32 e exceeds opt_tol / 64 exactly when it exceeds this
+  const float cost_thr32 = __double2float_rd(E.params->opt_tol * (1.0 / 64.0));
+  const bool vtx = E.params->vertex != 0;
   int cx_p = -1, cx_K = 0, cx_r = 0, cx_ftop = 0, cx_hw = 0;
   unsigned cx_beg = 0, cx_end = 0;
   const ProbDesc* D = nullptr;
@@ -709,7 +740,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
     const unsigned uend = min(items, ubeg + bsz);
     for (unsigned u = ubeg; u < uend; ++u) {
       if (u < cx_beg || u >= cx_end || cx_p < 0) {
-        cx_p = find_problem(E.kr_pre, E.np, u);
+        cx_p = find_problem_warp(E.kr_pre, E.np, u, lane);
         cx_beg = E.kr_pre[cx_p];
         cx_end = E.kr_pre[cx_p + 1];
         D = E.desc + cx_p;
@@ -729,14 +760,18 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
       ChildRec* recL = E.rec + slot_off + k;
       ChildRec* recR = E.rec + slot_off + k + Kl;
       const int l = D->l, cp = D->cp, C = D->cg;
-      // shared patches only while a constraint is active in the item
-      const bool any = D->lin_chunks > 64 ||
-                       *((const unsigned long long*)(parent + D->off_sum) + par) != 0ull;
-      // ---- stage the parent (coalesced)
+      // the parent's box index along axis lane - 16 (read early: the
+      // children's are written with the cost records)
+      const unsigned ivw = lane >= 16 && lane < 16 + l ? ((const unsigned*)parent)[lane - 16] : 0u;
+      // ---- stage the parent (coalesced).  Every read of the parent is issued
+      // before the first use of one: its summary, header, the shared patches'
+      // metadata and the patches themselves (read whatever the summary says,
+      // unused when it is empty)
+      const unsigned long long psum0 =
+          D->lin_chunks <= 64 ? *((const unsigned long long*)(parent + D->off_sum) + par) : ~0ull;
       T* pc = (T*)(parent + D->off_cost);
       T* rc = (T*)(right + D->off_cost);
       const T* gs = (const T*)(parent + D->off_g + par * D->copy_g);
-      lin_copy2<T, 4>(sc, pc, cp, sp, gs, any ? 4 * C : 0, lane);
       char* pm = parent + D->off_eg + par * D->copy_e;
       double Oc = 0.0, Om[K];
       float ecost = 0.0f, em[K];
@@ -748,14 +783,15 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
       if constexpr (RIG) {
         Oc = *(const double*)(parent + 32);
         ecost = *(const float*)(parent + 40);
-        if (any) {
 #pragma unroll
-          for (int m = 0; m < K; ++m) {
-            em[m] = fabsf(LinMeta<T>::err(pm, 4)[m]);
-            Om[m] = LinMeta<T>::off(pm, 4)[m];
-          }
+        for (int m = 0; m < K; ++m) {
+          em[m] = fabsf(LinMeta<T>::err(pm, 4)[m]);
+          Om[m] = LinMeta<T>::off(pm, 4)[m];
         }
       }
+      lin_copy2<T, 4>(sc, pc, cp, sp, gs, 4 * C, lane);
+      // shared patches only while a constraint is active in the item
+      const bool any = psum0 != 0ull;
       __syncwarp();
       // ---- every fibre of the cost patch and of the shared patches, a lane each
       const int nc = D->P[r], stc = axis_stride(D->P, l, r), nfc = cp / (nc + 1);
@@ -766,27 +802,37 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
       LinAcc<T> acc[K + 1];
 #pragma unroll
       for (int g = 0; g <= K; ++g) acc[g].init();
+      // (one code path for every task: the fibre's extremes are merged into
+      // its group's accumulator afterwards)
       for (int task = lane; task < ntask; task += 32) {
+        int grp = 0, base, sst, n = nc;
+        const T* src = sc;
+        T *dL = scL, *dR = scR;
         if (task < nfc) {
           const int o = task / stc;
-          const int base = o * blkc + (task - o * stc);
-          dispatch_fixed<16, NFIX>(nc, [&](auto c) {
-            lin_fibre<T, decltype(c)::value>(sc + base, scL + base, scR + base, stc, acc[0]);
-          });
+          base = o * blkc + (task - o * stc);
+          sst = stc;
         } else {
           const int t2 = task - nfc;
           const int m = t2 / nfs;
           const int f = t2 - m * nfs;
           const int o = f / sts;
-          const int base = (o * blks + (f - o * sts)) * 4;
-          dispatch_fixed<16, NFIX>(ns, [&](auto c) {
-#pragma unroll
-            for (int g = 0; g < K; ++g)
-              if (g == m)
-                lin_fibre<T, decltype(c)::value>(sp + base + g, spL + base + g, spR + base + g,
-                                                 4 * sts, acc[1 + g]);
-          });
+          base = (o * blks + (f - o * sts)) * 4 + m;
+          sst = 4 * sts;
+          grp = 1 + m;
+          n = ns;
+          src = sp;
+          dL = spL;
+          dR = spR;
         }
+        LinAcc<T> t;
+        t.init();
+        dispatch_fixed<16, NFIX>(n, [&](auto c) {
+          lin_fibre<T, decltype(c)::value>(src + base, dL + base, dR + base, sst, t);
+        });
+#pragma unroll
+        for (int g = 0; g <= K; ++g)
+          if (g == grp) acc[g].merge(t);
       }
       // ---- extremes per patch group, over the warp
 #pragma unroll
@@ -800,8 +846,9 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
       __syncwarp();
       // ---- cost children: re-centred on the middle of each child's range
       // (FP32), error bound grown by n (max |parent| 2^-24 + 2^-149) for the
-      // triangle and by max |stored| 2^-24 + 2^-149 + |O'| 2^-52 for the
-      // re-centring; the bounds go to the child records
+      // triangle and by max |stored| 2^-24 + 2^-149 + 2^-52 |O'| (rounded up
+      // to a power of two) for the re-centring; the bounds go to the child
+      // records
       T shc[2] = {T(0), T(0)};
       if constexpr (RIG) {
         shc[0] = __fmul_rn(__fadd_rn(acc[0].mnL, acc[0].mxL), 0.5f);
@@ -811,56 +858,62 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
         pc[j] = addrn(scL[j], -shc[0]);
         rc[j] = addrn(scR[j], -shc[1]);
       }
-      // the cost records (lane c for child c) and the box and slot map (lane 2)
-      if (lane < 2) {
-        const int c = lane;
+      // the cost records, lane 2 v + c for child c and value v: 0 the lower
+      // bound, 1 the upper bound, 2 + q the cost at corner q (vertex
+      // incumbents).  Every lane forms the child's offset and error bound,
+      // then one upward FP64 sum with them (the lower bound is the negated
+      // sum of the negated terms), so the warp issues each FP64 instruction
+      // of the records once.  Lane 16 + s: the children's box index along
+      // axis s, and (s = 0) the right child's slot.
+      if (lane < 12) {
+        const int c = lane & 1, v = lane >> 1;
         const T cmn = c ? acc[0].mnR : acc[0].mnL, cmx = c ? acc[0].mxR : acc[0].mxL;
+        const T* st = c ? scR : scL;
         ChildRec* rec = c ? recR : recL;
         if constexpr (RIG) {
-          const float e1 = __fadd_ru(__fadd_ru(ecost, __fmul_ru(acc[0].am, (float)nc * u24)),
-                                     (float)nc * 0x1p-149f);
-          const float sh = c ? shc[1] : shc[0];
-          const float smin = __fsub_rn(cmn, sh);
-          const float smax = __fsub_rn(cmx, sh);
-          const float Mr = fmaxf(fabsf(smin), fabsf(smax));
-          const double On = Oc + (double)sh;
-          const float e2 = __fadd_ru(__fadd_ru(__fadd_ru(e1, __fmul_ru(Mr, u24)), 0x1p-149f),
-                                     __double2float_ru(__dmul_ru(fabs(On), 0x1p-52)));
-          char* it = c ? right : parent;
-          *(double*)(it + 32) = On;
-          *(float*)(it + 40) = e2;
-          rec->pmin = okey(__dsub_rd(__dadd_rd(On, (double)smin), (double)e2));
-          rec->pmax = okey(__dadd_ru(__dadd_ru(On, (double)smax), (double)e2));
-          rec->perr = __float_as_uint(e2);
-          if ((double)e2 > cost_thr) lin_mark(E, par, p, c ? k + Kl : k, 2, 0);
-          if (E.params->vertex) {
-            // the cost at the child's corners: offset + stored value + e_p
-            const T* st = c ? scR : scL;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const float rq = __fsub_rn(st[corner_index(D->P, l, q)], sh);
-              rec->vtxc[q] =
-                  __double2float_ru(__dadd_ru(__dadd_ru(On, (double)rq), (double)e2));
+          if (v < (vtx ? 6 : 2)) {
+            const float e1 = __fadd_ru(__fadd_ru(ecost, __fmul_ru(acc[0].am, (float)nc * u24)),
+                                       (float)nc * 0x1p-149f);
+            const float sh = c ? shc[1] : shc[0];
+            const float smin = __fsub_rn(cmn, sh);
+            const float smax = __fsub_rn(cmx, sh);
+            const float Mr = fmaxf(fabsf(smin), fabsf(smax));
+            const double On = Oc + (double)sh;
+            const float e2 = __fadd_ru(__fadd_ru(__fadd_ru(e1, __fmul_ru(Mr, u24)), 0x1p-149f),
+                                       lin_f64_ulp_bound(On));
+            // the stored value at corner v - 2 is exactly the re-centred
+            // child coefficient written above
+            const float b = v == 0 ? __fsub_ru(e2, smin)
+                            : v == 1 ? __fadd_ru(smax, e2)
+                                     : __fadd_ru(__fsub_rn(st[corner_index(D->P, l, v - 2)], sh), e2);
+            const double y = __dadd_ru(lin_neg_if(On, v == 0), (double)b);
+            if (v == 0) {
+              rec->pmin = okey(lin_neg_if(y, true));
+            } else if (v == 1) {
+              char* it = c ? right : parent;
+              *(double*)(it + 32) = On;
+              *(float*)(it + 40) = e2;
+              rec->pmax = okey(y);
+              rec->perr = __float_as_uint(e2);
+              if (e2 > cost_thr32) lin_mark(E, par, p, c ? k + Kl : k, 2, 0);
+            } else {
+              rec->vtxc[v - 2] = __double2float_ru(y);
             }
           }
-        } else {
+        } else if (v == 0) {
           rec->pmin = okey((double)cmn);
           rec->pmax = okey((double)cmx);
-          if (E.params->vertex) {
-            const T* st = c ? scR : scL;
+          if (vtx) {
 #pragma unroll
             for (int q = 0; q < 4; ++q)
               rec->vtxc[q] = __double2float_ru((double)st[corner_index(D->P, l, q)]);
           }
         }
-      } else if (lane == 2) {
-        E.map[slot_off + k + Kl] = rslot;
-        unsigned* iL = (unsigned*)parent;
-        unsigned* iR = (unsigned*)right;
-        for (int s = 0; s < l; ++s) iR[s] = iL[s];
-        const unsigned v = iL[r];
-        iL[r] = 2u * v;
-        iR[r] = 2u * v + 1u;
+      } else if (lane >= 16 && lane < 16 + l) {
+        const int s = lane - 16;
+        ((unsigned*)right)[s] = s == r ? 2u * ivw + 1u : ivw;
+        if (s == r) ((unsigned*)parent)[s] = 2u * ivw;
+        if (s == 0) E.map[slot_off + k + Kl] = rslot;
       }
       // ---- shared children, re-centred likewise, to the other copy, with
       // their metadata (error bound, offset, extremes of the stored values)
@@ -925,7 +978,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
               vO = omv + (double)shv;
               lin_split_f64(vO, vOh, vOl);
               vec = __fadd_ru(__fadd_ru(__fadd_ru(e1, __fmul_ru(vM, u24)), 0x1p-149f),
-                              __double2float_ru(__dmul_ru(fabs(vO), 0x1p-52)));
+                              lin_f64_ulp_bound(vO));
               vmn = T(smin);
               vmx = T(smax);
             }
@@ -962,8 +1015,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
       {
         const int chunks = D->lin_chunks, mwords = D->mwords;
         const bool summ = chunks <= 64;  // (more chunks keep no summaries: all are read)
-        const unsigned long long psum =
-            summ ? *((const unsigned long long*)(parent + D->off_sum) + par) : 0ull;
+        const unsigned long long psum = summ ? psum0 : 0ull;
         if (lane == 0 && summ) {
           *((unsigned long long*)(parent + D->off_sum) + (par ^ 1)) = 0ull;
           *((unsigned long long*)(right + D->off_sum) + (par ^ 1)) = 0ull;
@@ -1065,7 +1117,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
           qb = __shfl_sync(0xffffffffu, qb, 0);
           for (int i2 = lane; i2 < nq; i2 += 32) {
             const unsigned q = qb + (unsigned)i2;
-            if (q < E.lin_qcap) E.lin_queue[q] = make_uint2(u, ls.sWin[i2]);
+            if (q < E.lin_qcap) E.lin_queue[q] = make_uint4(u, ls.sWin[i2], (unsigned)p, (unsigned)k);
           }
           mode = 2;
         }
@@ -1075,7 +1127,8 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
           qb = __shfl_sync(0xffffffffu, qb, 0);
           for (int t = lane; t < chunks; t += 32)
             if (qb + (unsigned)t < E.lin_qcap)
-              E.lin_queue[qb + (unsigned)t] = make_uint2(u, (unsigned)t | (1u << 16));
+              E.lin_queue[qb + (unsigned)t] =
+                  make_uint4(u, (unsigned)t | (1u << 16), (unsigned)p, (unsigned)k);
           mode = 3;
         }
         for (int i2 = 0; mode != 0; ++i2) {
@@ -1102,7 +1155,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
   }
 }
 
-// Heavy items' live chunks, queued by k2_lin_split as (item, chunk): the
+// Heavy items' live chunks, queued by k2_lin_split as (item, window): the
 // children are staged from memory.
 template <typename T, int K>
 __global__ void __launch_bounds__(256, PCBA_LIN_BOUND_BLOCKS) k2_lin_bound(Engine E, int cgmax) {
@@ -1128,14 +1181,14 @@ __global__ void __launch_bounds__(256, PCBA_LIN_BOUND_BLOCKS) k2_lin_bound(Engin
     if (ubeg >= units) break;
     const unsigned uend = min(units, ubeg + bsz);
     for (unsigned q = ubeg; q < uend; ++q) {
-      const uint2 ent = E.lin_queue[q];
+      const uint4 ent = E.lin_queue[q];  // (item, window, problem, index in the list)
       // an item's windows are queued one after another: the next window of
       // the same item reuses the staged children
       if (ent.x != cur) {
         cur = ent.x;
-        p = find_problem(E.kr_pre, E.np, ent.x);
+        p = (int)ent.z;
         D = E.desc + p;
-        k = (int)(ent.x - E.kr_pre[p]);
+        k = (int)ent.w;
         Kl = E.state[p].K;
         char* list = E.arena + D->list_off;
         left = list + (size_t)E.map[D->slot_off + k] * D->item_bytes;
