@@ -638,7 +638,7 @@ __device__ __forceinline__ void pup_phase(const Engine& E) {
   const unsigned tiles_total = E.plan->k3_tiles;
   const unsigned long long k_eq = okey(E.params->eq_tol);
   for (unsigned u = blockIdx.x; u < tiles_total; u += gridDim.x) {
-    const int p = find_problem(E.k3_pre, E.np, u);
+    const int p = find_problem_warp(E.k3_pre, E.np, u, threadIdx.x & 31);
     const ProbDesc* D = E.desc + p;
     ProbState* S = E.state + p;
     const int twoK = 2 * S->K;
@@ -897,7 +897,7 @@ __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan,
   const unsigned tiles_total = E.plan->k3_tiles;
   const unsigned long long k_eq = okey(E.params->eq_tol);
   for (unsigned u = blockIdx.x; u < tiles_total; u += gridDim.x) {
-    const int p = find_problem(E.k3_pre, E.np, u);
+    const int p = find_problem_warp(E.k3_pre, E.np, u, threadIdx.x & 31);
     const int tile = (int)(u - E.k3_pre[p]);
     const ProbDesc* D = E.desc + p;
     ProbState* S = E.state + p;
@@ -970,7 +970,7 @@ __global__ void __launch_bounds__(PCBA_TPB) k3_classify(Engine E) {
 __device__ __forceinline__ void index_phase(const Engine& E) {
   const unsigned tiles_total = E.plan->k3_tiles;
   for (unsigned u = blockIdx.x; u < tiles_total; u += gridDim.x) {
-    const int p = find_problem(E.k3_pre, E.np, u);
+    const int p = find_problem_warp(E.k3_pre, E.np, u, threadIdx.x & 31);
     const ProbState* S = E.state + p;
     // a problem that stops at this step (MEMCAP, MAXITER) is still compacted
     // (its list is returned); only running problems recycle slots
@@ -999,9 +999,20 @@ __global__ void __launch_bounds__(PCBA_TPB) k4_index(Engine E) { index_phase(E);
 // save position K_save-1-j (reading R11); one thread per hole.
 __device__ __forceinline__ void move_phase(const Engine& E) {
   const unsigned units = E.plan->k4_units;
-  for (unsigned u = blockIdx.x * blockDim.x + threadIdx.x; u < units;
-       u += gridDim.x * blockDim.x) {
-    const int p = find_problem(E.k4_pre, E.np, u);
+  const int lane = threadIdx.x & 31;
+  // a warp's 32 consecutive units: its first unit's problem by a warp
+  // search, and only when the units reach past that problem a second one
+  // for the last unit and a per-lane search between the two
+  for (unsigned base = blockIdx.x * blockDim.x + (threadIdx.x - lane); base < units;
+       base += gridDim.x * blockDim.x) {
+    const unsigned u = base + lane, ulast = min(units - 1u, base + 31u);
+    const int p0 = find_problem_warp(E.k4_pre, E.np, base, lane);
+    int p = p0;
+    if (__ldg(E.k4_pre + p0 + 1) <= ulast) {
+      const int p1 = find_problem_warp(E.k4_pre, E.np, ulast, lane);
+      if (u < units) p = p0 + find_problem(E.k4_pre + p0, p1 - p0 + 1, u);
+    }
+    if (u >= units) continue;
     const ProbDesc* D = E.desc + p;
     const unsigned j = u - E.k4_pre[p];
     const unsigned h = E.hole[D->slot_off + j];
