@@ -146,7 +146,7 @@ struct Grids {
   size_t k1_smem = 0;
   int k3_grid = 1, k4_grid = 1;
   // FP32 refresh kernel
-  int kr_grid = 1, kr_wpb = 4, kr_cmax = 1, kr_lmax = 1;
+  int kr_grid = 1, kr_cmax = 1, kr_lmax = 1;
   size_t kr_smem = 0;
 };
 
@@ -407,7 +407,7 @@ int launch_after_k2(pcba_batch* b, cudaStream_t s, int use_graph) {
   if (fp32) {
     PCBA_CK(cudaEventRecord(b->ev_fork, s));
     PCBA_CK(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
-    k_refresh<<<g.kr_grid, 32 * g.kr_wpb, g.kr_smem, b->side>>>(b->E, g.kr_cmax, g.kr_lmax);
+    k_refresh<<<g.kr_grid, PCBA_KRB, g.kr_smem, b->side>>>(b->E, g.kr_cmax, g.kr_lmax);
     PCBA_CK(cudaEventRecord(b->ev_join, b->side));
   }
   k_pup<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
@@ -456,28 +456,24 @@ int setup_kernels(pcba_batch* b) {
                                   : pcba_k2_prepare_f64(g.k2, b->desc, b->lin != 0, g.sms, smem_optin);
     if (rc) return rc;
   }
-  // FP32 refresh: per warp 4 patch buffers of the largest patch and the
-  // per-axis matrices; warps per block limited by shared memory
+  // FP32 refresh: a block per marked item, 4 patch buffers of the largest
+  // patch (all shared patches of a linear-family item) and the per-axis
+  // matrices in its shared memory
   if (sizeof(T) == 4) {
     g.kr_lmax = b->max_l;
-    // (a linear-family item's shared patches are refreshed together)
     long long krc = cmax;
     for (const ProbDesc& d : b->desc)
       if (d.lin) krc = std::max<long long>(krc, (long long)d.alpha * d.cg);
     g.kr_cmax = (int)krc;
-    auto need = [&](int wpb, long long c) {
-      return (size_t)wpb * (size_t)(4 * c + 2 * 289 * g.kr_lmax + PCBA_KR_SCRATCH) * sizeof(double);
+    auto need = [&](long long c) {
+      return refresh_smem_doubles((int)c, g.kr_lmax) * sizeof(double);
     };
-    g.kr_wpb = 4;
-    while (g.kr_wpb > 1 && need(g.kr_wpb, g.kr_cmax) > (size_t)smem_optin - 4096) g.kr_wpb /= 2;
-    while (g.kr_cmax > 1 && need(g.kr_wpb, g.kr_cmax) > (size_t)smem_optin - 4096) g.kr_cmax /= 2;
-    g.kr_smem = need(g.kr_wpb, g.kr_cmax);
+    while (g.kr_cmax > 1 && need(g.kr_cmax) > (size_t)smem_optin - 4096) g.kr_cmax /= 2;
+    g.kr_smem = need(g.kr_cmax);
     PCBA_CK(cudaFuncSetAttribute(k_refresh, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)g.kr_smem));
-    PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_refresh, 32 * g.kr_wpb,
-                                                          g.kr_smem));
-    // marks are tens to thousands per step, each a chain of FP64 work: as
-    // many resident blocks as fit (at most 4 per SM) to hide its latency
+    PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_refresh, PCBA_KRB, g.kr_smem));
+    // marks are tens to thousands per step: up to 4 resident blocks per SM
     g.kr_grid = std::max(1, std::min(occ, 4)) * g.sms;
     double binom[17 * 17], binom_inv[17 * 17];
     for (int n = 0; n < 17; ++n)

@@ -256,147 +256,165 @@ __global__ void __launch_bounds__(128) k1_convert(Engine E, const double* mat, i
 // k_move_control updates the slot map; the child boxes come from the state snapshot
 // child_level, which those kernels do not change.
 //
-// One warp per marked patch; the per-axis matrices of the item's box are
-// built in the warp's shared memory.
+// One block of PCBA_KRB threads per marked item: the per-axis matrices of the
+// item's box and the conversion are spread over the block's warps, which sit
+// on different SM partitions, so that the FP64 work of one mark runs on
+// several FP64 units at once (an FP64 instruction occupies its partition's
+// unit for many cycles, whatever the other warps do).
+#define PCBA_KRB 128
+
 // Binomial coefficients C(n, k), n, k <= 16 (exact integers), and their
 // rounded reciprocals, filled once by the library at start-up.
 __constant__ double c_binom[17 * 17];
 __constant__ double c_binom_inv[17 * 17];
 
-// Doubles of per-warp scratch of refresh_matrices: the factors U and V
-// ([17][17] each) and the powers lo^e, w^e ([17] each).
-#define PCBA_KR_SCRATCH (2 * 289 + 2 * 17)
+// Doubles of per-axis scratch of refresh_matrices: the factors U and V
+// ([17][17] each), the powers lo^e and w^e ([17] each), and U and V as
+// FP32 absolute values rounded up ([17][17] each, one double of space per
+// two floats).
+#define PCBA_KR_SCRATCH (2 * 289 + 2 * 17 + 289)
+
+// The mode products' axis r and in-axis index of flat item t over the axes'
+// (n_r + 1)^2 grids (sq) or (n_r + 1) ranges.
+__device__ __forceinline__ int refresh_axis(const int* deg, int l, bool sq, int& t) {
+  int r = 0;
+  for (; r < l - 1; ++r) {
+    const int m = sq ? (deg[r] + 1) * (deg[r] + 1) : deg[r] + 1;
+    if (t < m) break;
+    t -= m;
+  }
+  return r;
+}
 
 // T_r[i][j] = sum_k C(i,k) C(j,k) / C(n,k) lo^(j-k) w^k (power basis on the
 // box -> Bernstein basis), formed as sum_k U[i][k] V[j][k] with U[i][k] =
 // C(i,k) / C(n,k) w^k and V[j][k] = C(j,k) lo^(j-k) (each factor computed
-// once, the powers by lane e with e products), and A_r its absolute-value sum
-// widened by 2^-40, which covers the roundings of every term (at most
-// (j + n + 5) 2^-53 relative, the reciprocal and the sum included), stored
-// as floats rounded up (the 289 floats after T_r's 289 doubles).  scr is the
-// warp's PCBA_KR_SCRATCH doubles.
+// once, a power with at most e - 1 products by repeated squaring), for every
+// axis at once; A_r bounds the absolute-value sum sum_k |U[i][k]| |V[j][k]|
+// from above in FP32 (factors and products rounded up, then widened by
+// 2^-20, which covers the FP64 roundings of U and V), stored as the 289
+// floats after T_r's 289 doubles.  scr: l x PCBA_KR_SCRATCH doubles; box:
+// lo[0..l-1], then hi[0..l-1].  Whole block.
 __device__ __forceinline__ void refresh_matrices(const double* binom, int l, const int* deg,
-                                                 const double* blo, const double* bhi,
-                                                 double* sT, double* scr, int lane) {
-  double* U = scr;
-  double* V = scr + 289;
-  double* lp = scr + 578;
-  double* wp = lp + 17;
+                                                 const double* box, double* sT, double* scr) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  int n1 = 0, n2 = 0;
   for (int r = 0; r < l; ++r) {
-    const int n = deg[r];
-    const double lo = blo[r], w = bhi[r] - blo[r];
-    if (lane <= n) {
-      double a = 1.0, b = 1.0;
-      for (int e = 0; e < lane; ++e) {
-        a *= lo;
-        b *= w;
+    n1 += deg[r] + 1;
+    n2 += (deg[r] + 1) * (deg[r] + 1);
+  }
+  for (int t0 = tid; t0 < n1; t0 += nt) {
+    int e = t0;
+    const int r = refresh_axis(deg, l, false, e);
+    double xa = box[r], xb = box[l + r] - box[r], a = 1.0, b = 1.0;
+    for (int k = e; k > 0;) {
+      if (k & 1) {
+        a *= xa;
+        b *= xb;
       }
-      lp[lane] = a;
-      wp[lane] = b;
+      k >>= 1;
+      if (k) {
+        xa *= xa;
+        xb *= xb;
+      }
     }
-    __syncwarp();
-    // U and V over the pairs k <= i (k <= j) of a (n+1) x (n+1) grid
-    for (int e = lane; e < (n + 1) * (n + 1); e += 32) {
-      const int i = e / (n + 1), k = e - (e / (n + 1)) * (n + 1);
-      if (k > i) continue;
-      U[i * 17 + k] = binom[i * 17 + k] * c_binom_inv[n * 17 + k] * wp[k];
-      V[i * 17 + k] = binom[i * 17 + k] * lp[i - k];
+    double* s = scr + r * PCBA_KR_SCRATCH;
+    s[578 + e] = a;
+    s[595 + e] = b;
+  }
+  __syncthreads();
+  for (int t0 = tid; t0 < n2; t0 += nt) {
+    int e = t0;
+    const int r = refresh_axis(deg, l, true, e);
+    const int n = deg[r], i = e / (n + 1), k = e - i * (n + 1);
+    if (k > i) continue;
+    double* s = scr + r * PCBA_KR_SCRATCH;
+    float* f = (float*)(s + 612);
+    const double u = binom[i * 17 + k] * c_binom_inv[n * 17 + k] * s[595 + k];
+    const double v = binom[i * 17 + k] * s[578 + i - k];
+    s[i * 17 + k] = u;
+    s[289 + i * 17 + k] = v;
+    f[i * 17 + k] = __double2float_ru(fabs(u));
+    f[289 + i * 17 + k] = __double2float_ru(fabs(v));
+  }
+  __syncthreads();
+  for (int t0 = tid; t0 < n2; t0 += nt) {
+    int e = t0;
+    const int r = refresh_axis(deg, l, true, e);
+    const int n = deg[r], i = e / (n + 1), j = e - i * (n + 1);
+    const double* s = scr + r * PCBA_KR_SCRATCH;
+    const float* f = (const float*)(s + 612);
+    double t = 0.0;
+    float ta = 0.0f;
+    const int kmax = i < j ? i : j;
+    for (int k = 0; k <= kmax; ++k) {
+      t = fma(s[i * 17 + k], s[289 + j * 17 + k], t);
+      ta = __fmaf_ru(f[i * 17 + k], f[289 + j * 17 + k], ta);
     }
-    __syncwarp();
     double* T = sT + r * 578;
-    float* A = (float*)(T + 289);
-    for (int e = lane; e < (n + 1) * (n + 1); e += 32) {
-      const int i = e / (n + 1), j = e - (e / (n + 1)) * (n + 1);
-      double t = 0.0, ta = 0.0;
-      const int kmax = i < j ? i : j;
-      for (int k = 0; k <= kmax; ++k) {
-        const double u = U[i * 17 + k], v = V[j * 17 + k];
-        t = fma(u, v, t);
-        ta = fma(fabs(u), fabs(v), ta);
-      }
-      T[e] = t;
-      A[e] = __double2float_ru(ta * (1.0 + 0x1p-40));
-    }
-    __syncwarp();  // the next axis reuses U, V and the powers
+    T[e] = t;
+    ((float*)(T + 289))[e] = __fmul_ru(ta, 1.0f + 0x1p-20f);
   }
+  __syncthreads();
 }
 
-// Warp-cooperative conversion of one monomial tensor a (C coefficients,
-// multi-degree deg) with the matrices in sT; result in *sA, bound base in *sX.
-// The bound base (|A_1| x ... x |A_l|) |a| is carried in FP32 with every
-// input and every fused multiply-add rounded up, so it stays an upper bound
-// of the exact product and costs no FP64 operations (a value beyond the FP32
-// range gives an infinite bound: the patch is then never decided on).
-__device__ __forceinline__ double refresh_convert(const double* a, int C, int l, const int* deg,
-                                                  const double* sT, double*& sA, double*& sB,
-                                                  float*& sX, float*& sY, int lane) {
-  for (int j = lane; j < C; j += 32) {
-    const double v = a[j];
-    sA[j] = v;
-    sX[j] = __double2float_ru(fabs(v));
-  }
-  __syncwarp();
-  double gterms = 0.0;
-  for (int r = 0; r < l; ++r) {
-    const int n = deg[r];
-    int stride = 1;
-    for (int q = r + 1; q < l; ++q) stride *= deg[q] + 1;
-    const double* T = sT + r * 578;
-    const float* A = (const float*)(T + 289);
-    gterms += 4.0 * n + 8.0;
-    const int blk = (n + 1) * stride;
-    for (int o = lane; o < C; o += 32) {
-      const int hp = o / blk;
-      const int rem = o - hp * blk;
-      const int i = rem / stride;
-      const int in = rem - i * stride;
-      const double* src = sA + hp * blk + in;
-      const float* srcx = sX + hp * blk + in;
-      double s = 0.0;
-      float sx = 0.0f;
-      for (int j = 0; j <= n; ++j) {
-        s = fma(T[i * (n + 1) + j], src[j * stride], s);
-        sx = __fmaf_ru(A[i * (n + 1) + j], srcx[j * stride], sx);
-      }
-      sB[o] = s;
-      sY[o] = sx;
+// Minimum or maximum of NV values over the block, in every thread; red holds
+// NV x (warps per block) floats.
+template <int NV, bool MAX>
+__device__ __forceinline__ void refresh_block_reduce(float (&v)[NV], float* red) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NV; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const float y = __shfl_xor_sync(0xffffffffu, v[q], o);
+      v[q] = MAX ? fmaxf(v[q], y) : fminf(v[q], y);
     }
-    __syncwarp();
-    double* t = sA; sA = sB; sB = t;
-    float* tf = sX; sX = sY; sY = tf;
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < NV; ++q) red[w * NV + q] = v[q];
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < NV; ++q) {
+    float x = red[q];
+    for (int i = 1; i < nw; ++i) x = MAX ? fmaxf(x, red[i * NV + q]) : fminf(x, red[i * NV + q]);
+    v[q] = x;
   }
-  float amax = 0.0f;
-  for (int j = lane; j < C; j += 32) amax = fmaxf(amax, sX[j]);
-  for (int o = 16; o > 0; o >>= 1) amax = fmaxf(amax, __shfl_xor_sync(0xffffffffu, amax, o));
-  return __dmul_ru(__dmul_ru(2.0 * gterms, 0x1p-53), (double)amax);
+  __syncthreads();
 }
 
-// refresh_convert for the nf (<= PCBA_MAX_SHARED) patches a[g C + j] of one
-// multi-degree at once: every pass runs over all nf C coefficients, so the
-// patches' FP64 dependency chains overlap, and each output is summed in two
-// partial sums (at most n + 1 roundings on any path, as a single chain).
-// err[g] receives patch g's bound (in every lane).
-__device__ __forceinline__ void refresh_convert_multi(const double* a, int nf, int C, int l,
-                                                      const int* deg, const double* sT,
-                                                      double*& sA, double*& sB, float*& sX,
-                                                      float*& sY, int lane, double* err) {
+// Conversion of the nf (<= PCBA_MAX_SHARED) monomial tensors a[g C + j] of
+// one multi-degree with the matrices in sT (l mode products, every pass over
+// all nf C coefficients, each output summed in two partial sums: at most
+// n + 1 roundings on any path, as a single chain); result in *sA.  The bound
+// base (|A_1| x ... x |A_l|) |a| is carried in FP32 with every input and
+// every fused multiply-add rounded up, so it stays an upper bound of the
+// exact product and costs no FP64 operations (a value beyond the FP32 range
+// gives an infinite bound: the patch is then never decided on).  err[g]
+// receives patch g's conversion bound, rounded up (every thread).  Whole block; red:
+// PCBA_MAX_SHARED x warps floats.
+__device__ __forceinline__ void refresh_convert(const double* a, int nf, int C, int l,
+                                                const int* deg, const double* sT, double*& sA,
+                                                double*& sB, float*& sX, float*& sY, float* red,
+                                                float* err) {
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int N = nf * C;
-  for (int j = lane; j < N; j += 32) {
+  for (int j = tid; j < N; j += nt) {
     const double v = a[j];
     sA[j] = v;
     sX[j] = __double2float_ru(fabs(v));
   }
-  __syncwarp();
-  double gterms = 0.0;
+  __syncthreads();
+  int gterms = 0;
   for (int r = 0; r < l; ++r) {
     const int n = deg[r];
     int stride = 1;
     for (int q = r + 1; q < l; ++q) stride *= deg[q] + 1;
     const double* T = sT + r * 578;
     const float* A = (const float*)(T + 289);
-    gterms += 4.0 * n + 8.0;
+    gterms += 4 * n + 8;
     const int blk = (n + 1) * stride;
-    for (int o2 = lane; o2 < N; o2 += 32) {
+    for (int o2 = tid; o2 < N; o2 += nt) {
       const int g = o2 / C;
       const int o = o2 - g * C;
       const int hp = o / blk;
@@ -423,199 +441,181 @@ __device__ __forceinline__ void refresh_convert_multi(const double* a, int nf, i
       sB[o2] = s0 + s1;
       sY[o2] = __fadd_ru(x0, x1);
     }
-    __syncwarp();
+    __syncthreads();
     double* t = sA; sA = sB; sB = t;
     float* tf = sX; sX = sY; sY = tf;
   }
   float am[PCBA_MAX_SHARED] = {0.0f, 0.0f, 0.0f, 0.0f};
-  for (int j = lane; j < N; j += 32) {
+  for (int j = tid; j < N; j += nt) {
     const int g = j / C;
 #pragma unroll
     for (int q = 0; q < PCBA_MAX_SHARED; ++q)
       if (q == g) am[q] = fmaxf(am[q], sX[j]);
   }
+  refresh_block_reduce<PCBA_MAX_SHARED, true>(am, red);
+  // 2 gterms 2^-53 am, rounded up in FP32 (2 gterms < 2^11: the scale is exact)
 #pragma unroll
-  for (int q = 0; q < PCBA_MAX_SHARED; ++q) {
-    for (int o = 16; o > 0; o >>= 1) am[q] = fmaxf(am[q], __shfl_xor_sync(0xffffffffu, am[q], o));
-    err[q] = __dmul_ru(__dmul_ru(2.0 * gterms, 0x1p-53), (double)am[q]);
-  }
+  for (int q = 0; q < PCBA_MAX_SHARED; ++q)
+    err[q] = __fmul_ru((float)(2 * gterms) * 0x1p-53f, am[q]);
 }
 
-// Stores the nf converted patches of refresh_convert_multi (sA, C each),
-// each re-centred on the middle of its range, as FP32 values at
-// block[j * pad + g], with offset and error bound (err64[g] added) in the
-// FP32 metadata earr of a linear-family item.
-__device__ __forceinline__ void refresh_store_multi(const double* sA, int nf, int C,
-                                                    const double* err64, float* block, size_t pad,
-                                                    float* earr, size_t apad, int lane) {
+// An upper bound of |x| 2^-52 (at least the rounding error of an FP64 sum
+// whose result is x) from x's exponent field alone, without an FP64
+// instruction: |x| < 2^(E - 1022) for the biased exponent E.  At most twice
+// |x| 2^-52 above 2^-126, +inf for a non-finite x.
+__device__ __forceinline__ float refresh_ulp_bound(double x) {
+  const int fe = max(((__double2hiint(x) >> 20) & 0x7ff) - 947, 1);
+  return fe >= 255 ? INFINITY : __int_as_float(fe << 23);
+}
+
+// Stores the nf converted patches (sA, C each), each re-centred on an FP32
+// offset O_g near the middle of its range, as FP32 values at
+// dst[(j - g C) * pad + g]: stored = RN(b - O) with b - O formed in FP64 (error
+// at most |b - O| 2^-53), so the bound is |stored - (b - O)| + |b - O| 2^-52
+// (each rounded up), maximised over the patch, plus err[g].  Patch g's bound
+// goes to eout[g], its offset to o64[g] (FP64) or, when o64 is null, o32[g].  The range
+// is found in FP32 (any offset is valid; the middle only keeps the stored
+// values small); a patch whose values leave the FP32 range takes its offset
+// from an FP64 pass of one thread.  Whole block; red: 2 PCBA_MAX_SHARED x
+// warps floats, sO: PCBA_MAX_SHARED doubles.
+__device__ __forceinline__ void refresh_store(const double* sA, int nf, int C, const float* err,
+                                              float* dst, size_t pad, float* eout, double* o64,
+                                              float* o32, float* red, double* sO) {
+  const int tid = threadIdx.x, nt = blockDim.x;
   const int N = nf * C;
-  double bmin[PCBA_MAX_SHARED], bmax[PCBA_MAX_SHARED], O[PCBA_MAX_SHARED], em[PCBA_MAX_SHARED];
+  float mn[PCBA_MAX_SHARED], mx[PCBA_MAX_SHARED];
 #pragma unroll
   for (int q = 0; q < PCBA_MAX_SHARED; ++q) {
-    bmin[q] = INFINITY;
-    bmax[q] = -INFINITY;
-    em[q] = 0.0;
+    mn[q] = INFINITY;
+    mx[q] = -INFINITY;
   }
-  for (int j = lane; j < N; j += 32) {
+  for (int j = tid; j < N; j += nt) {
     const int g = j / C;
-    const double v = sA[j];
+    const float v = __double2float_rn(sA[j]);
 #pragma unroll
     for (int q = 0; q < PCBA_MAX_SHARED; ++q)
       if (q == g) {
-        bmin[q] = fmin(bmin[q], v);
-        bmax[q] = fmax(bmax[q], v);
+        mn[q] = fminf(mn[q], v);
+        mx[q] = fmaxf(mx[q], v);
       }
   }
+  refresh_block_reduce<PCBA_MAX_SHARED, false>(mn, red);
+  refresh_block_reduce<PCBA_MAX_SHARED, true>(mx, red + PCBA_MAX_SHARED * (nt >> 5));
+  if (tid < nf) {
+    float o = 0.0f;
 #pragma unroll
-  for (int q = 0; q < PCBA_MAX_SHARED; ++q) {
-    for (int o = 16; o > 0; o >>= 1) {
-      bmin[q] = fmin(bmin[q], __shfl_xor_sync(0xffffffffu, bmin[q], o));
-      bmax[q] = fmax(bmax[q], __shfl_xor_sync(0xffffffffu, bmax[q], o));
+    for (int q = 0; q < PCBA_MAX_SHARED; ++q)
+      if (q == tid) o = 0.5f * mn[q] + 0.5f * mx[q];
+    if (!isfinite(o)) {
+      double lo = INFINITY, hi = -INFINITY;
+      for (int j = tid * C; j < (tid + 1) * C; ++j) {
+        lo = fmin(lo, sA[j]);
+        hi = fmax(hi, sA[j]);
+      }
+      o = __double2float_rn(0.5 * lo + 0.5 * hi);
+      if (!isfinite(o)) o = 0.0f;
     }
-    O[q] = 0.5 * (bmin[q] + bmax[q]);
+    sO[tid] = (double)o;
   }
-  for (int j = lane; j < N; j += 32) {
+  __syncthreads();
+  float em[PCBA_MAX_SHARED] = {0.0f, 0.0f, 0.0f, 0.0f};
+  for (int j = tid; j < N; j += nt) {
     const int g = j / C;
-    double Og = 0.0;
-#pragma unroll
-    for (int q = 0; q < PCBA_MAX_SHARED; ++q)
-      if (q == g) Og = O[q];
-    const double d = sA[j] - Og;  // |d - (b - O)| <= |d| 2^-53
+    const double d = sA[j] - sO[g];  // |d - (b - O)| <= |d| 2^-53
     const float sv = __double2float_rn(d);
-    block[(size_t)(j - g * C) * pad + g] = sv;
-    const double e = __dadd_ru(fabs((double)sv - d), __dmul_ru(fabs(d), 0x1p-52));
+    dst[(size_t)(j - g * C) * pad + g] = sv;
+    const float e = __fadd_ru(__double2float_ru(fabs((double)sv - d)), refresh_ulp_bound(d));
 #pragma unroll
     for (int q = 0; q < PCBA_MAX_SHARED; ++q)
-      if (q == g) em[q] = fmax(em[q], e);
+      if (q == g) em[q] = fmaxf(em[q], e);
   }
+  refresh_block_reduce<PCBA_MAX_SHARED, true>(em, red);
+  if (tid < nf) {
+    float e = 0.0f;
 #pragma unroll
-  for (int q = 0; q < PCBA_MAX_SHARED; ++q) {
-    for (int o = 16; o > 0; o >>= 1) em[q] = fmax(em[q], __shfl_xor_sync(0xffffffffu, em[q], o));
-    if (lane == 0 && q < nf) {
-      ((double*)(earr + apad))[q] = O[q];
-      earr[q] = __double2float_ru(__dadd_ru(em[q], err64[q]));
-    }
+    for (int q = 0; q < PCBA_MAX_SHARED; ++q)
+      if (q == tid) e = em[q];
+    eout[tid] = __fadd_ru(e, err[tid]);
+    if (o64) o64[tid] = sO[tid];
+    else o32[tid] = (float)sO[tid];
   }
 }
 
-// Stores a converted patch (sA, C coefficients, bound base err64) as FP32
-// values at dst[j * pad] relative to the offset O (0, or the middle of its
-// range when centre is set; rounded to FP32 when o32 is set), and returns its
-// error bound (rounded up).
-__device__ __forceinline__ float refresh_store(const double* sA, int C, double err64, bool centre,
-                                               float* dst, size_t pad, double& O, int lane,
-                                               bool o32 = false) {
-  O = 0.0;
-  if (centre) {
-    double bmin = INFINITY, bmax = -INFINITY;
-    for (int j = lane; j < C; j += 32) {
-      bmin = fmin(bmin, sA[j]);
-      bmax = fmax(bmax, sA[j]);
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      bmin = fmin(bmin, __shfl_xor_sync(0xffffffffu, bmin, o));
-      bmax = fmax(bmax, __shfl_xor_sync(0xffffffffu, bmax, o));
-    }
-    O = 0.5 * (bmin + bmax);
-    if (o32) O = (double)__double2float_rn(O);
-  }
-  double emax = 0.0;
-  for (int j = lane; j < C; j += 32) {
-    const double d = sA[j] - O;  // |d - (b - O)| <= |d| 2^-53 (exact when O = 0)
-    const float sv = __double2float_rn(d);
-    dst[(size_t)j * pad] = sv;
-    emax = fmax(emax, centre ? __dadd_ru(fabs((double)sv - d), __dmul_ru(fabs(d), 0x1p-52))
-                             : fabs((double)sv - sA[j]));
-  }
-  for (int o = 16; o > 0; o >>= 1) emax = fmax(emax, __shfl_xor_sync(0xffffffffu, emax, o));
-  return __double2float_ru(__dadd_ru(emax, err64));
+// Shared memory of k_refresh (doubles): four patch buffers of cmax values,
+// the matrices of lmax axes, their scratch, the box, offsets and reduction
+// space.
+__host__ __device__ constexpr size_t refresh_smem_doubles(int cmax, int lmax) {
+  return 4 * (size_t)cmax + 2 * 289 * (size_t)lmax + (size_t)lmax * PCBA_KR_SCRATCH +
+         2 * PCBA_MAXD + PCBA_MAX_SHARED + PCBA_MAX_SHARED * (PCBA_KRB / 32);
 }
 
-__global__ void __launch_bounds__(128) k_refresh(Engine E, int cmax, int lmax) {
+__global__ void __launch_bounds__(PCBA_KRB) k_refresh(Engine E, int cmax, int lmax) {
   extern __shared__ double krs[];
   const int par = E.plan->steps_global & 1;  // the list this step's subdivision filled
   const unsigned count = min(E.plan->mark_count[par], E.mark_cap);
   if (count == 0) return;
   const double* binom = c_binom;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  double* wbase = krs + (size_t)warp * (4 * cmax + 2 * 289 * lmax + PCBA_KR_SCRATCH);
-  double* sA = wbase;
+  const int tid = threadIdx.x;
+  double* sA = krs;
   double* sB = sA + cmax;
   float* sX = (float*)(sB + cmax);
   float* sY = (float*)(sB + 2 * cmax);
   double* sT = sB + 3 * cmax;
   double* scr = sT + 2 * 289 * lmax;
+  double* box = scr + (size_t)lmax * PCBA_KR_SCRATCH;
+  double* sO = box + 2 * PCBA_MAXD;
+  float* red = (float*)(sO + PCBA_MAX_SHARED);  // 2 PCBA_MAX_SHARED x warps floats
+  float err[PCBA_MAX_SHARED];
   const uint4* list = E.marks + (size_t)par * E.mark_cap;
-  // marks are few (tens to thousands per step) and each is a chain of FP64
-  // work: warp-major numbering spreads consecutive marks over blocks (SMs)
-  // instead of stacking them on the FP64 units of one SM
-  for (unsigned q = warp * gridDim.x + blockIdx.x; q < count; q += gridDim.x * wpb) {
+  // marks are few (tens to thousands per step), each a chain of FP64 work:
+  // one per block, consecutive marks on different SMs
+  for (unsigned q = blockIdx.x; q < count; q += gridDim.x) {
     const uint4 m = list[q];
     const int p = (int)m.x, fam = (int)m.z, ip = (int)m.w;
     const ProbDesc* D = E.desc + p;
     const ProbState* S = E.state + p;
-    const int slot = (int)m.y;
+    const int slot = (int)m.y, l = D->l;
     if (slot >= S->child_twoK) continue;
+    const int nf = fam == PCBA_FAM_LIN ? D->alpha : 1;
+    const int C = fam == 2 ? D->cp : (fam == 1 ? D->ch : D->cg);
+    const int* deg = fam == 2 ? D->P : (fam == 1 ? D->H : D->G);
+    if (nf * C > cmax) continue;
     char* item = E.arena + D->list_off + (size_t)E.map[D->slot_off + slot] * D->item_bytes;
-    double blo[PCBA_MAXD], bhi[PCBA_MAXD];
-    for (int r = 0; r < D->l; ++r) {
-      const double w = ldexp(D->hi[r] - D->lo[r], -S->child_level[r]);
-      const unsigned idx = ((const unsigned*)item)[r];
-      blo[r] = D->lo[r] + w * (double)idx;
-      bhi[r] = D->lo[r] + w * (double)(idx + 1u);
+    if (tid < l) {
+      const double w = ldexp(D->hi[tid] - D->lo[tid], -S->child_level[tid]);
+      const unsigned idx = ((const unsigned*)item)[tid];
+      box[tid] = D->lo[tid] + w * (double)idx;
+      box[l + tid] = D->lo[tid] + w * (double)(idx + 1u);
     }
+    __syncthreads();
+    refresh_matrices(binom, l, deg, box, sT, scr);
     const double* mono = E.mono + D->mono_off;
+    const double* a = fam == 2 ? mono
+                               : mono + D->cp + (fam == 1 ? (long long)D->alpha * D->cg : 0) +
+                                     (fam == PCBA_FAM_LIN ? 0 : (long long)ip * C);
+    double *cA = sA, *cB = sB;
+    float *cX = sX, *cY = sY;
+    refresh_convert(a, nf, C, l, deg, sT, cA, cB, cX, cY, red, err);
     if (fam == 2) {
-      if (D->cp > cmax) continue;
-      // the cost patch: recomputed and re-centred on its range
-      refresh_matrices(binom, D->l, D->P, blo, bhi, sT, scr, lane);
-      const double err64 = refresh_convert(mono, D->cp, D->l, D->P, sT, sA, sB, sX, sY, lane);
-      double O;
-      const float e = refresh_store(sA, D->cp, err64, true, (float*)(item + D->off_cost), 1, O,
-                                    lane);
-      if (lane == 0) {
-        *(double*)(item + 32) = O;
-        *(float*)(item + 40) = e;
-        atomicAdd(&E.plan->refreshed_total, 1ull);
-      }
-      __syncwarp();
-      continue;
-    }
-    if (fam == PCBA_FAM_LIN) {
-      // every shared patch of a linear-family item (one set of matrices),
-      // re-centred, to the copy the next step reads
-      const int C = D->cg;
-      if (D->alpha * C > cmax) continue;
-      refresh_matrices(binom, D->l, D->G, blo, bhi, sT, scr, lane);
+      // the cost patch, re-centred on its range
+      refresh_store(cA, 1, C, err, (float*)(item + D->off_cost), 1, (float*)(item + 40),
+                    (double*)(item + 32), nullptr, red, sO);
+    } else if (fam == PCBA_FAM_LIN) {
+      // every shared patch of a linear-family item, to the copy the next
+      // step reads
       const int nxt = (E.plan->steps_global + 1) & 1;
-      double err64[PCBA_MAX_SHARED];
-      refresh_convert_multi(mono + D->cp, D->alpha, C, D->l, D->G, sT, sA, sB, sX, sY, lane,
-                            err64);
-      refresh_store_multi(sA, D->alpha, C, err64, (float*)(item + D->off_g + nxt * D->copy_g),
-                          D->apad, (float*)(item + D->off_eg + nxt * D->copy_e), D->apad, lane);
-      __syncwarp();
-      if (lane == 0) atomicAdd(&E.plan->refreshed_total, (unsigned long long)D->alpha);
-      continue;
+      float* earr = (float*)(item + D->off_eg + nxt * D->copy_e);
+      refresh_store(cA, nf, C, err, (float*)(item + D->off_g + nxt * D->copy_g), D->apad, earr,
+                    (double*)(earr + D->apad), nullptr, red, sO);
+    } else {
+      // one dense constraint patch, re-centred on an FP32 offset
+      const size_t pad = fam ? D->bpad : D->apad;
+      refresh_store(cA, 1, C, err, (float*)(item + (fam ? D->off_h : D->off_g)) + ip, pad,
+                    (float*)(item + (fam ? D->off_eh : D->off_eg)) + ip, nullptr,
+                    (float*)(item + (fam ? D->off_oh : D->off_og)) + ip, red, sO);
     }
-    const int C = fam ? D->ch : D->cg;
-    if (C > cmax) continue;
-    const int* deg = fam ? D->H : D->G;
-    refresh_matrices(binom, D->l, deg, blo, bhi, sT, scr, lane);
-    const size_t pad = fam ? D->bpad : D->apad;
-    float* block = (float*)(item + (fam ? D->off_h : D->off_g));
-    float* earr = (float*)(item + (fam ? D->off_eh : D->off_eg));
-    const double* fam_mono = mono + D->cp + (fam ? (long long)D->alpha * D->cg : 0);
-    const double err64 =
-        refresh_convert(fam_mono + (long long)ip * C, C, D->l, deg, sT, sA, sB, sX, sY, lane);
-    // dense families: re-centred on an FP32 offset
-    double O;
-    const float e = refresh_store(sA, C, err64, true, block + ip, pad, O, lane, true);
-    if (lane == 0) {
-      earr[ip] = e;
-      ((float*)(item + (fam ? D->off_oh : D->off_og)))[ip] = (float)O;
-      atomicAdd(&E.plan->refreshed_total, 1ull);
-    }
-    __syncwarp();
+    if (tid == 0) atomicAdd(&E.plan->refreshed_total, (unsigned long long)nf);
+    __syncthreads();  // the buffers are reused by the next mark
   }
 }
 
