@@ -25,6 +25,11 @@
 
 #include "pcba.h"
 #include "pcba_host.h"
+
+// 1: the kernels after the subdivision are launched as dependent steps
+#ifndef PCBA_PDL_STEPS
+#define PCBA_PDL_STEPS 1
+#endif
 #include "pcba_kernels.cuh"
 #include "pcba_warmstart.h"
 
@@ -410,11 +415,11 @@ int launch_after_k2(pcba_batch* b, cudaStream_t s, int use_graph) {
     k_refresh<<<g.kr_grid, PCBA_KRB, g.kr_smem, b->side>>>(b->E, g.kr_cmax, g.kr_lmax);
     PCBA_CK(cudaEventRecord(b->ev_join, b->side));
   }
-  k_pup<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
-  k3_classify<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
-  k4_index<<<g.k3_grid, PCBA_TPB, 0, s>>>(b->E);
+  PCBA_CK(pcba_launch_step(PCBA_PDL_STEPS, k_pup, g.k3_grid, PCBA_TPB, 0, s, b->E));
+  PCBA_CK(pcba_launch_step(PCBA_PDL_STEPS, k3_classify, g.k3_grid, PCBA_TPB, 0, s, b->E));
+  PCBA_CK(pcba_launch_step(PCBA_PDL_STEPS, k4_index, g.k3_grid, PCBA_TPB, 0, s, b->E));
   if (fp32) PCBA_CK(cudaStreamWaitEvent(s, b->ev_join, 0));
-  k_move_control<<<g.k4_grid, PCBA_TPB, 0, s>>>(b->E, b->cond, use_graph);
+  PCBA_CK(pcba_launch_step(PCBA_PDL_STEPS, k_move_control, g.k4_grid, PCBA_TPB, 0, s, b->E, b->cond, use_graph));
   PCBA_CK(cudaGetLastError());
   return 0;
 }
@@ -499,6 +504,10 @@ int setup_kernels(pcba_batch* b) {
   return 0;
 }
 
+#ifndef PCBA_BODY_STEPS
+#define PCBA_BODY_STEPS 4
+#endif
+
 template <typename T>
 int build_graph(pcba_batch* b) {
   PCBA_CK(cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking));
@@ -517,11 +526,11 @@ int build_graph(pcba_batch* b) {
   cudaGraph_t body = cp->conditional.phGraph_out[0];
   PCBA_CK(cudaStreamBeginCaptureToGraph(b->cap_stream, body, nullptr, nullptr, 0,
                                         cudaStreamCaptureModeThreadLocal));
-  // two iterations per body: the conditional node's relaunch between bodies
-  // costs a few microseconds; a second iteration after the loop's end finds
-  // no work in any kernel (and is not counted as a step)
-  int rc = launch_loop_body<T>(b, b->cap_stream, 1);
-  if (!rc) rc = launch_loop_body<T>(b, b->cap_stream, 1);
+  // PCBA_BODY_STEPS iterations per body: the conditional node's relaunch
+  // between bodies costs a few microseconds; an iteration after the loop's
+  // end finds no work in any kernel (and is not counted as a step)
+  int rc = 0;
+  for (int it = 0; it < PCBA_BODY_STEPS && !rc; ++it) rc = launch_loop_body<T>(b, b->cap_stream, 1);
   cudaGraph_t captured = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->cap_stream, &captured);
   if (rc) return rc;

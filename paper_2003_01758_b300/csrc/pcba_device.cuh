@@ -259,6 +259,14 @@ __device__ __forceinline__ int find_problem(const unsigned* pre, int np, unsigne
   return lo;
 }
 
+// Programmatic dependent launch of the per-step kernels: a kernel launched
+// with the attribute is scheduled as soon as its predecessor's blocks have
+// all left (no explicit trigger: a trigger at the start, which lets the
+// blocks of the next kernel wait on the SMs, measured slower), and before
+// touching any state it waits for that predecessor's completion and memory.
+// A kernel launched without the attribute passes the wait at once.
+__device__ __forceinline__ void pdl_begin() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // The same search by a whole warp (all 32 lanes, warp-uniform u): each round
 // splits [lo, hi) into 32 parts and reads one boundary per lane, so 1024
 // problems take two dependent loads instead of ten.

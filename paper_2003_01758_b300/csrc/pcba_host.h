@@ -9,6 +9,7 @@
 
 #include <cuda_runtime.h>
 
+#include <cstdlib>
 #include <string>
 #include <vector>
 
@@ -40,6 +41,27 @@ struct K2Plan {
 
 // Fills the plan for the batch's problems (kernel variant, feasible
 // configurations with their occupancy-sized grids); 0 or a PCBA_ERR_* code.
+// Launches one of the per-step kernels (those that begin with pdl_begin),
+// with programmatic stream serialization when pdl is set: it is scheduled
+// as its predecessor in the stream finishes, and waits for it itself.  The
+// environment variable PCBA_NO_PDL turns this off (plain launches).
+template <typename... P, typename... A>
+inline cudaError_t pcba_launch_step(bool pdl, void (*k)(P...), dim3 grid, dim3 block,
+                                    size_t smem, cudaStream_t s, A... args) {
+  static const bool no_pdl = std::getenv("PCBA_NO_PDL") != nullptr;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = no_pdl || !pdl ? 0 : 1;
+  return cudaLaunchKernelEx(&cfg, k, static_cast<P>(args)...);
+}
+
 int pcba_k2_prepare_f32(K2Plan& g, const std::vector<ProbDesc>& desc, bool lin, int sms,
                         int smem_optin);
 int pcba_k2_prepare_f64(K2Plan& g, const std::vector<ProbDesc>& desc, bool lin, int sms,

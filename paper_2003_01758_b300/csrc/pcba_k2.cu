@@ -14,6 +14,10 @@
 #include "pcba_subdivide.cuh"
 #include "pcba_linear.cuh"
 
+// 1: the linear-family kernels are launched as dependent steps
+#ifndef PCBA_PDL_K2
+#define PCBA_PDL_K2 1
+#endif
 #ifndef PCBA_K2_F64
 #define PCBA_K2_F64 0
 #endif
@@ -167,22 +171,18 @@ void launch(const K2Plan& g, int cfg, const Engine& E, cudaStream_t s) {
     // the split writes the children, then the bound reads them
     const int gs = g.lin_split_grid, cg = g.lin_cgmax, cp = g.lin_cpmax;
     const size_t ss = g.lin_split_smem;
-    if (g.lin_k == 3 && g.nfix == 6) {
-      k2_lin_split<T, 3, 6><<<gs, 256, ss, s>>>(E, cg, cp);
-    } else {
-      switch (g.lin_k) {
-        case 1: k2_lin_split<T, 1, 0><<<gs, 256, ss, s>>>(E, cg, cp); break;
-        case 2: k2_lin_split<T, 2, 0><<<gs, 256, ss, s>>>(E, cg, cp); break;
-        case 3: k2_lin_split<T, 3, 0><<<gs, 256, ss, s>>>(E, cg, cp); break;
-        default: k2_lin_split<T, 4, 0><<<gs, 256, ss, s>>>(E, cg, cp); break;
-      }
-    }
-    switch (g.lin_k) {
-      case 1: k2_lin_bound<T, 1><<<c.grid, blk, c.smem, s>>>(E, cg); break;
-      case 2: k2_lin_bound<T, 2><<<c.grid, blk, c.smem, s>>>(E, cg); break;
-      case 3: k2_lin_bound<T, 3><<<c.grid, blk, c.smem, s>>>(E, cg); break;
-      default: k2_lin_bound<T, 4><<<c.grid, blk, c.smem, s>>>(E, cg); break;
-    }
+    // (both begin with pdl_begin: launched as dependent steps)
+    auto split = g.lin_k == 3 && g.nfix == 6 ? k2_lin_split<T, 3, 6>
+                 : g.lin_k == 1             ? k2_lin_split<T, 1, 0>
+                 : g.lin_k == 2             ? k2_lin_split<T, 2, 0>
+                 : g.lin_k == 3             ? k2_lin_split<T, 3, 0>
+                                            : k2_lin_split<T, 4, 0>;
+    auto bound = g.lin_k == 1 ? k2_lin_bound<T, 1>
+                 : g.lin_k == 2 ? k2_lin_bound<T, 2>
+                 : g.lin_k == 3 ? k2_lin_bound<T, 3>
+                                : k2_lin_bound<T, 4>;
+    pcba_launch_step(PCBA_PDL_K2, split, gs, 256, ss, s, E, cg, cp);
+    pcba_launch_step(PCBA_PDL_K2, bound, c.grid, blk, c.smem, s, E, cg);
     return;
   }
   if (c.tma) {

@@ -672,7 +672,10 @@ __device__ __forceinline__ void pup_phase(const Engine& E) {
   }
 }
 
-__global__ void __launch_bounds__(PCBA_TPB) k_pup(Engine E) { pup_phase(E); }
+__global__ void __launch_bounds__(PCBA_TPB) k_pup(Engine E) {
+  pdl_begin();
+  pup_phase(E);
+}
 
 // ---------------------------------------------------------------------------
 // K3: classify, scan, finalize, plan
@@ -958,6 +961,7 @@ __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan,
 }
 
 __global__ void __launch_bounds__(PCBA_TPB) k3_classify(Engine E) {
+  pdl_begin();
   __shared__ unsigned sscan[8];
   __shared__ double sred[8 * 2];
   __shared__ int s_last, s_glast;
@@ -993,7 +997,10 @@ __device__ __forceinline__ void index_phase(const Engine& E) {
   }
 }
 
-__global__ void __launch_bounds__(PCBA_TPB) k4_index(Engine E) { index_phase(E); }
+__global__ void __launch_bounds__(PCBA_TPB) k4_index(Engine E) {
+  pdl_begin();
+  index_phase(E);
+}
 
 // Alg. 5 on the map: the j-th hole below K_save takes the slot of the item at
 // save position K_save-1-j (reading R11); one thread per hole.
@@ -1033,8 +1040,8 @@ __device__ __forceinline__ void control_phase(const Engine& E, cudaGraphConditio
   Plan* pl = E.plan;
   for (int q = threadIdx.x; q <= E.np; q += blockDim.x) E.k3_pre[q] = E.k3_pre_next[q];
   if (threadIdx.x == 0) {
-    // the graph's loop body holds two iterations; one that runs after the
-    // loop's end has no classify tiles, does no work and is not a step
+    // the graph's loop body holds several iterations; those that run after
+    // the loop's end have no classify tiles, do no work and are not steps
     const bool did = pl->k3_tiles > 0;
     pl->k3_tiles = pl->k3_tiles_next;
     // the refresh of this iteration consumed this step's list
@@ -1053,9 +1060,11 @@ __device__ __forceinline__ void control_phase(const Engine& E, cudaGraphConditio
     else if (running && pl->steps_global >= P->step_guard) { code = PCBA_RUNNING + 1; pl->guard_hit = 1; }
     if (code) {
       // the plan was made for problems that are now stopped: leave the
-      // iteration that may follow in the loop body nothing to do
+      // iterations that may follow in the loop body nothing to do (each
+      // copies the next step's tile count: it must stay zero too)
       pl->k2_units = 0u;
       pl->k3_tiles = 0u;
+      pl->k3_tiles_next = 0u;
       pl->k4_units = 0u;
       pl->kr_units = 0u;
     }
@@ -1090,6 +1099,7 @@ __device__ __forceinline__ void control_phase(const Engine& E, cudaGraphConditio
 __global__ void __launch_bounds__(PCBA_TPB) k_move_control(Engine E,
                                                            cudaGraphConditionalHandle handle,
                                                            int use_graph) {
+  pdl_begin();
   __shared__ int s_last, s_code, s_run;
   if (E.plan->k3_tiles > 0) move_phase(E);  // no moves after the loop's end
   __syncthreads();

@@ -702,6 +702,7 @@ __device__ __forceinline__ void lin_fibre(const T* src, T* dL, T* dR, int sst, L
 
 template <typename T, int K, int NFIX>
 __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engine E, int cgmax, int cpmax) {
+  pdl_begin();
   constexpr bool RIG = sizeof(T) == 4;
   constexpr float u24 = 0x1p-24f;
   extern __shared__ __align__(16) unsigned char kls[];
@@ -1159,6 +1160,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
 // children are staged from memory.
 template <typename T, int K>
 __global__ void __launch_bounds__(256, PCBA_LIN_BOUND_BLOCKS) k2_lin_bound(Engine E, int cgmax) {
+  pdl_begin();
   constexpr bool RIG = sizeof(T) == 4;
   extern __shared__ __align__(16) unsigned char klb[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
