@@ -26,6 +26,14 @@
 #include "pcba.h"
 #include "pcba_host.h"
 
+// Blocks per SM of the per-step kernels over child tiles (0: as many as fit)
+// and of the compaction.
+#ifndef PCBA_K3_BLOCKS_PER_SM
+#define PCBA_K3_BLOCKS_PER_SM 0
+#endif
+#ifndef PCBA_K4_BLOCKS_PER_SM
+#define PCBA_K4_BLOCKS_PER_SM 1
+#endif
 // 1: the kernels after the subdivision are launched as dependent steps
 #ifndef PCBA_PDL_STEPS
 #define PCBA_PDL_STEPS 1
@@ -497,10 +505,11 @@ int setup_kernels(pcba_batch* b) {
   PCBA_CK(cudaFuncSetAttribute(k_cand_first<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                (int)kCandStageMax));
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k3_classify, PCBA_TPB, 0));
-  g.k3_grid = std::max(1, occ) * g.sms;
-
+  g.k3_grid = std::max(1, PCBA_K3_BLOCKS_PER_SM > 0 ? std::min(occ, PCBA_K3_BLOCKS_PER_SM) : occ) * g.sms;
+  // the compaction: every block of k_move_control takes a ticket for the
+  // last-block test, so few blocks (the holes of a step fit one pass)
   PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_move_control, PCBA_TPB, 0));
-  g.k4_grid = std::max(1, occ) * g.sms;
+  g.k4_grid = std::max(1, std::min(occ, PCBA_K4_BLOCKS_PER_SM)) * g.sms;
   return 0;
 }
 

@@ -26,8 +26,9 @@
 //                             the last tile overall plans the next step.
 //   k4_index / k_move_control Alg. 5 (reading R11) on the slot map: the j-th
 //                             hole below K_save receives the slot of the item at
-//                             save position K_save-1-j; the last block then runs
-//                             the device-side loop control (graph conditional).
+//                             save position K_save-1-j; one block runs the
+//                             device-side loop control (graph conditional)
+//                             beside the moves.
 //   k_eval                    warm start: certified candidate points seed p_up
 //                             (FP32 with error bounds); final check of the
 //                             returned point in FP64 with an error bound.
@@ -1004,8 +1005,7 @@ __global__ void __launch_bounds__(PCBA_TPB) k4_index(Engine E) {
 
 // Alg. 5 on the map: the j-th hole below K_save takes the slot of the item at
 // save position K_save-1-j (reading R11); one thread per hole.
-__device__ __forceinline__ void move_phase(const Engine& E) {
-  const unsigned units = E.plan->k4_units;
+__device__ __forceinline__ void move_phase(const Engine& E, unsigned units) {
   const int lane = threadIdx.x & 31;
   // a warp's 32 consecutive units: its first unit's problem by a warp
   // search, and only when the units reach past that problem a second one
@@ -1095,23 +1095,31 @@ __device__ __forceinline__ void control_phase(const Engine& E, cudaGraphConditio
 }
 
 
-// Alg. 5 on the slot map, then the loop control in the last block to finish.
+// Alg. 5 on the slot map; the loop control runs beside it, in the block that
+// takes the last ticket.
 __global__ void __launch_bounds__(PCBA_TPB) k_move_control(Engine E,
                                                            cudaGraphConditionalHandle handle,
                                                            int use_graph) {
   pdl_begin();
   __shared__ int s_last, s_code, s_run;
-  if (E.plan->k3_tiles > 0) move_phase(E);  // no moves after the loop's end
-  __syncthreads();
+  __shared__ unsigned s_units;
+  // every block reads its part of the plan (this step's moves) before it
+  // takes a ticket; the block with the last ticket runs the loop control,
+  // which rewrites the plan but reads nothing the moves write, while the
+  // other blocks move
   if (threadIdx.x == 0) {
+    s_units = E.plan->k3_tiles > 0 ? E.plan->k4_units : 0u;  // no moves after the loop's end
     __threadfence();
     s_last = atomicAdd(&E.plan->k4_done, 1u) == gridDim.x - 1;
   }
   __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-  if (threadIdx.x == 0) E.plan->k4_done = 0u;
-  control_phase(E, handle, use_graph, s_code, s_run);
+  const unsigned units = s_units;
+  if (s_last) {
+    __threadfence();
+    if (threadIdx.x == 0) E.plan->k4_done = 0u;
+    control_phase(E, handle, use_graph, s_code, s_run);
+  }
+  move_phase(E, units);
 }
 
 __global__ void k_init(Engine E) {
