@@ -247,6 +247,7 @@ struct pcba_batch {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   cudaStream_t side = nullptr;                        // k_refresh beside k_pup..k4_index
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  bool refresh_pending = false;  // a refresh on the side stream not yet joined
   cudaEvent_t ev_k1f = nullptr, ev_k1j = nullptr;  // K1 on the side stream beside the warm start
   std::vector<cudaEvent_t> kev;
   Engine E{};
@@ -409,10 +410,22 @@ void launch_k2(const pcba_batch* b, cudaStream_t s) {
   else pcba_k2_launch_f64(b->g.k2, b->g.cfg, b->E, s);
 }
 
+// The main stream waits for the last refresh launched on the side stream:
+// before the next subdivision (which reads the refreshed patches), and
+// before anything reads results.
+int join_refresh(pcba_batch* b, cudaStream_t s) {
+  if (!b->refresh_pending) return 0;
+  b->refresh_pending = false;
+  PCBA_CK(cudaStreamWaitEvent(s, b->ev_join, 0));
+  return 0;
+}
+
 // The kernels of one device-loop iteration after the subdivision: the FP32
 // refresh of the patches it marked runs on a side stream beside k_pup,
-// k3_classify and k4_index (which read only the child records) and joins
-// before k_move_control updates the slot map.
+// k3_classify, k4_index and k_move_control (which read only the child
+// records and the slot map; the refresh finds its items through the map
+// before the compaction, whose moves change no item) and joins before the
+// next subdivision.
 template <typename T>
 int launch_after_k2(pcba_batch* b, cudaStream_t s, int use_graph) {
   const Grids& g = b->g;
@@ -422,11 +435,11 @@ int launch_after_k2(pcba_batch* b, cudaStream_t s, int use_graph) {
     PCBA_CK(cudaStreamWaitEvent(b->side, b->ev_fork, 0));
     k_refresh<<<g.kr_grid, PCBA_KRB, g.kr_smem, b->side>>>(b->E, g.kr_cmax, g.kr_lmax);
     PCBA_CK(cudaEventRecord(b->ev_join, b->side));
+    b->refresh_pending = true;
   }
   PCBA_CK(pcba_launch_step(PCBA_PDL_STEPS, k_pup, g.k3_grid, PCBA_TPB, 0, s, b->E));
   PCBA_CK(pcba_launch_step(PCBA_PDL_STEPS, k3_classify, g.k3_grid, PCBA_TPB, 0, s, b->E));
   PCBA_CK(pcba_launch_step(PCBA_PDL_STEPS, k4_index, g.k3_grid, PCBA_TPB, 0, s, b->E));
-  if (fp32) PCBA_CK(cudaStreamWaitEvent(s, b->ev_join, 0));
   PCBA_CK(pcba_launch_step(PCBA_PDL_STEPS, k_move_control, g.k4_grid, PCBA_TPB, 0, s, b->E, b->cond, use_graph));
   PCBA_CK(cudaGetLastError());
   return 0;
@@ -434,6 +447,7 @@ int launch_after_k2(pcba_batch* b, cudaStream_t s, int use_graph) {
 
 template <typename T>
 int launch_loop_body(pcba_batch* b, cudaStream_t s, int use_graph) {
+  if (int rc = join_refresh(b, s)) return rc;
   launch_k2<T>(b, s);
   return launch_after_k2<T>(b, s, use_graph);
 }
@@ -539,7 +553,9 @@ int build_graph(pcba_batch* b) {
   // between bodies costs a few microseconds; an iteration after the loop's
   // end finds no work in any kernel (and is not counted as a step)
   int rc = 0;
+  b->refresh_pending = false;
   for (int it = 0; it < PCBA_BODY_STEPS && !rc; ++it) rc = launch_loop_body<T>(b, b->cap_stream, 1);
+  if (!rc) rc = join_refresh(b, b->cap_stream);  // the body ends with every stream joined
   cudaGraph_t captured = nullptr;
   cudaError_t e = cudaStreamEndCapture(b->cap_stream, &captured);
   if (rc) return rc;
@@ -1028,6 +1044,7 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
     int it = 0;
     for (;; ++it) {
       if (it >= guard) return fail(PCBA_ERR_DEVICE_TIMEOUT, "host loop guard reached");
+      if (int rc2 = join_refresh(b, s)) return rc2;
       if (instrument) {
         double bytes = 0;
         for (int k = 0; k < n; ++k)
@@ -1060,6 +1077,7 @@ int run_solve(pcba_batch* b, const double* host_coeffs, double opt_tol, double e
       }
     }
   }
+  if (int rc2 = join_refresh(b, s)) return rc2;
   k_eval<<<n, PCBA_TPB, 0, s>>>(b->E, 1, b->d_eval);
   PCBA_CK(cudaGetLastError());
   PCBA_CK(cudaMemcpyAsync(b->h_state, b->d_state, sizeof(ProbState) * n, cudaMemcpyDeviceToHost, s));

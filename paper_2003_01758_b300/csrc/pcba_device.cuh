@@ -139,8 +139,11 @@ struct ProbState {
   int ftop;                     // free-slot stack height before the coming step's pops
   int hw;                       // physical slots >= hw have never been used
   int ftop_push;                // stack height after this step's pops (base of its pushes)
-  int child_level[PCBA_MAXD];   // levels of the children of the coming step (set between steps)
-  int child_twoK;               // children of the coming step
+  // levels and count of the children of a step, by the parity of the step:
+  // the loop control sets the coming step's while the refresh of the step
+  // just done still reads its own
+  int child_level[2][PCBA_MAXD];
+  int child_twoK[2];
   int seeded;                   // a warm-start candidate was certified feasible
   double seed_cost;             // its certified cost bound (the initial p_up)
   double seed_x[PCBA_MAXD];     // the candidate
@@ -167,6 +170,7 @@ struct Plan {
   unsigned kr_units;
   unsigned mark_count[2];  // marked patches appended by the subdivision of even / odd steps
   unsigned long long marks_total, refreshed_total;
+  unsigned kr_par;               // parity of the step whose marks the refresh takes (set by the subdivision)
   unsigned long long lin_pairs;  // linear families: (child, active constraint) bounds of the solve
   unsigned long long lin_full;   // of which bounded from the coefficient range (not the interval)
   unsigned lin_next;             // next unit of the linear bound kernel to hand out

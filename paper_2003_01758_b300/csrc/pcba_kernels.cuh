@@ -552,7 +552,9 @@ __host__ __device__ constexpr size_t refresh_smem_doubles(int cmax, int lmax) {
 
 __global__ void __launch_bounds__(PCBA_KRB) k_refresh(Engine E, int cmax, int lmax) {
   extern __shared__ double krs[];
-  const int par = E.plan->steps_global & 1;  // the list this step's subdivision filled
+  // the list this step's subdivision filled (the loop control, which runs
+  // beside this kernel, may already have counted the step)
+  const int par = (int)E.plan->kr_par;
   const unsigned count = min(E.plan->mark_count[par], E.mark_cap);
   if (count == 0) return;
   const double* binom = c_binom;
@@ -571,19 +573,19 @@ __global__ void __launch_bounds__(PCBA_KRB) k_refresh(Engine E, int cmax, int lm
   // marks are few (tens to thousands per step), each a chain of FP64 work:
   // one per block, consecutive marks on different SMs
   for (unsigned q = blockIdx.x; q < count; q += gridDim.x) {
-    const uint4 m = list[q];
-    const int p = (int)m.x, fam = (int)m.z, ip = (int)m.w;
+    const uint4 m = list[q];  // (problem, child position, physical slot, family | patch << 2)
+    const int p = (int)m.x, fam = (int)(m.w & 3u), ip = (int)(m.w >> 2);
     const ProbDesc* D = E.desc + p;
     const ProbState* S = E.state + p;
     const int slot = (int)m.y, l = D->l;
-    if (slot >= S->child_twoK) continue;
+    if (slot >= S->child_twoK[par]) continue;
     const int nf = fam == PCBA_FAM_LIN ? D->alpha : 1;
     const int C = fam == 2 ? D->cp : (fam == 1 ? D->ch : D->cg);
     const int* deg = fam == 2 ? D->P : (fam == 1 ? D->H : D->G);
     if (nf * C > cmax) continue;
-    char* item = E.arena + D->list_off + (size_t)E.map[D->slot_off + slot] * D->item_bytes;
+    char* item = E.arena + D->list_off + (size_t)m.z * D->item_bytes;
     if (tid < l) {
-      const double w = ldexp(D->hi[tid] - D->lo[tid], -S->child_level[tid]);
+      const double w = ldexp(D->hi[tid] - D->lo[tid], -S->child_level[par][tid]);
       const unsigned idx = ((const unsigned*)item)[tid];
       box[tid] = D->lo[tid] + w * (double)idx;
       box[l + tid] = D->lo[tid] + w * (double)(idx + 1u);
@@ -604,7 +606,7 @@ __global__ void __launch_bounds__(PCBA_KRB) k_refresh(Engine E, int cmax, int lm
     } else if (fam == PCBA_FAM_LIN) {
       // every shared patch of a linear-family item, to the copy the next
       // step reads
-      const int nxt = (E.plan->steps_global + 1) & 1;
+      const int nxt = par ^ 1;
       float* earr = (float*)(item + D->off_eg + nxt * D->copy_e);
       refresh_store(cA, nf, C, err, (float*)(item + D->off_g + nxt * D->copy_g), D->apad, earr,
                     (double*)(earr + D->apad), nullptr, red, sO);
@@ -675,6 +677,9 @@ __device__ __forceinline__ void pup_phase(const Engine& E) {
 
 __global__ void __launch_bounds__(PCBA_TPB) k_pup(Engine E) {
   pdl_begin();
+  // the previous step's mark list: its refresh finished before this step's
+  // subdivision began, and the next step's subdivision fills it again
+  if (blockIdx.x == 0 && threadIdx.x == 0) E.plan->mark_count[(E.plan->steps_global & 1) ^ 1] = 0u;
   pup_phase(E);
 }
 
@@ -1044,12 +1049,12 @@ __device__ __forceinline__ void control_phase(const Engine& E, cudaGraphConditio
     // the loop's end have no classify tiles, do no work and are not steps
     const bool did = pl->k3_tiles > 0;
     pl->k3_tiles = pl->k3_tiles_next;
-    // the refresh of this iteration consumed this step's list
+    // this step's marks (its refresh, which may still run, reads the same
+    // count; k_pup of the next step clears the list once that is done)
     pl->marks_total += min(pl->mark_count[pl->steps_global & 1], E.mark_cap);
     pl->lin_next = 0u;
     pl->lin_next2 = 0u;
     pl->lin_qcount = 0u;
-    pl->mark_count[pl->steps_global & 1] = 0u;
     if (did) pl->steps_global += 1;
     const int running = pl->any_running;
     const SolveParams* P = E.params;
@@ -1081,11 +1086,14 @@ __device__ __forceinline__ void control_phase(const Engine& E, cudaGraphConditio
       }
     }
   }
-  // boxes of the children of the coming step, for k_refresh
+  // boxes of the children of the coming step, for k_refresh (by its
+  // parity: the refresh of the step just done may still read its own)
+  const int cpar = pl->steps_global & 1;
   for (int q = threadIdx.x; q < E.np; q += blockDim.x) {
     ProbState* S = E.state + q;
-    for (int r = 0; r < PCBA_MAXD; ++r) S->child_level[r] = S->level[r] + (r == S->r ? 1 : 0);
-    S->child_twoK = 2 * S->K;
+    for (int r = 0; r < PCBA_MAXD; ++r)
+      S->child_level[cpar][r] = S->level[r] + (r == S->r ? 1 : 0);
+    S->child_twoK[cpar] = 2 * S->K;
   }
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -1142,9 +1150,9 @@ __global__ void k_init(Engine E) {
         S->level[q] = 0;
         S->best_index[q] = 0;
         S->best_level[q] = 0;
-        S->child_level[q] = q == 0 ? 1 : 0;
+        S->child_level[0][q] = S->child_level[1][q] = q == 0 ? 1 : 0;
       }
-      S->child_twoK = 2;
+      S->child_twoK[0] = S->child_twoK[1] = 2;
       S->ftop = 0;
       S->ftop_push = 0;
       S->hw = 1;
@@ -1212,6 +1220,7 @@ __global__ void k_init(Engine E) {
     pl->kr_units = runr;
     pl->mark_count[0] = 0u;
     pl->mark_count[1] = 0u;
+    pl->kr_par = 0u;
     pl->marks_total = 0ull;
     pl->refreshed_total = 0ull;
     pl->lin_pairs = 0ull;

@@ -194,13 +194,12 @@ __device__ __forceinline__ void lin_copy2(T* d1, const T* s1, int n1, T* d2, con
   else if (lane >= 8 && lane - 8 < r2) d2[b * V + lane - 8] = t;
 }
 
-// One mark (problem, child slot, family, patch) for k_refresh.
-__device__ __forceinline__ void lin_mark(const Engine& E, int mpar, int p, int slot, int fam,
-                                         int ip) {
+// One mark (problem, logical child position, physical slot, family, patch)
+// for k_refresh.
+__device__ __forceinline__ void lin_mark(const Engine& E, int mpar, int p, int slot,
+                                         unsigned phys, int fam, int ip) {
   const unsigned q = atomicAdd(&E.plan->mark_count[mpar], 1u);
-  if (q < E.mark_cap)
-    E.marks[(size_t)mpar * E.mark_cap + q] =
-        make_uint4((unsigned)p, (unsigned)slot, (unsigned)fam, (unsigned)ip);
+  if (q < E.mark_cap) E.marks[(size_t)mpar * E.mark_cap + q] = make_mark(p, slot, phys, fam, ip);
 }
 
 
@@ -386,8 +385,8 @@ __device__ __forceinline__ void lin_kappa(const float* hv, const float* lv, cons
 // summaries).  The window holds at most PCBA_LIN_IDX active constraints (a
 // single chunk at most PCBA_LIN_WORDS x 32, several at most PCBA_LIN_WIN, a
 // light item at most PCBA_LIN_LIGHT_MAX).  They are compacted and bounded on
-// both children (shared patches staged at sL / sR,
-// [C][4]); the children's words and their chunks' summary bits are written
+// both children (items left / right in slots slotL / slotR, shared patches
+// staged at sL / sR, [C][4]); the children's words and their chunks' summary bits are written
 // and the bound maxima go to the child records.  One warp; sIdx, sMw (the
 // children's words, 2 x 32) and sWi (the 32 word indices) are its buffers.
 static_assert(PCBA_LIN_WORDS * 32 <= PCBA_LIN_IDX && PCBA_LIN_WIN <= PCBA_LIN_IDX &&
@@ -396,6 +395,7 @@ static_assert(PCBA_LIN_WORDS * 32 <= PCBA_LIN_IDX && PCBA_LIN_WIN <= PCBA_LIN_ID
 template <typename T, int K>
 __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int Kl, int wi,
                            unsigned word, unsigned long long cbit, char* left, char* right,
+                           unsigned slotL, unsigned slotR,
                            const T* sL, const T* sR, const LinChildren<T, K>& ch,
                            unsigned short* sIdx, unsigned* sMw, int* sWi, int par) {
   constexpr bool RIG = sizeof(T) == 4;
@@ -614,7 +614,7 @@ __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int
     }
   }
   if constexpr (RIG) {
-    const MarkCtx mk{p, k, k + Kl, E.marks + (size_t)par * E.mark_cap,
+    const MarkCtx mk{p, k, k + Kl, slotL, slotR, E.marks + (size_t)par * E.mark_cap,
                      &E.plan->mark_count[par], E.mark_cap};
     // one mark per child for all its shared patches (family PCBA_FAM_LIN),
     // the first window to ask for it sets bit 32 of the child record's perr
@@ -703,6 +703,7 @@ __device__ __forceinline__ void lin_fibre(const T* src, T* dL, T* dR, int sst, L
 template <typename T, int K, int NFIX>
 __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engine E, int cgmax, int cpmax) {
   pdl_begin();
+  if (blockIdx.x == 0 && threadIdx.x == 0) E.plan->kr_par = E.plan->steps_global & 1;
   constexpr bool RIG = sizeof(T) == 4;
   constexpr float u24 = 0x1p-24f;
   extern __shared__ __align__(16) unsigned char kls[];
@@ -896,7 +897,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
               *(float*)(it + 40) = e2;
               rec->pmax = okey(y);
               rec->perr = __float_as_uint(e2);
-              if (e2 > cost_thr32) lin_mark(E, par, p, c ? k + Kl : k, 2, 0);
+              if (e2 > cost_thr32) lin_mark(E, par, p, c ? k + Kl : k, c ? rslot : pslot, 2, 0);
             } else {
               rec->vtxc[v - 2] = __double2float_ru(y);
             }
@@ -1147,7 +1148,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
             if (i2 >= chunks) break;
             lin_window_words(D, pmask, (unsigned)i2 | (1u << 16), false, wi, wv, cb);
           }
-          lin_window<T, K>(E, D, p, k, Kl, wi, wv, cb, parent, right, spL, spR, ch, ls.sIdx,
+          lin_window<T, K>(E, D, p, k, Kl, wi, wv, cb, parent, right, pslot, rslot, spL, spR, ch, ls.sIdx,
                            ls.sMw, ls.sWi, par);
         }
       }
@@ -1176,6 +1177,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_BOUND_BLOCKS) k2_lin_bound(Engin
   int p = 0, k = 0, Kl = 0;
   const ProbDesc* D = nullptr;
   char *left = nullptr, *right = nullptr;
+  unsigned sLs = 0u, sRs = 0u;  // their physical slots
   for (;;) {
     unsigned ubeg = 0;
     if (lane == 0) ubeg = atomicAdd(&E.plan->lin_next, bsz);
@@ -1193,8 +1195,10 @@ __global__ void __launch_bounds__(256, PCBA_LIN_BOUND_BLOCKS) k2_lin_bound(Engin
         k = (int)ent.w;
         Kl = E.state[p].K;
         char* list = E.arena + D->list_off;
-        left = list + (size_t)E.map[D->slot_off + k] * D->item_bytes;
-        right = list + (size_t)E.map[D->slot_off + k + Kl] * D->item_bytes;
+        sLs = E.map[D->slot_off + k];
+        sRs = E.map[D->slot_off + k + Kl];
+        left = list + (size_t)sLs * D->item_bytes;
+        right = list + (size_t)sRs * D->item_bytes;
         const int C = D->cg;
         __syncwarp();  // the previous unit's readers of the staging buffers are done
         // the children's shared patches, and their metadata (lane c K + g)
@@ -1226,7 +1230,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_BOUND_BLOCKS) k2_lin_bound(Engin
       lin_window_words(D, (const unsigned*)(left + D->off_mask), ent.y, D->lin_chunks <= 64, wi,
                        wv, cb);
       __syncwarp();
-      lin_window<T, K>(E, D, p, k, Kl, wi, wv, cb, left, right, sS, sS + 4 * (size_t)cgmax, ch,
+      lin_window<T, K>(E, D, p, k, Kl, wi, wv, cb, left, right, sLs, sRs, sS, sS + 4 * (size_t)cgmax, ch,
                        ls.sIdx, ls.sMw, ls.sWi, par);
     }
   }

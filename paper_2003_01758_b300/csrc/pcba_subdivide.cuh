@@ -227,11 +227,18 @@ __device__ __forceinline__ float mark_err(float e, float smin, float smax, float
 // Where a marked patch lives: problem, the two child slots, and the list of
 // the current step (steps alternate between two lists).
 struct MarkCtx {
-  int p, kL, kR;
+  int p, kL, kR;       // problem, logical positions of the children
+  unsigned sL, sR;     // their physical slots
   uint4* list;
   unsigned* count;
   unsigned cap;
 };
+
+// A mark: problem, logical child position, physical slot (the refresh runs
+// beside the compaction, which moves map entries), family | patch << 2.
+__device__ __forceinline__ uint4 make_mark(int p, int k, unsigned slot, int fam, int ip) {
+  return make_uint4((unsigned)p, (unsigned)k, slot, (unsigned)fam | ((unsigned)ip << 2));
+}
 
 // Warp-aggregated append of the marked children of this warp's patches
 // (fam 0/1: constraint family, fam 2: the cost patch, ip = patch index).
@@ -245,11 +252,11 @@ __device__ __forceinline__ void append_marks(const MarkCtx& m, bool mL, bool mR,
   const unsigned below = (1u << lane) - 1u;
   if (mL) {
     const unsigned q = base + __popc(bl & below);
-    if (q < m.cap) m.list[q] = make_uint4((unsigned)m.p, (unsigned)m.kL, (unsigned)fam, (unsigned)ip);
+    if (q < m.cap) m.list[q] = make_mark(m.p, m.kL, m.sL, fam, ip);
   }
   if (mR) {
     const unsigned q = base + __popc(bl) + __popc(br & below);
-    if (q < m.cap) m.list[q] = make_uint4((unsigned)m.p, (unsigned)m.kR, (unsigned)fam, (unsigned)ip);
+    if (q < m.cap) m.list[q] = make_mark(m.p, m.kR, m.sR, fam, ip);
   }
 }
 
@@ -512,6 +519,7 @@ __device__ __forceinline__ unsigned right_slot(const Engine& E, long long slot_o
 
 template <typename T, int NMAX>
 __global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) E.plan->kr_par = E.plan->steps_global & 1;  // for k_refresh
   extern __shared__ __align__(16) unsigned char k2stage[];
   __shared__ __align__(16) ProbDesc sD;
   __shared__ int sK, sR, sFtop, sHw;
@@ -554,8 +562,8 @@ __global__ void __launch_bounds__(PCBA_TPB) k2_subdivide(Engine E) {
     char* right = E.arena + D->list_off + (size_t)rslot * D->item_bytes;
     ChildRec* recL = E.rec + D->slot_off + k;
     ChildRec* recR = E.rec + D->slot_off + k + K;
-    const MarkCtx mk{p, k, k + K, E.marks + (size_t)mpar * E.mark_cap, &E.plan->mark_count[mpar],
-                     E.mark_cap};
+    const MarkCtx mk{p, k, k + K, pslot, rslot, E.marks + (size_t)mpar * E.mark_cap,
+                     &E.plan->mark_count[mpar], E.mark_cap};
     if (t == 0 && warp == 0) {
       cost_part<T, NMAX>(cost_geom(D, r), parent, parent, right, recL, recR, (T*)k2stage, mk,
                          cost_thr);
@@ -856,6 +864,7 @@ __device__ __forceinline__ void publish_bounds(int fam, bool any_valid, T (&v)[6
 template <typename T, int NMAX, int NFIX = 0>
 __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, int stage_elems,
                                                         int cpmax) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) E.plan->kr_par = E.plan->steps_global & 1;  // for k_refresh
   constexpr bool RIG = sizeof(T) == 4;
   extern __shared__ __align__(128) unsigned char k2t_smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
@@ -948,7 +957,7 @@ __global__ void __launch_bounds__(256) k2_subdivide_tma(Engine E, int stages, in
     char* right = cx_list + (size_t)rslot * cx_ib;
     ChildRec* recL = E.rec + cx_slot + w.k;
     ChildRec* recR = E.rec + cx_slot + w.k + K;
-    const MarkCtx mk{w.p, w.k, w.k + K, E.marks + (size_t)mpar * E.mark_cap,
+    const MarkCtx mk{w.p, w.k, w.k + K, w.pslot, rslot, E.marks + (size_t)mpar * E.mark_cap,
                      &E.plan->mark_count[mpar], E.mark_cap};
     bool ok = true;
     if (lane == 0) ok = mbar_wait_bounded(&bars[s], parity, E.plan);
