@@ -230,6 +230,26 @@ __device__ __forceinline__ unsigned long long okey(double x) {
   unsigned long long b = (unsigned long long)__double_as_longlong(x);
   return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
 }
+// okey((double)x) of an FP32 x by integer operations alone (the conversion
+// is exact; an FP64 conversion would occupy the SM partition's FP64 unit).
+__device__ __forceinline__ unsigned long long okey_f32(float x) {
+  const unsigned b = __float_as_uint(x), e = (b >> 23) & 0xffu, m = b & 0x7fffffu;
+  unsigned long long d;
+  if (e == 0xffu) {
+    d = (0x7ffull << 52) | ((unsigned long long)m << 29);  // infinities, NaN
+  } else if (e != 0u) {
+    d = ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)m << 29);
+  } else if (m == 0u) {
+    d = 0ull;  // zeros
+  } else {
+    // subnormal: m 2^-149 with its leading bit at p, a normal FP64 value
+    const int p = 31 - __clz(m);
+    d = ((unsigned long long)(p + 874) << 52) |
+        (((unsigned long long)m << (52 - p)) & 0xFFFFFFFFFFFFFull);
+  }
+  d |= (unsigned long long)(b >> 31) << 63;
+  return (d & 0x8000000000000000ull) ? ~d : (d | 0x8000000000000000ull);
+}
 __device__ __forceinline__ double okey_dec(unsigned long long k) {
   unsigned long long b = (k & 0x8000000000000000ull) ? (k & 0x7FFFFFFFFFFFFFFFull) : ~k;
   return __longlong_as_double((long long)b);

@@ -609,8 +609,13 @@ __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int
     const T gn = lin_wmax(gmin[c]);
     ChildRec* rc = E.rec + slot_off + k + (c ? Kl : 0);
     if (lane == 0 && gx > T(-INFINITY)) {
-      atomicMax(&rc->gmaxmax, okey((double)gx));
-      atomicMax(&rc->gminmax, okey((double)gn));
+      if constexpr (RIG) {
+        atomicMax(&rc->gmaxmax, okey_f32((float)gx));
+        atomicMax(&rc->gminmax, okey_f32((float)gn));
+      } else {
+        atomicMax(&rc->gmaxmax, okey((double)gx));
+        atomicMax(&rc->gminmax, okey((double)gn));
+      }
     }
   }
   if constexpr (RIG) {
