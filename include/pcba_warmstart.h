@@ -130,6 +130,15 @@ int pcba_batch_upload(pcba_batch* b, const double* host_coeffs);
 int pcba_batch_upload_rows(pcba_batch* b, const double* host_rows);
 long long pcba_batch_rows_doubles(const pcba_batch* b);
 
+/* Page-locked host memory for the inputs of pcba_batch_upload /
+ * pcba_batch_upload_rows (cudaHostAlloc: copied by DMA at the link's rate,
+ * and the uploads stay asynchronous).  bytes > 0; returns NULL on failure
+ * (the reason in pcba_last_error).  The caller owns the memory and releases
+ * it with pcba_host_free (NULL is accepted) after the last queued copy from
+ * it has completed. */
+void* pcba_host_alloc(size_t bytes);
+int pcba_host_free(void* p);
+
 /* The incumbent seed of problem k in the last solve of the batch: returns 1
  * if a candidate (or the warm start point) was certified feasible, writing it
  * (nvars coordinates) to x and its certified cost bound - the initial p_up -

@@ -1470,6 +1470,26 @@ long long pcba_batch_rows_doubles(const pcba_batch* b) {
   return b ? (long long)PCBA_LIN_STRIDE * b->lin_rows : 0;
 }
 
+void* pcba_host_alloc(size_t bytes) {
+  if (bytes == 0) {
+    fail(PCBA_ERR_INVALID, "bytes must be > 0");
+    return nullptr;
+  }
+  void* p = nullptr;
+  const cudaError_t e = cudaHostAlloc(&p, bytes, cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    fail(PCBA_ERR_CUDA, std::string("cudaHostAlloc: ") + cudaGetErrorString(e));
+    return nullptr;
+  }
+  return p;
+}
+
+int pcba_host_free(void* p) {
+  if (!p) return 0;
+  PCBA_CK(cudaFreeHost(p));
+  return 0;
+}
+
 int pcba_batch_warm_point(const pcba_batch* b, int k, double* x, double* cost) {
   if (!b || k < 0 || k >= b->np) return fail(PCBA_ERR_INVALID, "bad batch or index");
   const ProbState& S = b->h_state[k];

@@ -11,6 +11,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import weakref
 
 import numpy as np
 
@@ -103,6 +104,8 @@ def lib():
         "pcba_batch_linear_stats": ([P, P, P, P], I),
         "pcba_batch_upload_rows": ([P, P], I),
         "pcba_batch_rows_doubles": ([P], LL),
+        "pcba_host_alloc": ([S], P),
+        "pcba_host_free": ([P], I),
         "pcba_batch_polish": ([P, D, D, D, I, P], I),
         "pcba_batch_solve_polished": ([P, D, D, D, D, I, P], I),
         "pcba_batch_destroy": ([P], None),
@@ -156,7 +159,8 @@ def exported_symbols():
             "pcba_mlp_get_params", "pcba_mlp_forward", "pcba_mlp_gradient",
             "pcba_mlp_train_step", "pcba_set_time_limit", "pcba_batch_set_time_limit",
             "pcba_eval_points_f32", "pcba_create_linear", "pcba_get_active",
-            "pcba_batch_linear_stats", "pcba_batch_upload_rows", "pcba_batch_rows_doubles"]
+            "pcba_batch_linear_stats", "pcba_batch_upload_rows", "pcba_batch_rows_doubles",
+            "pcba_host_alloc", "pcba_host_free"]
 
 
 def _check(rc):
@@ -357,6 +361,20 @@ class LinearSolver(Solver):
 
 
 LIN_STRIDE = 8
+
+
+def host_empty(n, dtype=np.float64):
+    """A 1-D numpy array of n elements in page-locked host memory from
+    pcba_host_alloc (freed when the array and its views are gone): the
+    buffer for pcba_batch_upload / pcba_batch_upload_rows."""
+    dt = np.dtype(dtype)
+    nbytes = max(1, int(n) * dt.itemsize)
+    ptr = lib().pcba_host_alloc(nbytes)
+    if not ptr:
+        raise PcbaError(lib().pcba_last_error().decode())
+    buf = (ctypes.c_uint8 * nbytes).from_address(ptr)
+    weakref.finalize(buf, lib().pcba_host_free, ctypes.c_void_p(ptr))
+    return np.frombuffer(buf, dtype=dt, count=int(n))
 
 
 def linear_rows(problems):

@@ -179,3 +179,28 @@ def test_guided_solve_on_linear_families():
         seed = b.warm_point(k)
         if seed is not None:
             assert max(oracle.eval_monomial(gi, seed) for gi in q.ineq) <= 0.0
+
+
+def test_uploads_from_library_pinned_buffers():
+    """New rows and coefficients queued from pcba_host_alloc buffers
+    (pcba.host_empty) give the same results as the batch built from them."""
+    probs = [W.rtd(2100 + k, n_obstacles=n) for k, n in enumerate((64, 300, 37))]
+    b = pcba.Batch([pcba.linear_solver_from_problem(q, pcba.FP32) for q in probs], 3 << 30)
+    ref = b.solve(opt_tol=1e-3)
+    rows = pcba.linear_rows(probs)
+    h = pcba.host_empty(rows.size)
+    h[:] = rows.ravel()
+    assert h.ctypes.data % 16 == 0
+    b.upload_rows(h)
+    again = b.solve(opt_tol=1e-3)
+    for a, r in zip(again, ref):
+        for key in ("status", "lower", "upper", "steps"):
+            assert a[key] == r[key]
+    # other rows (a constraint moved off its obstacle) change the result
+    h2 = pcba.host_empty(rows.size)
+    h2[:] = rows.ravel()
+    h2[0] -= 1e3  # the first constraint of the first problem holds everywhere
+    b.upload_rows(h2)
+    moved = b.solve(opt_tol=1e-3)
+    assert moved[1]["lower"] == ref[1]["lower"] and moved[2]["lower"] == ref[2]["lower"]
+    b.close()
