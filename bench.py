@@ -497,16 +497,17 @@ def main():
     # rows), solve, results out; wall clock ----
     # (page-locked by the library with cudaHostAlloc: torch's pinned buffers
     # measured ~10 GB/s for these copies, the library's ~50 GB/s)
-    hc, hr = host_coeffs(probs), pcba.linear_rows(probs)
+    # the rows are sent without their padding (1 + K doubles per constraint)
+    hc, hr = host_coeffs(probs), pcba.linear_rows_packed(probs)
     h_coeffs = pcba.host_empty(hc.size)
     h_coeffs[:] = hc.ravel()
     h_rows = pcba.host_empty(hr.size)
     h_rows[:] = hr.ravel()
-    assert h_coeffs.size == batch.input_doubles() and h_rows.size == batch.rows_doubles()
+    assert h_coeffs.size == batch.input_doubles() and h_rows.size == batch.rows_packed_doubles()
 
     def e2e_step():
         batch.upload(h_coeffs)
-        batch.upload_rows(h_rows)
+        batch.upload_rows_packed(h_rows)
         return batch.solve(OPT_TOL, EQ_TOL, MAX_ITERS, raw=True)
 
     e2e_step()

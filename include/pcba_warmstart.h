@@ -130,8 +130,16 @@ int pcba_batch_upload(pcba_batch* b, const double* host_coeffs);
 int pcba_batch_upload_rows(pcba_batch* b, const double* host_rows);
 long long pcba_batch_rows_doubles(const pcba_batch* b);
 
-/* Page-locked host memory for the inputs of pcba_batch_upload /
- * pcba_batch_upload_rows (cudaHostAlloc: copied by DMA at the link's rate,
+/* The same rows without the padding: per constraint (offset, weight_0 ..
+ * weight_K-1), 1 + K doubles, for a batch whose problems all have K shared
+ * polynomials (PCBA_ERR_INVALID otherwise, and for a dense batch);
+ * pcba_batch_rows_packed_doubles(b) doubles (0 when the K differ).  The
+ * library pads them on the device. */
+int pcba_batch_upload_rows_packed(pcba_batch* b, const double* host_rows);
+long long pcba_batch_rows_packed_doubles(const pcba_batch* b);
+
+/* Page-locked host memory for the inputs of pcba_batch_upload and the row
+ * uploads (cudaHostAlloc: copied by DMA at the link's rate,
  * and the uploads stay asynchronous).  bytes > 0; returns NULL on failure
  * (the reason in pcba_last_error).  The caller owns the memory and releases
  * it with pcba_host_free (NULL is accepted) after the last queued copy from

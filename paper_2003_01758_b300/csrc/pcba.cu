@@ -1470,6 +1470,42 @@ long long pcba_batch_rows_doubles(const pcba_batch* b) {
   return b ? (long long)PCBA_LIN_STRIDE * b->lin_rows : 0;
 }
 
+// The packed row width 1 + K when every problem of the batch has K shared
+// polynomials, else 0.
+static int packed_row_width(const pcba_batch* b) {
+  if (!b || !b->lin || b->desc.empty()) return 0;
+  const int K = b->desc[0].alpha;
+  for (const ProbDesc& d : b->desc)
+    if (d.alpha != K) return 0;
+  return 1 + K;
+}
+
+long long pcba_batch_rows_packed_doubles(const pcba_batch* b) {
+  return (long long)packed_row_width(b) * (b ? b->lin_rows : 0);
+}
+
+int pcba_batch_upload_rows_packed(pcba_batch* b, const double* host_rows) {
+  if (!b || !host_rows) return fail(PCBA_ERR_INVALID, "batch or host_rows is null");
+  if (!b->lin) return fail(PCBA_ERR_INVALID, "the batch has no linear-family constraints");
+  const int w = packed_row_width(b);
+  if (w == 0) return fail(PCBA_ERR_INVALID, "packed rows need the same K in every problem");
+  const long long n = (long long)w * b->lin_rows;
+  if (n == 0) return 0;
+  // staged in the FP32 row table (64 bytes per row, w <= 5 doubles), which
+  // the conversion below then rewrites
+  double* stage = reinterpret_cast<double*>(b->d_lin32);
+  PCBA_CK(cudaMemcpyAsync(stage, host_rows, sizeof(double) * n, cudaMemcpyHostToDevice,
+                          b->stream));
+  const long long m = (long long)PCBA_LIN_STRIDE * b->lin_rows;
+  const unsigned g = (unsigned)std::min<long long>((m + 255) / 256, 4LL * b->g.sms);
+  k_rows_unpack<<<g, 256, 0, b->stream>>>(stage, b->d_lin64, b->lin_rows, w);
+  k_rows32<<<g, 256, 0, b->stream>>>(b->d_lin64, b->d_lin32, b->lin_rows);
+  PCBA_CK(cudaGetLastError());
+  b->pending_h2d += 8LL * n;
+  b->extra_launches_pending += 2;
+  return 0;
+}
+
 void* pcba_host_alloc(size_t bytes) {
   if (bytes == 0) {
     fail(PCBA_ERR_INVALID, "bytes must be > 0");

@@ -47,6 +47,17 @@ __global__ void k_rows32(const double* rows, float* out, long long nrows) {
   }
 }
 
+// Packed rows (w = 1 + K doubles each) to the padded FP64 layout
+// (PCBA_LIN_STRIDE doubles, zeros after the first w).
+__global__ void k_rows_unpack(const double* packed, double* rows, long long nrows, int w) {
+  const long long n = nrows * PCBA_LIN_STRIDE;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (long long)gridDim.x * blockDim.x) {
+    const long long q = i / PCBA_LIN_STRIDE, j = i - q * PCBA_LIN_STRIDE;
+    rows[i] = j < w ? packed[q * w + j] : 0.0;
+  }
+}
+
 #define PCBA_EVAL_CHUNK 8
 #define PCBA_MAX_CAND 1024
 #define PCBA_CAND_TPB 512  // threads of k_cand_first

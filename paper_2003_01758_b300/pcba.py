@@ -104,6 +104,8 @@ def lib():
         "pcba_batch_linear_stats": ([P, P, P, P], I),
         "pcba_batch_upload_rows": ([P, P], I),
         "pcba_batch_rows_doubles": ([P], LL),
+        "pcba_batch_upload_rows_packed": ([P, P], I),
+        "pcba_batch_rows_packed_doubles": ([P], LL),
         "pcba_host_alloc": ([S], P),
         "pcba_host_free": ([P], I),
         "pcba_batch_polish": ([P, D, D, D, I, P], I),
@@ -160,7 +162,8 @@ def exported_symbols():
             "pcba_mlp_train_step", "pcba_set_time_limit", "pcba_batch_set_time_limit",
             "pcba_eval_points_f32", "pcba_create_linear", "pcba_get_active",
             "pcba_batch_linear_stats", "pcba_batch_upload_rows", "pcba_batch_rows_doubles",
-            "pcba_host_alloc", "pcba_host_free"]
+            "pcba_host_alloc", "pcba_host_free", "pcba_batch_upload_rows_packed",
+            "pcba_batch_rows_packed_doubles"]
 
 
 def _check(rc):
@@ -390,6 +393,16 @@ def linear_rows(problems):
     return np.ascontiguousarray(np.concatenate(blocks), dtype=np.float64)
 
 
+def linear_rows_packed(problems):
+    """Host layout of pcba_batch_upload_rows_packed: per constraint (offset,
+    weights...), 1 + K doubles."""
+    blocks = []
+    for prob in problems:
+        _, weight, offset = prob.meta["linear"]
+        blocks.append(np.column_stack([offset, weight]).ravel())
+    return np.ascontiguousarray(np.concatenate(blocks), dtype=np.float64)
+
+
 def linear_solver_from_problem(prob, precision=FP32):
     """LinearSolver of a workloads problem that carries its linear form
     (meta["linear"] = (shared, weight, offset))."""
@@ -533,6 +546,15 @@ class Batch:
         constraint rows (see linear_rows)."""
         assert host_rows.dtype == np.float64 and host_rows.size == self.rows_doubles()
         _check(lib().pcba_batch_upload_rows(self._b, _p(host_rows)))
+
+    def upload_rows_packed(self, host_rows):
+        """pcba_batch_upload_rows_packed: the rows without padding (see
+        linear_rows_packed)."""
+        assert host_rows.dtype == np.float64 and host_rows.size == self.rows_packed_doubles()
+        _check(lib().pcba_batch_upload_rows_packed(self._b, _p(host_rows)))
+
+    def rows_packed_doubles(self) -> int:
+        return int(lib().pcba_batch_rows_packed_doubles(self._b))
 
     def rows_doubles(self) -> int:
         return int(lib().pcba_batch_rows_doubles(self._b))

@@ -204,3 +204,23 @@ def test_uploads_from_library_pinned_buffers():
     moved = b.solve(opt_tol=1e-3)
     assert moved[1]["lower"] == ref[1]["lower"] and moved[2]["lower"] == ref[2]["lower"]
     b.close()
+
+
+def test_packed_rows_equal_padded_rows():
+    """pcba_batch_upload_rows_packed: 1 + K doubles per constraint, padded on
+    the device, gives the lists and results of the padded upload."""
+    probs = [W.rtd(2200 + k, n_obstacles=n) for k, n in enumerate((128, 40))]
+    b = pcba.Batch([pcba.linear_solver_from_problem(q, pcba.FP32) for q in probs], 2 << 30)
+    assert b.rows_packed_doubles() * 8 == b.rows_doubles() * 4  # K = 3: 4 of 8 doubles
+    packed = pcba.linear_rows_packed(probs)
+    h = pcba.host_empty(packed.size)
+    h[:] = packed
+    b.upload_rows(pcba.linear_rows(probs))
+    ref = b.solve(opt_tol=1e-3)
+    b.upload_rows_packed(h)
+    got = b.solve(opt_tol=1e-3)
+    for a, r in zip(got, ref):
+        for key in ("status", "lower", "upper", "steps"):
+            assert a[key] == r[key]
+        np.testing.assert_array_equal(a["x"], r["x"])
+    b.close()
