@@ -56,7 +56,7 @@
 //                  the child records.  The children's shared patches go to the
 //                  copy of the other parity, so the parent's stay readable.
 //                  An item whose live chunks (chunks of PCBA_LIN_WORDS
-//                  activity words with an active constraint; at most 4) hold
+//                  activity words with an active constraint; at most 8) hold
 //                  at most PCBA_LIN_LIGHT_MAX active constraints is bounded
 //                  here from the children still staged in shared memory; the
 //                  live chunks of the other items are grouped into windows of
@@ -210,23 +210,23 @@ __device__ __forceinline__ void lin_mark(const Engine& E, int mpar, int p, int s
 // Per-warp buffers of the constraint bounds, after the staged patches.
 struct LinScratch {
   unsigned char* sCh;     // the children's metadata (a LinChildren), 256 bytes
-  unsigned* sMw;          // the children's words of a window, [2][32]
-  int* sWi;               // the window's word indices, [32]
+  unsigned* sMw;          // the children's words of a window, [2][64]
+  int* sWi;               // the window's word indices, [64] (two per lane)
   unsigned* sWin;         // the windows of an item, [64]
   unsigned short* sIdx;   // compacted constraints, [PCBA_LIN_IDX]
   unsigned short* sCnt;   // active constraints per live chunk, [64]
   unsigned char* sChunk;  // the live chunks, [64]
 };
 __host__ __device__ constexpr size_t lin_scratch_bytes() {
-  return 256 + 4 * 64 + 4 * 32 + 4 * 64 + 2 * PCBA_LIN_IDX + 2 * 64 + 64;
+  return 256 + 4 * 128 + 4 * 64 + 4 * 64 + 2 * PCBA_LIN_IDX + 2 * 64 + 64;
 }
 // base: 16-byte aligned
 __device__ __forceinline__ LinScratch lin_scratch(unsigned char* base) {
   LinScratch s;
   s.sCh = base;
   s.sMw = (unsigned*)(base + 256);
-  s.sWi = (int*)(s.sMw + 64);
-  s.sWin = (unsigned*)(s.sWi + 32);
+  s.sWi = (int*)(s.sMw + 128);
+  s.sWin = (unsigned*)(s.sWi + 64);
   s.sIdx = (unsigned short*)(s.sWin + 64);
   s.sCnt = s.sIdx + PCBA_LIN_IDX;
   s.sChunk = (unsigned char*)(s.sCnt + 64);
@@ -240,42 +240,52 @@ __host__ __device__ constexpr size_t lin_bound_warp_bytes(int cgmax) {
   return (8 * (size_t)cgmax * sizeof(T) + 15) / 16 * 16 + lin_scratch_bytes();
 }
 
-// A window, as lane q's word: its index wi (-1: none), value wv and summary
-// bit cb (0 without summaries).  Two forms (chunk t0 in bits 0..15):
+// A window, as lane q's two word slots q and q + 32: each slot's word index
+// wi (-1: none), value wv and summary bit cb (0 without summaries).  Two
+// forms (chunk t0 in bits 0..15):
 //   bit 31 clear: bit j of bits 16..30 says chunk t0 + j belongs to it (at
-//     most 4 chunks); lane q takes word q % 8 of its (q / 8)-th chunk;
+//     most PCBA_LIN_WCHUNKS chunks); slot s takes word s % 8 of its
+//     (s / 8)-th chunk;
 //   bit 31 set: words a .. b-1 of chunk t0 (a in bits 16..18, b in bits
 //     19..22), for a chunk with more active constraints than one window
-//     takes; lane q takes word a + q.
+//     takes; slot q (of lane q) takes word a + q.
+#define PCBA_LIN_WCHUNKS 8
 __device__ __forceinline__ unsigned lin_word_window(int t0, int a, int b) {
   return (unsigned)t0 | ((unsigned)a << 16) | ((unsigned)b << 19) | 0x80000000u;
 }
 __device__ __forceinline__ void lin_window_words(const ProbDesc* D, const unsigned* pmask,
-                                                 unsigned win, bool summ, int& wi, unsigned& wv,
-                                                 unsigned long long& cb) {
+                                                 unsigned win, bool summ, int (&wi)[2],
+                                                 unsigned (&wv)[2], unsigned long long (&cb)[2]) {
   const int lane = threadIdx.x & 31;
-  wi = -1;
-  wv = 0u;
-  cb = 0ull;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    wi[h] = -1;
+    wv[h] = 0u;
+    cb[h] = 0ull;
+  }
   if (win & 0x80000000u) {
     const int t = (int)(win & 0xFFFFu), a = (int)((win >> 16) & 7u), b = (int)((win >> 19) & 15u);
     const int w = t * PCBA_LIN_WORDS + a + lane;
     if (lane < b - a && w < D->mwords) {
-      wi = w;
-      wv = pmask[w];
-      cb = summ ? 1ull << t : 0ull;
+      wi[0] = w;
+      wv[0] = pmask[w];
+      cb[0] = summ ? 1ull << t : 0ull;
     }
     return;
   }
-  unsigned m = (win >> 16) & 0x7FFFu;
-  for (int i = 0; i < (lane >> 3); ++i) m &= m - 1u;
-  if (m != 0u) {
-    const int t = (int)(win & 0xFFFFu) + __ffs(m) - 1;
-    const int w = t * PCBA_LIN_WORDS + (lane & 7);
-    if (w < D->mwords) {
-      wi = w;
-      wv = pmask[w];
-      cb = summ ? 1ull << t : 0ull;
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int sl = lane + 32 * h;
+    unsigned m = (win >> 16) & 0x7FFFu;
+    for (int i = 0; i < (sl >> 3); ++i) m &= m - 1u;
+    if (m != 0u) {
+      const int t = (int)(win & 0xFFFFu) + __ffs(m) - 1;
+      const int w = t * PCBA_LIN_WORDS + (sl & 7);
+      if (w < D->mwords) {
+        wi[h] = w;
+        wv[h] = pmask[w];
+        cb[h] = summ ? 1ull << t : 0ull;
+      }
     }
   }
 }
@@ -379,22 +389,24 @@ __device__ __forceinline__ void lin_kappa(const float* hv, const float* lv, cons
   ekap = __fadd_ru(__fmul_ru(A, 0x1p-40f), (float)(8 * K + 2) * 0x1p-149f);
 }
 
-// A window of up to 32 of parent item k's activity words (problem p, list
-// length Kl): lane q holds the index wi of one of the item's words (-1:
-// none), its value word and its chunk's summary bit cbit (0 without
-// summaries).  The window holds at most PCBA_LIN_IDX active constraints (a
-// single chunk at most PCBA_LIN_WORDS x 32, several at most PCBA_LIN_WIN, a
-// light item at most PCBA_LIN_LIGHT_MAX).  They are compacted and bounded on
-// both children (items left / right in slots slotL / slotR, shared patches
-// staged at sL / sR, [C][4]); the children's words and their chunks' summary bits are written
-// and the bound maxima go to the child records.  One warp; sIdx, sMw (the
-// children's words, 2 x 32) and sWi (the 32 word indices) are its buffers.
+// A window of up to 64 of parent item k's activity words (problem p, list
+// length Kl): lane q holds two word slots (q and q + 32), each the index wi
+// of one of the item's words (-1: none), its value word and its chunk's
+// summary bit cbit (0 without summaries).  The window holds at most
+// PCBA_LIN_IDX active constraints (a single chunk at most PCBA_LIN_WORDS x 32,
+// several at most PCBA_LIN_WIN, a light item at most PCBA_LIN_LIGHT_MAX).
+// They are compacted and bounded on both children (items left / right in
+// slots slotL / slotR, shared patches staged at sL / sR, [C][4]); the
+// children's words and their chunks' summary bits are written and the bound
+// maxima go to the child records.  One warp; sIdx, sMw (the children's
+// words, 2 x 64) and sWi (the 64 word indices) are its buffers.
 static_assert(PCBA_LIN_WORDS * 32 <= PCBA_LIN_IDX && PCBA_LIN_WIN <= PCBA_LIN_IDX &&
                   PCBA_LIN_LIGHT_MAX <= PCBA_LIN_IDX,
               "a window's active constraints fit the compaction buffer");
 template <typename T, int K>
-__device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int Kl, int wi,
-                           unsigned word, unsigned long long cbit, char* left, char* right,
+__device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int Kl,
+                           const int (&wi)[2], const unsigned (&word)[2],
+                           const unsigned long long (&cbit)[2], char* left, char* right,
                            unsigned slotL, unsigned slotR,
                            const T* sL, const T* sR, const LinChildren<T, K>& ch,
                            unsigned short* sIdx, unsigned* sMw, int* sWi, int par) {
@@ -407,8 +419,8 @@ __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int
   unsigned* rm = (unsigned*)(right + D->off_mask);
   unsigned long long* sumL = (unsigned long long*)(left + D->off_sum) + (par ^ 1);
   unsigned long long* sumR = (unsigned long long*)(right + D->off_sum) + (par ^ 1);
-  if (wi < 0) word = 0u;
-  const unsigned cnt = __popc(word);
+  const unsigned w0 = wi[0] >= 0 ? word[0] : 0u, w1 = wi[1] >= 0 ? word[1] : 0u;
+  const unsigned cnt = __popc(w0) + __popc(w1);
   unsigned incl = cnt;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -419,13 +431,15 @@ __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int
   if (na == 0) {
     // no active constraint here: the children's words are zero (the left
     // child shares the parent's, already zero)
-    if (wi >= 0) rm[wi] = 0u;
+    if (wi[0] >= 0) rm[wi[0]] = 0u;
+    if (wi[1] >= 0) rm[wi[1]] = 0u;
     return;
   }
   __syncwarp();  // earlier readers of the buffers are done
-  sWi[lane] = wi;
-  sMw[lane] = 0u;
-  sMw[32 + lane] = 0u;
+  sWi[lane] = wi[0];
+  sWi[32 + lane] = wi[1];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) sMw[32 * i + lane] = 0u;  // [child][slot]
   T gmax[2] = {T(-INFINITY), T(-INFINITY)}, gmin[2] = {T(-INFINITY), T(-INFINITY)};
   bool mark[2] = {false, false};
   unsigned nfull = 0;  // coefficient-range evaluations of this lane
@@ -446,11 +460,15 @@ __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int
     vmax[0][q] = vmax[1][q] = T(-INFINITY);
   }
   {
-    unsigned pos = incl - cnt, bits = word;
-    while (bits) {
-      const int b = __ffs(bits) - 1;
-      bits &= bits - 1u;
-      sIdx[pos++] = (unsigned short)(lane * 32 + b);
+    unsigned pos = incl - cnt;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      unsigned bits = h ? w1 : w0;
+      while (bits) {
+        const int b = __ffs(bits) - 1;
+        bits &= bits - 1u;
+        sIdx[pos++] = (unsigned short)((lane + 32 * h) * 32 + b);
+      }
     }
   }
   __syncwarp();
@@ -558,7 +576,7 @@ __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int
       const bool sat = up <= T(0);
       const bool inf = dn > T(0);
       if (!sat) {
-        atomicOr(&sMw[c * 32 + (li >> 5)], 1u << (li & 31));
+        atomicOr(&sMw[c * 64 + (li >> 5)], 1u << (li & 31));
         gmax[c] = max(gmax[c], up);
         gmin[c] = max(gmin[c], dn);
       }
@@ -571,13 +589,17 @@ __device__ void lin_window(const Engine& E, const ProbDesc* D, int p, int k, int
       }
     }
   }
-  if (wi >= 0) {
-    pm[wi] = sMw[lane];       // left child: in place (this window's words)
-    rm[wi] = sMw[32 + lane];  // right child
-  }
-  // the summary bits of the chunks that keep an active constraint
-  const unsigned long long kl = (wi >= 0 && sMw[lane] != 0u) ? cbit : 0ull;
-  const unsigned long long kr = (wi >= 0 && sMw[32 + lane] != 0u) ? cbit : 0ull;
+  unsigned long long kl = 0ull, kr = 0ull;
+#pragma unroll
+  for (int h = 0; h < 2; ++h)
+    if (wi[h] >= 0) {
+      const unsigned vl = sMw[lane + 32 * h], vr = sMw[64 + lane + 32 * h];
+      pm[wi[h]] = vl;  // left child: in place (this window's words)
+      rm[wi[h]] = vr;  // right child
+      // the summary bits of the chunks that keep an active constraint
+      if (vl != 0u) kl |= cbit[h];
+      if (vr != 0u) kr |= cbit[h];
+    }
   const unsigned long long keepL =
       ((unsigned long long)__reduce_or_sync(0xffffffffu, (unsigned)(kl >> 32)) << 32) |
       __reduce_or_sync(0xffffffffu, (unsigned)kl);
@@ -696,10 +718,10 @@ __device__ __forceinline__ void lin_fibre(const T* src, T* dL, T* dR, int sst, L
 // NFIX > 0: every patch of the batch has degree NFIX along every axis (a
 // smaller kernel body); 0: any degree up to 16.
 // Resident blocks per SM the register allocation of the two kernels aims at
-// (the split kernel's latency chains gain more from a third block's warps
-// than its few spills cost).
+// (128 registers: with two word slots per lane, a third block's 80 registers
+// made the split kernel spill more than its extra warps gained).
 #ifndef PCBA_LIN_SPLIT_BLOCKS
-#define PCBA_LIN_SPLIT_BLOCKS 3
+#define PCBA_LIN_SPLIT_BLOCKS 2
 #endif
 #ifndef PCBA_LIN_BOUND_BLOCKS
 #define PCBA_LIN_BOUND_BLOCKS 2
@@ -1012,10 +1034,10 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
       // ---- the constraints.  The children's summaries start empty (each
       // window sets the bits of its chunks that keep an active constraint)
       // and their words of chunks without one are zero.  An item whose live
-      // chunks (at most 4) hold at most PCBA_LIN_LIGHT_MAX active
-      // constraints is bounded here, from the children still staged.  The
-      // live chunks of the other items are grouped into windows (at most 4
-      // chunks within 16 consecutive ones, at most PCBA_LIN_WIN active
+      // chunks (at most PCBA_LIN_WCHUNKS) hold at most PCBA_LIN_LIGHT_MAX
+      // active constraints is bounded here, from the children still staged.
+      // The live chunks of the other items are grouped into windows (at most
+      // PCBA_LIN_WCHUNKS chunks within 16 consecutive ones, at most PCBA_LIN_WIN active
       // constraints unless a single chunk); a single window stays here,
       // several are queued for k2_lin_bound (those the full queue refuses
       // stay here too).
@@ -1040,24 +1062,30 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
         // the queue refused
         int mode = 0, nwin = 0, nq = 0;
         unsigned qb = 0u;
-        int lwi = -1;
-        unsigned lwv = 0u;
-        unsigned long long lcb = 0ull;
-        if (nlive > 0 && summ && nlive <= 4) {
-          // lane q: word q % 8 of the (q / 8)-th live chunk
-          const int j = lane >> 3;
-          if (j < nlive) {
-            unsigned long long m = psum;
-            for (int i2 = 0; i2 < j; ++i2) m &= m - 1ull;
-            const int t = __ffsll((long long)m) - 1;
-            const int w = t * PCBA_LIN_WORDS + (lane & 7);
-            if (w < mwords) {
-              lwi = w;
-              lwv = pmask[w];
-              lcb = 1ull << t;
+        int lwi[2] = {-1, -1};
+        unsigned lwv[2] = {0u, 0u};
+        unsigned long long lcb[2] = {0ull, 0ull};
+        if (nlive > 0 && summ && nlive <= PCBA_LIN_WCHUNKS) {
+          // word slot s (q and q + 32 of lane q): word s % 8 of the (s / 8)-th
+          // live chunk
+#pragma unroll
+          for (int h = 0; h < 2; ++h) {
+            const int j = (lane + 32 * h) >> 3;
+            if (j < nlive) {
+              unsigned long long m = psum;
+              for (int i2 = 0; i2 < j; ++i2) m &= m - 1ull;
+              const int t = __ffsll((long long)m) - 1;
+              const int w = t * PCBA_LIN_WORDS + (lane & 7);
+              if (w < mwords) {
+                lwi[h] = w;
+                lwv[h] = pmask[w];
+                lcb[h] = 1ull << t;
+              }
             }
           }
-          if (__reduce_add_sync(0xffffffffu, (unsigned)__popc(lwv)) <= PCBA_LIN_LIGHT_MAX) mode = 1;
+          if (__reduce_add_sync(0xffffffffu, (unsigned)(__popc(lwv[0]) + __popc(lwv[1]))) <=
+              PCBA_LIN_LIGHT_MAX)
+            mode = 1;
         }
         if (nlive > 0 && summ && mode == 0) {
           // the live chunks in order and their active constraints
@@ -1105,7 +1133,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
               unsigned mask = 1u, cw = ls.sCnt[j];
               int nch = 1;
               ++j;
-              while (j < nlive && nch < 4 && ls.sChunk[j] - t0 < 15 &&
+              while (j < nlive && nch < PCBA_LIN_WCHUNKS && ls.sChunk[j] - t0 < 15 &&
                      cw + ls.sCnt[j] <= (unsigned)PCBA_LIN_WIN) {
                 mask |= 1u << (ls.sChunk[j] - t0);
                 cw += ls.sCnt[j];
@@ -1139,9 +1167,9 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
           mode = 3;
         }
         for (int i2 = 0; mode != 0; ++i2) {
-          int wi = lwi;
-          unsigned wv = lwv;
-          unsigned long long cb = lcb;
+          int wi[2] = {lwi[0], lwi[1]};
+          unsigned wv[2] = {lwv[0], lwv[1]};
+          unsigned long long cb[2] = {lcb[0], lcb[1]};
           if (mode == 1) {
             if (i2 > 0) break;
           } else if (mode == 2) {
@@ -1229,9 +1257,9 @@ __global__ void __launch_bounds__(256, PCBA_LIN_BOUND_BLOCKS) k2_lin_bound(Engin
           ch.Ol[c][g] = vOl;
         }
       }
-      int wi;
-      unsigned wv;
-      unsigned long long cb;
+      int wi[2];
+      unsigned wv[2];
+      unsigned long long cb[2];
       lin_window_words(D, (const unsigned*)(left + D->off_mask), ent.y, D->lin_chunks <= 64, wi,
                        wv, cb);
       __syncwarp();
