@@ -207,18 +207,29 @@ __device__ __forceinline__ void lin_mark(const Engine& E, int mpar, int p, int s
 // k2_lin_bound: one warp per (parent item, chunk of activity words)
 // ---------------------------------------------------------------------------
 
+// Windows one item may form: every chunk with more active constraints than a
+// window takes is cut into word ranges while this many fit (so that an item
+// with all of 4096 constraints active, at the root, gives 64 windows of 64
+// rather than whole chunks of 256 that one warp would walk alone).  A cut
+// chunk gives at most 4 windows (a word holds at most 32 of a window's 64),
+// any other at most one, and items with summaries have at most 64 chunks, so
+// 4 x 64 entries never overflow.
+#define PCBA_LIN_MAXWIN 256
+static_assert(PCBA_LIN_MAXWIN >= 4 * 64 && PCBA_LIN_WIN >= 64,
+              "the window list of an item holds every window it can form");
+
 // Per-warp buffers of the constraint bounds, after the staged patches.
 struct LinScratch {
   unsigned char* sCh;     // the children's metadata (a LinChildren), 256 bytes
   unsigned* sMw;          // the children's words of a window, [2][64]
   int* sWi;               // the window's word indices, [64] (two per lane)
-  unsigned* sWin;         // the windows of an item, [64]
+  unsigned* sWin;         // the windows of an item, [PCBA_LIN_MAXWIN]
   unsigned short* sIdx;   // compacted constraints, [PCBA_LIN_IDX]
   unsigned short* sCnt;   // active constraints per live chunk, [64]
   unsigned char* sChunk;  // the live chunks, [64]
 };
 __host__ __device__ constexpr size_t lin_scratch_bytes() {
-  return 256 + 4 * 128 + 4 * 64 + 4 * 64 + 2 * PCBA_LIN_IDX + 2 * 64 + 64;
+  return 256 + 4 * 128 + 4 * 64 + 4 * PCBA_LIN_MAXWIN + 2 * PCBA_LIN_IDX + 2 * 64 + 64;
 }
 // base: 16-byte aligned
 __device__ __forceinline__ LinScratch lin_scratch(unsigned char* base) {
@@ -227,7 +238,7 @@ __device__ __forceinline__ LinScratch lin_scratch(unsigned char* base) {
   s.sMw = (unsigned*)(base + 256);
   s.sWi = (int*)(s.sMw + 128);
   s.sWin = (unsigned*)(s.sWi + 64);
-  s.sIdx = (unsigned short*)(s.sWin + 64);
+  s.sIdx = (unsigned short*)(s.sWin + PCBA_LIN_MAXWIN);
   s.sCnt = s.sIdx + PCBA_LIN_IDX;
   s.sChunk = (unsigned char*)(s.sCnt + 64);
   return s;
@@ -1113,7 +1124,7 @@ __global__ void __launch_bounds__(256, PCBA_LIN_SPLIT_BLOCKS) k2_lin_split(Engin
             int j = 0;
             while (j < nlive) {
               const int t0 = ls.sChunk[j];
-              if (ls.sCnt[j] > PCBA_LIN_WIN && nwin + PCBA_LIN_WORDS <= 64) {
+              if (ls.sCnt[j] > PCBA_LIN_WIN && nwin + PCBA_LIN_WORDS <= PCBA_LIN_MAXWIN) {
                 int a = 0;
                 unsigned cw = 0u;
                 for (int b = 0; b < PCBA_LIN_WORDS; ++b) {

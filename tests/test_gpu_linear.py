@@ -224,3 +224,20 @@ def test_packed_rows_equal_padded_rows():
             assert a[key] == r[key]
         np.testing.assert_array_equal(a["x"], r["x"])
     b.close()
+
+
+def test_items_with_many_chunks_are_windowed_soundly():
+    """12,000 obstacles: 47 chunks of 256 constraints, many with more active
+    constraints at the first steps than one window takes, so that they are cut
+    into word-range windows (up to four each, the window list sized for 64
+    such chunks).  The linear family in FP32 certifies an interval that
+    overlaps the dense FP64 solve's (an independent path), and its point is
+    feasible."""
+    p = W.rtd(2300, n_obstacles=12000)
+    g = lin(p, pcba.FP32).solve(opt_tol=1e-3, mem_cap=4 << 30)
+    d = pcba.solver_from_problem(p, pcba.FP64).solve(opt_tol=1e-3, mem_cap=8 << 30)
+    assert g["status"] == d["status"], (g["status"], d["status"])
+    if d["status"] == pcba.OPTIMAL:
+        assert g["upper"] - g["lower"] <= 1e-3
+        assert g["lower"] <= d["upper"] and d["lower"] <= g["upper"], (g, d)
+        assert max(oracle.eval_monomial(gi, g["x"]) for gi in p.ineq) <= 0.0
