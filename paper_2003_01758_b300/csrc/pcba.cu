@@ -31,6 +31,9 @@
 #ifndef PCBA_K3_BLOCKS_PER_SM
 #define PCBA_K3_BLOCKS_PER_SM 0
 #endif
+#ifndef PCBA_KR_BLOCKS_PER_SM
+#define PCBA_KR_BLOCKS_PER_SM 8
+#endif
 #ifndef PCBA_K4_BLOCKS_PER_SM
 #define PCBA_K4_BLOCKS_PER_SM 1
 #endif
@@ -500,8 +503,9 @@ int setup_kernels(pcba_batch* b) {
     PCBA_CK(cudaFuncSetAttribute(k_refresh, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  (int)g.kr_smem));
     PCBA_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_refresh, PCBA_KRB, g.kr_smem));
-    // marks are tens to thousands per step: up to 4 resident blocks per SM
-    g.kr_grid = std::max(1, std::min(occ, 4)) * g.sms;
+    // marks are tens to thousands per step: up to PCBA_KR_BLOCKS_PER_SM
+    // resident blocks per SM
+    g.kr_grid = std::max(1, std::min(occ, PCBA_KR_BLOCKS_PER_SM)) * g.sms;
     double binom[17 * 17], binom_inv[17 * 17];
     for (int n = 0; n < 17; ++n)
       for (int k = 0; k < 17; ++k) {
