@@ -266,9 +266,10 @@ int pcba_batch_launch_bytes(const pcba_batch* b, double* bytes, int max_launches
  * bytes the call copied host->device and device->host. */
 int pcba_batch_stats(const pcba_batch* b, long long* loop_iters, long long* kernel_launches,
                      long long* h2d_bytes, long long* d2h_bytes);
-/* FP32 mode: patches marked for a refresh from the FP64 monomials during the
- * last solve (their error bound changed a classification) and patches actually
- * refreshed (marked children that survived the cut-off). */
+/* FP32 mode: marks for a refresh from the FP64 monomials during the last
+ * solve (a patch, or all shared patches of a linear-family child, whose error
+ * bound changed a classification) and patches recomputed (K per linear-family
+ * mark; marks of patches larger than the refresh buffers are skipped). */
 int pcba_batch_refresh_stats(const pcba_batch* b, long long* marked, long long* refreshed);
 /* Linear families: constraint bounds computed by the last solve - pairs of
  * (child box, active constraint), and how many of them needed the range of
