@@ -923,12 +923,9 @@ __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan,
     // least slot of a child that attains p_up: integer reductions, no FP64
     unsigned long long kmin = ~0ull;
     unsigned long long smin = ~0ull;
+    ChildRec* R = E.rec + D->slot_off + c;
     if (c < twoK) {
-      ChildRec* R = E.rec + D->slot_off + c;
       const ChildRec rc = load_rec_cg(R);
-      unsigned long long* w = (unsigned long long*)R;
-#pragma unroll
-      for (int q = 0; q < (int)(sizeof(ChildRec) / 8); ++q) w[q] = 0ull;  // identity for the next step
       // Def. 3 and the cut-off on the keys: "value > 0" for a max-reduced
       // field is key > okey(+0.0); pmin <= p_up is a key compare once a zero
       // p_up is taken as +0.0 (-0.0 <= +0.0 either way)
@@ -953,6 +950,14 @@ __device__ __forceinline__ void classify_phase(const Engine& E, unsigned* sscan,
       s_last = old == (unsigned)ntiles - 1;
     }
     __syncthreads();
+    // the record back to the identity for the next step, after the fence
+    // above (which need not wait for these stores: nothing in this kernel
+    // reads the records again)
+    if (c < twoK) {
+      unsigned long long* w = (unsigned long long*)R;
+#pragma unroll
+      for (int q = 0; q < (int)(sizeof(ChildRec) / 8); ++q) w[q] = 0ull;
+    }
     if (s_last) finalize_problem(E, p, sscan);
     __syncthreads();
     if (threadIdx.x == 0) {
