@@ -996,15 +996,17 @@ __device__ __forceinline__ void index_phase(const Engine& E) {
     const int twoK = S->twoK, K_save = S->K_save;
     const int c = tile * PCBA_TPB + threadIdx.x;
     if (c >= twoK) continue;
+    // (the child's slot is read with its flag, before it is known to be needed)
     const unsigned fr = E.flagrank[D->slot_off + c];
+    const unsigned slot = E.map[D->slot_off + c];
+    const int ftop_push = S->ftop_push;
     const unsigned keep = fr >> 31;
     const int grank = (int)(E.tilecnt[D->tile_off + tile] + (fr & 0x7FFFFFFFu));
     if (c < K_save && !keep) E.hole[D->slot_off + (c - grank)] = (unsigned)c;
     if (c >= K_save && keep) E.filler[D->slot_off + (K_save - 1 - grank)] = (unsigned)c;
     // the slot of an eliminated child goes back on the free stack (grank =
     // kept children before c, so c - grank eliminated ones precede it)
-    if (running && !keep)
-      E.fstack[D->slot_off + S->ftop_push + (c - grank)] = E.map[D->slot_off + c];
+    if (running && !keep) E.fstack[D->slot_off + ftop_push + (c - grank)] = slot;
   }
 }
 
