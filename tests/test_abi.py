@@ -106,3 +106,18 @@ def test_failed_device_allocation_reports_oom(lib, monkeypatch):
     with pytest.raises(pcba.PcbaError, match="ERR_OOM"):
         pcba.Batch([s], 1 << 24)
     assert s.item_bytes() > 0
+
+
+def test_host_alloc_argument_checks(lib):
+    """pcba_host_alloc rejects a zero size (NULL, with the reason), and
+    pcba_host_free accepts NULL; both without touching a device."""
+    assert not lib.pcba_host_alloc(0)
+    assert b"bytes" in lib.pcba_last_error()
+    assert lib.pcba_host_free(None) == 0
+
+
+def test_packed_row_upload_argument_checks(lib):
+    """pcba_batch_upload_rows_packed rejects null arguments before any device
+    work; the packed size of a null batch is 0."""
+    assert lib.pcba_batch_upload_rows_packed(None, None) != 0
+    assert lib.pcba_batch_rows_packed_doubles(None) == 0
